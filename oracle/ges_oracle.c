@@ -1,0 +1,815 @@
+/*
+ * FP64 reference ("oracle") of the Gaussian-enhanced Surfels (GES) render.
+ *
+ * TEST INFRASTRUCTURE.  Only the test-suite, the smoke check and the CPU
+ * baseline of the benchmark call this code.  It shares nothing with the CUDA
+ * path: no headers, no helpers, no constants.  It is deliberately plain: every
+ * pixel is evaluated straight from the paper's definitions in double
+ * precision, with no blocking, fusion or reordering beyond skipping pixels
+ * that lie outside a primitive's conservative screen rectangle.
+ *
+ * What it follows:
+ *   Sec. 3        surfel = opaque disc in its local XY plane, placed by scale,
+ *                 rotation, translation; colour = SH at the direction from the
+ *                 surfel centre to the camera (Eq. 1).
+ *   Sec. 4.1      opaque extent: G(x,y) >= 1/255, i.e. x^2+y^2 <= 2 ln 255
+ *                 (Eq. 6-7 with w_i = 255).
+ *   Sec. 3        pass 1: per-pixel z-buffer of surfel fragments -> C_s, D_s.
+ *   Sec. 3        pass 2: C_G, W_G accumulated over Gaussians passing the
+ *                 depth test d_i < D_s + eps (Eq. 2-3) with the 2D opacity of
+ *                 Eq. 4, clamped to zero below 1/255.
+ *   Sec. 3        composite C = (C_s W_s + C_G)/(W_s + W_G), W_s = 1 (Eq. 5).
+ *   Sec. 5        eps_i = (5/D) sum_j s_ij with D = 3.
+ *   Sec. 7 (ablation) "only surfels" C = C_s, "only Gaussians" C = C_G/W_G.
+ *   Sec. 4.2      joint stage: gradients w.r.t. Gaussian p, s, r, sigma, SH
+ *                 and surfel SH, surfel geometry fixed.
+ * Readings where the paper is silent (camera model, SH basis, low-pass filter,
+ * tie-break, pixel centres) are the ones listed in the design notes; the
+ * comments at each use restate them.
+ *
+ * Parity status: every function below is pinned by the CPU tests against
+ * closed forms, library routines, invariants, brute force or finite
+ * differences; nothing here is "parity unpinned".
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+    int64_t n_surfels, n_gaussians;
+    int32_t sh_degree;
+    const double *s_pos, *s_rot, *s_scale, *s_sh;            /* [N,3] [N,4] [N,2] [N,K,3] */
+    const double *g_pos, *g_rot, *g_scale, *g_opac, *g_sh;   /* [M,3] [M,4] [M,3] [M] [M,K,3] */
+} ora_scene;
+
+typedef struct {
+    int32_t width, height;
+    double fx, fy, cx, cy;
+    double w2c[12];      /* row-major [R|t], world -> camera */
+    double znear;
+    double bg[3];
+} ora_camera;
+
+typedef struct {
+    int32_t eps_mode;    /* 0: eps_i = eps_factor/3 * (s1+s2+s3); 1: 0; 2: eps_value */
+    double eps_value, eps_factor, lowpass, alpha_min, surfel_r2;
+    int32_t mode;        /* 0 full, 1 surfels only, 2 Gaussians only */
+    /* ambiguity bands (pixels where several results are correct) */
+    double tol_depth_rel, tol_disc_rel, tol_graze, tol_alpha, tol_gdepth_rel;
+} ora_opts;
+
+enum { ORA_OK = 0, ORA_BAD_ARG = 1, ORA_BAD_QUAT = 2, ORA_NOMEM = 3 };
+enum { AMB_ID = 1, AMB_COLOR = 2 };
+
+/* ------------------------------------------------------------------------ */
+/* small linear algebra                                                      */
+
+static double dot3(const double *a, const double *b) { return a[0]*b[0] + a[1]*b[1] + a[2]*b[2]; }
+
+static void matvec3(const double *M /*3x3 rm*/, const double *v, double *out)
+{
+    for (int i = 0; i < 3; ++i) out[i] = M[3*i]*v[0] + M[3*i+1]*v[1] + M[3*i+2]*v[2];
+}
+
+/* rotation matrix of the normalised quaternion (w,x,y,z) */
+static int quat_rot(const double *q, double *R, double *qn, double *norm)
+{
+    double n = sqrt(q[0]*q[0] + q[1]*q[1] + q[2]*q[2] + q[3]*q[3]);
+    if (!(n > 0.0) || !isfinite(n)) return 0;
+    double w = q[0]/n, x = q[1]/n, y = q[2]/n, z = q[3]/n;
+    if (qn) { qn[0] = w; qn[1] = x; qn[2] = y; qn[3] = z; }
+    if (norm) *norm = n;
+    R[0] = 1 - 2*(y*y + z*z); R[1] = 2*(x*y - w*z);     R[2] = 2*(x*z + w*y);
+    R[3] = 2*(x*y + w*z);     R[4] = 1 - 2*(x*x + z*z); R[5] = 2*(y*z - w*x);
+    R[6] = 2*(x*z - w*y);     R[7] = 2*(y*z + w*x);     R[8] = 1 - 2*(x*x + y*y);
+    return 1;
+}
+
+static void cam_rot(const ora_camera *c, double *R)
+{
+    for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) R[3*i+j] = c->w2c[4*i+j];
+}
+
+static void cam_to_camera(const ora_camera *c, const double *pw, double *pc)
+{
+    for (int i = 0; i < 3; ++i)
+        pc[i] = c->w2c[4*i]*pw[0] + c->w2c[4*i+1]*pw[1] + c->w2c[4*i+2]*pw[2] + c->w2c[4*i+3];
+}
+
+/* camera centre o = -R^T t */
+static void cam_centre(const ora_camera *c, double *o)
+{
+    for (int j = 0; j < 3; ++j)
+        o[j] = -(c->w2c[j]*c->w2c[3] + c->w2c[4+j]*c->w2c[7] + c->w2c[8+j]*c->w2c[11]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Real spherical harmonics, Condon-Shortley phase, index k = l^2 + l + m.   */
+/* Y_l^m = sqrt2 K_l^m P_l^|m|(cos t) {cos,sin}(|m| phi), K_l^m from its     */
+/* factorial closed form.  On the unit sphere sin^m(t) e^{i m phi} equals    */
+/* (x+iy)^m and P_l^m(z) = (-1)^m (1-z^2)^{m/2} d^m P_l/dz^m, so each Y is a  */
+/* polynomial in (x,y,z) evaluated here from the explicit Legendre series.   */
+
+static double factd(int n) { double f = 1.0; for (int i = 2; i <= n; ++i) f *= i; return f; }
+
+/* d^m/dz^m P_l(z), P_l(z) = 2^-l sum_k (-1)^k (2l-2k)!/(k!(l-k)!(l-2k)!) z^(l-2k) */
+static double legendre_dm(int l, int m, double z)
+{
+    double s = 0.0;
+    for (int k = 0; 2*k <= l; ++k) {
+        int p = l - 2*k;
+        if (p < m) continue;
+        double c = factd(2*l - 2*k) / (factd(k) * factd(l - k) * factd(p)) / ldexp(1.0, l);
+        if (k & 1) c = -c;
+        c *= factd(p) / factd(p - m);
+        s += c * pow(z, p - m);
+    }
+    return s;
+}
+
+void ora_sh_basis(int deg, const double *d, double *Y, double *dY /* [K][3] or NULL */)
+{
+    const double x = d[0], y = d[1], z = d[2];
+    for (int l = 0; l <= deg; ++l) {
+        for (int m = -l; m <= l; ++m) {
+            int am = m < 0 ? -m : m, k = l*l + l + m;
+            double K = sqrt((2.0*l + 1.0) / (4.0*M_PI) * factd(l - am) / factd(l + am));
+            double D = legendre_dm(l, am, z), dD = legendre_dm(l, am + 1, z);
+            /* (x+iy)^am and (x+iy)^(am-1) */
+            double re = 1.0, im = 0.0, gre = 0.0, gim = 0.0;
+            for (int i = 0; i < am; ++i) {
+                gre = re; gim = im;
+                double nr = re*x - im*y, ni = re*y + im*x;
+                re = nr; im = ni;
+            }
+            double c = (am & 1) ? -M_SQRT2 * K : M_SQRT2 * K;
+            if (m == 0) {
+                Y[k] = K * D;
+                if (dY) { dY[3*k] = 0.0; dY[3*k+1] = 0.0; dY[3*k+2] = K * dD; }
+            } else if (m > 0) {
+                Y[k] = c * D * re;
+                if (dY) { dY[3*k] = c*D*am*gre; dY[3*k+1] = -c*D*am*gim; dY[3*k+2] = c*dD*re; }
+            } else {
+                Y[k] = c * D * im;
+                if (dY) { dY[3*k] = c*D*am*gim; dY[3*k+1] = c*D*am*gre; dY[3*k+2] = c*dD*im; }
+            }
+        }
+    }
+}
+
+/* Eq. 1: colour = max(0, 0.5 + sum_k SH_k Y_k(dir)), dir = (o - p)/|o - p|. */
+static void sh_colour(int deg, const double *sh, const double *dir, double *rgb, double *raw)
+{
+    double Y[16];
+    int K = (deg + 1) * (deg + 1);
+    ora_sh_basis(deg, dir, Y, NULL);
+    for (int ch = 0; ch < 3; ++ch) {
+        double s = 0.5;
+        for (int k = 0; k < K; ++k) s += sh[3*k + ch] * Y[k];
+        if (raw) raw[ch] = s;
+        rgb[ch] = s > 0.0 ? s : 0.0;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* per-primitive set-up                                                      */
+
+typedef struct {
+    int valid;
+    double pc[3], tu[3], tv[3], n[3];   /* camera space */
+    double s1, s2;
+    double rgb[3], raw[3], dir[3];
+    int x0, x1, y0, y1;                 /* conservative pixel rectangle (culled mode) */
+} surf_t;
+
+typedef struct {
+    int valid;
+    double t[3];                        /* camera-space centre */
+    double px, py;                      /* projected centre */
+    double ca, cb, cc;                  /* conic = inverse of Sigma2 */
+    double S2a, S2b, S2c;               /* Sigma2 entries (a b; b c) */
+    double sigma, d, eps;
+    double rgb[3], raw[3], dir[3], dist;
+    double R[9], qn[4], qnorm;
+    int x0, x1, y0, y1;
+} gauss_t;
+
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+static int surfel_setup(const ora_scene *S, const ora_camera *c, const ora_opts *o,
+                        const double *ocam, int64_t i, surf_t *sf)
+{
+    double R[9], Rc[9];
+    memset(sf, 0, sizeof *sf);
+    if (!quat_rot(S->s_rot + 4*i, R, NULL, NULL)) return 0;
+    cam_rot(c, Rc);
+    double tu[3] = {R[0], R[3], R[6]}, tv[3] = {R[1], R[4], R[7]}, n[3] = {R[2], R[5], R[8]};
+    const double *p = S->s_pos + 3*i;
+    cam_to_camera(c, p, sf->pc);
+    matvec3(Rc, tu, sf->tu); matvec3(Rc, tv, sf->tv); matvec3(Rc, n, sf->n);
+    sf->s1 = S->s_scale[2*i]; sf->s2 = S->s_scale[2*i + 1];
+    double v[3] = {ocam[0] - p[0], ocam[1] - p[1], ocam[2] - p[2]};
+    double L = sqrt(dot3(v, v));
+    for (int k = 0; k < 3; ++k) sf->dir[k] = L > 0 ? v[k] / L : 0.0;
+    sh_colour(S->sh_degree, S->s_sh + (int64_t)3 * (S->sh_degree + 1) * (S->sh_degree + 1) * i,
+              sf->dir, sf->rgb, sf->raw);
+    sf->valid = (sf->s1 > 0.0 && sf->s2 > 0.0 && isfinite(sf->s1) && isfinite(sf->s2));
+    /* conservative rectangle: the disc (slightly enlarged by the ambiguity band)
+       lies inside the rectangle pc +- r s1 tu +- r s2 tv; clip that rectangle to
+       z >= znear, project its vertices, pad by one pixel. */
+    sf->x0 = 1; sf->x1 = 0; sf->y0 = 1; sf->y1 = 0;
+    if (!sf->valid) return 1;
+    double r = sqrt(o->surfel_r2 * (1.0 + 2.0 * o->tol_disc_rel));
+    double cor[4][3], poly[8][3];
+    const double sg[4][2] = {{1, 1}, {-1, 1}, {-1, -1}, {1, -1}};
+    for (int k = 0; k < 4; ++k)
+        for (int j = 0; j < 3; ++j)
+            cor[k][j] = sf->pc[j] + sg[k][0]*r*sf->s1*sf->tu[j] + sg[k][1]*r*sf->s2*sf->tv[j];
+    int np = 0;
+    double zc = c->znear;
+    for (int k = 0; k < 4; ++k) {
+        const double *a = cor[k], *b = cor[(k + 1) & 3];
+        int ia = a[2] >= zc, ib = b[2] >= zc;
+        if (ia) { memcpy(poly[np++], a, sizeof(double) * 3); }
+        if (ia != ib) {
+            double tt = (zc - a[2]) / (b[2] - a[2]);
+            for (int j = 0; j < 3; ++j) poly[np][j] = a[j] + tt * (b[j] - a[j]);
+            poly[np][2] = zc;
+            ++np;
+        }
+    }
+    if (np == 0) return 1;
+    double umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+    for (int k = 0; k < np; ++k) {
+        double u = c->fx * poly[k][0] / poly[k][2] + c->cx, w = c->fy * poly[k][1] / poly[k][2] + c->cy;
+        umin = fmin(umin, u); umax = fmax(umax, u); vmin = fmin(vmin, w); vmax = fmax(vmax, w);
+    }
+    if (!(umax >= -1.0 && vmax >= -1.0 && umin <= c->width + 1.0 && vmin <= c->height + 1.0)) return 1;
+    sf->x0 = clampi((int)floor(umin - 0.5) - 1, 0, c->width - 1);
+    sf->x1 = clampi((int)ceil(umax - 0.5) + 1, 0, c->width - 1);
+    sf->y0 = clampi((int)floor(vmin - 0.5) - 1, 0, c->height - 1);
+    sf->y1 = clampi((int)ceil(vmax - 0.5) + 1, 0, c->height - 1);
+    return 1;
+}
+
+/* Gaussian: Sigma3 = R diag(s^2) R^T, EWA projection with the affine Jacobian at
+   the centre, fixed screen low-pass Sigma2 += lowpass I (3DGS's fixed-size EWA
+   filter, Sec. 6.1), conic = Sigma2^-1, depth d_i = camera z of the centre. */
+static int gauss_setup(const ora_scene *S, const ora_camera *c, const ora_opts *o,
+                       const double *ocam, int64_t i, gauss_t *g)
+{
+    double Rc[9];
+    memset(g, 0, sizeof *g);
+    g->x0 = 1; g->x1 = 0; g->y0 = 1; g->y1 = 0;
+    if (!quat_rot(S->g_rot + 4*i, g->R, g->qn, &g->qnorm)) return 0;
+    cam_rot(c, Rc);
+    const double *p = S->g_pos + 3*i, *s = S->g_scale + 3*i;
+    cam_to_camera(c, p, g->t);
+    g->sigma = S->g_opac[i];
+    switch (o->eps_mode) {
+    case 0: g->eps = o->eps_factor / 3.0 * (s[0] + s[1] + s[2]); break;
+    case 1: g->eps = 0.0; break;
+    default: g->eps = o->eps_value; break;
+    }
+    g->d = g->t[2];
+    double v[3] = {ocam[0] - p[0], ocam[1] - p[1], ocam[2] - p[2]};
+    g->dist = sqrt(dot3(v, v));
+    for (int k = 0; k < 3; ++k) g->dir[k] = g->dist > 0 ? v[k] / g->dist : 0.0;
+    sh_colour(S->sh_degree, S->g_sh + (int64_t)3 * (S->sh_degree + 1) * (S->sh_degree + 1) * i,
+              g->dir, g->rgb, g->raw);
+    if (!(g->t[2] > c->znear)) return 1;
+    double S3[9];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += g->R[3*a + k] * s[k] * s[k] * g->R[3*b + k];
+            S3[3*a + b] = acc;
+        }
+    double x = g->t[0], y = g->t[1], z = g->t[2];
+    double J[6] = {c->fx / z, 0.0, -c->fx * x / (z*z), 0.0, c->fy / z, -c->fy * y / (z*z)};
+    double T[6];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 3; ++b)
+            T[3*a + b] = J[3*a]*Rc[b] + J[3*a + 1]*Rc[3 + b] + J[3*a + 2]*Rc[6 + b];
+    double S2[4];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k)
+                for (int l = 0; l < 3; ++l) acc += T[3*a + k] * S3[3*k + l] * T[3*b + l];
+            S2[2*a + b] = acc;
+        }
+    g->S2a = S2[0] + o->lowpass; g->S2b = 0.5 * (S2[1] + S2[2]); g->S2c = S2[3] + o->lowpass;
+    double det = g->S2a * g->S2c - g->S2b * g->S2b;
+    if (!(det > 0.0) || !isfinite(det)) return 1;
+    g->ca = g->S2c / det; g->cb = -g->S2b / det; g->cc = g->S2a / det;
+    g->px = c->fx * x / z + c->cx;
+    g->py = c->fy * y / z + c->cy;
+    g->valid = 1;
+    /* exact support (Eq. 4 with the 1/255 clamp): alpha >= a  <=>  q <= 2 ln(sigma/a);
+       widened by the alpha ambiguity band so that culled == brute force exactly. */
+    double amin = o->alpha_min - o->tol_alpha;
+    if (!(g->sigma > amin) || amin <= 0.0) return 1;
+    double Tq = 2.0 * log(g->sigma / amin);
+    double hx = sqrt(Tq * g->S2a), hy = sqrt(Tq * g->S2c);
+    double umin = g->px - hx, umax = g->px + hx, vmin = g->py - hy, vmax = g->py + hy;
+    if (!(umax >= -1.0 && vmax >= -1.0 && umin <= c->width + 1.0 && vmin <= c->height + 1.0)) return 1;
+    g->x0 = clampi((int)floor(umin - 0.5) - 1, 0, c->width - 1);
+    g->x1 = clampi((int)ceil(umax - 0.5) + 1, 0, c->width - 1);
+    g->y0 = clampi((int)floor(vmin - 0.5) - 1, 0, c->height - 1);
+    g->y1 = clampi((int)ceil(vmax - 0.5) + 1, 0, c->height - 1);
+    return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* per-pixel definitions                                                     */
+
+/* Ray through the pixel centre (i+0.5, j+0.5): d = ((u-cx)/fx, (v-cy)/fy, 1). */
+static void pixel_ray(const ora_camera *c, int i, int j, double *d)
+{
+    d[0] = ((i + 0.5) - c->cx) / c->fx;
+    d[1] = ((j + 0.5) - c->cy) / c->fy;
+    d[2] = 1.0;
+}
+
+/* Surfel fragment at a pixel: ray-plane hit depth z (camera z), local disc
+   coordinates (a,b) of the hit scaled by (s1,s2), rho = a^2 + b^2.
+   Returns 0 when the ray is parallel to the plane. */
+static int surfel_hit(const surf_t *sf, const double *d, double *z, double *rho, double *ndot)
+{
+    double den = dot3(sf->n, d);
+    if (ndot) *ndot = den / sqrt(dot3(d, d));
+    if (den == 0.0) return 0;
+    double zz = dot3(sf->n, sf->pc) / den;
+    double X[3] = {zz*d[0] - sf->pc[0], zz*d[1] - sf->pc[1], zz*d[2] - sf->pc[2]};
+    double a = dot3(X, sf->tu) / sf->s1, b = dot3(X, sf->tv) / sf->s2;
+    *z = zz;
+    *rho = a*a + b*b;
+    return 1;
+}
+
+/* Eq. 4 before the clamp */
+static double gauss_alpha(const gauss_t *g, int i, int j)
+{
+    double dx = (i + 0.5) - g->px, dy = (j + 0.5) - g->py;
+    double q = g->ca*dx*dx + 2.0*g->cb*dx*dy + g->cc*dy*dy;
+    return g->sigma * exp(-0.5 * q);
+}
+
+/* ------------------------------------------------------------------------ */
+/* candidate lists per image row (culled mode); brute force uses every index */
+
+typedef struct { int64_t *off; int64_t *idx; } rowlists;
+
+static int build_rows(int H, int64_t n, const int *y0, const int *y1, size_t stride, rowlists *rl)
+{
+    rl->off = calloc((size_t)H + 1, sizeof(int64_t));
+    if (!rl->off) return 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int a = *(const int *)((const char *)y0 + stride * i), b = *(const int *)((const char *)y1 + stride * i);
+        for (int y = a; y <= b; ++y) rl->off[y + 1]++;
+    }
+    for (int y = 0; y < H; ++y) rl->off[y + 1] += rl->off[y];
+    rl->idx = malloc(sizeof(int64_t) * (size_t)(rl->off[H] > 0 ? rl->off[H] : 1));
+    int64_t *cur = malloc(sizeof(int64_t) * (size_t)(H > 0 ? H : 1));
+    if (!rl->idx || !cur) { free(cur); return 0; }
+    for (int y = 0; y < H; ++y) cur[y] = rl->off[y];
+    for (int64_t i = 0; i < n; ++i) {
+        int a = *(const int *)((const char *)y0 + stride * i), b = *(const int *)((const char *)y1 + stride * i);
+        for (int y = a; y <= b; ++y) rl->idx[cur[y]++] = i;
+    }
+    free(cur);
+    return 1;
+}
+
+static void free_rows(rowlists *rl) { free(rl->off); free(rl->idx); }
+
+/* ------------------------------------------------------------------------ */
+/* forward                                                                   */
+
+typedef struct {
+    surf_t *sf; gauss_t *gs;
+    rowlists rs, rg;
+} prep_t;
+
+static void prep_free(prep_t *P)
+{
+    free(P->sf); free(P->gs);
+    free_rows(&P->rs); free_rows(&P->rg);
+}
+
+static int prepare(const ora_scene *S, const ora_camera *c, const ora_opts *o, int culled, prep_t *P)
+{
+    memset(P, 0, sizeof *P);
+    double ocam[3];
+    cam_centre(c, ocam);
+    int64_t N = S->n_surfels, M = S->n_gaussians;
+    P->sf = calloc((size_t)(N > 0 ? N : 1), sizeof(surf_t));
+    P->gs = calloc((size_t)(M > 0 ? M : 1), sizeof(gauss_t));
+    if (!P->sf || !P->gs) return ORA_NOMEM;
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(|:bad)
+    for (int64_t i = 0; i < N; ++i) bad |= !surfel_setup(S, c, o, ocam, i, &P->sf[i]);
+#pragma omp parallel for schedule(static) reduction(|:bad)
+    for (int64_t i = 0; i < M; ++i) bad |= !gauss_setup(S, c, o, ocam, i, &P->gs[i]);
+    if (bad) return ORA_BAD_QUAT;
+    if (culled) {
+        if (!build_rows(c->height, N, &P->sf[0].y0, &P->sf[0].y1, sizeof(surf_t), &P->rs)) return ORA_NOMEM;
+        if (!build_rows(c->height, M, &P->gs[0].y0, &P->gs[0].y1, sizeof(gauss_t), &P->rg)) return ORA_NOMEM;
+    }
+    return ORA_OK;
+}
+
+/* One pixel of both passes.  Writes C, D_s, surfel id, W_G, the ambiguity
+   bits and the number of Gaussians that contributed. */
+static void shade_pixel(const ora_scene *S, const ora_camera *c, const ora_opts *o, const prep_t *P,
+                        int culled, int i, int j, double *C, double *Ds_out, int32_t *id_out,
+                        double *wg_out, uint8_t *amb_out, int32_t *nc_out)
+{
+    double d[3];
+    pixel_ray(c, i, j, d);
+    const double r2 = o->surfel_r2;
+    int64_t best = -1, second = -1;
+    double z1 = INFINITY, z2 = INFINITY, rho1 = 0.0, nd1 = 1.0, zband = INFINITY;
+    uint8_t amb = 0;
+
+    /* pass 1: z-buffer of opaque surfels; lexicographic min of (z, index) */
+    if (o->mode != 2) {
+        int64_t lo = 0, hi = S->n_surfels;
+        if (culled) { lo = P->rs.off[j]; hi = P->rs.off[j + 1]; }
+        for (int64_t t = lo; t < hi; ++t) {
+            int64_t s = culled ? P->rs.idx[t] : t;
+            const surf_t *sf = &P->sf[s];
+            if (!sf->valid) continue;
+            if (culled && (i < sf->x0 || i > sf->x1)) continue;
+            double z, rho, nd;
+            if (!surfel_hit(sf, d, &z, &rho, &nd)) continue;
+            if (!(z > c->znear)) continue;
+            if (fabs(rho - r2) <= o->tol_disc_rel * r2) zband = fmin(zband, z);
+            if (!(rho <= r2)) continue;
+            if (fabs(z - c->znear) <= o->tol_depth_rel * fmax(1.0, c->znear)) amb |= AMB_ID;
+            if (z < z1 || (z == z1 && s < best)) {
+                second = best; z2 = z1;
+                best = s; z1 = z; rho1 = rho; nd1 = nd;
+            } else if (z < z2 || (z == z2 && s < second)) {
+                second = s; z2 = z;
+            }
+        }
+        if (second >= 0 && (z2 - z1) <= o->tol_depth_rel * z1) amb |= AMB_ID;
+        if (best >= 0 && fabs(rho1 - r2) <= o->tol_disc_rel * r2) amb |= AMB_ID;
+        if (best >= 0 && fabs(nd1) < o->tol_graze) amb |= AMB_ID;
+        if (zband < INFINITY && (best < 0 || zband <= z1 * (1.0 + o->tol_depth_rel))) amb |= AMB_ID;
+    }
+    double Ds = best >= 0 ? z1 : INFINITY;
+    double Cs[3];
+    for (int ch = 0; ch < 3; ++ch) Cs[ch] = best >= 0 ? P->sf[best].rgb[ch] : c->bg[ch];
+
+    /* pass 2: order-independent accumulation (Eq. 2-4) */
+    double CG[3] = {0, 0, 0}, WG = 0.0;
+    int32_t nc = 0;
+    if (o->mode != 1) {
+        int64_t lo = 0, hi = S->n_gaussians;
+        if (culled) { lo = P->rg.off[j]; hi = P->rg.off[j + 1]; }
+        for (int64_t t = lo; t < hi; ++t) {
+            int64_t k = culled ? P->rg.idx[t] : t;
+            const gauss_t *g = &P->gs[k];
+            if (!g->valid) continue;
+            if (culled && (i < g->x0 || i > g->x1)) continue;
+            double a = gauss_alpha(g, i, j);
+            double lim = g->d - (Ds + g->eps);
+            int pass = g->d < Ds + g->eps;
+            if (fabs(a - o->alpha_min) <= o->tol_alpha && (pass || fabs(lim) <= o->tol_gdepth_rel * fmax(1.0, Ds)))
+                amb |= AMB_COLOR;
+            if (a >= o->alpha_min - o->tol_alpha && isfinite(Ds) &&
+                fabs(lim) <= o->tol_gdepth_rel * fmax(1.0, Ds))
+                amb |= AMB_COLOR;
+            if (!(a >= o->alpha_min) || !pass) continue;
+            for (int ch = 0; ch < 3; ++ch) CG[ch] += a * g->rgb[ch];
+            WG += a;
+            ++nc;
+        }
+    }
+    /* Eq. 5 and the two ablation modes */
+    for (int ch = 0; ch < 3; ++ch) {
+        if (o->mode == 0) C[ch] = (Cs[ch] * 1.0 + CG[ch]) / (1.0 + WG);
+        else if (o->mode == 1) C[ch] = Cs[ch];
+        else C[ch] = WG > 0.0 ? CG[ch] / WG : c->bg[ch];
+    }
+    *Ds_out = Ds;
+    *id_out = (int32_t)best;
+    *wg_out = WG;
+    *amb_out = amb;
+    *nc_out = nc;
+}
+
+static int check_args(const ora_scene *S, const ora_camera *c, const ora_opts *o)
+{
+    if (!S || !c || !o) return 0;
+    if (c->width <= 0 || c->height <= 0) return 0;
+    if (S->sh_degree < 0 || S->sh_degree > 3) return 0;
+    if (S->n_surfels < 0 || S->n_gaussians < 0) return 0;
+    if (!(c->fx > 0 && c->fy > 0 && c->znear > 0)) return 0;
+    return 1;
+}
+
+int ora_render(const ora_scene *S, const ora_camera *c, const ora_opts *o, int culled, int nthreads,
+               double *rgb, double *depth, int32_t *sid, double *wg, uint8_t *amb, int32_t *ncontrib)
+{
+    if (!check_args(S, c, o)) return ORA_BAD_ARG;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    prep_t P;
+    int st = prepare(S, c, o, culled, &P);
+    if (st != ORA_OK) { prep_free(&P); return st; }
+    const int W = c->width, H = c->height;
+    const int64_t HW = (int64_t)W * H;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int j = 0; j < H; ++j) {
+        for (int i = 0; i < W; ++i) {
+            int64_t pix = (int64_t)j * W + i;
+            double C[3], Ds, WG;
+            int32_t id, nc;
+            uint8_t a;
+            shade_pixel(S, c, o, &P, culled, i, j, C, &Ds, &id, &WG, &a, &nc);
+            for (int ch = 0; ch < 3; ++ch) rgb[ch * HW + pix] = C[ch];
+            depth[pix] = Ds;
+            sid[pix] = id;
+            wg[pix] = WG;
+            amb[pix] = a;
+            if (ncontrib) ncontrib[pix] = nc;
+        }
+    }
+    prep_free(&P);
+    return ORA_OK;
+}
+
+/* Evaluate surfel sid[k] at pixel (px[k], py[k]): hit depth, rho = a^2+b^2 and
+   the cosine between the plane normal and the ray.  Returns per entry 1 on a
+   hit, 0 if parallel or invalid. */
+int ora_surfel_eval(const ora_scene *S, const ora_camera *c, const ora_opts *o, int64_t n,
+                    const int32_t *px, const int32_t *py, const int32_t *sid,
+                    double *z, double *rho, double *ndot, int32_t *ok)
+{
+    if (!check_args(S, c, o)) return ORA_BAD_ARG;
+    double ocam[3];
+    cam_centre(c, ocam);
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < n; ++k) {
+        surf_t sf;
+        ok[k] = 0; z[k] = NAN; rho[k] = NAN; ndot[k] = NAN;
+        if (sid[k] < 0 || sid[k] >= S->n_surfels) continue;
+        if (!surfel_setup(S, c, o, ocam, sid[k], &sf) || !sf.valid) continue;
+        double d[3];
+        pixel_ray(c, px[k], py[k], d);
+        ok[k] = surfel_hit(&sf, d, &z[k], &rho[k], &ndot[k]);
+    }
+    return ORA_OK;
+}
+
+/* Per-primitive quantities for unit pins.
+   surfel: out = [valid, rgb(3), pc(3), n(3), x0, x1, y0, y1]                 (14)
+   gauss:  out = [valid, px, py, ca, cb, cc, S2a, S2b, S2c, sigma, d, eps,
+                  rgb(3), x0, x1, y0, y1]                                      (19) */
+int ora_surfel_info(const ora_scene *S, const ora_camera *c, const ora_opts *o, int64_t i, double *out)
+{
+    if (!check_args(S, c, o) || i < 0 || i >= S->n_surfels) return ORA_BAD_ARG;
+    double ocam[3];
+    cam_centre(c, ocam);
+    surf_t sf;
+    if (!surfel_setup(S, c, o, ocam, i, &sf)) return ORA_BAD_QUAT;
+    out[0] = sf.valid;
+    for (int k = 0; k < 3; ++k) { out[1 + k] = sf.rgb[k]; out[4 + k] = sf.pc[k]; out[7 + k] = sf.n[k]; }
+    out[10] = sf.x0; out[11] = sf.x1; out[12] = sf.y0; out[13] = sf.y1;
+    return ORA_OK;
+}
+
+int ora_gauss_info(const ora_scene *S, const ora_camera *c, const ora_opts *o, int64_t i, double *out)
+{
+    if (!check_args(S, c, o) || i < 0 || i >= S->n_gaussians) return ORA_BAD_ARG;
+    double ocam[3];
+    cam_centre(c, ocam);
+    gauss_t g;
+    if (!gauss_setup(S, c, o, ocam, i, &g)) return ORA_BAD_QUAT;
+    double v[] = {g.valid, g.px, g.py, g.ca, g.cb, g.cc, g.S2a, g.S2b, g.S2c, g.sigma, g.d, g.eps,
+                  g.rgb[0], g.rgb[1], g.rgb[2], g.x0, g.x1, g.y0, g.y1};
+    memcpy(out, v, sizeof v);
+    return ORA_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* backward: analytic gradients of L = sum_pixels sum_ch dL_drgb * C           */
+/* (Sec. 4.2: Gaussians and surfel SH are optimised, surfel geometry fixed).   */
+/* The indicator of the depth test and the 1/255 clamp are piecewise constant, */
+/* so they pass no gradient; the colour clamp max(0,.) passes gradient only    */
+/* where its argument is positive.                                             */
+
+static void sh_backward(int deg, const double *sh, const double *dir, double dist, const double *raw,
+                        const double *dLdc, double *g_sh /* [K,3] */, double *g_pos /* or NULL */)
+{
+    double Y[16], dY[48];
+    int K = (deg + 1) * (deg + 1);
+    ora_sh_basis(deg, dir, Y, dY);
+    double gd[3] = {0, 0, 0};
+    for (int ch = 0; ch < 3; ++ch) {
+        double gc = raw[ch] > 0.0 ? dLdc[ch] : 0.0;
+        for (int k = 0; k < K; ++k) {
+            g_sh[3*k + ch] = Y[k] * gc;
+            for (int a = 0; a < 3; ++a) gd[a] += gc * sh[3*k + ch] * dY[3*k + a];
+        }
+    }
+    if (g_pos && dist > 0.0) {
+        /* dir = (o - p)/|o - p|:  d dir / d p = -(I - dir dir^T)/|o - p| */
+        double pr = dot3(gd, dir);
+        for (int a = 0; a < 3; ++a) g_pos[a] += -(gd[a] - pr * dir[a]) / dist;
+    }
+}
+
+int ora_backward(const ora_scene *S, const ora_camera *c, const ora_opts *o, int nthreads,
+                 const double *dL_drgb,
+                 double *gg_pos, double *gg_rot, double *gg_scale, double *gg_opac, double *gg_sh,
+                 double *gs_sh)
+{
+    if (!check_args(S, c, o)) return ORA_BAD_ARG;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    const int W = c->width, H = c->height;
+    const int64_t HW = (int64_t)W * H, N = S->n_surfels, M = S->n_gaussians;
+    const int K = (S->sh_degree + 1) * (S->sh_degree + 1);
+    double *rgb = malloc(sizeof(double) * 3 * (size_t)HW), *Ds = malloc(sizeof(double) * (size_t)HW);
+    double *WG = malloc(sizeof(double) * (size_t)HW);
+    int32_t *sid = malloc(sizeof(int32_t) * (size_t)HW);
+    uint8_t *amb = malloc((size_t)HW);
+    double *gcs = calloc((size_t)(N > 0 ? N : 1) * 3, sizeof(double));
+    if (!rgb || !Ds || !WG || !sid || !amb || !gcs) {
+        free(rgb); free(Ds); free(WG); free(sid); free(amb); free(gcs);
+        return ORA_NOMEM;
+    }
+    int st = ora_render(S, c, o, 1, nthreads, rgb, Ds, sid, WG, amb, NULL);
+    if (st != ORA_OK) { free(rgb); free(Ds); free(WG); free(sid); free(amb); free(gcs); return st; }
+    prep_t P;
+    st = prepare(S, c, o, 1, &P);
+    if (st != ORA_OK) { prep_free(&P); free(rgb); free(Ds); free(WG); free(sid); free(amb); free(gcs); return st; }
+    double Rc[9];
+    cam_rot(c, Rc);
+
+    /* surfel colours: C depends on c_s through C_s at pixels the surfel wins */
+    if (o->mode != 2) {
+        for (int64_t pix = 0; pix < HW; ++pix) {
+            int32_t s = sid[pix];
+            if (s < 0) continue;
+            double k = o->mode == 0 ? 1.0 / (1.0 + WG[pix]) : 1.0;
+            for (int ch = 0; ch < 3; ++ch) gcs[3*s + ch] += k * dL_drgb[ch * HW + pix];
+        }
+    }
+    memset(gs_sh, 0, sizeof(double) * 3 * (size_t)K * (size_t)N);
+#pragma omp parallel for schedule(static)
+    for (int64_t s = 0; s < N; ++s) {
+        const surf_t *sf = &P.sf[s];
+        if (!sf->valid) continue;
+        sh_backward(S->sh_degree, S->s_sh + (int64_t)3*K*s, sf->dir, 0.0, sf->raw, gcs + 3*s,
+                    gs_sh + (int64_t)3*K*s, NULL);
+    }
+
+    memset(gg_pos, 0, sizeof(double) * 3 * (size_t)M);
+    memset(gg_rot, 0, sizeof(double) * 4 * (size_t)M);
+    memset(gg_scale, 0, sizeof(double) * 3 * (size_t)M);
+    memset(gg_opac, 0, sizeof(double) * (size_t)M);
+    memset(gg_sh, 0, sizeof(double) * 3 * (size_t)K * (size_t)M);
+    if (o->mode != 1) {
+#pragma omp parallel for schedule(dynamic, 64)
+        for (int64_t gi = 0; gi < M; ++gi) {
+            const gauss_t *g = &P.gs[gi];
+            if (!g->valid) continue;
+            /* 2D-level gradients summed over the Gaussian's pixels */
+            double dc[3] = {0, 0, 0}, dsig = 0, dpx = 0, dpy = 0, dca = 0, dcb = 0, dcc = 0;
+            for (int j = g->y0; j <= g->y1; ++j) {
+                for (int i = g->x0; i <= g->x1; ++i) {
+                    int64_t pix = (int64_t)j * W + i;
+                    double dx = (i + 0.5) - g->px, dy = (j + 0.5) - g->py;
+                    double q = g->ca*dx*dx + 2.0*g->cb*dx*dy + g->cc*dy*dy;
+                    double e = exp(-0.5 * q), a = g->sigma * e;
+                    if (!(a >= o->alpha_min) || !(g->d < Ds[pix] + g->eps)) continue;
+                    double k = o->mode == 0 ? 1.0 / (1.0 + WG[pix]) : 1.0 / WG[pix];
+                    double gdotcC = 0.0;
+                    for (int ch = 0; ch < 3; ++ch) {
+                        double gch = dL_drgb[ch * HW + pix];
+                        dc[ch] += a * k * gch;
+                        gdotcC += gch * (g->rgb[ch] - rgb[ch * HW + pix]);
+                    }
+                    double dLda = k * gdotcC;
+                    dsig += dLda * e;
+                    double dLdq = dLda * a * (-0.5);
+                    /* q = ca dx^2 + 2 cb dx dy + cc dy^2, dx = u - px */
+                    dpx += dLdq * (-(2.0*g->ca*dx + 2.0*g->cb*dy));
+                    dpy += dLdq * (-(2.0*g->cb*dx + 2.0*g->cc*dy));
+                    dca += dLdq * dx * dx;
+                    dcb += dLdq * 2.0 * dx * dy;
+                    dcc += dLdq * dy * dy;
+                }
+            }
+            const double *s = S->g_scale + 3*gi;
+            double *gp = gg_pos + 3*gi;
+            /* colour -> SH and position (through the view direction) */
+            sh_backward(S->sh_degree, S->g_sh + (int64_t)3*K*gi, g->dir, g->dist, g->raw, dc,
+                        gg_sh + (int64_t)3*K*gi, gp);
+            gg_opac[gi] = dsig;
+            /* conic Q = Sigma2^-1 (symmetric), dL/dQ as a symmetric matrix */
+            double Q[4] = {g->ca, g->cb, g->cb, g->cc};
+            double GQ[4] = {dca, 0.5*dcb, 0.5*dcb, dcc};
+            double GS2[4];
+            /* dL/dSigma2 = -Q GQ Q */
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b) {
+                    double acc = 0.0;
+                    for (int k = 0; k < 2; ++k)
+                        for (int l = 0; l < 2; ++l) acc += Q[2*a + k] * GQ[2*k + l] * Q[2*l + b];
+                    GS2[2*a + b] = -acc;
+                }
+            /* rebuild J, T = J Rc, Sigma3 */
+            double x = g->t[0], y = g->t[1], z = g->t[2];
+            double J[6] = {c->fx / z, 0.0, -c->fx * x / (z*z), 0.0, c->fy / z, -c->fy * y / (z*z)};
+            double T[6], S3[9];
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 3; ++b)
+                    T[3*a + b] = J[3*a]*Rc[b] + J[3*a + 1]*Rc[3 + b] + J[3*a + 2]*Rc[6 + b];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    double acc = 0.0;
+                    for (int k = 0; k < 3; ++k) acc += g->R[3*a + k] * s[k] * s[k] * g->R[3*b + k];
+                    S3[3*a + b] = acc;
+                }
+            /* Sigma2 = T S3 T^T (+ lowpass I):  dL/dS3 = T^T GS2 T,  dL/dT = 2 GS2 T S3 */
+            double GS3[9], GT[6];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    double acc = 0.0;
+                    for (int k = 0; k < 2; ++k)
+                        for (int l = 0; l < 2; ++l) acc += T[3*k + a] * GS2[2*k + l] * T[3*l + b];
+                    GS3[3*a + b] = acc;
+                }
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    double acc = 0.0;
+                    for (int k = 0; k < 2; ++k)
+                        for (int l = 0; l < 3; ++l) acc += GS2[2*a + k] * T[3*k + l] * S3[3*l + b];
+                    GT[3*a + b] = 2.0 * acc;
+                }
+            /* T = J Rc:  dL/dJ = GT Rc^T */
+            double GJ[6];
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 3; ++b)
+                    GJ[3*a + b] = GT[3*a]*Rc[3*b] + GT[3*a + 1]*Rc[3*b + 1] + GT[3*a + 2]*Rc[3*b + 2];
+            /* camera-space centre: through J and the projected centre */
+            double gt[3];
+            gt[0] = GJ[2] * (-c->fx / (z*z)) + dpx * (c->fx / z);
+            gt[1] = GJ[5] * (-c->fy / (z*z)) + dpy * (c->fy / z);
+            gt[2] = GJ[0] * (-c->fx / (z*z)) + GJ[2] * (2.0 * c->fx * x / (z*z*z))
+                  + GJ[4] * (-c->fy / (z*z)) + GJ[5] * (2.0 * c->fy * y / (z*z*z))
+                  + dpx * (-c->fx * x / (z*z)) + dpy * (-c->fy * y / (z*z));
+            /* t = Rc p + tc:  dL/dp += Rc^T gt */
+            for (int a = 0; a < 3; ++a) gp[a] += Rc[a]*gt[0] + Rc[3 + a]*gt[1] + Rc[6 + a]*gt[2];
+            /* S3 = Mm Mm^T with Mm = R diag(s):  dL/dMm = 2 GS3 Mm */
+            double GM[9];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    double acc = 0.0;
+                    for (int k = 0; k < 3; ++k) acc += GS3[3*a + k] * g->R[3*k + b] * s[b];
+                    GM[3*a + b] = 2.0 * acc;
+                }
+            double GR[9];
+            for (int b = 0; b < 3; ++b) {
+                double acc = 0.0;
+                for (int a = 0; a < 3; ++a) { acc += GM[3*a + b] * g->R[3*a + b]; GR[3*a + b] = GM[3*a + b] * s[b]; }
+                gg_scale[3*gi + b] = acc;
+            }
+            /* R(qhat): partial derivatives of each entry w.r.t. (w,x,y,z) */
+            double w = g->qn[0], qx = g->qn[1], qy = g->qn[2], qz = g->qn[3];
+            double dR[4][9] = {
+                {0, -2*qz, 2*qy, 2*qz, 0, -2*qx, -2*qy, 2*qx, 0},
+                {0, 2*qy, 2*qz, 2*qy, -4*qx, -2*w, 2*qz, 2*w, -4*qx},
+                {-4*qy, 2*qx, 2*w, 2*qx, 0, 2*qz, -2*w, 2*qz, -4*qy},
+                {-4*qz, -2*w, 2*qx, 2*w, -4*qz, 2*qy, 2*qx, 2*qy, 0},
+            };
+            double gqn[4];
+            for (int a = 0; a < 4; ++a) {
+                double acc = 0.0;
+                for (int k = 0; k < 9; ++k) acc += GR[k] * dR[a][k];
+                gqn[a] = acc;
+            }
+            /* qhat = q/|q|:  dL/dq = (gqn - qhat (qhat . gqn)) / |q| */
+            double pr = gqn[0]*w + gqn[1]*qx + gqn[2]*qy + gqn[3]*qz;
+            for (int a = 0; a < 4; ++a) gg_rot[4*gi + a] = (gqn[a] - pr * g->qn[a]) / g->qnorm;
+        }
+    }
+    prep_free(&P);
+    free(rgb); free(Ds); free(WG); free(sid); free(amb); free(gcs);
+    return ORA_OK;
+}
+
+int ora_version(void) { return 1; }

@@ -1,0 +1,210 @@
+"""ctypes binding of the FP64 oracle (``ges_oracle.c``).
+
+TEST INFRASTRUCTURE: used by the tests, the smoke check and the benchmark's
+CPU-baseline leg only.  Every array handed to the C code is float64; FP32 (or
+dequantised FP16/BF16) scene attributes are widened exactly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ges_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_OUT_DIR, "libges_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# Paper defaults: eps_i = 5 * mean axis length (Sec. 5), 1/255 clamp (Sec. 3),
+# opaque extent 2 ln 255 (Sec. 4.1), 3DGS's fixed screen low-pass 0.3.
+# The tol_* entries are the ambiguity bands of the parity tests.
+DEFAULT_OPTS = dict(eps_mode=0, eps_value=0.1, eps_factor=5.0, lowpass=0.3,
+                    alpha_min=1.0 / 255.0, surfel_r2=2.0 * math.log(255.0), mode=0,
+                    tol_depth_rel=1e-6, tol_disc_rel=1e-5, tol_graze=1e-3, tol_alpha=1e-5,
+                    tol_gdepth_rel=2e-6)
+
+
+class _Scene(C.Structure):
+    _fields_ = [("n_surfels", C.c_int64), ("n_gaussians", C.c_int64), ("sh_degree", C.c_int32)] + \
+               [(n, C.c_void_p) for n in ("s_pos", "s_rot", "s_scale", "s_sh",
+                                          "g_pos", "g_rot", "g_scale", "g_opac", "g_sh")]
+
+
+class _Camera(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("fx", C.c_double), ("fy", C.c_double),
+                ("cx", C.c_double), ("cy", C.c_double), ("w2c", C.c_double * 12),
+                ("znear", C.c_double), ("bg", C.c_double * 3)]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("eps_mode", C.c_int32), ("eps_value", C.c_double), ("eps_factor", C.c_double),
+                ("lowpass", C.c_double), ("alpha_min", C.c_double), ("surfel_r2", C.c_double),
+                ("mode", C.c_int32), ("tol_depth_rel", C.c_double), ("tol_disc_rel", C.c_double),
+                ("tol_graze", C.c_double), ("tol_alpha", C.c_double), ("tol_gdepth_rel", C.c_double)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP, no fast-math, no FMA contraction)."""
+    with _lock:
+        if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+            return _LIB
+        os.makedirs(_OUT_DIR, exist_ok=True)
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-fopenmp",
+               "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+def load():
+    global _lib
+    if _lib is None:
+        lib = C.CDLL(build())
+        P = C.POINTER
+        lib.ora_render.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_int, C.c_int] + [C.c_void_p] * 6
+        lib.ora_backward.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_int] + [C.c_void_p] * 7
+        lib.ora_sh_basis.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.ora_surfel_eval.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_int64] + [C.c_void_p] * 7
+        lib.ora_surfel_info.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_int64, C.c_void_p]
+        lib.ora_gauss_info.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_int64, C.c_void_p]
+        _lib = lib
+    return _lib
+
+
+def _d(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+class _Pinned:
+    """Keeps the float64 copies alive while the C structure points at them."""
+
+    def __init__(self, scene, cam, opts):
+        self.arrs = {k: _d(v) for k, v in scene.arrays().items()}
+        self.s = _Scene(scene.n_surfels, scene.n_gaussians, scene.sh_degree,
+                        *[self.arrs[k].ctypes.data for k in ("s_pos", "s_rot", "s_scale", "s_sh",
+                                                              "g_pos", "g_rot", "g_scale", "g_opac", "g_sh")])
+        w2c = np.asarray(cam.world_to_cam, np.float64).reshape(12)
+        self.c = _Camera(cam.width, cam.height, float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy),
+                         (C.c_double * 12)(*w2c), float(cam.znear), (C.c_double * 3)(*map(float, cam.bg)))
+        o = dict(DEFAULT_OPTS)
+        o.update(opts or {})
+        self.o = _Opts(**o)
+
+
+def _check(st, what):
+    if st != 0:
+        raise RuntimeError(f"oracle {what} failed with status {st}")
+
+
+def render(scene, cam, opts=None, culled: bool = True, nthreads: int = 0):
+    """FP64 render: rgb [3,H,W], depth [H,W] (+inf where no surfel), id [H,W]
+    (-1), wg [H,W] (W_G), amb [H,W] (bit 1: id/depth ambiguous, bit 2:
+    colour ambiguous) and ncontrib [H,W] (Gaussians that contributed)."""
+    lib = load()
+    pin = _Pinned(scene, cam, opts)
+    H, W = cam.height, cam.width
+    out = dict(rgb=np.empty((3, H, W)), depth=np.empty((H, W)), id=np.empty((H, W), np.int32),
+               wg=np.empty((H, W)), amb=np.empty((H, W), np.uint8), ncontrib=np.empty((H, W), np.int32))
+    st = lib.ora_render(C.byref(pin.s), C.byref(pin.c), C.byref(pin.o), int(culled), int(nthreads),
+                        *[out[k].ctypes.data for k in ("rgb", "depth", "id", "wg", "amb", "ncontrib")])
+    _check(st, "render")
+    return out
+
+
+def backward(scene, cam, dL_drgb, opts=None, nthreads: int = 0):
+    """Analytic FP64 gradients of sum(dL_drgb * C)."""
+    lib = load()
+    pin = _Pinned(scene, cam, opts)
+    K = (scene.sh_degree + 1) ** 2
+    M, N = scene.n_gaussians, scene.n_surfels
+    g = _d(dL_drgb)
+    assert g.shape == (3, cam.height, cam.width)
+    out = dict(g_pos=np.empty((M, 3)), g_rot=np.empty((M, 4)), g_scale=np.empty((M, 3)),
+               g_opac=np.empty((M,)), g_sh=np.empty((M, K, 3)), s_sh=np.empty((N, K, 3)))
+    st = lib.ora_backward(C.byref(pin.s), C.byref(pin.c), C.byref(pin.o), int(nthreads), g.ctypes.data,
+                          *[out[k].ctypes.data for k in ("g_pos", "g_rot", "g_scale", "g_opac", "g_sh", "s_sh")])
+    _check(st, "backward")
+    return out
+
+
+def sh_basis(deg: int, d):
+    """Real SH basis values Y[K] and gradients dY[K,3] at the unit vector d."""
+    lib = load()
+    K = (deg + 1) ** 2
+    dd = _d(d)
+    Y, dY = np.empty(K), np.empty((K, 3))
+    lib.ora_sh_basis(int(deg), dd.ctypes.data, Y.ctypes.data, dY.ctypes.data)
+    return Y, dY
+
+
+def surfel_eval(scene, cam, px, py, sid, opts=None):
+    """Evaluate surfel sid[k] at pixel (px[k], py[k]): depth, rho=a^2+b^2, cos(n, ray), hit flag."""
+    lib = load()
+    pin = _Pinned(scene, cam, opts)
+    px = np.ascontiguousarray(px, np.int32)
+    py = np.ascontiguousarray(py, np.int32)
+    sid = np.ascontiguousarray(sid, np.int32)
+    n = px.size
+    z, rho, nd = np.empty(n), np.empty(n), np.empty(n)
+    ok = np.empty(n, np.int32)
+    st = lib.ora_surfel_eval(C.byref(pin.s), C.byref(pin.c), C.byref(pin.o), n, px.ctypes.data,
+                             py.ctypes.data, sid.ctypes.data, z.ctypes.data, rho.ctypes.data,
+                             nd.ctypes.data, ok.ctypes.data)
+    _check(st, "surfel_eval")
+    return z, rho, nd, ok
+
+
+def surfel_info(scene, cam, i, opts=None):
+    lib = load()
+    pin = _Pinned(scene, cam, opts)
+    out = np.empty(14)
+    _check(lib.ora_surfel_info(C.byref(pin.s), C.byref(pin.c), C.byref(pin.o), int(i), out.ctypes.data),
+           "surfel_info")
+    return dict(valid=bool(out[0]), rgb=out[1:4], pc=out[4:7], n=out[7:10], bbox=out[10:14].astype(int))
+
+
+def gauss_info(scene, cam, i, opts=None):
+    lib = load()
+    pin = _Pinned(scene, cam, opts)
+    out = np.empty(19)
+    _check(lib.ora_gauss_info(C.byref(pin.s), C.byref(pin.c), C.byref(pin.o), int(i), out.ctypes.data),
+           "gauss_info")
+    return dict(valid=bool(out[0]), px=out[1], py=out[2], conic=out[3:6], sigma2=out[6:9],
+                sigma=out[9], d=out[10], eps=out[11], rgb=out[12:15], bbox=out[15:19].astype(int))
+
+
+def id_validity(scene, cam, ref, ids, opts=None):
+    """Which surfel ids are acceptable answers at each pixel.
+
+    ``ref`` is an oracle render.  At a pixel the candidate id is valid when it
+    equals the oracle's winner, or, where the oracle flagged the pixel as
+    ambiguous, when the candidate's own FP64 fragment is inside its disc up to
+    the disc band and no farther than the winner's depth up to the depth band
+    (an empty answer is valid only if every covering fragment lies in the
+    disc band).  Returns a bool [H,W] array."""
+    o = dict(DEFAULT_OPTS)
+    o.update(opts or {})
+    ids = np.asarray(ids, np.int32)
+    valid = ids == ref["id"]
+    amb = (ref["amb"] & 1) != 0
+    yy, xx = np.nonzero(amb & ~valid)
+    if yy.size:
+        cand = ids[yy, xx]
+        z, rho, nd, ok = surfel_eval(scene, cam, xx, yy, np.maximum(cand, 0), opts)
+        r2 = o["surfel_r2"]
+        zw = ref["depth"][yy, xx]
+        good_hit = (ok == 1) & (rho <= r2 * (1 + o["tol_disc_rel"])) & (z > cam.znear) & \
+                   (z <= zw * (1 + 2 * o["tol_depth_rel"]))
+        wid = ref["id"][yy, xx]
+        zw2, rhow, _, okw = surfel_eval(scene, cam, xx, yy, np.maximum(wid, 0), opts)
+        # empty answer: acceptable only if the oracle's winner sits in the disc band
+        good_empty = (cand < 0) & ((wid < 0) | ((okw == 1) & (np.abs(rhow - r2) <= o["tol_disc_rel"] * r2)))
+        valid[yy, xx] = np.where(cand >= 0, good_hit, good_empty)
+    return valid
