@@ -484,3 +484,19 @@ def test_backward_surfel_geometry_gets_no_gradient_and_hidden_gaussians_none(ora
     assert np.all(gr["g_pos"] == 0) and np.all(gr["g_opac"] == 0) and np.all(gr["g_sh"] == 0)
     # the wall wins every pixel with k = 1/(1+0) = 1: dL/dc_s = #pixels, dL/dSH_0 = Y00 * that
     np.testing.assert_allclose(gr["s_sh"][0, 0], 1600 / (2 * math.sqrt(math.pi)), rtol=1e-13)
+
+
+def test_sh_direction_points_from_primitive_to_camera(oracle_lib):
+    """Eq. 1 evaluates SH at the direction from the surfel centre to the
+    camera position (Sec. 3).  A surfel/Gaussian carrying only the l=1, m=0
+    coefficient (Y = sqrt(3/4pi) z) seen from -z gets 0.5 - sqrt(3/4pi) * c."""
+    c1 = math.sqrt(3.0 / (4.0 * math.pi))
+    cam = ident_cam(33, 33, 30.0, cx=16.5, cy=16.5)   # camera at the origin, looking along +z
+    sh = np.zeros((1, 4, 3))
+    sh[0, 2] = (0.4, 0.2, -0.1)
+    sc = mk_scene(1, s_pos=[[0, 0, 2.0]], s_rot=[[1.0, 0, 0, 0]], s_scale=[[0.2, 0.2]], s_sh=sh)
+    out = oracle_lib.render(sc, cam)
+    np.testing.assert_allclose(out["rgb"][:, 16, 16], 0.5 - c1 * np.array([0.4, 0.2, -0.1]), rtol=1e-14)
+    sg_ = mk_scene(1, g_pos=[[0, 0, 2.0]], g_rot=[[1.0, 0, 0, 0]], g_scale=[[0.01] * 3], g_opac=[0.5], g_sh=sh)
+    info = oracle_lib.gauss_info(sg_, cam, 0)
+    np.testing.assert_allclose(info["rgb"], 0.5 - c1 * np.array([0.4, 0.2, -0.1]), rtol=1e-14)
