@@ -6,7 +6,8 @@
  * path: no headers, no helpers, no constants.  It is deliberately plain: every
  * pixel is evaluated straight from the paper's definitions in double
  * precision, with no blocking, fusion or reordering beyond skipping pixels
- * that lie outside a primitive's conservative screen rectangle.
+ * that lie outside a primitive's conservative screen rectangle (found through
+ * 16x16-pixel cell lists kept in ascending primitive index).
  *
  * What it follows:
  *   Sec. 3        surfel = opaque disc in its local XY plane, placed by scale,
@@ -361,27 +362,38 @@ static double gauss_alpha(const gauss_t *g, int i, int j)
 }
 
 /* ------------------------------------------------------------------------ */
-/* candidate lists per image row (culled mode); brute force uses every index */
+/* candidate lists per 16x16 pixel cell (culled mode), each in ascending
+   primitive index; brute force uses every index */
 
-typedef struct { int64_t *off; int64_t *idx; } rowlists;
+#define ORA_CELL 16
+typedef struct { int64_t *off; int64_t *idx; int cx; } rowlists;
 
-static int build_rows(int H, int64_t n, const int *y0, const int *y1, size_t stride, rowlists *rl)
+static int build_rows(int W, int H, int64_t n, const int *x0, const int *x1, const int *y0, const int *y1,
+                      size_t stride, rowlists *rl)
 {
-    rl->off = calloc((size_t)H + 1, sizeof(int64_t));
+    const int cx = (W + ORA_CELL - 1) / ORA_CELL, cy = (H + ORA_CELL - 1) / ORA_CELL;
+    const int64_t nc = (int64_t)cx * cy;
+    rl->cx = cx;
+    rl->off = calloc((size_t)nc + 1, sizeof(int64_t));
     if (!rl->off) return 0;
+#define FLD(p, i) (*(const int *)((const char *)(p) + stride * (i)))
     for (int64_t i = 0; i < n; ++i) {
-        int a = *(const int *)((const char *)y0 + stride * i), b = *(const int *)((const char *)y1 + stride * i);
-        for (int y = a; y <= b; ++y) rl->off[y + 1]++;
+        if (FLD(x0, i) > FLD(x1, i) || FLD(y0, i) > FLD(y1, i)) continue;
+        for (int b = FLD(y0, i) / ORA_CELL; b <= FLD(y1, i) / ORA_CELL; ++b)
+            for (int a = FLD(x0, i) / ORA_CELL; a <= FLD(x1, i) / ORA_CELL; ++a) rl->off[(int64_t)b * cx + a + 1]++;
     }
-    for (int y = 0; y < H; ++y) rl->off[y + 1] += rl->off[y];
-    rl->idx = malloc(sizeof(int64_t) * (size_t)(rl->off[H] > 0 ? rl->off[H] : 1));
-    int64_t *cur = malloc(sizeof(int64_t) * (size_t)(H > 0 ? H : 1));
+    for (int64_t c = 0; c < nc; ++c) rl->off[c + 1] += rl->off[c];
+    rl->idx = malloc(sizeof(int64_t) * (size_t)(rl->off[nc] > 0 ? rl->off[nc] : 1));
+    int64_t *cur = malloc(sizeof(int64_t) * (size_t)(nc > 0 ? nc : 1));
     if (!rl->idx || !cur) { free(cur); return 0; }
-    for (int y = 0; y < H; ++y) cur[y] = rl->off[y];
+    for (int64_t c = 0; c < nc; ++c) cur[c] = rl->off[c];
     for (int64_t i = 0; i < n; ++i) {
-        int a = *(const int *)((const char *)y0 + stride * i), b = *(const int *)((const char *)y1 + stride * i);
-        for (int y = a; y <= b; ++y) rl->idx[cur[y]++] = i;
+        if (FLD(x0, i) > FLD(x1, i) || FLD(y0, i) > FLD(y1, i)) continue;
+        for (int b = FLD(y0, i) / ORA_CELL; b <= FLD(y1, i) / ORA_CELL; ++b)
+            for (int a = FLD(x0, i) / ORA_CELL; a <= FLD(x1, i) / ORA_CELL; ++a)
+                rl->idx[cur[(int64_t)b * cx + a]++] = i;
     }
+#undef FLD
     free(cur);
     return 1;
 }
@@ -418,8 +430,10 @@ static int prepare(const ora_scene *S, const ora_camera *c, const ora_opts *o, i
     for (int64_t i = 0; i < M; ++i) bad |= !gauss_setup(S, c, o, ocam, i, &P->gs[i]);
     if (bad) return ORA_BAD_QUAT;
     if (culled) {
-        if (!build_rows(c->height, N, &P->sf[0].y0, &P->sf[0].y1, sizeof(surf_t), &P->rs)) return ORA_NOMEM;
-        if (!build_rows(c->height, M, &P->gs[0].y0, &P->gs[0].y1, sizeof(gauss_t), &P->rg)) return ORA_NOMEM;
+        if (!build_rows(c->width, c->height, N, &P->sf[0].x0, &P->sf[0].x1, &P->sf[0].y0, &P->sf[0].y1,
+                        sizeof(surf_t), &P->rs)) return ORA_NOMEM;
+        if (!build_rows(c->width, c->height, M, &P->gs[0].x0, &P->gs[0].x1, &P->gs[0].y0, &P->gs[0].y1,
+                        sizeof(gauss_t), &P->rg)) return ORA_NOMEM;
     }
     return ORA_OK;
 }
@@ -440,12 +454,15 @@ static void shade_pixel(const ora_scene *S, const ora_camera *c, const ora_opts 
     /* pass 1: z-buffer of opaque surfels; lexicographic min of (z, index) */
     if (o->mode != 2) {
         int64_t lo = 0, hi = S->n_surfels;
-        if (culled) { lo = P->rs.off[j]; hi = P->rs.off[j + 1]; }
+        if (culled) {
+            const int64_t cell = (int64_t)(j / ORA_CELL) * P->rs.cx + i / ORA_CELL;
+            lo = P->rs.off[cell]; hi = P->rs.off[cell + 1];
+        }
         for (int64_t t = lo; t < hi; ++t) {
             int64_t s = culled ? P->rs.idx[t] : t;
             const surf_t *sf = &P->sf[s];
             if (!sf->valid) continue;
-            if (culled && (i < sf->x0 || i > sf->x1)) continue;
+            if (culled && (i < sf->x0 || i > sf->x1 || j < sf->y0 || j > sf->y1)) continue;
             double z, rho, nd;
             if (!surfel_hit(sf, d, &z, &rho, &nd)) continue;
             if (!(z > c->znear)) continue;
@@ -473,12 +490,15 @@ static void shade_pixel(const ora_scene *S, const ora_camera *c, const ora_opts 
     int32_t nc = 0;
     if (o->mode != 1) {
         int64_t lo = 0, hi = S->n_gaussians;
-        if (culled) { lo = P->rg.off[j]; hi = P->rg.off[j + 1]; }
+        if (culled) {
+            const int64_t cell = (int64_t)(j / ORA_CELL) * P->rg.cx + i / ORA_CELL;
+            lo = P->rg.off[cell]; hi = P->rg.off[cell + 1];
+        }
         for (int64_t t = lo; t < hi; ++t) {
             int64_t k = culled ? P->rg.idx[t] : t;
             const gauss_t *g = &P->gs[k];
             if (!g->valid) continue;
-            if (culled && (i < g->x0 || i > g->x1)) continue;
+            if (culled && (i < g->x0 || i > g->x1 || j < g->y0 || j > g->y1)) continue;
             double a = gauss_alpha(g, i, j);
             double lim = g->d - (Ds + g->eps);
             int pass = g->d < Ds + g->eps;
