@@ -1,0 +1,225 @@
+/*
+ * ges.h -- C ABI of the Gaussian-enhanced Surfels (GES) renderer for GB300.
+ *
+ * The problem (Sec. 3): a scene is a set of opaque 2D surfels
+ * S = {p_i, r_i, s_i, SH_i} and a set of 3D Gaussians G = {p_i, sigma_i, r_i,
+ * s_i, SH_i}.  Rendering runs two passes.  Pass 1 rasterises the surfels with
+ * a z-buffer into a colour map C_s and a depth map D_s.  Pass 2 splats the
+ * Gaussians, keeps those whose centre depth passes d_i < D_s + eps_i (Eq. 2-3),
+ * weights them by the 2D opacity of Eq. 4 (zero below 1/255) and composites
+ * C = (C_s W_s + C_G) / (W_s + W_G) with W_s = 1 (Eq. 5).  No sorting is
+ * involved anywhere.  The joint optimisation stage (Sec. 4.2) needs the
+ * gradients of C with respect to the Gaussians and the surfel SH
+ * coefficients; surfel geometry is fixed there and receives none.
+ *
+ * Conventions (readings where the paper is silent):
+ *  - cameras: OpenCV axes (x right, y down, z forward), row-major world-to-
+ *    camera [R|t], pinhole fx, fy, cx, cy; pixel (i,j) is sampled at its
+ *    centre (i+0.5, j+0.5); depths are camera-space z; images are planar CHW
+ *    float32, row-major.
+ *  - quaternions are (w,x,y,z) and are normalised before use; scales are
+ *    linear axis lengths; opacities are activated values in [0,1].
+ *  - SH: real spherical harmonics with the Condon-Shortley phase, index
+ *    k = l^2 + l + m, degree <= 3, evaluated at the unit direction from the
+ *    primitive centre to the camera (Eq. 1); colour = max(0, 0.5 + sum).
+ *  - surfel opaque extent: a^2 + b^2 <= 2 ln 255 in scale-normalised local
+ *    coordinates (Sec. 4.1, Eq. 6-7 at w = 255).  z-buffer ties go to the
+ *    lower surfel index.  Surfels are two-sided.
+ *  - Gaussians: EWA projection with the affine Jacobian at the centre and a
+ *    fixed screen-space low-pass of 0.3 added to the 2D covariance;
+ *    eps_i = (5/3)(s_1 + s_2 + s_3) (Sec. 5).
+ *  - background: C_s = bg, D_s = +inf where no surfel covers a pixel.
+ *
+ * Memory: every pointer passed to the render and backward calls is a DEVICE
+ * pointer, C-contiguous, owned by the caller; the library never frees it.
+ * The library owns only its scratch (per-primitive records and tile lists),
+ * which grows on demand, is reused across calls and is released by
+ * ges_destroy_scene.  A scene is not thread-safe: use one scene per host
+ * thread and stream.
+ *
+ * Errors: every call returns a ges_status and never aborts.  On any status
+ * other than GES_OK the outputs are undefined; ges_last_error_message()
+ * returns a thread-local description of the last failure.
+ */
+#ifndef GES_H
+#define GES_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GES_API __attribute__((visibility("default")))
+#else
+#define GES_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GES_OK = 0,
+    GES_ERR_INVALID_ARG = 1,   /* null pointer, bad size, bad enum, zero-norm quaternion */
+    GES_ERR_CUDA = 2,          /* a CUDA runtime call failed (message says which) */
+    GES_ERR_OOM = 3,           /* scratch allocation failed */
+    GES_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up */
+    GES_ERR_INTERNAL = 5,      /* a device-side consistency check failed */
+    GES_ERR_UNSUPPORTED = 6,   /* no usable CUDA device of the required architecture */
+    GES_ERR_CAPACITY = 7       /* fixed-capacity (graph) buffers were too small */
+} ges_status;
+
+typedef enum { GES_F32 = 0, GES_F16 = 1, GES_BF16 = 2 } ges_dtype;
+
+typedef enum {
+    GES_MODE_FULL = 0,            /* Eq. 5 */
+    GES_MODE_SURFELS_ONLY = 1,    /* C = C_s (Table 5 ablation) */
+    GES_MODE_GAUSSIANS_ONLY = 2   /* C = C_G / W_G, no surfels (Table 5 ablation); bg where W_G = 0 */
+} ges_mode;
+
+typedef enum {
+    GES_EPS_ADAPTIVE = 0,  /* eps_i = eps_factor/3 * (s_1+s_2+s_3), Sec. 5 */
+    GES_EPS_ZERO = 1,      /* eps = 0, Table 5 ablation */
+    GES_EPS_CONST = 2      /* eps = eps_value (0.1 in Table 5) */
+} ges_eps_mode;
+
+typedef struct ges_scene ges_scene;   /* opaque */
+
+/* Scene description: DEVICE pointers, SoA, C-contiguous.  N = n_surfels,
+ * M = n_gaussians, K = (sh_degree+1)^2.  Positions are always float32;
+ * rotations, scales and opacities use attr_dtype, SH coefficients sh_dtype.
+ *   s_pos [N,3]  s_rot [N,4] (w,x,y,z)  s_scale [N,2]  s_sh [N,K,3]
+ *   g_pos [M,3]  g_rot [M,4] (w,x,y,z)  g_scale [M,3]  g_opac [M]  g_sh [M,K,3]
+ * The arrays must stay valid and unchanged while a render or backward call
+ * that uses them is in flight; the scene holds views, not copies. */
+typedef struct {
+    int64_t n_surfels, n_gaussians;
+    int32_t sh_degree;            /* 0..3 */
+    int32_t attr_dtype;           /* ges_dtype */
+    int32_t sh_dtype;             /* ges_dtype */
+    const float *s_pos;
+    const void *s_rot, *s_scale, *s_sh;
+    const float *g_pos;
+    const void *g_rot, *g_scale, *g_opac, *g_sh;
+} ges_scene_desc;
+
+/* Pinhole camera; width, height in [1, 16384]; fx, fy > 0; znear > 0. */
+typedef struct {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    float world_to_cam[12];       /* row-major [R|t] */
+    float znear;
+    float bg[3];
+} ges_camera;
+
+/* Render options; pass NULL for the paper's defaults (ges_default_opts). */
+typedef struct {
+    int32_t eps_mode;             /* ges_eps_mode */
+    float eps_value;              /* used by GES_EPS_CONST */
+    float eps_factor;             /* 5 (Sec. 5) */
+    float lowpass;                /* 0.3, added to the 2D covariance diagonal */
+    float alpha_min;              /* 1/255 (Sec. 3, after Eq. 4) */
+    float surfel_r2;              /* 2 ln 255 (Sec. 4.1) */
+    int32_t mode;                 /* ges_mode */
+} ges_render_opts;
+
+/* Gradient outputs (DEVICE pointers, float32, overwritten, not accumulated).
+ * Shapes follow the inputs: g_pos [M,3], g_rot [M,4], g_scale [M,3],
+ * g_opac [M], g_sh [M,K,3], s_sh [N,K,3].  Any pointer may be NULL to skip
+ * that group. */
+typedef struct {
+    float *g_pos, *g_rot, *g_scale, *g_opac, *g_sh, *s_sh;
+} ges_grads;
+
+/* Counters of the last completed render on a scene. */
+typedef struct {
+    int64_t visible_surfels, visible_gaussians;   /* passed culling */
+    int64_t surfel_tile_pairs, gauss_tile_pairs;  /* tile-list entries */
+    int32_t tiles_x, tiles_y;
+} ges_stats;
+
+/* Per-kernel device time accumulated while profiling is on
+ * (CUDA events on the scene's stream). */
+#define GES_PROFILE_SLOTS 8
+typedef struct {
+    int32_t n;                                  /* slots used */
+    char names[GES_PROFILE_SLOTS][24];
+    double ms[GES_PROFILE_SLOTS];               /* summed device milliseconds */
+    int64_t launches[GES_PROFILE_SLOTS];
+} ges_profile;
+
+/* Fill *out with the paper's defaults: adaptive eps with factor 5, lowpass
+ * 0.3, alpha_min 1/255, surfel_r2 2 ln 255, full mode.  GES_ERR_INVALID_ARG
+ * if out is NULL. */
+GES_API ges_status ges_default_opts(ges_render_opts *out);
+
+/* Create a scene that views the caller's attribute arrays (Sec. 3 defines the
+ * attributes).  Validates sizes, sh_degree, dtypes and pointers (NULL allowed
+ * only for empty primitive sets); selects the current CUDA device and checks
+ * that it is sm_103.  *out receives the handle, to be released with
+ * ges_destroy_scene. */
+GES_API ges_status ges_create_scene(const ges_scene_desc *desc, ges_scene **out);
+
+/* Re-point the scene at new arrays or sizes (after an optimiser step or a
+ * densification).  Same checks as ges_create_scene; scratch is kept and
+ * grown when needed. */
+GES_API ges_status ges_scene_update(ges_scene *scene, const ges_scene_desc *desc);
+
+/* Release the scene and its scratch (synchronises its stream first).
+ * NULL is accepted and ignored. */
+GES_API ges_status ges_destroy_scene(ges_scene *scene);
+
+/* Launch all further work of this scene on `stream` (a cudaStream_t; NULL is
+ * the legacy default stream). */
+GES_API ges_status ges_set_stream(ges_scene *scene, void *stream);
+
+/* Both passes of Sec. 3 and the composite of Eq. 5 for one camera.
+ * out_rgb [3,H,W] and out_depth [H,W] (D_s, +inf where no surfel) are device
+ * buffers.  Returns after the stream has completed the render (the call
+ * checks the device status word). */
+GES_API ges_status ges_render(ges_scene *scene, const ges_camera *cam, float *out_rgb, float *out_depth);
+
+/* As ges_render with options and two optional outputs: out_surfel_id [H,W]
+ * (z-buffer winner, -1 where none) and aux [H,W] (W_G of Eq. 3).  The
+ * backward pass needs both.  opts may be NULL (defaults). */
+GES_API ges_status ges_render_ex(ges_scene *scene, const ges_camera *cam, const ges_render_opts *opts,
+                         float *out_rgb, float *out_depth, int32_t *out_surfel_id, float *aux);
+
+/* Gradients of L = sum(dL_drgb * C) for the joint stage (Sec. 4.2): Gaussian
+ * position, rotation (through the normalisation), scale, opacity and SH, and
+ * surfel SH.  out_rgb, out_depth, surfel_id and aux must be the outputs of a
+ * ges_render_ex call with the same scene arrays, camera and options.  The
+ * depth-test indicator and the 1/255 clamp are piecewise constant and pass no
+ * gradient.  Results are deterministic (no floating-point atomics). */
+GES_API ges_status ges_render_backward(ges_scene *scene, const ges_camera *cam, const ges_render_opts *opts,
+                               const float *dL_drgb, const float *out_rgb, const float *out_depth,
+                               const int32_t *surfel_id, const float *aux, const ges_grads *grads);
+
+/* Render n_views cameras in one batch: view v uses scenes[scene_of_view[v]]
+ * (host arrays) and writes out_rgb[v] [3,H_v,W_v] and out_depth[v] [H_v,W_v]
+ * (host arrays of device pointers; out_depth entries may be NULL).  All
+ * scenes must live on the same device; the batch runs on the stream of
+ * scenes[0].  Per-view semantics are exactly those of ges_render_ex. */
+GES_API ges_status ges_render_batch(ges_scene *const *scenes, const ges_camera *cams, const int32_t *scene_of_view,
+                            int32_t n_views, const ges_render_opts *opts,
+                            float *const *out_rgb, float *const *out_depth);
+
+/* Counters of the last render on this scene. */
+GES_API ges_status ges_get_stats(const ges_scene *scene, ges_stats *out);
+
+/* Turn per-kernel CUDA-event timing on (1) or off (0) and reset it. */
+GES_API ges_status ges_set_profiling(ges_scene *scene, int32_t enable);
+
+/* Read the per-kernel timing accumulated since profiling was enabled
+ * (synchronises the scene's stream). */
+GES_API ges_status ges_get_profile(ges_scene *scene, ges_profile *out);
+
+/* Thread-local message of the last failing call ("" if none). */
+GES_API const char *ges_last_error_message(void);
+
+/* ABI version of this header. */
+GES_API int32_t ges_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GES_H */

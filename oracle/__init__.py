@@ -5,7 +5,7 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 its Python binding) never does; the two share no code.
 """
 from .oracle import (DEFAULT_OPTS, build, load, render, backward, sh_basis, surfel_eval,
-                     surfel_info, gauss_info, id_validity)
+                     surfel_info, gauss_info, id_validity, touching)
 
 __all__ = ["DEFAULT_OPTS", "build", "load", "render", "backward", "sh_basis", "surfel_eval",
-           "surfel_info", "gauss_info", "id_validity"]
+           "surfel_info", "gauss_info", "id_validity", "touching"]

@@ -591,6 +591,49 @@ int ora_surfel_eval(const ora_scene *S, const ora_camera *c, const ora_opts *o, 
     return ORA_OK;
 }
 
+/* Primitives that touch a flagged pixel (flag[pix] != 0): a Gaussian whose
+   alpha (before the clamp) reaches alpha_min - tol_alpha there, a surfel whose
+   fragment there lies inside its disc band in front of the near plane.  Used to
+   leave out of gradient comparisons the primitives whose gradient depends on
+   which of several equally correct forward answers was taken. */
+int ora_touching(const ora_scene *S, const ora_camera *c, const ora_opts *o, const uint8_t *flag,
+                 uint8_t *s_touch, uint8_t *g_touch)
+{
+    if (!check_args(S, c, o)) return ORA_BAD_ARG;
+    prep_t P;
+    int st = prepare(S, c, o, 0, &P);
+    if (st != ORA_OK) { prep_free(&P); return st; }
+    const int W = c->width;
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t s = 0; s < S->n_surfels; ++s) {
+        const surf_t *sf = &P.sf[s];
+        s_touch[s] = 0;
+        if (!sf->valid) continue;
+        for (int j = sf->y0; j <= sf->y1 && !s_touch[s]; ++j)
+            for (int i = sf->x0; i <= sf->x1; ++i) {
+                if (!flag[(int64_t)j * W + i]) continue;
+                double d[3], z, rho;
+                pixel_ray(c, i, j, d);
+                if (surfel_hit(sf, d, &z, &rho, NULL) && z > c->znear &&
+                    rho <= o->surfel_r2 * (1.0 + o->tol_disc_rel)) { s_touch[s] = 1; break; }
+            }
+    }
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t k = 0; k < S->n_gaussians; ++k) {
+        const gauss_t *g = &P.gs[k];
+        g_touch[k] = 0;
+        if (!g->valid) continue;
+        for (int j = g->y0; j <= g->y1 && !g_touch[k]; ++j)
+            for (int i = g->x0; i <= g->x1; ++i)
+                if (flag[(int64_t)j * W + i] && gauss_alpha(g, i, j) >= o->alpha_min - o->tol_alpha) {
+                    g_touch[k] = 1;
+                    break;
+                }
+    }
+    prep_free(&P);
+    return ORA_OK;
+}
+
 /* Per-primitive quantities for unit pins.
    surfel: out = [valid, rgb(3), pc(3), n(3), x0, x1, y0, y1]                 (14)
    gauss:  out = [valid, px, py, ca, cb, cc, S2a, S2b, S2c, sigma, d, eps,

@@ -74,6 +74,7 @@ def load():
         lib.ora_surfel_eval.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_int64] + [C.c_void_p] * 7
         lib.ora_surfel_info.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_int64, C.c_void_p]
         lib.ora_gauss_info.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_int64, C.c_void_p]
+        lib.ora_touching.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_void_p, C.c_void_p, C.c_void_p]
         _lib = lib
     return _lib
 
@@ -208,3 +209,16 @@ def id_validity(scene, cam, ref, ids, opts=None):
         good_empty = (cand < 0) & ((wid < 0) | ((okw == 1) & (np.abs(rhow - r2) <= o["tol_disc_rel"] * r2)))
         valid[yy, xx] = np.where(cand >= 0, good_hit, good_empty)
     return valid
+
+
+def touching(scene, cam, flag, opts=None):
+    """(surfel_mask, gaussian_mask): primitives that touch a pixel where ``flag`` is set."""
+    lib = load()
+    pin = _Pinned(scene, cam, opts)
+    f = np.ascontiguousarray(flag, np.uint8)
+    assert f.shape == (cam.height, cam.width)
+    st_ = np.empty(scene.n_surfels, np.uint8)
+    gt_ = np.empty(scene.n_gaussians, np.uint8)
+    _check(lib.ora_touching(C.byref(pin.s), C.byref(pin.c), C.byref(pin.o), f.ctypes.data, st_.ctypes.data,
+                            gt_.ctypes.data), "touching")
+    return st_.astype(bool), gt_.astype(bool)

@@ -1,0 +1,19 @@
+"""GES (Gaussian-enhanced Surfels) renderer for GB300 (sm_103a).
+
+The CUDA library ``libges.so`` implements the two-pass render of Sec. 3
+(surfel z-buffer, depth-tested sorting-free Gaussian accumulation, Eq. 5
+composite), its backward pass for the joint optimisation stage (Sec. 4.2) and
+batched multi-view rendering, behind the C ABI of ``include/ges.h``.
+``native`` is the ctypes binding with the ABI's names; ``render`` is the thin
+PyTorch layer (device memory, streams, autograd).
+"""
+from . import build, native  # noqa: F401
+
+__all__ = ["build", "native", "render"]
+
+
+def __getattr__(name):
+    if name == "render":
+        from . import render as _r
+        return _r
+    raise AttributeError(name)

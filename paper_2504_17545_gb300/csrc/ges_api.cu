@@ -1,0 +1,492 @@
+// Host side of the C ABI declared in include/ges.h.
+//
+// Owns the per-scene scratch (raster records, visible lists, tile counts and
+// lists), validates every argument before anything is launched, converts the
+// camera to the kernels' parameter block, and reads the device status word
+// after each render (list overflow -> grow and re-render; zero-norm
+// quaternion -> GES_ERR_INVALID_ARG).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ges_internal.cuh"
+
+using namespace ges;
+
+namespace {
+
+thread_local std::string g_err;
+
+ges_status fail(ges_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+ges_status cuda_fail(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation) return fail(GES_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(GES_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define GES_CUDA(call)                                          \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);     \
+    } while (0)
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t want)
+    {
+        if (want <= bytes) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e == cudaSuccess) bytes = want;
+        return e;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+};
+
+const char *kFwdNames[4] = {"preprocess", "scan", "fill", "raster"};
+const char *kBwdNames[2] = {"gauss_bwd", "surfel_bwd"};
+
+}  // namespace
+
+struct ges_scene {
+    ges_scene_desc desc{};
+    SceneView view{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    DevBuf s_rec, s_rgb, g_rec, s_vis, g_vis;
+    DevBuf s_cnt, g_cnt, s_off, g_off, s_cur, g_cur;
+    DevBuf s_list, g_list;
+    DevBuf status;                 // ST_WORDS per view slot
+    unsigned *status_host = nullptr;
+    int status_slots = 0;
+    int64_t tiles_cap = 0;
+    int64_t s_cap = 0, g_cap = 0;
+    ges_stats stats{};
+    // profiling
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;
+    ges_profile profile{};
+};
+
+namespace {
+
+bool dtype_ok(int d) { return d == GES_F32 || d == GES_F16 || d == GES_BF16; }
+
+ges_status check_desc(const ges_scene_desc *d)
+{
+    if (!d) return fail(GES_ERR_INVALID_ARG, "scene description is NULL");
+    if (d->n_surfels < 0 || d->n_gaussians < 0) return fail(GES_ERR_INVALID_ARG, "negative primitive count");
+    if (d->n_surfels > (int64_t)1 << 30 || d->n_gaussians > (int64_t)1 << 30)
+        return fail(GES_ERR_INVALID_ARG, "more than 2^30 primitives of one kind");
+    if (d->sh_degree < 0 || d->sh_degree > 3) return fail(GES_ERR_INVALID_ARG, "sh_degree %d not in [0,3]", d->sh_degree);
+    if (!dtype_ok(d->attr_dtype) || !dtype_ok(d->sh_dtype)) return fail(GES_ERR_INVALID_ARG, "unknown dtype");
+    if (d->n_surfels > 0 && (!d->s_pos || !d->s_rot || !d->s_scale || !d->s_sh))
+        return fail(GES_ERR_INVALID_ARG, "surfel attribute pointer is NULL");
+    if (d->n_gaussians > 0 && (!d->g_pos || !d->g_rot || !d->g_scale || !d->g_opac || !d->g_sh))
+        return fail(GES_ERR_INVALID_ARG, "Gaussian attribute pointer is NULL");
+    return GES_OK;
+}
+
+ges_status check_device(int *dev)
+{
+    GES_CUDA(cudaGetDevice(dev));
+    cudaDeviceProp p;
+    GES_CUDA(cudaGetDeviceProperties(&p, *dev));
+    if (!(p.major == 10 && p.minor == 3))
+        return fail(GES_ERR_UNSUPPORTED, "device %d is sm_%d%d; this library is built for sm_103a only", *dev,
+                    p.major, p.minor);
+    return GES_OK;
+}
+
+void set_view(ges_scene *s)
+{
+    const ges_scene_desc &d = s->desc;
+    s->view = SceneView{d.n_surfels, d.n_gaussians, d.sh_degree, d.attr_dtype, d.sh_dtype,
+                        d.s_pos, d.s_rot, d.s_scale, d.s_sh, d.g_pos, d.g_rot, d.g_scale, d.g_opac, d.g_sh};
+}
+
+bool finite_all(const float *v, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+ges_status make_cam(const ges_camera *c, CamParams &C)
+{
+    if (!c) return fail(GES_ERR_INVALID_ARG, "camera is NULL");
+    if (c->width < 1 || c->height < 1 || c->width > 16384 || c->height > 16384)
+        return fail(GES_ERR_INVALID_ARG, "image size %dx%d not in [1,16384]", c->width, c->height);
+    if (!(c->fx > 0.f) || !(c->fy > 0.f) || !std::isfinite(c->fx) || !std::isfinite(c->fy))
+        return fail(GES_ERR_INVALID_ARG, "focal lengths must be positive and finite");
+    if (!std::isfinite(c->cx) || !std::isfinite(c->cy) || !finite_all(c->world_to_cam, 12) || !finite_all(c->bg, 3))
+        return fail(GES_ERR_INVALID_ARG, "camera has a non-finite entry");
+    if (!(c->znear > 0.f) || !std::isfinite(c->znear)) return fail(GES_ERR_INVALID_ARG, "znear must be positive");
+    for (int r = 0; r < 3; ++r) {
+        for (int k = 0; k < 3; ++k) C.R[3 * r + k] = c->world_to_cam[4 * r + k];
+        C.t[r] = c->world_to_cam[4 * r + 3];
+    }
+    // camera centre o = -R^T t in double, then rounded
+    for (int j = 0; j < 3; ++j) {
+        double o = 0.0;
+        for (int r = 0; r < 3; ++r) o -= (double)c->world_to_cam[4 * r + j] * (double)c->world_to_cam[4 * r + 3];
+        C.ocam[j] = (float)o;
+    }
+    C.fx = c->fx; C.fy = c->fy; C.cx = c->cx; C.cy = c->cy;
+    C.znear = c->znear;
+    C.izn = 1.f / c->znear;
+    for (int k = 0; k < 3; ++k) C.bg[k] = c->bg[k];
+    C.W = c->width; C.H = c->height;
+    C.tiles_x = (c->width + kTile - 1) / kTile;
+    C.tiles_y = (c->height + kTile - 1) / kTile;
+    return GES_OK;
+}
+
+ges_status make_opts(const ges_render_opts *o, OptParams &O)
+{
+    ges_render_opts d;
+    ges_default_opts(&d);
+    if (!o) o = &d;
+    if (o->eps_mode < 0 || o->eps_mode > 2) return fail(GES_ERR_INVALID_ARG, "eps_mode %d unknown", o->eps_mode);
+    if (o->mode < 0 || o->mode > 2) return fail(GES_ERR_INVALID_ARG, "mode %d unknown", o->mode);
+    if (!(o->alpha_min > 0.f && o->alpha_min <= 1.f)) return fail(GES_ERR_INVALID_ARG, "alpha_min must be in (0,1]");
+    if (!(o->surfel_r2 > 0.f) || !std::isfinite(o->surfel_r2)) return fail(GES_ERR_INVALID_ARG, "surfel_r2 must be > 0");
+    if (!(o->lowpass >= 0.f) || !std::isfinite(o->lowpass)) return fail(GES_ERR_INVALID_ARG, "lowpass must be >= 0");
+    if (!std::isfinite(o->eps_factor) || !std::isfinite(o->eps_value))
+        return fail(GES_ERR_INVALID_ARG, "eps parameters must be finite");
+    O.eps_mode = o->eps_mode;
+    O.eps_value = o->eps_value;
+    O.eps_factor = o->eps_factor;
+    O.lowpass = o->lowpass;
+    O.alpha_min = o->alpha_min;
+    O.surfel_r2 = o->surfel_r2;
+    O.surfel_r = std::sqrt(o->surfel_r2);
+    O.mode = o->mode;
+    return GES_OK;
+}
+
+ges_status ensure_scratch(ges_scene *s, int64_t T, int slots, cudaStream_t st)
+{
+    const int64_t N = std::max<int64_t>(s->desc.n_surfels, 1), M = std::max<int64_t>(s->desc.n_gaussians, 1);
+    cudaError_t e;
+    if ((e = s->s_rec.ensure(N * 64)) || (e = s->s_rgb.ensure(N * 16)) || (e = s->g_rec.ensure(M * 64)) ||
+        (e = s->s_vis.ensure(N * 4)) || (e = s->g_vis.ensure(M * 4)))
+        return cuda_fail(e, "scratch allocation (records)");
+    if (T > s->tiles_cap) {
+        const int64_t Tc = T;
+        DevBuf *cnts[2] = {&s->s_cnt, &s->g_cnt};
+        for (DevBuf *b : cnts) {
+            if ((e = b->ensure((Tc + 1) * 4))) return cuda_fail(e, "scratch allocation (tile counts)");
+            if ((e = cudaMemsetAsync(b->p, 0, (Tc + 1) * 4, st))) return cuda_fail(e, "cudaMemsetAsync");
+        }
+        if ((e = s->s_off.ensure((Tc + 1) * 4)) || (e = s->g_off.ensure((Tc + 1) * 4)) ||
+            (e = s->s_cur.ensure((Tc + 1) * 4)) || (e = s->g_cur.ensure((Tc + 1) * 4)))
+            return cuda_fail(e, "scratch allocation (tile offsets)");
+        s->tiles_cap = Tc;
+    }
+    if (s->s_cap == 0) s->s_cap = std::max<int64_t>((int64_t)1 << 20, 4 * s->desc.n_surfels);
+    if (s->g_cap == 0) s->g_cap = std::max<int64_t>((int64_t)1 << 20, 4 * s->desc.n_gaussians);
+    if ((e = s->s_list.ensure(s->s_cap * 4)) || (e = s->g_list.ensure(s->g_cap * 4)))
+        return cuda_fail(e, "scratch allocation (tile lists)");
+    if (slots > s->status_slots) {
+        if ((e = s->status.ensure((size_t)slots * ST_WORDS * 4))) return cuda_fail(e, "status allocation");
+        if (s->status_host) cudaFreeHost(s->status_host);
+        s->status_host = nullptr;
+        if ((e = cudaMallocHost(&s->status_host, (size_t)slots * ST_WORDS * 4))) return cuda_fail(e, "cudaMallocHost");
+        s->status_slots = slots;
+    }
+    return GES_OK;
+}
+
+ViewScratch scratch_of(ges_scene *s, int slot)
+{
+    ViewScratch X;
+    X.s_rec = (float4 *)s->s_rec.p; X.s_rgb = (float4 *)s->s_rgb.p; X.g_rec = (float4 *)s->g_rec.p;
+    X.s_vis = (int *)s->s_vis.p; X.g_vis = (int *)s->g_vis.p;
+    X.s_cnt = (int *)s->s_cnt.p; X.g_cnt = (int *)s->g_cnt.p;
+    X.s_off = (int *)s->s_off.p; X.g_off = (int *)s->g_off.p;
+    X.s_cur = (int *)s->s_cur.p; X.g_cur = (int *)s->g_cur.p;
+    X.s_list = (int *)s->s_list.p; X.g_list = (int *)s->g_list.p;
+    X.s_cap = s->s_cap; X.g_cap = s->g_cap;
+    X.status = (unsigned *)s->status.p + (size_t)slot * ST_WORDS;
+    return X;
+}
+
+ges_status ensure_events(ges_scene *s, int n)
+{
+    while ((int)s->ev.size() < n) {
+        cudaEvent_t e;
+        GES_CUDA(cudaEventCreate(&e));
+        s->ev.push_back(e);
+    }
+    return GES_OK;
+}
+
+int prof_slot(ges_scene *s, const char *name)
+{
+    for (int i = 0; i < s->profile.n; ++i)
+        if (std::strncmp(s->profile.names[i], name, 23) == 0) return i;
+    if (s->profile.n >= GES_PROFILE_SLOTS) return -1;
+    const int i = s->profile.n++;
+    std::strncpy(s->profile.names[i], name, 23);
+    s->profile.names[i][23] = 0;
+    return i;
+}
+
+// Accumulate the event intervals of the last launch group (stream already synchronised).
+void prof_collect(ges_scene *s, int first_ev, const char *const *names, int n)
+{
+    for (int k = 0; k < n; ++k) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, s->ev[first_ev + k], s->ev[first_ev + k + 1]) != cudaSuccess) continue;
+        const int i = prof_slot(s, names[k]);
+        if (i < 0) continue;
+        s->profile.ms[i] += ms;
+        s->profile.launches[i] += 1;
+    }
+}
+
+// Launch the forward of every view, synchronise once, check every status
+// slot; on list overflow grow the lists and repeat.
+ges_status render_views(ges_scene *const *scenes, const CamParams *cams, const int32_t *scene_of_view, int n,
+                        const OptParams &O, float *const *rgb, float *const *depth, int32_t *const *ids,
+                        float *const *auxs)
+{
+    ges_scene *s0 = scenes[scene_of_view[0]];
+    cudaStream_t st = s0->stream;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        // scratch for every scene used; status slots live in the first scene
+        for (int v = 0; v < n; ++v) {
+            ges_scene *s = scenes[scene_of_view[v]];
+            ges_status r = ensure_scratch(s, (int64_t)cams[v].tiles_x * cams[v].tiles_y, s == s0 ? n : 1, st);
+            if (r != GES_OK) return r;
+        }
+        if (s0->status_slots < n) {
+            ges_status r = ensure_scratch(s0, 1, n, st);
+            if (r != GES_OK) return r;
+        }
+        GES_CUDA(cudaMemsetAsync(s0->status.p, 0, (size_t)n * ST_WORDS * 4, st));
+        const bool prof = s0->prof && n == 1;
+        if (prof) {
+            ges_status r = ensure_events(s0, 5);
+            if (r != GES_OK) return r;
+        }
+        for (int v = 0; v < n; ++v) {
+            ges_scene *s = scenes[scene_of_view[v]];
+            ViewScratch X = scratch_of(s, 0);
+            X.status = (unsigned *)s0->status.p + (size_t)v * ST_WORDS;
+            cudaError_t e = launch_forward(s->view, cams[v], O, X, rgb[v], depth ? depth[v] : nullptr,
+                                           ids ? ids[v] : nullptr, auxs ? auxs[v] : nullptr, st,
+                                           prof ? s0->ev.data() : nullptr);
+            if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+        }
+        GES_CUDA(cudaMemcpyAsync(s0->status_host, s0->status.p, (size_t)n * ST_WORDS * 4, cudaMemcpyDeviceToHost, st));
+        GES_CUDA(cudaStreamSynchronize(st));
+        if (prof) prof_collect(s0, 0, kFwdNames, 4);
+        bool overflow = false;
+        for (int v = 0; v < n; ++v) {
+            const unsigned *w = s0->status_host + (size_t)v * ST_WORDS;
+            ges_scene *s = scenes[scene_of_view[v]];
+            if (w[ST_FLAGS] & FLAG_BADQ)
+                return fail(GES_ERR_INVALID_ARG, "view %d: a rotation quaternion has zero norm or is not finite", v);
+            if (w[ST_FLAGS] & FLAG_SOVF) {
+                s->s_cap = std::max<int64_t>(s->s_cap * 2, (int64_t)(w[ST_SPAIRS] * 1.25) + 1024);
+                overflow = true;
+            }
+            if (w[ST_FLAGS] & FLAG_GOVF) {
+                s->g_cap = std::max<int64_t>(s->g_cap * 2, (int64_t)(w[ST_GPAIRS] * 1.25) + 1024);
+                overflow = true;
+            }
+            s->stats.visible_surfels = w[ST_SVIS];
+            s->stats.visible_gaussians = w[ST_GVIS];
+            s->stats.surfel_tile_pairs = w[ST_SPAIRS];
+            s->stats.gauss_tile_pairs = w[ST_GPAIRS];
+            s->stats.tiles_x = cams[v].tiles_x;
+            s->stats.tiles_y = cams[v].tiles_y;
+        }
+        if (!overflow) return GES_OK;
+    }
+    return fail(GES_ERR_INTERNAL, "tile lists kept overflowing after growing them");
+}
+
+}  // namespace
+
+extern "C" {
+
+ges_status ges_default_opts(ges_render_opts *out)
+{
+    if (!out) return fail(GES_ERR_INVALID_ARG, "opts is NULL");
+    out->eps_mode = GES_EPS_ADAPTIVE;
+    out->eps_value = 0.1f;
+    out->eps_factor = 5.f;
+    out->lowpass = 0.3f;
+    out->alpha_min = 1.f / 255.f;
+    out->surfel_r2 = (float)(2.0 * std::log(255.0));
+    out->mode = GES_MODE_FULL;
+    return GES_OK;
+}
+
+ges_status ges_create_scene(const ges_scene_desc *desc, ges_scene **out)
+{
+    if (!out) return fail(GES_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    ges_status r = check_desc(desc);
+    if (r != GES_OK) return r;
+    int dev = 0;
+    if ((r = check_device(&dev)) != GES_OK) return r;
+    ges_scene *s = new (std::nothrow) ges_scene();
+    if (!s) return fail(GES_ERR_OOM, "host allocation failed");
+    s->desc = *desc;
+    s->device = dev;
+    set_view(s);
+    *out = s;
+    return GES_OK;
+}
+
+ges_status ges_scene_update(ges_scene *s, const ges_scene_desc *desc)
+{
+    if (!s) return fail(GES_ERR_INVALID_ARG, "scene is NULL");
+    ges_status r = check_desc(desc);
+    if (r != GES_OK) return r;
+    s->desc = *desc;
+    set_view(s);
+    return GES_OK;
+}
+
+ges_status ges_destroy_scene(ges_scene *s)
+{
+    if (!s) return GES_OK;
+    cudaStreamSynchronize(s->stream);
+    DevBuf *bufs[] = {&s->s_rec, &s->s_rgb, &s->g_rec, &s->s_vis, &s->g_vis, &s->s_cnt, &s->g_cnt, &s->s_off,
+                      &s->g_off, &s->s_cur, &s->g_cur, &s->s_list, &s->g_list, &s->status};
+    for (DevBuf *b : bufs) b->release();
+    if (s->status_host) cudaFreeHost(s->status_host);
+    for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
+    delete s;
+    return GES_OK;
+}
+
+ges_status ges_set_stream(ges_scene *s, void *stream)
+{
+    if (!s) return fail(GES_ERR_INVALID_ARG, "scene is NULL");
+    s->stream = (cudaStream_t)stream;
+    return GES_OK;
+}
+
+ges_status ges_render_ex(ges_scene *s, const ges_camera *cam, const ges_render_opts *opts, float *out_rgb,
+                         float *out_depth, int32_t *out_surfel_id, float *aux)
+{
+    if (!s) return fail(GES_ERR_INVALID_ARG, "scene is NULL");
+    if (!out_rgb) return fail(GES_ERR_INVALID_ARG, "out_rgb is NULL");
+    CamParams C;
+    OptParams O;
+    ges_status r = make_cam(cam, C);
+    if (r != GES_OK) return r;
+    if ((r = make_opts(opts, O)) != GES_OK) return r;
+    const int32_t zero = 0;
+    float *rgb[1] = {out_rgb};
+    float *dep[1] = {out_depth};
+    int32_t *ids[1] = {out_surfel_id};
+    float *aux1[1] = {aux};
+    return render_views(&s, &C, &zero, 1, O, rgb, dep, ids, aux1);
+}
+
+ges_status ges_render(ges_scene *s, const ges_camera *cam, float *out_rgb, float *out_depth)
+{
+    return ges_render_ex(s, cam, nullptr, out_rgb, out_depth, nullptr, nullptr);
+}
+
+ges_status ges_render_backward(ges_scene *s, const ges_camera *cam, const ges_render_opts *opts,
+                               const float *dL_drgb, const float *out_rgb, const float *out_depth,
+                               const int32_t *surfel_id, const float *aux, const ges_grads *grads)
+{
+    if (!s) return fail(GES_ERR_INVALID_ARG, "scene is NULL");
+    if (!grads) return fail(GES_ERR_INVALID_ARG, "grads is NULL");
+    if (!dL_drgb || !out_rgb || !out_depth || !surfel_id || !aux)
+        return fail(GES_ERR_INVALID_ARG, "backward needs dL_drgb, out_rgb, out_depth, surfel_id and aux");
+    CamParams C;
+    OptParams O;
+    ges_status r = make_cam(cam, C);
+    if (r != GES_OK) return r;
+    if ((r = make_opts(opts, O)) != GES_OK) return r;
+    const bool prof = s->prof;
+    if (prof && (r = ensure_events(s, 8)) != GES_OK) return r;
+    cudaError_t e = launch_backward(s->view, C, O, dL_drgb, out_rgb, out_depth, surfel_id, aux, *grads, nullptr,
+                                    s->stream, prof ? s->ev.data() + 5 : nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+    GES_CUDA(cudaStreamSynchronize(s->stream));
+    if (prof) prof_collect(s, 5, kBwdNames, 2);
+    return GES_OK;
+}
+
+ges_status ges_render_batch(ges_scene *const *scenes, const ges_camera *cams, const int32_t *scene_of_view,
+                            int32_t n_views, const ges_render_opts *opts, float *const *out_rgb,
+                            float *const *out_depth)
+{
+    if (!scenes || !cams || !scene_of_view || !out_rgb) return fail(GES_ERR_INVALID_ARG, "NULL batch argument");
+    if (n_views <= 0) return fail(GES_ERR_INVALID_ARG, "n_views must be positive");
+    OptParams O;
+    ges_status r = make_opts(opts, O);
+    if (r != GES_OK) return r;
+    std::vector<CamParams> C(n_views);
+    int max_scene = 0;
+    for (int v = 0; v < n_views; ++v) {
+        if (scene_of_view[v] < 0) return fail(GES_ERR_INVALID_ARG, "scene_of_view[%d] is negative", v);
+        max_scene = std::max(max_scene, (int)scene_of_view[v]);
+        if (!out_rgb[v]) return fail(GES_ERR_INVALID_ARG, "out_rgb[%d] is NULL", v);
+        if ((r = make_cam(cams + v, C[v])) != GES_OK) return r;
+    }
+    for (int k = 0; k <= max_scene; ++k)
+        if (!scenes[k]) return fail(GES_ERR_INVALID_ARG, "scenes[%d] is NULL", k);
+    return render_views(scenes, C.data(), scene_of_view, n_views, O, out_rgb, out_depth, nullptr, nullptr);
+}
+
+ges_status ges_get_stats(const ges_scene *s, ges_stats *out)
+{
+    if (!s || !out) return fail(GES_ERR_INVALID_ARG, "NULL argument");
+    *out = s->stats;
+    return GES_OK;
+}
+
+ges_status ges_set_profiling(ges_scene *s, int32_t enable)
+{
+    if (!s) return fail(GES_ERR_INVALID_ARG, "scene is NULL");
+    s->prof = enable != 0;
+    std::memset(&s->profile, 0, sizeof s->profile);
+    return GES_OK;
+}
+
+ges_status ges_get_profile(ges_scene *s, ges_profile *out)
+{
+    if (!s || !out) return fail(GES_ERR_INVALID_ARG, "NULL argument");
+    GES_CUDA(cudaStreamSynchronize(s->stream));
+    *out = s->profile;
+    return GES_OK;
+}
+
+const char *ges_last_error_message(void) { return g_err.c_str(); }
+
+int32_t ges_version(void) { return 1; }
+
+}  // extern "C"

@@ -1,0 +1,288 @@
+// Backward pass of the GES render for the joint optimisation stage (Sec. 4.2):
+// gradients of L = sum(dL/dC * C) with respect to Gaussian position, rotation,
+// scale, opacity and SH coefficients, and surfel SH coefficients (surfel
+// geometry is fixed in that stage and gets none).
+//
+// Gather form, no atomics: a warp owns 32 consecutive primitives.  Each lane
+// sets up one primitive (the same device function as the forward pass, so the
+// alpha and depth-test decisions are bit-identical); then, primitive by
+// primitive, the warp sweeps that primitive's pixel bbox with one pixel per
+// lane and reduces the per-lane partial sums with a fixed butterfly.  Finally
+// each lane runs the chain rule for its own primitive.  The result is
+// deterministic.
+//
+// Per (Gaussian i, pixel) that passes the clamp and the depth test, with
+// k = 1/(1+W_G) (Eq. 5; 1/W_G in the Gaussians-only mode) and g = dL/dC:
+//   dL/dc_i += alpha k g,  dL/dalpha = k g.(c_i - C),
+//   alpha = sigma e^(-q/2):  dalpha/dsigma = e^(-q/2),  dalpha/dq = -alpha/2,
+// then q -> (projected centre, conic) -> Sigma2 -> (Sigma3 -> s, r) and
+// (Jacobian, centre -> p), and c_i -> SH and p through the view direction.
+// Surfel s: dL/dc_s = sum over pixels won by s of k g, then SH.
+#include "ges_internal.cuh"
+
+namespace ges {
+
+namespace {
+
+__device__ __forceinline__ float warp_sum(float x)
+{
+    for (int d = 16; d >= 1; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
+    return x;
+}
+
+struct GStage {
+    float px, py, pxl, pyl, ca, cb, cc, sigma, key, r, g, b;
+    float ia, ib, ic;
+    int x0, y0, x1, y1;
+    int vis;
+};
+
+__global__ void __launch_bounds__(256) k_gauss_bwd(SceneView S, CamParams C, OptParams O,
+                                                  const float *__restrict__ dL, const float *__restrict__ rgb,
+                                                  const float *__restrict__ depth, const float *__restrict__ aux,
+                                                  ges_grads G)
+{
+    __shared__ GStage sg[8][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t base = ((int64_t)blockIdx.x * 8 + warp) * 32;
+    if (base >= S.M) return;
+    const int64_t gi = base + lane;
+    const int64_t HW = (int64_t)C.W * C.H;
+    // 1) lane-parallel set-up
+    {
+        GaussOut o;
+        o.visible = false;
+        if (gi < S.M) gauss_setup(S, C, O, gi, o);
+        GStage &s = sg[warp][lane];
+        s.vis = o.visible ? 1 : 0;
+        if (o.visible) {
+            s.px = o.rec.px; s.py = o.rec.py; s.pxl = o.rec.pxl; s.pyl = o.rec.pyl;
+            s.ca = o.rec.ca; s.cb = o.rec.cb; s.cc = o.rec.cc; s.sigma = o.rec.sigma; s.key = o.rec.key;
+            s.r = o.rec.r; s.g = o.rec.g; s.b = o.rec.b;
+            s.ia = o.ia; s.ib = o.ib; s.ic = o.ic;
+            s.x0 = o.x0; s.y0 = o.y0; s.x1 = o.x1; s.y1 = o.y1;
+        }
+    }
+    __syncwarp();
+    // 2) per Gaussian, sweep its pixels
+    float my[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // dc(3), dsigma, dpx, dpy, dia, dib, dic
+    const bool gmode = O.mode == GES_MODE_GAUSSIANS_ONLY;
+    for (int j = 0; j < 32; ++j) {
+        const GStage &s = sg[warp][j];
+        if (!s.vis) continue;
+        GaussRec g;
+        g.px = s.px; g.py = s.py; g.pxl = s.pxl; g.pyl = s.pyl;
+        g.ca = s.ca; g.cb = s.cb; g.cc = s.cc; g.sigma = s.sigma;
+        const int w = s.x1 - s.x0 + 1, npx = w * (s.y1 - s.y0 + 1);
+        float acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int k = lane; k < npx; k += 32) {
+            const int x = s.x0 + k % w, y = s.y0 + k / w;
+            const int64_t pix = (int64_t)y * C.W + x;
+            float e;
+            const float a = gauss_alpha(g, x + 0.5f, y + 0.5f, e);
+            if (!(a >= O.alpha_min) || !(s.key < __ldg(depth + pix))) continue;
+            const float W = __ldg(aux + pix);
+            const float kk = gmode ? 1.f / W : 1.f / (1.f + W);
+            const float g0 = __ldg(dL + pix), g1 = __ldg(dL + HW + pix), g2 = __ldg(dL + 2 * HW + pix);
+            const float C0 = __ldg(rgb + pix), C1 = __ldg(rgb + HW + pix), C2 = __ldg(rgb + 2 * HW + pix);
+            acc[0] += a * kk * g0;
+            acc[1] += a * kk * g1;
+            acc[2] += a * kk * g2;
+            const float dLda = kk * (g0 * (s.r - C0) + g1 * (s.g - C1) + g2 * (s.b - C2));
+            acc[3] += dLda * e;
+            const float dLdq = -0.5f * dLda * a;
+            const float dx = (x + 0.5f - s.px) - s.pxl, dy = (y + 0.5f - s.py) - s.pyl;
+            acc[4] += dLdq * -2.f * (s.ia * dx + s.ib * dy);
+            acc[5] += dLdq * -2.f * (s.ib * dx + s.ic * dy);
+            acc[6] += dLdq * dx * dx;
+            acc[7] += dLdq * 2.f * dx * dy;
+            acc[8] += dLdq * dy * dy;
+        }
+        for (int c = 0; c < 9; ++c) {
+            const float t = warp_sum(acc[c]);
+            if (lane == j) my[c] = t;
+        }
+    }
+    if (gi >= S.M) return;
+    const int K = (S.deg + 1) * (S.deg + 1);
+    // 3) chain rule for this lane's Gaussian
+    GaussOut o;
+    gauss_setup(S, C, O, gi, o);
+    if (!o.visible || O.mode == GES_MODE_SURFELS_ONLY) {
+        if (G.g_pos) for (int a = 0; a < 3; ++a) G.g_pos[3 * gi + a] = 0.f;
+        if (G.g_rot) for (int a = 0; a < 4; ++a) G.g_rot[4 * gi + a] = 0.f;
+        if (G.g_scale) for (int a = 0; a < 3; ++a) G.g_scale[3 * gi + a] = 0.f;
+        if (G.g_opac) G.g_opac[gi] = 0.f;
+        if (G.g_sh) for (int a = 0; a < 3 * K; ++a) G.g_sh[3 * K * gi + a] = 0.f;
+        return;
+    }
+    const float *dc = my;
+    float gp[3] = {0.f, 0.f, 0.f};
+    // colour -> SH coefficients and position (through the view direction)
+    {
+        float Y[16], dY[16][3];
+        sh_basis(K, o.dir[0], o.dir[1], o.dir[2], Y);
+        sh_basis_grad(K, o.dir[0], o.dir[1], o.dir[2], dY);
+        float gc[3];
+        for (int c = 0; c < 3; ++c) gc[c] = o.raw[c] > 0.f ? dc[c] : 0.f;
+        float gd[3] = {0.f, 0.f, 0.f};
+        for (int k = 0; k < K; ++k) {
+            float sh[3];
+            for (int c = 0; c < 3; ++c) sh[c] = load_attr(S.g_sh, 3 * K * gi + 3 * k + c, S.sh_dtype);
+            if (G.g_sh) for (int c = 0; c < 3; ++c) G.g_sh[3 * K * gi + 3 * k + c] = Y[k] * gc[c];
+            const float w = sh[0] * gc[0] + sh[1] * gc[1] + sh[2] * gc[2];
+            for (int a = 0; a < 3; ++a) gd[a] += w * dY[k][a];
+        }
+        if (o.dist > 0.f) {
+            const float pr = gd[0] * o.dir[0] + gd[1] * o.dir[1] + gd[2] * o.dir[2];
+            for (int a = 0; a < 3; ++a) gp[a] -= (gd[a] - pr * o.dir[a]) / o.dist;
+        }
+    }
+    if (G.g_opac) G.g_opac[gi] = my[3];
+    // conic Q = Sigma2^-1:  dL/dSigma2 = -Q GQ Q with GQ = [[dia, dib/2], [dib/2, dic]]
+    const float Q00 = o.ia, Q01 = o.ib, Q11 = o.ic;
+    const float G00 = my[6], G01 = 0.5f * my[7], G11 = my[8];
+    // M1 = GQ Q
+    const float m00 = G00 * Q00 + G01 * Q01, m01 = G00 * Q01 + G01 * Q11;
+    const float m10 = G01 * Q00 + G11 * Q01, m11 = G01 * Q01 + G11 * Q11;
+    const float S00 = -(Q00 * m00 + Q01 * m10), S01 = -(Q00 * m01 + Q01 * m11);
+    const float S11 = -(Q01 * m01 + Q11 * m11);
+    const float GS2[2][2] = {{S00, S01}, {S01, S11}};
+    // rebuild T = J Rc and Sigma3 = (R S)(R S)^T
+    const float x = o.tx, y = o.ty, z = o.tz, iz = 1.f / z;
+    const float J00 = C.fx * iz, J02 = -C.fx * x * iz * iz, J11 = C.fy * iz, J12 = -C.fy * y * iz * iz;
+    float T[2][3], Mm[3][3], S3[3][3];
+    for (int b = 0; b < 3; ++b) {
+        T[0][b] = J00 * C.R[b] + J02 * C.R[6 + b];
+        T[1][b] = J11 * C.R[3 + b] + J12 * C.R[6 + b];
+    }
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) Mm[a][b] = o.R[3 * a + b] * o.s[b];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) S3[a][b] = Mm[a][0] * Mm[b][0] + Mm[a][1] * Mm[b][1] + Mm[a][2] * Mm[b][2];
+    // dL/dSigma3 = T^T GS2 T ; dL/dT = 2 GS2 T S3
+    float GT2[2][3];   // GS2 T
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 3; ++b) GT2[a][b] = GS2[a][0] * T[0][b] + GS2[a][1] * T[1][b];
+    float GS3[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) GS3[a][b] = T[0][a] * GT2[0][b] + T[1][a] * GT2[1][b];
+    float GT[2][3];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 3; ++b)
+            GT[a][b] = 2.f * (GT2[a][0] * S3[0][b] + GT2[a][1] * S3[1][b] + GT2[a][2] * S3[2][b]);
+    // T = J Rc  ->  dL/dJ = GT Rc^T (only the non-zero entries of J matter)
+    float GJ[2][3];
+    for (int a = 0; a < 2; ++a)
+        for (int k = 0; k < 3; ++k)
+            GJ[a][k] = GT[a][0] * C.R[3 * k] + GT[a][1] * C.R[3 * k + 1] + GT[a][2] * C.R[3 * k + 2];
+    const float dpx = my[4], dpy = my[5];
+    float gt[3];
+    gt[0] = GJ[0][2] * (-C.fx * iz * iz) + dpx * C.fx * iz;
+    gt[1] = GJ[1][2] * (-C.fy * iz * iz) + dpy * C.fy * iz;
+    gt[2] = GJ[0][0] * (-C.fx * iz * iz) + GJ[0][2] * (2.f * C.fx * x * iz * iz * iz) +
+            GJ[1][1] * (-C.fy * iz * iz) + GJ[1][2] * (2.f * C.fy * y * iz * iz * iz) +
+            dpx * (-C.fx * x * iz * iz) + dpy * (-C.fy * y * iz * iz);
+    for (int a = 0; a < 3; ++a) gp[a] += C.R[a] * gt[0] + C.R[3 + a] * gt[1] + C.R[6 + a] * gt[2];
+    if (G.g_pos) for (int a = 0; a < 3; ++a) G.g_pos[3 * gi + a] = gp[a];
+    // Sigma3 = Mm Mm^T, Mm = R diag(s): dL/dMm = 2 GS3 Mm
+    float GR[3][3];
+    float gsc[3] = {0.f, 0.f, 0.f};
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            const float gm = 2.f * (GS3[a][0] * Mm[0][b] + GS3[a][1] * Mm[1][b] + GS3[a][2] * Mm[2][b]);
+            gsc[b] += gm * o.R[3 * a + b];
+            GR[a][b] = gm * o.s[b];
+        }
+    if (G.g_scale) for (int b = 0; b < 3; ++b) G.g_scale[3 * gi + b] = gsc[b];
+    // R(qhat) -> qhat -> q (through the normalisation)
+    const float w = o.qn[0], qx = o.qn[1], qy = o.qn[2], qz = o.qn[3];
+    float gq[4];
+    gq[0] = 2.f * (-qz * GR[0][1] + qy * GR[0][2] + qz * GR[1][0] - qx * GR[1][2] - qy * GR[2][0] + qx * GR[2][1]);
+    gq[1] = 2.f * (qy * GR[0][1] + qz * GR[0][2] + qy * GR[1][0] - 2.f * qx * GR[1][1] - w * GR[1][2] +
+                   qz * GR[2][0] + w * GR[2][1] - 2.f * qx * GR[2][2]);
+    gq[2] = 2.f * (-2.f * qy * GR[0][0] + qx * GR[0][1] + w * GR[0][2] + qx * GR[1][0] + qz * GR[1][2] -
+                   w * GR[2][0] + qz * GR[2][1] - 2.f * qy * GR[2][2]);
+    gq[3] = 2.f * (-2.f * qz * GR[0][0] - w * GR[0][1] + qx * GR[0][2] + w * GR[1][0] - 2.f * qz * GR[1][1] +
+                   qy * GR[1][2] + qx * GR[2][0] + qy * GR[2][1]);
+    const float pr = gq[0] * w + gq[1] * qx + gq[2] * qy + gq[3] * qz;
+    if (G.g_rot)
+        for (int a = 0; a < 4; ++a) G.g_rot[4 * gi + a] = (gq[a] - pr * o.qn[a]) / o.qnorm;
+}
+
+struct SStage {
+    int x0, y0, x1, y1, vis;
+};
+
+__global__ void __launch_bounds__(256) k_surfel_bwd(SceneView S, CamParams C, OptParams O,
+                                                   const float *__restrict__ dL, const int32_t *__restrict__ sid,
+                                                   const float *__restrict__ aux, float *__restrict__ g_sh)
+{
+    __shared__ SStage ss[8][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t base = ((int64_t)blockIdx.x * 8 + warp) * 32;
+    if (base >= S.N) return;
+    const int64_t si = base + lane;
+    const int64_t HW = (int64_t)C.W * C.H;
+    SurfelOut o;
+    o.visible = false;
+    if (si < S.N && O.mode != GES_MODE_GAUSSIANS_ONLY) surfel_setup(S, C, O, si, o);
+    ss[warp][lane] = SStage{o.x0, o.y0, o.x1, o.y1, o.visible ? 1 : 0};
+    __syncwarp();
+    float my[3] = {0.f, 0.f, 0.f};
+    const bool full = O.mode == GES_MODE_FULL;
+    for (int j = 0; j < 32; ++j) {
+        const SStage s = ss[warp][j];
+        if (!s.vis) continue;
+        const int32_t want = (int32_t)(base + j);
+        const int w = s.x1 - s.x0 + 1, npx = w * (s.y1 - s.y0 + 1);
+        float acc[3] = {0.f, 0.f, 0.f};
+        for (int k = lane; k < npx; k += 32) {
+            const int x = s.x0 + k % w, y = s.y0 + k / w;
+            const int64_t pix = (int64_t)y * C.W + x;
+            if (__ldg(sid + pix) != want) continue;
+            const float kk = full ? 1.f / (1.f + __ldg(aux + pix)) : 1.f;
+            acc[0] += kk * __ldg(dL + pix);
+            acc[1] += kk * __ldg(dL + HW + pix);
+            acc[2] += kk * __ldg(dL + 2 * HW + pix);
+        }
+        for (int c = 0; c < 3; ++c) {
+            const float t = warp_sum(acc[c]);
+            if (lane == j) my[c] = t;
+        }
+    }
+    if (si >= S.N) return;
+    const int K = (S.deg + 1) * (S.deg + 1);
+    if (!o.visible) {
+        for (int a = 0; a < 3 * K; ++a) g_sh[3 * K * si + a] = 0.f;
+        return;
+    }
+    float Y[16];
+    sh_basis(K, o.dir[0], o.dir[1], o.dir[2], Y);
+    for (int k = 0; k < K; ++k)
+        for (int c = 0; c < 3; ++c) g_sh[3 * K * si + 3 * k + c] = o.raw[c] > 0.f ? Y[k] * my[c] : 0.f;
+}
+
+}  // namespace
+
+cudaError_t launch_backward(const SceneView &S, const CamParams &C, const OptParams &O, const float *dL_drgb,
+                            const float *out_rgb, const float *out_depth, const int32_t *surfel_id,
+                            const float *aux, const ges_grads &G, unsigned *status, cudaStream_t st,
+                            cudaEvent_t *ev)
+{
+    (void)status;
+    if (ev) cudaEventRecord(ev[0], st);
+    if (S.M > 0) {
+        const int64_t warps = (S.M + 31) / 32;
+        k_gauss_bwd<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(S, C, O, dL_drgb, out_rgb, out_depth, aux, G);
+    }
+    if (ev) cudaEventRecord(ev[1], st);
+    if (S.N > 0 && G.s_sh) {
+        const int64_t warps = (S.N + 31) / 32;
+        k_surfel_bwd<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(S, C, O, dL_drgb, surfel_id, aux, G.s_sh);
+    }
+    if (ev) cudaEventRecord(ev[2], st);
+    return cudaGetLastError();
+}
+
+}  // namespace ges

@@ -1,0 +1,616 @@
+// Internal declarations and device math of the GES renderer (sm_103a).
+//
+// Shared by the forward (ges_forward.cu), backward (ges_backward.cu) and host
+// (ges_api.cu) translation units.  The per-primitive set-up functions here are
+// the single definition used by both the forward and the backward kernels, so
+// that a Gaussian's alpha and depth-test decisions are bit-identical in both.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "ges.h"
+
+namespace ges {
+
+constexpr int kTile = 16;               // binning tile edge (pixels)
+constexpr int kRasterThreads = 256;     // 8 warps, each an 8x4 pixel block
+constexpr int kWarpW = 8, kWarpH = 4;
+
+// status word layout (uint32 words)
+enum : int {
+    ST_FLAGS = 0,         // bit0 surfel list overflow, bit1 Gaussian list overflow, bit2 bad quaternion
+    ST_SVIS = 1,          // visible surfels
+    ST_GVIS = 2,          // visible Gaussians
+    ST_SPAIRS = 3,        // surfel tile pairs
+    ST_GPAIRS = 4,        // Gaussian tile pairs
+    ST_WORDS = 16,
+};
+enum : unsigned { FLAG_SOVF = 1u, FLAG_GOVF = 2u, FLAG_BADQ = 4u };
+
+struct CamParams {
+    float R[9];           // world -> camera rotation, row-major
+    float t[3];
+    float fx, fy, cx, cy;
+    float ocam[3];        // camera centre in world space (rounded from FP64)
+    float znear, izn;     // z_near and 1/z_near
+    float bg[3];
+    int W, H, tiles_x, tiles_y;
+};
+
+struct OptParams {
+    int eps_mode;
+    float eps_value, eps_factor, lowpass, alpha_min, surfel_r2, surfel_r;
+    int mode;
+};
+
+struct SceneView {
+    int64_t N, M;
+    int deg, attr_dtype, sh_dtype;
+    const float *s_pos;
+    const void *s_rot, *s_scale, *s_sh;
+    const float *g_pos;
+    const void *g_rot, *g_scale, *g_opac, *g_sh;
+};
+
+// Scratch of one view (device pointers owned by the scene).
+struct ViewScratch {
+    float4 *s_rec;        // [N][4]  surfel raster records
+    float4 *s_rgb;        // [N]     surfel colours
+    float4 *g_rec;        // [M][4]  Gaussian raster records
+    int *s_vis, *g_vis;   // compact lists of visible primitives
+    int *s_cnt, *g_cnt;   // [T]     per-tile counts (zero between renders)
+    int *s_off, *g_off;   // [T+1]   exclusive offsets
+    int *s_cur, *g_cur;   // [T]     fill cursors
+    int *s_list, *g_list; // tile lists
+    int64_t s_cap, g_cap; // list capacities (entries)
+    unsigned *status;     // [ST_WORDS]
+};
+
+// ---------------------------------------------------------------------------
+// host launchers (ges_forward.cu / ges_backward.cu)
+
+cudaError_t launch_forward(const SceneView &S, const CamParams &C, const OptParams &O, const ViewScratch &X,
+                           float *out_rgb, float *out_depth, int32_t *out_id, float *aux, cudaStream_t st,
+                           cudaEvent_t *ev /* 5 events or nullptr */);
+
+cudaError_t launch_backward(const SceneView &S, const CamParams &C, const OptParams &O, const float *dL_drgb,
+                            const float *out_rgb, const float *out_depth, const int32_t *surfel_id,
+                            const float *aux, const ges_grads &G, unsigned *status, cudaStream_t st,
+                            cudaEvent_t *ev /* 3 events or nullptr */);
+
+// ---------------------------------------------------------------------------
+// device helpers
+
+#if defined(__CUDACC__)
+
+// Double-float ("df") arithmetic: value = hi + lo with |lo| <= ulp(hi)/2.
+// Error-free transformations after Knuth (two-sum) and the FMA residual of a
+// product; used where a camera-space position must keep ~48 bits so that a
+// pixel-sized disc 15 m away is located to 1e-7 of its radius.
+struct df { float hi, lo; };
+
+__device__ __forceinline__ df df_two_sum(float a, float b)
+{
+    float s = a + b;
+    float bb = s - a;
+    float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+__device__ __forceinline__ df df_fast_two_sum(float a, float b)
+{
+    float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ df df_two_prod(float a, float b)
+{
+    float p = a * b;
+    return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ df df_add(df a, df b)
+{
+    df s = df_two_sum(a.hi, b.hi);
+    float e = s.lo + (a.lo + b.lo);
+    return df_fast_two_sum(s.hi, e);
+}
+__device__ __forceinline__ df df_add_f(df a, float b)
+{
+    df s = df_two_sum(a.hi, b);
+    return df_fast_two_sum(s.hi, s.lo + a.lo);
+}
+__device__ __forceinline__ df df_mul_f(df a, float b)
+{
+    df p = df_two_prod(a.hi, b);
+    p.lo = fmaf(a.lo, b, p.lo);
+    return df_fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ df df_div(df a, df b)
+{
+    float q1 = a.hi / b.hi;
+    // r = a - q1*b (exact product residual kept)
+    df p = df_mul_f(b, q1);
+    df r = df_add(a, df{-p.hi, -p.lo});
+    float q2 = r.hi / b.hi;
+    return df_fast_two_sum(q1, q2);
+}
+// sum_j R[j] * v[j] + t, products exact, accumulation in df
+__device__ __forceinline__ df df_dot3_plus(const float *R, float v0, float v1, float v2, float t)
+{
+    df acc = df_two_prod(R[0], v0);
+    acc = df_add(acc, df_two_prod(R[1], v1));
+    acc = df_add(acc, df_two_prod(R[2], v2));
+    return df_add_f(acc, t);
+}
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float load_attr(const void *p, int64_t idx, int dtype)
+{
+    if (dtype == GES_F32) return __ldg(reinterpret_cast<const float *>(p) + idx);
+    if (dtype == GES_F16) return __half2float(__ldg(reinterpret_cast<const __half *>(p) + idx));
+    return __bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16 *>(p) + idx));
+}
+
+// Real SH basis (Condon-Shortley phase, k = l^2 + l + m) at a unit vector,
+// written as Cartesian polynomials.  The constants are the normalisations
+// K_l^m = sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) times sqrt2 for m != 0,
+// multiplied by the integer coefficients of the associated Legendre
+// functions:  Y00 = 1/(2 sqrt(pi));  l=1: sqrt(3/(4pi));
+// l=2: sqrt(15/pi)/2, sqrt(5/pi)/4, sqrt(15/pi)/4;
+// l=3: sqrt(35/(2pi))/4, sqrt(105/pi)/2, sqrt(21/(2pi))/4, sqrt(7/pi)/4,
+//      sqrt(105/pi)/4.
+struct ShConst {
+    static constexpr float c0 = 0.28209479177387814f;
+    static constexpr float c1 = 0.48860251190291992f;
+    static constexpr float c2a = 1.09254843059207907f;   // sqrt(15/pi)/2
+    static constexpr float c2b = 0.31539156525252001f;   // sqrt(5/pi)/4
+    static constexpr float c2c = 0.54627421529603954f;   // sqrt(15/pi)/4
+    static constexpr float c3a = 0.59004358992664352f;   // sqrt(35/(2pi))/4
+    static constexpr float c3b = 2.89061144264055405f;   // sqrt(105/pi)/2
+    static constexpr float c3c = 0.45704579946446572f;   // sqrt(21/(2pi))/4
+    static constexpr float c3d = 0.37317633259011540f;   // sqrt(7/pi)/4
+    static constexpr float c3e = 1.44530572132027703f;   // sqrt(105/pi)/4
+};
+
+__device__ __forceinline__ void sh_basis(int K, float x, float y, float z, float *Y)
+{
+    Y[0] = ShConst::c0;
+    if (K <= 1) return;
+    Y[1] = -ShConst::c1 * y;
+    Y[2] = ShConst::c1 * z;
+    Y[3] = -ShConst::c1 * x;
+    if (K <= 4) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = ShConst::c2a * x * y;
+    Y[5] = -ShConst::c2a * y * z;
+    Y[6] = ShConst::c2b * (2.f * zz - xx - yy);
+    Y[7] = -ShConst::c2a * x * z;
+    Y[8] = ShConst::c2c * (xx - yy);
+    if (K <= 9) return;
+    Y[9] = -ShConst::c3a * y * (3.f * xx - yy);
+    Y[10] = ShConst::c3b * x * y * z;
+    Y[11] = -ShConst::c3c * y * (4.f * zz - xx - yy);
+    Y[12] = ShConst::c3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+    Y[13] = -ShConst::c3c * x * (4.f * zz - xx - yy);
+    Y[14] = ShConst::c3e * z * (xx - yy);
+    Y[15] = -ShConst::c3a * x * (xx - 3.f * yy);
+}
+
+// Gradient of the polynomials above with respect to (x,y,z) (any extension
+// off the sphere works once projected onto the tangent plane).
+__device__ __forceinline__ void sh_basis_grad(int K, float x, float y, float z, float (*dY)[3])
+{
+    dY[0][0] = dY[0][1] = dY[0][2] = 0.f;
+    if (K <= 1) return;
+    const float c1 = ShConst::c1;
+    dY[1][0] = 0.f; dY[1][1] = -c1; dY[1][2] = 0.f;
+    dY[2][0] = 0.f; dY[2][1] = 0.f; dY[2][2] = c1;
+    dY[3][0] = -c1; dY[3][1] = 0.f; dY[3][2] = 0.f;
+    if (K <= 4) return;
+    const float a = ShConst::c2a, b = ShConst::c2b, c = ShConst::c2c;
+    dY[4][0] = a * y; dY[4][1] = a * x; dY[4][2] = 0.f;
+    dY[5][0] = 0.f; dY[5][1] = -a * z; dY[5][2] = -a * y;
+    dY[6][0] = -2.f * b * x; dY[6][1] = -2.f * b * y; dY[6][2] = 4.f * b * z;
+    dY[7][0] = -a * z; dY[7][1] = 0.f; dY[7][2] = -a * x;
+    dY[8][0] = 2.f * c * x; dY[8][1] = -2.f * c * y; dY[8][2] = 0.f;
+    if (K <= 9) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    const float A = ShConst::c3a, B = ShConst::c3b, Cc = ShConst::c3c, D = ShConst::c3d, E = ShConst::c3e;
+    dY[9][0] = -6.f * A * x * y; dY[9][1] = -3.f * A * (xx - yy); dY[9][2] = 0.f;
+    dY[10][0] = B * y * z; dY[10][1] = B * x * z; dY[10][2] = B * x * y;
+    dY[11][0] = 2.f * Cc * x * y; dY[11][1] = -Cc * (4.f * zz - xx - 3.f * yy); dY[11][2] = -8.f * Cc * y * z;
+    dY[12][0] = -6.f * D * x * z; dY[12][1] = -6.f * D * y * z; dY[12][2] = D * (6.f * zz - 3.f * xx - 3.f * yy);
+    dY[13][0] = -Cc * (4.f * zz - 3.f * xx - yy); dY[13][1] = 2.f * Cc * x * y; dY[13][2] = -8.f * Cc * x * z;
+    dY[14][0] = 2.f * E * x * z; dY[14][1] = -2.f * E * y * z; dY[14][2] = E * (xx - yy);
+    dY[15][0] = -3.f * A * (xx - yy); dY[15][1] = 6.f * A * x * y; dY[15][2] = 0.f;
+}
+
+// Eq. 1: colour = max(0, 0.5 + sum_k SH_k Y_k(dir)) per channel; also returns
+// the unclamped value (its sign gates the gradient).
+__device__ __forceinline__ void sh_colour(const void *sh, int64_t base, int K, int dtype, const float *Y,
+                                          float *rgb, float *raw)
+{
+    float r = 0.5f, g = 0.5f, b = 0.5f;
+    if (dtype == GES_F32) {
+        const float *p = reinterpret_cast<const float *>(sh) + base;
+        for (int k = 0; k < K; ++k) {
+            r = fmaf(__ldg(p + 3 * k), Y[k], r);
+            g = fmaf(__ldg(p + 3 * k + 1), Y[k], g);
+            b = fmaf(__ldg(p + 3 * k + 2), Y[k], b);
+        }
+    } else {
+        for (int k = 0; k < K; ++k) {
+            r = fmaf(load_attr(sh, base + 3 * k, dtype), Y[k], r);
+            g = fmaf(load_attr(sh, base + 3 * k + 1, dtype), Y[k], g);
+            b = fmaf(load_attr(sh, base + 3 * k + 2, dtype), Y[k], b);
+        }
+    }
+    raw[0] = r; raw[1] = g; raw[2] = b;
+    rgb[0] = fmaxf(r, 0.f); rgb[1] = fmaxf(g, 0.f); rgb[2] = fmaxf(b, 0.f);
+}
+
+// Rotation of the normalised quaternion (w,x,y,z); columns are the local axes.
+// Returns false for a zero-norm or non-finite quaternion.
+__device__ __forceinline__ bool quat_to_rot(float w, float x, float y, float z, float *R, float *qn, float *qnorm)
+{
+    float n2 = w * w + x * x + y * y + z * z;
+    if (!(n2 > 0.f) || !isfinite(n2)) return false;
+    float n = sqrtf(n2), inv = 1.f / n;
+    w *= inv; x *= inv; y *= inv; z *= inv;
+    if (qn) { qn[0] = w; qn[1] = x; qn[2] = y; qn[3] = z; }
+    if (qnorm) *qnorm = n;
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z); R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z); R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y); R[7] = 2.f * (y * z + w * x); R[8] = 1.f - 2.f * (x * x + y * y);
+    return true;
+}
+
+__device__ __forceinline__ unsigned pack_xy(int x, int y) { return (unsigned)x | ((unsigned)y << 16); }
+
+// ---------------------------------------------------------------------------
+// Surfel raster record (64 B).  For a pixel centre (u,v), with du = u - ur,
+// dv = v - vr (exact in float: ur, vr are multiples of 1/256):
+//   invz = iz0 + gu du + gv dv          1/z of the ray-plane hit
+//   A    = a0  + au du + av dv          a * invz / r   (a, b: disc coordinates
+//   B    = b0  + bu du + bv dv          b * invz / r    scaled by s1, s2)
+// The pixel is inside the opaque disc iff invz > 0 and A^2 + B^2 <= invz^2.
+struct SurfelRec {
+    float ur, vr, iz0, gu;
+    float gv, au, av, a0;
+    float bu, bv, b0, izmax;      // izmax: largest 1/z over the disc (culling)
+    int id;
+    unsigned bb_lo, bb_hi;        // pixel bbox (x | y << 16), inclusive
+    float pad;
+};
+static_assert(sizeof(SurfelRec) == 64, "surfel record is 64 B");
+
+// Gaussian raster record (64 B).  alpha(u,v) = sigma * 2^(ca dx^2 + cb dx dy + cc dy^2)
+// with dx = (u - px) - pxl (projected centre in double-float), conic scaled by
+// -log2(e)/2 (cb by -log2(e)).  Depth test: key = d - eps < D_s.
+struct GaussRec {
+    float px, py, pxl, pyl;
+    float ca, cb, cc, sigma;
+    float key, r, g, b;
+    int id;
+    unsigned bb_lo, bb_hi;
+    float pad;
+};
+static_assert(sizeof(GaussRec) == 64, "Gaussian record is 64 B");
+
+struct SurfelOut {
+    bool valid_quat;
+    bool visible;
+    SurfelRec rec;
+    float rgb[3], raw[3], dir[3];
+    int x0, y0, x1, y1;
+};
+
+// Conservative pixel range [lo, hi] of centres (i + 0.5) inside [a, b], clamped.
+__device__ __forceinline__ void pixel_span(float a, float b, int n, int &lo, int &hi)
+{
+    float m = 0.02f + 1e-3f * fmaxf(b - a, 0.f);
+    a -= m; b += m;
+    float fl = ceilf(a - 0.5f), fh = floorf(b - 0.5f);
+    // clamp before converting: NaN and huge values land in [-1, n]
+    fl = fminf(fmaxf(fl, 0.f), (float)n);
+    fh = fmaxf(fminf(fh, (float)(n - 1)), -1.f);
+    lo = (int)fl; hi = (int)fh;
+}
+
+// Per-surfel set-up for the view (Sec. 3: disc placed by scale, rotation,
+// translation; opaque extent of Sec. 4.1).  Produces the raster record, the
+// colour (Eq. 1) and a conservative pixel bbox.
+__device__ __forceinline__ void surfel_setup(const SceneView &S, const CamParams &C, const OptParams &O,
+                                             int64_t i, SurfelOut &o)
+{
+    o.visible = false;
+    o.valid_quat = true;
+    const float px = __ldg(S.s_pos + 3 * i), py = __ldg(S.s_pos + 3 * i + 1), pz = __ldg(S.s_pos + 3 * i + 2);
+    float q[4], R[9];
+    for (int k = 0; k < 4; ++k) q[k] = load_attr(S.s_rot, 4 * i + k, S.attr_dtype);
+    if (!quat_to_rot(q[0], q[1], q[2], q[3], R, nullptr, nullptr)) { o.valid_quat = false; return; }
+    const float s1 = load_attr(S.s_scale, 2 * i, S.attr_dtype), s2 = load_attr(S.s_scale, 2 * i + 1, S.attr_dtype);
+    // view direction for the SH colour: from the surfel centre to the camera
+    {
+        float vx = C.ocam[0] - px, vy = C.ocam[1] - py, vz = C.ocam[2] - pz;
+        float L = sqrtf(vx * vx + vy * vy + vz * vz);
+        float il = L > 0.f ? 1.f / L : 0.f;
+        o.dir[0] = vx * il; o.dir[1] = vy * il; o.dir[2] = vz * il;
+    }
+    if (!(s1 > 0.f && s2 > 0.f && isfinite(s1) && isfinite(s2))) return;
+    // camera-space frame (float) and centre (double-float)
+    float tu[3], tv[3], n[3];
+    for (int r = 0; r < 3; ++r) {
+        tu[r] = C.R[3 * r] * R[0] + C.R[3 * r + 1] * R[3] + C.R[3 * r + 2] * R[6];
+        tv[r] = C.R[3 * r] * R[1] + C.R[3 * r + 1] * R[4] + C.R[3 * r + 2] * R[7];
+        n[r] = C.R[3 * r] * R[2] + C.R[3 * r + 1] * R[5] + C.R[3 * r + 2] * R[8];
+    }
+    df P[3];
+    for (int r = 0; r < 3; ++r) P[r] = df_dot3_plus(C.R + 3 * r, px, py, pz, C.t[r]);
+    const float Ph[3] = {P[0].hi, P[1].hi, P[2].hi};
+    const float nP = fmaf(n[0], Ph[0], fmaf(n[1], Ph[1], n[2] * Ph[2])) +
+                     (n[0] * P[0].lo + n[1] * P[1].lo + n[2] * P[2].lo);
+    if (!(nP != 0.f) || !isfinite(nP)) return;
+    const float r = O.surfel_r;
+    const float ez = r * sqrtf(s1 * tu[2] * s1 * tu[2] + s2 * tv[2] * s2 * tv[2]);
+    const float zmax = Ph[2] + ez, zmin = Ph[2] - ez;
+    if (!(zmax > C.znear * (1.f - 1e-5f) - 1e-6f)) return;
+
+    // --- affine coefficients (see SurfelRec) ---
+    const float inP = 1.f / nP;
+    const float gu = n[0] * inP / C.fx, gv = n[1] * inP / C.fy;
+    float cA[3] = {tv[1] * Ph[2] - tv[2] * Ph[1], tv[2] * Ph[0] - tv[0] * Ph[2], tv[0] * Ph[1] - tv[1] * Ph[0]};
+    float cB[3] = {Ph[1] * tu[2] - Ph[2] * tu[1], Ph[2] * tu[0] - Ph[0] * tu[2], Ph[0] * tu[1] - Ph[1] * tu[0]};
+    const float ka = inP / (s1 * r), kb = inP / (s2 * r);
+    const float au = cA[0] * ka / C.fx, av = cA[1] * ka / C.fy;
+    const float bu = cB[0] * kb / C.fx, bv = cB[1] * kb / C.fy;
+
+    // --- reference pixel: projection of a disc point in front of the camera,
+    // rounded to 1/256 px; its local coordinates from small quantities only.
+    float ur = 0.f, vr = 0.f, iz0 = 0.f, a0 = 0.f, b0 = 0.f;
+    bool precise = false;
+    {
+        float oa = 0.f, ob = 0.f;
+        float zp = Ph[2];
+        if (!(Ph[2] > 0.5f * ez + C.znear)) {
+            // centre too close to / behind the camera: take the disc point of
+            // largest depth at 0.9 r
+            float ga = s1 * tu[2], gb = s2 * tv[2];
+            float gl = sqrtf(ga * ga + gb * gb);
+            if (gl > 0.f) { oa = 0.9f * r * ga / gl; ob = 0.9f * r * gb / gl; }
+            zp = Ph[2] + 0.9f * ez;
+        }
+        if (zp > C.znear * 1.01f) {
+            df X[3];
+            for (int k = 0; k < 3; ++k) X[k] = df_add_f(P[k], oa * s1 * tu[k] + ob * s2 * tv[k]);
+            df uq = df_add_f(df_mul_f(df_div(X[0], X[2]), C.fx), C.cx);
+            df vq = df_add_f(df_mul_f(df_div(X[1], X[2]), C.fy), C.cy);
+            if (fabsf(uq.hi) < 16000.f && fabsf(vq.hi) < 16000.f) {
+                ur = rintf(uq.hi * 256.f) * (1.f / 256.f);
+                vr = rintf(vq.hi * 256.f) * (1.f / 256.f);
+                float dur = (ur - uq.hi) - uq.lo, dvr = (vr - vq.hi) - vq.lo;
+                float dr[3] = {dur / C.fx, dvr / C.fy, 0.f};
+                float Xz = X[2].hi;
+                float kap = Xz * (n[0] * dr[0] + n[1] * dr[1]) * inP;
+                float opk = 1.f + kap;
+                float zref = Xz / opk;
+                float f = -kap / opk;
+                float dX[3];
+                for (int k = 0; k < 3; ++k) dX[k] = fmaf(f, X[k].hi, zref * dr[k]) + f * X[k].lo;
+                float aref = oa + (dX[0] * tu[0] + dX[1] * tu[1] + dX[2] * tu[2]) / s1;
+                float bref = ob + (dX[0] * tv[0] + dX[1] * tv[1] + dX[2] * tv[2]) / s2;
+                // 1/zref = (1+kap)/(X.hi + X.lo)
+                float izx = 1.f / Xz;
+                izx = izx * (1.f - X[2].lo * izx);
+                iz0 = opk * izx;
+                a0 = iz0 * aref / r;
+                b0 = iz0 * bref / r;
+                precise = true;
+            }
+        }
+        if (!precise) {
+            // plain evaluation at the image centre (rare: huge discs at the camera)
+            ur = rintf(C.cx * 256.f) * (1.f / 256.f);
+            vr = rintf(C.cy * 256.f) * (1.f / 256.f);
+            float d[3] = {(ur - C.cx) / C.fx, (vr - C.cy) / C.fy, 1.f};
+            iz0 = (n[0] * d[0] + n[1] * d[1] + n[2] * d[2]) * inP;
+            float dtu = d[0] * tu[0] + d[1] * tu[1] + d[2] * tu[2];
+            float dtv = d[0] * tv[0] + d[1] * tv[1] + d[2] * tv[2];
+            float Ptu = Ph[0] * tu[0] + Ph[1] * tu[1] + Ph[2] * tu[2];
+            float Ptv = Ph[0] * tv[0] + Ph[1] * tv[1] + Ph[2] * tv[2];
+            a0 = (dtu - iz0 * Ptu) / (s1 * r);
+            b0 = (dtv - iz0 * Ptv) / (s2 * r);
+        }
+    }
+
+    // --- conservative screen bbox ---
+    float umin = 1e30f, umax = -1e30f, vmin = 1e30f, vmax = -1e30f;
+    bool have_box = false;
+    if (zmin > C.znear * 1.001f && precise) {
+        // exact bbox of the projected ellipse from its dual conic, in
+        // coordinates relative to the reference pixel: the disc is
+        // {A^2 + B^2 - invz^2 <= 0}; its dual is adj(M), M = a a^T + b b^T - c c^T
+        const float a_[3] = {au, av, a0}, b_[3] = {bu, bv, b0}, c_[3] = {gu, gv, iz0};
+        float M[3][3];
+        for (int x = 0; x < 3; ++x)
+            for (int y = 0; y < 3; ++y) M[x][y] = a_[x] * a_[y] + b_[x] * b_[y] - c_[x] * c_[y];
+        const float D00 = M[1][1] * M[2][2] - M[1][2] * M[2][1];
+        const float D11 = M[0][0] * M[2][2] - M[0][2] * M[2][0];
+        const float D22 = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+        const float D02 = M[0][1] * M[1][2] - M[0][2] * M[1][1];
+        const float D12 = M[0][2] * M[1][0] - M[0][0] * M[1][2];
+        const float du = D02 * D02 - D00 * D22, dv = D12 * D12 - D11 * D22;
+        if (D22 != 0.f && du >= 0.f && dv >= 0.f && isfinite(du) && isfinite(dv)) {
+            const float sdu = sqrtf(du), sdv = sqrtf(dv);
+            const float u1 = (D02 - sdu) / D22, u2 = (D02 + sdu) / D22;
+            const float v1 = (D12 - sdv) / D22, v2 = (D12 + sdv) / D22;
+            umin = ur + fminf(u1, u2); umax = ur + fmaxf(u1, u2);
+            vmin = vr + fminf(v1, v2); vmax = vr + fmaxf(v1, v2);
+            have_box = isfinite(umin) && isfinite(umax) && isfinite(vmin) && isfinite(vmax);
+        }
+    }
+    if (!have_box) {
+        // rectangle p +- r s1 tu +- r s2 tv clipped to z >= znear
+        float cor[4][3], poly[8][3];
+        const float sg[4][2] = {{1.f, 1.f}, {-1.f, 1.f}, {-1.f, -1.f}, {1.f, -1.f}};
+        const float rr = r * 1.0001f;
+        for (int k = 0; k < 4; ++k)
+            for (int j = 0; j < 3; ++j)
+                cor[k][j] = Ph[j] + sg[k][0] * rr * s1 * tu[j] + sg[k][1] * rr * s2 * tv[j];
+        int np = 0;
+        const float zc = C.znear * 0.999f;
+        for (int k = 0; k < 4; ++k) {
+            const float *a = cor[k], *b = cor[(k + 1) & 3];
+            bool ia = a[2] >= zc, ib = b[2] >= zc;
+            if (ia) { poly[np][0] = a[0]; poly[np][1] = a[1]; poly[np][2] = a[2]; ++np; }
+            if (ia != ib) {
+                float tt = (zc - a[2]) / (b[2] - a[2]);
+                poly[np][0] = a[0] + tt * (b[0] - a[0]);
+                poly[np][1] = a[1] + tt * (b[1] - a[1]);
+                poly[np][2] = zc;
+                ++np;
+            }
+        }
+        if (np == 0) return;
+        for (int k = 0; k < np; ++k) {
+            float izk = 1.f / poly[k][2];
+            float u = C.fx * poly[k][0] * izk + C.cx, v = C.fy * poly[k][1] * izk + C.cy;
+            umin = fminf(umin, u); umax = fmaxf(umax, u); vmin = fminf(vmin, v); vmax = fmaxf(vmax, v);
+        }
+        // one pixel of slack for the float projection of the clipped polygon
+        umin -= 1.f; vmin -= 1.f; umax += 1.f; vmax += 1.f;
+    }
+    int x0, x1, y0, y1;
+    pixel_span(fmaxf(umin, -1e6f), fminf(umax, 1e6f), C.W, x0, x1);
+    pixel_span(fmaxf(vmin, -1e6f), fminf(vmax, 1e6f), C.H, y0, y1);
+    if (x0 > x1 || y0 > y1) return;
+    o.x0 = x0; o.x1 = x1; o.y0 = y0; o.y1 = y1;
+
+    float izmax = zmin > C.znear ? (1.f / zmin) * (1.f + 4e-6f) : C.izn * (1.f + 4e-6f);
+    o.rec = SurfelRec{ur, vr, iz0, gu, gv, au, av, a0, bu, bv, b0, izmax, (int)i,
+                      pack_xy(x0, y0), pack_xy(x1, y1), 0.f};
+    const int K = (S.deg + 1) * (S.deg + 1);
+    float Y[16];
+    sh_basis(K, o.dir[0], o.dir[1], o.dir[2], Y);
+    sh_colour(S.s_sh, (int64_t)3 * K * i, K, S.sh_dtype, Y, o.rgb, o.raw);
+    o.visible = true;
+}
+
+struct GaussOut {
+    bool valid_quat;
+    bool visible;
+    GaussRec rec;
+    float rgb[3], raw[3], dir[3], dist;
+    // intermediates for the backward pass
+    float R[9], qn[4], qnorm, s[3];
+    float tx, ty, tz;
+    float S2a, S2b, S2c;      // Sigma2 (with low-pass)
+    float ia, ib, ic;         // conic (unscaled)
+    int x0, y0, x1, y1;
+};
+
+// Per-Gaussian set-up (Eq. 4: projected covariance and centre; 1/255 clamp
+// gives the exact support q <= 2 ln(sigma/alpha_min); eps of Sec. 5).
+__device__ __forceinline__ void gauss_setup(const SceneView &S, const CamParams &C, const OptParams &O,
+                                            int64_t i, GaussOut &o)
+{
+    o.visible = false;
+    o.valid_quat = true;
+    const float px = __ldg(S.g_pos + 3 * i), py = __ldg(S.g_pos + 3 * i + 1), pz = __ldg(S.g_pos + 3 * i + 2);
+    float q[4];
+    for (int k = 0; k < 4; ++k) q[k] = load_attr(S.g_rot, 4 * i + k, S.attr_dtype);
+    if (!quat_to_rot(q[0], q[1], q[2], q[3], o.R, o.qn, &o.qnorm)) { o.valid_quat = false; return; }
+    for (int k = 0; k < 3; ++k) o.s[k] = load_attr(S.g_scale, 3 * i + k, S.attr_dtype);
+    const float sigma = load_attr(S.g_opac, i, S.attr_dtype);
+    {
+        float vx = C.ocam[0] - px, vy = C.ocam[1] - py, vz = C.ocam[2] - pz;
+        float L = sqrtf(vx * vx + vy * vy + vz * vz);
+        float il = L > 0.f ? 1.f / L : 0.f;
+        o.dir[0] = vx * il; o.dir[1] = vy * il; o.dir[2] = vz * il;
+        o.dist = L;
+    }
+    if (!(sigma >= O.alpha_min)) return;       // alpha <= sigma < alpha_min everywhere
+    df t[3];
+    for (int r = 0; r < 3; ++r) t[r] = df_dot3_plus(C.R + 3 * r, px, py, pz, C.t[r]);
+    if (!(t[2].hi > C.znear || (t[2].hi == C.znear && t[2].lo > 0.f))) return;
+    const float x = t[0].hi, y = t[1].hi, z = t[2].hi;
+    o.tx = x; o.ty = y; o.tz = z;
+    // Sigma3 = (R S)(R S)^T
+    float Mm[9], S3[9];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) Mm[3 * a + b] = o.R[3 * a + b] * o.s[b];
+    for (int a = 0; a < 3; ++a)
+        for (int b = a; b < 3; ++b) {
+            float acc = Mm[3 * a] * Mm[3 * b] + Mm[3 * a + 1] * Mm[3 * b + 1] + Mm[3 * a + 2] * Mm[3 * b + 2];
+            S3[3 * a + b] = acc; S3[3 * b + a] = acc;
+        }
+    // T = J Rc with the affine Jacobian of the perspective map at the centre
+    const float iz = 1.f / z;
+    const float J00 = C.fx * iz, J02 = -C.fx * x * iz * iz, J11 = C.fy * iz, J12 = -C.fy * y * iz * iz;
+    float T[6];
+    for (int b = 0; b < 3; ++b) {
+        T[b] = J00 * C.R[b] + J02 * C.R[6 + b];
+        T[3 + b] = J11 * C.R[3 + b] + J12 * C.R[6 + b];
+    }
+    float TS[6];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 3; ++b)
+            TS[3 * a + b] = T[3 * a] * S3[b] + T[3 * a + 1] * S3[3 + b] + T[3 * a + 2] * S3[6 + b];
+    const float s2a = TS[0] * T[0] + TS[1] * T[1] + TS[2] * T[2] + O.lowpass;
+    const float s2b = TS[0] * T[3] + TS[1] * T[4] + TS[2] * T[5];
+    const float s2c = TS[3] * T[3] + TS[4] * T[4] + TS[5] * T[5] + O.lowpass;
+    const float det = s2a * s2c - s2b * s2b;
+    if (!(det > 0.f) || !isfinite(det)) return;
+    const float idet = 1.f / det;
+    const float ia = s2c * idet, ib = -s2b * idet, ic = s2a * idet;
+    o.S2a = s2a; o.S2b = s2b; o.S2c = s2c; o.ia = ia; o.ib = ib; o.ic = ic;
+    // projected centre in double-float
+    df uq = df_add_f(df_mul_f(df_div(t[0], t[2]), C.fx), C.cx);
+    df vq = df_add_f(df_mul_f(df_div(t[1], t[2]), C.fy), C.cy);
+    // exact support bbox: alpha >= alpha_min  <=>  q <= 2 ln(sigma / alpha_min)
+    const float Ts = 2.f * logf(sigma / O.alpha_min);
+    const float hx = sqrtf(fmaxf(Ts, 0.f) * s2a), hy = sqrtf(fmaxf(Ts, 0.f) * s2c);
+    int x0, x1, y0, y1;
+    pixel_span(uq.hi - hx, uq.hi + hx, C.W, x0, x1);
+    pixel_span(vq.hi - hy, vq.hi + hy, C.H, y0, y1);
+    if (x0 > x1 || y0 > y1) return;
+    o.x0 = x0; o.x1 = x1; o.y0 = y0; o.y1 = y1;
+    float eps;
+    if (O.eps_mode == GES_EPS_ADAPTIVE) eps = O.eps_factor * (1.f / 3.f) * (o.s[0] + o.s[1] + o.s[2]);
+    else if (O.eps_mode == GES_EPS_ZERO) eps = 0.f;
+    else eps = O.eps_value;
+    const float key = (t[2].hi - eps) + t[2].lo;
+    const float L2E = 1.4426950408889634f;
+    o.rec.px = uq.hi; o.rec.py = vq.hi; o.rec.pxl = uq.lo; o.rec.pyl = vq.lo;
+    o.rec.ca = -0.5f * L2E * ia; o.rec.cb = -L2E * ib; o.rec.cc = -0.5f * L2E * ic;
+    o.rec.sigma = sigma; o.rec.key = key;
+    o.rec.id = (int)i;
+    o.rec.bb_lo = pack_xy(x0, y0); o.rec.bb_hi = pack_xy(x1, y1);
+    o.rec.pad = 0.f;
+    const int K = (S.deg + 1) * (S.deg + 1);
+    float Y[16];
+    sh_basis(K, o.dir[0], o.dir[1], o.dir[2], Y);
+    sh_colour(S.g_sh, (int64_t)3 * K * i, K, S.sh_dtype, Y, o.rgb, o.raw);
+    o.rec.r = o.rgb[0]; o.rec.g = o.rgb[1]; o.rec.b = o.rgb[2];
+    o.visible = true;
+}
+
+// Eq. 4 at pixel centre (u, v): the one definition used by forward and backward.
+__device__ __forceinline__ float gauss_alpha(const GaussRec &g, float u, float v, float &e)
+{
+    const float dx = (u - g.px) - g.pxl, dy = (v - g.py) - g.pyl;
+    const float p2 = fmaf(g.ca, dx * dx, fmaf(g.cb, dx * dy, g.cc * (dy * dy)));
+    e = ex2_approx(p2);
+    return g.sigma * e;
+}
+
+#endif  // __CUDACC__
+
+}  // namespace ges

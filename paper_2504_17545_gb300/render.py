@@ -1,0 +1,215 @@
+"""PyTorch-facing layer over the C ABI: device tensors in, device tensors out.
+
+PyTorch supplies device memory and the current stream; every step of the
+render and of its backward runs in the library's CUDA kernels.  Nothing here
+computes any part of the method.
+"""
+from __future__ import annotations
+
+import math
+from typing import Dict, Optional, Sequence
+
+import torch
+
+from . import native as N
+
+_DTYPES = {torch.float32: N.GES_F32, torch.float16: N.GES_F16, torch.bfloat16: N.GES_BF16}
+_SCENE_KEYS = ("s_pos", "s_rot", "s_scale", "s_sh", "g_pos", "g_rot", "g_scale", "g_opac", "g_sh")
+_GRAD_KEYS = ("g_pos", "g_rot", "g_scale", "g_opac", "g_sh", "s_sh")
+
+
+def camera_struct(cam) -> N.ges_camera:
+    """ges_camera from any object (or dict) with width, height, fx, fy, cx, cy,
+    world_to_cam (3x4), znear, bg."""
+    get = (lambda k: cam[k]) if isinstance(cam, dict) else (lambda k: getattr(cam, k))
+    c = N.ges_camera()
+    c.width, c.height = int(get("width")), int(get("height"))
+    c.fx, c.fy, c.cx, c.cy = (float(get(k)) for k in ("fx", "fy", "cx", "cy"))
+    w2c = [float(x) for row in get("world_to_cam") for x in row]
+    if len(w2c) != 12:
+        raise ValueError("world_to_cam must be 3x4")
+    c.world_to_cam[:] = w2c
+    c.znear = float(get("znear"))
+    c.bg[:] = [float(x) for x in get("bg")]
+    return c
+
+
+def opts_struct(opts: Optional[dict]) -> N.ges_render_opts:
+    o = N.ges_default_opts()
+    for k, v in (opts or {}).items():
+        if k.startswith("tol_"):
+            continue  # ambiguity bands of the parity tests, not render options
+        if not hasattr(o, k):
+            raise KeyError(f"unknown render option {k!r}")
+        setattr(o, k, v)
+    return o
+
+
+class GESScene:
+    """A GES scene resident in device memory (tensors owned here) and the
+    library's handle that views them."""
+
+    def __init__(self, sh_degree: int, **tensors: torch.Tensor):
+        missing = [k for k in _SCENE_KEYS if k not in tensors]
+        if missing:
+            raise KeyError(f"missing scene tensors {missing}")
+        self.sh_degree = int(sh_degree)
+        self.t: Dict[str, torch.Tensor] = {}
+        for k in _SCENE_KEYS:
+            v = tensors[k]
+            if not v.is_cuda:
+                raise ValueError(f"{k} must be a CUDA tensor")
+            self.t[k] = v.contiguous()
+        attr = self.t["s_rot"].dtype
+        for k in ("s_scale", "g_rot", "g_scale", "g_opac"):
+            if self.t[k].dtype != attr:
+                raise TypeError("rotations, scales and opacities must share one dtype")
+        if self.t["s_sh"].dtype != self.t["g_sh"].dtype:
+            raise TypeError("surfel and Gaussian SH must share one dtype")
+        if self.t["s_pos"].dtype != torch.float32 or self.t["g_pos"].dtype != torch.float32:
+            raise TypeError("positions are float32")
+        self.attr_dtype = _DTYPES[attr]
+        self.sh_dtype = _DTYPES[self.t["s_sh"].dtype]
+        self._desc = self._make_desc()
+        self.handle = N.ges_create_scene(self._desc)
+
+    @classmethod
+    def from_arrays(cls, scene, device="cuda", attr_dtype=torch.float32, sh_dtype=torch.float32) -> "GESScene":
+        """From a host scene (``scenegen.Scene`` or anything with the same array attributes)."""
+        t = {}
+        for k in _SCENE_KEYS:
+            a = torch.as_tensor(getattr(scene, k))
+            dt = torch.float32
+            if k in ("s_rot", "s_scale", "g_rot", "g_scale", "g_opac"):
+                dt = attr_dtype
+            elif k in ("s_sh", "g_sh"):
+                dt = sh_dtype
+            t[k] = a.to(device=device, dtype=dt).contiguous()
+        return cls(scene.sh_degree, **t)
+
+    @property
+    def n_surfels(self) -> int:
+        return int(self.t["s_pos"].shape[0])
+
+    @property
+    def n_gaussians(self) -> int:
+        return int(self.t["g_pos"].shape[0])
+
+    def _make_desc(self) -> N.ges_scene_desc:
+        d = N.ges_scene_desc()
+        d.n_surfels, d.n_gaussians = self.n_surfels, self.n_gaussians
+        d.sh_degree, d.attr_dtype, d.sh_dtype = self.sh_degree, self.attr_dtype, self.sh_dtype
+        for k in _SCENE_KEYS:
+            setattr(d, k, self.t[k].data_ptr() if self.t[k].numel() else None)
+        return d
+
+    def update(self, **tensors: torch.Tensor):
+        """Swap some attribute tensors (same dtypes) and re-point the handle."""
+        for k, v in tensors.items():
+            if k not in _SCENE_KEYS:
+                raise KeyError(k)
+            self.t[k] = v.contiguous()
+        self._desc = self._make_desc()
+        N.ges_scene_update(self.handle, self._desc)
+
+    def bind_stream(self):
+        N.ges_set_stream(self.handle, torch.cuda.current_stream(self.t["s_pos"].device).cuda_stream)
+
+    def stats(self) -> N.ges_stats:
+        return N.ges_get_stats(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            N.ges_destroy_scene(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def render(scene: GESScene, cam, opts: Optional[dict] = None, with_aux: bool = True):
+    """Forward render.  Returns dict(rgb [3,H,W], depth [H,W], id [H,W] int32,
+    aux [H,W] (W_G)); id and aux only when ``with_aux``."""
+    c = camera_struct(cam)
+    dev = scene.t["s_pos"].device
+    H, W = c.height, c.width
+    rgb = torch.empty((3, H, W), device=dev, dtype=torch.float32)
+    depth = torch.empty((H, W), device=dev, dtype=torch.float32)
+    out = dict(rgb=rgb, depth=depth)
+    sid = aux = None
+    if with_aux:
+        sid = torch.empty((H, W), device=dev, dtype=torch.int32)
+        aux = torch.empty((H, W), device=dev, dtype=torch.float32)
+        out.update(id=sid, aux=aux)
+    scene.bind_stream()
+    N.ges_render_ex(scene.handle, c, opts_struct(opts), rgb.data_ptr(), depth.data_ptr(),
+                    sid.data_ptr() if sid is not None else 0, aux.data_ptr() if aux is not None else 0)
+    return out
+
+
+def render_backward(scene: GESScene, cam, fwd: dict, dL_drgb: torch.Tensor, opts: Optional[dict] = None):
+    """Gradients of sum(dL_drgb * C) (Sec. 4.2); returns a dict of float32 tensors."""
+    c = camera_struct(cam)
+    dev = scene.t["s_pos"].device
+    g = {
+        "g_pos": torch.empty((scene.n_gaussians, 3), device=dev),
+        "g_rot": torch.empty((scene.n_gaussians, 4), device=dev),
+        "g_scale": torch.empty((scene.n_gaussians, 3), device=dev),
+        "g_opac": torch.empty((scene.n_gaussians,), device=dev),
+        "g_sh": torch.empty(tuple(scene.t["g_sh"].shape), device=dev),
+        "s_sh": torch.empty(tuple(scene.t["s_sh"].shape), device=dev),
+    }
+    gr = N.ges_grads()
+    for k in _GRAD_KEYS:
+        setattr(gr, k, g[k].data_ptr() if g[k].numel() else None)
+    dl = dL_drgb.contiguous().float()
+    scene.bind_stream()
+    N.ges_render_backward(scene.handle, c, opts_struct(opts), dl.data_ptr(), fwd["rgb"].data_ptr(),
+                          fwd["depth"].data_ptr(), fwd["id"].data_ptr(), fwd["aux"].data_ptr(), gr)
+    return g
+
+
+class _RenderFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, scene, cam, opts, g_pos, g_rot, g_scale, g_opac, g_sh, s_sh):
+        out = render(scene, cam, opts, with_aux=True)
+        ctx.scene, ctx.cam, ctx.opts = scene, cam, opts
+        ctx.save_for_backward(out["rgb"], out["depth"], out["id"], out["aux"])
+        ctx.mark_non_differentiable(out["depth"], out["id"], out["aux"])
+        return out["rgb"], out["depth"], out["id"], out["aux"]
+
+    @staticmethod
+    def backward(ctx, grad_rgb, _gd, _gi, _ga):
+        rgb, depth, sid, aux = ctx.saved_tensors
+        g = render_backward(ctx.scene, ctx.cam, dict(rgb=rgb, depth=depth, id=sid, aux=aux), grad_rgb, ctx.opts)
+        return (None, None, None, g["g_pos"], g["g_rot"], g["g_scale"], g["g_opac"], g["g_sh"], g["s_sh"])
+
+
+def render_differentiable(scene: GESScene, cam, opts: Optional[dict] = None):
+    """Differentiable render: gradients flow to the scene's Gaussian tensors and
+    surfel SH (set requires_grad on them).  Returns (rgb, depth, id, aux)."""
+    t = scene.t
+    return _RenderFn.apply(scene, cam, opts, t["g_pos"], t["g_rot"], t["g_scale"], t["g_opac"], t["g_sh"],
+                           t["s_sh"])
+
+
+def render_batch(scenes: Sequence[GESScene], cams: Sequence, scene_of_view: Optional[Sequence[int]] = None,
+                 opts: Optional[dict] = None, outputs=None):
+    """Render many views in one batch (one host synchronisation).  Returns a
+    list of (rgb, depth) tensor pairs (or fills ``outputs``)."""
+    n = len(cams)
+    if scene_of_view is None:
+        scene_of_view = [0] * n
+    cstructs = [camera_struct(c) for c in cams]
+    dev = scenes[0].t["s_pos"].device
+    if outputs is None:
+        outputs = [(torch.empty((3, c.height, c.width), device=dev), torch.empty((c.height, c.width), device=dev))
+                   for c in cstructs]
+    scenes[0].bind_stream()
+    N.ges_render_batch([s.handle for s in scenes], cstructs, list(scene_of_view), opts_struct(opts),
+                       [o[0].data_ptr() for o in outputs], [o[1].data_ptr() if o[1] is not None else 0
+                                                            for o in outputs])
+    return outputs

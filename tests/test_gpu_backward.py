@@ -1,0 +1,112 @@
+"""GPU backward pass vs the oracle's analytic FP64 gradients (which are pinned
+to central finite differences by the CPU tests)."""
+import numpy as np
+import pytest
+
+import oracle
+import scenegen as sg
+
+pytestmark = pytest.mark.gpu
+
+GRAD_TOL = 1e-3   # of the largest |gradient| in each parameter group
+
+
+@pytest.fixture(scope="module")
+def R():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_17545_gb300 import render as R
+    return R
+
+
+def _grads_gpu(R, scene, cam, g, opts=None):
+    import torch
+    gs = R.GESScene.from_arrays(scene)
+    fwd = R.render(gs, cam, opts)
+    gr = R.render_backward(gs, cam, fwd, torch.as_tensor(g, dtype=torch.float32, device="cuda"), opts)
+    out = {k: v.cpu().numpy().astype(np.float64) for k, v in gr.items()}
+    gs.close()
+    return out, fwd
+
+
+def _check(gpu, ref, keys, scene=None, cam=None, opts=None):
+    """Per parameter group, max |gpu - oracle| <= GRAD_TOL * max |oracle|,
+    leaving out primitives that touch a pixel the oracle flags as ambiguous
+    (several forward answers are correct there; see parity.py)."""
+    s_keep = g_keep = None
+    if scene is not None:
+        amb = oracle.render(scene, cam, opts)["amb"] != 0
+        st, gt = oracle.touching(scene, cam, amb, opts)
+        s_keep, g_keep = ~st, ~gt
+        assert g_keep.mean() > 0.9 and s_keep.mean() > 0.9
+    for k in keys:
+        keep = s_keep if k == "s_sh" else g_keep
+        a, b = (gpu[k], ref[k]) if keep is None else (gpu[k][keep], ref[k][keep])
+        scale = max(np.abs(b).max(), 1e-12)
+        err = np.abs(a - b).max()
+        assert err <= GRAD_TOL * scale, (k, err, scale)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_backward_crop_matches_oracle(R, mode):
+    scene, cam = sg.crop_scene(7)
+    g = np.random.default_rng(8).standard_normal((3, cam.height, cam.width))
+    opts = dict(mode=mode)
+    ref = oracle.backward(scene, cam, g, opts)
+    gpu, _ = _grads_gpu(R, scene, cam, g, opts)
+    keys = {0: ["g_pos", "g_rot", "g_scale", "g_opac", "g_sh", "s_sh"], 1: ["s_sh"],
+            2: ["g_pos", "g_rot", "g_scale", "g_opac", "g_sh"]}[mode]
+    assert (oracle.render(scene, cam, opts)["amb"] == 0).all()   # nothing ambiguous: compare everything
+    _check(gpu, ref, keys)
+    if mode == 1:
+        assert np.all(gpu["g_pos"] == 0) and np.all(gpu["g_sh"] == 0)
+    if mode == 2:
+        assert np.all(gpu["s_sh"] == 0)
+
+
+def test_backward_parity_workload(R):
+    scene, cams = sg.config_scene(0)
+    g = np.random.default_rng(11).standard_normal((3, 128, 128))
+    ref = oracle.backward(scene, cams[0], g)
+    gpu, _ = _grads_gpu(R, scene, cams[0], g)
+    _check(gpu, ref, ["g_pos", "g_rot", "g_scale", "g_opac", "g_sh", "s_sh"], scene, cams[0])
+
+
+def test_backward_train_step_workload(R):
+    """1600x1060, 500k surfels + 500k Gaussians, L1 loss against the render of
+    a perturbed scene (the training-step workload).  dL/dC = sign(C - T)/(3HW)
+    is formed from the oracle's C and T and fed to both sides."""
+    scene, cams = sg.config_scene(3)
+    cam = cams[0]
+    target = oracle.render(sg.perturbed_scene(scene, 1003), cam)["rgb"]
+    C = oracle.render(scene, cam)["rgb"]
+    g = np.sign(C - target) / (3.0 * cam.width * cam.height)
+    ref = oracle.backward(scene, cam, g)
+    gpu, _ = _grads_gpu(R, scene, cam, g)
+    _check(gpu, ref, ["g_pos", "g_rot", "g_scale", "g_opac", "g_sh", "s_sh"], scene, cam)
+
+
+def test_backward_deterministic(R):
+    scene, cams = sg.config_scene(0)
+    g = np.random.default_rng(12).standard_normal((3, 128, 128))
+    a, _ = _grads_gpu(R, scene, cams[0], g)
+    b, _ = _grads_gpu(R, scene, cams[0], g)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_autograd_function_matches_explicit_backward(R):
+    import torch
+    scene, cam = sg.crop_scene(13)
+    gs = R.GESScene.from_arrays(scene)
+    for k in ("g_pos", "g_rot", "g_scale", "g_opac", "g_sh", "s_sh"):
+        gs.t[k].requires_grad_(True)
+    rgb, depth, sid, aux = R.render_differentiable(gs, cam)
+    w = torch.randn_like(rgb)
+    (rgb * w).sum().backward()
+    fwd = dict(rgb=rgb.detach(), depth=depth, id=sid, aux=aux)
+    ref = R.render_backward(gs, cam, fwd, w)
+    for k in ref:
+        assert torch.equal(gs.t[k].grad, ref[k]), k
+    gs.close()

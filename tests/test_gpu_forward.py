@@ -1,0 +1,193 @@
+"""GPU forward render vs the FP64 oracle, through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import scenegen as sg
+from parity import compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_17545_gb300 import render as R
+    return R
+
+
+def _render(R, scene, cam, opts=None, **kw):
+    gs = R.GESScene.from_arrays(scene, **kw)
+    out = R.render(gs, cam, opts)
+    gs.close()
+    return out
+
+
+def _assert(res):
+    assert res["pass"], res
+
+
+def test_parity_workload_128(R):
+    scene, cams = sg.config_scene(0)
+    ref = oracle.render(scene, cams[0])
+    res = compare(scene, cams[0], _render(R, scene, cams[0]), ref)
+    _assert(res)
+    assert res["compared_px"] > 0.95 * 128 * 128
+
+
+def _small(seed, n_s=400, n_g=1500):
+    return sg.random_scene(seed, n_s, n_g, n_objects=5, box=1.0, sphere_r=(0.3, 0.6), plane_side=(0.6, 1.2),
+                           surfel_scale=(0.03, 0.1), gauss_logscale=(-3.8, 0.4))
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_parity_ragged_and_modes(R, mode):
+    scene = _small(31)
+    cams = [sg.look_at((0.2, 0.3, -2.8), (0, 0, 0), (0, 1, 0), 203, 141, 55.0),
+            sg.look_at((0.1, 0.05, -0.6), (0, 0.1, 1), (0, 1, 0), 97, 61, 95.0)]   # inside the scene
+    for cam in cams:
+        ref = oracle.render(scene, cam, dict(mode=mode))
+        _assert(compare(scene, cam, _render(R, scene, cam, dict(mode=mode)), ref, dict(mode=mode)))
+
+
+@pytest.mark.parametrize("opts", [dict(eps_mode=1), dict(eps_mode=2, eps_value=0.1), dict(lowpass=0.1)])
+def test_parity_options(R, opts):
+    scene = _small(32)
+    cam = sg.look_at((0.0, -0.4, -2.5), (0, 0, 0), (0, 1, 0), 120, 88, 60.0)
+    ref = oracle.render(scene, cam, opts)
+    _assert(compare(scene, cam, _render(R, scene, cam, opts), ref, opts))
+
+
+def test_parity_1080p_orbit_cameras(R):
+    """The 1M-surfel / 300k-Gaussian 1080p workload, full frames of two
+    cameras of the orbit, in the launch configuration the benchmark times."""
+    scene, cams = sg.config_scene(1)
+    gs = R.GESScene.from_arrays(scene)
+    for k in (0, 32):
+        ref = oracle.render(scene, cams[k])
+        out = R.render(gs, cams[k])
+        res = compare(scene, cams[k], out, ref)
+        _assert(res)
+        assert res["masked_frac"] < 0.01
+    gs.close()
+
+
+def test_empty_and_degenerate_inputs(R):
+    torch = pytest.importorskip("torch")
+    base = _small(33, 50, 80)
+    cam = sg.look_at((0, 0, -2.5), (0, 0, 0), (0, 1, 0), 33, 17, 60.0, bg=(0.1, 0.2, 0.3))
+    cases = [base.subset(s_idx=np.zeros(0, int), g_idx=np.zeros(0, int)),   # nothing at all
+             base.subset(g_idx=np.zeros(0, int)),                           # surfels only
+             base.subset(s_idx=np.zeros(0, int))]                           # Gaussians only
+    for sc in cases:
+        ref = oracle.render(sc, cam)
+        _assert(compare(sc, cam, _render(R, sc, cam), ref))
+    # 1x1 and 1-row images
+    for w, h in ((1, 1), (37, 1), (1, 23)):
+        c = sg.look_at((0, 0, -2.5), (0, 0, 0), (0, 1, 0), w, h, 60.0)
+        ref = oracle.render(base, c)
+        _assert(compare(base, c, _render(R, base, c), ref))
+    # zero and negative surfel scales never cover anything
+    sc = base.subset()
+    sc.s_scale = sc.s_scale.copy()
+    sc.s_scale[::3, 0] = 0.0
+    sc.s_scale[1::7, 1] = -0.1
+    ref = oracle.render(sc, cam)
+    _assert(compare(sc, cam, _render(R, sc, cam), ref))
+
+
+def test_zero_norm_quaternion_is_invalid_argument(R):
+    from paper_2504_17545_gb300 import native as N
+    sc = _small(34, 30, 30)
+    sc.g_rot = sc.g_rot.copy()
+    sc.g_rot[5] = 0.0
+    cam = sg.look_at((0, 0, -2.5), (0, 0, 0), (0, 1, 0), 32, 32, 60.0)
+    with pytest.raises(N.GesError) as ei:
+        _render(R, sc, cam)
+    assert ei.value.status == N.GES_ERR_INVALID_ARG and "quaternion" in str(ei.value)
+
+
+def test_bad_camera_is_invalid_argument(R):
+    from paper_2504_17545_gb300 import native as N
+    sc = _small(35, 10, 10)
+    gs = R.GESScene.from_arrays(sc)
+    for bad in (dict(width=0), dict(fx=-1.0), dict(znear=0.0), dict(width=20000)):
+        cam = sg.look_at((0, 0, -2.5), (0, 0, 0), (0, 1, 0), 32, 32, 60.0)
+        for k, v in bad.items():
+            setattr(cam, k, v)
+        with pytest.raises(N.GesError) as ei:
+            R.render(gs, cam)
+        assert ei.value.status == N.GES_ERR_INVALID_ARG
+    gs.close()
+
+
+def test_deterministic_and_gaussian_order_independent_bitwise(R):
+    """Sorting-free accumulation (Sec. 3): the GPU sums in exact fixed point, so
+    any Gaussian order gives the identical image, bit for bit."""
+    scene, cams = sg.config_scene(0)
+    a = _render(R, scene, cams[0])
+    b = _render(R, scene, cams[0])
+    perm = np.random.default_rng(9).permutation(scene.n_gaussians)
+    c = _render(R, scene.subset(g_idx=perm), cams[0])
+    for k in ("rgb", "depth", "id", "aux"):
+        assert (a[k] == b[k]).all(), k
+    for k in ("rgb", "depth", "aux"):
+        assert (a[k] == c[k]).all(), k
+
+
+def test_surfel_order_only_relabels(R):
+    scene, cams = sg.config_scene(0)
+    a = _render(R, scene, cams[0])
+    perm = np.random.default_rng(10).permutation(scene.n_surfels)
+    b = _render(R, scene.subset(s_idx=perm), cams[0])
+    ida, idb = a["id"].cpu().numpy(), b["id"].cpu().numpy()
+    lab = np.where(idb >= 0, perm[np.maximum(idb, 0)], -1)
+    ref = oracle.render(scene, cams[0])
+    ok = (ref["amb"] & 1) == 0
+    assert (lab[ok] == ida[ok]).all()
+
+
+@pytest.mark.parametrize("dtype", ["float16", "bfloat16"])
+def test_reduced_precision_storage(R, dtype):
+    """FP16/BF16 attributes and SH, FP32 evaluation: parity against the oracle
+    fed the same dequantised values."""
+    torch = pytest.importorskip("torch")
+    dt = getattr(torch, dtype)
+    scene, cams = sg.config_scene(0)
+    deq = scene.subset()
+    for k in ("s_rot", "s_scale", "g_rot", "g_scale", "g_opac", "s_sh", "g_sh"):
+        setattr(deq, k, torch.as_tensor(getattr(scene, k)).to(dt).float().numpy())
+    out = _render(R, scene, cams[0], attr_dtype=dt, sh_dtype=dt)
+    ref = oracle.render(deq, cams[0])
+    _assert(compare(deq, cams[0], out, ref))
+
+
+def test_batch_equals_single_views(R):
+    torch = pytest.importorskip("torch")
+    scene, cams = sg.config_scene(0)
+    other = _small(36, 300, 900)
+    ga, gb = R.GESScene.from_arrays(scene), R.GESScene.from_arrays(other)
+    views = [cams[0], sg.look_at((0.5, 0, -2.8), (0, 0, 0), (0, 1, 0), 77, 50, 60.0),
+             sg.look_at((0, 0.3, -2.6), (0, 0, 0), (0, 1, 0), 128, 96, 50.0)]
+    sov = [0, 1, 0]
+    outs = R.render_batch([ga, gb], views, sov)
+    for v, (rgb, depth) in enumerate(outs):
+        single = R.render([ga, gb][sov[v]], views[v])
+        assert (rgb == single["rgb"]).all() and (depth == single["depth"]).all()
+    ga.close()
+    gb.close()
+
+
+def test_stats_count_visible_primitives(R):
+    from paper_2504_17545_gb300 import native as N
+    scene, cams = sg.config_scene(0)
+    gs = R.GESScene.from_arrays(scene)
+    R.render(gs, cams[0])
+    st = gs.stats()
+    assert 0 < st.visible_surfels <= scene.n_surfels and 0 < st.visible_gaussians <= scene.n_gaussians
+    assert st.surfel_tile_pairs >= st.visible_surfels and st.tiles_x == 8 and st.tiles_y == 8
+    gs.close()

@@ -500,3 +500,22 @@ def test_sh_direction_points_from_primitive_to_camera(oracle_lib):
     sg_ = mk_scene(1, g_pos=[[0, 0, 2.0]], g_rot=[[1.0, 0, 0, 0]], g_scale=[[0.01] * 3], g_opac=[0.5], g_sh=sh)
     info = oracle_lib.gauss_info(sg_, cam, 0)
     np.testing.assert_allclose(info["rgb"], 0.5 - c1 * np.array([0.4, 0.2, -0.1]), rtol=1e-14)
+
+
+def test_touching_marks_exactly_the_primitives_at_flagged_pixels(oracle_lib):
+    f, z0, s, sig = 40.0, 2.0, 0.05, 0.7
+    cam = ident_cam(65, 65, f, cx=32.5, cy=32.5)
+    sc = _one_gaussian(z0, s, sig)
+    sc = mk_scene(0, s_pos=[[0.0, 0.0, 3.0], [5.0, 5.0, 3.0]], s_rot=[[1.0, 0, 0, 0]] * 2,
+                  s_scale=[[0.1, 0.1]] * 2, s_sh=np.zeros((2, 1, 3)), g_pos=sc.g_pos, g_rot=sc.g_rot,
+                  g_scale=sc.g_scale, g_opac=sc.g_opac, g_sh=sc.g_sh)
+    flag = np.zeros((65, 65), np.uint8)
+    st, gt = oracle_lib.touching(sc, cam, flag)
+    assert not st.any() and not gt.any()
+    flag[32, 32] = 1   # the Gaussian's centre pixel, inside surfel 0's disc
+    st, gt = oracle_lib.touching(sc, cam, flag)
+    assert st.tolist() == [True, False] and gt.tolist() == [True]
+    flag[:] = 0
+    flag[0, 0] = 1     # far from everything
+    st, gt = oracle_lib.touching(sc, cam, flag)
+    assert not st.any() and not gt.any()
