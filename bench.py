@@ -1,0 +1,280 @@
+"""Benchmark of the GES render path on GB300.
+
+Workload: 1920x1080, 1M surfels + 300k Gaussians (FP32 attributes, SH degree
+3) placed on 200 seeded spheres and squares in a 20 m box, rendered from a
+64-camera orbit (radius 15 m, height 5 m, 60 deg vertical field of view).
+Synthetic, seeded inputs stand in for the paper's scenes.
+
+One step renders all 64 orbit views in one batched call (preprocess, tile
+binning, surfel z-buffer, Gaussian accumulation and composite for every
+view).  `value` = 1080p frames per second over the whole job (all ranks).
+The scene (332 MB) is larger than the 129 MB L2, so no flush is needed
+between steps.
+
+Under torchrun each rank renders its own copy of the orbit (independent
+frames, no collective on the data path): weak scaling.
+
+`--impl reference` times the FP64 CPU oracle on the same workload and metric
+(one full-resolution orbit view per step), on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_VIEWS = 64
+WORKLOAD = "1080p-1M-surfels-300k-gaussians-fp32-orbit64"
+METRIC = "1080p frames/s (1M surfels + 300k Gaussians, FP32)"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [l.split(",") for l in open(self.path).read().strip().splitlines() if l.strip()]
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        if not sm:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows if len(r) >= 9 for k in range(4) if "Active" in r[5 + k]
+                          and "Not" not in r[5 + k]})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "samples": len(sm),
+                "reasons": reasons}
+
+
+def algorithmic_bytes(n_s, n_g, s_vis, g_vis, hw, attr_bytes=4, sh_bytes=4, deg=3):
+    """Bytes one view must move: every position, the other attributes and SH
+    of the visible primitives, and the RGB + depth outputs."""
+    K = (deg + 1) ** 2
+    b_s = 12 + attr_bytes * (4 + 2) + sh_bytes * 3 * K     # 228 B in FP32
+    b_g = 12 + attr_bytes * (4 + 3 + 1) + sh_bytes * 3 * K  # 236 B in FP32
+    prep = 12 * (n_s + n_g) + (b_s - 12) * s_vis + (b_g - 12) * g_vis
+    return prep, prep + 16 * hw
+
+
+def run_reference(args, rank, world):
+    """FP64 oracle on the host cores, one full 1080p orbit view per step."""
+    import numpy as np
+    import oracle
+    import scenegen as sg
+    if rank != 0:
+        return
+    oracle.build()
+    scene, cams = sg.config_scene(1)
+    for k in range(args.warmup):
+        oracle.render(scene, cams[k % N_VIEWS])
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.render(scene, cams[(args.warmup + k) % N_VIEWS])
+    dt = time.perf_counter() - t0
+    fps = args.steps / dt
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "views_per_step": 1, "resolution": "1920x1080"},
+            "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} full 1080p orbit views, FP64, OpenMP over all host cores"},
+            "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample(scene, cams):
+    """The oracle as it stands on a bounded sample (2 orbit views)."""
+    import oracle
+    oracle.build()
+    oracle.render(scene, cams[1])   # page in
+    t0 = time.perf_counter()
+    n = 2
+    for k in range(n):
+        oracle.render(scene, cams[(16 * k) % N_VIEWS])
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} full 1080p orbit views (of 64), FP64, OpenMP over all host cores"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+    import scenegen as sg
+    from paper_2504_17545_gb300 import native as N
+    from paper_2504_17545_gb300 import render as R
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    scene, cams = sg.config_scene(1)
+    gs = R.GESScene.from_arrays(scene)
+    H, W = cams[0].height, cams[0].width
+    outs = [(torch.empty((3, H, W), device="cuda"), torch.empty((H, W), device="cuda")) for _ in cams]
+    cstructs = [R.camera_struct(c) for c in cams]
+    opts = R.opts_struct(None)
+    stream = torch.cuda.current_stream()
+    gs.bind_stream()
+
+    def step(outputs=outs):
+        N.ges_render_batch([gs.handle], cstructs, [0] * N_VIEWS, opts,
+                           [o[0].data_ptr() for o in outputs], [o[1].data_ptr() for o in outputs])
+
+    # per-view visible counts (algorithmic bytes)
+    vis = []
+    for c in cams:
+        R.render(gs, c, with_aux=False)
+        st = gs.stats()
+        vis.append((st.visible_surfels, st.visible_gaussians))
+    prep_b, frame_b = zip(*[algorithmic_bytes(scene.n_surfels, scene.n_gaussians, s, g, H * W) for s, g in vis])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: K steps, per-kernel CUDA events inside the library
+    N.ges_set_profiling(gs.handle, True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    prof = N.ges_get_profile(gs.handle)
+    N.ges_set_profiling(gs.handle, False)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    frames = N_VIEWS * args.steps * world
+    value = frames / (ms / 1e3)
+
+    # end-to-end through the C ABI with host buffers: camera structs in,
+    # RGB + depth copied back to pinned host memory, every step
+    host = [(torch.empty((3, H, W), pin_memory=True), torch.empty((H, W), pin_memory=True)) for _ in cams]
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = max(3, args.steps // 3)
+    for _ in range(e2e_steps):
+        step()
+        for (dr, dd), (hr, hd) in zip(outs, host):
+            hr.copy_(dr, non_blocking=True)
+            hd.copy_(dd, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_dt = time.perf_counter() - t0
+    e2e = {"value": N_VIEWS * e2e_steps * world / e2e_dt, "unit": "frames/s",
+           "h2d_bytes_per_step": N_VIEWS * 88, "d2h_bytes_per_step": N_VIEWS * 4 * 4 * H * W}
+
+    if rank != 0:
+        return
+    # roofline of the dominant kernel (largest share of device time)
+    names = sorted(prof, key=lambda k: -prof[k][0])
+    top = names[0]
+    top_ms, top_launches = prof[top]
+    peak, peak_src = _peaks()
+    if top == "preprocess":
+        bytes_per_launch = float(np.mean(prep_b))
+        bound = "hbm"
+    else:
+        bytes_per_launch = float(np.mean(frame_b)) - float(np.mean(prep_b))   # outputs the raster writes
+        bound = "hbm"
+    achieved = bytes_per_launch / (top_ms / top_launches / 1e3) / 1e9
+    frame_achieved = float(np.mean(frame_b)) * frames / world / (ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "resolution": f"{W}x{H}", "n_surfels": scene.n_surfels,
+                   "n_gaussians": scene.n_gaussians, "views_per_step": N_VIEWS,
+                   "l2": "inputs 332 MB > 129 MB L2, no flush", "parallelism": f"replicas{world}"},
+        "roofline": {"bound": bound, "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_source": peak_src},
+        "frame_roofline": {"algorithmic_bytes_per_frame": float(np.mean(frame_b)), "achieved": frame_achieved,
+                           "frac": frame_achieved / peak, "unit": "GB/s"},
+        "kernel_ms_per_frame": {k: prof[k][0] / prof[k][1] for k in names},
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": 4 * N_VIEWS * args.steps,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline_sample(scene, cams)
+    print(json.dumps(line), flush=True)
+    gs.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -287,9 +287,9 @@ ges_status render_views(ges_scene *const *scenes, const CamParams *cams, const i
             if (r != GES_OK) return r;
         }
         GES_CUDA(cudaMemsetAsync(s0->status.p, 0, (size_t)n * ST_WORDS * 4, st));
-        const bool prof = s0->prof && n == 1;
+        const bool prof = s0->prof;
         if (prof) {
-            ges_status r = ensure_events(s0, 5);
+            ges_status r = ensure_events(s0, 8 + 5 * n);
             if (r != GES_OK) return r;
         }
         for (int v = 0; v < n; ++v) {
@@ -298,12 +298,13 @@ ges_status render_views(ges_scene *const *scenes, const CamParams *cams, const i
             X.status = (unsigned *)s0->status.p + (size_t)v * ST_WORDS;
             cudaError_t e = launch_forward(s->view, cams[v], O, X, rgb[v], depth ? depth[v] : nullptr,
                                            ids ? ids[v] : nullptr, auxs ? auxs[v] : nullptr, st,
-                                           prof ? s0->ev.data() : nullptr);
+                                           prof ? s0->ev.data() + 8 + 5 * v : nullptr);
             if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
         }
         GES_CUDA(cudaMemcpyAsync(s0->status_host, s0->status.p, (size_t)n * ST_WORDS * 4, cudaMemcpyDeviceToHost, st));
         GES_CUDA(cudaStreamSynchronize(st));
-        if (prof) prof_collect(s0, 0, kFwdNames, 4);
+        if (prof)
+            for (int v = 0; v < n; ++v) prof_collect(s0, 8 + 5 * v, kFwdNames, 4);
         bool overflow = false;
         for (int v = 0; v < n; ++v) {
             const unsigned *w = s0->status_host + (size_t)v * ST_WORDS;
@@ -433,10 +434,10 @@ ges_status ges_render_backward(ges_scene *s, const ges_camera *cam, const ges_re
     const bool prof = s->prof;
     if (prof && (r = ensure_events(s, 8)) != GES_OK) return r;
     cudaError_t e = launch_backward(s->view, C, O, dL_drgb, out_rgb, out_depth, surfel_id, aux, *grads, nullptr,
-                                    s->stream, prof ? s->ev.data() + 5 : nullptr);
+                                    s->stream, prof ? s->ev.data() : nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "backward launch");
     GES_CUDA(cudaStreamSynchronize(s->stream));
-    if (prof) prof_collect(s, 5, kBwdNames, 2);
+    if (prof) prof_collect(s, 0, kBwdNames, 2);
     return GES_OK;
 }
 
