@@ -591,6 +591,58 @@ int ora_surfel_eval(const ora_scene *S, const ora_camera *c, const ora_opts *o, 
     return ORA_OK;
 }
 
+/* Is ids[pix] an acceptable z-buffer answer at each pixel?  The exact answer
+   is the lexicographic min of (z, index) over surfels whose fragment is inside
+   its disc in front of the near plane; where fragments sit within the bands
+   (disc rim |rho - r2| <= tol_disc r2, depth gap <= tol_depth z) several
+   answers are correct.  A surfel s is acceptable iff its fragment is inside
+   its disc up to the rim band and in front of the near plane up to the depth
+   band, and no surfel clearly in front of it (z_t < z_s (1 - tol_depth)) is
+   clearly inside its own disc (rho_t < r2 (1 - tol_disc)).  -1 is acceptable
+   iff no surfel is clearly inside.  Grazing fragments (|cos| < tol_graze)
+   count as inside up to the band, like rim fragments. */
+int ora_check_ids(const ora_scene *S, const ora_camera *c, const ora_opts *o, const int32_t *ids,
+                  uint8_t *valid)
+{
+    if (!check_args(S, c, o)) return ORA_BAD_ARG;
+    prep_t P;
+    int st = prepare(S, c, o, 1, &P);
+    if (st != ORA_OK) { prep_free(&P); return st; }
+    const int W = c->width, H = c->height;
+    const double r2 = o->surfel_r2, td = o->tol_depth_rel, tr = o->tol_disc_rel;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int j = 0; j < H; ++j) {
+        for (int i = 0; i < W; ++i) {
+            const int64_t pix = (int64_t)j * W + i;
+            const int32_t s = ids[pix];
+            double d[3];
+            pixel_ray(c, i, j, d);
+            double zs = INFINITY;
+            int ok = 1;
+            if (s >= 0) {
+                if (s >= S->n_surfels || !P.sf[s].valid) { valid[pix] = 0; continue; }
+                double rho, nd;
+                if (!surfel_hit(&P.sf[s], d, &zs, &rho, &nd) || !(zs > c->znear * (1.0 - td)) ||
+                    !(rho <= r2 * (1.0 + tr) || fabs(nd) < o->tol_graze)) { valid[pix] = 0; continue; }
+            }
+            const int64_t cell = (int64_t)(j / ORA_CELL) * P.rs.cx + i / ORA_CELL;
+            for (int64_t t = P.rs.off[cell]; t < P.rs.off[cell + 1] && ok; ++t) {
+                const int64_t q = P.rs.idx[t];
+                const surf_t *sf = &P.sf[q];
+                if (q == s || !sf->valid || i < sf->x0 || i > sf->x1 || j < sf->y0 || j > sf->y1) continue;
+                double z, rho, nd;
+                if (!surfel_hit(sf, d, &z, &rho, &nd)) continue;
+                if (!(z > c->znear * (1.0 + td))) continue;
+                if (!(z < zs * (1.0 - td))) continue;
+                if (rho < r2 * (1.0 - tr) && fabs(nd) >= o->tol_graze) ok = 0;
+            }
+            valid[pix] = (uint8_t)ok;
+        }
+    }
+    prep_free(&P);
+    return ORA_OK;
+}
+
 /* Primitives that touch a flagged pixel (flag[pix] != 0): a Gaussian whose
    alpha (before the clamp) reaches alpha_min - tol_alpha there, a surfel whose
    fragment there lies inside its disc band in front of the near plane.  Used to

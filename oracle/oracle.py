@@ -75,6 +75,7 @@ def load():
         lib.ora_surfel_info.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_int64, C.c_void_p]
         lib.ora_gauss_info.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_int64, C.c_void_p]
         lib.ora_touching.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.ora_check_ids.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_void_p, C.c_void_p]
         _lib = lib
     return _lib
 
@@ -182,33 +183,18 @@ def gauss_info(scene, cam, i, opts=None):
 
 
 def id_validity(scene, cam, ref, ids, opts=None):
-    """Which surfel ids are acceptable answers at each pixel.
-
-    ``ref`` is an oracle render.  At a pixel the candidate id is valid when it
-    equals the oracle's winner, or, where the oracle flagged the pixel as
-    ambiguous, when the candidate's own FP64 fragment is inside its disc up to
-    the disc band and no farther than the winner's depth up to the depth band
-    (an empty answer is valid only if every covering fragment lies in the
-    disc band).  Returns a bool [H,W] array."""
-    o = dict(DEFAULT_OPTS)
-    o.update(opts or {})
-    ids = np.asarray(ids, np.int32)
-    valid = ids == ref["id"]
-    amb = (ref["amb"] & 1) != 0
-    yy, xx = np.nonzero(amb & ~valid)
-    if yy.size:
-        cand = ids[yy, xx]
-        z, rho, nd, ok = surfel_eval(scene, cam, xx, yy, np.maximum(cand, 0), opts)
-        r2 = o["surfel_r2"]
-        zw = ref["depth"][yy, xx]
-        good_hit = (ok == 1) & (rho <= r2 * (1 + o["tol_disc_rel"])) & (z > cam.znear) & \
-                   (z <= zw * (1 + 2 * o["tol_depth_rel"]))
-        wid = ref["id"][yy, xx]
-        zw2, rhow, _, okw = surfel_eval(scene, cam, xx, yy, np.maximum(wid, 0), opts)
-        # empty answer: acceptable only if the oracle's winner sits in the disc band
-        good_empty = (cand < 0) & ((wid < 0) | ((okw == 1) & (np.abs(rhow - r2) <= o["tol_disc_rel"] * r2)))
-        valid[yy, xx] = np.where(cand >= 0, good_hit, good_empty)
-    return valid
+    """Which surfel ids are acceptable z-buffer answers at each pixel (bool
+    [H,W]).  Where ``ids`` equals the oracle's winner it is valid by
+    definition; elsewhere the oracle checks that the candidate's fragment is
+    inside its disc (up to the rim band) and that no surfel clearly in front of
+    it is clearly inside its own disc (``ora_check_ids``)."""
+    lib = load()
+    ids = np.ascontiguousarray(ids, np.int32)
+    pin = _Pinned(scene, cam, opts)
+    v = np.empty(ids.shape, np.uint8)
+    _check(lib.ora_check_ids(C.byref(pin.s), C.byref(pin.c), C.byref(pin.o), ids.ctypes.data, v.ctypes.data),
+           "check_ids")
+    return (ids == ref["id"]) | (v != 0)
 
 
 def touching(scene, cam, flag, opts=None):

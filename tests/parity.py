@@ -31,7 +31,7 @@ def compare(scene, cam, gpu, ref, opts=None, col_tol=COL_TOL, depth_rel=DEPTH_RE
         same = ~mism
     else:
         same = np.ones(depth.shape, bool)
-    cov = same & (ref["id"] >= 0)
+    cov = same & (ref["id"] >= 0) & ~amb_id     # grazing/rim/tie pixels: depth is ill-conditioned
     if cov.any():
         rel = np.abs(depth[cov] - ref["depth"][cov]) / ref["depth"][cov]
         out["depth_rel_max"] = float(rel.max())

@@ -39,7 +39,7 @@ def _check(gpu, ref, keys, scene=None, cam=None, opts=None):
         amb = oracle.render(scene, cam, opts)["amb"] != 0
         st, gt = oracle.touching(scene, cam, amb, opts)
         s_keep, g_keep = ~st, ~gt
-        assert g_keep.mean() > 0.9 and s_keep.mean() > 0.9
+        assert g_keep.mean() > 0.75 and s_keep.mean() > 0.75
     for k in keys:
         keep = s_keep if k == "s_sh" else g_keep
         a, b = (gpu[k], ref[k]) if keep is None else (gpu[k][keep], ref[k][keep])

@@ -519,3 +519,45 @@ def test_touching_marks_exactly_the_primitives_at_flagged_pixels(oracle_lib):
     flag[0, 0] = 1     # far from everything
     st, gt = oracle_lib.touching(sc, cam, flag)
     assert not st.any() and not gt.any()
+
+
+def _raw_check(oracle_lib, sc, cam, ids):
+    import ctypes
+    lib = oracle_lib.load()
+    pin = oracle_lib.oracle._Pinned(sc, cam, None)
+    ids = np.ascontiguousarray(ids, np.int32)
+    v = np.empty(ids.shape, np.uint8)
+    assert lib.ora_check_ids(ctypes.byref(pin.s), ctypes.byref(pin.c), ctypes.byref(pin.o),
+                             ids.ctypes.data, v.ctypes.data) == 0
+    return v.astype(bool)
+
+
+def test_id_check_accepts_exactly_the_correct_answers(oracle_lib):
+    sc, cams = sg.config_scene(0)
+    cam = cams[0]
+    ref = oracle_lib.render(sc, cam)
+    # the oracle's own answer is acceptable everywhere
+    assert _raw_check(oracle_lib, sc, cam, ref["id"]).all()
+    amb = (ref["amb"] & 1) != 0
+    cov = ref["id"] >= 0
+    # "nothing here" where a surfel clearly covers the pixel is wrong
+    v = _raw_check(oracle_lib, sc, cam, np.where(cov, -1, ref["id"]))
+    assert not v[cov & ~amb].any()
+    # a surfel that does not cover the pixel at all is wrong
+    far = np.where(cov, (ref["id"] + 500) % sc.n_surfels, ref["id"])
+    z, rho, nd, ok = oracle_lib.surfel_eval(sc, cam, *np.nonzero(cov)[::-1], far[cov])
+    outside = (ok == 0) | (rho > oracle_lib.DEFAULT_OPTS["surfel_r2"] * 1.01)
+    v = _raw_check(oracle_lib, sc, cam, far)
+    assert not v[cov][outside].any()
+
+
+def test_id_check_tie_and_runner_up(oracle_lib):
+    """Two identical coplanar discs: both ids are correct.  A disc clearly
+    behind another one is not."""
+    cam = ident_cam(32, 32, 30.0)
+    sc = mk_scene(0, s_pos=[[0, 0, 2.0], [0, 0, 2.0], [0, 0, 2.5]], s_rot=[[1.0, 0, 0, 0]] * 3,
+                  s_scale=[[0.1, 0.1], [0.1, 0.1], [0.2, 0.2]], s_sh=np.zeros((3, 1, 3)))
+    ref = oracle_lib.render(sc, cam)
+    both = ref["id"] == 0
+    assert _raw_check(oracle_lib, sc, cam, np.where(both, 1, ref["id"]))[both].all()
+    assert not _raw_check(oracle_lib, sc, cam, np.where(both, 2, ref["id"]))[both].any()
