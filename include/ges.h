@@ -202,6 +202,30 @@ GES_API ges_status ges_render_batch(ges_scene *const *scenes, const ges_camera *
                             int32_t n_views, const ges_render_opts *opts,
                             float *const *out_rgb, float *const *out_depth);
 
+/* Forward render (same result as ges_render_ex) that allocates no device
+ * memory (and, when it succeeds, no host memory either), for callers that
+ * cannot: applications that hand out device memory
+ * from their own fixed budget or pool, and render threads that must never
+ * block on cudaMalloc/cudaFree (cudaFree waits for the whole device).  The
+ * paper has no counterpart; this is a deployment convenience.
+ *
+ * No scene handle: desc, cam, opts (NULL = defaults) are read directly; the
+ * outputs are as in ges_render_ex (out_rgb required, the others may be
+ * NULL); work is queued on `stream` and the call returns after that stream
+ * has finished the render.  Intermediate data lives in one fixed device array
+ * of 18 MiB that every GPU loading this library holds until the process
+ * exits.  Limits: n_surfels <= 65536, n_gaussians <= 65536, at most 16384
+ * tiles of 16x16 pixels (e.g. 2048x2048), at most 1048576 tile entries per
+ * primitive kind; larger inputs get GES_ERR_CAPACITY and a message.  The
+ * first call on a device looks up that array's device address, so make it
+ * before any stream capture.  All calls share the one array and it keeps
+ * the previous call's contents (the call clears what must start at zero):
+ * calls whose GPU work overlaps in time, from any thread or stream, race and
+ * corrupt each other's results; serialise them. */
+GES_API ges_status ges_render_noalloc(const ges_scene_desc *desc, const ges_camera *cam,
+                                      const ges_render_opts *opts, float *out_rgb, float *out_depth,
+                                      int32_t *out_surfel_id, float *aux, void *stream);
+
 /* Counters of the last render on this scene. */
 GES_API ges_status ges_get_stats(const ges_scene *scene, ges_stats *out);
 

@@ -491,3 +491,112 @@ const char *ges_last_error_message(void) { return g_err.c_str(); }
 int32_t ges_version(void) { return 1; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// ges_render_noalloc: the forward render with every intermediate buffer in one
+// fixed device array, for callers that cannot allocate device memory.
+
+#include <mutex>
+
+namespace {
+
+constexpr int64_t kNaMaxSurfels = 65536, kNaMaxGaussians = 65536, kNaMaxTiles = 16384;
+constexpr int64_t kNaMaxPairs = 1048576;
+
+constexpr size_t na_align(size_t x) { return (x + 255) & ~(size_t)255; }
+// byte offsets of the regions inside the array
+constexpr size_t kNaSRec = 0;
+constexpr size_t kNaSRgb = na_align(kNaSRec + kNaMaxSurfels * 64);
+constexpr size_t kNaGRec = na_align(kNaSRgb + kNaMaxSurfels * 16);
+constexpr size_t kNaSVis = na_align(kNaGRec + kNaMaxGaussians * 64);
+constexpr size_t kNaGVis = na_align(kNaSVis + kNaMaxSurfels * 4);
+constexpr size_t kNaTileBytes = na_align((kNaMaxTiles + 1) * 4);
+constexpr size_t kNaSCnt = na_align(kNaGVis + kNaMaxGaussians * 4);   // s_cnt, g_cnt adjacent (cleared together)
+constexpr size_t kNaGCnt = kNaSCnt + kNaTileBytes;
+constexpr size_t kNaSOff = kNaGCnt + kNaTileBytes;
+constexpr size_t kNaGOff = kNaSOff + kNaTileBytes;
+constexpr size_t kNaSCur = kNaGOff + kNaTileBytes;
+constexpr size_t kNaGCur = kNaSCur + kNaTileBytes;
+constexpr size_t kNaStatus = kNaGCur + kNaTileBytes;
+constexpr size_t kNaSList = na_align(kNaStatus + ST_WORDS * 4);
+constexpr size_t kNaGList = na_align(kNaSList + kNaMaxPairs * 4);
+constexpr size_t kNaBytes = na_align(kNaGList + kNaMaxPairs * 4);
+static_assert(kNaBytes <= (size_t)18 << 20, "fixed scratch exceeds its stated 18 MiB");
+
+constexpr int kNaMaxDevices = 64;
+std::once_flag g_na_once[kNaMaxDevices];
+unsigned char *g_na_ptr[kNaMaxDevices];
+cudaError_t g_na_err[kNaMaxDevices];
+ges_status g_na_arch[kNaMaxDevices];
+
+}  // namespace
+
+// The fixed scratch.  In host code this name is only a stand-in for the
+// device symbol: its device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+extern "C" GES_API ges_status ges_render_noalloc(const ges_scene_desc *desc, const ges_camera *cam,
+                                                 const ges_render_opts *opts, float *out_rgb, float *out_depth,
+                                                 int32_t *out_surfel_id, float *aux, void *stream)
+{
+    ges_status r = check_desc(desc);
+    if (r != GES_OK) return r;
+    if (!out_rgb) return fail(GES_ERR_INVALID_ARG, "out_rgb is NULL");
+    CamParams C;
+    OptParams O;
+    if ((r = make_cam(cam, C)) != GES_OK) return r;
+    if ((r = make_opts(opts, O)) != GES_OK) return r;
+    if (desc->n_surfels > kNaMaxSurfels || desc->n_gaussians > kNaMaxGaussians)
+        return fail(GES_ERR_CAPACITY, "ges_render_noalloc: at most %lld surfels and %lld Gaussians (got %lld, %lld)",
+                    (long long)kNaMaxSurfels, (long long)kNaMaxGaussians, (long long)desc->n_surfels,
+                    (long long)desc->n_gaussians);
+    const int64_t T = (int64_t)C.tiles_x * C.tiles_y;
+    if (T > kNaMaxTiles)
+        return fail(GES_ERR_CAPACITY, "ges_render_noalloc: image %dx%d needs %lld tiles, at most %lld", C.W, C.H,
+                    (long long)T, (long long)kNaMaxTiles);
+    int dev = 0;
+    GES_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNaMaxDevices) return fail(GES_ERR_UNSUPPORTED, "device ordinal %d too large", dev);
+    // once per device, with that device current: check the architecture and
+    // look up the array's device address
+    std::call_once(g_na_once[dev], [dev]() {
+        int d = dev;
+        g_na_arch[dev] = check_device(&d);
+        void *p = nullptr;
+        g_na_err[dev] = g_na_arch[dev] == GES_OK ? cudaGetSymbolAddress(&p, g_noalloc_scratch) : cudaSuccess;
+        g_na_ptr[dev] = (unsigned char *)p;
+    });
+    if (g_na_arch[dev] != GES_OK)
+        return fail(g_na_arch[dev], "device %d is not an sm_103 GPU (this library is built for sm_103a only)", dev);
+    if (g_na_err[dev] != cudaSuccess) return cuda_fail(g_na_err[dev], "cudaGetSymbolAddress(fixed scratch)");
+    unsigned char *base = g_na_ptr[dev];
+    cudaStream_t st = (cudaStream_t)stream;
+
+    ViewScratch X;
+    X.s_rec = (float4 *)(base + kNaSRec); X.s_rgb = (float4 *)(base + kNaSRgb); X.g_rec = (float4 *)(base + kNaGRec);
+    X.s_vis = (int *)(base + kNaSVis); X.g_vis = (int *)(base + kNaGVis);
+    X.s_cnt = (int *)(base + kNaSCnt); X.g_cnt = (int *)(base + kNaGCnt);
+    X.s_off = (int *)(base + kNaSOff); X.g_off = (int *)(base + kNaGOff);
+    X.s_cur = (int *)(base + kNaSCur); X.g_cur = (int *)(base + kNaGCur);
+    X.s_list = (int *)(base + kNaSList); X.g_list = (int *)(base + kNaGList);
+    X.s_cap = kNaMaxPairs; X.g_cap = kNaMaxPairs;
+    X.status = (unsigned *)(base + kNaStatus);
+    // the array keeps the previous call's contents: clear the tile counters
+    // (adjacent) and the status words, which must start at zero
+    GES_CUDA(cudaMemsetAsync(base + kNaSCnt, 0, 2 * kNaTileBytes, st));
+    GES_CUDA(cudaMemsetAsync(X.status, 0, ST_WORDS * 4, st));
+    SceneView S{desc->n_surfels, desc->n_gaussians, desc->sh_degree, desc->attr_dtype, desc->sh_dtype,
+                desc->s_pos, desc->s_rot, desc->s_scale, desc->s_sh, desc->g_pos, desc->g_rot, desc->g_scale,
+                desc->g_opac, desc->g_sh};
+    cudaError_t e = launch_forward(S, C, O, X, out_rgb, out_depth, out_surfel_id, aux, st, nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    unsigned w[ST_WORDS];
+    GES_CUDA(cudaMemcpyAsync(w, X.status, sizeof w, cudaMemcpyDeviceToHost, st));
+    GES_CUDA(cudaStreamSynchronize(st));
+    if (w[ST_FLAGS] & FLAG_BADQ)
+        return fail(GES_ERR_INVALID_ARG, "a rotation quaternion has zero norm or is not finite");
+    if (w[ST_FLAGS] & (FLAG_SOVF | FLAG_GOVF))
+        return fail(GES_ERR_CAPACITY, "ges_render_noalloc: %u surfel and %u Gaussian tile entries exceed the %lld "
+                    "entries per kind of the fixed scratch", w[ST_SPAIRS], w[ST_GPAIRS], (long long)kNaMaxPairs);
+    return GES_OK;
+}

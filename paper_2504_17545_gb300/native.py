@@ -78,6 +78,8 @@ _SIGS = {
                                       C.c_void_p, C.c_void_p, C.c_void_p, _P(ges_grads)]),
     "ges_render_batch": (C.c_int, [_P(C.c_void_p), _P(ges_camera), _P(C.c_int32), C.c_int32,
                                    _P(ges_render_opts), _P(C.c_void_p), _P(C.c_void_p)]),
+    "ges_render_noalloc": (C.c_int, [_P(ges_scene_desc), _P(ges_camera), _P(ges_render_opts), C.c_void_p,
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ges_get_stats": (C.c_int, [C.c_void_p, _P(ges_stats)]),
     "ges_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
     "ges_get_profile": (C.c_int, [C.c_void_p, _P(ges_profile)]),
