@@ -77,6 +77,7 @@ struct ges_scene {
     DevBuf s_rec, s_rgb, g_rec, s_vis, g_vis;
     DevBuf s_cnt, g_cnt, s_off, g_off, s_cur, g_cur;
     DevBuf s_list, g_list;
+    DevBuf hist, base, vcount;     // local binning
     DevBuf status;                 // ST_WORDS per view slot
     unsigned *status_host = nullptr;
     int status_slots = 0;
@@ -205,6 +206,16 @@ ges_status ensure_scratch(ges_scene *s, int64_t T, int slots, cudaStream_t st)
             return cuda_fail(e, "scratch allocation (tile offsets)");
         s->tiles_cap = Tc;
     }
+    {
+        // local binning: one histogram row and one base row per preprocess CTA
+        int sms = 152;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+        const LocalBins B = plan_local_bins(s->desc.n_surfels, s->desc.n_gaussians, sms);
+        const int64_t P = std::max(B.Ps + B.Pg, 1), Tl = std::min<int64_t>(T, kLocalMaxTiles);
+        if ((e = s->hist.ensure((size_t)P * ((Tl + 1) / 2) * 4)) || (e = s->base.ensure((size_t)P * Tl * 4)) ||
+            (e = s->vcount.ensure((size_t)P * 4)))
+            return cuda_fail(e, "scratch allocation (bins)");
+    }
     if (s->s_cap == 0) s->s_cap = std::max<int64_t>((int64_t)1 << 20, 4 * s->desc.n_surfels);
     if (s->g_cap == 0) s->g_cap = std::max<int64_t>((int64_t)1 << 20, 4 * s->desc.n_gaussians);
     if ((e = s->s_list.ensure(s->s_cap * 4)) || (e = s->g_list.ensure(s->g_cap * 4)))
@@ -230,6 +241,9 @@ ViewScratch scratch_of(ges_scene *s, int slot)
     X.s_list = (int *)s->s_list.p; X.g_list = (int *)s->g_list.p;
     X.s_cap = s->s_cap; X.g_cap = s->g_cap;
     X.status = (unsigned *)s->status.p + (size_t)slot * ST_WORDS;
+    X.hist = (unsigned *)s->hist.p;
+    X.base = (unsigned *)s->base.p;
+    X.vcount = (unsigned *)s->vcount.p;
     return X;
 }
 
@@ -356,6 +370,7 @@ ges_status ges_create_scene(const ges_scene_desc *desc, ges_scene **out)
     if (r != GES_OK) return r;
     int dev = 0;
     if ((r = check_device(&dev)) != GES_OK) return r;
+    GES_CUDA(prepare_forward_kernels());
     ges_scene *s = new (std::nothrow) ges_scene();
     if (!s) return fail(GES_ERR_OOM, "host allocation failed");
     s->desc = *desc;
@@ -380,7 +395,8 @@ ges_status ges_destroy_scene(ges_scene *s)
     if (!s) return GES_OK;
     cudaStreamSynchronize(s->stream);
     DevBuf *bufs[] = {&s->s_rec, &s->s_rgb, &s->g_rec, &s->s_vis, &s->g_vis, &s->s_cnt, &s->g_cnt, &s->s_off,
-                      &s->g_off, &s->s_cur, &s->g_cur, &s->s_list, &s->g_list, &s->status};
+                      &s->g_off, &s->s_cur, &s->g_cur, &s->s_list, &s->g_list, &s->hist, &s->base,
+                      &s->vcount, &s->status};
     for (DevBuf *b : bufs) b->release();
     if (s->status_host) cudaFreeHost(s->status_host);
     for (cudaEvent_t e : s->ev) cudaEventDestroy(e);

@@ -1,28 +1,208 @@
 // Forward render of Gaussian-enhanced Surfels (Sec. 3, Eq. 1-5) for sm_103a.
 //
-// Per view, four launches on one stream:
-//   k_preprocess  one thread per primitive: surfel raster record + colour, or
-//                 Gaussian record (projection, conic, exact support, colour);
-//                 counts tile overlaps with integer atomics and appends the
-//                 primitive to a compact visible list.
-//   k_scan        exclusive scan of the per-tile counts (one CTA per list),
-//                 capacity check, counts reset for the next render.
-//   k_fill        scatters visible primitives into their tiles' lists.
-//   k_raster      one CTA per 16x16 tile, one warp per 8x4 pixel block:
-//                 pass 1 z-buffer (lexicographic min of (depth, surfel id)),
-//                 pass 2 depth-tested Gaussian accumulation (Eq. 2-4) and the
-//                 composite of Eq. 5, all in registers.
-// List order inside a tile is whatever the fill atomics produce: the z-buffer
-// min is order independent and the Gaussian sums are accumulated exactly in
-// 64-bit fixed point (2^-32 units), so the image is bit-identical run to run
-// without any sort and without floating-point atomics.
+// Per view, on one stream:
+//   k_prep_local  each CTA owns a fixed range of surfels or Gaussians: it sets
+//                 each primitive up (surfel raster record + colour, or Gaussian
+//                 record: projection, conic, exact support, colour), appends
+//                 the visible ones to its own segment of the visible list, and
+//                 counts tile overlaps in a shared-memory histogram (16-bit
+//                 counters packed in pairs), which it writes out as one row.
+//   k_colscan     per tile, exclusive scan of those rows over the CTAs (each
+//                 CTA's start inside the tile's list) and the tile total.
+//   k_scan        exclusive scan of the tile totals, capacity check.
+//   k_fill_local  each CTA re-walks its visible segment and places every
+//                 (tile, primitive) pair with shared-memory cursors.
+//   k_raster      one CTA per 16x16 tile: the CTA stages 256 records at a time
+//                 in shared memory; each warp (an 8x4 pixel block) culls them
+//                 by bbox and depth and tests the survivors.  Pass 1 keeps the
+//                 lexicographic min of (depth, surfel id); pass 2 accumulates
+//                 the depth-tested Gaussians (Eq. 2-4); the epilogue applies
+//                 Eq. 5.  Everything per pixel stays in registers.
+// No global atomics are needed for binning, so hot tiles do not serialise.
+// Very large images (more than 32768 tiles) and callers without binning
+// scratch use k_prep_atomic / k_fill_atomic instead (global counters).
+//
+// List order inside a tile is not fixed (shared-memory atomics), but the
+// z-buffer min is order independent and the Gaussian sums are accumulated
+// exactly in 64-bit fixed point (units of 2^-32), so the image is
+// bit-identical run to run without any sort and without float atomics.
 #include "ges_internal.cuh"
 
 namespace ges {
 
+LocalBins plan_local_bins(int64_t N, int64_t M, int num_sms)
+{
+    LocalBins b{0, 0, 1, 1};
+    const int P = num_sms;   // one 16-warp CTA per SM
+    if (N > 0 && M > 0) {
+        b.Ps = (int)((P * N + (N + M) / 2) / (N + M));
+        b.Ps = b.Ps < 1 ? 1 : (b.Ps > P - 1 ? P - 1 : b.Ps);
+        b.Pg = P - b.Ps;
+    } else if (N > 0) {
+        b.Ps = P;
+    } else if (M > 0) {
+        b.Pg = P;
+    }
+    // a CTA's count for one tile must fit in 16 bits
+    const int64_t cap = 60000;
+    if (N > 0 && (N + b.Ps - 1) / b.Ps > cap) b.Ps = (int)((N + cap - 1) / cap);
+    if (M > 0 && (M + b.Pg - 1) / b.Pg > cap) b.Pg = (int)((M + cap - 1) / cap);
+    if (b.Ps > 0) b.Rs = (N + b.Ps - 1) / b.Ps;
+    if (b.Pg > 0) b.Rg = (M + b.Pg - 1) / b.Pg;
+    // ranges start on multiples of 4 primitives (keeps vector stores aligned)
+    b.Rs = (b.Rs + 3) & ~(int64_t)3;
+    b.Rg = (b.Rg + 3) & ~(int64_t)3;
+    return b;
+}
+
 namespace {
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ void store_rec(float4 *dst, const void *rec)
+{
+    const float4 *src = reinterpret_cast<const float4 *>(rec);
+    dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2]; dst[3] = src[3];
+}
+
+// Set up primitive i of the given kind; on success write its record and
+// return its pixel bbox.
+__device__ __forceinline__ bool setup_and_store(const SceneView &S, const CamParams &C, const OptParams &O,
+                                                const ViewScratch &X, bool surf, int64_t i, int &x0, int &y0,
+                                                int &x1, int &y1)
+{
+    if (surf) {
+        SurfelOut o;
+        surfel_setup(S, C, O, i, o);
+        if (!o.valid_quat) atomicOr(X.status + ST_FLAGS, FLAG_BADQ);
+        if (!o.visible) return false;
+        store_rec(X.s_rec + 4 * i, &o.rec);
+        X.s_rgb[i] = make_float4(o.rgb[0], o.rgb[1], o.rgb[2], 0.f);
+        x0 = o.x0; y0 = o.y0; x1 = o.x1; y1 = o.y1;
+    } else {
+        GaussOut o;
+        gauss_setup(S, C, O, i, o);
+        if (!o.valid_quat) atomicOr(X.status + ST_FLAGS, FLAG_BADQ);
+        if (!o.visible) return false;
+        store_rec(X.g_rec + 4 * i, &o.rec);
+        x0 = o.x0; y0 = o.y0; x1 = o.x1; y1 = o.y1;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// local binning
+
+__global__ void __launch_bounds__(kPrepThreads, 1) k_prep_local(SceneView S, CamParams C, OptParams O,
+                                                                ViewScratch X, LocalBins B)
+{
+    extern __shared__ unsigned hist[];   // ceil(T/2) words, two 16-bit counters each
+    __shared__ unsigned vcnt;
+    const int T = C.tiles_x * C.tiles_y, words = (T + 1) >> 1;
+    const int c = blockIdx.x;
+    const bool surf = c < B.Ps;
+    const int64_t R = surf ? B.Rs : B.Rg, n = surf ? S.N : S.M;
+    const int64_t beg = (int64_t)(surf ? c : c - B.Ps) * R;
+    const int64_t end = beg + R < n ? beg + R : n;
+    for (int w = threadIdx.x; w < words; w += kPrepThreads) hist[w] = 0u;
+    if (threadIdx.x == 0) vcnt = 0u;
+    __syncthreads();
+    int *seg = (surf ? X.s_vis : X.g_vis) + beg;
+    for (int64_t i0 = beg; i0 < end; i0 += kPrepThreads) {
+        const int64_t i = i0 + threadIdx.x;
+        int x0 = 0, y0 = 0, x1 = -1, y1 = -1;
+        const bool vis = i < end && setup_and_store(S, C, O, X, surf, i, x0, y0, x1, y1);
+        const unsigned m = __ballot_sync(0xffffffffu, vis);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            unsigned b = 0;
+            if ((int)lane_id() == leader) b = atomicAdd(&vcnt, (unsigned)__popc(m));
+            b = __shfl_sync(0xffffffffu, b, leader);
+            if (vis) seg[b + __popc(m & ((1u << lane_id()) - 1u))] = (int)i;
+        }
+        if (vis) {
+            const int tx0 = x0 / kTile, tx1 = x1 / kTile, ty0 = y0 / kTile, ty1 = y1 / kTile;
+            for (int ty = ty0; ty <= ty1; ++ty)
+                for (int tx = tx0; tx <= tx1; ++tx) {
+                    const int t = ty * C.tiles_x + tx;
+                    atomicAdd(hist + (t >> 1), (t & 1) ? 65536u : 1u);
+                }
+        }
+    }
+    __syncthreads();
+    unsigned *row = X.hist + (size_t)c * words;
+    for (int w = threadIdx.x; w < words; w += kPrepThreads) row[w] = hist[w];
+    if (threadIdx.x == 0) {
+        X.vcount[c] = vcnt;
+        atomicAdd(X.status + (surf ? ST_SVIS : ST_GVIS), vcnt);
+    }
+}
+
+__device__ __forceinline__ unsigned hist_get(const unsigned *row, int t)
+{
+    const unsigned w = row[t >> 1];
+    return (t & 1) ? (w >> 16) : (w & 0xffffu);
+}
+
+// Per tile: exclusive scan over the CTAs of one kind.  Block = 32 tiles x 8
+// warps; warp w scans CTAs [w*P/8, (w+1)*P/8).
+__global__ void __launch_bounds__(256) k_colscan(ViewScratch X, int T, LocalBins B)
+{
+    __shared__ unsigned part[8][33];
+    const bool surf = blockIdx.y == 0;
+    const int P = surf ? B.Ps : B.Pg, r0 = surf ? 0 : B.Ps;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int t = blockIdx.x * 32 + lane;
+    const int words = (T + 1) >> 1;
+    const int a = r0 + (int)((int64_t)P * w / 8), b = r0 + (int)((int64_t)P * (w + 1) / 8);
+    unsigned s = 0;
+    if (t < T)
+        for (int r = a; r < b; ++r) s += hist_get(X.hist + (size_t)r * words, t);
+    part[w][lane] = s;
+    __syncthreads();
+    unsigned pre = 0, tot = 0;
+    for (int k = 0; k < 8; ++k) {
+        const unsigned v = part[k][lane];
+        if (k < w) pre += v;
+        tot += v;
+    }
+    if (t < T) {
+        for (int r = a; r < b; ++r) {
+            X.base[(size_t)r * T + t] = pre;
+            pre += hist_get(X.hist + (size_t)r * words, t);
+        }
+        if (w == 0) (surf ? X.s_cnt : X.g_cnt)[t] = (int)tot;
+    }
+}
+
+__global__ void __launch_bounds__(kPrepThreads) k_fill_local(ViewScratch X, int T, int tiles_x, LocalBins B)
+{
+    extern __shared__ unsigned cur[];    // T cursors
+    if (X.status[ST_FLAGS] & (FLAG_SOVF | FLAG_GOVF)) return;
+    const int c = blockIdx.x;
+    const bool surf = c < B.Ps;
+    const int *off = surf ? X.s_off : X.g_off;
+    const unsigned *brow = X.base + (size_t)c * T;
+    for (int t = threadIdx.x; t < T; t += kPrepThreads) cur[t] = (unsigned)off[t] + brow[t];
+    __syncthreads();
+    const int64_t beg = (int64_t)(surf ? c : c - B.Ps) * (surf ? B.Rs : B.Rg);
+    const int *seg = (surf ? X.s_vis : X.g_vis) + beg;
+    const float4 *rec = surf ? X.s_rec : X.g_rec;
+    int *list = surf ? X.s_list : X.g_list;
+    const unsigned n = X.vcount[c];
+    for (unsigned k = threadIdx.x; k < n; k += kPrepThreads) {
+        const int id = seg[k];
+        const float4 r3 = rec[4 * (int64_t)id + 3];
+        const unsigned lo = __float_as_uint(r3.y), hi = __float_as_uint(r3.z);
+        const int tx0 = (lo & 0xffff) / kTile, ty0 = (lo >> 16) / kTile;
+        const int tx1 = (hi & 0xffff) / kTile, ty1 = (hi >> 16) / kTile;
+        for (int ty = ty0; ty <= ty1; ++ty)
+            for (int tx = tx0; tx <= tx1; ++tx) list[atomicAdd(cur + ty * tiles_x + tx, 1u)] = id;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// atomic binning (fallback)
 
 __device__ __forceinline__ void append_visible(bool vis, int64_t i, unsigned *counter, int *list)
 {
@@ -36,53 +216,44 @@ __device__ __forceinline__ void append_visible(bool vis, int64_t i, unsigned *co
     if (vis) list[base + __popc(m & ((1u << lane) - 1u))] = (int)i;
 }
 
-__device__ __forceinline__ void count_tiles(int x0, int y0, int x1, int y1, int tiles_x, int *cnt)
+__global__ void __launch_bounds__(256) k_prep_atomic(SceneView S, CamParams C, OptParams O, ViewScratch X,
+                                                     int n_sblocks)
 {
-    const int tx0 = x0 / kTile, tx1 = x1 / kTile, ty0 = y0 / kTile, ty1 = y1 / kTile;
-    for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(cnt + ty * tiles_x + tx, 1);
+    const bool surf = (int)blockIdx.x < n_sblocks;
+    const int64_t i = (int64_t)(surf ? blockIdx.x : blockIdx.x - n_sblocks) * 256 + threadIdx.x;
+    int x0 = 0, y0 = 0, x1 = -1, y1 = -1;
+    const bool vis = i < (surf ? S.N : S.M) && setup_and_store(S, C, O, X, surf, i, x0, y0, x1, y1);
+    if (vis) {
+        int *cnt = surf ? X.s_cnt : X.g_cnt;
+        for (int ty = y0 / kTile; ty <= y1 / kTile; ++ty)
+            for (int tx = x0 / kTile; tx <= x1 / kTile; ++tx) atomicAdd(cnt + ty * C.tiles_x + tx, 1);
+    }
+    append_visible(vis, i, X.status + (surf ? ST_SVIS : ST_GVIS), surf ? X.s_vis : X.g_vis);
 }
 
-__global__ void __launch_bounds__(256) k_preprocess(SceneView S, CamParams C, OptParams O, ViewScratch X,
-                                                    int n_sblocks)
+__device__ __forceinline__ void fill_one(const float4 *rec, int id, int tiles_x, int *cur, int *list)
 {
-    if ((int)blockIdx.x < n_sblocks) {
-        const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
-        bool vis = false;
-        if (i < S.N) {
-            SurfelOut o;
-            surfel_setup(S, C, O, i, o);
-            if (!o.valid_quat) atomicOr(X.status + ST_FLAGS, FLAG_BADQ);
-            if (o.visible) {
-                const float4 *src = reinterpret_cast<const float4 *>(&o.rec);
-                float4 *dst = X.s_rec + 4 * i;
-                dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2]; dst[3] = src[3];
-                X.s_rgb[i] = make_float4(o.rgb[0], o.rgb[1], o.rgb[2], 0.f);
-                count_tiles(o.x0, o.y0, o.x1, o.y1, C.tiles_x, X.s_cnt);
-                vis = true;
-            }
-        }
-        append_visible(vis, i, X.status + ST_SVIS, X.s_vis);
-    } else {
-        const int64_t i = (int64_t)(blockIdx.x - n_sblocks) * 256 + threadIdx.x;
-        bool vis = false;
-        if (i < S.M) {
-            GaussOut o;
-            gauss_setup(S, C, O, i, o);
-            if (!o.valid_quat) atomicOr(X.status + ST_FLAGS, FLAG_BADQ);
-            if (o.visible) {
-                const float4 *src = reinterpret_cast<const float4 *>(&o.rec);
-                float4 *dst = X.g_rec + 4 * i;
-                dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2]; dst[3] = src[3];
-                count_tiles(o.x0, o.y0, o.x1, o.y1, C.tiles_x, X.g_cnt);
-                vis = true;
-            }
-        }
-        append_visible(vis, i, X.status + ST_GVIS, X.g_vis);
+    const float4 r3 = rec[4 * (int64_t)id + 3];
+    const unsigned lo = __float_as_uint(r3.y), hi = __float_as_uint(r3.z);
+    const int x0 = lo & 0xffff, y0 = lo >> 16, x1 = hi & 0xffff, y1 = hi >> 16;
+    for (int ty = y0 / kTile; ty <= y1 / kTile; ++ty)
+        for (int tx = x0 / kTile; tx <= x1 / kTile; ++tx) list[atomicAdd(cur + ty * tiles_x + tx, 1)] = id;
+}
+
+__global__ void __launch_bounds__(256) k_fill_atomic(ViewScratch X, int tiles_x)
+{
+    if (X.status[ST_FLAGS] & (FLAG_SOVF | FLAG_GOVF)) return;
+    const unsigned ns = X.status[ST_SVIS], ng = X.status[ST_GVIS];
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < ns + ng; k += stride) {
+        if (k < ns) fill_one(X.s_rec, X.s_vis[k], tiles_x, X.s_cur, X.s_list);
+        else fill_one(X.g_rec, X.g_vis[k - ns], tiles_x, X.g_cur, X.g_list);
     }
 }
 
-// Exclusive scan of T tile counts by one CTA of 1024 threads.
+// ---------------------------------------------------------------------------
+// scan of tile totals (both binning modes)
+
 __global__ void __launch_bounds__(1024) k_scan(ViewScratch X, int T)
 {
     const bool surf = blockIdx.x == 0;
@@ -95,7 +266,6 @@ __global__ void __launch_bounds__(1024) k_scan(ViewScratch X, int T)
     const int b = min(tid * per, T), e = min(b + per, T);
     long long local = 0;
     for (int t = b; t < e; ++t) local += cnt[t];
-    // block exclusive scan of the per-thread sums
     long long incl = local;
     for (int d = 1; d < 32; d <<= 1) {
         long long y = __shfl_up_sync(0xffffffffu, incl, d);
@@ -109,7 +279,7 @@ __global__ void __launch_bounds__(1024) k_scan(ViewScratch X, int T)
             long long y = __shfl_up_sync(0xffffffffu, wi, d);
             if (tid >= d) wi += y;
         }
-        warp_tot[tid] = wi - w;   // exclusive prefix of warp totals
+        warp_tot[tid] = wi - w;
     }
     __syncthreads();
     long long run = warp_tot[tid >> 5] + incl - local;
@@ -127,29 +297,8 @@ __global__ void __launch_bounds__(1024) k_scan(ViewScratch X, int T)
     }
 }
 
-__device__ __forceinline__ void fill_one(const float4 *rec, int id, int tiles_x, int *cur, int *list)
-{
-    const float4 r3 = rec[4 * (int64_t)id + 3];
-    const unsigned lo = __float_as_uint(r3.y), hi = __float_as_uint(r3.z);
-    const int x0 = lo & 0xffff, y0 = lo >> 16, x1 = hi & 0xffff, y1 = hi >> 16;
-    const int tx0 = x0 / kTile, tx1 = x1 / kTile, ty0 = y0 / kTile, ty1 = y1 / kTile;
-    for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1; ++tx) {
-            const int slot = atomicAdd(cur + ty * tiles_x + tx, 1);
-            list[slot] = id;
-        }
-}
-
-__global__ void __launch_bounds__(256) k_fill(ViewScratch X, int tiles_x)
-{
-    if (X.status[ST_FLAGS] & (FLAG_SOVF | FLAG_GOVF)) return;
-    const unsigned ns = X.status[ST_SVIS], ng = X.status[ST_GVIS];
-    const unsigned stride = gridDim.x * blockDim.x;
-    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < ns + ng; k += stride) {
-        if (k < ns) fill_one(X.s_rec, X.s_vis[k], tiles_x, X.s_cur, X.s_list);
-        else fill_one(X.g_rec, X.g_vis[k - ns], tiles_x, X.g_cur, X.g_list);
-    }
-}
+// ---------------------------------------------------------------------------
+// raster
 
 __device__ __forceinline__ bool box_overlap(unsigned lo, unsigned hi, int wx0, int wy0, int wx1, int wy1)
 {
@@ -157,7 +306,8 @@ __device__ __forceinline__ bool box_overlap(unsigned lo, unsigned hi, int wx0, i
     return x0 <= wx1 && x1 >= wx0 && y0 <= wy1 && y1 >= wy0;
 }
 
-constexpr int kStage = 5;   // float4 per staged record (4 used + 1 pad: conflict-free STS.128)
+constexpr int kChunk = kRasterThreads;   // records staged per CTA round
+constexpr int kStage = 5;                // float4 per staged record (4 used + 1 pad: conflict-free STS.128)
 
 __global__ void __launch_bounds__(kRasterThreads) k_raster(ViewScratch X, CamParams C, OptParams O,
                                                            float *__restrict__ out_rgb,
@@ -165,56 +315,64 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(ViewScratch X, CamPar
                                                            int32_t *__restrict__ out_id,
                                                            float *__restrict__ aux)
 {
-    __shared__ float4 stage[kRasterThreads / 32][32][kStage];
+    __shared__ float4 stage[kChunk][kStage];
     if (X.status[ST_FLAGS] & (FLAG_SOVF | FLAG_GOVF)) return;
     const int tile = blockIdx.x;
     const int tx = tile % C.tiles_x, ty = tile / C.tiles_x;
     const unsigned warp = threadIdx.x >> 5, lane = lane_id();
     const int wx0 = tx * kTile + (warp & 1) * kWarpW, wy0 = ty * kTile + (warp >> 1) * kWarpH;
-    if (wx0 >= C.W || wy0 >= C.H) return;   // warp-uniform: no pixel of this block is in the image
+    const bool wactive = wx0 < C.W && wy0 < C.H;        // warp-uniform
     const int wx1 = min(wx0 + kWarpW - 1, C.W - 1), wy1 = min(wy0 + kWarpH - 1, C.H - 1);
     const int px = wx0 + (int)(lane & 7), py = wy0 + (int)(lane >> 3);
     const bool in_img = px < C.W && py < C.H;
     const float u = px + 0.5f, v = py + 0.5f;
-    float4(*st)[kStage] = stage[warp];
 
     // ---------------- pass 1: surfel z-buffer ----------------
     float best = in_img ? 0.f : INFINITY;   // 1/z of the nearest hit (0: none)
     int bid = 0x7fffffff;
     if (O.mode != GES_MODE_GAUSSIANS_ONLY) {
         const int s0 = X.s_off[tile], s1 = X.s_off[tile + 1];
-        float wmin = 0.f;   // smallest 'best' in the warp: surfels nearer than 1/wmin nowhere can't win
-        for (int base = s0; base < s1; base += 32) {
-            const int k = base + (int)lane;
-            bool keep = false;
+        float wmin = 0.f;   // smallest 'best' in the warp: a surfel whose 1/z never exceeds it cannot win
+        for (int base = s0; base < s1; base += kChunk) {
+            const int k = base + (int)threadIdx.x;
             if (k < s1) {
-                const int id = X.s_list[k];
-                const float4 *rp = X.s_rec + 4 * (int64_t)id;
+                const float4 *rp = X.s_rec + 4 * (int64_t)X.s_list[k];
                 const float4 r0 = rp[0], r1 = rp[1], r2 = rp[2], r3 = rp[3];
-                keep = box_overlap(__float_as_uint(r3.y), __float_as_uint(r3.z), wx0, wy0, wx1, wy1) &&
-                       r2.w >= wmin;
-                st[lane][0] = r0; st[lane][1] = r1; st[lane][2] = r2; st[lane][3] = r3;
+                stage[threadIdx.x][0] = r0; stage[threadIdx.x][1] = r1;
+                stage[threadIdx.x][2] = r2; stage[threadIdx.x][3] = r3;
             }
-            unsigned mask = __ballot_sync(0xffffffffu, keep);
-            __syncwarp();
-            while (mask) {
-                const int j = __ffs(mask) - 1;
-                mask &= mask - 1;
-                const float4 r2 = st[j][2];
-                if (r2.w < wmin) continue;                      // warp-uniform re-check
-                const float4 r0 = st[j][0], r1 = st[j][1];
-                const int id = __float_as_int(st[j][3].x);
-                const float du = u - r0.x, dv = v - r0.y;
-                const float iz = fmaf(r0.w, du, fmaf(r1.x, dv, r0.z));
-                const float A = fmaf(r1.y, du, fmaf(r1.z, dv, r1.w));
-                const float B = fmaf(r2.x, du, fmaf(r2.y, dv, r2.z));
-                const float q = fmaf(A, A, fmaf(B, B, -iz * iz));
-                const bool hit = q <= 0.f && iz < C.izn && (iz > best || (iz == best && id < bid));
-                if (hit) { best = iz; bid = id; }
-                if (__any_sync(0xffffffffu, hit))
-                    wmin = __uint_as_float(__reduce_min_sync(0xffffffffu, __float_as_uint(best)));
+            __syncthreads();
+            const int n = min(kChunk, s1 - base);
+            if (wactive) {
+                for (int j0 = 0; j0 < n; j0 += 32) {
+                    const int j = j0 + (int)lane;
+                    bool keep = false;
+                    if (j < n) {
+                        const float4 r3 = stage[j][3];
+                        keep = box_overlap(__float_as_uint(r3.y), __float_as_uint(r3.z), wx0, wy0, wx1, wy1) &&
+                               stage[j][2].w >= wmin;
+                    }
+                    unsigned mask = __ballot_sync(0xffffffffu, keep);
+                    while (mask) {
+                        const int jj = j0 + __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        const float4 r2 = stage[jj][2];
+                        if (r2.w < wmin) continue;                      // warp-uniform re-check
+                        const float4 r0 = stage[jj][0], r1 = stage[jj][1];
+                        const int id = __float_as_int(stage[jj][3].x);
+                        const float du = u - r0.x, dv = v - r0.y;
+                        const float iz = fmaf(r0.w, du, fmaf(r1.x, dv, r0.z));
+                        const float A = fmaf(r1.y, du, fmaf(r1.z, dv, r1.w));
+                        const float B = fmaf(r2.x, du, fmaf(r2.y, dv, r2.z));
+                        const float q = fmaf(A, A, fmaf(B, B, -iz * iz));
+                        const bool hit = q <= 0.f && iz < C.izn && (iz > best || (iz == best && id < bid));
+                        if (hit) { best = iz; bid = id; }
+                        if (__any_sync(0xffffffffu, hit))
+                            wmin = __uint_as_float(__reduce_min_sync(0xffffffffu, __float_as_uint(best)));
+                    }
+                }
             }
-            __syncwarp();
+            __syncthreads();
         }
     }
     const bool covered = bid != 0x7fffffff;
@@ -229,41 +387,50 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(ViewScratch X, CamPar
     long long acc_r = 0, acc_g = 0, acc_b = 0, acc_w = 0;
     if (O.mode != GES_MODE_SURFELS_ONLY) {
         const int g0 = X.g_off[tile], g1 = X.g_off[tile + 1];
-        // no Gaussian with key >= max_lanes(D_s) can pass the depth test here
+        // no Gaussian with key >= max over the warp's pixels of D_s can pass the depth test there
         const float wmaxD = __uint_as_float(__reduce_max_sync(0xffffffffu, in_img ? __float_as_uint(Ds) : 0u));
         const float amin32 = O.alpha_min * 4294967296.f;
-        for (int base = g0; base < g1; base += 32) {
-            const int k = base + (int)lane;
-            bool keep = false;
+        for (int base = g0; base < g1; base += kChunk) {
+            const int k = base + (int)threadIdx.x;
             if (k < g1) {
-                const int id = X.g_list[k];
-                const float4 *rp = X.g_rec + 4 * (int64_t)id;
+                const float4 *rp = X.g_rec + 4 * (int64_t)X.g_list[k];
                 const float4 r0 = rp[0], r1 = rp[1], r2 = rp[2], r3 = rp[3];
-                keep = box_overlap(__float_as_uint(r3.y), __float_as_uint(r3.z), wx0, wy0, wx1, wy1) &&
-                       r2.x < wmaxD;
-                st[lane][0] = r0; st[lane][1] = r1; st[lane][2] = r2; st[lane][3] = r3;
+                stage[threadIdx.x][0] = r0; stage[threadIdx.x][1] = r1;
+                stage[threadIdx.x][2] = r2; stage[threadIdx.x][3] = r3;
             }
-            unsigned mask = __ballot_sync(0xffffffffu, keep);
-            __syncwarp();
-            while (mask) {
-                const int j = __ffs(mask) - 1;
-                mask &= mask - 1;
-                GaussRec g;
-                *reinterpret_cast<float4 *>(&g.px) = st[j][0];
-                *reinterpret_cast<float4 *>(&g.ca) = st[j][1];
-                *reinterpret_cast<float4 *>(&g.key) = st[j][2];
-                float e;
-                const float a = gauss_alpha(g, u, v, e);
-                // alpha * 2^32 is exact scaling: the clamp decision equals alpha >= alpha_min
-                const float a32 = a * 4294967296.f;
-                if (in_img && a32 >= amin32 && g.key < Ds) {
-                    acc_w += __float2ll_rn(a32);
-                    acc_r += __float2ll_rn(a32 * g.r);
-                    acc_g += __float2ll_rn(a32 * g.g);
-                    acc_b += __float2ll_rn(a32 * g.b);
+            __syncthreads();
+            const int n = min(kChunk, g1 - base);
+            if (wactive) {
+                for (int j0 = 0; j0 < n; j0 += 32) {
+                    const int j = j0 + (int)lane;
+                    bool keep = false;
+                    if (j < n) {
+                        const float4 r3 = stage[j][3];
+                        keep = box_overlap(__float_as_uint(r3.y), __float_as_uint(r3.z), wx0, wy0, wx1, wy1) &&
+                               stage[j][2].x < wmaxD;
+                    }
+                    unsigned mask = __ballot_sync(0xffffffffu, keep);
+                    while (mask) {
+                        const int jj = j0 + __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        GaussRec g;
+                        *reinterpret_cast<float4 *>(&g.px) = stage[jj][0];
+                        *reinterpret_cast<float4 *>(&g.ca) = stage[jj][1];
+                        *reinterpret_cast<float4 *>(&g.key) = stage[jj][2];
+                        float e;
+                        const float a = gauss_alpha(g, u, v, e);
+                        // alpha * 2^32 is exact scaling: the clamp decision equals alpha >= alpha_min
+                        const float a32 = a * 4294967296.f;
+                        if (in_img && a32 >= amin32 && g.key < Ds) {
+                            acc_w += __float2ll_rn(a32);
+                            acc_r += __float2ll_rn(a32 * g.r);
+                            acc_g += __float2ll_rn(a32 * g.g);
+                            acc_b += __float2ll_rn(a32 * g.b);
+                        }
+                    }
                 }
             }
-            __syncwarp();
+            __syncthreads();
         }
     }
     if (!in_img) return;
@@ -292,22 +459,48 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(ViewScratch X, CamPar
 
 }  // namespace
 
+size_t local_bins_smem(int T, bool fill) { return fill ? (size_t)T * 4 : (size_t)((T + 1) / 2) * 4; }
+
+cudaError_t prepare_forward_kernels()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_prep_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)local_bins_smem(kLocalMaxTiles, false));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_fill_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)local_bins_smem(kLocalMaxTiles, true));
+}
+
 cudaError_t launch_forward(const SceneView &S, const CamParams &C, const OptParams &O, const ViewScratch &X,
                            float *out_rgb, float *out_depth, int32_t *out_id, float *aux, cudaStream_t st,
                            cudaEvent_t *ev)
 {
     const int T = C.tiles_x * C.tiles_y;
-    const int nsb = O.mode == GES_MODE_GAUSSIANS_ONLY ? 0 : (int)((S.N + 255) / 256);
-    const int ngb = O.mode == GES_MODE_SURFELS_ONLY ? 0 : (int)((S.M + 255) / 256);
     SceneView Sv = S;
     if (O.mode == GES_MODE_GAUSSIANS_ONLY) Sv.N = 0;
     if (O.mode == GES_MODE_SURFELS_ONLY) Sv.M = 0;
+    const bool local = X.hist != nullptr && T <= kLocalMaxTiles;
     if (ev) cudaEventRecord(ev[0], st);
-    if (nsb + ngb > 0) k_preprocess<<<nsb + ngb, 256, 0, st>>>(Sv, C, O, X, nsb);
+    LocalBins B{};
+    if (local) {
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        B = plan_local_bins(Sv.N, Sv.M, sms);
+        if (B.Ps + B.Pg > 0)
+            k_prep_local<<<B.Ps + B.Pg, kPrepThreads, local_bins_smem(T, false), st>>>(Sv, C, O, X, B);
+    } else {
+        const int nsb = (int)((Sv.N + 255) / 256), ngb = (int)((Sv.M + 255) / 256);
+        if (nsb + ngb > 0) k_prep_atomic<<<nsb + ngb, 256, 0, st>>>(Sv, C, O, X, nsb);
+    }
     if (ev) cudaEventRecord(ev[1], st);
+    if (local && B.Ps + B.Pg > 0) k_colscan<<<dim3((T + 31) / 32, 2), 256, 0, st>>>(X, T, B);
     k_scan<<<2, 1024, 0, st>>>(X, T);
     if (ev) cudaEventRecord(ev[2], st);
-    k_fill<<<152 * 8, 256, 0, st>>>(X, C.tiles_x);
+    if (local) {
+        if (B.Ps + B.Pg > 0) k_fill_local<<<B.Ps + B.Pg, kPrepThreads, local_bins_smem(T, true), st>>>(X, T, C.tiles_x, B);
+    } else {
+        k_fill_atomic<<<152 * 8, 256, 0, st>>>(X, C.tiles_x);
+    }
     if (ev) cudaEventRecord(ev[3], st);
     k_raster<<<T, kRasterThreads, 0, st>>>(X, C, O, out_rgb, out_depth, out_id, aux);
     if (ev) cudaEventRecord(ev[4], st);

@@ -60,14 +60,30 @@ struct ViewScratch {
     float4 *s_rec;        // [N][4]  surfel raster records
     float4 *s_rgb;        // [N]     surfel colours
     float4 *g_rec;        // [M][4]  Gaussian raster records
-    int *s_vis, *g_vis;   // compact lists of visible primitives
+    int *s_vis, *g_vis;   // visible primitives (per-CTA segments with local bins)
     int *s_cnt, *g_cnt;   // [T]     per-tile counts (zero between renders)
     int *s_off, *g_off;   // [T+1]   exclusive offsets
-    int *s_cur, *g_cur;   // [T]     fill cursors
+    int *s_cur, *g_cur;   // [T]     fill cursors (atomic binning)
     int *s_list, *g_list; // tile lists
     int64_t s_cap, g_cap; // list capacities (entries)
     unsigned *status;     // [ST_WORDS]
+    // local binning (per-CTA primitive ranges with shared-memory histograms);
+    // left null, the render bins with global atomics instead
+    unsigned *hist = nullptr;    // [P][ceil(T/2)] packed 16-bit per-CTA tile counts
+    unsigned *base = nullptr;    // [P][T] per-CTA start inside each tile's list
+    unsigned *vcount = nullptr;  // [P] visible primitives per CTA
 };
+
+// Number of preprocess CTAs for local binning and the size of their ranges.
+struct LocalBins {
+    int Ps, Pg;           // CTAs over surfels, over Gaussians
+    int64_t Rs, Rg;       // primitives per CTA
+};
+constexpr int kLocalMaxTiles = 32768;   // shared-memory cursors of the fill: 4 B per tile
+constexpr int kPrepThreads = 512;
+LocalBins plan_local_bins(int64_t N, int64_t M, int num_sms);
+size_t local_bins_smem(int T, bool fill);
+cudaError_t prepare_forward_kernels();   // once per device: large dynamic shared memory
 
 // ---------------------------------------------------------------------------
 // host launchers (ges_forward.cu / ges_backward.cu)
@@ -232,28 +248,79 @@ __device__ __forceinline__ void sh_basis_grad(int K, float x, float y, float z, 
     dY[15][0] = -3.f * A * (xx - yy); dY[15][1] = 6.f * A * x * y; dY[15][2] = 0.f;
 }
 
-// Eq. 1: colour = max(0, 0.5 + sum_k SH_k Y_k(dir)) per channel; also returns
-// the unclamped value (its sign gates the gradient).
-__device__ __forceinline__ void sh_colour(const void *sh, int64_t base, int K, int dtype, const float *Y,
-                                          float *rgb, float *raw)
+// One primitive's 3K SH coefficients as floats.  When the row is a multiple
+// of 16 bytes (K = 4, 16 in FP32; K = 16 in 16-bit) it is read with 128-bit
+// loads; the rows of consecutive primitives are contiguous.
+template <int K>
+__device__ __forceinline__ void load_sh_row(const void *sh, int64_t i, int dtype, float *c)
 {
-    float r = 0.5f, g = 0.5f, b = 0.5f;
+    constexpr int n = 3 * K;
     if (dtype == GES_F32) {
-        const float *p = reinterpret_cast<const float *>(sh) + base;
-        for (int k = 0; k < K; ++k) {
-            r = fmaf(__ldg(p + 3 * k), Y[k], r);
-            g = fmaf(__ldg(p + 3 * k + 1), Y[k], g);
-            b = fmaf(__ldg(p + 3 * k + 2), Y[k], b);
+        const float *p = reinterpret_cast<const float *>(sh) + (int64_t)n * i;
+        if ((n % 4) == 0 && (reinterpret_cast<uintptr_t>(sh) & 15) == 0) {
+#pragma unroll
+            for (int j = 0; j < n / 4; ++j) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(p) + j);
+                c[4 * j] = v.x; c[4 * j + 1] = v.y; c[4 * j + 2] = v.z; c[4 * j + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < n; ++j) c[j] = __ldg(p + j);
         }
     } else {
-        for (int k = 0; k < K; ++k) {
-            r = fmaf(load_attr(sh, base + 3 * k, dtype), Y[k], r);
-            g = fmaf(load_attr(sh, base + 3 * k + 1, dtype), Y[k], g);
-            b = fmaf(load_attr(sh, base + 3 * k + 2, dtype), Y[k], b);
+        const unsigned short *p = reinterpret_cast<const unsigned short *>(sh) + (int64_t)n * i;
+        if ((n % 8) == 0 && (reinterpret_cast<uintptr_t>(sh) & 15) == 0) {
+#pragma unroll
+            for (int j = 0; j < n / 8; ++j) {
+                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p) + j);
+                const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const unsigned short lo = (unsigned short)(w[q] & 0xffffu), hi = (unsigned short)(w[q] >> 16);
+                    if (dtype == GES_F16) {
+                        c[8 * j + 2 * q] = __half2float(__ushort_as_half(lo));
+                        c[8 * j + 2 * q + 1] = __half2float(__ushort_as_half(hi));
+                    } else {
+                        c[8 * j + 2 * q] = __bfloat162float(__ushort_as_bfloat16(lo));
+                        c[8 * j + 2 * q + 1] = __bfloat162float(__ushort_as_bfloat16(hi));
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < n; ++j) c[j] = load_attr(sh, (int64_t)n * i + j, dtype);
         }
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void sh_colour_k(const void *sh, int64_t i, int dtype, const float *Y, float *rgb,
+                                            float *raw)
+{
+    float c[3 * K];
+    load_sh_row<K>(sh, i, dtype, c);
+    float r = 0.5f, g = 0.5f, b = 0.5f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        r = fmaf(c[3 * k], Y[k], r);
+        g = fmaf(c[3 * k + 1], Y[k], g);
+        b = fmaf(c[3 * k + 2], Y[k], b);
     }
     raw[0] = r; raw[1] = g; raw[2] = b;
     rgb[0] = fmaxf(r, 0.f); rgb[1] = fmaxf(g, 0.f); rgb[2] = fmaxf(b, 0.f);
+}
+
+// Eq. 1: colour = max(0, 0.5 + sum_k SH_k Y_k(dir)) per channel, accumulated in
+// index order; also returns the unclamped value (its sign gates the gradient).
+__device__ __forceinline__ void sh_colour(const void *sh, int64_t i, int K, int dtype, const float *Y, float *rgb,
+                                          float *raw)
+{
+    switch (K) {
+    case 16: sh_colour_k<16>(sh, i, dtype, Y, rgb, raw); break;
+    case 9: sh_colour_k<9>(sh, i, dtype, Y, rgb, raw); break;
+    case 4: sh_colour_k<4>(sh, i, dtype, Y, rgb, raw); break;
+    default: sh_colour_k<1>(sh, i, dtype, Y, rgb, raw); break;
+    }
 }
 
 // Rotation of the normalised quaternion (w,x,y,z); columns are the local axes.
@@ -499,7 +566,7 @@ __device__ __forceinline__ void surfel_setup(const SceneView &S, const CamParams
     const int K = (S.deg + 1) * (S.deg + 1);
     float Y[16];
     sh_basis(K, o.dir[0], o.dir[1], o.dir[2], Y);
-    sh_colour(S.s_sh, (int64_t)3 * K * i, K, S.sh_dtype, Y, o.rgb, o.raw);
+    sh_colour(S.s_sh, i, K, S.sh_dtype, Y, o.rgb, o.raw);
     o.visible = true;
 }
 
@@ -597,7 +664,7 @@ __device__ __forceinline__ void gauss_setup(const SceneView &S, const CamParams 
     const int K = (S.deg + 1) * (S.deg + 1);
     float Y[16];
     sh_basis(K, o.dir[0], o.dir[1], o.dir[2], Y);
-    sh_colour(S.g_sh, (int64_t)3 * K * i, K, S.sh_dtype, Y, o.rgb, o.raw);
+    sh_colour(S.g_sh, i, K, S.sh_dtype, Y, o.rgb, o.raw);
     o.rec.r = o.rgb[0]; o.rec.g = o.rgb[1]; o.rec.b = o.rgb[2];
     o.visible = true;
 }
