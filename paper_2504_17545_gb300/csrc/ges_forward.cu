@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(256) k_colscan(ViewScratch X, int T, LocalBins
     }
 }
 
-__global__ void __launch_bounds__(kPrepThreads) k_fill_local(ViewScratch X, int T, int tiles_x, LocalBins B)
+__global__ void __launch_bounds__(kFillThreads) k_fill_local(ViewScratch X, int T, int tiles_x, LocalBins B)
 {
     extern __shared__ unsigned cur[];    // T cursors
     if (X.status[ST_FLAGS] & (FLAG_SOVF | FLAG_GOVF)) return;
@@ -183,14 +183,14 @@ __global__ void __launch_bounds__(kPrepThreads) k_fill_local(ViewScratch X, int 
     const bool surf = c < B.Ps;
     const int *off = surf ? X.s_off : X.g_off;
     const unsigned *brow = X.base + (size_t)c * T;
-    for (int t = threadIdx.x; t < T; t += kPrepThreads) cur[t] = (unsigned)off[t] + brow[t];
+    for (int t = threadIdx.x; t < T; t += kFillThreads) cur[t] = (unsigned)off[t] + brow[t];
     __syncthreads();
     const int64_t beg = (int64_t)(surf ? c : c - B.Ps) * (surf ? B.Rs : B.Rg);
     const int *seg = (surf ? X.s_vis : X.g_vis) + beg;
     const float4 *rec = surf ? X.s_rec : X.g_rec;
     int *list = surf ? X.s_list : X.g_list;
     const unsigned n = X.vcount[c];
-    for (unsigned k = threadIdx.x; k < n; k += kPrepThreads) {
+    for (unsigned k = threadIdx.x; k < n; k += kFillThreads) {
         const int id = seg[k];
         const float4 r3 = rec[4 * (int64_t)id + 3];
         const unsigned lo = __float_as_uint(r3.y), hi = __float_as_uint(r3.z);
@@ -307,15 +307,25 @@ __device__ __forceinline__ bool box_overlap(unsigned lo, unsigned hi, int wx0, i
 }
 
 constexpr int kChunk = kRasterThreads;   // records staged per CTA round
-constexpr int kStage = 5;                // float4 per staged record (4 used + 1 pad: conflict-free STS.128)
 
-__global__ void __launch_bounds__(kRasterThreads) k_raster(ViewScratch X, CamParams C, OptParams O,
+__device__ __forceinline__ void stage_rec(float4 (*st)[kChunk], const float4 *rec, int id, int slot)
+{
+    const float4 *rp = rec + 4 * (int64_t)id;
+    const float4 r0 = rp[0], r1 = rp[1], r2 = rp[2], r3 = rp[3];
+    st[0][slot] = r0; st[1][slot] = r1; st[2][slot] = r2; st[3][slot] = r3;
+}
+
+__global__ void __launch_bounds__(kRasterThreads, 5) k_raster(ViewScratch X, CamParams C, OptParams O,
                                                            float *__restrict__ out_rgb,
                                                            float *__restrict__ out_depth,
                                                            int32_t *__restrict__ out_id,
                                                            float *__restrict__ aux)
 {
-    __shared__ float4 stage[kChunk][kStage];
+    // records staged as structure-of-arrays (one float4 plane per 16-byte
+    // quarter): consecutive threads store consecutive 16 B, and a warp reading
+    // one record gets a broadcast
+    __shared__ float4 ss[4][kChunk];        // surfels
+    __shared__ float4 sgs[4][kChunk];       // Gaussians
     if (X.status[ST_FLAGS] & (FLAG_SOVF | FLAG_GOVF)) return;
     const int tile = blockIdx.x;
     const int tx = tile % C.tiles_x, ty = tile / C.tiles_x;
@@ -326,53 +336,68 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(ViewScratch X, CamPar
     const int px = wx0 + (int)(lane & 7), py = wy0 + (int)(lane >> 3);
     const bool in_img = px < C.W && py < C.H;
     const float u = px + 0.5f, v = py + 0.5f;
+    const bool do_s = O.mode != GES_MODE_GAUSSIANS_ONLY, do_g = O.mode != GES_MODE_SURFELS_ONLY;
+    const int s0 = do_s ? X.s_off[tile] : 0, s1 = do_s ? X.s_off[tile + 1] : 0;
+    const int g0 = do_g ? X.g_off[tile] : 0, g1 = do_g ? X.g_off[tile + 1] : 0;
+    const int t = threadIdx.x;
+
+    // first chunk of both lists together: one round trip, one barrier
+    if (s0 + t < s1) stage_rec(ss, X.s_rec, X.s_list[s0 + t], t);
+    if (g0 + t < g1) stage_rec(sgs, X.g_rec, X.g_list[g0 + t], t);
+    __syncthreads();
 
     // ---------------- pass 1: surfel z-buffer ----------------
+    // A warp skips a surfel whose bbox misses its 8x4 block, or whose largest
+    // 1/z over the disc (izmax) is below every 1/z its pixels already hold
+    // (it cannot win anywhere in the block).  Survivors are tested two at a
+    // time; the lexicographic (depth, id) min does not depend on the order.
     float best = in_img ? 0.f : INFINITY;   // 1/z of the nearest hit (0: none)
     int bid = 0x7fffffff;
-    if (O.mode != GES_MODE_GAUSSIANS_ONLY) {
-        const int s0 = X.s_off[tile], s1 = X.s_off[tile + 1];
-        float wmin = 0.f;   // smallest 'best' in the warp: a surfel whose 1/z never exceeds it cannot win
-        for (int base = s0; base < s1; base += kChunk) {
-            const int k = base + (int)threadIdx.x;
-            if (k < s1) {
-                const float4 *rp = X.s_rec + 4 * (int64_t)X.s_list[k];
-                const float4 r0 = rp[0], r1 = rp[1], r2 = rp[2], r3 = rp[3];
-                stage[threadIdx.x][0] = r0; stage[threadIdx.x][1] = r1;
-                stage[threadIdx.x][2] = r2; stage[threadIdx.x][3] = r3;
-            }
+    float wmin = 0.f;                        // smallest 'best' over the warp's pixels
+    for (int base = s0; base < s1; base += kChunk) {
+        if (base != s0) {
             __syncthreads();
-            const int n = min(kChunk, s1 - base);
-            if (wactive) {
-                for (int j0 = 0; j0 < n; j0 += 32) {
-                    const int j = j0 + (int)lane;
-                    bool keep = false;
-                    if (j < n) {
-                        const float4 r3 = stage[j][3];
-                        keep = box_overlap(__float_as_uint(r3.y), __float_as_uint(r3.z), wx0, wy0, wx1, wy1) &&
-                               stage[j][2].w >= wmin;
-                    }
-                    unsigned mask = __ballot_sync(0xffffffffu, keep);
-                    while (mask) {
-                        const int jj = j0 + __ffs(mask) - 1;
-                        mask &= mask - 1;
-                        const float4 r2 = stage[jj][2];
-                        if (r2.w < wmin) continue;                      // warp-uniform re-check
-                        const float4 r0 = stage[jj][0], r1 = stage[jj][1];
-                        const int id = __float_as_int(stage[jj][3].x);
-                        const float du = u - r0.x, dv = v - r0.y;
-                        const float iz = fmaf(r0.w, du, fmaf(r1.x, dv, r0.z));
-                        const float A = fmaf(r1.y, du, fmaf(r1.z, dv, r1.w));
-                        const float B = fmaf(r2.x, du, fmaf(r2.y, dv, r2.z));
-                        const float q = fmaf(A, A, fmaf(B, B, -iz * iz));
-                        const bool hit = q <= 0.f && iz < C.izn && (iz > best || (iz == best && id < bid));
-                        if (hit) { best = iz; bid = id; }
-                        if (__any_sync(0xffffffffu, hit))
-                            wmin = __uint_as_float(__reduce_min_sync(0xffffffffu, __float_as_uint(best)));
-                    }
+            if (base + t < s1) stage_rec(ss, X.s_rec, X.s_list[base + t], t);
+            __syncthreads();
+        }
+        const int n = min(kChunk, s1 - base);
+        if (wactive) {
+            for (int j0 = 0; j0 < n; j0 += 32) {
+                const int j = j0 + (int)lane;
+                bool keep = false;
+                if (j < n) {
+                    const float4 r3 = ss[3][j];
+                    keep = box_overlap(__float_as_uint(r3.y), __float_as_uint(r3.z), wx0, wy0, wx1, wy1) &&
+                           ss[2][j].w >= wmin;
+                }
+                unsigned mask = __ballot_sync(0xffffffffu, keep);
+                while (mask) {
+                    const int ja = j0 + __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    const bool two = mask != 0u;
+                    const int jb = two ? j0 + __ffs(mask) - 1 : ja;
+                    if (two) mask &= mask - 1;
+                    const float4 a2 = ss[2][ja], b2 = ss[2][jb];
+                    if (a2.w < wmin && b2.w < wmin) continue;       // warp-uniform re-check
+                    const float4 a0 = ss[0][ja], a1 = ss[1][ja], b0 = ss[0][jb], b1 = ss[1][jb];
+                    const int ida = __float_as_int(ss[3][ja].x), idb = __float_as_int(ss[3][jb].x);
+                    const float dua = u - a0.x, dva = v - a0.y, dub = u - b0.x, dvb = v - b0.y;
+                    const float iza = fmaf(a0.w, dua, fmaf(a1.x, dva, a0.z));
+                    const float izb = fmaf(b0.w, dub, fmaf(b1.x, dvb, b0.z));
+                    const float Aa = fmaf(a1.y, dua, fmaf(a1.z, dva, a1.w));
+                    const float Ab = fmaf(b1.y, dub, fmaf(b1.z, dvb, b1.w));
+                    const float Ba = fmaf(a2.x, dua, fmaf(a2.y, dva, a2.z));
+                    const float Bb = fmaf(b2.x, dub, fmaf(b2.y, dvb, b2.z));
+                    const float qa = fmaf(Aa, Aa, fmaf(Ba, Ba, -iza * iza));
+                    const float qb = fmaf(Ab, Ab, fmaf(Bb, Bb, -izb * izb));
+                    const bool ina = qa <= 0.f && iza < C.izn, inb = qb <= 0.f && izb < C.izn && two;
+                    bool hit = false;
+                    if (ina && (iza > best || (iza == best && ida < bid))) { best = iza; bid = ida; hit = true; }
+                    if (inb && (izb > best || (izb == best && idb < bid))) { best = izb; bid = idb; hit = true; }
+                    if (__any_sync(0xffffffffu, hit))
+                        wmin = __uint_as_float(__reduce_min_sync(0xffffffffu, __float_as_uint(best)));
                 }
             }
-            __syncthreads();
         }
     }
     const bool covered = bid != 0x7fffffff;
@@ -385,52 +410,45 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(ViewScratch X, CamPar
 
     // ---------------- pass 2: Gaussians (Eq. 2-4) ----------------
     long long acc_r = 0, acc_g = 0, acc_b = 0, acc_w = 0;
-    if (O.mode != GES_MODE_SURFELS_ONLY) {
-        const int g0 = X.g_off[tile], g1 = X.g_off[tile + 1];
-        // no Gaussian with key >= max over the warp's pixels of D_s can pass the depth test there
-        const float wmaxD = __uint_as_float(__reduce_max_sync(0xffffffffu, in_img ? __float_as_uint(Ds) : 0u));
-        const float amin32 = O.alpha_min * 4294967296.f;
-        for (int base = g0; base < g1; base += kChunk) {
-            const int k = base + (int)threadIdx.x;
-            if (k < g1) {
-                const float4 *rp = X.g_rec + 4 * (int64_t)X.g_list[k];
-                const float4 r0 = rp[0], r1 = rp[1], r2 = rp[2], r3 = rp[3];
-                stage[threadIdx.x][0] = r0; stage[threadIdx.x][1] = r1;
-                stage[threadIdx.x][2] = r2; stage[threadIdx.x][3] = r3;
-            }
+    // no Gaussian with key >= max over the warp's pixels of D_s can pass the depth test there
+    const float wmaxD = __uint_as_float(__reduce_max_sync(0xffffffffu, in_img ? __float_as_uint(Ds) : 0u));
+    const float amin32 = O.alpha_min * 4294967296.f;
+    for (int base = g0; base < g1; base += kChunk) {
+        if (base != g0) {
             __syncthreads();
-            const int n = min(kChunk, g1 - base);
-            if (wactive) {
-                for (int j0 = 0; j0 < n; j0 += 32) {
-                    const int j = j0 + (int)lane;
-                    bool keep = false;
-                    if (j < n) {
-                        const float4 r3 = stage[j][3];
-                        keep = box_overlap(__float_as_uint(r3.y), __float_as_uint(r3.z), wx0, wy0, wx1, wy1) &&
-                               stage[j][2].x < wmaxD;
-                    }
-                    unsigned mask = __ballot_sync(0xffffffffu, keep);
-                    while (mask) {
-                        const int jj = j0 + __ffs(mask) - 1;
-                        mask &= mask - 1;
-                        GaussRec g;
-                        *reinterpret_cast<float4 *>(&g.px) = stage[jj][0];
-                        *reinterpret_cast<float4 *>(&g.ca) = stage[jj][1];
-                        *reinterpret_cast<float4 *>(&g.key) = stage[jj][2];
-                        float e;
-                        const float a = gauss_alpha(g, u, v, e);
-                        // alpha * 2^32 is exact scaling: the clamp decision equals alpha >= alpha_min
-                        const float a32 = a * 4294967296.f;
-                        if (in_img && a32 >= amin32 && g.key < Ds) {
-                            acc_w += __float2ll_rn(a32);
-                            acc_r += __float2ll_rn(a32 * g.r);
-                            acc_g += __float2ll_rn(a32 * g.g);
-                            acc_b += __float2ll_rn(a32 * g.b);
-                        }
+            if (base + t < g1) stage_rec(sgs, X.g_rec, X.g_list[base + t], t);
+            __syncthreads();
+        }
+        const int n = min(kChunk, g1 - base);
+        if (wactive) {
+            for (int j0 = 0; j0 < n; j0 += 32) {
+                const int j = j0 + (int)lane;
+                bool keep = false;
+                if (j < n) {
+                    const float4 r3 = sgs[3][j];
+                    keep = box_overlap(__float_as_uint(r3.y), __float_as_uint(r3.z), wx0, wy0, wx1, wy1) &&
+                           sgs[2][j].x < wmaxD;
+                }
+                unsigned mask = __ballot_sync(0xffffffffu, keep);
+                while (mask) {
+                    const int jj = j0 + __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    GaussRec g;
+                    *reinterpret_cast<float4 *>(&g.px) = sgs[0][jj];
+                    *reinterpret_cast<float4 *>(&g.ca) = sgs[1][jj];
+                    *reinterpret_cast<float4 *>(&g.key) = sgs[2][jj];
+                    float e;
+                    const float a = gauss_alpha(g, u, v, e);
+                    // alpha * 2^32 is exact scaling: the clamp decision equals alpha >= alpha_min
+                    const float a32 = a * 4294967296.f;
+                    if (in_img && a32 >= amin32 && g.key < Ds) {
+                        acc_w += __float2ll_rn(a32);
+                        acc_r += __float2ll_rn(a32 * g.r);
+                        acc_g += __float2ll_rn(a32 * g.g);
+                        acc_b += __float2ll_rn(a32 * g.b);
                     }
                 }
             }
-            __syncthreads();
         }
     }
     if (!in_img) return;
@@ -497,7 +515,7 @@ cudaError_t launch_forward(const SceneView &S, const CamParams &C, const OptPara
     k_scan<<<2, 1024, 0, st>>>(X, T);
     if (ev) cudaEventRecord(ev[2], st);
     if (local) {
-        if (B.Ps + B.Pg > 0) k_fill_local<<<B.Ps + B.Pg, kPrepThreads, local_bins_smem(T, true), st>>>(X, T, C.tiles_x, B);
+        if (B.Ps + B.Pg > 0) k_fill_local<<<B.Ps + B.Pg, kFillThreads, local_bins_smem(T, true), st>>>(X, T, C.tiles_x, B);
     } else {
         k_fill_atomic<<<152 * 8, 256, 0, st>>>(X, C.tiles_x);
     }

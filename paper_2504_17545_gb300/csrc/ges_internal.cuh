@@ -81,6 +81,7 @@ struct LocalBins {
 };
 constexpr int kLocalMaxTiles = 32768;   // shared-memory cursors of the fill: 4 B per tile
 constexpr int kPrepThreads = 512;
+constexpr int kFillThreads = 1024;
 LocalBins plan_local_bins(int64_t N, int64_t M, int num_sms);
 size_t local_bins_smem(int T, bool fill);
 cudaError_t prepare_forward_kernels();   // once per device: large dynamic shared memory

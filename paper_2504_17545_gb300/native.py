@@ -92,7 +92,9 @@ _lock = threading.Lock()
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The in-tree build, or the library named by GES_LIBRARY (another build
+    of the same sources, e.g. with different compile options)."""
+    return os.environ.get("GES_LIBRARY") or _build.LIB
 
 
 def load(build_if_missing: bool = True):
@@ -101,11 +103,12 @@ def load(build_if_missing: bool = True):
     global _lib
     with _lock:
         if _lib is None:
-            if build_if_missing:
+            path = library_path()
+            if build_if_missing and path == _build.LIB:
                 _build.build()
-            if not os.path.exists(_build.LIB):
-                raise RuntimeError(f"CUDA library {_build.LIB} is missing; run paper_2504_17545_gb300.build.build()")
-            lib = C.CDLL(_build.LIB)
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library {path} is missing; run paper_2504_17545_gb300.build.build()")
+            lib = C.CDLL(path)
             for name, (res, args) in _SIGS.items():
                 fn = getattr(lib, name)
                 fn.restype = res
