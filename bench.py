@@ -88,6 +88,43 @@ class ClockSampler:
                 "reasons": reasons}
 
 
+# Per-unit work of the raster (plain FP32 ALU work): ~20 FP32 instructions per
+# (pixel, surfel) fragment test and ~12 + one exp per (pixel, Gaussian) term.
+OPS_PER_SURFEL_FRAGMENT = 20
+OPS_PER_GAUSS_TERM = 13
+
+
+def alu_peak():
+    """FP32 lane-instructions per second: 152 SMs x 128 FP32 lanes x the
+    maximum SM clock (MEASURED_PEAKS.json, else 2070 MHz)."""
+    mhz = 2070.0
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        mhz = float(json.load(open(p)).get("sm_max_mhz", mhz))
+    return 152 * 128 * mhz * 1e6
+
+
+def source_digest():
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2504_17545_gb300", "csrc", "*.cu*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu record, or None
+    when the kernel sources changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(kernel)
+    if not d or d.get("source_digest") != source_digest():
+        return None
+    return float(d["dram_bytes_per_launch"])
+
+
 def algorithmic_bytes(n_s, n_g, s_vis, g_vis, hw, attr_bytes=4, sh_bytes=4, deg=3):
     """Bytes one view must move: every position, the other attributes and SH
     of the visible primitives, and the RGB + depth outputs."""
@@ -139,6 +176,66 @@ def cpu_baseline_sample(scene, cams):
             "sample": f"{n} full 1080p orbit views (of 64), FP64, OpenMP over all host cores"}
 
 
+def _time(fn, iters, warm=2):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(iters):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / iters
+
+
+def train_step_extra(R, N, sg):
+    """Forward + backward on the training-step workload: 1600x1060, 500k
+    surfels + 500k Gaussians, FP32, L1 loss gradient against a target."""
+    import torch
+    scene, cams = sg.config_scene(3)
+    gs = R.GESScene.from_arrays(scene)
+    cam = cams[0]
+    fwd = R.render(gs, cam)
+    target = torch.rand_like(fwd["rgb"])
+    g = torch.sign(fwd["rgb"] - target) / fwd["rgb"].numel()
+    state = {}
+
+    def f():
+        state["fwd"] = R.render(gs, cam)
+
+    def fb():
+        out = R.render(gs, cam)
+        R.render_backward(gs, cam, out, g)
+
+    fwd_ms = _time(f, 10)
+    fb_ms = _time(fb, 10)
+    gs.close()
+    return {"workload": "1600x1060-500k-surfels-500k-gaussians-fp32", "fwd_ms_per_view": fwd_ms,
+            "fwd_bwd_ms_per_view": fb_ms, "bwd_ms_per_view": fb_ms - fwd_ms}
+
+
+def batched_extra(R, N, sg):
+    """16 views at 1264x832 over 2M surfels + 500k Gaussians: one batched call
+    with FP32, FP16 and BF16 attribute/SH storage, against the plain FP32
+    single-view path (one ges_render_ex call, and one synchronisation, per view)."""
+    import torch
+    scene, cams = sg.config_scene(2)
+    res = {"workload": "16x1264x832-2M-surfels-500k-gaussians"}
+    H, W = cams[0].height, cams[0].width
+    outs = [(torch.empty((3, H, W), device="cuda"), torch.empty((H, W), device="cuda")) for _ in cams]
+    for name, dt in (("fp32", torch.float32), ("fp16", torch.float16), ("bf16", torch.bfloat16)):
+        gs = R.GESScene.from_arrays(scene, attr_dtype=dt, sh_dtype=dt)
+        ms = _time(lambda: R.render_batch([gs], cams, outputs=outs), 5)
+        res[f"batched_{name}_views_per_s"] = len(cams) / (ms / 1e3)
+        if name == "fp32":
+            ms1 = _time(lambda: [R.render(gs, c, with_aux=False) for c in cams], 3)
+            res["single_view_fp32_views_per_s"] = len(cams) / (ms1 / 1e3)
+        gs.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -181,13 +278,17 @@ def main():
         N.ges_render_batch([gs.handle], cstructs, [0] * N_VIEWS, opts,
                            [o[0].data_ptr() for o in outputs], [o[1].data_ptr() for o in outputs])
 
-    # per-view visible counts (algorithmic bytes)
-    vis = []
-    for c in cams:
+    # per-view visible counts (algorithmic bytes) and exact fragment counts (ALU work)
+    vis, frags = [], []
+    for k, c in enumerate(cams):
         R.render(gs, c, with_aux=False)
         st = gs.stats()
         vis.append((st.visible_surfels, st.visible_gaussians))
+        if k % 8 == 0:
+            frags.append(N.ges_count_fragments(gs.handle, cstructs[k], opts))
     prep_b, frame_b = zip(*[algorithmic_bytes(scene.n_surfels, scene.n_gaussians, s, g, H * W) for s, g in vis])
+    sfrag = float(np.mean([f[0] for f in frags]))
+    gterm = float(np.mean([f[1] for f in frags]))
 
     for _ in range(args.warmup):
         step()
@@ -237,6 +338,10 @@ def main():
     e2e = {"value": N_VIEWS * e2e_steps * world / e2e_dt, "unit": "frames/s",
            "h2d_bytes_per_step": N_VIEWS * 88, "d2h_bytes_per_step": N_VIEWS * 4 * 4 * H * W}
 
+    extras = {}
+    if rank == 0:
+        extras["train_step"] = train_step_extra(R, N, sg)
+        extras["batched_precision"] = batched_extra(R, N, sg)
     if rank != 0:
         return
     # roofline of the dominant kernel (largest share of device time)
@@ -244,13 +349,20 @@ def main():
     top = names[0]
     top_ms, top_launches = prof[top]
     peak, peak_src = _peaks()
-    if top == "preprocess":
-        bytes_per_launch = float(np.mean(prep_b))
-        bound = "hbm"
+    sec = top_ms / top_launches / 1e3
+    if top == "raster":
+        ops = OPS_PER_SURFEL_FRAGMENT * sfrag + OPS_PER_GAUSS_TERM * gterm
+        roof = {"bound": "alu", "kernel": "k_raster", "achieved": ops / sec / 1e12, "peak": alu_peak() / 1e12,
+                "unit": "TFLOP/s", "frac": ops / sec / alu_peak(), "traffic": ncu_traffic("k_raster"),
+                "peak_source": "152 SMs x 128 FP32 lanes x max SM clock",
+                "units_per_launch": {"surfel_fragments": sfrag, "gauss_terms": gterm}}
     else:
-        bytes_per_launch = float(np.mean(frame_b)) - float(np.mean(prep_b))   # outputs the raster writes
-        bound = "hbm"
-    achieved = bytes_per_launch / (top_ms / top_launches / 1e3) / 1e9
+        bpl = float(np.mean(prep_b))
+        roof = {"bound": "hbm", "kernel": "k_prep_local", "achieved": bpl / sec / 1e9, "peak": peak,
+                "unit": "GB/s", "frac": bpl / sec / 1e9 / peak, "traffic": ncu_traffic("k_prep_local"),
+                "peak_source": peak_src}
+    prep_ms, prep_n = prof.get("preprocess", (0.0, 1))
+    prep_gbs = float(np.mean(prep_b)) / (prep_ms / prep_n / 1e3) / 1e9 if prep_ms > 0 else None
     frame_achieved = float(np.mean(frame_b)) * frames / world / (ms / 1e3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
@@ -259,14 +371,18 @@ def main():
         "config": {"workload": WORKLOAD, "resolution": f"{W}x{H}", "n_surfels": scene.n_surfels,
                    "n_gaussians": scene.n_gaussians, "views_per_step": N_VIEWS,
                    "l2": "inputs 332 MB > 129 MB L2, no flush", "parallelism": f"replicas{world}"},
-        "roofline": {"bound": bound, "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_source": peak_src},
-        "frame_roofline": {"algorithmic_bytes_per_frame": float(np.mean(frame_b)), "achieved": frame_achieved,
-                           "frac": frame_achieved / peak, "unit": "GB/s"},
+        "roofline": roof,
+        "frame_roofline": {"bound": "hbm", "algorithmic_bytes_per_frame": float(np.mean(frame_b)),
+                           "achieved": frame_achieved, "peak": peak, "frac": frame_achieved / peak, "unit": "GB/s"},
+        "preprocess_roofline": {"bound": "hbm", "kernel": "k_prep_local", "achieved": prep_gbs, "peak": peak,
+                                "frac": prep_gbs / peak if prep_gbs else None, "unit": "GB/s",
+                                "algorithmic_bytes_per_launch": float(np.mean(prep_b)),
+                                "traffic": ncu_traffic("k_prep_local")},
         "kernel_ms_per_frame": {k: prof[k][0] / prof[k][1] for k in names},
         "clocks": clocks,
         "e2e": e2e,
-        "gpu_launches": 4 * N_VIEWS * args.steps,
+        "gpu_launches": 5 * N_VIEWS * args.steps,
+        "extra": extras,
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline_sample(scene, cams)

@@ -226,6 +226,16 @@ GES_API ges_status ges_render_noalloc(const ges_scene_desc *desc, const ges_came
                                       const ges_render_opts *opts, float *out_rgb, float *out_depth,
                                       int32_t *out_surfel_id, float *aux, void *stream);
 
+/* Exact work counts of one view, for measurement: *surfel_fragments receives
+ * the number of (pixel, surfel) pairs whose fragment lies inside the surfel's
+ * opaque disc in front of the near plane -- the fragments any exact z-buffer
+ * must test in pass 1 (Sec. 3) -- and *gauss_terms the number of
+ * (pixel, Gaussian) pairs with alpha >= alpha_min, the terms of Eq. 2-3 before
+ * the depth test.  Runs the preprocess and binning of a render, then counts
+ * over the full tile lists without any culling.  Synchronises the stream. */
+GES_API ges_status ges_count_fragments(ges_scene *scene, const ges_camera *cam, const ges_render_opts *opts,
+                                       int64_t *surfel_fragments, int64_t *gauss_terms);
+
 /* Counters of the last render on this scene. */
 GES_API ges_status ges_get_stats(const ges_scene *scene, ges_stats *out);
 

@@ -5,7 +5,9 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 its Python binding) never does; the two share no code.
 """
 from .oracle import (DEFAULT_OPTS, build, load, render, backward, sh_basis, surfel_eval,
-                     surfel_info, gauss_info, id_validity, touching)
+                     surfel_info, gauss_info, id_validity, touching,
+                     count_fragments)
 
 __all__ = ["DEFAULT_OPTS", "build", "load", "render", "backward", "sh_basis", "surfel_eval",
-           "surfel_info", "gauss_info", "id_validity", "touching"]
+           "surfel_info", "gauss_info", "id_validity", "touching",
+           "count_fragments"]

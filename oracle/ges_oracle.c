@@ -568,6 +568,44 @@ int ora_render(const ora_scene *S, const ora_camera *c, const ora_opts *o, int c
     return ORA_OK;
 }
 
+/* Work counts: (pixel, surfel) fragments inside the opaque disc in front of
+   the near plane, and (pixel, Gaussian) pairs with alpha >= alpha_min. */
+int ora_count_fragments(const ora_scene *S, const ora_camera *c, const ora_opts *o, int64_t *n_surf,
+                        int64_t *n_gauss)
+{
+    if (!check_args(S, c, o)) return ORA_BAD_ARG;
+    prep_t P;
+    int st = prepare(S, c, o, 1, &P);
+    if (st != ORA_OK) { prep_free(&P); return st; }
+    const int W = c->width, H = c->height;
+    int64_t ns = 0, ng = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+:ns, ng)
+    for (int j = 0; j < H; ++j) {
+        for (int i = 0; i < W; ++i) {
+            const int64_t cell = (int64_t)(j / ORA_CELL) * P.rs.cx + i / ORA_CELL;
+            double d[3];
+            pixel_ray(c, i, j, d);
+            if (o->mode != 2)
+                for (int64_t t = P.rs.off[cell]; t < P.rs.off[cell + 1]; ++t) {
+                    const surf_t *sf = &P.sf[P.rs.idx[t]];
+                    if (!sf->valid || i < sf->x0 || i > sf->x1 || j < sf->y0 || j > sf->y1) continue;
+                    double z, rho;
+                    if (surfel_hit(sf, d, &z, &rho, NULL) && z > c->znear && rho <= o->surfel_r2) ++ns;
+                }
+            if (o->mode != 1)
+                for (int64_t t = P.rg.off[cell]; t < P.rg.off[cell + 1]; ++t) {
+                    const gauss_t *g = &P.gs[P.rg.idx[t]];
+                    if (!g->valid || i < g->x0 || i > g->x1 || j < g->y0 || j > g->y1) continue;
+                    if (gauss_alpha(g, i, j) >= o->alpha_min) ++ng;
+                }
+        }
+    }
+    prep_free(&P);
+    *n_surf = ns;
+    *n_gauss = ng;
+    return ORA_OK;
+}
+
 /* Evaluate surfel sid[k] at pixel (px[k], py[k]): hit depth, rho = a^2+b^2 and
    the cosine between the plane normal and the ray.  Returns per entry 1 on a
    hit, 0 if parallel or invalid. */

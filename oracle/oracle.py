@@ -76,6 +76,7 @@ def load():
         lib.ora_gauss_info.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_int64, C.c_void_p]
         lib.ora_touching.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_void_p, C.c_void_p, C.c_void_p]
         lib.ora_check_ids.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_void_p, C.c_void_p]
+        lib.ora_count_fragments.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_void_p, C.c_void_p]
         _lib = lib
     return _lib
 
@@ -208,3 +209,13 @@ def touching(scene, cam, flag, opts=None):
     _check(lib.ora_touching(C.byref(pin.s), C.byref(pin.c), C.byref(pin.o), f.ctypes.data, st_.ctypes.data,
                             gt_.ctypes.data), "touching")
     return st_.astype(bool), gt_.astype(bool)
+
+
+def count_fragments(scene, cam, opts=None):
+    """(surfel fragments inside their discs, Gaussian terms with alpha >= alpha_min)."""
+    lib = load()
+    pin = _Pinned(scene, cam, opts)
+    a, b = C.c_int64(), C.c_int64()
+    _check(lib.ora_count_fragments(C.byref(pin.s), C.byref(pin.c), C.byref(pin.o), C.addressof(a), C.addressof(b)),
+           "count_fragments")
+    return a.value, b.value

@@ -479,6 +479,36 @@ ges_status ges_render_batch(ges_scene *const *scenes, const ges_camera *cams, co
     return render_views(scenes, C.data(), scene_of_view, n_views, O, out_rgb, out_depth, nullptr, nullptr);
 }
 
+ges_status ges_count_fragments(ges_scene *s, const ges_camera *cam, const ges_render_opts *opts,
+                               int64_t *surfel_fragments, int64_t *gauss_terms)
+{
+    if (!s || !surfel_fragments || !gauss_terms) return fail(GES_ERR_INVALID_ARG, "NULL argument");
+    CamParams C;
+    OptParams O;
+    ges_status r = make_cam(cam, C);
+    if (r != GES_OK) return r;
+    if ((r = make_opts(opts, O)) != GES_OK) return r;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        if ((r = ensure_scratch(s, (int64_t)C.tiles_x * C.tiles_y, 1, s->stream)) != GES_OK) return r;
+        ViewScratch X = scratch_of(s, 0);
+        GES_CUDA(cudaMemsetAsync(X.status, 0, ST_WORDS * 4, s->stream));
+        cudaError_t e = launch_count(s->view, C, O, X, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+        GES_CUDA(cudaMemcpyAsync(s->status_host, X.status, ST_WORDS * 4, cudaMemcpyDeviceToHost, s->stream));
+        GES_CUDA(cudaStreamSynchronize(s->stream));
+        const unsigned *w = s->status_host;
+        if (w[ST_FLAGS] & FLAG_BADQ) return fail(GES_ERR_INVALID_ARG, "a rotation quaternion has zero norm or is not finite");
+        bool overflow = false;
+        if (w[ST_FLAGS] & FLAG_SOVF) { s->s_cap = std::max<int64_t>(s->s_cap * 2, (int64_t)(w[ST_SPAIRS] * 1.25) + 1024); overflow = true; }
+        if (w[ST_FLAGS] & FLAG_GOVF) { s->g_cap = std::max<int64_t>(s->g_cap * 2, (int64_t)(w[ST_GPAIRS] * 1.25) + 1024); overflow = true; }
+        if (overflow) continue;
+        *surfel_fragments = w[ST_SFRAG];
+        *gauss_terms = w[ST_GFRAG];
+        return GES_OK;
+    }
+    return fail(GES_ERR_INTERNAL, "tile lists kept overflowing after growing them");
+}
+
 ges_status ges_get_stats(const ges_scene *s, ges_stats *out)
 {
     if (!s || !out) return fail(GES_ERR_INVALID_ARG, "NULL argument");

@@ -488,9 +488,10 @@ cudaError_t prepare_forward_kernels()
                                 (int)local_bins_smem(kLocalMaxTiles, true));
 }
 
-cudaError_t launch_forward(const SceneView &S, const CamParams &C, const OptParams &O, const ViewScratch &X,
-                           float *out_rgb, float *out_depth, int32_t *out_id, float *aux, cudaStream_t st,
-                           cudaEvent_t *ev)
+namespace {
+// preprocess + binning of one view (everything before the raster)
+cudaError_t launch_binning(const SceneView &S, const CamParams &C, const OptParams &O, const ViewScratch &X,
+                           cudaStream_t st, cudaEvent_t *ev)
 {
     const int T = C.tiles_x * C.tiles_y;
     SceneView Sv = S;
@@ -520,8 +521,86 @@ cudaError_t launch_forward(const SceneView &S, const CamParams &C, const OptPara
         k_fill_atomic<<<152 * 8, 256, 0, st>>>(X, C.tiles_x);
     }
     if (ev) cudaEventRecord(ev[3], st);
-    k_raster<<<T, kRasterThreads, 0, st>>>(X, C, O, out_rgb, out_depth, out_id, aux);
+    return cudaGetLastError();
+}
+
+// Exact work counts of one view: every (pixel, surfel) fragment inside the
+// opaque disc in front of the near plane, and every (pixel, Gaussian) pair
+// with alpha >= alpha_min, over the full tile lists (no culling).
+__global__ void __launch_bounds__(256) k_count(ViewScratch X, CamParams C, OptParams O)
+{
+    __shared__ float4 st[4][256];
+    __shared__ unsigned red[2][8];
+    if (X.status[ST_FLAGS] & (FLAG_SOVF | FLAG_GOVF)) return;
+    const int tile = blockIdx.x, t = threadIdx.x;
+    const int tx = tile % C.tiles_x, ty = tile / C.tiles_x;
+    const int px = tx * kTile + (t & 15), py = ty * kTile + (t >> 4);
+    const bool in_img = px < C.W && py < C.H;
+    const float u = px + 0.5f, v = py + 0.5f;
+    unsigned ns = 0, ng = 0;
+    for (int kind = 0; kind < 2; ++kind) {
+        if (kind == 0 && O.mode == GES_MODE_GAUSSIANS_ONLY) continue;
+        if (kind == 1 && O.mode == GES_MODE_SURFELS_ONLY) continue;
+        const int *off = kind == 0 ? X.s_off : X.g_off;
+        const int *list = kind == 0 ? X.s_list : X.g_list;
+        const float4 *rec = kind == 0 ? X.s_rec : X.g_rec;
+        const int a = off[tile], b = off[tile + 1];
+        for (int base = a; base < b; base += 256) {
+            __syncthreads();
+            if (base + t < b) stage_rec(st, rec, list[base + t], t);
+            __syncthreads();
+            const int n = min(256, b - base);
+            if (!in_img) continue;
+            for (int j = 0; j < n; ++j) {
+                if (kind == 0) {
+                    const float4 r0 = st[0][j], r1 = st[1][j], r2 = st[2][j];
+                    const float du = u - r0.x, dv = v - r0.y;
+                    const float iz = fmaf(r0.w, du, fmaf(r1.x, dv, r0.z));
+                    const float A = fmaf(r1.y, du, fmaf(r1.z, dv, r1.w));
+                    const float B = fmaf(r2.x, du, fmaf(r2.y, dv, r2.z));
+                    ns += (fmaf(A, A, fmaf(B, B, -iz * iz)) <= 0.f && iz > 0.f && iz < C.izn) ? 1u : 0u;
+                } else {
+                    GaussRec g;
+                    *reinterpret_cast<float4 *>(&g.px) = st[0][j];
+                    *reinterpret_cast<float4 *>(&g.ca) = st[1][j];
+                    float e;
+                    ng += gauss_alpha(g, u, v, e) >= O.alpha_min ? 1u : 0u;
+                }
+            }
+        }
+    }
+    for (int d = 16; d >= 1; d >>= 1) {
+        ns += __shfl_xor_sync(0xffffffffu, ns, d);
+        ng += __shfl_xor_sync(0xffffffffu, ng, d);
+    }
+    if ((t & 31) == 0) { red[0][t >> 5] = ns; red[1][t >> 5] = ng; }
+    __syncthreads();
+    if (t == 0) {
+        unsigned a = 0, b = 0;
+        for (int w = 0; w < 8; ++w) { a += red[0][w]; b += red[1][w]; }
+        atomicAdd(X.status + ST_SFRAG, a);
+        atomicAdd(X.status + ST_GFRAG, b);
+    }
+}
+}  // namespace
+
+cudaError_t launch_forward(const SceneView &S, const CamParams &C, const OptParams &O, const ViewScratch &X,
+                           float *out_rgb, float *out_depth, int32_t *out_id, float *aux, cudaStream_t st,
+                           cudaEvent_t *ev)
+{
+    cudaError_t e = launch_binning(S, C, O, X, st, ev);
+    if (e != cudaSuccess) return e;
+    k_raster<<<C.tiles_x * C.tiles_y, kRasterThreads, 0, st>>>(X, C, O, out_rgb, out_depth, out_id, aux);
     if (ev) cudaEventRecord(ev[4], st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count(const SceneView &S, const CamParams &C, const OptParams &O, const ViewScratch &X,
+                         cudaStream_t st)
+{
+    cudaError_t e = launch_binning(S, C, O, X, st, nullptr);
+    if (e != cudaSuccess) return e;
+    k_count<<<C.tiles_x * C.tiles_y, 256, 0, st>>>(X, C, O);
     return cudaGetLastError();
 }
 

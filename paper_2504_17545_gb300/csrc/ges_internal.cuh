@@ -26,6 +26,8 @@ enum : int {
     ST_GVIS = 2,          // visible Gaussians
     ST_SPAIRS = 3,        // surfel tile pairs
     ST_GPAIRS = 4,        // Gaussian tile pairs
+    ST_SFRAG = 5,         // surfel fragments inside their discs (work count)
+    ST_GFRAG = 6,         // Gaussian pixel terms with alpha >= alpha_min (work count)
     ST_WORDS = 16,
 };
 enum : unsigned { FLAG_SOVF = 1u, FLAG_GOVF = 2u, FLAG_BADQ = 4u };
@@ -92,6 +94,9 @@ cudaError_t prepare_forward_kernels();   // once per device: large dynamic share
 cudaError_t launch_forward(const SceneView &S, const CamParams &C, const OptParams &O, const ViewScratch &X,
                            float *out_rgb, float *out_depth, int32_t *out_id, float *aux, cudaStream_t st,
                            cudaEvent_t *ev /* 5 events or nullptr */);
+
+cudaError_t launch_count(const SceneView &S, const CamParams &C, const OptParams &O, const ViewScratch &X,
+                         cudaStream_t st);
 
 cudaError_t launch_backward(const SceneView &S, const CamParams &C, const OptParams &O, const float *dL_drgb,
                             const float *out_rgb, const float *out_depth, const int32_t *surfel_id,

@@ -80,6 +80,8 @@ _SIGS = {
                                    _P(ges_render_opts), _P(C.c_void_p), _P(C.c_void_p)]),
     "ges_render_noalloc": (C.c_int, [_P(ges_scene_desc), _P(ges_camera), _P(ges_render_opts), C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ges_count_fragments": (C.c_int, [C.c_void_p, _P(ges_camera), _P(ges_render_opts), _P(C.c_int64),
+                                      _P(C.c_int64)]),
     "ges_get_stats": (C.c_int, [C.c_void_p, _P(ges_stats)]),
     "ges_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
     "ges_get_profile": (C.c_int, [C.c_void_p, _P(ges_profile)]),
@@ -194,3 +196,10 @@ def ges_last_error_message() -> str:
 
 def ges_version() -> int:
     return int(load().ges_version())
+
+
+def ges_count_fragments(scene, cam: ges_camera, opts):
+    a, b = C.c_int64(), C.c_int64()
+    _check(load().ges_count_fragments(scene, C.byref(cam), C.byref(opts) if opts is not None else None,
+                                      C.byref(a), C.byref(b)))
+    return a.value, b.value

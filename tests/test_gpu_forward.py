@@ -191,3 +191,38 @@ def test_stats_count_visible_primitives(R):
     assert 0 < st.visible_surfels <= scene.n_surfels and 0 < st.visible_gaussians <= scene.n_gaussians
     assert st.surfel_tile_pairs >= st.visible_surfels and st.tiles_x == 8 and st.tiles_y == 8
     gs.close()
+
+
+def test_fragment_counts_match_oracle(R):
+    from paper_2504_17545_gb300 import native as N
+    small = sg.config_scene(0)
+    big = sg.config_scene(1)
+    for scene, cam in [(small[0], small[1][0]), (big[0], big[1][16])]:
+        gs = R.GESScene.from_arrays(scene)
+        ns, ng = N.ges_count_fragments(gs.handle, R.camera_struct(cam), R.opts_struct(None))
+        os_, og = oracle.count_fragments(scene, cam)
+        # rim and cut-off fragments decided in FP32 vs FP64 may differ by a few
+        assert abs(ns - os_) <= max(3, 1e-4 * os_) and abs(ng - og) <= max(3, 1e-4 * og), (ns, os_, ng, og)
+        gs.close()
+
+
+@pytest.mark.parametrize("dtype", ["float16", "bfloat16"])
+def test_batched_workload_reduced_precision_views(R, dtype):
+    """The batched workload (2M surfels + 500k Gaussians, 1264x832), FP16/BF16
+    storage rendered in one batched call; views 0 and 8 against the oracle fed
+    the same dequantised values."""
+    torch = pytest.importorskip("torch")
+    dt = getattr(torch, dtype)
+    scene, cams = sg.config_scene(2)
+    gs = R.GESScene.from_arrays(scene, attr_dtype=dt, sh_dtype=dt)
+    outs = R.render_batch([gs], cams)
+    deq = scene.subset()
+    for k in ("s_rot", "s_scale", "g_rot", "g_scale", "g_opac", "s_sh", "g_sh"):
+        setattr(deq, k, torch.as_tensor(getattr(scene, k)).to(dt).float().numpy())
+    for v in (0, 8):
+        single = R.render(gs, cams[v])
+        assert (single["rgb"] == outs[v][0]).all() and (single["depth"] == outs[v][1]).all()
+        ref = oracle.render(deq, cams[v])
+        res = compare(deq, cams[v], single, ref)
+        _assert(res)
+    gs.close()

@@ -561,3 +561,18 @@ def test_id_check_tie_and_runner_up(oracle_lib):
     both = ref["id"] == 0
     assert _raw_check(oracle_lib, sc, cam, np.where(both, 1, ref["id"]))[both].all()
     assert not _raw_check(oracle_lib, sc, cam, np.where(both, 2, ref["id"]))[both].any()
+
+
+def test_fragment_counts_closed_form(oracle_lib):
+    """A lone fronto-parallel disc covers exactly the closed-form pixel set; a
+    lone on-axis Gaussian has exactly its closed-form 1/255 footprint."""
+    cam = ident_cam(64, 64, 50.0)
+    z0, s = 2.0, 0.1
+    ns, ng = oracle_lib.count_fragments(_disc_scene(z0, s), cam)
+    dx, dy = pixel_dirs(cam)
+    assert ns == int(((dx ** 2 + dy ** 2) * (z0 / s) ** 2 <= oracle_lib.DEFAULT_OPTS["surfel_r2"]).sum()) and ng == 0
+    cam = ident_cam(65, 65, 40.0, cx=32.5, cy=32.5)
+    ns, ng = oracle_lib.count_fragments(_one_gaussian(2.0, 0.05, 0.7), cam)
+    var = (40.0 * 0.05 / 2.0) ** 2 + 0.3
+    dx, dy = np.meshgrid(np.arange(65) + 0.5 - 32.5, np.arange(65) + 0.5 - 32.5)
+    assert ns == 0 and ng == int((0.7 * np.exp(-0.5 * (dx ** 2 + dy ** 2) / var) >= 1 / 255).sum())
