@@ -236,6 +236,57 @@ GES_API ges_status ges_render_noalloc(const ges_scene_desc *desc, const ges_came
 GES_API ges_status ges_count_fragments(ges_scene *scene, const ges_camera *cam, const ges_render_opts *opts,
                                        int64_t *surfel_fragments, int64_t *gauss_terms);
 
+/* A batch: a fixed set of views (each a camera on one of several scenes,
+ * uneven sizes allowed) rendered by one CUDA graph.  Every phase of the
+ * render -- preprocess, binning, fill, raster -- is a single launch over all
+ * views; the raster is persistent and hands out (view, tile) work items, so
+ * small and large views balance across the GPU.  Per-view semantics are
+ * exactly those of ges_render_ex.
+ *
+ * ges_batch_create renders every view once through the scene's own path to
+ * size the tile lists (x1.5 headroom), allocates the batch's own scratch,
+ * then autotunes the primitives per preprocess CTA and the persistent raster
+ * grid by timing each candidate graph, and keeps the fastest.  Pointers
+ * (scenes' arrays, outputs) are baked into the graph and must stay valid
+ * until ges_batch_destroy.  Images must have at most 32768 tiles of 16x16
+ * (otherwise GES_ERR_UNSUPPORTED; ges_render_batch has no such limit).
+ * out_depth may be NULL (no depth output) or have NULL entries. */
+typedef struct ges_batch ges_batch;
+typedef struct {
+    int32_t n_views;
+    int32_t prims_per_cta;         /* chosen preprocess range per CTA */
+    int32_t raster_ctas_per_sm;    /* chosen persistent raster occupancy */
+    int32_t candidates;            /* configurations timed by the autotuner */
+    double tuned_ms;               /* best measured time of one launch */
+} ges_batch_info;
+
+GES_API ges_status ges_batch_create(ges_scene *const *scenes, const ges_camera *cams, const int32_t *scene_of_view,
+                                    int32_t n_views, const ges_render_opts *opts, float *const *out_rgb,
+                                    float *const *out_depth, ges_batch **out);
+
+/* Change the camera of one view for the following launches; the image size
+ * must stay the one given at creation.  Call it when no launch of this batch
+ * is in flight (after ges_batch_sync). */
+GES_API ges_status ges_batch_set_camera(ges_batch *batch, int32_t view, const ges_camera *cam);
+
+/* Enqueue one replay of the batch's graph on `stream` (cudaStream_t). */
+GES_API ges_status ges_batch_launch(ges_batch *batch, void *stream);
+
+/* Wait for the last launch and check every view's status word: tile lists
+ * too small for a changed camera -> GES_ERR_CAPACITY (recreate the batch);
+ * zero-norm quaternion -> GES_ERR_INVALID_ARG. */
+GES_API ges_status ges_batch_sync(ges_batch *batch);
+
+GES_API ges_status ges_batch_get_info(const ges_batch *batch, ges_batch_info *out);
+
+/* Device time per phase (preprocess, scan, fill, raster) summed over the
+ * launches waited for by ges_batch_sync (CUDA-event nodes inside the graph
+ * time the most recent launch at each sync); reset != 0 clears the sums. */
+GES_API ges_status ges_batch_get_profile(ges_batch *batch, ges_profile *out, int32_t reset);
+
+/* Release the batch (waits for its last launch).  NULL is ignored. */
+GES_API ges_status ges_batch_destroy(ges_batch *batch);
+
 /* Counters of the last render on this scene. */
 GES_API ges_status ges_get_stats(const ges_scene *scene, ges_stats *out);
 

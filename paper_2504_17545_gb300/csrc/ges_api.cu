@@ -539,6 +539,326 @@ int32_t ges_version(void) { return 1; }
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// ges_batch: every phase one launch over all views, captured in a CUDA graph
+
+struct ges_batch {
+    int n = 0;
+    int device = 0;
+    OptParams O{};
+    std::vector<BatchView> views;          // host copy of the table (built per candidate)
+    std::vector<int64_t> s_cap, g_cap;
+    BatchView *h_table = nullptr;          // pinned: copied to the device by the graph
+    BatchView *d_table = nullptr;
+    unsigned *d_status = nullptr;          // n * ST_WORDS + work counter
+    unsigned *h_status = nullptr;          // pinned
+    void *arena = nullptr;                 // all per-view scratch
+    cudaStream_t stream = nullptr;         // capture / tuning stream
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;
+    cudaEvent_t phase[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // event nodes in the graph
+    ges_batch_info info{};
+    ges_profile profile{};
+};
+
+namespace {
+
+void batch_release(ges_batch *b)
+{
+    if (b->done) cudaEventSynchronize(b->done);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->done) cudaEventDestroy(b->done);
+    for (cudaEvent_t e : b->phase)
+        if (e) cudaEventDestroy(e);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    if (b->arena) cudaFree(b->arena);
+    if (b->d_table) cudaFree(b->d_table);
+    if (b->d_status) cudaFree(b->d_status);
+    if (b->h_table) cudaFreeHost(b->h_table);
+    if (b->h_status) cudaFreeHost(b->h_status);
+    delete b;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Lay every view's scratch out in the arena for a given primitives-per-CTA
+// (returns the bytes needed; with base == nullptr only sizes are computed).
+size_t batch_layout(ges_batch *b, const std::vector<SceneView> &S, const std::vector<CamParams> &C,
+                    int64_t prims_per_cta, unsigned char *base)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) { unsigned char *p = base ? base + off : nullptr; off = align256(off + bytes); return p; };
+    int prep_base = 0, tile_base = 0, col_base = 0;
+    for (int v = 0; v < b->n; ++v) {
+        BatchView &bv = b->views[v];
+        const int64_t N = std::max<int64_t>(S[v].N, 1), M = std::max<int64_t>(S[v].M, 1);
+        const int T = C[v].tiles_x * C[v].tiles_y;
+        const LocalBins B = plan_local_bins_per_cta(S[v].N, S[v].M, prims_per_cta);
+        const int P = std::max(B.Ps + B.Pg, 1);
+        bv.S = S[v];
+        bv.C = C[v];
+        bv.B = B;
+        bv.T = T;
+        bv.tile_base = tile_base;
+        bv.prep_base = prep_base;
+        bv.colscan_base = col_base;
+        tile_base += T;
+        prep_base += B.Ps + B.Pg;
+        col_base += (T + 31) / 32;
+        ViewScratch &X = bv.X;
+        X.s_rec = (float4 *)take(N * 64);
+        X.s_rgb = (float4 *)take(N * 16);
+        X.g_rec = (float4 *)take(M * 64);
+        X.s_vis = (int *)take(N * 4);
+        X.g_vis = (int *)take(M * 4);
+        X.s_cnt = (int *)take((T + 1) * 4);
+        X.g_cnt = (int *)take((T + 1) * 4);
+        X.s_off = (int *)take((T + 1) * 4);
+        X.g_off = (int *)take((T + 1) * 4);
+        X.s_cur = (int *)take((T + 1) * 4);
+        X.g_cur = (int *)take((T + 1) * 4);
+        X.s_cap = b->s_cap[v];
+        X.g_cap = b->g_cap[v];
+        X.s_list = (int *)take(b->s_cap[v] * 4);
+        X.g_list = (int *)take(b->g_cap[v] * 4);
+        X.hist = (unsigned *)take((size_t)P * ((T + 1) / 2) * 4);
+        X.base = (unsigned *)take((size_t)P * T * 4);
+        X.vcount = (unsigned *)take((size_t)P * 4);
+        X.status = b->d_status + (size_t)v * ST_WORDS;
+    }
+    return off;
+}
+
+}  // namespace
+
+extern "C" {
+
+ges_status ges_batch_create(ges_scene *const *scenes, const ges_camera *cams, const int32_t *scene_of_view,
+                            int32_t n_views, const ges_render_opts *opts, float *const *out_rgb,
+                            float *const *out_depth, ges_batch **out)
+{
+    if (!out) return fail(GES_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!scenes || !cams || !scene_of_view || !out_rgb) return fail(GES_ERR_INVALID_ARG, "NULL batch argument");
+    if (n_views <= 0) return fail(GES_ERR_INVALID_ARG, "n_views must be positive");
+    OptParams O;
+    ges_status r = make_opts(opts, O);
+    if (r != GES_OK) return r;
+    std::vector<SceneView> S(n_views);
+    std::vector<CamParams> C(n_views);
+    for (int v = 0; v < n_views; ++v) {
+        if (scene_of_view[v] < 0 || !scenes[scene_of_view[v]])
+            return fail(GES_ERR_INVALID_ARG, "view %d has no scene", v);
+        if (!out_rgb[v]) return fail(GES_ERR_INVALID_ARG, "out_rgb[%d] is NULL", v);
+        if ((r = make_cam(cams + v, C[v])) != GES_OK) return r;
+        if (C[v].tiles_x * C[v].tiles_y > kLocalMaxTiles)
+            return fail(GES_ERR_UNSUPPORTED, "view %d: %dx%d has more than %d tiles", v, C[v].W, C[v].H,
+                        kLocalMaxTiles);
+        S[v] = scenes[scene_of_view[v]]->view;
+        if (O.mode == GES_MODE_GAUSSIANS_ONLY) S[v].N = 0;
+        if (O.mode == GES_MODE_SURFELS_ONLY) S[v].M = 0;
+    }
+    ges_batch *b = new (std::nothrow) ges_batch();
+    if (!b) return fail(GES_ERR_OOM, "host allocation failed");
+    b->n = n_views;
+    b->O = O;
+    b->views.resize(n_views);
+    b->s_cap.resize(n_views);
+    b->g_cap.resize(n_views);
+    cudaError_t e;
+#define BATCH_CUDA(call)                                              \
+    do {                                                              \
+        if ((e = (call)) != cudaSuccess) {                            \
+            batch_release(b);                                         \
+            return cuda_fail(e, #call);                               \
+        }                                                             \
+    } while (0)
+    BATCH_CUDA(cudaGetDevice(&b->device));
+    // size the tile lists from one render of every view (scene's own path)
+    for (int v = 0; v < n_views; ++v) {
+        ges_scene *sc = scenes[scene_of_view[v]];
+        r = ges_render_ex(sc, cams + v, opts, out_rgb[v], out_depth ? out_depth[v] : nullptr, nullptr, nullptr);
+        if (r != GES_OK) {
+            batch_release(b);
+            return r;
+        }
+        b->s_cap[v] = (int64_t)(sc->stats.surfel_tile_pairs * 1.5) + 65536;
+        b->g_cap[v] = (int64_t)(sc->stats.gauss_tile_pairs * 1.5) + 65536;
+    }
+    BATCH_CUDA(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+    BATCH_CUDA(cudaEventCreate(&b->done));
+    for (cudaEvent_t &ev : b->phase) BATCH_CUDA(cudaEventCreate(&ev));
+    const size_t status_words = (size_t)n_views * ST_WORDS + 16;
+    BATCH_CUDA(cudaMalloc(&b->d_status, status_words * 4));
+    BATCH_CUDA(cudaMallocHost(&b->h_status, status_words * 4));
+    BATCH_CUDA(cudaMalloc(&b->d_table, sizeof(BatchView) * n_views));
+    BATCH_CUDA(cudaMallocHost(&b->h_table, sizeof(BatchView) * n_views));
+    for (int v = 0; v < n_views; ++v) {
+        b->views[v].rgb = out_rgb[v];
+        b->views[v].depth = out_depth ? out_depth[v] : nullptr;
+    }
+    // arena sized for the smallest primitives-per-CTA tried (most histogram rows)
+    const int64_t kR[] = {4096, 8192, 16384, 32768, 60000};
+    const size_t bytes = batch_layout(b, S, C, kR[0], nullptr);
+    BATCH_CUDA(cudaMalloc(&b->arena, bytes));
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+
+    // autotune: capture a graph per candidate, time it, keep the fastest
+    float best_ms = 1e30f;
+    int cand = 0;
+    for (int64_t R : kR) {
+        for (int per_sm : {4, 5}) {
+            batch_layout(b, S, C, R, (unsigned char *)b->arena);
+            BatchPlan P{n_views, 0, 0, 0, 0, sms * per_sm};
+            for (int v = 0; v < n_views; ++v) {
+                P.total_tiles += b->views[v].T;
+                P.total_prep += b->views[v].B.Ps + b->views[v].B.Pg;
+                P.total_colscan += (b->views[v].T + 31) / 32;
+                P.max_T = std::max(P.max_T, b->views[v].T);
+            }
+            std::memcpy(b->h_table, b->views.data(), sizeof(BatchView) * n_views);
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ex = nullptr;
+            BATCH_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            cudaMemcpyAsync(b->d_table, b->h_table, sizeof(BatchView) * n_views, cudaMemcpyHostToDevice, b->stream);
+            cudaMemsetAsync(b->d_status, 0, status_words * 4, b->stream);
+            launch_batch(b->d_table, P, O, b->d_status + (size_t)n_views * ST_WORDS, b->stream, b->phase);
+            cudaMemcpyAsync(b->h_status, b->d_status, status_words * 4, cudaMemcpyDeviceToHost, b->stream);
+            BATCH_CUDA(cudaStreamEndCapture(b->stream, &g));
+            e = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                batch_release(b);
+                return cuda_fail(e, "cudaGraphInstantiate");
+            }
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            cudaGraphLaunch(ex, b->stream);
+            cudaEventRecord(e0, b->stream);
+            for (int k = 0; k < 3; ++k) cudaGraphLaunch(ex, b->stream);
+            cudaEventRecord(e1, b->stream);
+            e = cudaStreamSynchronize(b->stream);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (e != cudaSuccess) {
+                cudaGraphExecDestroy(ex);
+                batch_release(b);
+                return cuda_fail(e, "batch launch");
+            }
+            ++cand;
+            ms /= 3.f;
+            if (ms < best_ms) {
+                best_ms = ms;
+                if (b->exec) cudaGraphExecDestroy(b->exec);
+                b->exec = ex;
+                b->info.prims_per_cta = (int32_t)R;
+                b->info.raster_ctas_per_sm = per_sm;
+            } else {
+                cudaGraphExecDestroy(ex);
+            }
+        }
+    }
+    // the table the chosen graph reads: rebuild it for that candidate
+    batch_layout(b, S, C, b->info.prims_per_cta, (unsigned char *)b->arena);
+    std::memcpy(b->h_table, b->views.data(), sizeof(BatchView) * n_views);
+    b->info.n_views = n_views;
+    b->info.candidates = cand;
+    b->info.tuned_ms = best_ms;
+#undef BATCH_CUDA
+    // one checked launch with the chosen configuration
+    cudaGraphLaunch(b->exec, b->stream);
+    cudaEventRecord(b->done, b->stream);
+    *out = b;
+    r = ges_batch_sync(b);
+    std::memset(&b->profile, 0, sizeof b->profile);
+    if (r != GES_OK) {
+        batch_release(b);
+        *out = nullptr;
+    }
+    return r;
+}
+
+ges_status ges_batch_set_camera(ges_batch *b, int32_t view, const ges_camera *cam)
+{
+    if (!b) return fail(GES_ERR_INVALID_ARG, "batch is NULL");
+    if (view < 0 || view >= b->n) return fail(GES_ERR_INVALID_ARG, "view %d out of range", view);
+    CamParams C;
+    ges_status r = make_cam(cam, C);
+    if (r != GES_OK) return r;
+    if (C.W != b->views[view].C.W || C.H != b->views[view].C.H)
+        return fail(GES_ERR_INVALID_ARG, "view %d: image size must stay %dx%d", view, b->views[view].C.W,
+                    b->views[view].C.H);
+    b->views[view].C = C;
+    b->h_table[view].C = C;
+    return GES_OK;
+}
+
+ges_status ges_batch_launch(ges_batch *b, void *stream)
+{
+    if (!b) return fail(GES_ERR_INVALID_ARG, "batch is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    GES_CUDA(cudaGraphLaunch(b->exec, st));
+    GES_CUDA(cudaEventRecord(b->done, st));
+    return GES_OK;
+}
+
+ges_status ges_batch_sync(ges_batch *b)
+{
+    if (!b) return fail(GES_ERR_INVALID_ARG, "batch is NULL");
+    GES_CUDA(cudaEventSynchronize(b->done));
+    // per-phase device time of the last launch (graph event nodes)
+    static const char *names[4] = {"preprocess", "scan", "fill", "raster"};
+    for (int k = 0; k < 4; ++k) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, b->phase[k], b->phase[k + 1]) != cudaSuccess) continue;
+        int i = -1;
+        for (int j = 0; j < b->profile.n; ++j)
+            if (std::strncmp(b->profile.names[j], names[k], 23) == 0) i = j;
+        if (i < 0 && b->profile.n < GES_PROFILE_SLOTS) {
+            i = b->profile.n++;
+            std::strncpy(b->profile.names[i], names[k], 23);
+        }
+        if (i >= 0) { b->profile.ms[i] += ms; b->profile.launches[i] += 1; }
+    }
+    for (int v = 0; v < b->n; ++v) {
+        const unsigned *w = b->h_status + (size_t)v * ST_WORDS;
+        if (w[ST_FLAGS] & FLAG_BADQ)
+            return fail(GES_ERR_INVALID_ARG, "view %d: a rotation quaternion has zero norm or is not finite", v);
+        if (w[ST_FLAGS] & (FLAG_SOVF | FLAG_GOVF))
+            return fail(GES_ERR_CAPACITY, "view %d: %u surfel / %u Gaussian tile entries exceed the batch's "
+                        "lists (%lld / %lld); recreate the batch", v, w[ST_SPAIRS], w[ST_GPAIRS],
+                        (long long)b->s_cap[v], (long long)b->g_cap[v]);
+    }
+    return GES_OK;
+}
+
+ges_status ges_batch_get_info(const ges_batch *b, ges_batch_info *out)
+{
+    if (!b || !out) return fail(GES_ERR_INVALID_ARG, "NULL argument");
+    *out = b->info;
+    return GES_OK;
+}
+
+ges_status ges_batch_get_profile(ges_batch *b, ges_profile *out, int32_t reset)
+{
+    if (!b || !out) return fail(GES_ERR_INVALID_ARG, "NULL argument");
+    *out = b->profile;
+    if (reset) std::memset(&b->profile, 0, sizeof b->profile);
+    return GES_OK;
+}
+
+ges_status ges_batch_destroy(ges_batch *b)
+{
+    if (b) batch_release(b);
+    return GES_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
 // ges_render_noalloc: the forward render with every intermediate buffer in one
 // fixed device array, for callers that cannot allocate device memory.
 

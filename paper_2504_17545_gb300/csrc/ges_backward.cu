@@ -3,13 +3,15 @@
 // scale, opacity and SH coefficients, and surfel SH coefficients (surfel
 // geometry is fixed in that stage and gets none).
 //
-// Gather form, no atomics: a warp owns 32 consecutive primitives.  Each lane
-// sets up one primitive (the same device function as the forward pass, so the
-// alpha and depth-test decisions are bit-identical); then, primitive by
-// primitive, the warp sweeps that primitive's pixel bbox with one pixel per
-// lane and reduces the per-lane partial sums with a fixed butterfly.  Finally
-// each lane runs the chain rule for its own primitive.  The result is
-// deterministic.
+// Gather form, no atomics: one thread per primitive.  Each thread sets its
+// primitive up with the same device function as the forward pass (so the alpha
+// and depth-test decisions are bit-identical); then the warp sweeps its 32
+// primitives' pixel bboxes one primitive at a time, one pixel per lane (rows
+// read coalesced), and reduces the per-lane partial sums with a fixed
+// butterfly into the owning lane.  Finally each thread runs the chain rule for
+// its own primitive.  The summation order is fixed, so the result is
+// deterministic.  (Sweeping each footprint in its own lane was measured slower:
+// scattered rows, long dependent loops.)
 //
 // Per (Gaussian i, pixel) that passes the clamp and the depth test, with
 // k = 1/(1+W_G) (Eq. 5; 1/W_G in the Gaussians-only mode) and g = dL/dC:
@@ -30,85 +32,95 @@ __device__ __forceinline__ float warp_sum(float x)
     return x;
 }
 
-struct GStage {
-    float px, py, pxl, pyl, ca, cb, cc, sigma, key, r, g, b;
-    float ia, ib, ic;
+
+struct GLoop {
+    float px, py, pxl, pyl, ca, cb, cc, sigma, key, r, g, b, ia, ib, ic;
     int x0, y0, x1, y1;
-    int vis;
 };
+
+// One pixel of one Gaussian: add its 2D-level gradients to acc (dc(3),
+// dsigma, dpx, dpy, dia, dib, dic).  Same alpha and depth test as the forward.
+__device__ __forceinline__ void gauss_pixel(const GLoop &s, int x, int y, const CamParams &C, const OptParams &O,
+                                            bool gmode, const float *__restrict__ dL,
+                                            const float *__restrict__ rgb, const float *__restrict__ depth,
+                                            const float *__restrict__ aux, float *acc)
+{
+    const int64_t HW = (int64_t)C.W * C.H, pix = (int64_t)y * C.W + x;
+    GaussRec g;
+    g.px = s.px; g.py = s.py; g.pxl = s.pxl; g.pyl = s.pyl;
+    g.ca = s.ca; g.cb = s.cb; g.cc = s.cc; g.sigma = s.sigma;
+    float e;
+    const float a = gauss_alpha(g, x + 0.5f, y + 0.5f, e);
+    if (!(a >= O.alpha_min) || !(s.key < __ldg(depth + pix))) return;
+    const float W = __ldg(aux + pix);
+    const float kk = gmode ? 1.f / W : 1.f / (1.f + W);
+    const float g0 = __ldg(dL + pix), g1 = __ldg(dL + HW + pix), g2 = __ldg(dL + 2 * HW + pix);
+    const float C0 = __ldg(rgb + pix), C1 = __ldg(rgb + HW + pix), C2 = __ldg(rgb + 2 * HW + pix);
+    acc[0] += a * kk * g0;
+    acc[1] += a * kk * g1;
+    acc[2] += a * kk * g2;
+    const float dLda = kk * (g0 * (s.r - C0) + g1 * (s.g - C1) + g2 * (s.b - C2));
+    acc[3] += dLda * e;
+    const float dLdq = -0.5f * dLda * a;
+    const float dx = (x + 0.5f - s.px) - s.pxl, dy = (y + 0.5f - s.py) - s.pyl;
+    acc[4] += dLdq * -2.f * (s.ia * dx + s.ib * dy);
+    acc[5] += dLdq * -2.f * (s.ib * dx + s.ic * dy);
+    acc[6] += dLdq * dx * dx;
+    acc[7] += dLdq * 2.f * dx * dy;
+    acc[8] += dLdq * dy * dy;
+}
+
+__device__ __forceinline__ float shfl_f(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ int shfl_i(int v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
 __global__ void __launch_bounds__(256) k_gauss_bwd(SceneView S, CamParams C, OptParams O,
                                                   const float *__restrict__ dL, const float *__restrict__ rgb,
                                                   const float *__restrict__ depth, const float *__restrict__ aux,
                                                   ges_grads G)
 {
-    __shared__ GStage sg[8][32];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t base = ((int64_t)blockIdx.x * 8 + warp) * 32;
-    if (base >= S.M) return;
-    const int64_t gi = base + lane;
-    const int64_t HW = (int64_t)C.W * C.H;
-    // 1) lane-parallel set-up
-    {
+    const int64_t gi = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool gmode = O.mode == GES_MODE_GAUSSIANS_ONLY;
+    // 1) set-up (the forward's definition), keep only what the sweep needs
+    GLoop s;
+    bool vis = false;
+    if (gi < S.M && O.mode != GES_MODE_SURFELS_ONLY) {
         GaussOut o;
-        o.visible = false;
-        if (gi < S.M) gauss_setup(S, C, O, gi, o);
-        GStage &s = sg[warp][lane];
-        s.vis = o.visible ? 1 : 0;
-        if (o.visible) {
-            s.px = o.rec.px; s.py = o.rec.py; s.pxl = o.rec.pxl; s.pyl = o.rec.pyl;
-            s.ca = o.rec.ca; s.cb = o.rec.cb; s.cc = o.rec.cc; s.sigma = o.rec.sigma; s.key = o.rec.key;
-            s.r = o.rec.r; s.g = o.rec.g; s.b = o.rec.b;
-            s.ia = o.ia; s.ib = o.ib; s.ic = o.ic;
-            s.x0 = o.x0; s.y0 = o.y0; s.x1 = o.x1; s.y1 = o.y1;
+        gauss_setup(S, C, O, gi, o);
+        vis = o.visible;
+        if (vis) {
+            s = GLoop{o.rec.px, o.rec.py, o.rec.pxl, o.rec.pyl, o.rec.ca, o.rec.cb, o.rec.cc, o.rec.sigma,
+                      o.rec.key, o.rec.r, o.rec.g, o.rec.b, o.ia, o.ib, o.ic, o.x0, o.y0, o.x1, o.y1};
         }
     }
-    __syncwarp();
-    // 2) per Gaussian, sweep its pixels
-    float my[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // dc(3), dsigma, dpx, dpy, dia, dib, dic
-    const bool gmode = O.mode == GES_MODE_GAUSSIANS_ONLY;
-    for (int j = 0; j < 32; ++j) {
-        const GStage &s = sg[warp][j];
-        if (!s.vis) continue;
-        GaussRec g;
-        g.px = s.px; g.py = s.py; g.pxl = s.pxl; g.pyl = s.pyl;
-        g.ca = s.ca; g.cb = s.cb; g.cc = s.cc; g.sigma = s.sigma;
-        const int w = s.x1 - s.x0 + 1, npx = w * (s.y1 - s.y0 + 1);
-        float acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        for (int k = lane; k < npx; k += 32) {
-            const int x = s.x0 + k % w, y = s.y0 + k / w;
-            const int64_t pix = (int64_t)y * C.W + x;
-            float e;
-            const float a = gauss_alpha(g, x + 0.5f, y + 0.5f, e);
-            if (!(a >= O.alpha_min) || !(s.key < __ldg(depth + pix))) continue;
-            const float W = __ldg(aux + pix);
-            const float kk = gmode ? 1.f / W : 1.f / (1.f + W);
-            const float g0 = __ldg(dL + pix), g1 = __ldg(dL + HW + pix), g2 = __ldg(dL + 2 * HW + pix);
-            const float C0 = __ldg(rgb + pix), C1 = __ldg(rgb + HW + pix), C2 = __ldg(rgb + 2 * HW + pix);
-            acc[0] += a * kk * g0;
-            acc[1] += a * kk * g1;
-            acc[2] += a * kk * g2;
-            const float dLda = kk * (g0 * (s.r - C0) + g1 * (s.g - C1) + g2 * (s.b - C2));
-            acc[3] += dLda * e;
-            const float dLdq = -0.5f * dLda * a;
-            const float dx = (x + 0.5f - s.px) - s.pxl, dy = (y + 0.5f - s.py) - s.pyl;
-            acc[4] += dLdq * -2.f * (s.ia * dx + s.ib * dy);
-            acc[5] += dLdq * -2.f * (s.ib * dx + s.ic * dy);
-            acc[6] += dLdq * dx * dx;
-            acc[7] += dLdq * 2.f * dx * dy;
-            acc[8] += dLdq * dy * dy;
-        }
+    float acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    // 2) the whole warp sweeps one Gaussian's pixels at a time (rows are read
+    //    coalesced), then reduces with a fixed butterfly
+    unsigned big = __ballot_sync(0xffffffffu, vis);
+    while (big) {
+        const int j = __ffs(big) - 1;
+        big &= big - 1;
+        GLoop t;
+        t.px = shfl_f(s.px, j); t.py = shfl_f(s.py, j); t.pxl = shfl_f(s.pxl, j); t.pyl = shfl_f(s.pyl, j);
+        t.ca = shfl_f(s.ca, j); t.cb = shfl_f(s.cb, j); t.cc = shfl_f(s.cc, j); t.sigma = shfl_f(s.sigma, j);
+        t.key = shfl_f(s.key, j); t.r = shfl_f(s.r, j); t.g = shfl_f(s.g, j); t.b = shfl_f(s.b, j);
+        t.ia = shfl_f(s.ia, j); t.ib = shfl_f(s.ib, j); t.ic = shfl_f(s.ic, j);
+        t.x0 = shfl_i(s.x0, j); t.y0 = shfl_i(s.y0, j); t.x1 = shfl_i(s.x1, j); t.y1 = shfl_i(s.y1, j);
+        const int w = t.x1 - t.x0 + 1, n = w * (t.y1 - t.y0 + 1);
+        float part[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int k = lane; k < n; k += 32) gauss_pixel(t, t.x0 + k % w, t.y0 + k / w, C, O, gmode, dL, rgb, depth, aux, part);
         for (int c = 0; c < 9; ++c) {
-            const float t = warp_sum(acc[c]);
-            if (lane == j) my[c] = t;
+            const float v = warp_sum(part[c]);
+            if (lane == j) acc[c] = v;
         }
     }
     if (gi >= S.M) return;
     const int K = (S.deg + 1) * (S.deg + 1);
-    // 3) chain rule for this lane's Gaussian
+    // 3) chain rule for this lane's Gaussian (set-up recomputed: fewer live registers in the sweep)
     GaussOut o;
-    gauss_setup(S, C, O, gi, o);
-    if (!o.visible || O.mode == GES_MODE_SURFELS_ONLY) {
+    o.visible = false;
+    if (vis) gauss_setup(S, C, O, gi, o);
+    if (!o.visible) {
         if (G.g_pos) for (int a = 0; a < 3; ++a) G.g_pos[3 * gi + a] = 0.f;
         if (G.g_rot) for (int a = 0; a < 4; ++a) G.g_rot[4 * gi + a] = 0.f;
         if (G.g_scale) for (int a = 0; a < 3; ++a) G.g_scale[3 * gi + a] = 0.f;
@@ -116,6 +128,7 @@ __global__ void __launch_bounds__(256) k_gauss_bwd(SceneView S, CamParams C, Opt
         if (G.g_sh) for (int a = 0; a < 3 * K; ++a) G.g_sh[3 * K * gi + a] = 0.f;
         return;
     }
+    const float *my = acc;
     const float *dc = my;
     float gp[3] = {0.f, 0.f, 0.f};
     // colour -> SH coefficients and position (through the view direction)
@@ -210,57 +223,55 @@ __global__ void __launch_bounds__(256) k_gauss_bwd(SceneView S, CamParams C, Opt
         for (int a = 0; a < 4; ++a) G.g_rot[4 * gi + a] = (gq[a] - pr * o.qn[a]) / o.qnorm;
 }
 
-struct SStage {
-    int x0, y0, x1, y1, vis;
-};
-
 __global__ void __launch_bounds__(256) k_surfel_bwd(SceneView S, CamParams C, OptParams O,
                                                    const float *__restrict__ dL, const int32_t *__restrict__ sid,
                                                    const float *__restrict__ aux, float *__restrict__ g_sh)
 {
-    __shared__ SStage ss[8][32];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t base = ((int64_t)blockIdx.x * 8 + warp) * 32;
-    if (base >= S.N) return;
-    const int64_t si = base + lane;
+    const int64_t si = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const int lane = threadIdx.x & 31;
     const int64_t HW = (int64_t)C.W * C.H;
+    const bool full = O.mode == GES_MODE_FULL;
     SurfelOut o;
     o.visible = false;
     if (si < S.N && O.mode != GES_MODE_GAUSSIANS_ONLY) surfel_setup(S, C, O, si, o);
-    ss[warp][lane] = SStage{o.x0, o.y0, o.x1, o.y1, o.visible ? 1 : 0};
-    __syncwarp();
-    float my[3] = {0.f, 0.f, 0.f};
-    const bool full = O.mode == GES_MODE_FULL;
-    for (int j = 0; j < 32; ++j) {
-        const SStage s = ss[warp][j];
-        if (!s.vis) continue;
-        const int32_t want = (int32_t)(base + j);
-        const int w = s.x1 - s.x0 + 1, npx = w * (s.y1 - s.y0 + 1);
-        float acc[3] = {0.f, 0.f, 0.f};
-        for (int k = lane; k < npx; k += 32) {
-            const int x = s.x0 + k % w, y = s.y0 + k / w;
-            const int64_t pix = (int64_t)y * C.W + x;
+    const bool vis = o.visible;
+    int x0 = 0, y0 = 0, x1 = -1, y1 = -1;
+    if (vis) { x0 = o.x0; y0 = o.y0; x1 = o.x1; y1 = o.y1; }
+    float acc[3] = {0.f, 0.f, 0.f};
+    // dL/dc_s = sum over the pixels s won of k g (k = 1/(1+W_G), or 1 with
+    // surfels only); the warp sweeps one surfel's bbox at a time
+    unsigned big = __ballot_sync(0xffffffffu, vis);
+    while (big) {
+        const int j = __ffs(big) - 1;
+        big &= big - 1;
+        const int bx0 = shfl_i(x0, j), by0 = shfl_i(y0, j), bx1 = shfl_i(x1, j), by1 = shfl_i(y1, j);
+        const int32_t want = (int32_t)(si - lane + j);
+        const int w = bx1 - bx0 + 1, n = w * (by1 - by0 + 1);
+        float part[3] = {0.f, 0.f, 0.f};
+        for (int k = lane; k < n; k += 32) {
+            const int64_t pix = (int64_t)(by0 + k / w) * C.W + bx0 + k % w;
             if (__ldg(sid + pix) != want) continue;
             const float kk = full ? 1.f / (1.f + __ldg(aux + pix)) : 1.f;
-            acc[0] += kk * __ldg(dL + pix);
-            acc[1] += kk * __ldg(dL + HW + pix);
-            acc[2] += kk * __ldg(dL + 2 * HW + pix);
+            part[0] += kk * __ldg(dL + pix);
+            part[1] += kk * __ldg(dL + HW + pix);
+            part[2] += kk * __ldg(dL + 2 * HW + pix);
         }
         for (int c = 0; c < 3; ++c) {
-            const float t = warp_sum(acc[c]);
-            if (lane == j) my[c] = t;
+            const float v = warp_sum(part[c]);
+            if (lane == j) acc[c] = v;
         }
     }
     if (si >= S.N) return;
     const int K = (S.deg + 1) * (S.deg + 1);
-    if (!o.visible) {
-        for (int a = 0; a < 3 * K; ++a) g_sh[3 * K * si + a] = 0.f;
+    float *out = g_sh + (int64_t)3 * K * si;
+    if (!vis) {
+        for (int a = 0; a < 3 * K; ++a) out[a] = 0.f;
         return;
     }
     float Y[16];
     sh_basis(K, o.dir[0], o.dir[1], o.dir[2], Y);
     for (int k = 0; k < K; ++k)
-        for (int c = 0; c < 3; ++c) g_sh[3 * K * si + 3 * k + c] = o.raw[c] > 0.f ? Y[k] * my[c] : 0.f;
+        for (int c = 0; c < 3; ++c) out[3 * k + c] = o.raw[c] > 0.f ? Y[k] * acc[c] : 0.f;
 }
 
 }  // namespace
@@ -272,15 +283,11 @@ cudaError_t launch_backward(const SceneView &S, const CamParams &C, const OptPar
 {
     (void)status;
     if (ev) cudaEventRecord(ev[0], st);
-    if (S.M > 0) {
-        const int64_t warps = (S.M + 31) / 32;
-        k_gauss_bwd<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(S, C, O, dL_drgb, out_rgb, out_depth, aux, G);
-    }
+    if (S.M > 0)
+        k_gauss_bwd<<<(unsigned)((S.M + 255) / 256), 256, 0, st>>>(S, C, O, dL_drgb, out_rgb, out_depth, aux, G);
     if (ev) cudaEventRecord(ev[1], st);
-    if (S.N > 0 && G.s_sh) {
-        const int64_t warps = (S.N + 31) / 32;
-        k_surfel_bwd<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(S, C, O, dL_drgb, surfel_id, aux, G.s_sh);
-    }
+    if (S.N > 0 && G.s_sh)
+        k_surfel_bwd<<<(unsigned)((S.N + 255) / 256), 256, 0, st>>>(S, C, O, dL_drgb, surfel_id, aux, G.s_sh);
     if (ev) cudaEventRecord(ev[2], st);
     return cudaGetLastError();
 }

@@ -55,6 +55,17 @@ LocalBins plan_local_bins(int64_t N, int64_t M, int num_sms)
     return b;
 }
 
+LocalBins plan_local_bins_per_cta(int64_t N, int64_t M, int64_t prims_per_cta)
+{
+    const int64_t R = prims_per_cta < 256 ? 256 : (prims_per_cta > 60000 ? 60000 : prims_per_cta);
+    LocalBins b{0, 0, 1, 1};
+    b.Ps = (int)((N + R - 1) / R);
+    b.Pg = (int)((M + R - 1) / R);
+    if (b.Ps > 0) b.Rs = ((N + b.Ps - 1) / b.Ps + 3) & ~(int64_t)3;
+    if (b.Pg > 0) b.Rg = ((M + b.Pg - 1) / b.Pg + 3) & ~(int64_t)3;
+    return b;
+}
+
 namespace {
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
@@ -93,13 +104,13 @@ __device__ __forceinline__ bool setup_and_store(const SceneView &S, const CamPar
 // ---------------------------------------------------------------------------
 // local binning
 
-__global__ void __launch_bounds__(kPrepThreads, 1) k_prep_local(SceneView S, CamParams C, OptParams O,
-                                                                ViewScratch X, LocalBins B)
+// CTA c of a view: its range of primitives.  hist: ceil(T/2) shared words
+// (two 16-bit counters each); vcnt: a shared counter.
+__device__ __forceinline__ void prep_local_body(const SceneView &S, const CamParams &C, const OptParams &O,
+                                                const ViewScratch &X, const LocalBins &B, int c, unsigned *hist,
+                                                unsigned &vcnt)
 {
-    extern __shared__ unsigned hist[];   // ceil(T/2) words, two 16-bit counters each
-    __shared__ unsigned vcnt;
     const int T = C.tiles_x * C.tiles_y, words = (T + 1) >> 1;
-    const int c = blockIdx.x;
     const bool surf = c < B.Ps;
     const int64_t R = surf ? B.Rs : B.Rg, n = surf ? S.N : S.M;
     const int64_t beg = (int64_t)(surf ? c : c - B.Ps) * R;
@@ -138,6 +149,14 @@ __global__ void __launch_bounds__(kPrepThreads, 1) k_prep_local(SceneView S, Cam
     }
 }
 
+__global__ void __launch_bounds__(kPrepThreads, 1) k_prep_local(SceneView S, CamParams C, OptParams O,
+                                                                ViewScratch X, LocalBins B)
+{
+    extern __shared__ unsigned hist[];
+    __shared__ unsigned vcnt;
+    prep_local_body(S, C, O, X, B, blockIdx.x, hist, vcnt);
+}
+
 __device__ __forceinline__ unsigned hist_get(const unsigned *row, int t)
 {
     const unsigned w = row[t >> 1];
@@ -146,13 +165,12 @@ __device__ __forceinline__ unsigned hist_get(const unsigned *row, int t)
 
 // Per tile: exclusive scan over the CTAs of one kind.  Block = 32 tiles x 8
 // warps; warp w scans CTAs [w*P/8, (w+1)*P/8).
-__global__ void __launch_bounds__(256) k_colscan(ViewScratch X, int T, LocalBins B)
+__device__ __forceinline__ void colscan_body(const ViewScratch &X, int T, const LocalBins &B, int bx, bool surf,
+                                             unsigned (*part)[33])
 {
-    __shared__ unsigned part[8][33];
-    const bool surf = blockIdx.y == 0;
     const int P = surf ? B.Ps : B.Pg, r0 = surf ? 0 : B.Ps;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int t = blockIdx.x * 32 + lane;
+    const int t = bx * 32 + lane;
     const int words = (T + 1) >> 1;
     const int a = r0 + (int)((int64_t)P * w / 8), b = r0 + (int)((int64_t)P * (w + 1) / 8);
     unsigned s = 0;
@@ -175,11 +193,16 @@ __global__ void __launch_bounds__(256) k_colscan(ViewScratch X, int T, LocalBins
     }
 }
 
-__global__ void __launch_bounds__(kFillThreads) k_fill_local(ViewScratch X, int T, int tiles_x, LocalBins B)
+__global__ void __launch_bounds__(256) k_colscan(ViewScratch X, int T, LocalBins B)
 {
-    extern __shared__ unsigned cur[];    // T cursors
+    __shared__ unsigned part[8][33];
+    colscan_body(X, T, B, blockIdx.x, blockIdx.y == 0, part);
+}
+
+__device__ __forceinline__ void fill_local_body(const ViewScratch &X, int T, int tiles_x, const LocalBins &B, int c,
+                                                unsigned *cur)
+{
     if (X.status[ST_FLAGS] & (FLAG_SOVF | FLAG_GOVF)) return;
-    const int c = blockIdx.x;
     const bool surf = c < B.Ps;
     const int *off = surf ? X.s_off : X.g_off;
     const unsigned *brow = X.base + (size_t)c * T;
@@ -199,6 +222,12 @@ __global__ void __launch_bounds__(kFillThreads) k_fill_local(ViewScratch X, int 
         for (int ty = ty0; ty <= ty1; ++ty)
             for (int tx = tx0; tx <= tx1; ++tx) list[atomicAdd(cur + ty * tiles_x + tx, 1u)] = id;
     }
+}
+
+__global__ void __launch_bounds__(kFillThreads) k_fill_local(ViewScratch X, int T, int tiles_x, LocalBins B)
+{
+    extern __shared__ unsigned cur[];    // T cursors
+    fill_local_body(X, T, tiles_x, B, blockIdx.x, cur);
 }
 
 // ---------------------------------------------------------------------------
@@ -254,14 +283,12 @@ __global__ void __launch_bounds__(256) k_fill_atomic(ViewScratch X, int tiles_x)
 // ---------------------------------------------------------------------------
 // scan of tile totals (both binning modes)
 
-__global__ void __launch_bounds__(1024) k_scan(ViewScratch X, int T)
+__device__ __forceinline__ void scan_body(const ViewScratch &X, int T, bool surf, long long *warp_tot)
 {
-    const bool surf = blockIdx.x == 0;
     int *cnt = surf ? X.s_cnt : X.g_cnt;
     int *off = surf ? X.s_off : X.g_off;
     int *cur = surf ? X.s_cur : X.g_cur;
     const int64_t cap = surf ? X.s_cap : X.g_cap;
-    __shared__ long long warp_tot[32];
     const int tid = threadIdx.x, per = (T + 1023) / 1024;
     const int b = min(tid * per, T), e = min(b + per, T);
     long long local = 0;
@@ -297,6 +324,12 @@ __global__ void __launch_bounds__(1024) k_scan(ViewScratch X, int T)
     }
 }
 
+__global__ void __launch_bounds__(1024) k_scan(ViewScratch X, int T)
+{
+    __shared__ long long warp_tot[32];
+    scan_body(X, T, blockIdx.x == 0, warp_tot);
+}
+
 // ---------------------------------------------------------------------------
 // raster
 
@@ -315,19 +348,15 @@ __device__ __forceinline__ void stage_rec(float4 (*st)[kChunk], const float4 *re
     st[0][slot] = r0; st[1][slot] = r1; st[2][slot] = r2; st[3][slot] = r3;
 }
 
-__global__ void __launch_bounds__(kRasterThreads, 5) k_raster(ViewScratch X, CamParams C, OptParams O,
-                                                           float *__restrict__ out_rgb,
-                                                           float *__restrict__ out_depth,
-                                                           int32_t *__restrict__ out_id,
-                                                           float *__restrict__ aux)
+// One 16x16 tile.  ss/sgs: shared staging for surfel and Gaussian records,
+// structure-of-arrays (one float4 plane per 16-byte quarter): consecutive
+// threads store consecutive 16 B, and a warp reading one record gets a
+// broadcast.
+__device__ __forceinline__ void raster_tile(const ViewScratch &X, const CamParams &C, const OptParams &O,
+                                            float *__restrict__ out_rgb, float *__restrict__ out_depth,
+                                            int32_t *__restrict__ out_id, float *__restrict__ aux, int tile,
+                                            float4 (*ss)[kChunk], float4 (*sgs)[kChunk])
 {
-    // records staged as structure-of-arrays (one float4 plane per 16-byte
-    // quarter): consecutive threads store consecutive 16 B, and a warp reading
-    // one record gets a broadcast
-    __shared__ float4 ss[4][kChunk];        // surfels
-    __shared__ float4 sgs[4][kChunk];       // Gaussians
-    if (X.status[ST_FLAGS] & (FLAG_SOVF | FLAG_GOVF)) return;
-    const int tile = blockIdx.x;
     const int tx = tile % C.tiles_x, ty = tile / C.tiles_x;
     const unsigned warp = threadIdx.x >> 5, lane = lane_id();
     const int wx0 = tx * kTile + (warp & 1) * kWarpW, wy0 = ty * kTile + (warp >> 1) * kWarpH;
@@ -475,16 +504,159 @@ __global__ void __launch_bounds__(kRasterThreads, 5) k_raster(ViewScratch X, Cam
     if (aux) aux[pix] = WG;
 }
 
+__global__ void __launch_bounds__(kRasterThreads, 5) k_raster(ViewScratch X, CamParams C, OptParams O,
+                                                           float *__restrict__ out_rgb,
+                                                           float *__restrict__ out_depth,
+                                                           int32_t *__restrict__ out_id,
+                                                           float *__restrict__ aux)
+{
+    __shared__ float4 ss[4][kChunk];
+    __shared__ float4 sgs[4][kChunk];
+    if (X.status[ST_FLAGS] & (FLAG_SOVF | FLAG_GOVF)) return;
+    raster_tile(X, C, O, out_rgb, out_depth, out_id, aux, blockIdx.x, ss, sgs);
+}
+
+// ---------------------------------------------------------------------------
+// batch: each phase is one launch over all views of all scenes
+
+// largest v with base(v) <= x (bases ascending, base(0) = 0)
+template <typename F>
+__device__ __forceinline__ int find_view(int n, int x, F base)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base(mid) <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void load_view(const BatchView *V, int v, BatchView &dst)
+{
+    const int *src = reinterpret_cast<const int *>(V + v);
+    int *d = reinterpret_cast<int *>(&dst);
+    for (int k = threadIdx.x; k < (int)(sizeof(BatchView) / 4); k += blockDim.x) d[k] = src[k];
+}
+
+__global__ void __launch_bounds__(kPrepThreads, 1) k_bprep(const BatchView *V, int n, OptParams O)
+{
+    extern __shared__ unsigned hist[];
+    __shared__ unsigned vcnt;
+    __shared__ __align__(16) unsigned char bv_raw[sizeof(BatchView)];
+    BatchView &bv = *reinterpret_cast<BatchView *>(bv_raw);
+    __shared__ int sv;
+    if (threadIdx.x == 0) sv = find_view(n, blockIdx.x, [&](int k) { return V[k].prep_base; });
+    __syncthreads();
+    load_view(V, sv, bv);
+    __syncthreads();
+    prep_local_body(bv.S, bv.C, O, bv.X, bv.B, blockIdx.x - bv.prep_base, hist, vcnt);
+}
+
+__global__ void __launch_bounds__(256) k_bcolscan(const BatchView *V, int n)
+{
+    __shared__ unsigned part[8][33];
+    __shared__ __align__(16) unsigned char bv_raw[sizeof(BatchView)];
+    BatchView &bv = *reinterpret_cast<BatchView *>(bv_raw);
+    __shared__ int sv;
+    if (threadIdx.x == 0) sv = find_view(n, blockIdx.x, [&](int k) { return V[k].colscan_base; });
+    __syncthreads();
+    load_view(V, sv, bv);
+    __syncthreads();
+    colscan_body(bv.X, bv.T, bv.B, blockIdx.x - bv.colscan_base, blockIdx.y == 0, part);
+}
+
+__global__ void __launch_bounds__(1024) k_bscan(const BatchView *V)
+{
+    __shared__ long long warp_tot[32];
+    __shared__ __align__(16) unsigned char bv_raw[sizeof(BatchView)];
+    BatchView &bv = *reinterpret_cast<BatchView *>(bv_raw);
+    load_view(V, blockIdx.x >> 1, bv);
+    __syncthreads();
+    scan_body(bv.X, bv.T, (blockIdx.x & 1) == 0, warp_tot);
+}
+
+__global__ void __launch_bounds__(kFillThreads) k_bfill(const BatchView *V, int n)
+{
+    extern __shared__ unsigned cur[];
+    __shared__ __align__(16) unsigned char bv_raw[sizeof(BatchView)];
+    BatchView &bv = *reinterpret_cast<BatchView *>(bv_raw);
+    __shared__ int sv;
+    if (threadIdx.x == 0) sv = find_view(n, blockIdx.x, [&](int k) { return V[k].prep_base; });
+    __syncthreads();
+    load_view(V, sv, bv);
+    __syncthreads();
+    fill_local_body(bv.X, bv.T, bv.C.tiles_x, bv.B, blockIdx.x - bv.prep_base, cur);
+}
+
+// Persistent raster over the (view, tile) items of the whole batch: each CTA
+// takes the next item from a counter until none is left, so uneven views
+// balance across the GPU.
+__global__ void __launch_bounds__(kRasterThreads, 5) k_braster(const BatchView *V, int n, OptParams O,
+                                                            unsigned *counter, int total)
+{
+    __shared__ float4 ss[4][kChunk];
+    __shared__ float4 sgs[4][kChunk];
+    __shared__ __align__(16) unsigned char bv_raw[sizeof(BatchView)];
+    BatchView &bv = *reinterpret_cast<BatchView *>(bv_raw);
+    __shared__ int item, sv;
+    int cur_v = -1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            item = (int)atomicAdd(counter, 1u);
+            if (item < total) sv = find_view(n, item, [&](int k) { return V[k].tile_base; });
+        }
+        __syncthreads();
+        const int it = item;
+        if (it >= total) break;
+        if (sv != cur_v) {
+            cur_v = sv;
+            load_view(V, cur_v, bv);
+        }
+        __syncthreads();
+        if (!(bv.X.status[ST_FLAGS] & (FLAG_SOVF | FLAG_GOVF)))
+            raster_tile(bv.X, bv.C, O, bv.rgb, bv.depth, nullptr, nullptr, it - bv.tile_base, ss, sgs);
+        __syncthreads();
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const OptParams &O, unsigned *work_counter,
+                         cudaStream_t st, cudaEvent_t *ev)
+{
+    // ev (5 events or null): recorded as graph event nodes when captured
+    auto mark = [&](int k) { if (ev) cudaEventRecordWithFlags(ev[k], st, cudaEventRecordExternal); };
+    mark(0);
+    if (P.total_prep > 0)
+        k_bprep<<<P.total_prep, kPrepThreads, local_bins_smem(P.max_T, false), st>>>(d_views, P.n, O);
+    mark(1);
+    if (P.total_colscan > 0) k_bcolscan<<<dim3(P.total_colscan, 2), 256, 0, st>>>(d_views, P.n);
+    k_bscan<<<2 * P.n, 1024, 0, st>>>(d_views);
+    mark(2);
+    if (P.total_prep > 0)
+        k_bfill<<<P.total_prep, kFillThreads, local_bins_smem(P.max_T, true), st>>>(d_views, P.n);
+    mark(3);
+    k_braster<<<P.raster_ctas, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
+    mark(4);
+    return cudaGetLastError();
+}
 
 size_t local_bins_smem(int T, bool fill) { return fill ? (size_t)T * 4 : (size_t)((T + 1) / 2) * 4; }
 
 cudaError_t prepare_forward_kernels()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_prep_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)local_bins_smem(kLocalMaxTiles, false));
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_fill_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_prep_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)local_bins_smem(kLocalMaxTiles, false))) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_bprep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)local_bins_smem(kLocalMaxTiles, false))) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_fill_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)local_bins_smem(kLocalMaxTiles, true))) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(k_bfill, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)local_bins_smem(kLocalMaxTiles, true));
 }
 

@@ -82,6 +82,25 @@ struct LocalBins {
     int64_t Rs, Rg;       // primitives per CTA
 };
 constexpr int kLocalMaxTiles = 32768;   // shared-memory cursors of the fill: 4 B per tile
+
+// One view of a batch (device table entry).  The batch kernels find their view
+// from the per-phase bases (prefix sums over the views).
+struct BatchView {
+    SceneView S;          // counts already zeroed for the render mode
+    CamParams C;
+    ViewScratch X;
+    LocalBins B;
+    float *rgb, *depth;
+    int T, tile_base, prep_base, colscan_base;
+};
+struct BatchPlan {
+    int n;                                   // views
+    int total_tiles, total_prep, total_colscan, max_T;
+    int raster_ctas;                         // persistent raster grid
+};
+cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const OptParams &O, unsigned *work_counter,
+                         cudaStream_t st, cudaEvent_t *ev /* 5 events or nullptr */);
+LocalBins plan_local_bins_per_cta(int64_t N, int64_t M, int64_t prims_per_cta);
 constexpr int kPrepThreads = 512;
 constexpr int kFillThreads = 1024;
 LocalBins plan_local_bins(int64_t N, int64_t M, int num_sms);

@@ -58,6 +58,11 @@ class ges_stats(C.Structure):
                 ("tiles_x", C.c_int32), ("tiles_y", C.c_int32)]
 
 
+class ges_batch_info(C.Structure):
+    _fields_ = [("n_views", C.c_int32), ("prims_per_cta", C.c_int32), ("raster_ctas_per_sm", C.c_int32),
+                ("candidates", C.c_int32), ("tuned_ms", C.c_double)]
+
+
 class ges_profile(C.Structure):
     _fields_ = [("n", C.c_int32), ("names", (C.c_char * 24) * GES_PROFILE_SLOTS),
                 ("ms", C.c_double * GES_PROFILE_SLOTS), ("launches", C.c_int64 * GES_PROFILE_SLOTS)]
@@ -82,6 +87,14 @@ _SIGS = {
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ges_count_fragments": (C.c_int, [C.c_void_p, _P(ges_camera), _P(ges_render_opts), _P(C.c_int64),
                                       _P(C.c_int64)]),
+    "ges_batch_create": (C.c_int, [_P(C.c_void_p), _P(ges_camera), _P(C.c_int32), C.c_int32,
+                                   _P(ges_render_opts), _P(C.c_void_p), _P(C.c_void_p), _P(C.c_void_p)]),
+    "ges_batch_set_camera": (C.c_int, [C.c_void_p, C.c_int32, _P(ges_camera)]),
+    "ges_batch_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ges_batch_sync": (C.c_int, [C.c_void_p]),
+    "ges_batch_get_info": (C.c_int, [C.c_void_p, _P(ges_batch_info)]),
+    "ges_batch_get_profile": (C.c_int, [C.c_void_p, _P(ges_profile), C.c_int32]),
+    "ges_batch_destroy": (C.c_int, [C.c_void_p]),
     "ges_get_stats": (C.c_int, [C.c_void_p, _P(ges_stats)]),
     "ges_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
     "ges_get_profile": (C.c_int, [C.c_void_p, _P(ges_profile)]),
@@ -203,3 +216,43 @@ def ges_count_fragments(scene, cam: ges_camera, opts):
     _check(load().ges_count_fragments(scene, C.byref(cam), C.byref(opts) if opts is not None else None,
                                       C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+def ges_batch_create(scenes, cams, scene_of_view, opts, out_rgb, out_depth):
+    n = len(cams)
+    sc = (C.c_void_p * len(scenes))(*[x.value if isinstance(x, C.c_void_p) else x for x in scenes])
+    cm = (ges_camera * n)(*cams)
+    sv = (C.c_int32 * n)(*scene_of_view)
+    rg = (C.c_void_p * n)(*out_rgb)
+    dp = (C.c_void_p * n)(*out_depth) if out_depth is not None else None
+    h = C.c_void_p()
+    _check(load().ges_batch_create(sc, cm, sv, n, C.byref(opts) if opts is not None else None, rg, dp, C.byref(h)))
+    return h
+
+
+def ges_batch_set_camera(batch, view: int, cam: ges_camera):
+    _check(load().ges_batch_set_camera(batch, int(view), C.byref(cam)))
+
+
+def ges_batch_launch(batch, stream: int):
+    _check(load().ges_batch_launch(batch, C.c_void_p(stream)))
+
+
+def ges_batch_sync(batch):
+    _check(load().ges_batch_sync(batch))
+
+
+def ges_batch_get_info(batch) -> ges_batch_info:
+    i = ges_batch_info()
+    _check(load().ges_batch_get_info(batch, C.byref(i)))
+    return i
+
+
+def ges_batch_destroy(batch):
+    _check(load().ges_batch_destroy(batch))
+
+
+def ges_batch_get_profile(batch, reset: bool = False) -> dict:
+    p = ges_profile()
+    _check(load().ges_batch_get_profile(batch, C.byref(p), int(bool(reset))))
+    return {bytes(p.names[i]).split(b"\0")[0].decode(): (p.ms[i], p.launches[i]) for i in range(p.n)}

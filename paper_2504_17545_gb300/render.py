@@ -213,3 +213,49 @@ def render_batch(scenes: Sequence[GESScene], cams: Sequence, scene_of_view: Opti
                        [o[0].data_ptr() for o in outputs], [o[1].data_ptr() if o[1] is not None else 0
                                                             for o in outputs])
     return outputs
+
+
+class GESBatch:
+    """A fixed set of views rendered by one captured CUDA graph (every phase one
+    launch over all views, persistent raster, autotuned launch shape).  Output
+    tensors are allocated here and overwritten by every launch."""
+
+    def __init__(self, scenes: Sequence[GESScene], cams: Sequence, scene_of_view: Optional[Sequence[int]] = None,
+                 opts: Optional[dict] = None, with_depth: bool = True):
+        n = len(cams)
+        self.scenes = list(scenes)
+        self.scene_of_view = list(scene_of_view) if scene_of_view is not None else [0] * n
+        cs = [camera_struct(c) for c in cams]
+        dev = self.scenes[0].t["s_pos"].device
+        self.rgb = [torch.empty((3, c.height, c.width), device=dev) for c in cs]
+        self.depth = [torch.empty((c.height, c.width), device=dev) for c in cs] if with_depth else None
+        self.scenes[0].bind_stream()
+        self.handle = N.ges_batch_create([s.handle for s in self.scenes], cs, self.scene_of_view,
+                                         opts_struct(opts), [t.data_ptr() for t in self.rgb],
+                                         [t.data_ptr() for t in self.depth] if with_depth else None)
+
+    def launch(self):
+        N.ges_batch_launch(self.handle, torch.cuda.current_stream(self.rgb[0].device).cuda_stream)
+
+    def sync(self):
+        N.ges_batch_sync(self.handle)
+
+    def set_camera(self, view: int, cam):
+        N.ges_batch_set_camera(self.handle, view, camera_struct(cam))
+
+    def info(self):
+        return N.ges_batch_get_info(self.handle)
+
+    def profile(self, reset: bool = False):
+        return N.ges_batch_get_profile(self.handle, reset)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            N.ges_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -226,3 +226,31 @@ def test_batched_workload_reduced_precision_views(R, dtype):
         res = compare(deq, cams[v], single, ref)
         _assert(res)
     gs.close()
+
+
+def test_batch_graph_uneven_scenes_equal_single_views(R):
+    """One captured graph over views of two scenes of different sizes and
+    resolutions: every image identical to the per-view render, also after
+    moving one camera between replays."""
+    scene, cams = sg.config_scene(0)
+    other = _small(37, 2000, 6000)
+    ga, gb = R.GESScene.from_arrays(scene), R.GESScene.from_arrays(other)
+    views = [cams[0], sg.look_at((0.5, 0, -2.8), (0, 0, 0), (0, 1, 0), 301, 173, 60.0),
+             sg.look_at((0, 0.3, -2.6), (0, 0, 0), (0, 1, 0), 128, 96, 50.0),
+             sg.look_at((-0.4, 0.2, -2.2), (0, 0, 0), (0, 1, 0), 64, 200, 45.0)]
+    sov = [0, 1, 0, 1]
+    b = R.GESBatch([ga, gb], views, sov)
+    info = b.info()
+    assert info.candidates >= 2 and info.n_views == 4
+    for rep in range(2):
+        b.launch()
+        b.sync()
+        for v in range(4):
+            single = R.render([ga, gb][sov[v]], views[v])
+            assert (b.rgb[v] == single["rgb"]).all() and (b.depth[v] == single["depth"]).all(), (rep, v)
+        moved = sg.look_at((0.45, 0.05, -2.75), (0, 0, 0), (0, 1, 0), 301, 173, 60.0)
+        b.set_camera(1, moved)
+        views[1] = moved
+    b.close()
+    ga.close()
+    gb.close()
