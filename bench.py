@@ -114,16 +114,18 @@ def source_digest():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu record, or None
-    when the kernel sources changed since it was taken."""
+def ncu_traffic(kernel, n_views):
+    """DRAM bytes of one launch of `kernel` over n_views views, from the
+    committed ncu record (taken on a smaller batch of the same views and
+    scaled by the views processed), or None when the kernel sources changed
+    since it was taken."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p)).get(kernel)
     if not d or d.get("source_digest") != source_digest():
         return None
-    return float(d["dram_bytes_per_launch"])
+    return float(d["dram_bytes_per_view"]) * n_views
 
 
 def algorithmic_bytes(n_s, n_g, s_vis, g_vis, hw, attr_bytes=4, sh_bytes=4, deg=3):
@@ -171,10 +173,25 @@ def cpu_baseline_sample(scene, cams):
     t0 = time.perf_counter()
     n = 2
     for k in range(n):
-        oracle.render(scene, cams[(16 * k) % N_VIEWS])
+        oracle.render(scene, cams[(16 * k) % len(cams)])
     dt = time.perf_counter() - t0
     return {"value": n / dt, "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"{n} full 1080p orbit views (of 64), FP64, OpenMP over all host cores"}
+
+
+def reduce_max_over_ranks(ms: float, dist, device) -> float:
+    """Slowest rank's time (the job is done when the last rank is)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(frames_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job frames per second: every rank's frames over the slowest time."""
+    return frames_per_rank * world / (ms / 1e3)
 
 
 def _time(fn, iters, warm=2):
@@ -277,6 +294,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--views", type=int, default=N_VIEWS,
+                    help="orbit views per step (the workload is 64; fewer only for profiling captures)")
+    ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -300,6 +320,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     scene, cams = sg.config_scene(1)
+    cams = cams[:max(1, min(args.views, N_VIEWS))]
+    n_views = len(cams)
     gs = R.GESScene.from_arrays(scene)
     H, W = cams[0].height, cams[0].width
     cstructs = [R.camera_struct(c) for c in cams]
@@ -348,12 +370,9 @@ def main():
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     prof = batch.profile()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    frames = N_VIEWS * args.steps * world
-    value = frames / (ms / 1e3)
+    ms = reduce_max_over_ranks(ms, dist, "cuda")
+    frames = n_views * args.steps * world
+    value = job_throughput(n_views * args.steps, world, ms)
 
     # end-to-end through the C ABI with host buffers: camera structs in,
     # RGB + depth copied back to pinned host memory, every step
@@ -370,15 +389,15 @@ def main():
         torch.cuda.synchronize()
         batch.sync()
     e2e_dt = time.perf_counter() - t0
-    e2e = {"value": N_VIEWS * e2e_steps * world / e2e_dt, "unit": "frames/s",
-           "h2d_bytes_per_step": N_VIEWS * 88, "d2h_bytes_per_step": N_VIEWS * 4 * 4 * H * W}
+    e2e = {"value": n_views * e2e_steps * world / e2e_dt, "unit": "frames/s",
+           "h2d_bytes_per_step": n_views * 88, "d2h_bytes_per_step": n_views * 4 * 4 * H * W}
 
     extras = {}
-    if rank == 0:
+    if rank == 0 and not args.no_extra:
         # the same orbit through the per-view path (one launch sequence per view)
         outs = [(torch.empty((3, H, W), device="cuda"), torch.empty((H, W), device="cuda")) for _ in cams]
         ms_loop = _time(lambda: R.render_batch([gs], cams, outputs=outs), 5)
-        extras["orbit_per_view_loop_frames_per_s"] = N_VIEWS / (ms_loop / 1e3)
+        extras["orbit_per_view_loop_frames_per_s"] = n_views / (ms_loop / 1e3)
         extras["train_step"] = train_step_extra(R, N, sg)
         extras["batched_precision"] = batched_extra(R, N, sg)
         extras["uneven_batch"] = uneven_extra(R, N, sg)
@@ -392,36 +411,36 @@ def main():
     peak, peak_src = _peaks()
     sec = top_ms / top_launches / 1e3
     if top == "raster":
-        ops = N_VIEWS * (OPS_PER_SURFEL_FRAGMENT * sfrag + OPS_PER_GAUSS_TERM * gterm)
+        ops = n_views * (OPS_PER_SURFEL_FRAGMENT * sfrag + OPS_PER_GAUSS_TERM * gterm)
         roof = {"bound": "alu", "kernel": "k_braster", "achieved": ops / sec / 1e12, "peak": alu_peak() / 1e12,
-                "unit": "TFLOP/s", "frac": ops / sec / alu_peak(), "traffic": ncu_traffic("k_braster"),
+                "unit": "TFLOP/s", "frac": ops / sec / alu_peak(), "traffic": ncu_traffic("k_braster", n_views),
                 "peak_source": "152 SMs x 128 FP32 lanes x max SM clock",
-                "units_per_launch": {"surfel_fragments": N_VIEWS * sfrag, "gauss_terms": N_VIEWS * gterm}}
+                "units_per_launch": {"surfel_fragments": n_views * sfrag, "gauss_terms": n_views * gterm}}
     else:
-        bpl = N_VIEWS * float(np.mean(prep_b))
+        bpl = n_views * float(np.mean(prep_b))
         roof = {"bound": "hbm", "kernel": "k_bprep", "achieved": bpl / sec / 1e9, "peak": peak,
-                "unit": "GB/s", "frac": bpl / sec / 1e9 / peak, "traffic": ncu_traffic("k_bprep"),
+                "unit": "GB/s", "frac": bpl / sec / 1e9 / peak, "traffic": ncu_traffic("k_bprep", n_views),
                 "peak_source": peak_src}
     prep_ms, prep_n = prof.get("preprocess", (0.0, 1))
-    prep_gbs = N_VIEWS * float(np.mean(prep_b)) / (prep_ms / prep_n / 1e3) / 1e9 if prep_ms > 0 else None
+    prep_gbs = n_views * float(np.mean(prep_b)) / (prep_ms / prep_n / 1e3) / 1e9 if prep_ms > 0 else None
     frame_achieved = float(np.mean(frame_b)) * frames / world / (ms / 1e3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "resolution": f"{W}x{H}", "n_surfels": scene.n_surfels,
-                   "n_gaussians": scene.n_gaussians, "views_per_step": N_VIEWS,
+                   "n_gaussians": scene.n_gaussians, "views_per_step": n_views,
                    "l2": "inputs 332 MB > 129 MB L2, no flush", "parallelism": f"replicas{world}",
-                   "launch": "one CUDA graph per step (5 kernels over all 64 views)",
+                   "launch": f"one CUDA graph per step (5 kernels over all {n_views} views)",
                    "autotuned": {"prims_per_cta": info.prims_per_cta, "raster_ctas_per_sm": info.raster_ctas_per_sm}},
         "roofline": roof,
         "frame_roofline": {"bound": "hbm", "algorithmic_bytes_per_frame": float(np.mean(frame_b)),
                            "achieved": frame_achieved, "peak": peak, "frac": frame_achieved / peak, "unit": "GB/s"},
         "preprocess_roofline": {"bound": "hbm", "kernel": "k_bprep", "achieved": prep_gbs, "peak": peak,
                                 "frac": prep_gbs / peak if prep_gbs else None, "unit": "GB/s",
-                                "algorithmic_bytes_per_launch": N_VIEWS * float(np.mean(prep_b)),
-                                "traffic": ncu_traffic("k_bprep")},
-        "kernel_ms_per_frame": {k: prof[k][0] / prof[k][1] / N_VIEWS for k in names},
+                                "algorithmic_bytes_per_launch": n_views * float(np.mean(prep_b)),
+                                "traffic": ncu_traffic("k_bprep", n_views)},
+        "kernel_ms_per_frame": {k: prof[k][0] / prof[k][1] / n_views for k in names},
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": 5 * args.steps,

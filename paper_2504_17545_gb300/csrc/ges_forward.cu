@@ -33,7 +33,7 @@ namespace ges {
 LocalBins plan_local_bins(int64_t N, int64_t M, int num_sms)
 {
     LocalBins b{0, 0, 1, 1};
-    const int P = num_sms;   // one 16-warp CTA per SM
+    const int P = 2 * num_sms;   // two 16-warp CTAs per SM
     if (N > 0 && M > 0) {
         b.Ps = (int)((P * N + (N + M) / 2) / (N + M));
         b.Ps = b.Ps < 1 ? 1 : (b.Ps > P - 1 ? P - 1 : b.Ps);
@@ -149,7 +149,7 @@ __device__ __forceinline__ void prep_local_body(const SceneView &S, const CamPar
     }
 }
 
-__global__ void __launch_bounds__(kPrepThreads, 1) k_prep_local(SceneView S, CamParams C, OptParams O,
+__global__ void __launch_bounds__(kPrepThreads, 2) k_prep_local(SceneView S, CamParams C, OptParams O,
                                                                 ViewScratch X, LocalBins B)
 {
     extern __shared__ unsigned hist[];
@@ -539,7 +539,7 @@ __device__ __forceinline__ void load_view(const BatchView *V, int v, BatchView &
     for (int k = threadIdx.x; k < (int)(sizeof(BatchView) / 4); k += blockDim.x) d[k] = src[k];
 }
 
-__global__ void __launch_bounds__(kPrepThreads, 1) k_bprep(const BatchView *V, int n, OptParams O)
+__global__ void __launch_bounds__(kPrepThreads, 2) k_bprep(const BatchView *V, int n, OptParams O)
 {
     extern __shared__ unsigned hist[];
     __shared__ unsigned vcnt;
