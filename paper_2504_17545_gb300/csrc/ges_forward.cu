@@ -407,7 +407,6 @@ __device__ __forceinline__ void raster_tile(const ViewScratch &X, const CamParam
                     const int jb = two ? j0 + __ffs(mask) - 1 : ja;
                     if (two) mask &= mask - 1;
                     const float4 a2 = ss[2][ja], b2 = ss[2][jb];
-                    if (a2.w < wmin && b2.w < wmin) continue;       // warp-uniform re-check
                     const float4 a0 = ss[0][ja], a1 = ss[1][ja], b0 = ss[0][jb], b1 = ss[1][jb];
                     const int ida = __float_as_int(ss[3][ja].x), idb = __float_as_int(ss[3][jb].x);
                     const float dua = u - a0.x, dva = v - a0.y, dub = u - b0.x, dvb = v - b0.y;
@@ -420,12 +419,13 @@ __device__ __forceinline__ void raster_tile(const ViewScratch &X, const CamParam
                     const float qa = fmaf(Aa, Aa, fmaf(Ba, Ba, -iza * iza));
                     const float qb = fmaf(Ab, Ab, fmaf(Bb, Bb, -izb * izb));
                     const bool ina = qa <= 0.f && iza < C.izn, inb = qb <= 0.f && izb < C.izn && two;
-                    bool hit = false;
-                    if (ina && (iza > best || (iza == best && ida < bid))) { best = iza; bid = ida; hit = true; }
-                    if (inb && (izb > best || (izb == best && idb < bid))) { best = izb; bid = idb; hit = true; }
-                    if (__any_sync(0xffffffffu, hit))
-                        wmin = __uint_as_float(__reduce_min_sync(0xffffffffu, __float_as_uint(best)));
+                    if (ina && (iza > best || (iza == best && ida < bid))) { best = iza; bid = ida; }
+                    if (inb && (izb > best || (izb == best && idb < bid))) { best = izb; bid = idb; }
                 }
+                // the warp's depth bound is refreshed once per group of 32
+                // entries: per-survivor refreshes and re-checks cost more
+                // instructions than they cull
+                wmin = __uint_as_float(__reduce_min_sync(0xffffffffu, __float_as_uint(best)));
             }
         }
     }
