@@ -22,6 +22,9 @@
  *   Sec. 3        composite C = (C_s W_s + C_G)/(W_s + W_G), W_s = 1 (Eq. 5).
  *   Sec. 5        eps_i = (5/D) sum_j s_ij with D = 3.
  *   Sec. 7 (ablation) "only surfels" C = C_s, "only Gaussians" C = C_G/W_G.
+ *   Sec. 4.1, 5   4x supersampling of the surfel pass (a render at twice the
+ *                 resolution, downsampled), done as 4x multisampling in the
+ *                 OpenGL renderer; the Gaussians are not multisampled.
  *   Sec. 4.2      joint stage: gradients w.r.t. Gaussian p, s, r, sigma, SH
  *                 and surfel SH, surfel geometry fixed.
  * Readings where the paper is silent (camera model, SH basis, low-pass filter,
@@ -61,6 +64,7 @@ typedef struct {
     int32_t mode;        /* 0 full, 1 surfels only, 2 Gaussians only */
     /* ambiguity bands (pixels where several results are correct) */
     double tol_depth_rel, tol_disc_rel, tol_graze, tol_alpha, tol_gdepth_rel;
+    int32_t samples;     /* 1: the pixel centre; 4: 4x multisampling of the surfel pass (Sec. 5) */
 } ora_opts;
 
 enum { ORA_OK = 0, ORA_BAD_ARG = 1, ORA_BAD_QUAT = 2, ORA_NOMEM = 3 };
@@ -337,6 +341,18 @@ static void pixel_ray(const ora_camera *c, int i, int j, double *d)
     d[2] = 1.0;
 }
 
+/* Sample k of pixel (i,j).  One sample: the centre.  Four samples (4x
+   multisampling, Sec. 5, which equals 4x supersampling for opaque single-
+   colour surfels): the 2x2 grid (i + 0.25 + 0.5 (k mod 2), j + 0.25 + 0.5 (k div 2)). */
+static void sample_ray(const ora_camera *c, int samples, int i, int j, int k, double *d)
+{
+    double u = i + 0.5, v = j + 0.5;
+    if (samples == 4) { u = i + 0.25 + 0.5 * (k & 1); v = j + 0.25 + 0.5 * (k >> 1); }
+    d[0] = (u - c->cx) / c->fx;
+    d[1] = (v - c->cy) / c->fy;
+    d[2] = 1.0;
+}
+
 /* Surfel fragment at a pixel: ray-plane hit depth z (camera z), local disc
    coordinates (a,b) of the hit scaled by (s1,s2), rho = a^2 + b^2.
    Returns 0 when the ray is parallel to the plane. */
@@ -438,52 +454,71 @@ static int prepare(const ora_scene *S, const ora_camera *c, const ora_opts *o, i
     return ORA_OK;
 }
 
-/* One pixel of both passes.  Writes C, D_s, surfel id, W_G, the ambiguity
-   bits and the number of Gaussians that contributed. */
+/* Pass 1 at one sample ray: the lexicographic min of (z, index) over surfels
+   whose fragment is inside the opaque disc in front of the near plane, and
+   the ambiguity flag of that decision. */
+static void zbuffer_sample(const ora_scene *S, const ora_camera *c, const ora_opts *o, const prep_t *P, int culled,
+                           int i, int j, const double *d, int64_t *best_out, double *z_out, uint8_t *amb)
+{
+    const double r2 = o->surfel_r2;
+    int64_t best = -1, second = -1;
+    double z1 = INFINITY, z2 = INFINITY, rho1 = 0.0, nd1 = 1.0, zband = INFINITY;
+    int64_t lo = 0, hi = S->n_surfels;
+    if (culled) {
+        const int64_t cell = (int64_t)(j / ORA_CELL) * P->rs.cx + i / ORA_CELL;
+        lo = P->rs.off[cell]; hi = P->rs.off[cell + 1];
+    }
+    for (int64_t t = lo; t < hi; ++t) {
+        int64_t s = culled ? P->rs.idx[t] : t;
+        const surf_t *sf = &P->sf[s];
+        if (!sf->valid) continue;
+        if (culled && (i < sf->x0 || i > sf->x1 || j < sf->y0 || j > sf->y1)) continue;
+        double z, rho, nd;
+        if (!surfel_hit(sf, d, &z, &rho, &nd)) continue;
+        if (!(z > c->znear)) continue;
+        if (fabs(rho - r2) <= o->tol_disc_rel * r2) zband = fmin(zband, z);
+        if (!(rho <= r2)) continue;
+        if (fabs(z - c->znear) <= o->tol_depth_rel * fmax(1.0, c->znear)) *amb |= AMB_ID;
+        if (z < z1 || (z == z1 && s < best)) {
+            second = best; z2 = z1;
+            best = s; z1 = z; rho1 = rho; nd1 = nd;
+        } else if (z < z2 || (z == z2 && s < second)) {
+            second = s; z2 = z;
+        }
+    }
+    if (second >= 0 && (z2 - z1) <= o->tol_depth_rel * z1) *amb |= AMB_ID;
+    if (best >= 0 && fabs(rho1 - r2) <= o->tol_disc_rel * r2) *amb |= AMB_ID;
+    if (best >= 0 && fabs(nd1) < o->tol_graze) *amb |= AMB_ID;
+    if (zband < INFINITY && (best < 0 || zband <= z1 * (1.0 + o->tol_depth_rel))) *amb |= AMB_ID;
+    *best_out = best;
+    *z_out = z1;
+}
+
+/* One pixel of both passes.  Writes C, D_s, the surfel id of every sample,
+   W_G, the ambiguity bits and the number of Gaussians that contributed.
+   With 4 samples the surfel pass is multisampled (Sec. 5): C_s is the mean
+   of the samples' colours (bg where a sample hits nothing) and D_s, for the
+   Gaussians' depth test, the nearest sample's depth; the Gaussians are
+   evaluated at the pixel centre only. */
 static void shade_pixel(const ora_scene *S, const ora_camera *c, const ora_opts *o, const prep_t *P,
                         int culled, int i, int j, double *C, double *Ds_out, int32_t *id_out,
                         double *wg_out, uint8_t *amb_out, int32_t *nc_out)
 {
-    double d[3];
-    pixel_ray(c, i, j, d);
-    const double r2 = o->surfel_r2;
-    int64_t best = -1, second = -1;
-    double z1 = INFINITY, z2 = INFINITY, rho1 = 0.0, nd1 = 1.0, zband = INFINITY;
+    const int ns = o->samples == 4 ? 4 : 1;
     uint8_t amb = 0;
-
-    /* pass 1: z-buffer of opaque surfels; lexicographic min of (z, index) */
-    if (o->mode != 2) {
-        int64_t lo = 0, hi = S->n_surfels;
-        if (culled) {
-            const int64_t cell = (int64_t)(j / ORA_CELL) * P->rs.cx + i / ORA_CELL;
-            lo = P->rs.off[cell]; hi = P->rs.off[cell + 1];
+    double Ds = INFINITY, Cs[3] = {0, 0, 0};
+    for (int k = 0; k < ns; ++k) {
+        int64_t best = -1;
+        double z = INFINITY;
+        if (o->mode != 2) {
+            double d[3];
+            sample_ray(c, ns, i, j, k, d);
+            zbuffer_sample(S, c, o, P, culled, i, j, d, &best, &z, &amb);
         }
-        for (int64_t t = lo; t < hi; ++t) {
-            int64_t s = culled ? P->rs.idx[t] : t;
-            const surf_t *sf = &P->sf[s];
-            if (!sf->valid) continue;
-            if (culled && (i < sf->x0 || i > sf->x1 || j < sf->y0 || j > sf->y1)) continue;
-            double z, rho, nd;
-            if (!surfel_hit(sf, d, &z, &rho, &nd)) continue;
-            if (!(z > c->znear)) continue;
-            if (fabs(rho - r2) <= o->tol_disc_rel * r2) zband = fmin(zband, z);
-            if (!(rho <= r2)) continue;
-            if (fabs(z - c->znear) <= o->tol_depth_rel * fmax(1.0, c->znear)) amb |= AMB_ID;
-            if (z < z1 || (z == z1 && s < best)) {
-                second = best; z2 = z1;
-                best = s; z1 = z; rho1 = rho; nd1 = nd;
-            } else if (z < z2 || (z == z2 && s < second)) {
-                second = s; z2 = z;
-            }
-        }
-        if (second >= 0 && (z2 - z1) <= o->tol_depth_rel * z1) amb |= AMB_ID;
-        if (best >= 0 && fabs(rho1 - r2) <= o->tol_disc_rel * r2) amb |= AMB_ID;
-        if (best >= 0 && fabs(nd1) < o->tol_graze) amb |= AMB_ID;
-        if (zband < INFINITY && (best < 0 || zband <= z1 * (1.0 + o->tol_depth_rel))) amb |= AMB_ID;
+        if (best >= 0) Ds = fmin(Ds, z);
+        for (int ch = 0; ch < 3; ++ch) Cs[ch] += (best >= 0 ? P->sf[best].rgb[ch] : c->bg[ch]) / ns;
+        id_out[k] = (int32_t)best;
     }
-    double Ds = best >= 0 ? z1 : INFINITY;
-    double Cs[3];
-    for (int ch = 0; ch < 3; ++ch) Cs[ch] = best >= 0 ? P->sf[best].rgb[ch] : c->bg[ch];
 
     /* pass 2: order-independent accumulation (Eq. 2-4) */
     double CG[3] = {0, 0, 0}, WG = 0.0;
@@ -520,7 +555,6 @@ static void shade_pixel(const ora_scene *S, const ora_camera *c, const ora_opts 
         else C[ch] = WG > 0.0 ? CG[ch] / WG : c->bg[ch];
     }
     *Ds_out = Ds;
-    *id_out = (int32_t)best;
     *wg_out = WG;
     *amb_out = amb;
     *nc_out = nc;
@@ -533,6 +567,7 @@ static int check_args(const ora_scene *S, const ora_camera *c, const ora_opts *o
     if (S->sh_degree < 0 || S->sh_degree > 3) return 0;
     if (S->n_surfels < 0 || S->n_gaussians < 0) return 0;
     if (!(c->fx > 0 && c->fy > 0 && c->znear > 0)) return 0;
+    if (o->samples != 1 && o->samples != 4) return 0;
     return 1;
 }
 
@@ -553,12 +588,12 @@ int ora_render(const ora_scene *S, const ora_camera *c, const ora_opts *o, int c
         for (int i = 0; i < W; ++i) {
             int64_t pix = (int64_t)j * W + i;
             double C[3], Ds, WG;
-            int32_t id, nc;
+            int32_t id[4], nc;
             uint8_t a;
-            shade_pixel(S, c, o, &P, culled, i, j, C, &Ds, &id, &WG, &a, &nc);
+            shade_pixel(S, c, o, &P, culled, i, j, C, &Ds, id, &WG, &a, &nc);
             for (int ch = 0; ch < 3; ++ch) rgb[ch * HW + pix] = C[ch];
             depth[pix] = Ds;
-            sid[pix] = id;
+            for (int k = 0; k < (o->samples == 4 ? 4 : 1); ++k) sid[k * HW + pix] = id[k];
             wg[pix] = WG;
             amb[pix] = a;
             if (ncontrib) ncontrib[pix] = nc;
@@ -568,7 +603,7 @@ int ora_render(const ora_scene *S, const ora_camera *c, const ora_opts *o, int c
     return ORA_OK;
 }
 
-/* Work counts: (pixel, surfel) fragments inside the opaque disc in front of
+/* Work counts: (sample, surfel) fragments inside the opaque disc in front of
    the near plane, and (pixel, Gaussian) pairs with alpha >= alpha_min. */
 int ora_count_fragments(const ora_scene *S, const ora_camera *c, const ora_opts *o, int64_t *n_surf,
                         int64_t *n_gauss)
@@ -583,14 +618,17 @@ int ora_count_fragments(const ora_scene *S, const ora_camera *c, const ora_opts 
     for (int j = 0; j < H; ++j) {
         for (int i = 0; i < W; ++i) {
             const int64_t cell = (int64_t)(j / ORA_CELL) * P.rs.cx + i / ORA_CELL;
-            double d[3];
-            pixel_ray(c, i, j, d);
+            const int nsamp = o->samples == 4 ? 4 : 1;
             if (o->mode != 2)
-                for (int64_t t = P.rs.off[cell]; t < P.rs.off[cell + 1]; ++t) {
-                    const surf_t *sf = &P.sf[P.rs.idx[t]];
-                    if (!sf->valid || i < sf->x0 || i > sf->x1 || j < sf->y0 || j > sf->y1) continue;
-                    double z, rho;
-                    if (surfel_hit(sf, d, &z, &rho, NULL) && z > c->znear && rho <= o->surfel_r2) ++ns;
+                for (int k = 0; k < nsamp; ++k) {
+                    double d[3];
+                    sample_ray(c, nsamp, i, j, k, d);
+                    for (int64_t t = P.rs.off[cell]; t < P.rs.off[cell + 1]; ++t) {
+                        const surf_t *sf = &P.sf[P.rs.idx[t]];
+                        if (!sf->valid || i < sf->x0 || i > sf->x1 || j < sf->y0 || j > sf->y1) continue;
+                        double z, rho;
+                        if (surfel_hit(sf, d, &z, &rho, NULL) && z > c->znear && rho <= o->surfel_r2) ++ns;
+                    }
                 }
             if (o->mode != 1)
                 for (int64_t t = P.rg.off[cell]; t < P.rg.off[cell + 1]; ++t) {
@@ -629,7 +667,8 @@ int ora_surfel_eval(const ora_scene *S, const ora_camera *c, const ora_opts *o, 
     return ORA_OK;
 }
 
-/* Is ids[pix] an acceptable z-buffer answer at each pixel?  The exact answer
+/* Is ids[pix] an acceptable z-buffer answer at each pixel (each sample:
+   ids and valid are [samples, H, W])?  The exact answer
    is the lexicographic min of (z, index) over surfels whose fragment is inside
    its disc in front of the near plane; where fragments sit within the bands
    (disc rim |rho - r2| <= tol_disc r2, depth gap <= tol_depth z) several
@@ -646,15 +685,17 @@ int ora_check_ids(const ora_scene *S, const ora_camera *c, const ora_opts *o, co
     prep_t P;
     int st = prepare(S, c, o, 1, &P);
     if (st != ORA_OK) { prep_free(&P); return st; }
-    const int W = c->width, H = c->height;
+    const int W = c->width, H = c->height, nsamp = o->samples == 4 ? 4 : 1;
+    const int64_t HW = (int64_t)W * H;
     const double r2 = o->surfel_r2, td = o->tol_depth_rel, tr = o->tol_disc_rel;
 #pragma omp parallel for schedule(dynamic, 1)
-    for (int j = 0; j < H; ++j) {
+    for (int jk = 0; jk < H * nsamp; ++jk) {
+        const int j = jk % H, smp = jk / H;
         for (int i = 0; i < W; ++i) {
-            const int64_t pix = (int64_t)j * W + i;
+            const int64_t pix = smp * HW + (int64_t)j * W + i;
             const int32_t s = ids[pix];
             double d[3];
-            pixel_ray(c, i, j, d);
+            sample_ray(c, nsamp, i, j, smp, d);
             double zs = INFINITY;
             int ok = 1;
             if (s >= 0) {
@@ -702,10 +743,14 @@ int ora_touching(const ora_scene *S, const ora_camera *c, const ora_opts *o, con
         for (int j = sf->y0; j <= sf->y1 && !s_touch[s]; ++j)
             for (int i = sf->x0; i <= sf->x1; ++i) {
                 if (!flag[(int64_t)j * W + i]) continue;
-                double d[3], z, rho;
-                pixel_ray(c, i, j, d);
-                if (surfel_hit(sf, d, &z, &rho, NULL) && z > c->znear &&
-                    rho <= o->surfel_r2 * (1.0 + o->tol_disc_rel)) { s_touch[s] = 1; break; }
+                const int nsamp = o->samples == 4 ? 4 : 1;
+                for (int k = 0; k < nsamp && !s_touch[s]; ++k) {
+                    double d[3], z, rho;
+                    sample_ray(c, nsamp, i, j, k, d);
+                    if (surfel_hit(sf, d, &z, &rho, NULL) && z > c->znear &&
+                        rho <= o->surfel_r2 * (1.0 + o->tol_disc_rel)) s_touch[s] = 1;
+                }
+                if (s_touch[s]) break;
             }
     }
 #pragma omp parallel for schedule(dynamic, 256)
@@ -796,7 +841,8 @@ int ora_backward(const ora_scene *S, const ora_camera *c, const ora_opts *o, int
     const int K = (S->sh_degree + 1) * (S->sh_degree + 1);
     double *rgb = malloc(sizeof(double) * 3 * (size_t)HW), *Ds = malloc(sizeof(double) * (size_t)HW);
     double *WG = malloc(sizeof(double) * (size_t)HW);
-    int32_t *sid = malloc(sizeof(int32_t) * (size_t)HW);
+    const int nsamp = o->samples == 4 ? 4 : 1;
+    int32_t *sid = malloc(sizeof(int32_t) * (size_t)HW * nsamp);
     uint8_t *amb = malloc((size_t)HW);
     double *gcs = calloc((size_t)(N > 0 ? N : 1) * 3, sizeof(double));
     if (!rgb || !Ds || !WG || !sid || !amb || !gcs) {
@@ -811,14 +857,16 @@ int ora_backward(const ora_scene *S, const ora_camera *c, const ora_opts *o, int
     double Rc[9];
     cam_rot(c, Rc);
 
-    /* surfel colours: C depends on c_s through C_s at pixels the surfel wins */
+    /* surfel colours: C depends on c_s through C_s at the samples the surfel
+       wins, each weighing 1/samples in the resolve */
     if (o->mode != 2) {
-        for (int64_t pix = 0; pix < HW; ++pix) {
-            int32_t s = sid[pix];
-            if (s < 0) continue;
-            double k = o->mode == 0 ? 1.0 / (1.0 + WG[pix]) : 1.0;
-            for (int ch = 0; ch < 3; ++ch) gcs[3*s + ch] += k * dL_drgb[ch * HW + pix];
-        }
+        for (int smp = 0; smp < nsamp; ++smp)
+            for (int64_t pix = 0; pix < HW; ++pix) {
+                int32_t s = sid[smp * HW + pix];
+                if (s < 0) continue;
+                double k = (o->mode == 0 ? 1.0 / (1.0 + WG[pix]) : 1.0) / nsamp;
+                for (int ch = 0; ch < 3; ++ch) gcs[3*s + ch] += k * dL_drgb[ch * HW + pix];
+            }
     }
     memset(gs_sh, 0, sizeof(double) * 3 * (size_t)K * (size_t)N);
 #pragma omp parallel for schedule(static)

@@ -27,7 +27,7 @@ _lib = None
 DEFAULT_OPTS = dict(eps_mode=0, eps_value=0.1, eps_factor=5.0, lowpass=0.3,
                     alpha_min=1.0 / 255.0, surfel_r2=2.0 * math.log(255.0), mode=0,
                     tol_depth_rel=1e-6, tol_disc_rel=1e-5, tol_graze=1e-3, tol_alpha=1e-5,
-                    tol_gdepth_rel=2e-6)
+                    tol_gdepth_rel=2e-6, samples=1)
 
 
 class _Scene(C.Structure):
@@ -46,7 +46,8 @@ class _Opts(C.Structure):
     _fields_ = [("eps_mode", C.c_int32), ("eps_value", C.c_double), ("eps_factor", C.c_double),
                 ("lowpass", C.c_double), ("alpha_min", C.c_double), ("surfel_r2", C.c_double),
                 ("mode", C.c_int32), ("tol_depth_rel", C.c_double), ("tol_disc_rel", C.c_double),
-                ("tol_graze", C.c_double), ("tol_alpha", C.c_double), ("tol_gdepth_rel", C.c_double)]
+                ("tol_graze", C.c_double), ("tol_alpha", C.c_double), ("tol_gdepth_rel", C.c_double),
+                ("samples", C.c_int32)]
 
 
 def build(force: bool = False) -> str:
@@ -108,12 +109,17 @@ def _check(st, what):
 
 def render(scene, cam, opts=None, culled: bool = True, nthreads: int = 0):
     """FP64 render: rgb [3,H,W], depth [H,W] (+inf where no surfel), id [H,W]
-    (-1), wg [H,W] (W_G), amb [H,W] (bit 1: id/depth ambiguous, bit 2:
-    colour ambiguous) and ncontrib [H,W] (Gaussians that contributed)."""
+    (-1; [4,H,W], one plane per sample, with ``samples=4``), wg [H,W] (W_G),
+    amb [H,W] (bit 1: id/depth ambiguous at some sample, bit 2: colour
+    ambiguous) and ncontrib [H,W] (Gaussians that contributed)."""
     lib = load()
     pin = _Pinned(scene, cam, opts)
     H, W = cam.height, cam.width
-    out = dict(rgb=np.empty((3, H, W)), depth=np.empty((H, W)), id=np.empty((H, W), np.int32),
+    ns = int(pin.o.samples)
+    if ns not in (1, 4):
+        raise ValueError("samples must be 1 or 4")
+    out = dict(rgb=np.empty((3, H, W)), depth=np.empty((H, W)),
+               id=np.empty((H, W) if ns == 1 else (4, H, W), np.int32),
                wg=np.empty((H, W)), amb=np.empty((H, W), np.uint8), ncontrib=np.empty((H, W), np.int32))
     st = lib.ora_render(C.byref(pin.s), C.byref(pin.c), C.byref(pin.o), int(culled), int(nthreads),
                         *[out[k].ctypes.data for k in ("rgb", "depth", "id", "wg", "amb", "ncontrib")])
