@@ -119,6 +119,10 @@ typedef struct {
     float alpha_min;              /* 1/255 (Sec. 3, after Eq. 4) */
     float surfel_r2;              /* 2 ln 255 (Sec. 4.1) */
     int32_t mode;                 /* ges_mode */
+    int32_t samples;              /* surfel samples per pixel: 1 (the pixel centre, default) or 4
+                                     (4x multisampling of the surfel pass, Sec. 5: samples on the
+                                     2x2 grid at +-0.25 px, colour = their mean, D_s = the nearest
+                                     covered sample's depth; Gaussians stay at the centre) */
 } ges_render_opts;
 
 /* Gradient outputs (DEVICE pointers, float32, overwritten, not accumulated).
@@ -177,9 +181,10 @@ GES_API ges_status ges_set_stream(ges_scene *scene, void *stream);
  * checks the device status word). */
 GES_API ges_status ges_render(ges_scene *scene, const ges_camera *cam, float *out_rgb, float *out_depth);
 
-/* As ges_render with options and two optional outputs: out_surfel_id [H,W]
- * (z-buffer winner, -1 where none) and aux [H,W] (W_G of Eq. 3).  The
- * backward pass needs both.  opts may be NULL (defaults). */
+/* As ges_render with options and two optional outputs: out_surfel_id
+ * [samples,H,W] (z-buffer winner of each sample, -1 where none) and aux [H,W]
+ * (W_G of Eq. 3).  The backward pass needs both.  opts may be NULL
+ * (defaults); samples other than 1 or 4 is GES_ERR_INVALID_ARG. */
 GES_API ges_status ges_render_ex(ges_scene *scene, const ges_camera *cam, const ges_render_opts *opts,
                          float *out_rgb, float *out_depth, int32_t *out_surfel_id, float *aux);
 

@@ -176,6 +176,7 @@ ges_status make_opts(const ges_render_opts *o, OptParams &O)
     if (!(o->lowpass >= 0.f) || !std::isfinite(o->lowpass)) return fail(GES_ERR_INVALID_ARG, "lowpass must be >= 0");
     if (!std::isfinite(o->eps_factor) || !std::isfinite(o->eps_value))
         return fail(GES_ERR_INVALID_ARG, "eps parameters must be finite");
+    if (o->samples != 1 && o->samples != 4) return fail(GES_ERR_INVALID_ARG, "samples must be 1 or 4, not %d", o->samples);
     O.eps_mode = o->eps_mode;
     O.eps_value = o->eps_value;
     O.eps_factor = o->eps_factor;
@@ -184,6 +185,7 @@ ges_status make_opts(const ges_render_opts *o, OptParams &O)
     O.surfel_r2 = o->surfel_r2;
     O.surfel_r = std::sqrt(o->surfel_r2);
     O.mode = o->mode;
+    O.samples = o->samples;
     return GES_OK;
 }
 
@@ -359,6 +361,7 @@ ges_status ges_default_opts(ges_render_opts *out)
     out->alpha_min = 1.f / 255.f;
     out->surfel_r2 = (float)(2.0 * std::log(255.0));
     out->mode = GES_MODE_FULL;
+    out->samples = 1;
     return GES_OK;
 }
 
@@ -707,7 +710,8 @@ ges_status ges_batch_create(ges_scene *const *scenes, const ges_camera *cams, co
     float best_ms = 1e30f;
     int cand = 0;
     for (int64_t R : kR) {
-        for (int per_sm : {4, 5}) {
+        // resident raster CTAs per SM: the 4-sample kernel is built for one fewer
+        for (int per_sm : {O.samples == 4 ? 3 : 4, O.samples == 4 ? 4 : 5}) {
             batch_layout(b, S, C, R, (unsigned char *)b->arena);
             BatchPlan P{n_views, 0, 0, 0, 0, sms * per_sm};
             for (int v = 0; v < n_views; ++v) {

@@ -34,7 +34,7 @@ __device__ __forceinline__ float warp_sum(float x)
 
 
 struct GLoop {
-    float px, py, pxl, pyl, ca, cb, cc, sigma, key, r, g, b, ia, ib, ic;
+    float px, py, pxl, pyl, la, lb, lc, sigma, key, r, g, b, ia, ib, ic;
     int x0, y0, x1, y1;
 };
 
@@ -48,7 +48,7 @@ __device__ __forceinline__ void gauss_pixel(const GLoop &s, int x, int y, const 
     const int64_t HW = (int64_t)C.W * C.H, pix = (int64_t)y * C.W + x;
     GaussRec g;
     g.px = s.px; g.py = s.py; g.pxl = s.pxl; g.pyl = s.pyl;
-    g.ca = s.ca; g.cb = s.cb; g.cc = s.cc; g.sigma = s.sigma;
+    g.la = s.la; g.lb = s.lb; g.lc = s.lc; g.sigma = s.sigma;
     float e;
     const float a = gauss_alpha(g, x + 0.5f, y + 0.5f, e);
     if (!(a >= O.alpha_min) || !(s.key < __ldg(depth + pix))) return;
@@ -63,8 +63,13 @@ __device__ __forceinline__ void gauss_pixel(const GLoop &s, int x, int y, const 
     acc[3] += dLda * e;
     const float dLdq = -0.5f * dLda * a;
     const float dx = (x + 0.5f - s.px) - s.pxl, dy = (y + 0.5f - s.py) - s.pyl;
-    acc[4] += dLdq * -2.f * (s.ia * dx + s.ib * dy);
-    acc[5] += dLdq * -2.f * (s.ib * dx + s.ic * dy);
+    // dq/d(px, py) = -2 Sigma2^-1 (dx, dy), from the Cholesky form (accurate far
+    // from the centre): Sigma2^-1 d = (a y0 + b y1, c y1) with the record's
+    // factors scaled by kL, hence the 1/kL^2
+    const float kL2 = 0.72134752044448170f;   // log2(e) / 2
+    const float y0 = s.la * dx, y1 = fmaf(s.lb, dx, s.lc * dy);
+    acc[4] += dLdq * -2.f * fmaf(s.la, y0, s.lb * y1) / kL2;
+    acc[5] += dLdq * -2.f * (s.lc * y1) / kL2;
     acc[6] += dLdq * dx * dx;
     acc[7] += dLdq * 2.f * dx * dy;
     acc[8] += dLdq * dy * dy;
@@ -89,7 +94,7 @@ __global__ void __launch_bounds__(256) k_gauss_bwd(SceneView S, CamParams C, Opt
         gauss_setup(S, C, O, gi, o);
         vis = o.visible;
         if (vis) {
-            s = GLoop{o.rec.px, o.rec.py, o.rec.pxl, o.rec.pyl, o.rec.ca, o.rec.cb, o.rec.cc, o.rec.sigma,
+            s = GLoop{o.rec.px, o.rec.py, o.rec.pxl, o.rec.pyl, o.rec.la, o.rec.lb, o.rec.lc, o.rec.sigma,
                       o.rec.key, o.rec.r, o.rec.g, o.rec.b, o.ia, o.ib, o.ic, o.x0, o.y0, o.x1, o.y1};
         }
     }
@@ -102,7 +107,7 @@ __global__ void __launch_bounds__(256) k_gauss_bwd(SceneView S, CamParams C, Opt
         big &= big - 1;
         GLoop t;
         t.px = shfl_f(s.px, j); t.py = shfl_f(s.py, j); t.pxl = shfl_f(s.pxl, j); t.pyl = shfl_f(s.pyl, j);
-        t.ca = shfl_f(s.ca, j); t.cb = shfl_f(s.cb, j); t.cc = shfl_f(s.cc, j); t.sigma = shfl_f(s.sigma, j);
+        t.la = shfl_f(s.la, j); t.lb = shfl_f(s.lb, j); t.lc = shfl_f(s.lc, j); t.sigma = shfl_f(s.sigma, j);
         t.key = shfl_f(s.key, j); t.r = shfl_f(s.r, j); t.g = shfl_f(s.g, j); t.b = shfl_f(s.b, j);
         t.ia = shfl_f(s.ia, j); t.ib = shfl_f(s.ib, j); t.ic = shfl_f(s.ic, j);
         t.x0 = shfl_i(s.x0, j); t.y0 = shfl_i(s.y0, j); t.x1 = shfl_i(s.x1, j); t.y1 = shfl_i(s.y1, j);
@@ -238,8 +243,8 @@ __global__ void __launch_bounds__(256) k_surfel_bwd(SceneView S, CamParams C, Op
     int x0 = 0, y0 = 0, x1 = -1, y1 = -1;
     if (vis) { x0 = o.x0; y0 = o.y0; x1 = o.x1; y1 = o.y1; }
     float acc[3] = {0.f, 0.f, 0.f};
-    // dL/dc_s = sum over the pixels s won of k g (k = 1/(1+W_G), or 1 with
-    // surfels only); the warp sweeps one surfel's bbox at a time
+    // dL/dc_s = sum over the samples s won of k g / samples (k = 1/(1+W_G),
+    // or 1 with surfels only); the warp sweeps one surfel's bbox at a time
     unsigned big = __ballot_sync(0xffffffffu, vis);
     while (big) {
         const int j = __ffs(big) - 1;
@@ -250,8 +255,11 @@ __global__ void __launch_bounds__(256) k_surfel_bwd(SceneView S, CamParams C, Op
         float part[3] = {0.f, 0.f, 0.f};
         for (int k = lane; k < n; k += 32) {
             const int64_t pix = (int64_t)(by0 + k / w) * C.W + bx0 + k % w;
-            if (__ldg(sid + pix) != want) continue;
-            const float kk = full ? 1.f / (1.f + __ldg(aux + pix)) : 1.f;
+            // with 4 samples each won sample carries a quarter of the pixel
+            int won = 0;
+            for (int q = 0; q < O.samples; ++q) won += __ldg(sid + q * HW + pix) == want;
+            if (won == 0) continue;
+            const float kk = (full ? 1.f / (1.f + __ldg(aux + pix)) : 1.f) * (float)won / (float)O.samples;
             part[0] += kk * __ldg(dL + pix);
             part[1] += kk * __ldg(dL + HW + pix);
             part[2] += kk * __ldg(dL + 2 * HW + pix);

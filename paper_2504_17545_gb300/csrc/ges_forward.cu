@@ -351,7 +351,9 @@ __device__ __forceinline__ void stage_rec(float4 (*st)[kChunk], const float4 *re
 // One 16x16 tile.  ss/sgs: shared staging for surfel and Gaussian records,
 // structure-of-arrays (one float4 plane per 16-byte quarter): consecutive
 // threads store consecutive 16 B, and a warp reading one record gets a
-// broadcast.
+// broadcast.  kS surfel samples per pixel: 1 (the centre) or 4 (the 2x2 grid
+// at +-0.25 px, 4x multisampling of Sec. 5; the Gaussians stay at the centre).
+template <int kS>
 __device__ __forceinline__ void raster_tile(const ViewScratch &X, const CamParams &C, const OptParams &O,
                                             float *__restrict__ out_rgb, float *__restrict__ out_depth,
                                             int32_t *__restrict__ out_id, float *__restrict__ aux, int tile,
@@ -365,6 +367,8 @@ __device__ __forceinline__ void raster_tile(const ViewScratch &X, const CamParam
     const int px = wx0 + (int)(lane & 7), py = wy0 + (int)(lane >> 3);
     const bool in_img = px < C.W && py < C.H;
     const float u = px + 0.5f, v = py + 0.5f;
+    // sample k sits at (us + 0.5 (k & 1), vs + 0.5 (k >> 1))
+    const float us = kS == 4 ? px + 0.25f : u, vs = kS == 4 ? py + 0.25f : v;
     const bool do_s = O.mode != GES_MODE_GAUSSIANS_ONLY, do_g = O.mode != GES_MODE_SURFELS_ONLY;
     const int s0 = do_s ? X.s_off[tile] : 0, s1 = do_s ? X.s_off[tile + 1] : 0;
     const int g0 = do_g ? X.g_off[tile] : 0, g1 = do_g ? X.g_off[tile + 1] : 0;
@@ -380,9 +384,11 @@ __device__ __forceinline__ void raster_tile(const ViewScratch &X, const CamParam
     // 1/z over the disc (izmax) is below every 1/z its pixels already hold
     // (it cannot win anywhere in the block).  Survivors are tested two at a
     // time; the lexicographic (depth, id) min does not depend on the order.
-    float best = in_img ? 0.f : INFINITY;   // 1/z of the nearest hit (0: none)
-    int bid = 0x7fffffff;
-    float wmin = 0.f;                        // smallest 'best' over the warp's pixels
+    float best[kS];                          // per sample: 1/z of the nearest hit (0: none)
+    int bid[kS];
+#pragma unroll
+    for (int k = 0; k < kS; ++k) { best[k] = in_img ? 0.f : INFINITY; bid[k] = 0x7fffffff; }
+    float wmin = 0.f;                        // smallest 'best' over the warp's samples
     for (int base = s0; base < s1; base += kChunk) {
         if (base != s0) {
             __syncthreads();
@@ -409,32 +415,55 @@ __device__ __forceinline__ void raster_tile(const ViewScratch &X, const CamParam
                     const float4 a2 = ss[2][ja], b2 = ss[2][jb];
                     const float4 a0 = ss[0][ja], a1 = ss[1][ja], b0 = ss[0][jb], b1 = ss[1][jb];
                     const int ida = __float_as_int(ss[3][ja].x), idb = __float_as_int(ss[3][jb].x);
-                    const float dua = u - a0.x, dva = v - a0.y, dub = u - b0.x, dvb = v - b0.y;
-                    const float iza = fmaf(a0.w, dua, fmaf(a1.x, dva, a0.z));
-                    const float izb = fmaf(b0.w, dub, fmaf(b1.x, dvb, b0.z));
-                    const float Aa = fmaf(a1.y, dua, fmaf(a1.z, dva, a1.w));
-                    const float Ab = fmaf(b1.y, dub, fmaf(b1.z, dvb, b1.w));
-                    const float Ba = fmaf(a2.x, dua, fmaf(a2.y, dva, a2.z));
-                    const float Bb = fmaf(b2.x, dub, fmaf(b2.y, dvb, b2.z));
-                    const float qa = fmaf(Aa, Aa, fmaf(Ba, Ba, -iza * iza));
-                    const float qb = fmaf(Ab, Ab, fmaf(Bb, Bb, -izb * izb));
-                    const bool ina = qa <= 0.f && iza < C.izn, inb = qb <= 0.f && izb < C.izn && two;
-                    if (ina && (iza > best || (iza == best && ida < bid))) { best = iza; bid = ida; }
-                    if (inb && (izb > best || (izb == best && idb < bid))) { best = izb; bid = idb; }
+#pragma unroll
+                    for (int k = 0; k < kS; ++k) {
+                        const float uk = us + 0.5f * (k & 1), vk = vs + 0.5f * (k >> 1);
+                        const float dua = uk - a0.x, dva = vk - a0.y, dub = uk - b0.x, dvb = vk - b0.y;
+                        const float iza = fmaf(a0.w, dua, fmaf(a1.x, dva, a0.z));
+                        const float izb = fmaf(b0.w, dub, fmaf(b1.x, dvb, b0.z));
+                        const float Aa = fmaf(a1.y, dua, fmaf(a1.z, dva, a1.w));
+                        const float Ab = fmaf(b1.y, dub, fmaf(b1.z, dvb, b1.w));
+                        const float Ba = fmaf(a2.x, dua, fmaf(a2.y, dva, a2.z));
+                        const float Bb = fmaf(b2.x, dub, fmaf(b2.y, dvb, b2.z));
+                        const float qa = fmaf(Aa, Aa, fmaf(Ba, Ba, -iza * iza));
+                        const float qb = fmaf(Ab, Ab, fmaf(Bb, Bb, -izb * izb));
+                        const bool ina = qa <= 0.f && iza < C.izn, inb = qb <= 0.f && izb < C.izn && two;
+                        if (ina && (iza > best[k] || (iza == best[k] && ida < bid[k]))) { best[k] = iza; bid[k] = ida; }
+                        if (inb && (izb > best[k] || (izb == best[k] && idb < bid[k]))) { best[k] = izb; bid[k] = idb; }
+                    }
                 }
                 // the warp's depth bound is refreshed once per group of 32
                 // entries: per-survivor refreshes and re-checks cost more
                 // instructions than they cull
-                wmin = __uint_as_float(__reduce_min_sync(0xffffffffu, __float_as_uint(best)));
+                float bmin = best[0];
+#pragma unroll
+                for (int k = 1; k < kS; ++k) bmin = fminf(bmin, best[k]);
+                wmin = __uint_as_float(__reduce_min_sync(0xffffffffu, __float_as_uint(bmin)));
             }
         }
     }
-    const bool covered = bid != 0x7fffffff;
-    const float Ds = covered ? 1.f / best : INFINITY;
-    float Cs[3] = {C.bg[0], C.bg[1], C.bg[2]};
-    if (covered) {
-        const float4 c = X.s_rgb[bid];
-        Cs[0] = c.x; Cs[1] = c.y; Cs[2] = c.z;
+    // resolve: C_s is the mean of the samples' colours (background where a
+    // sample hits nothing), D_s the nearest sample's depth
+    float bmax = best[0];
+#pragma unroll
+    for (int k = 1; k < kS; ++k) bmax = fmaxf(bmax, best[k]);
+    const float Ds = bmax > 0.f ? 1.f / bmax : INFINITY;
+    float Cs[3];
+    if (kS == 1) {
+        Cs[0] = C.bg[0]; Cs[1] = C.bg[1]; Cs[2] = C.bg[2];
+        if (bid[0] != 0x7fffffff) {
+            const float4 c = X.s_rgb[bid[0]];
+            Cs[0] = c.x; Cs[1] = c.y; Cs[2] = c.z;
+        }
+    } else {
+        float sr = 0.f, sgc = 0.f, sb = 0.f;
+#pragma unroll
+        for (int k = 0; k < kS; ++k) {
+            float4 c = make_float4(C.bg[0], C.bg[1], C.bg[2], 0.f);
+            if (in_img && bid[k] != 0x7fffffff) c = X.s_rgb[bid[k]];
+            sr += c.x; sgc += c.y; sb += c.z;
+        }
+        Cs[0] = sr * (1.f / kS); Cs[1] = sgc * (1.f / kS); Cs[2] = sb * (1.f / kS);
     }
 
     // ---------------- pass 2: Gaussians (Eq. 2-4) ----------------
@@ -464,7 +493,7 @@ __device__ __forceinline__ void raster_tile(const ViewScratch &X, const CamParam
                     mask &= mask - 1;
                     GaussRec g;
                     *reinterpret_cast<float4 *>(&g.px) = sgs[0][jj];
-                    *reinterpret_cast<float4 *>(&g.ca) = sgs[1][jj];
+                    *reinterpret_cast<float4 *>(&g.la) = sgs[1][jj];
                     *reinterpret_cast<float4 *>(&g.key) = sgs[2][jj];
                     float e;
                     const float a = gauss_alpha(g, u, v, e);
@@ -500,11 +529,15 @@ __device__ __forceinline__ void raster_tile(const ViewScratch &X, const CamParam
     out_rgb[HW + pix] = out[1];
     out_rgb[2 * HW + pix] = out[2];
     if (out_depth) out_depth[pix] = Ds;
-    if (out_id) out_id[pix] = covered ? bid : -1;
+    if (out_id) {
+#pragma unroll
+        for (int k = 0; k < kS; ++k) out_id[k * HW + pix] = bid[k] != 0x7fffffff ? bid[k] : -1;
+    }
     if (aux) aux[pix] = WG;
 }
 
-__global__ void __launch_bounds__(kRasterThreads, 5) k_raster(ViewScratch X, CamParams C, OptParams O,
+template <int kS>
+__global__ void __launch_bounds__(kRasterThreads, kS == 1 ? 5 : 4) k_raster(ViewScratch X, CamParams C, OptParams O,
                                                            float *__restrict__ out_rgb,
                                                            float *__restrict__ out_depth,
                                                            int32_t *__restrict__ out_id,
@@ -513,7 +546,7 @@ __global__ void __launch_bounds__(kRasterThreads, 5) k_raster(ViewScratch X, Cam
     __shared__ float4 ss[4][kChunk];
     __shared__ float4 sgs[4][kChunk];
     if (X.status[ST_FLAGS] & (FLAG_SOVF | FLAG_GOVF)) return;
-    raster_tile(X, C, O, out_rgb, out_depth, out_id, aux, blockIdx.x, ss, sgs);
+    raster_tile<kS>(X, C, O, out_rgb, out_depth, out_id, aux, blockIdx.x, ss, sgs);
 }
 
 // ---------------------------------------------------------------------------
@@ -592,7 +625,8 @@ __global__ void __launch_bounds__(kFillThreads) k_bfill(const BatchView *V, int 
 // Persistent raster over the (view, tile) items of the whole batch: each CTA
 // takes the next item from a counter until none is left, so uneven views
 // balance across the GPU.
-__global__ void __launch_bounds__(kRasterThreads, 5) k_braster(const BatchView *V, int n, OptParams O,
+template <int kS>
+__global__ void __launch_bounds__(kRasterThreads, kS == 1 ? 5 : 4) k_braster(const BatchView *V, int n, OptParams O,
                                                             unsigned *counter, int total)
 {
     __shared__ float4 ss[4][kChunk];
@@ -615,7 +649,7 @@ __global__ void __launch_bounds__(kRasterThreads, 5) k_braster(const BatchView *
         }
         __syncthreads();
         if (!(bv.X.status[ST_FLAGS] & (FLAG_SOVF | FLAG_GOVF)))
-            raster_tile(bv.X, bv.C, O, bv.rgb, bv.depth, nullptr, nullptr, it - bv.tile_base, ss, sgs);
+            raster_tile<kS>(bv.X, bv.C, O, bv.rgb, bv.depth, nullptr, nullptr, it - bv.tile_base, ss, sgs);
         __syncthreads();
     }
 }
@@ -637,7 +671,10 @@ cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const Opt
     if (P.total_prep > 0)
         k_bfill<<<P.total_prep, kFillThreads, local_bins_smem(P.max_T, true), st>>>(d_views, P.n);
     mark(3);
-    k_braster<<<P.raster_ctas, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
+    if (O.samples == 4)
+        k_braster<4><<<P.raster_ctas, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
+    else
+        k_braster<1><<<P.raster_ctas, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
     mark(4);
     return cudaGetLastError();
 }
@@ -696,7 +733,7 @@ cudaError_t launch_binning(const SceneView &S, const CamParams &C, const OptPara
     return cudaGetLastError();
 }
 
-// Exact work counts of one view: every (pixel, surfel) fragment inside the
+// Exact work counts of one view: every (sample, surfel) fragment inside the
 // opaque disc in front of the near plane, and every (pixel, Gaussian) pair
 // with alpha >= alpha_min, over the full tile lists (no culling).
 __global__ void __launch_bounds__(256) k_count(ViewScratch X, CamParams C, OptParams O)
@@ -726,15 +763,19 @@ __global__ void __launch_bounds__(256) k_count(ViewScratch X, CamParams C, OptPa
             for (int j = 0; j < n; ++j) {
                 if (kind == 0) {
                     const float4 r0 = st[0][j], r1 = st[1][j], r2 = st[2][j];
-                    const float du = u - r0.x, dv = v - r0.y;
-                    const float iz = fmaf(r0.w, du, fmaf(r1.x, dv, r0.z));
-                    const float A = fmaf(r1.y, du, fmaf(r1.z, dv, r1.w));
-                    const float B = fmaf(r2.x, du, fmaf(r2.y, dv, r2.z));
-                    ns += (fmaf(A, A, fmaf(B, B, -iz * iz)) <= 0.f && iz > 0.f && iz < C.izn) ? 1u : 0u;
+                    for (int k = 0; k < O.samples; ++k) {
+                        const float uk = O.samples == 4 ? px + 0.25f + 0.5f * (k & 1) : u;
+                        const float vk = O.samples == 4 ? py + 0.25f + 0.5f * (k >> 1) : v;
+                        const float du = uk - r0.x, dv = vk - r0.y;
+                        const float iz = fmaf(r0.w, du, fmaf(r1.x, dv, r0.z));
+                        const float A = fmaf(r1.y, du, fmaf(r1.z, dv, r1.w));
+                        const float B = fmaf(r2.x, du, fmaf(r2.y, dv, r2.z));
+                        ns += (fmaf(A, A, fmaf(B, B, -iz * iz)) <= 0.f && iz > 0.f && iz < C.izn) ? 1u : 0u;
+                    }
                 } else {
                     GaussRec g;
                     *reinterpret_cast<float4 *>(&g.px) = st[0][j];
-                    *reinterpret_cast<float4 *>(&g.ca) = st[1][j];
+                    *reinterpret_cast<float4 *>(&g.la) = st[1][j];
                     float e;
                     ng += gauss_alpha(g, u, v, e) >= O.alpha_min ? 1u : 0u;
                 }
@@ -762,7 +803,10 @@ cudaError_t launch_forward(const SceneView &S, const CamParams &C, const OptPara
 {
     cudaError_t e = launch_binning(S, C, O, X, st, ev);
     if (e != cudaSuccess) return e;
-    k_raster<<<C.tiles_x * C.tiles_y, kRasterThreads, 0, st>>>(X, C, O, out_rgb, out_depth, out_id, aux);
+    if (O.samples == 4)
+        k_raster<4><<<C.tiles_x * C.tiles_y, kRasterThreads, 0, st>>>(X, C, O, out_rgb, out_depth, out_id, aux);
+    else
+        k_raster<1><<<C.tiles_x * C.tiles_y, kRasterThreads, 0, st>>>(X, C, O, out_rgb, out_depth, out_id, aux);
     if (ev) cudaEventRecord(ev[4], st);
     return cudaGetLastError();
 }

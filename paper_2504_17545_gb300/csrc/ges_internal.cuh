@@ -46,6 +46,7 @@ struct OptParams {
     int eps_mode;
     float eps_value, eps_factor, lowpass, alpha_min, surfel_r2, surfel_r;
     int mode;
+    int samples;          // surfel samples per pixel: 1 or 4
 };
 
 struct SceneView {
@@ -383,12 +384,16 @@ struct SurfelRec {
 };
 static_assert(sizeof(SurfelRec) == 64, "surfel record is 64 B");
 
-// Gaussian raster record (64 B).  alpha(u,v) = sigma * 2^(ca dx^2 + cb dx dy + cc dy^2)
-// with dx = (u - px) - pxl (projected centre in double-float), conic scaled by
-// -log2(e)/2 (cb by -log2(e)).  Depth test: key = d - eps < D_s.
+// Gaussian raster record (64 B).  alpha(u,v) = sigma * 2^-(y0^2 + y1^2) with
+// y0 = la dx, y1 = lb dx + lc dy, dx = (u - px) - pxl (projected centre in
+// double-float): (la, lb, lc) is the Cholesky factor of the conic
+// Sigma2^-1 = [[a^2+b^2, bc], [bc, c^2]] scaled by sqrt(log2(e)/2), so that
+// q = dx^T Sigma2^-1 dx = (a dx)^2 + (b dx + c dy)^2.  This sum of squares
+// stays accurate far from the centre of elongated Gaussians, where the
+// expanded quadratic form cancels.  Depth test: key = d - eps < D_s.
 struct GaussRec {
     float px, py, pxl, pyl;
-    float ca, cb, cc, sigma;
+    float la, lb, lc, sigma;
     float key, r, g, b;
     int id;
     unsigned bb_lo, bb_hi;
@@ -579,6 +584,9 @@ __device__ __forceinline__ void surfel_setup(const SceneView &S, const CamParams
         // one pixel of slack for the float projection of the clipped polygon
         umin -= 1.f; vmin -= 1.f; umax += 1.f; vmax += 1.f;
     }
+    // with 4 samples a pixel is touched when a sample at +-0.25 px from its
+    // centre falls inside: widen the interval of centres by that much
+    if (O.samples == 4) { umin -= 0.25f; vmin -= 0.25f; umax += 0.25f; vmax += 0.25f; }
     int x0, x1, y0, y1;
     pixel_span(fmaxf(umin, -1e6f), fminf(umax, 1e6f), C.W, x0, x1);
     pixel_span(fmaxf(vmin, -1e6f), fminf(vmax, 1e6f), C.H, y0, y1);
@@ -604,7 +612,7 @@ struct GaussOut {
     float R[9], qn[4], qnorm, s[3];
     float tx, ty, tz;
     float S2a, S2b, S2c;      // Sigma2 (with low-pass)
-    float ia, ib, ic;         // conic (unscaled)
+    float ia, ib, ic;         // conic Sigma2^-1 (unscaled)
     int x0, y0, x1, y1;
 };
 
@@ -634,15 +642,10 @@ __device__ __forceinline__ void gauss_setup(const SceneView &S, const CamParams 
     if (!(t[2].hi > C.znear || (t[2].hi == C.znear && t[2].lo > 0.f))) return;
     const float x = t[0].hi, y = t[1].hi, z = t[2].hi;
     o.tx = x; o.ty = y; o.tz = z;
-    // Sigma3 = (R S)(R S)^T
-    float Mm[9], S3[9];
+    // Sigma3 = (R S)(R S)^T, kept factored as Mm = R S
+    float Mm[9];
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) Mm[3 * a + b] = o.R[3 * a + b] * o.s[b];
-    for (int a = 0; a < 3; ++a)
-        for (int b = a; b < 3; ++b) {
-            float acc = Mm[3 * a] * Mm[3 * b] + Mm[3 * a + 1] * Mm[3 * b + 1] + Mm[3 * a + 2] * Mm[3 * b + 2];
-            S3[3 * a + b] = acc; S3[3 * b + a] = acc;
-        }
     // T = J Rc with the affine Jacobian of the perspective map at the centre
     const float iz = 1.f / z;
     const float J00 = C.fx * iz, J02 = -C.fx * x * iz * iz, J11 = C.fy * iz, J12 = -C.fy * y * iz * iz;
@@ -651,17 +654,29 @@ __device__ __forceinline__ void gauss_setup(const SceneView &S, const CamParams 
         T[b] = J00 * C.R[b] + J02 * C.R[6 + b];
         T[3 + b] = J11 * C.R[3 + b] + J12 * C.R[6 + b];
     }
-    float TS[6];
-    for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 3; ++b)
-            TS[3 * a + b] = T[3 * a] * S3[b] + T[3 * a + 1] * S3[3 + b] + T[3 * a + 2] * S3[6 + b];
-    const float s2a = TS[0] * T[0] + TS[1] * T[1] + TS[2] * T[2] + O.lowpass;
-    const float s2b = TS[0] * T[3] + TS[1] * T[4] + TS[2] * T[5];
-    const float s2c = TS[3] * T[3] + TS[4] * T[4] + TS[5] * T[5] + O.lowpass;
-    const float det = s2a * s2c - s2b * s2b;
-    if (!(det > 0.f) || !isfinite(det)) return;
+    // Sigma2 = P P^T + lowpass I with P = T (R S) (2x3).  Its determinant by
+    // the Lagrange identity, |P0 x P1|^2 + lowpass (|P0|^2 + |P1|^2) +
+    // lowpass^2: a sum of non-negative terms, where s2a s2c - s2b^2 cancels
+    // for elongated footprints.
+    float P0[3], P1[3];
+    for (int b = 0; b < 3; ++b) {
+        P0[b] = T[0] * Mm[b] + T[1] * Mm[3 + b] + T[2] * Mm[6 + b];
+        P1[b] = T[3] * Mm[b] + T[4] * Mm[3 + b] + T[5] * Mm[6 + b];
+    }
+    const float n0 = P0[0] * P0[0] + P0[1] * P0[1] + P0[2] * P0[2];
+    const float n1 = P1[0] * P1[0] + P1[1] * P1[1] + P1[2] * P1[2];
+    const float s2a = n0 + O.lowpass;
+    const float s2b = P0[0] * P1[0] + P0[1] * P1[1] + P0[2] * P1[2];
+    const float s2c = n1 + O.lowpass;
+    const float x0c = P0[1] * P1[2] - P0[2] * P1[1], x1c = P0[2] * P1[0] - P0[0] * P1[2];
+    const float x2c = P0[0] * P1[1] - P0[1] * P1[0];
+    const float det = (x0c * x0c + x1c * x1c + x2c * x2c) + O.lowpass * (n0 + n1) + O.lowpass * O.lowpass;
+    if (!(det > 0.f) || !isfinite(det) || !(s2a > 0.f)) return;
     const float idet = 1.f / det;
     const float ia = s2c * idet, ib = -s2b * idet, ic = s2a * idet;
+    // Cholesky factor of the conic: a = 1/sqrt(s2a), b = -s2b/(sqrt(s2a det)), c = sqrt(s2a/det)
+    const float l00 = sqrtf(s2a), sdet = sqrtf(det);
+    const float fa = 1.f / l00, fb = -s2b / (l00 * sdet), fc = l00 / sdet;
     o.S2a = s2a; o.S2b = s2b; o.S2c = s2c; o.ia = ia; o.ib = ib; o.ic = ic;
     // projected centre in double-float
     df uq = df_add_f(df_mul_f(df_div(t[0], t[2]), C.fx), C.cx);
@@ -679,9 +694,9 @@ __device__ __forceinline__ void gauss_setup(const SceneView &S, const CamParams 
     else if (O.eps_mode == GES_EPS_ZERO) eps = 0.f;
     else eps = O.eps_value;
     const float key = (t[2].hi - eps) + t[2].lo;
-    const float L2E = 1.4426950408889634f;
+    const float kL = 0.84932180028801904f;   // sqrt(log2(e) / 2)
     o.rec.px = uq.hi; o.rec.py = vq.hi; o.rec.pxl = uq.lo; o.rec.pyl = vq.lo;
-    o.rec.ca = -0.5f * L2E * ia; o.rec.cb = -L2E * ib; o.rec.cc = -0.5f * L2E * ic;
+    o.rec.la = kL * fa; o.rec.lb = kL * fb; o.rec.lc = kL * fc;
     o.rec.sigma = sigma; o.rec.key = key;
     o.rec.id = (int)i;
     o.rec.bb_lo = pack_xy(x0, y0); o.rec.bb_hi = pack_xy(x1, y1);
@@ -698,8 +713,8 @@ __device__ __forceinline__ void gauss_setup(const SceneView &S, const CamParams 
 __device__ __forceinline__ float gauss_alpha(const GaussRec &g, float u, float v, float &e)
 {
     const float dx = (u - g.px) - g.pxl, dy = (v - g.py) - g.pyl;
-    const float p2 = fmaf(g.ca, dx * dx, fmaf(g.cb, dx * dy, g.cc * (dy * dy)));
-    e = ex2_approx(p2);
+    const float y0 = g.la * dx, y1 = fmaf(g.lb, dx, g.lc * dy);
+    e = ex2_approx(-fmaf(y0, y0, y1 * y1));
     return g.sigma * e;
 }
 

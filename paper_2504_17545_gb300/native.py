@@ -45,7 +45,8 @@ class ges_camera(C.Structure):
 
 class ges_render_opts(C.Structure):
     _fields_ = [("eps_mode", C.c_int32), ("eps_value", C.c_float), ("eps_factor", C.c_float),
-                ("lowpass", C.c_float), ("alpha_min", C.c_float), ("surfel_r2", C.c_float), ("mode", C.c_int32)]
+                ("lowpass", C.c_float), ("alpha_min", C.c_float), ("surfel_r2", C.c_float), ("mode", C.c_int32),
+                ("samples", C.c_int32)]
 
 
 class ges_grads(C.Structure):

@@ -131,9 +131,11 @@ class GESScene:
 
 
 def render(scene: GESScene, cam, opts: Optional[dict] = None, with_aux: bool = True):
-    """Forward render.  Returns dict(rgb [3,H,W], depth [H,W], id [H,W] int32,
-    aux [H,W] (W_G)); id and aux only when ``with_aux``."""
+    """Forward render.  Returns dict(rgb [3,H,W], depth [H,W], id [H,W] int32
+    ([4,H,W] with ``samples=4``), aux [H,W] (W_G)); id and aux only when
+    ``with_aux``."""
     c = camera_struct(cam)
+    o = opts_struct(opts)
     dev = scene.t["s_pos"].device
     H, W = c.height, c.width
     rgb = torch.empty((3, H, W), device=dev, dtype=torch.float32)
@@ -141,11 +143,11 @@ def render(scene: GESScene, cam, opts: Optional[dict] = None, with_aux: bool = T
     out = dict(rgb=rgb, depth=depth)
     sid = aux = None
     if with_aux:
-        sid = torch.empty((H, W), device=dev, dtype=torch.int32)
+        sid = torch.empty((H, W) if o.samples == 1 else (o.samples, H, W), device=dev, dtype=torch.int32)
         aux = torch.empty((H, W), device=dev, dtype=torch.float32)
         out.update(id=sid, aux=aux)
     scene.bind_stream()
-    N.ges_render_ex(scene.handle, c, opts_struct(opts), rgb.data_ptr(), depth.data_ptr(),
+    N.ges_render_ex(scene.handle, c, o, rgb.data_ptr(), depth.data_ptr(),
                     sid.data_ptr() if sid is not None else 0, aux.data_ptr() if aux is not None else 0)
     return out
 

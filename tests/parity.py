@@ -2,7 +2,8 @@
 
 Surfel ids must match bit-for-bit wherever the oracle did not flag the pixel
 as ambiguous (competing depths within 1e-6 relative, a disc rim within 1e-5
-relative of r^2, a near-plane or grazing fragment); at flagged pixels the GPU's
+relative of r^2, a near-plane or grazing fragment; with 4 samples, at any
+sample of the pixel); at flagged pixels the GPU's
 id must still be an acceptable answer (``oracle.id_validity``).  Depth must
 match to ``depth_rel`` where the ids match; colour to ``col_tol`` max abs per
 channel where the ids match and no Gaussian sits on the 1/255 clamp or the
@@ -32,16 +33,19 @@ def compare(scene, cam, gpu, ref, opts=None, col_tol=COL_TOL, depth_rel=DEPTH_RE
         out["id_mismatch_unmasked"] = int((mism & ~amb_id).sum())
         valid = oracle.id_validity(scene, cam, ref, ids, opts)
         out["id_invalid"] = int((~valid).sum())
-        same = ~mism
+        same = ~mism if mism.ndim == 2 else ~mism.any(0)   # [samples,H,W]: every sample agrees
     else:
         same = np.ones(depth.shape, bool)
-    cov = same & (ref["id"] >= 0) & ~amb_id     # grazing/rim/tie pixels: depth is ill-conditioned
+    hit = ref["id"] >= 0
+    if hit.ndim == 3:
+        hit = hit.any(0)
+    cov = same & hit & ~amb_id     # grazing/rim/tie pixels: depth is ill-conditioned
     if cov.any():
         rel = np.abs(depth[cov] - ref["depth"][cov]) / ref["depth"][cov]
         out["depth_rel_max"] = float(rel.max())
     else:
         out["depth_rel_max"] = 0.0
-    out["depth_inf_ok"] = bool(np.all(np.isinf(depth[same & (ref["id"] < 0)])))
+    out["depth_inf_ok"] = bool(np.all(np.isinf(depth[same & ~hit])))
     ok = same & ~amb_col & ~amb_id
     err = np.abs(rgb - ref["rgb"])[:, ok]
     out["col_max"] = float(err.max()) if err.size else 0.0

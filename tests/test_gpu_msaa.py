@@ -1,0 +1,151 @@
+"""4x multisampled surfel pass (Sec. 5) on the GPU vs the FP64 oracle: per
+sample ids, the resolved colour and depth, the backward, the batch graph."""
+import numpy as np
+import pytest
+
+import oracle
+import scenegen as sg
+from parity import compare
+from test_gpu_backward import _check, _grads_gpu
+from test_gpu_forward import _render, _small
+
+pytestmark = pytest.mark.gpu
+
+MS = dict(samples=4)
+
+
+@pytest.fixture(scope="module")
+def R():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_17545_gb300 import render as R
+    return R
+
+
+def _assert(res):
+    assert res["pass"], res
+
+
+def test_msaa_parity_workload_128(R):
+    scene, cams = sg.config_scene(0)
+    ref = oracle.render(scene, cams[0], MS)
+    out = _render(R, scene, cams[0], MS)
+    assert tuple(out["id"].shape) == (4, 128, 128)
+    res = compare(scene, cams[0], out, ref, MS)
+    _assert(res)
+    assert res["compared_px"] > 0.9 * 128 * 128
+    # the samples disagree on many pixels (edges), so the resolve is exercised
+    ids = out["id"].cpu().numpy()
+    assert (ids != ids[0:1]).any(0).sum() > 200
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_msaa_parity_ragged_and_modes(R, mode):
+    scene = _small(41)
+    opts = dict(mode=mode, samples=4)
+    cams = [sg.look_at((0.2, 0.3, -2.8), (0, 0, 0), (0, 1, 0), 203, 141, 55.0),
+            sg.look_at((0.1, 0.05, -0.6), (0, 0.1, 1), (0, 1, 0), 97, 61, 95.0)]   # inside the scene
+    for cam in cams:
+        ref = oracle.render(scene, cam, opts)
+        _assert(compare(scene, cam, _render(R, scene, cam, opts), ref, opts))
+
+
+def test_msaa_parity_1080p_orbit_camera(R):
+    """The 1M-surfel / 300k-Gaussian 1080p workload with 4 samples, one full
+    frame of the orbit."""
+    scene, cams = sg.config_scene(1)
+    gs = R.GESScene.from_arrays(scene)
+    ref = oracle.render(scene, cams[8], MS)
+    out = R.render(gs, cams[8], MS)
+    res = compare(scene, cams[8], out, ref, MS)
+    _assert(res)
+    assert res["masked_frac"] < 0.02
+    gs.close()
+
+
+def test_msaa_tiny_and_empty_images(R):
+    base = _small(42, 50, 80)
+    for w, h in ((1, 1), (37, 1), (1, 23), (17, 9)):
+        c = sg.look_at((0, 0, -2.5), (0, 0, 0), (0, 1, 0), w, h, 60.0, bg=(0.2, 0.4, 0.6))
+        ref = oracle.render(base, c, MS)
+        _assert(compare(base, c, _render(R, base, c, MS), ref, MS))
+    none = base.subset(s_idx=np.zeros(0, int), g_idx=np.zeros(0, int))
+    c = sg.look_at((0, 0, -2.5), (0, 0, 0), (0, 1, 0), 33, 17, 60.0, bg=(0.2, 0.4, 0.6))
+    out = _render(R, none, c, MS)
+    assert (out["id"] == -1).all() and np.isinf(out["depth"].cpu().numpy()).all()
+
+
+def test_msaa_bad_sample_count_is_invalid_argument(R):
+    from paper_2504_17545_gb300 import native as N
+    sc = _small(43, 10, 10)
+    gs = R.GESScene.from_arrays(sc)
+    cam = sg.look_at((0, 0, -2.5), (0, 0, 0), (0, 1, 0), 32, 32, 60.0)
+    for bad in (0, 2, 8, -1):
+        with pytest.raises(N.GesError) as ei:
+            R.render(gs, cam, dict(samples=bad), with_aux=False)
+        assert ei.value.status == N.GES_ERR_INVALID_ARG
+    gs.close()
+
+
+def test_msaa_deterministic_bitwise(R):
+    scene, cams = sg.config_scene(0)
+    a = _render(R, scene, cams[0], MS)
+    b = _render(R, scene, cams[0], MS)
+    perm = np.random.default_rng(12).permutation(scene.n_gaussians)
+    c = _render(R, scene.subset(g_idx=perm), cams[0], MS)
+    for k in ("rgb", "depth", "id", "aux"):
+        assert (a[k] == b[k]).all(), k
+    for k in ("rgb", "depth", "aux"):
+        assert (a[k] == c[k]).all(), k
+
+
+def test_msaa_fragment_counts_match_oracle(R):
+    from paper_2504_17545_gb300 import native as N
+    scene, cams = sg.config_scene(0)
+    gs = R.GESScene.from_arrays(scene)
+    ns4, ng4 = N.ges_count_fragments(gs.handle, R.camera_struct(cams[0]), R.opts_struct(MS))
+    ns1, ng1 = N.ges_count_fragments(gs.handle, R.camera_struct(cams[0]), R.opts_struct(None))
+    os_, og = oracle.count_fragments(scene, cams[0], MS)
+    assert abs(ns4 - os_) <= max(3, 1e-4 * os_) and ng4 == ng1, (ns4, os_, ng4, ng1)
+    assert 3.5 * ns1 < ns4 < 4.5 * ns1
+    gs.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_msaa_backward_crop_matches_oracle(R, mode):
+    scene, cam = sg.crop_scene(7)
+    g = np.random.default_rng(13).standard_normal((3, cam.height, cam.width))
+    opts = dict(mode=mode, samples=4)
+    ref = oracle.backward(scene, cam, g, opts)
+    gpu, fwd = _grads_gpu(R, scene, cam, g, opts)
+    keys = ["s_sh"] + (["g_pos", "g_rot", "g_scale", "g_opac", "g_sh"] if mode == 0 else [])
+    _check(gpu, ref, keys, scene, cam, opts)
+
+
+def test_msaa_backward_parity_workload(R):
+    scene, cams = sg.config_scene(0)
+    g = np.random.default_rng(14).standard_normal((3, 128, 128))
+    ref = oracle.backward(scene, cams[0], g, MS)
+    gpu, _ = _grads_gpu(R, scene, cams[0], g, MS)
+    _check(gpu, ref, ["g_pos", "g_rot", "g_scale", "g_opac", "g_sh", "s_sh"], scene, cams[0], MS)
+
+
+def test_msaa_batch_graph_equals_single_views(R):
+    scene, cams = sg.config_scene(0)
+    other = _small(44, 2000, 6000)
+    ga, gb = R.GESScene.from_arrays(scene), R.GESScene.from_arrays(other)
+    views = [cams[0], sg.look_at((0.5, 0, -2.8), (0, 0, 0), (0, 1, 0), 301, 173, 60.0),
+             sg.look_at((0, 0.3, -2.6), (0, 0, 0), (0, 1, 0), 128, 96, 50.0)]
+    sov = [0, 1, 0]
+    b = R.GESBatch([ga, gb], views, sov, opts=MS)
+    b.launch()
+    b.sync()
+    outs = R.render_batch([ga, gb], views, sov, opts=MS)
+    for v in range(3):
+        single = R.render([ga, gb][sov[v]], views[v], MS)
+        assert (b.rgb[v] == single["rgb"]).all() and (b.depth[v] == single["depth"]).all(), v
+        assert (outs[v][0] == single["rgb"]).all() and (outs[v][1] == single["depth"]).all(), v
+    b.close()
+    ga.close()
+    gb.close()
