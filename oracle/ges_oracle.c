@@ -48,6 +48,7 @@ typedef struct {
     int32_t sh_degree;
     const double *s_pos, *s_rot, *s_scale, *s_sh;            /* [N,3] [N,4] [N,2] [N,K,3] */
     const double *g_pos, *g_rot, *g_scale, *g_opac, *g_sh;   /* [M,3] [M,4] [M,3] [M] [M,K,3] */
+    const double *g_filt3;   /* [M] Mip-GES 3D filter variance (world units^2), NULL: none */
 } ora_scene;
 
 typedef struct {
@@ -65,6 +66,9 @@ typedef struct {
     /* ambiguity bands (pixels where several results are correct) */
     double tol_depth_rel, tol_disc_rel, tol_graze, tol_alpha, tol_gdepth_rel;
     int32_t samples;     /* 1: the pixel centre; 4: 4x multisampling of the surfel pass (Sec. 5) */
+    int32_t filter;      /* 0: fixed EWA dilation Sigma2 + lowpass I (3DGS, basic GES);
+                            1: Mip-GES screen filter: the same dilation with the opacity
+                               scaled by sqrt(|Sigma2| / |Sigma2 + lowpass I|) (Sec. 6.1) */
 } ora_opts;
 
 enum { ORA_OK = 0, ORA_BAD_ARG = 1, ORA_BAD_QUAT = 2, ORA_NOMEM = 3 };
@@ -197,7 +201,10 @@ typedef struct {
     double px, py;                      /* projected centre */
     double ca, cb, cc;                  /* conic = inverse of Sigma2 */
     double S2a, S2b, S2c;               /* Sigma2 entries (a b; b c) */
-    double sigma, d, eps;
+    double sigma, d, eps;               /* sigma: the opacity after the Mip-GES factors */
+    double sigma0, k3, k2;              /* stored opacity, 3D and 2D filter factors */
+    double se[3];                       /* axis lengths after the 3D filter */
+    double R2a, R2b, R2c;               /* projected covariance before the screen filter */
     double rgb[3], raw[3], dir[3], dist;
     double R[9], qn[4], qnorm;
     int x0, x1, y0, y1;
@@ -263,7 +270,15 @@ static int surfel_setup(const ora_scene *S, const ora_camera *c, const ora_opts 
 
 /* Gaussian: Sigma3 = R diag(s^2) R^T, EWA projection with the affine Jacobian at
    the centre, fixed screen low-pass Sigma2 += lowpass I (3DGS's fixed-size EWA
-   filter, Sec. 6.1), conic = Sigma2^-1, depth d_i = camera z of the centre. */
+   filter, Sec. 6.1), conic = Sigma2^-1, depth d_i = camera z of the centre.
+   Mip-GES (Sec. 6.1, the filters of Mip-Splatting): a 3D filter of variance v
+   per Gaussian, Sigma3 + v I = R diag(s^2 + v) R^T, with the opacity scaled
+   by sqrt(|Sigma3| / |Sigma3 + v I|) = prod_j s_j / sqrt(s_j^2 + v); and with
+   filter = 1 the screen filter scales the opacity by
+   sqrt(|Sigma2'| / |Sigma2' + lowpass I|), Sigma2' the projection before it.
+   Both factors keep the Gaussian's integral unchanged (the convolution of a
+   Gaussian with a normalised Gaussian kernel).  eps_i uses the stored axis
+   lengths s. */
 static int gauss_setup(const ora_scene *S, const ora_camera *c, const ora_opts *o,
                        const double *ocam, int64_t i, gauss_t *g)
 {
@@ -274,7 +289,17 @@ static int gauss_setup(const ora_scene *S, const ora_camera *c, const ora_opts *
     cam_rot(c, Rc);
     const double *p = S->g_pos + 3*i, *s = S->g_scale + 3*i;
     cam_to_camera(c, p, g->t);
-    g->sigma = S->g_opac[i];
+    g->sigma0 = S->g_opac[i];
+    g->sigma = g->sigma0;
+    g->k3 = 1.0; g->k2 = 1.0;
+    {
+        const double v = S->g_filt3 ? S->g_filt3[i] : 0.0;
+        for (int k = 0; k < 3; ++k) {
+            g->se[k] = sqrt(s[k] * s[k] + v);
+            g->k3 *= fabs(s[k]) / g->se[k];
+        }
+        if (v == 0.0) { g->k3 = 1.0; for (int k = 0; k < 3; ++k) g->se[k] = s[k]; }
+    }
     switch (o->eps_mode) {
     case 0: g->eps = o->eps_factor / 3.0 * (s[0] + s[1] + s[2]); break;
     case 1: g->eps = 0.0; break;
@@ -291,7 +316,7 @@ static int gauss_setup(const ora_scene *S, const ora_camera *c, const ora_opts *
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
             double acc = 0.0;
-            for (int k = 0; k < 3; ++k) acc += g->R[3*a + k] * s[k] * s[k] * g->R[3*b + k];
+            for (int k = 0; k < 3; ++k) acc += g->R[3*a + k] * g->se[k] * g->se[k] * g->R[3*b + k];
             S3[3*a + b] = acc;
         }
     double x = g->t[0], y = g->t[1], z = g->t[2];
@@ -308,9 +333,15 @@ static int gauss_setup(const ora_scene *S, const ora_camera *c, const ora_opts *
                 for (int l = 0; l < 3; ++l) acc += T[3*a + k] * S3[3*k + l] * T[3*b + l];
             S2[2*a + b] = acc;
         }
-    g->S2a = S2[0] + o->lowpass; g->S2b = 0.5 * (S2[1] + S2[2]); g->S2c = S2[3] + o->lowpass;
+    g->R2a = S2[0]; g->R2b = 0.5 * (S2[1] + S2[2]); g->R2c = S2[3];
+    g->S2a = S2[0] + o->lowpass; g->S2b = g->R2b; g->S2c = S2[3] + o->lowpass;
     double det = g->S2a * g->S2c - g->S2b * g->S2b;
     if (!(det > 0.0) || !isfinite(det)) return 1;
+    if (o->filter == 1) {
+        double det0 = g->R2a * g->R2c - g->R2b * g->R2b;
+        g->k2 = det0 > 0.0 ? sqrt(det0 / det) : 0.0;
+    }
+    g->sigma = g->sigma0 * g->k3 * g->k2;
     g->ca = g->S2c / det; g->cb = -g->S2b / det; g->cc = g->S2a / det;
     g->px = c->fx * x / z + c->cx;
     g->py = c->fy * y / z + c->cy;
@@ -568,6 +599,7 @@ static int check_args(const ora_scene *S, const ora_camera *c, const ora_opts *o
     if (S->n_surfels < 0 || S->n_gaussians < 0) return 0;
     if (!(c->fx > 0 && c->fy > 0 && c->znear > 0)) return 0;
     if (o->samples != 1 && o->samples != 4) return 0;
+    if (o->filter != 0 && o->filter != 1) return 0;
     return 1;
 }
 
@@ -919,7 +951,9 @@ int ora_backward(const ora_scene *S, const ora_camera *c, const ora_opts *o, int
             /* colour -> SH and position (through the view direction) */
             sh_backward(S->sh_degree, S->g_sh + (int64_t)3*K*gi, g->dir, g->dist, g->raw, dc,
                         gg_sh + (int64_t)3*K*gi, gp);
-            gg_opac[gi] = dsig;
+            /* sigma = sigma0 k3 k2 (Mip-GES factors; both 1 without the filters) */
+            gg_opac[gi] = dsig * g->k3 * g->k2;
+            const double dk2 = dsig * g->sigma0 * g->k3, dk3 = dsig * g->sigma0 * g->k2;
             /* conic Q = Sigma2^-1 (symmetric), dL/dQ as a symmetric matrix */
             double Q[4] = {g->ca, g->cb, g->cb, g->cc};
             double GQ[4] = {dca, 0.5*dcb, 0.5*dcb, dcc};
@@ -932,6 +966,13 @@ int ora_backward(const ora_scene *S, const ora_camera *c, const ora_opts *o, int
                         for (int l = 0; l < 2; ++l) acc += Q[2*a + k] * GQ[2*k + l] * Q[2*l + b];
                     GS2[2*a + b] = -acc;
                 }
+            /* screen filter: k2 = sqrt(det R2 / det Sigma2) with Sigma2 = R2 + lowpass I,
+               d ln det A / dA = A^-1, so dk2/dR2 = (k2/2) (R2^-1 - Sigma2^-1) */
+            if (o->filter == 1 && g->k2 > 0.0) {
+                double d0 = g->R2a * g->R2c - g->R2b * g->R2b;
+                double I0[4] = {g->R2c / d0, -g->R2b / d0, -g->R2b / d0, g->R2a / d0};
+                for (int a = 0; a < 4; ++a) GS2[a] += dk2 * 0.5 * g->k2 * (I0[a] - Q[a]);
+            }
             /* rebuild J, T = J Rc, Sigma3 */
             double x = g->t[0], y = g->t[1], z = g->t[2];
             double J[6] = {c->fx / z, 0.0, -c->fx * x / (z*z), 0.0, c->fy / z, -c->fy * y / (z*z)};
@@ -942,7 +983,7 @@ int ora_backward(const ora_scene *S, const ora_camera *c, const ora_opts *o, int
             for (int a = 0; a < 3; ++a)
                 for (int b = 0; b < 3; ++b) {
                     double acc = 0.0;
-                    for (int k = 0; k < 3; ++k) acc += g->R[3*a + k] * s[k] * s[k] * g->R[3*b + k];
+                    for (int k = 0; k < 3; ++k) acc += g->R[3*a + k] * g->se[k] * g->se[k] * g->R[3*b + k];
                     S3[3*a + b] = acc;
                 }
             /* Sigma2 = T S3 T^T (+ lowpass I):  dL/dS3 = T^T GS2 T,  dL/dT = 2 GS2 T S3 */
@@ -975,19 +1016,23 @@ int ora_backward(const ora_scene *S, const ora_camera *c, const ora_opts *o, int
                   + dpx * (-c->fx * x / (z*z)) + dpy * (-c->fy * y / (z*z));
             /* t = Rc p + tc:  dL/dp += Rc^T gt */
             for (int a = 0; a < 3; ++a) gp[a] += Rc[a]*gt[0] + Rc[3 + a]*gt[1] + Rc[6 + a]*gt[2];
-            /* S3 = Mm Mm^T with Mm = R diag(s):  dL/dMm = 2 GS3 Mm */
+            /* S3 = Mm Mm^T with Mm = R diag(se), se = sqrt(s^2 + v):  dL/dMm = 2 GS3 Mm */
             double GM[9];
             for (int a = 0; a < 3; ++a)
                 for (int b = 0; b < 3; ++b) {
                     double acc = 0.0;
-                    for (int k = 0; k < 3; ++k) acc += GS3[3*a + k] * g->R[3*k + b] * s[b];
+                    for (int k = 0; k < 3; ++k) acc += GS3[3*a + k] * g->R[3*k + b] * g->se[b];
                     GM[3*a + b] = 2.0 * acc;
                 }
             double GR[9];
+            const double v3 = S->g_filt3 ? S->g_filt3[gi] : 0.0;
             for (int b = 0; b < 3; ++b) {
                 double acc = 0.0;
-                for (int a = 0; a < 3; ++a) { acc += GM[3*a + b] * g->R[3*a + b]; GR[3*a + b] = GM[3*a + b] * s[b]; }
-                gg_scale[3*gi + b] = acc;
+                for (int a = 0; a < 3; ++a) { acc += GM[3*a + b] * g->R[3*a + b]; GR[3*a + b] = GM[3*a + b] * g->se[b]; }
+                /* dse/ds = s/se;  k3 = prod |s_j|/se_j:  dk3/ds_j = k3 v / (s_j se_j^2) */
+                double gs = v3 != 0.0 ? acc * s[b] / g->se[b] : acc;
+                if (v3 != 0.0 && s[b] != 0.0) gs += dk3 * g->k3 * v3 / (s[b] * g->se[b] * g->se[b]);
+                gg_scale[3*gi + b] = gs;
             }
             /* R(qhat): partial derivatives of each entry w.r.t. (w,x,y,z) */
             double w = g->qn[0], qx = g->qn[1], qy = g->qn[2], qz = g->qn[3];
@@ -1010,6 +1055,40 @@ int ora_backward(const ora_scene *S, const ora_camera *c, const ora_opts *o, int
     }
     prep_free(&P);
     free(rgb); free(Ds); free(WG); free(sid); free(amb); free(gcs);
+    return ORA_OK;
+}
+
+/* Mip-GES 3D filter variance per Gaussian (Sec. 6.1, Mip-Splatting's world-space
+   filter): v_i = s3d / nu_i^2 with nu_i the highest sampling rate at which the
+   training cameras see the centre, nu = max(fx, fy) / z over the cameras whose
+   image rectangle [0,W] x [0,H] contains the projected centre at z > znear.  A
+   Gaussian no camera sees gets the largest v among those seen (0 if none is). */
+int ora_filter3d(const ora_scene *S, const ora_camera *cams, int n_cams, double s3d, double *out_v)
+{
+    if (!S || !cams || n_cams <= 0 || !(s3d >= 0.0) || S->n_gaussians < 0) return ORA_BAD_ARG;
+    double vmax = 0.0;
+    int any = 0;
+    for (int64_t i = 0; i < S->n_gaussians; ++i) {
+        double nu = 0.0;
+        for (int k = 0; k < n_cams; ++k) {
+            const ora_camera *c = &cams[k];
+            double t[3];
+            cam_to_camera(c, S->g_pos + 3*i, t);
+            if (!(t[2] > c->znear)) continue;
+            double u = c->fx * t[0] / t[2] + c->cx, v = c->fy * t[1] / t[2] + c->cy;
+            if (!(u >= 0.0 && u <= c->width && v >= 0.0 && v <= c->height)) continue;
+            nu = fmax(nu, fmax(c->fx, c->fy) / t[2]);
+        }
+        if (nu > 0.0) {
+            out_v[i] = s3d / (nu * nu);
+            vmax = any ? fmax(vmax, out_v[i]) : out_v[i];
+            any = 1;
+        } else {
+            out_v[i] = -1.0;
+        }
+    }
+    for (int64_t i = 0; i < S->n_gaussians; ++i)
+        if (out_v[i] < 0.0) out_v[i] = any ? vmax : 0.0;
     return ORA_OK;
 }
 

@@ -27,13 +27,13 @@ _lib = None
 DEFAULT_OPTS = dict(eps_mode=0, eps_value=0.1, eps_factor=5.0, lowpass=0.3,
                     alpha_min=1.0 / 255.0, surfel_r2=2.0 * math.log(255.0), mode=0,
                     tol_depth_rel=1e-6, tol_disc_rel=1e-5, tol_graze=1e-3, tol_alpha=1e-5,
-                    tol_gdepth_rel=2e-6, samples=1)
+                    tol_gdepth_rel=2e-6, samples=1, filter=0)
 
 
 class _Scene(C.Structure):
     _fields_ = [("n_surfels", C.c_int64), ("n_gaussians", C.c_int64), ("sh_degree", C.c_int32)] + \
                [(n, C.c_void_p) for n in ("s_pos", "s_rot", "s_scale", "s_sh",
-                                          "g_pos", "g_rot", "g_scale", "g_opac", "g_sh")]
+                                          "g_pos", "g_rot", "g_scale", "g_opac", "g_sh", "g_filt3")]
 
 
 class _Camera(C.Structure):
@@ -47,7 +47,7 @@ class _Opts(C.Structure):
                 ("lowpass", C.c_double), ("alpha_min", C.c_double), ("surfel_r2", C.c_double),
                 ("mode", C.c_int32), ("tol_depth_rel", C.c_double), ("tol_disc_rel", C.c_double),
                 ("tol_graze", C.c_double), ("tol_alpha", C.c_double), ("tol_gdepth_rel", C.c_double),
-                ("samples", C.c_int32)]
+                ("samples", C.c_int32), ("filter", C.c_int32)]
 
 
 def build(force: bool = False) -> str:
@@ -78,6 +78,7 @@ def load():
         lib.ora_touching.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_void_p, C.c_void_p, C.c_void_p]
         lib.ora_check_ids.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_void_p, C.c_void_p]
         lib.ora_count_fragments.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_void_p, C.c_void_p]
+        lib.ora_filter3d.argtypes = [P(_Scene), C.c_void_p, C.c_int, C.c_double, C.c_void_p]
         _lib = lib
     return _lib
 
@@ -91,9 +92,14 @@ class _Pinned:
 
     def __init__(self, scene, cam, opts):
         self.arrs = {k: _d(v) for k, v in scene.arrays().items()}
+        f3 = getattr(scene, "g_filter3d", None)
+        if f3 is not None:
+            self.arrs["g_filt3"] = _d(f3)
+            assert self.arrs["g_filt3"].shape == (scene.n_gaussians,)
         self.s = _Scene(scene.n_surfels, scene.n_gaussians, scene.sh_degree,
                         *[self.arrs[k].ctypes.data for k in ("s_pos", "s_rot", "s_scale", "s_sh",
-                                                              "g_pos", "g_rot", "g_scale", "g_opac", "g_sh")])
+                                                              "g_pos", "g_rot", "g_scale", "g_opac", "g_sh")],
+                        self.arrs["g_filt3"].ctypes.data if f3 is not None else None)
         w2c = np.asarray(cam.world_to_cam, np.float64).reshape(12)
         self.c = _Camera(cam.width, cam.height, float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy),
                          (C.c_double * 12)(*w2c), float(cam.znear), (C.c_double * 3)(*map(float, cam.bg)))
@@ -215,6 +221,18 @@ def touching(scene, cam, flag, opts=None):
     _check(lib.ora_touching(C.byref(pin.s), C.byref(pin.c), C.byref(pin.o), f.ctypes.data, st_.ctypes.data,
                             gt_.ctypes.data), "touching")
     return st_.astype(bool), gt_.astype(bool)
+
+
+def filter3d(scene, cams, s3d: float = 0.2):
+    """Mip-GES 3D filter variance per Gaussian from the cameras ``cams``
+    (``ora_filter3d``); s3d = 0.2 is Mip-Splatting's filter size."""
+    lib = load()
+    pins = [_Pinned(scene, c, None) for c in cams]
+    arr = (_Camera * len(cams))(*[p.c for p in pins])
+    out = np.empty(scene.n_gaussians)
+    _check(lib.ora_filter3d(C.byref(pins[0].s), C.cast(arr, C.c_void_p), len(cams), float(s3d), out.ctypes.data),
+           "filter3d")
+    return out
 
 
 def count_fragments(scene, cam, opts=None):

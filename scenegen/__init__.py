@@ -32,7 +32,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
-from typing import List, Sequence, Tuple
+from typing import List, Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -54,6 +54,7 @@ class Scene:
     g_scale: np.ndarray
     g_opac: np.ndarray
     g_sh: np.ndarray
+    g_filter3d: Optional[np.ndarray] = None   # per-Gaussian 3D filter variance (Mip-GES), or none
 
     @property
     def n_surfels(self) -> int:
@@ -70,7 +71,8 @@ class Scene:
         return Scene(self.sh_degree,
                      c(self.s_pos[s_idx]), c(self.s_rot[s_idx]), c(self.s_scale[s_idx]), c(self.s_sh[s_idx]),
                      c(self.g_pos[g_idx]), c(self.g_rot[g_idx]), c(self.g_scale[g_idx]),
-                     c(self.g_opac[g_idx]), c(self.g_sh[g_idx]))
+                     c(self.g_opac[g_idx]), c(self.g_sh[g_idx]),
+                     None if self.g_filter3d is None else c(self.g_filter3d[g_idx]))
 
     def arrays(self):
         return dict(s_pos=self.s_pos, s_rot=self.s_rot, s_scale=self.s_scale, s_sh=self.s_sh,
