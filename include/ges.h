@@ -76,6 +76,13 @@ typedef enum {
 } ges_mode;
 
 typedef enum {
+    GES_FILTER_EWA = 0,    /* Sigma2 + lowpass I, opacity unchanged (3DGS's fixed dilation; basic GES) */
+    GES_FILTER_MIP = 1     /* Mip-GES (Sec. 6.1): Sigma2 + lowpass I with the opacity scaled by
+                              sqrt(|Sigma2| / |Sigma2 + lowpass I|) (Mip-Splatting's screen filter;
+                              that method uses lowpass = 0.1) */
+} ges_filter;
+
+typedef enum {
     GES_EPS_ADAPTIVE = 0,  /* eps_i = eps_factor/3 * (s_1+s_2+s_3), Sec. 5 */
     GES_EPS_ZERO = 1,      /* eps = 0, Table 5 ablation */
     GES_EPS_CONST = 2      /* eps = eps_value (0.1 in Table 5) */
@@ -88,6 +95,10 @@ typedef struct ges_scene ges_scene;   /* opaque */
  * rotations, scales and opacities use attr_dtype, SH coefficients sh_dtype.
  *   s_pos [N,3]  s_rot [N,4] (w,x,y,z)  s_scale [N,2]  s_sh [N,K,3]
  *   g_pos [M,3]  g_rot [M,4] (w,x,y,z)  g_scale [M,3]  g_opac [M]  g_sh [M,K,3]
+ *   g_filter3d [M] float32 or NULL: Mip-GES 3D filter variance per Gaussian
+ *     (Sec. 6.1, Mip-Splatting's world-space filter; see ges_compute_filter3d).
+ *     Rendering uses Sigma3 + v I = R diag(s^2 + v) R^T and scales the opacity
+ *     by prod_j |s_j| / sqrt(s_j^2 + v); eps_i keeps the stored s.  NULL: none.
  * The arrays must stay valid and unchanged while a render or backward call
  * that uses them is in flight; the scene holds views, not copies. */
 typedef struct {
@@ -99,6 +110,7 @@ typedef struct {
     const void *s_rot, *s_scale, *s_sh;
     const float *g_pos;
     const void *g_rot, *g_scale, *g_opac, *g_sh;
+    const float *g_filter3d;
 } ges_scene_desc;
 
 /* Pinhole camera; width, height in [1, 16384]; fx, fy > 0; znear > 0. */
@@ -123,6 +135,7 @@ typedef struct {
                                      (4x multisampling of the surfel pass, Sec. 5: samples on the
                                      2x2 grid at +-0.25 px, colour = their mean, D_s = the nearest
                                      covered sample's depth; Gaussians stay at the centre) */
+    int32_t filter;               /* ges_filter: GES_FILTER_EWA (default) or GES_FILTER_MIP */
 } ges_render_opts;
 
 /* Gradient outputs (DEVICE pointers, float32, overwritten, not accumulated).
@@ -166,6 +179,18 @@ GES_API ges_status ges_create_scene(const ges_scene_desc *desc, ges_scene **out)
  * densification).  Same checks as ges_create_scene; scratch is kept and
  * grown when needed. */
 GES_API ges_status ges_scene_update(ges_scene *scene, const ges_scene_desc *desc);
+
+/* Mip-GES 3D filter variance per Gaussian (Sec. 6.1, Mip-Splatting's world
+ * filter) from the training cameras cams[0..n_cams): out_var [M] (DEVICE,
+ * float32) receives v_i = s3d / nu_i^2, where nu_i = max(fx, fy) / z is the
+ * highest sampling rate among the cameras whose image rectangle [0,W] x [0,H]
+ * holds the Gaussian's projected centre at z > znear.  A Gaussian no camera
+ * sees gets the largest v of the others (0 if none is seen).  Mip-Splatting
+ * uses s3d = 0.2.  Pass out_var as the scene's g_filter3d to render with it.
+ * Returns after the scene's stream has finished.  GES_ERR_INVALID_ARG on a
+ * NULL pointer, n_cams < 1, a negative or non-finite s3d or a bad camera. */
+GES_API ges_status ges_compute_filter3d(ges_scene *scene, const ges_camera *cams, int32_t n_cams, float s3d,
+                                        float *out_var);
 
 /* Release the scene and its scratch (synchronises its stream first).
  * NULL is accepted and ignored. */

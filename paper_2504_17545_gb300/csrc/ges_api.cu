@@ -79,6 +79,7 @@ struct ges_scene {
     DevBuf s_list, g_list;
     DevBuf hist, base, vcount;     // local binning
     DevBuf status;                 // ST_WORDS per view slot
+    DevBuf filt;                   // ges_compute_filter3d: cameras + one scratch word
     unsigned *status_host = nullptr;
     int status_slots = 0;
     int64_t tiles_cap = 0;
@@ -124,7 +125,8 @@ void set_view(ges_scene *s)
 {
     const ges_scene_desc &d = s->desc;
     s->view = SceneView{d.n_surfels, d.n_gaussians, d.sh_degree, d.attr_dtype, d.sh_dtype,
-                        d.s_pos, d.s_rot, d.s_scale, d.s_sh, d.g_pos, d.g_rot, d.g_scale, d.g_opac, d.g_sh};
+                        d.s_pos, d.s_rot, d.s_scale, d.s_sh, d.g_pos, d.g_rot, d.g_scale, d.g_opac, d.g_sh,
+                        d.g_filter3d};
 }
 
 bool finite_all(const float *v, int n)
@@ -177,6 +179,8 @@ ges_status make_opts(const ges_render_opts *o, OptParams &O)
     if (!std::isfinite(o->eps_factor) || !std::isfinite(o->eps_value))
         return fail(GES_ERR_INVALID_ARG, "eps parameters must be finite");
     if (o->samples != 1 && o->samples != 4) return fail(GES_ERR_INVALID_ARG, "samples must be 1 or 4, not %d", o->samples);
+    if (o->filter != GES_FILTER_EWA && o->filter != GES_FILTER_MIP)
+        return fail(GES_ERR_INVALID_ARG, "filter %d unknown", o->filter);
     O.eps_mode = o->eps_mode;
     O.eps_value = o->eps_value;
     O.eps_factor = o->eps_factor;
@@ -186,6 +190,7 @@ ges_status make_opts(const ges_render_opts *o, OptParams &O)
     O.surfel_r = std::sqrt(o->surfel_r2);
     O.mode = o->mode;
     O.samples = o->samples;
+    O.filter = o->filter;
     return GES_OK;
 }
 
@@ -362,6 +367,7 @@ ges_status ges_default_opts(ges_render_opts *out)
     out->surfel_r2 = (float)(2.0 * std::log(255.0));
     out->mode = GES_MODE_FULL;
     out->samples = 1;
+    out->filter = GES_FILTER_EWA;
     return GES_OK;
 }
 
@@ -399,7 +405,7 @@ ges_status ges_destroy_scene(ges_scene *s)
     cudaStreamSynchronize(s->stream);
     DevBuf *bufs[] = {&s->s_rec, &s->s_rgb, &s->g_rec, &s->s_vis, &s->g_vis, &s->s_cnt, &s->g_cnt, &s->s_off,
                       &s->g_off, &s->s_cur, &s->g_cur, &s->s_list, &s->g_list, &s->hist, &s->base,
-                      &s->vcount, &s->status};
+                      &s->vcount, &s->status, &s->filt};
     for (DevBuf *b : bufs) b->release();
     if (s->status_host) cudaFreeHost(s->status_host);
     for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
@@ -510,6 +516,27 @@ ges_status ges_count_fragments(ges_scene *s, const ges_camera *cam, const ges_re
         return GES_OK;
     }
     return fail(GES_ERR_INTERNAL, "tile lists kept overflowing after growing them");
+}
+
+ges_status ges_compute_filter3d(ges_scene *s, const ges_camera *cams, int32_t n_cams, float s3d, float *out_var)
+{
+    if (!s || !cams || (!out_var && s->desc.n_gaussians > 0)) return fail(GES_ERR_INVALID_ARG, "NULL argument");
+    if (n_cams < 1) return fail(GES_ERR_INVALID_ARG, "n_cams must be >= 1");
+    if (!(s3d >= 0.f) || !std::isfinite(s3d)) return fail(GES_ERR_INVALID_ARG, "s3d must be finite and >= 0");
+    std::vector<CamParams> C((size_t)n_cams);
+    for (int k = 0; k < n_cams; ++k) {
+        ges_status r = make_cam(cams + k, C[(size_t)k]);
+        if (r != GES_OK) return r;
+    }
+    const size_t cam_bytes = sizeof(CamParams) * (size_t)n_cams, word_at = (cam_bytes + 15) & ~(size_t)15;
+    GES_CUDA(s->filt.ensure(word_at + 16));
+    unsigned char *base = (unsigned char *)s->filt.p;
+    GES_CUDA(cudaMemcpyAsync(base, C.data(), cam_bytes, cudaMemcpyHostToDevice, s->stream));
+    cudaError_t e = launch_filter3d(s->view, (const CamParams *)base, n_cams, s3d, out_var,
+                                    (unsigned *)(base + word_at), s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    GES_CUDA(cudaStreamSynchronize(s->stream));
+    return GES_OK;
 }
 
 ges_status ges_get_stats(const ges_scene *s, ges_stats *out)
@@ -957,7 +984,7 @@ extern "C" GES_API ges_status ges_render_noalloc(const ges_scene_desc *desc, con
     GES_CUDA(cudaMemsetAsync(X.status, 0, ST_WORDS * 4, st));
     SceneView S{desc->n_surfels, desc->n_gaussians, desc->sh_degree, desc->attr_dtype, desc->sh_dtype,
                 desc->s_pos, desc->s_rot, desc->s_scale, desc->s_sh, desc->g_pos, desc->g_rot, desc->g_scale,
-                desc->g_opac, desc->g_sh};
+                desc->g_opac, desc->g_sh, desc->g_filter3d};
     cudaError_t e = launch_forward(S, C, O, X, out_rgb, out_depth, out_surfel_id, aux, st, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     unsigned w[ST_WORDS];

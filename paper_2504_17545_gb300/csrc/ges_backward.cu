@@ -156,15 +156,26 @@ __global__ void __launch_bounds__(256) k_gauss_bwd(SceneView S, CamParams C, Opt
             for (int a = 0; a < 3; ++a) gp[a] -= (gd[a] - pr * o.dir[a]) / o.dist;
         }
     }
-    if (G.g_opac) G.g_opac[gi] = my[3];
+    // my[3] is dL/dsigma with sigma = sigma0 k3 k2 (the Mip-GES factors, 1 without them)
+    if (G.g_opac) G.g_opac[gi] = my[3] * o.k3 * o.k2;
     // conic Q = Sigma2^-1:  dL/dSigma2 = -Q GQ Q with GQ = [[dia, dib/2], [dib/2, dic]]
     const float Q00 = o.ia, Q01 = o.ib, Q11 = o.ic;
     const float G00 = my[6], G01 = 0.5f * my[7], G11 = my[8];
     // M1 = GQ Q
     const float m00 = G00 * Q00 + G01 * Q01, m01 = G00 * Q01 + G01 * Q11;
     const float m10 = G01 * Q00 + G11 * Q01, m11 = G01 * Q01 + G11 * Q11;
-    const float S00 = -(Q00 * m00 + Q01 * m10), S01 = -(Q00 * m01 + Q01 * m11);
-    const float S11 = -(Q01 * m01 + Q11 * m11);
+    float S00 = -(Q00 * m00 + Q01 * m10), S01 = -(Q00 * m01 + Q01 * m11);
+    float S11 = -(Q01 * m01 + Q11 * m11);
+    // screen filter k2 = sqrt(det R2 / det Sigma2), Sigma2 = R2 + lowpass I:
+    // dk2/dR2 = (k2/2) (R2^-1 - Sigma2^-1), and k2 R2^-1 = adj(R2) / sqrt(det R2 det Sigma2)
+    if (O.filter == GES_FILTER_MIP && o.det0 > 0.f) {
+        const float h = 0.5f * my[3] * o.sigma0 * o.k3;
+        const float det = o.det0 + O.lowpass * (o.n0 + o.n1) + O.lowpass * O.lowpass;
+        const float r = h / sqrtf(o.det0 * det), hk = h * o.k2;
+        S00 += r * o.n1 - hk * Q00;
+        S01 += -r * o.S2b - hk * Q01;
+        S11 += r * o.n0 - hk * Q11;
+    }
     const float GS2[2][2] = {{S00, S01}, {S01, S11}};
     // rebuild T = J Rc and Sigma3 = (R S)(R S)^T
     const float x = o.tx, y = o.ty, z = o.tz, iz = 1.f / z;
@@ -175,7 +186,7 @@ __global__ void __launch_bounds__(256) k_gauss_bwd(SceneView S, CamParams C, Opt
         T[1][b] = J11 * C.R[3 + b] + J12 * C.R[6 + b];
     }
     for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) Mm[a][b] = o.R[3 * a + b] * o.s[b];
+        for (int b = 0; b < 3; ++b) Mm[a][b] = o.R[3 * a + b] * o.se[b];
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) S3[a][b] = Mm[a][0] * Mm[b][0] + Mm[a][1] * Mm[b][1] + Mm[a][2] * Mm[b][2];
     // dL/dSigma3 = T^T GS2 T ; dL/dT = 2 GS2 T S3
@@ -203,15 +214,24 @@ __global__ void __launch_bounds__(256) k_gauss_bwd(SceneView S, CamParams C, Opt
             dpx * (-C.fx * x * iz * iz) + dpy * (-C.fy * y * iz * iz);
     for (int a = 0; a < 3; ++a) gp[a] += C.R[a] * gt[0] + C.R[3 + a] * gt[1] + C.R[6 + a] * gt[2];
     if (G.g_pos) for (int a = 0; a < 3; ++a) G.g_pos[3 * gi + a] = gp[a];
-    // Sigma3 = Mm Mm^T, Mm = R diag(s): dL/dMm = 2 GS3 Mm
+    // Sigma3 = Mm Mm^T, Mm = R diag(se), se = sqrt(s^2 + v): dL/dMm = 2 GS3 Mm
     float GR[3][3];
     float gsc[3] = {0.f, 0.f, 0.f};
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
             const float gm = 2.f * (GS3[a][0] * Mm[0][b] + GS3[a][1] * Mm[1][b] + GS3[a][2] * Mm[2][b]);
             gsc[b] += gm * o.R[3 * a + b];
-            GR[a][b] = gm * o.s[b];
+            GR[a][b] = gm * o.se[b];
         }
+    const float v3 = S.g_filt3 ? __ldg(S.g_filt3 + gi) : 0.f;
+    if (v3 != 0.f) {
+        // dse/ds = s/se; k3 = prod |s_j|/se_j: dk3/ds_j = k3 v / (s_j se_j^2)
+        const float dk3 = my[3] * o.sigma0 * o.k2;
+        for (int b = 0; b < 3; ++b) {
+            gsc[b] *= o.s[b] / o.se[b];
+            if (o.s[b] != 0.f) gsc[b] += dk3 * o.k3 * v3 / (o.s[b] * o.se[b] * o.se[b]);
+        }
+    }
     if (G.g_scale) for (int b = 0; b < 3; ++b) G.g_scale[3 * gi + b] = gsc[b];
     // R(qhat) -> qhat -> q (through the normalisation)
     const float w = o.qn[0], qx = o.qn[1], qy = o.qn[2], qz = o.qn[3];

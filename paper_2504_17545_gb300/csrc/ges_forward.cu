@@ -811,6 +811,71 @@ cudaError_t launch_forward(const SceneView &S, const CamParams &C, const OptPara
     return cudaGetLastError();
 }
 
+namespace {
+// Mip-GES 3D filter variance (Sec. 6.1, Mip-Splatting's world filter): per
+// Gaussian, the highest sampling rate max(fx, fy)/z over the cameras whose
+// image rectangle holds the projected centre at z > znear; v = s3d / rate^2,
+// -1 while unseen.  The largest v seen is kept in *vmax (non-negative floats
+// order like their bit patterns, so an integer max is exact and order free).
+constexpr int kFiltCams = 32;
+
+__global__ void __launch_bounds__(256) k_filter3d(SceneView S, const CamParams *__restrict__ cams, int n_cams,
+                                                  float s3d, float *__restrict__ out, unsigned *vmax)
+{
+    __shared__ __align__(16) unsigned char cbuf[kFiltCams * sizeof(CamParams)];
+    const CamParams *sc = reinterpret_cast<const CamParams *>(cbuf);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float px = 0.f, py = 0.f, pz = 0.f;
+    if (i < S.M) { px = __ldg(S.g_pos + 3 * i); py = __ldg(S.g_pos + 3 * i + 1); pz = __ldg(S.g_pos + 3 * i + 2); }
+    float nu = 0.f;
+    for (int c0 = 0; c0 < n_cams; c0 += kFiltCams) {
+        const int nc = min(kFiltCams, n_cams - c0);
+        __syncthreads();
+        const int *src = reinterpret_cast<const int *>(cams + c0);
+        int *dst = reinterpret_cast<int *>(cbuf);
+        for (int k = threadIdx.x; k < nc * (int)(sizeof(CamParams) / 4); k += blockDim.x) dst[k] = src[k];
+        __syncthreads();
+        if (i >= S.M) continue;
+        for (int c = 0; c < nc; ++c) {
+            const CamParams &C = sc[c];
+            const df tz = df_dot3_plus(C.R + 6, px, py, pz, C.t[2]);
+            if (!(tz.hi > C.znear || (tz.hi == C.znear && tz.lo > 0.f))) continue;
+            const df tx = df_dot3_plus(C.R, px, py, pz, C.t[0]);
+            const df ty = df_dot3_plus(C.R + 3, px, py, pz, C.t[1]);
+            const float u = df_add_f(df_mul_f(df_div(tx, tz), C.fx), C.cx).hi;
+            const float v = df_add_f(df_mul_f(df_div(ty, tz), C.fy), C.cy).hi;
+            if (!(u >= 0.f && u <= (float)C.W && v >= 0.f && v <= (float)C.H)) continue;
+            nu = fmaxf(nu, fmaxf(C.fx, C.fy) / tz.hi);
+        }
+    }
+    if (i >= S.M) return;
+    if (nu > 0.f) {
+        const float v = s3d / (nu * nu);
+        out[i] = v;
+        atomicMax(vmax, __float_as_uint(v));
+    } else {
+        out[i] = -1.f;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_filter3d_fill(int64_t M, float *__restrict__ out, const unsigned *vmax)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < M && out[i] < 0.f) out[i] = __uint_as_float(*vmax);
+}
+}  // namespace
+
+cudaError_t launch_filter3d(const SceneView &S, const CamParams *d_cams, int n_cams, float s3d, float *out,
+                            unsigned *d_vmax, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(d_vmax, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess || S.M == 0) return e;
+    const unsigned blocks = (unsigned)((S.M + 255) / 256);
+    k_filter3d<<<blocks, 256, 0, st>>>(S, d_cams, n_cams, s3d, out, d_vmax);
+    k_filter3d_fill<<<blocks, 256, 0, st>>>(S.M, out, d_vmax);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_count(const SceneView &S, const CamParams &C, const OptParams &O, const ViewScratch &X,
                          cudaStream_t st)
 {

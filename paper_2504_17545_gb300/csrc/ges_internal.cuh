@@ -47,6 +47,7 @@ struct OptParams {
     float eps_value, eps_factor, lowpass, alpha_min, surfel_r2, surfel_r;
     int mode;
     int samples;          // surfel samples per pixel: 1 or 4
+    int filter;           // GES_FILTER_EWA or GES_FILTER_MIP
 };
 
 struct SceneView {
@@ -56,6 +57,7 @@ struct SceneView {
     const void *s_rot, *s_scale, *s_sh;
     const float *g_pos;
     const void *g_rot, *g_scale, *g_opac, *g_sh;
+    const float *g_filt3;     // Mip-GES 3D filter variance [M], or null
 };
 
 // Scratch of one view (device pointers owned by the scene).
@@ -117,6 +119,10 @@ cudaError_t launch_forward(const SceneView &S, const CamParams &C, const OptPara
 
 cudaError_t launch_count(const SceneView &S, const CamParams &C, const OptParams &O, const ViewScratch &X,
                          cudaStream_t st);
+// Mip-GES 3D filter variance per Gaussian from n_cams cameras (device array);
+// d_vmax: one device word of scratch.
+cudaError_t launch_filter3d(const SceneView &S, const CamParams *d_cams, int n_cams, float s3d, float *out,
+                            unsigned *d_vmax, cudaStream_t st);
 
 cudaError_t launch_backward(const SceneView &S, const CamParams &C, const OptParams &O, const float *dL_drgb,
                             const float *out_rgb, const float *out_depth, const int32_t *surfel_id,
@@ -613,11 +619,18 @@ struct GaussOut {
     float tx, ty, tz;
     float S2a, S2b, S2c;      // Sigma2 (with low-pass)
     float ia, ib, ic;         // conic Sigma2^-1 (unscaled)
+    float sigma0, k3, k2;     // stored opacity and the Mip-GES 3D / screen filter factors
+    float se[3];              // axis lengths after the 3D filter (= s without it)
+    float n0, n1, det0;       // Sigma2 before the screen filter: diagonal and determinant
     int x0, y0, x1, y1;
 };
 
 // Per-Gaussian set-up (Eq. 4: projected covariance and centre; 1/255 clamp
 // gives the exact support q <= 2 ln(sigma/alpha_min); eps of Sec. 5).
+// Mip-GES (Sec. 6.1): the 3D filter variance v widens the axes to
+// sqrt(s^2 + v) and scales the opacity by prod |s_j| / sqrt(s_j^2 + v); the
+// screen filter (GES_FILTER_MIP) scales it by sqrt(|Sigma2'| / |Sigma2' + lowpass I|),
+// Sigma2' the projected covariance before the dilation.
 __device__ __forceinline__ void gauss_setup(const SceneView &S, const CamParams &C, const OptParams &O,
                                             int64_t i, GaussOut &o)
 {
@@ -628,7 +641,19 @@ __device__ __forceinline__ void gauss_setup(const SceneView &S, const CamParams 
     for (int k = 0; k < 4; ++k) q[k] = load_attr(S.g_rot, 4 * i + k, S.attr_dtype);
     if (!quat_to_rot(q[0], q[1], q[2], q[3], o.R, o.qn, &o.qnorm)) { o.valid_quat = false; return; }
     for (int k = 0; k < 3; ++k) o.s[k] = load_attr(S.g_scale, 3 * i + k, S.attr_dtype);
-    const float sigma = load_attr(S.g_opac, i, S.attr_dtype);
+    float sigma = load_attr(S.g_opac, i, S.attr_dtype);
+    o.sigma0 = sigma;
+    o.k3 = 1.f; o.k2 = 1.f;
+    o.se[0] = o.s[0]; o.se[1] = o.s[1]; o.se[2] = o.s[2];
+    if (S.g_filt3) {
+        const float v = __ldg(S.g_filt3 + i);
+        if (v != 0.f) {
+            for (int k = 0; k < 3; ++k) {
+                o.se[k] = sqrtf(fmaf(o.s[k], o.s[k], v));
+                o.k3 *= fabsf(o.s[k]) / o.se[k];
+            }
+        }
+    }
     {
         float vx = C.ocam[0] - px, vy = C.ocam[1] - py, vz = C.ocam[2] - pz;
         float L = sqrtf(vx * vx + vy * vy + vz * vz);
@@ -636,7 +661,8 @@ __device__ __forceinline__ void gauss_setup(const SceneView &S, const CamParams 
         o.dir[0] = vx * il; o.dir[1] = vy * il; o.dir[2] = vz * il;
         o.dist = L;
     }
-    if (!(sigma >= O.alpha_min)) return;       // alpha <= sigma < alpha_min everywhere
+    // alpha <= sigma k3 k2 <= sigma k3 < alpha_min everywhere
+    if (!(sigma * o.k3 >= O.alpha_min)) return;
     df t[3];
     for (int r = 0; r < 3; ++r) t[r] = df_dot3_plus(C.R + 3 * r, px, py, pz, C.t[r]);
     if (!(t[2].hi > C.znear || (t[2].hi == C.znear && t[2].lo > 0.f))) return;
@@ -645,7 +671,7 @@ __device__ __forceinline__ void gauss_setup(const SceneView &S, const CamParams 
     // Sigma3 = (R S)(R S)^T, kept factored as Mm = R S
     float Mm[9];
     for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) Mm[3 * a + b] = o.R[3 * a + b] * o.s[b];
+        for (int b = 0; b < 3; ++b) Mm[3 * a + b] = o.R[3 * a + b] * o.se[b];
     // T = J Rc with the affine Jacobian of the perspective map at the centre
     const float iz = 1.f / z;
     const float J00 = C.fx * iz, J02 = -C.fx * x * iz * iz, J11 = C.fy * iz, J12 = -C.fy * y * iz * iz;
@@ -670,8 +696,13 @@ __device__ __forceinline__ void gauss_setup(const SceneView &S, const CamParams 
     const float s2c = n1 + O.lowpass;
     const float x0c = P0[1] * P1[2] - P0[2] * P1[1], x1c = P0[2] * P1[0] - P0[0] * P1[2];
     const float x2c = P0[0] * P1[1] - P0[1] * P1[0];
-    const float det = (x0c * x0c + x1c * x1c + x2c * x2c) + O.lowpass * (n0 + n1) + O.lowpass * O.lowpass;
+    const float det0 = x0c * x0c + x1c * x1c + x2c * x2c;
+    const float det = det0 + O.lowpass * (n0 + n1) + O.lowpass * O.lowpass;
     if (!(det > 0.f) || !isfinite(det) || !(s2a > 0.f)) return;
+    o.n0 = n0; o.n1 = n1; o.det0 = det0;
+    if (O.filter == GES_FILTER_MIP) o.k2 = sqrtf(det0 / det);
+    sigma *= o.k3 * o.k2;
+    if (!(sigma >= O.alpha_min)) return;
     const float idet = 1.f / det;
     const float ia = s2c * idet, ib = -s2b * idet, ic = s2a * idet;
     // Cholesky factor of the conic: a = 1/sqrt(s2a), b = -s2b/(sqrt(s2a det)), c = sqrt(s2a/det)

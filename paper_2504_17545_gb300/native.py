@@ -16,6 +16,7 @@ GES_OK, GES_ERR_INVALID_ARG, GES_ERR_CUDA, GES_ERR_OOM, GES_ERR_TIMEOUT, GES_ERR
     GES_ERR_UNSUPPORTED, GES_ERR_CAPACITY = range(8)
 GES_F32, GES_F16, GES_BF16 = 0, 1, 2
 GES_MODE_FULL, GES_MODE_SURFELS_ONLY, GES_MODE_GAUSSIANS_ONLY = 0, 1, 2
+GES_FILTER_EWA, GES_FILTER_MIP = 0, 1
 GES_EPS_ADAPTIVE, GES_EPS_ZERO, GES_EPS_CONST = 0, 1, 2
 GES_PROFILE_SLOTS = 8
 
@@ -34,7 +35,7 @@ class ges_scene_desc(C.Structure):
                 ("attr_dtype", C.c_int32), ("sh_dtype", C.c_int32),
                 ("s_pos", C.c_void_p), ("s_rot", C.c_void_p), ("s_scale", C.c_void_p), ("s_sh", C.c_void_p),
                 ("g_pos", C.c_void_p), ("g_rot", C.c_void_p), ("g_scale", C.c_void_p), ("g_opac", C.c_void_p),
-                ("g_sh", C.c_void_p)]
+                ("g_sh", C.c_void_p), ("g_filter3d", C.c_void_p)]
 
 
 class ges_camera(C.Structure):
@@ -46,7 +47,7 @@ class ges_camera(C.Structure):
 class ges_render_opts(C.Structure):
     _fields_ = [("eps_mode", C.c_int32), ("eps_value", C.c_float), ("eps_factor", C.c_float),
                 ("lowpass", C.c_float), ("alpha_min", C.c_float), ("surfel_r2", C.c_float), ("mode", C.c_int32),
-                ("samples", C.c_int32)]
+                ("samples", C.c_int32), ("filter", C.c_int32)]
 
 
 class ges_grads(C.Structure):
@@ -86,6 +87,7 @@ _SIGS = {
                                    _P(ges_render_opts), _P(C.c_void_p), _P(C.c_void_p)]),
     "ges_render_noalloc": (C.c_int, [_P(ges_scene_desc), _P(ges_camera), _P(ges_render_opts), C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ges_compute_filter3d": (C.c_int, [C.c_void_p, _P(ges_camera), C.c_int32, C.c_float, C.c_void_p]),
     "ges_count_fragments": (C.c_int, [C.c_void_p, _P(ges_camera), _P(ges_render_opts), _P(C.c_int64),
                                       _P(C.c_int64)]),
     "ges_batch_create": (C.c_int, [_P(C.c_void_p), _P(ges_camera), _P(C.c_int32), C.c_int32,
@@ -217,6 +219,12 @@ def ges_count_fragments(scene, cam: ges_camera, opts):
     _check(load().ges_count_fragments(scene, C.byref(cam), C.byref(opts) if opts is not None else None,
                                       C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+def ges_compute_filter3d(scene, cams, s3d: float, out_var) -> None:
+    n = len(cams)
+    cm = (ges_camera * n)(*cams)
+    _check(load().ges_compute_filter3d(scene, cm, n, float(s3d), out_var))
 
 
 def ges_batch_create(scenes, cams, scene_of_view, opts, out_rgb, out_depth):

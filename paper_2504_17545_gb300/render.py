@@ -49,7 +49,7 @@ class GESScene:
     """A GES scene resident in device memory (tensors owned here) and the
     library's handle that views them."""
 
-    def __init__(self, sh_degree: int, **tensors: torch.Tensor):
+    def __init__(self, sh_degree: int, g_filter3d: Optional[torch.Tensor] = None, **tensors: torch.Tensor):
         missing = [k for k in _SCENE_KEYS if k not in tensors]
         if missing:
             raise KeyError(f"missing scene tensors {missing}")
@@ -60,6 +60,7 @@ class GESScene:
             if not v.is_cuda:
                 raise ValueError(f"{k} must be a CUDA tensor")
             self.t[k] = v.contiguous()
+        self.g_filter3d = self._check_filter(g_filter3d)
         attr = self.t["s_rot"].dtype
         for k in ("s_scale", "g_rot", "g_scale", "g_opac"):
             if self.t[k].dtype != attr:
@@ -73,9 +74,17 @@ class GESScene:
         self._desc = self._make_desc()
         self.handle = N.ges_create_scene(self._desc)
 
+    def _check_filter(self, f: Optional[torch.Tensor]) -> Optional[torch.Tensor]:
+        if f is None:
+            return None
+        if not f.is_cuda or f.dtype != torch.float32 or tuple(f.shape) != (self.n_gaussians,):
+            raise ValueError("g_filter3d must be a float32 CUDA tensor of shape [M]")
+        return f.contiguous()
+
     @classmethod
     def from_arrays(cls, scene, device="cuda", attr_dtype=torch.float32, sh_dtype=torch.float32) -> "GESScene":
-        """From a host scene (``scenegen.Scene`` or anything with the same array attributes)."""
+        """From a host scene (``scenegen.Scene`` or anything with the same array
+        attributes; an optional ``g_filter3d`` array is carried over)."""
         t = {}
         for k in _SCENE_KEYS:
             a = torch.as_tensor(getattr(scene, k))
@@ -85,7 +94,9 @@ class GESScene:
             elif k in ("s_sh", "g_sh"):
                 dt = sh_dtype
             t[k] = a.to(device=device, dtype=dt).contiguous()
-        return cls(scene.sh_degree, **t)
+        f3 = getattr(scene, "g_filter3d", None)
+        f3 = None if f3 is None else torch.as_tensor(f3).to(device=device, dtype=torch.float32).contiguous()
+        return cls(scene.sh_degree, g_filter3d=f3, **t)
 
     @property
     def n_surfels(self) -> int:
@@ -101,16 +112,32 @@ class GESScene:
         d.sh_degree, d.attr_dtype, d.sh_dtype = self.sh_degree, self.attr_dtype, self.sh_dtype
         for k in _SCENE_KEYS:
             setattr(d, k, self.t[k].data_ptr() if self.t[k].numel() else None)
+        f3 = getattr(self, "g_filter3d", None)
+        d.g_filter3d = f3.data_ptr() if f3 is not None and f3.numel() else None
         return d
 
     def update(self, **tensors: torch.Tensor):
-        """Swap some attribute tensors (same dtypes) and re-point the handle."""
+        """Swap some attribute tensors (same dtypes) and re-point the handle.
+        ``g_filter3d=None`` removes the Mip-GES 3D filter."""
         for k, v in tensors.items():
+            if k == "g_filter3d":
+                continue
             if k not in _SCENE_KEYS:
                 raise KeyError(k)
             self.t[k] = v.contiguous()
+        if "g_filter3d" in tensors:
+            self.g_filter3d = self._check_filter(tensors["g_filter3d"])
         self._desc = self._make_desc()
         N.ges_scene_update(self.handle, self._desc)
+
+    def compute_filter3d(self, cams, s3d: float = 0.2) -> torch.Tensor:
+        """Mip-GES 3D filter variance per Gaussian from training cameras
+        (ges_compute_filter3d); pass it to ``update(g_filter3d=...)``."""
+        out = torch.empty((self.n_gaussians,), device=self.t["g_pos"].device, dtype=torch.float32)
+        self.bind_stream()
+        N.ges_compute_filter3d(self.handle, [camera_struct(c) for c in cams], s3d,
+                               out.data_ptr() if out.numel() else None)
+        return out
 
     def bind_stream(self):
         N.ges_set_stream(self.handle, torch.cuda.current_stream(self.t["s_pos"].device).cuda_stream)

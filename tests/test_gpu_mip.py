@@ -1,0 +1,167 @@
+"""Mip-GES (Sec. 6.1) on the GPU vs the FP64 oracle: the 3D filter variance
+from training cameras, the filtered forward pass, its backward, the batch
+graph."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import scenegen as sg
+from parity import compare
+from test_gpu_backward import _check, _grads_gpu
+from test_gpu_forward import _render, _small
+
+pytestmark = pytest.mark.gpu
+
+MIP = dict(filter=1, lowpass=0.1)
+
+
+@pytest.fixture(scope="module")
+def R():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_17545_gb300 import render as R
+    return R
+
+
+def _assert(res):
+    assert res["pass"], res
+
+
+def _ring(n, W, H, r=2.8, fov=55.0):
+    return [sg.look_at((r * math.cos(a), 0.3, r * math.sin(a)), (0, 0, 0), (0, 1, 0), W, H, fov)
+            for a in np.linspace(0, 2 * math.pi, n, endpoint=False)]
+
+
+def _filter_matches(gpu, ref):
+    """GPU float32 vs FP64: relative 1e-5, except where a centre sits on an
+    image edge of some camera (then the seen/unseen decision may differ)."""
+    rel = np.abs(gpu - ref) / np.maximum(np.abs(ref), 1e-30)
+    bad = rel > 1e-5
+    return int(bad.sum()), float(rel[~bad].max()) if (~bad).any() else 0.0
+
+
+def test_filter3d_matches_oracle(R):
+    scene, cams = sg.config_scene(1)
+    gs = R.GESScene.from_arrays(scene)
+    v = gs.compute_filter3d(cams, 0.2).cpu().numpy().astype(np.float64)
+    ref = oracle.filter3d(scene, cams, 0.2)
+    nbad, worst = _filter_matches(v, ref)
+    assert nbad <= max(3, scene.n_gaussians // 100000), (nbad, worst)
+    assert (ref > 0).all() and worst < 1e-5
+    gs.close()
+
+
+def test_filter3d_unseen_gaussians(R):
+    sc = _small(61, 50, 400)
+    sc.g_pos = sc.g_pos.copy()
+    sc.g_pos[:9] += np.array([0.0, 60.0, 0.0], np.float32)
+    cams = _ring(5, 90, 70)
+    gs = R.GESScene.from_arrays(sc)
+    v = gs.compute_filter3d(cams, 0.2).cpu().numpy().astype(np.float64)
+    ref = oracle.filter3d(sc, cams, 0.2)
+    assert _filter_matches(v, ref)[0] == 0
+    assert np.all(v[:9] == v.max())
+    gs.close()
+
+
+def test_mip_parity_workload_128(R):
+    scene, cams = sg.config_scene(0)
+    scene.g_filter3d = oracle.filter3d(scene, _ring(8, 128, 128), 0.2).astype(np.float32)
+    ref = oracle.render(scene, cams[0], MIP)
+    res = compare(scene, cams[0], _render(R, scene, cams[0], MIP), ref, MIP)
+    _assert(res)
+    assert res["compared_px"] > 0.95 * 128 * 128
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+def test_mip_parity_ragged_and_modes(R, mode):
+    scene = _small(62)
+    scene.g_filter3d = np.random.default_rng(3).uniform(0.0, 3e-3, scene.n_gaussians).astype(np.float32)
+    opts = dict(MIP, mode=mode)
+    cams = [sg.look_at((0.2, 0.3, -2.8), (0, 0, 0), (0, 1, 0), 203, 141, 55.0),
+            sg.look_at((0.1, 0.05, -0.6), (0, 0.1, 1), (0, 1, 0), 97, 61, 95.0)]
+    for cam in cams:
+        ref = oracle.render(scene, cam, opts)
+        _assert(compare(scene, cam, _render(R, scene, cam, opts), ref, opts))
+
+
+def test_mip_screen_filter_alone_and_options(R):
+    """Screen filter without a 3D filter, at two filter sizes; the 3D filter
+    with the plain EWA dilation."""
+    scene = _small(63)
+    cam = sg.look_at((0.0, -0.4, -2.5), (0, 0, 0), (0, 1, 0), 120, 88, 60.0)
+    for opts in (dict(filter=1, lowpass=0.1), dict(filter=1, lowpass=0.5)):
+        ref = oracle.render(scene, cam, opts)
+        _assert(compare(scene, cam, _render(R, scene, cam, opts), ref, opts))
+    scene.g_filter3d = np.random.default_rng(4).uniform(0.0, 3e-3, scene.n_gaussians).astype(np.float32)
+    ref = oracle.render(scene, cam)
+    _assert(compare(scene, cam, _render(R, scene, cam), ref))
+
+
+def test_mip_parity_1080p_orbit_camera(R):
+    """The 1080p workload with the 3D filter from all 64 orbit cameras and the
+    screen filter."""
+    scene, cams = sg.config_scene(1)
+    gs = R.GESScene.from_arrays(scene)
+    f3 = gs.compute_filter3d(cams, 0.2)
+    gs.update(g_filter3d=f3)
+    scene.g_filter3d = f3.cpu().numpy().astype(np.float64)   # the oracle renders the same filter values
+    for k in (16, 40):
+        ref = oracle.render(scene, cams[k], MIP)
+        res = compare(scene, cams[k], R.render(gs, cams[k], MIP), ref, MIP)
+        _assert(res)
+        assert res["masked_frac"] < 0.01
+    gs.close()
+
+
+def test_mip_reduced_precision_storage(R):
+    torch = pytest.importorskip("torch")
+    scene, cams = sg.config_scene(0)
+    scene.g_filter3d = oracle.filter3d(scene, _ring(8, 128, 128), 0.2).astype(np.float32)
+    deq = scene.subset()
+    for k in ("s_rot", "s_scale", "g_rot", "g_scale", "g_opac", "s_sh", "g_sh"):
+        setattr(deq, k, torch.as_tensor(getattr(scene, k)).to(torch.float16).float().numpy())
+    deq.g_filter3d = scene.g_filter3d.astype(np.float32).astype(np.float64)
+    out = _render(R, scene, cams[0], MIP, attr_dtype=torch.float16, sh_dtype=torch.float16)
+    _assert(compare(deq, cams[0], out, oracle.render(deq, cams[0], MIP), MIP))
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+def test_mip_backward_crop_matches_oracle(R, mode):
+    scene, cam = sg.crop_scene(7)
+    scene.g_filter3d = np.random.default_rng(18).uniform(0.0, 2e-4, scene.n_gaussians).astype(np.float32)
+    g = np.random.default_rng(19).standard_normal((3, cam.height, cam.width))
+    opts = dict(MIP, mode=mode)
+    ref = oracle.backward(scene, cam, g, opts)
+    gpu, _ = _grads_gpu(R, scene, cam, g, opts)
+    _check(gpu, ref, ["g_pos", "g_rot", "g_scale", "g_opac", "g_sh"], scene, cam, opts)
+
+
+def test_mip_backward_parity_workload(R):
+    scene, cams = sg.config_scene(0)
+    scene.g_filter3d = oracle.filter3d(scene, _ring(8, 128, 128), 0.2).astype(np.float32)
+    g = np.random.default_rng(20).standard_normal((3, 128, 128))
+    ref = oracle.backward(scene, cams[0], g, MIP)
+    gpu, _ = _grads_gpu(R, scene, cams[0], g, MIP)
+    _check(gpu, ref, ["g_pos", "g_rot", "g_scale", "g_opac", "g_sh", "s_sh"], scene, cams[0], MIP)
+
+
+def test_mip_batch_graph_equals_single_views(R):
+    scene, cams = sg.config_scene(0)
+    scene.g_filter3d = oracle.filter3d(scene, _ring(8, 128, 128), 0.2).astype(np.float32)
+    other = _small(64, 2000, 6000)
+    ga, gb = R.GESScene.from_arrays(scene), R.GESScene.from_arrays(other)
+    views = [cams[0], sg.look_at((0.5, 0, -2.8), (0, 0, 0), (0, 1, 0), 301, 173, 60.0)]
+    sov = [0, 1]
+    b = R.GESBatch([ga, gb], views, sov, opts=MIP)
+    b.launch()
+    b.sync()
+    for v in range(2):
+        single = R.render([ga, gb][sov[v]], views[v], MIP)
+        assert (b.rgb[v] == single["rgb"]).all() and (b.depth[v] == single["depth"]).all(), v
+    b.close()
+    ga.close()
+    gb.close()
