@@ -262,6 +262,7 @@ def uneven_extra(R, N, sg):
     3840x2160, FP16 storage, one camera each: aggregate Mpixel/s of the
     batch graph (one launch per phase over all scenes) and of the per-view
     loop."""
+    import numpy as np
     import torch
     scenes, cams = [], []
     for part in sg.uneven_parts():
@@ -274,6 +275,18 @@ def uneven_extra(R, N, sg):
     ms_graph = _time(lambda: b.launch(), 10)
     b.sync()
     info = b.info()
+    # per-scene completion (device %globaltimer stamps when each scene's last
+    # tile retires, from the start of the batch), over 200 launches
+    times = []
+    for _ in range(200):
+        b.launch()
+        b.sync()
+        times.append(b.view_times())
+    T = np.array(times)
+    per_scene = [{"scene_prims": scenes[k].n_surfels + scenes[k].n_gaussians,
+                  "pixels": cams[k].width * cams[k].height,
+                  "p50_ms": float(np.percentile(T[:, k], 50)), "p99_ms": float(np.percentile(T[:, k], 99))}
+                 for k in range(len(cams))]
     outs = [(torch.empty((3, c.height, c.width), device="cuda"), torch.empty((c.height, c.width), device="cuda"))
             for c in cams]
     ms_loop = _time(lambda: R.render_batch(scenes, cams, sov, outputs=outs), 5)
@@ -282,7 +295,8 @@ def uneven_extra(R, N, sg):
         g.close()
     return {"workload": "uneven-8-scenes-100k-to-3M-fp16", "pixels": px,
             "graph_mpix_per_s": px / (ms_graph / 1e3) / 1e6, "loop_mpix_per_s": px / (ms_loop / 1e3) / 1e6,
-            "graph_ms": ms_graph, "autotuned": {"prims_per_cta": info.prims_per_cta,
+            "graph_ms": ms_graph, "per_scene_completion": per_scene,
+            "autotuned": {"prims_per_cta": info.prims_per_cta,
                                                 "raster_ctas_per_sm": info.raster_ctas_per_sm,
                                                 "candidates": info.candidates}}
 
@@ -342,6 +356,27 @@ def mip_extra(R, N, gs, cams):
             "kernel_ms_per_frame": {k: prof[k][0] / prof[k][1] / len(cams) for k in prof},
             "gauss_terms_per_frame": float(np.mean([f[1] for f in frags])),
             "autotuned": {"prims_per_cta": info.prims_per_cta, "raster_ctas_per_sm": info.raster_ctas_per_sm}}
+
+
+def paper_shaped_extra(R, N, sg):
+    """Context workload with the paper's primitive mix (Table 6, Garden:
+    0.2M surfels + 2.5M Gaussians) at 1080p, 8 orbit views as one batch graph,
+    FP32 and FP16 storage."""
+    import torch
+    scene, cams = sg.config_scene(100)
+    res = {"workload": "1080p-200k-surfels-2.5M-gaussians-orbit8"}
+    for name, dt in (("fp32", torch.float32), ("fp16", torch.float16)):
+        gs = R.GESScene.from_arrays(scene, attr_dtype=dt, sh_dtype=dt)
+        b = R.GESBatch([gs], cams)
+        ms = _time(lambda: (b.launch(), b.sync()), 5)
+        b.profile(reset=True)
+        _time(lambda: (b.launch(), b.sync()), 5, warm=0)
+        prof = b.profile()
+        b.close()
+        gs.close()
+        res[f"{name}_frames_per_s"] = len(cams) / (ms / 1e3)
+        res[f"{name}_kernel_ms_per_frame"] = {k: prof[k][0] / prof[k][1] / len(cams) for k in prof}
+    return res
 
 
 def main():
@@ -460,6 +495,7 @@ def main():
         extras["uneven_batch"] = uneven_extra(R, N, sg)
         extras["msaa_4x"] = msaa_extra(R, N, gs, cams)
         extras["mip_ges"] = mip_extra(R, N, gs, cams)
+        extras["paper_shaped"] = paper_shaped_extra(R, N, sg)
     if rank != 0:
         return
     # roofline of the dominant kernel (largest share of device time); one

@@ -309,6 +309,12 @@ GES_API ges_status ges_batch_sync(ges_batch *batch);
 
 GES_API ges_status ges_batch_get_info(const ges_batch *batch, ges_batch_info *out);
 
+/* Per-view completion times of the last synchronised launch: ms_out[v] (host,
+ * n_views entries) = milliseconds from the start of the batch's first kernel
+ * to the moment the raster finished view v's last tile (%globaltimer stamps
+ * taken on the device), or -1 if unavailable.  Call after ges_batch_sync. */
+GES_API ges_status ges_batch_get_view_times(const ges_batch *batch, double *ms_out);
+
 /* Device time per phase (preprocess, scan, fill, raster) summed over the
  * launches waited for by ges_batch_sync (CUDA-event nodes inside the graph
  * time the most recent launch at each sync); reset != 0 clears the sums. */

@@ -873,6 +873,19 @@ ges_status ges_batch_get_info(const ges_batch *b, ges_batch_info *out)
     return GES_OK;
 }
 
+ges_status ges_batch_get_view_times(const ges_batch *b, double *ms_out)
+{
+    if (!b || !ms_out) return fail(GES_ERR_INVALID_ARG, "NULL argument");
+    uint64_t t0 = 0;
+    std::memcpy(&t0, b->h_status + (size_t)b->n * ST_WORDS + 2, sizeof t0);
+    for (int v = 0; v < b->n; ++v) {
+        uint64_t t = 0;
+        std::memcpy(&t, b->h_status + (size_t)v * ST_WORDS + ST_TDONE, sizeof t);
+        ms_out[v] = (t0 != 0 && t >= t0) ? (double)(t - t0) * 1e-6 : -1.0;
+    }
+    return GES_OK;
+}
+
 ges_status ges_batch_get_profile(ges_batch *b, ges_profile *out, int32_t reset)
 {
     if (!b || !out) return fail(GES_ERR_INVALID_ARG, "NULL argument");

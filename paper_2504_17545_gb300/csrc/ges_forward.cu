@@ -572,14 +572,19 @@ __device__ __forceinline__ void load_view(const BatchView *V, int v, BatchView &
     for (int k = threadIdx.x; k < (int)(sizeof(BatchView) / 4); k += blockDim.x) d[k] = src[k];
 }
 
-__global__ void __launch_bounds__(kPrepThreads, 2) k_bprep(const BatchView *V, int n, OptParams O)
+__global__ void __launch_bounds__(kPrepThreads, 2) k_bprep(const BatchView *V, int n, OptParams O,
+                                                          unsigned long long *t0)
 {
     extern __shared__ unsigned hist[];
     __shared__ unsigned vcnt;
     __shared__ __align__(16) unsigned char bv_raw[sizeof(BatchView)];
     BatchView &bv = *reinterpret_cast<BatchView *>(bv_raw);
     __shared__ int sv;
-    if (threadIdx.x == 0) sv = find_view(n, blockIdx.x, [&](int k) { return V[k].prep_base; });
+    if (threadIdx.x == 0) {
+        // the first CTA to start stamps the batch's start time (t0 is zeroed per launch)
+        atomicCAS(t0, 0ull, global_timer_ns());
+        sv = find_view(n, blockIdx.x, [&](int k) { return V[k].prep_base; });
+    }
     __syncthreads();
     load_view(V, sv, bv);
     __syncthreads();
@@ -651,6 +656,9 @@ __global__ void __launch_bounds__(kRasterThreads, kS == 1 ? 5 : 4) k_braster(con
         if (!(bv.X.status[ST_FLAGS] & (FLAG_SOVF | FLAG_GOVF)))
             raster_tile<kS>(bv.X, bv.C, O, bv.rgb, bv.depth, nullptr, nullptr, it - bv.tile_base, ss, sgs);
         __syncthreads();
+        // per-view completion time: the CTA that finishes the view's last tile stamps it
+        if (threadIdx.x == 0 && atomicAdd(bv.X.status + ST_RETIRED, 1u) + 1u == (unsigned)bv.T)
+            *reinterpret_cast<unsigned long long *>(bv.X.status + ST_TDONE) = global_timer_ns();
     }
 }
 
@@ -663,7 +671,8 @@ cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const Opt
     auto mark = [&](int k) { if (ev) cudaEventRecordWithFlags(ev[k], st, cudaEventRecordExternal); };
     mark(0);
     if (P.total_prep > 0)
-        k_bprep<<<P.total_prep, kPrepThreads, local_bins_smem(P.max_T, false), st>>>(d_views, P.n, O);
+        k_bprep<<<P.total_prep, kPrepThreads, local_bins_smem(P.max_T, false), st>>>(
+            d_views, P.n, O, reinterpret_cast<unsigned long long *>(work_counter + 2));
     mark(1);
     if (P.total_colscan > 0) k_bcolscan<<<dim3(P.total_colscan, 2), 256, 0, st>>>(d_views, P.n);
     k_bscan<<<2 * P.n, 1024, 0, st>>>(d_views);

@@ -28,6 +28,8 @@ enum : int {
     ST_GPAIRS = 4,        // Gaussian tile pairs
     ST_SFRAG = 5,         // surfel fragments inside their discs (work count)
     ST_GFRAG = 6,         // Gaussian pixel terms with alpha >= alpha_min (work count)
+    ST_RETIRED = 7,       // batch raster: tiles of this view finished
+    ST_TDONE = 8,         // batch raster: %globaltimer (ns, 64-bit, words 8-9) when the last tile finished
     ST_WORDS = 16,
 };
 enum : unsigned { FLAG_SOVF = 1u, FLAG_GOVF = 2u, FLAG_BADQ = 4u };
@@ -190,6 +192,13 @@ __device__ __forceinline__ df df_dot3_plus(const float *R, float v0, float v1, f
     acc = df_add(acc, df_two_prod(R[1], v1));
     acc = df_add(acc, df_two_prod(R[2], v2));
     return df_add_f(acc, t);
+}
+
+__device__ __forceinline__ unsigned long long global_timer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
 __device__ __forceinline__ float ex2_approx(float x)

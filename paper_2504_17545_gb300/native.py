@@ -97,6 +97,7 @@ _SIGS = {
     "ges_batch_sync": (C.c_int, [C.c_void_p]),
     "ges_batch_get_info": (C.c_int, [C.c_void_p, _P(ges_batch_info)]),
     "ges_batch_get_profile": (C.c_int, [C.c_void_p, _P(ges_profile), C.c_int32]),
+    "ges_batch_get_view_times": (C.c_int, [C.c_void_p, _P(C.c_double)]),
     "ges_batch_destroy": (C.c_int, [C.c_void_p]),
     "ges_get_stats": (C.c_int, [C.c_void_p, _P(ges_stats)]),
     "ges_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
@@ -259,6 +260,12 @@ def ges_batch_get_info(batch) -> ges_batch_info:
 
 def ges_batch_destroy(batch):
     _check(load().ges_batch_destroy(batch))
+
+
+def ges_batch_get_view_times(batch, n_views: int):
+    out = (C.c_double * n_views)()
+    _check(load().ges_batch_get_view_times(batch, out))
+    return list(out)
 
 
 def ges_batch_get_profile(batch, reset: bool = False) -> dict:

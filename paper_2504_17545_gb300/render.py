@@ -278,6 +278,11 @@ class GESBatch:
     def profile(self, reset: bool = False):
         return N.ges_batch_get_profile(self.handle, reset)
 
+    def view_times(self):
+        """Per-view completion times (ms from the batch's start) of the last
+        synchronised launch."""
+        return N.ges_batch_get_view_times(self.handle, len(self.rgb))
+
     def close(self):
         if getattr(self, "handle", None) is not None:
             N.ges_batch_destroy(self.handle)

@@ -257,3 +257,20 @@ def test_batch_graph_uneven_scenes_equal_single_views(R):
     b.close()
     ga.close()
     gb.close()
+
+
+def test_batch_view_completion_times(R):
+    """Per-view completion stamps of the batch graph: every view gets one, no
+    later than the whole launch."""
+    scene, cams = sg.config_scene(0)
+    other = _small(38, 2000, 6000)
+    ga, gb = R.GESScene.from_arrays(scene), R.GESScene.from_arrays(other)
+    views = [cams[0], sg.look_at((0.5, 0, -2.8), (0, 0, 0), (0, 1, 0), 640, 480, 60.0)]
+    b = R.GESBatch([ga, gb], views, [0, 1])
+    b.launch()
+    b.sync()
+    t = b.view_times()
+    assert len(t) == 2 and all(0.0 < x < 1000.0 for x in t), t
+    b.close()
+    ga.close()
+    gb.close()
