@@ -6,8 +6,8 @@ its Python binding) never does; the two share no code.
 """
 from .oracle import (DEFAULT_OPTS, build, load, render, backward, sh_basis, surfel_eval,
                      surfel_info, gauss_info, id_validity, touching,
-                     count_fragments, filter3d)
+                     count_fragments, filter3d, render_geom)
 
 __all__ = ["DEFAULT_OPTS", "build", "load", "render", "backward", "sh_basis", "surfel_eval",
            "surfel_info", "gauss_info", "id_validity", "touching",
-           "count_fragments", "filter3d"]
+           "count_fragments", "filter3d", "render_geom"]

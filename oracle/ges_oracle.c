@@ -49,6 +49,8 @@ typedef struct {
     const double *s_pos, *s_rot, *s_scale, *s_sh;            /* [N,3] [N,4] [N,2] [N,K,3] */
     const double *g_pos, *g_rot, *g_scale, *g_opac, *g_sh;   /* [M,3] [M,4] [M,3] [M] [M,K,3] */
     const double *g_filt3;   /* [M] Mip-GES 3D filter variance (world units^2), NULL: none */
+    int32_t gauss_dim;       /* 3 (or 0): 3D Gaussians, g_scale [M,3];
+                                2: 2D Gaussians of 2D-GES (Sec. 6.4), g_scale [M,2] */
 } ora_scene;
 
 typedef struct {
@@ -208,9 +210,51 @@ typedef struct {
     double rgb[3], raw[3], dir[3], dist;
     double R[9], qn[4], qnorm;
     int x0, x1, y0, y1;
+    int dim;                            /* 3 or 2 */
+    surf_t geo;                         /* 2D: splat frame, filtered scales (geo.s1, geo.s2) */
+    double S1, S2;                      /* 2D: object-space filter factors (Eq. 18) */
+    double nrm[3];                      /* geometry normal (camera space, facing the camera) */
 } gauss_t;
 
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* Conservative pixel rectangle of the disc a^2 + b^2 <= r^2 of a planar frame
+   (camera-space centre pc, axes tu, tv, scales s1, s2): the disc lies inside
+   the rectangle pc +- r s1 tu +- r s2 tv; clip it to z >= znear, project the
+   vertices, pad by one pixel.  Leaves an empty rectangle when nothing is in
+   front of the near plane or on screen. */
+static void disc_rect(const ora_camera *c, surf_t *sf, double r)
+{
+    double cor[4][3], poly[8][3];
+    const double sg[4][2] = {{1, 1}, {-1, 1}, {-1, -1}, {1, -1}};
+    for (int k = 0; k < 4; ++k)
+        for (int j = 0; j < 3; ++j)
+            cor[k][j] = sf->pc[j] + sg[k][0]*r*sf->s1*sf->tu[j] + sg[k][1]*r*sf->s2*sf->tv[j];
+    int np = 0;
+    double zc = c->znear;
+    for (int k = 0; k < 4; ++k) {
+        const double *a = cor[k], *b = cor[(k + 1) & 3];
+        int ia = a[2] >= zc, ib = b[2] >= zc;
+        if (ia) { memcpy(poly[np++], a, sizeof(double) * 3); }
+        if (ia != ib) {
+            double tt = (zc - a[2]) / (b[2] - a[2]);
+            for (int j = 0; j < 3; ++j) poly[np][j] = a[j] + tt * (b[j] - a[j]);
+            poly[np][2] = zc;
+            ++np;
+        }
+    }
+    if (np == 0) return;
+    double umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+    for (int k = 0; k < np; ++k) {
+        double u = c->fx * poly[k][0] / poly[k][2] + c->cx, w = c->fy * poly[k][1] / poly[k][2] + c->cy;
+        umin = fmin(umin, u); umax = fmax(umax, u); vmin = fmin(vmin, w); vmax = fmax(vmax, w);
+    }
+    if (!(umax >= -1.0 && vmax >= -1.0 && umin <= c->width + 1.0 && vmin <= c->height + 1.0)) return;
+    sf->x0 = clampi((int)floor(umin - 0.5) - 1, 0, c->width - 1);
+    sf->x1 = clampi((int)ceil(umax - 0.5) + 1, 0, c->width - 1);
+    sf->y0 = clampi((int)floor(vmin - 0.5) - 1, 0, c->height - 1);
+    sf->y1 = clampi((int)ceil(vmax - 0.5) + 1, 0, c->height - 1);
+}
 
 static int surfel_setup(const ora_scene *S, const ora_camera *c, const ora_opts *o,
                         const double *ocam, int64_t i, surf_t *sf)
@@ -235,36 +279,7 @@ static int surfel_setup(const ora_scene *S, const ora_camera *c, const ora_opts 
        z >= znear, project its vertices, pad by one pixel. */
     sf->x0 = 1; sf->x1 = 0; sf->y0 = 1; sf->y1 = 0;
     if (!sf->valid) return 1;
-    double r = sqrt(o->surfel_r2 * (1.0 + 2.0 * o->tol_disc_rel));
-    double cor[4][3], poly[8][3];
-    const double sg[4][2] = {{1, 1}, {-1, 1}, {-1, -1}, {1, -1}};
-    for (int k = 0; k < 4; ++k)
-        for (int j = 0; j < 3; ++j)
-            cor[k][j] = sf->pc[j] + sg[k][0]*r*sf->s1*sf->tu[j] + sg[k][1]*r*sf->s2*sf->tv[j];
-    int np = 0;
-    double zc = c->znear;
-    for (int k = 0; k < 4; ++k) {
-        const double *a = cor[k], *b = cor[(k + 1) & 3];
-        int ia = a[2] >= zc, ib = b[2] >= zc;
-        if (ia) { memcpy(poly[np++], a, sizeof(double) * 3); }
-        if (ia != ib) {
-            double tt = (zc - a[2]) / (b[2] - a[2]);
-            for (int j = 0; j < 3; ++j) poly[np][j] = a[j] + tt * (b[j] - a[j]);
-            poly[np][2] = zc;
-            ++np;
-        }
-    }
-    if (np == 0) return 1;
-    double umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
-    for (int k = 0; k < np; ++k) {
-        double u = c->fx * poly[k][0] / poly[k][2] + c->cx, w = c->fy * poly[k][1] / poly[k][2] + c->cy;
-        umin = fmin(umin, u); umax = fmax(umax, u); vmin = fmin(vmin, w); vmax = fmax(vmax, w);
-    }
-    if (!(umax >= -1.0 && vmax >= -1.0 && umin <= c->width + 1.0 && vmin <= c->height + 1.0)) return 1;
-    sf->x0 = clampi((int)floor(umin - 0.5) - 1, 0, c->width - 1);
-    sf->x1 = clampi((int)ceil(umax - 0.5) + 1, 0, c->width - 1);
-    sf->y0 = clampi((int)floor(vmin - 0.5) - 1, 0, c->height - 1);
-    sf->y1 = clampi((int)ceil(vmax - 0.5) + 1, 0, c->height - 1);
+    disc_rect(c, sf, sqrt(o->surfel_r2 * (1.0 + 2.0 * o->tol_disc_rel)));
     return 1;
 }
 
@@ -279,14 +294,82 @@ static int surfel_setup(const ora_scene *S, const ora_camera *c, const ora_opts 
    Both factors keep the Gaussian's integral unchanged (the convolution of a
    Gaussian with a normalised Gaussian kernel).  eps_i uses the stored axis
    lengths s. */
+/* 2D Gaussian of 2D-GES (Sec. 6.4): a planar splat like a surfel (centre p,
+   axes t_u = R e_x, t_v = R e_y, normal R e_z, scales s1, s2) whose opacity is
+   sigma exp(-(a^2 + b^2)/2) at the ray-plane hit (a, b in scale units), with
+   the planar depth of that hit for the depth test.  The screen-space EWA
+   filter of size r = lowpass is back-projected into object space (Eq. 17-18):
+   with J the Jacobian of local unit coordinates -> pixels at the centre, the
+   filtered covariance I + r J^-1 J^-T is approximated by diag(S1^2, S2^2),
+   S_k = sqrt(1 + r ((J^T J)^-1)_kk) (its diagonal), so the scales become
+   s_k S_k and the opacity sigma / (S1 S2).  eps_i = (5/2)(s1 + s2) (D = 2).
+   The Mip-GES 3D filter does not apply to 2D Gaussians. */
+static int gauss2d_setup(const ora_scene *S, const ora_camera *c, const ora_opts *o,
+                         const double *ocam, int64_t i, gauss_t *g, const double *Rc)
+{
+    g->dim = 2;
+    const double *p = S->g_pos + 3*i, *s = S->g_scale + 2*i;
+    cam_to_camera(c, p, g->t);
+    g->sigma0 = S->g_opac[i];
+    g->sigma = g->sigma0;
+    g->k3 = 1.0; g->k2 = 1.0;
+    surf_t *f = &g->geo;
+    double tu[3] = {g->R[0], g->R[3], g->R[6]}, tv[3] = {g->R[1], g->R[4], g->R[7]};
+    double n[3] = {g->R[2], g->R[5], g->R[8]};
+    memcpy(f->pc, g->t, sizeof g->t);
+    matvec3(Rc, tu, f->tu); matvec3(Rc, tv, f->tv); matvec3(Rc, n, f->n);
+    f->x0 = 1; f->x1 = 0; f->y0 = 1; f->y1 = 0;
+    const double fl = dot3(f->n, f->pc) > 0.0 ? -1.0 : 1.0;   /* face the camera */
+    for (int k = 0; k < 3; ++k) g->nrm[k] = fl * f->n[k];
+    switch (o->eps_mode) {
+    case 0: g->eps = o->eps_factor / 2.0 * (s[0] + s[1]); break;
+    case 1: g->eps = 0.0; break;
+    default: g->eps = o->eps_value; break;
+    }
+    g->d = g->t[2];
+    double v[3] = {ocam[0] - p[0], ocam[1] - p[1], ocam[2] - p[2]};
+    g->dist = sqrt(dot3(v, v));
+    for (int k = 0; k < 3; ++k) g->dir[k] = g->dist > 0 ? v[k] / g->dist : 0.0;
+    sh_colour(S->sh_degree, S->g_sh + (int64_t)3 * (S->sh_degree + 1) * (S->sh_degree + 1) * i,
+              g->dir, g->rgb, g->raw);
+    if (!(g->t[2] > c->znear) || !(s[0] > 0.0 && s[1] > 0.0) || !isfinite(s[0]) || !isfinite(s[1])) return 1;
+    /* J = Jp [s1 t_u, s2 t_v]: local unit coordinates -> pixels, at the centre */
+    const double x = g->t[0], y = g->t[1], z = g->t[2];
+    const double Jp[6] = {c->fx / z, 0.0, -c->fx * x / (z*z), 0.0, c->fy / z, -c->fy * y / (z*z)};
+    double J[4];
+    for (int a = 0; a < 2; ++a) {
+        J[2*a] = s[0] * (Jp[3*a]*f->tu[0] + Jp[3*a + 1]*f->tu[1] + Jp[3*a + 2]*f->tu[2]);
+        J[2*a + 1] = s[1] * (Jp[3*a]*f->tv[0] + Jp[3*a + 1]*f->tv[1] + Jp[3*a + 2]*f->tv[2]);
+    }
+    const double M00 = J[0]*J[0] + J[2]*J[2], M01 = J[0]*J[1] + J[2]*J[3], M11 = J[1]*J[1] + J[3]*J[3];
+    const double det = M00 * M11 - M01 * M01;
+    if (!(det > 0.0) || !isfinite(det)) return 1;
+    g->S1 = sqrt(1.0 + o->lowpass * M11 / det);
+    g->S2 = sqrt(1.0 + o->lowpass * M00 / det);
+    f->s1 = s[0] * g->S1;
+    f->s2 = s[1] * g->S2;
+    f->valid = 1;
+    g->sigma = g->sigma0 / (g->S1 * g->S2);
+    g->valid = 1;
+    /* exact support: alpha >= a  <=>  a'^2 + b'^2 <= 2 ln(sigma/a) in filtered units;
+       widened by the alpha ambiguity band so that culled == brute force exactly */
+    double amin = o->alpha_min - o->tol_alpha;
+    if (!(g->sigma > amin) || amin <= 0.0) return 1;
+    disc_rect(c, f, sqrt(2.0 * log(g->sigma / amin)));
+    g->x0 = f->x0; g->x1 = f->x1; g->y0 = f->y0; g->y1 = f->y1;
+    return 1;
+}
+
 static int gauss_setup(const ora_scene *S, const ora_camera *c, const ora_opts *o,
                        const double *ocam, int64_t i, gauss_t *g)
 {
     double Rc[9];
     memset(g, 0, sizeof *g);
     g->x0 = 1; g->x1 = 0; g->y0 = 1; g->y1 = 0;
+    g->dim = 3;
     if (!quat_rot(S->g_rot + 4*i, g->R, g->qn, &g->qnorm)) return 0;
     cam_rot(c, Rc);
+    if (S->gauss_dim == 2) return gauss2d_setup(S, c, o, ocam, i, g, Rc);
     const double *p = S->g_pos + 3*i, *s = S->g_scale + 3*i;
     cam_to_camera(c, p, g->t);
     g->sigma0 = S->g_opac[i];
@@ -306,6 +389,16 @@ static int gauss_setup(const ora_scene *S, const ora_camera *c, const ora_opts *
     default: g->eps = o->eps_value; break;
     }
     g->d = g->t[2];
+    {
+        /* geometry normal (Sec. 6.4): the axis of the smallest scale, facing the camera */
+        int km = 0;
+        for (int k = 1; k < 3; ++k)
+            if (fabs(s[k]) < fabs(s[km])) km = k;
+        double ax[3] = {g->R[km], g->R[3 + km], g->R[6 + km]};
+        matvec3(Rc, ax, g->nrm);
+        if (dot3(g->nrm, g->t) > 0.0)
+            for (int k = 0; k < 3; ++k) g->nrm[k] = -g->nrm[k];
+    }
     double v[3] = {ocam[0] - p[0], ocam[1] - p[1], ocam[2] - p[2]};
     g->dist = sqrt(dot3(v, v));
     for (int k = 0; k < 3; ++k) g->dir[k] = g->dist > 0 ? v[k] / g->dist : 0.0;
@@ -400,9 +493,23 @@ static int surfel_hit(const surf_t *sf, const double *d, double *z, double *rho,
     return 1;
 }
 
-/* Eq. 4 before the clamp */
-static double gauss_alpha(const gauss_t *g, int i, int j)
+/* Eq. 4 before the clamp at pixel (i, j), and the depth its depth test uses:
+   3D, the centre depth d_i; 2D, the planar depth of the ray-splat hit (no hit
+   in front of the near plane: alpha 0, depth +inf).  *ndot: for 2D, the
+   cosine between the splat normal and the ray (1 for 3D). */
+static double gauss_eval(const ora_camera *c, const gauss_t *g, int i, int j, double *depth, double *ndot)
 {
+    if (g->dim == 2) {
+        double d[3], z, rho, nd;
+        pixel_ray(c, i, j, d);
+        int hit = surfel_hit(&g->geo, d, &z, &rho, &nd);
+        if (ndot) *ndot = nd;
+        if (!hit || !(z > c->znear)) { *depth = INFINITY; return 0.0; }
+        *depth = z;
+        return g->sigma * exp(-0.5 * rho);
+    }
+    if (ndot) *ndot = 1.0;
+    *depth = g->d;
     double dx = (i + 0.5) - g->px, dy = (j + 0.5) - g->py;
     double q = g->ca*dx*dx + 2.0*g->cb*dx*dy + g->cc*dy*dy;
     return g->sigma * exp(-0.5 * q);
@@ -531,13 +638,21 @@ static void zbuffer_sample(const ora_scene *S, const ora_camera *c, const ora_op
    of the samples' colours (bg where a sample hits nothing) and D_s, for the
    Gaussians' depth test, the nearest sample's depth; the Gaussians are
    evaluated at the pixel centre only. */
+/* Geometry of one pixel (Sec. 6.4, Eq. 10-12): the surfel normal N_s (of the
+   nearest sample's surfel, facing the camera; 0 where none), D_G and N_G. */
+typedef struct {
+    double Ns[3], DG, NG[3];
+    int covered;
+} geo_px;
+
 static void shade_pixel(const ora_scene *S, const ora_camera *c, const ora_opts *o, const prep_t *P,
                         int culled, int i, int j, double *C, double *Ds_out, int32_t *id_out,
-                        double *wg_out, uint8_t *amb_out, int32_t *nc_out)
+                        double *wg_out, uint8_t *amb_out, int32_t *nc_out, geo_px *geo)
 {
     const int ns = o->samples == 4 ? 4 : 1;
     uint8_t amb = 0;
     double Ds = INFINITY, Cs[3] = {0, 0, 0};
+    int64_t nearest = -1;
     for (int k = 0; k < ns; ++k) {
         int64_t best = -1;
         double z = INFINITY;
@@ -546,9 +661,19 @@ static void shade_pixel(const ora_scene *S, const ora_camera *c, const ora_opts 
             sample_ray(c, ns, i, j, k, d);
             zbuffer_sample(S, c, o, P, culled, i, j, d, &best, &z, &amb);
         }
+        if (best >= 0 && (z < Ds || (z == Ds && best < nearest))) nearest = best;
         if (best >= 0) Ds = fmin(Ds, z);
         for (int ch = 0; ch < 3; ++ch) Cs[ch] += (best >= 0 ? P->sf[best].rgb[ch] : c->bg[ch]) / ns;
         id_out[k] = (int32_t)best;
+    }
+    if (geo) {
+        memset(geo, 0, sizeof *geo);
+        geo->covered = nearest >= 0;
+        if (nearest >= 0) {
+            const surf_t *sf = &P->sf[nearest];
+            const double fl = dot3(sf->n, sf->pc) > 0.0 ? -1.0 : 1.0;
+            for (int k = 0; k < 3; ++k) geo->Ns[k] = fl * sf->n[k];
+        }
     }
 
     /* pass 2: order-independent accumulation (Eq. 2-4) */
@@ -565,17 +690,24 @@ static void shade_pixel(const ora_scene *S, const ora_camera *c, const ora_opts 
             const gauss_t *g = &P->gs[k];
             if (!g->valid) continue;
             if (culled && (i < g->x0 || i > g->x1 || j < g->y0 || j > g->y1)) continue;
-            double a = gauss_alpha(g, i, j);
-            double lim = g->d - (Ds + g->eps);
-            int pass = g->d < Ds + g->eps;
+            double gd, nd;
+            double a = gauss_eval(c, g, i, j, &gd, &nd);
+            double lim = gd - (Ds + g->eps);
+            int pass = gd < Ds + g->eps;
             if (fabs(a - o->alpha_min) <= o->tol_alpha && (pass || fabs(lim) <= o->tol_gdepth_rel * fmax(1.0, Ds)))
                 amb |= AMB_COLOR;
             if (a >= o->alpha_min - o->tol_alpha && isfinite(Ds) &&
                 fabs(lim) <= o->tol_gdepth_rel * fmax(1.0, Ds))
                 amb |= AMB_COLOR;
+            /* a splat seen edge-on: its hit and planar depth are ill-conditioned */
+            if (g->dim == 2 && a >= o->alpha_min - o->tol_alpha && fabs(nd) < o->tol_graze) amb |= AMB_COLOR;
             if (!(a >= o->alpha_min) || !pass) continue;
             for (int ch = 0; ch < 3; ++ch) CG[ch] += a * g->rgb[ch];
             WG += a;
+            if (geo) {
+                geo->DG += a * gd;
+                for (int ch = 0; ch < 3; ++ch) geo->NG[ch] += a * g->nrm[ch];
+            }
             ++nc;
         }
     }
@@ -600,6 +732,7 @@ static int check_args(const ora_scene *S, const ora_camera *c, const ora_opts *o
     if (!(c->fx > 0 && c->fy > 0 && c->znear > 0)) return 0;
     if (o->samples != 1 && o->samples != 4) return 0;
     if (o->filter != 0 && o->filter != 1) return 0;
+    if (S->gauss_dim != 0 && S->gauss_dim != 2 && S->gauss_dim != 3) return 0;
     return 1;
 }
 
@@ -622,13 +755,56 @@ int ora_render(const ora_scene *S, const ora_camera *c, const ora_opts *o, int c
             double C[3], Ds, WG;
             int32_t id[4], nc;
             uint8_t a;
-            shade_pixel(S, c, o, &P, culled, i, j, C, &Ds, id, &WG, &a, &nc);
+            shade_pixel(S, c, o, &P, culled, i, j, C, &Ds, id, &WG, &a, &nc, NULL);
             for (int ch = 0; ch < 3; ++ch) rgb[ch * HW + pix] = C[ch];
             depth[pix] = Ds;
             for (int k = 0; k < (o->samples == 4 ? 4 : 1); ++k) sid[k * HW + pix] = id[k];
             wg[pix] = WG;
             amb[pix] = a;
             if (ncontrib) ncontrib[pix] = nc;
+        }
+    }
+    prep_free(&P);
+    return ORA_OK;
+}
+
+/* Geometry maps (Sec. 6.4, Eq. 10-12), camera space: N_s [3,H,W], D_G [H,W],
+   N_G [3,H,W] and the smoothed maps D_smooth = (W_s D_s + D_G)/(W_s + W_G),
+   N_smooth = (W_s N_s + N_G)/(W_s + W_G) with W_s = 1 where a surfel covers
+   the pixel and 0 elsewhere (no surfel depth exists there); where both
+   weights are 0, D_smooth = +inf and N_smooth = 0.  d_i, n_i: centre depth and
+   smallest-scale axis for 3D Gaussians, planar depth and splat normal for 2D
+   ones; normals face the camera.  Also writes amb like ora_render. */
+int ora_render_geom(const ora_scene *S, const ora_camera *c, const ora_opts *o, int culled, int nthreads,
+                    double *ns_out, double *dg_out, double *ng_out, double *dsm_out, double *nsm_out, uint8_t *amb)
+{
+    if (!check_args(S, c, o)) return ORA_BAD_ARG;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    prep_t P;
+    int st = prepare(S, c, o, culled, &P);
+    if (st != ORA_OK) { prep_free(&P); return st; }
+    const int W = c->width, H = c->height;
+    const int64_t HW = (int64_t)W * H;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int j = 0; j < H; ++j) {
+        for (int i = 0; i < W; ++i) {
+            int64_t pix = (int64_t)j * W + i;
+            double C[3], Ds, WG;
+            int32_t id[4], nc;
+            uint8_t a;
+            geo_px g;
+            shade_pixel(S, c, o, &P, culled, i, j, C, &Ds, id, &WG, &a, &nc, &g);
+            const double ws = g.covered ? 1.0 : 0.0, wt = ws + WG;
+            dg_out[pix] = g.DG;
+            dsm_out[pix] = wt > 0.0 ? ((g.covered ? Ds : 0.0) + g.DG) / wt : INFINITY;
+            for (int ch = 0; ch < 3; ++ch) {
+                ns_out[ch * HW + pix] = g.Ns[ch];
+                ng_out[ch * HW + pix] = g.NG[ch];
+                nsm_out[ch * HW + pix] = wt > 0.0 ? (ws * g.Ns[ch] + g.NG[ch]) / wt : 0.0;
+            }
+            amb[pix] = a;
         }
     }
     prep_free(&P);
@@ -666,7 +842,8 @@ int ora_count_fragments(const ora_scene *S, const ora_camera *c, const ora_opts 
                 for (int64_t t = P.rg.off[cell]; t < P.rg.off[cell + 1]; ++t) {
                     const gauss_t *g = &P.gs[P.rg.idx[t]];
                     if (!g->valid || i < g->x0 || i > g->x1 || j < g->y0 || j > g->y1) continue;
-                    if (gauss_alpha(g, i, j) >= o->alpha_min) ++ng;
+                    double gd;
+                    if (gauss_eval(c, g, i, j, &gd, NULL) >= o->alpha_min) ++ng;
                 }
         }
     }
@@ -791,11 +968,13 @@ int ora_touching(const ora_scene *S, const ora_camera *c, const ora_opts *o, con
         g_touch[k] = 0;
         if (!g->valid) continue;
         for (int j = g->y0; j <= g->y1 && !g_touch[k]; ++j)
-            for (int i = g->x0; i <= g->x1; ++i)
-                if (flag[(int64_t)j * W + i] && gauss_alpha(g, i, j) >= o->alpha_min - o->tol_alpha) {
+            for (int i = g->x0; i <= g->x1; ++i) {
+                double gd;
+                if (flag[(int64_t)j * W + i] && gauss_eval(c, g, i, j, &gd, NULL) >= o->alpha_min - o->tol_alpha) {
                     g_touch[k] = 1;
                     break;
                 }
+            }
     }
     prep_free(&P);
     return ORA_OK;
@@ -804,7 +983,9 @@ int ora_touching(const ora_scene *S, const ora_camera *c, const ora_opts *o, con
 /* Per-primitive quantities for unit pins.
    surfel: out = [valid, rgb(3), pc(3), n(3), x0, x1, y0, y1]                 (14)
    gauss:  out = [valid, px, py, ca, cb, cc, S2a, S2b, S2c, sigma, d, eps,
-                  rgb(3), x0, x1, y0, y1]                                      (19) */
+                  rgb(3), x0, x1, y0, y1, nrm(3), S1, S2, s1', s2']           (26)
+           (2D Gaussians: px..S2c are 0; S1, S2 the object-space filter
+            factors, s1', s2' the filtered scales) */
 int ora_surfel_info(const ora_scene *S, const ora_camera *c, const ora_opts *o, int64_t i, double *out)
 {
     if (!check_args(S, c, o) || i < 0 || i >= S->n_surfels) return ORA_BAD_ARG;
@@ -826,7 +1007,8 @@ int ora_gauss_info(const ora_scene *S, const ora_camera *c, const ora_opts *o, i
     gauss_t g;
     if (!gauss_setup(S, c, o, ocam, i, &g)) return ORA_BAD_QUAT;
     double v[] = {g.valid, g.px, g.py, g.ca, g.cb, g.cc, g.S2a, g.S2b, g.S2c, g.sigma, g.d, g.eps,
-                  g.rgb[0], g.rgb[1], g.rgb[2], g.x0, g.x1, g.y0, g.y1};
+                  g.rgb[0], g.rgb[1], g.rgb[2], g.x0, g.x1, g.y0, g.y1,
+                  g.nrm[0], g.nrm[1], g.nrm[2], g.S1, g.S2, g.geo.s1, g.geo.s2};
     memcpy(out, v, sizeof v);
     return ORA_OK;
 }
@@ -864,7 +1046,7 @@ int ora_backward(const ora_scene *S, const ora_camera *c, const ora_opts *o, int
                  double *gg_pos, double *gg_rot, double *gg_scale, double *gg_opac, double *gg_sh,
                  double *gs_sh)
 {
-    if (!check_args(S, c, o)) return ORA_BAD_ARG;
+    if (!check_args(S, c, o) || S->gauss_dim == 2) return ORA_BAD_ARG;   /* 3D Gaussians only */
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #endif

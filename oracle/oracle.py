@@ -33,7 +33,8 @@ DEFAULT_OPTS = dict(eps_mode=0, eps_value=0.1, eps_factor=5.0, lowpass=0.3,
 class _Scene(C.Structure):
     _fields_ = [("n_surfels", C.c_int64), ("n_gaussians", C.c_int64), ("sh_degree", C.c_int32)] + \
                [(n, C.c_void_p) for n in ("s_pos", "s_rot", "s_scale", "s_sh",
-                                          "g_pos", "g_rot", "g_scale", "g_opac", "g_sh", "g_filt3")]
+                                          "g_pos", "g_rot", "g_scale", "g_opac", "g_sh", "g_filt3")] + \
+               [("gauss_dim", C.c_int32)]
 
 
 class _Camera(C.Structure):
@@ -79,6 +80,7 @@ def load():
         lib.ora_check_ids.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_void_p, C.c_void_p]
         lib.ora_count_fragments.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_void_p, C.c_void_p]
         lib.ora_filter3d.argtypes = [P(_Scene), C.c_void_p, C.c_int, C.c_double, C.c_void_p]
+        lib.ora_render_geom.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_int, C.c_int] + [C.c_void_p] * 6
         _lib = lib
     return _lib
 
@@ -99,7 +101,9 @@ class _Pinned:
         self.s = _Scene(scene.n_surfels, scene.n_gaussians, scene.sh_degree,
                         *[self.arrs[k].ctypes.data for k in ("s_pos", "s_rot", "s_scale", "s_sh",
                                                               "g_pos", "g_rot", "g_scale", "g_opac", "g_sh")],
-                        self.arrs["g_filt3"].ctypes.data if f3 is not None else None)
+                        self.arrs["g_filt3"].ctypes.data if f3 is not None else None,
+                        int(np.asarray(scene.g_scale).reshape(scene.n_gaussians, -1).shape[1])
+                        if scene.n_gaussians else 3)
         w2c = np.asarray(cam.world_to_cam, np.float64).reshape(12)
         self.c = _Camera(cam.width, cam.height, float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy),
                          (C.c_double * 12)(*w2c), float(cam.znear), (C.c_double * 3)(*map(float, cam.bg)))
@@ -130,6 +134,21 @@ def render(scene, cam, opts=None, culled: bool = True, nthreads: int = 0):
     st = lib.ora_render(C.byref(pin.s), C.byref(pin.c), C.byref(pin.o), int(culled), int(nthreads),
                         *[out[k].ctypes.data for k in ("rgb", "depth", "id", "wg", "amb", "ncontrib")])
     _check(st, "render")
+    return out
+
+
+def render_geom(scene, cam, opts=None, culled: bool = True, nthreads: int = 0):
+    """FP64 geometry maps (Sec. 6.4, Eq. 10-12), camera space: ns [3,H,W]
+    (surfel normal), dg [H,W] (D_G), ng [3,H,W] (N_G), dsmooth [H,W],
+    nsmooth [3,H,W], amb [H,W]."""
+    lib = load()
+    pin = _Pinned(scene, cam, opts)
+    H, W = cam.height, cam.width
+    out = dict(ns=np.empty((3, H, W)), dg=np.empty((H, W)), ng=np.empty((3, H, W)),
+               dsmooth=np.empty((H, W)), nsmooth=np.empty((3, H, W)), amb=np.empty((H, W), np.uint8))
+    st = lib.ora_render_geom(C.byref(pin.s), C.byref(pin.c), C.byref(pin.o), int(culled), int(nthreads),
+                             *[out[k].ctypes.data for k in ("ns", "dg", "ng", "dsmooth", "nsmooth", "amb")])
+    _check(st, "render_geom")
     return out
 
 
@@ -188,11 +207,12 @@ def surfel_info(scene, cam, i, opts=None):
 def gauss_info(scene, cam, i, opts=None):
     lib = load()
     pin = _Pinned(scene, cam, opts)
-    out = np.empty(19)
+    out = np.empty(26)
     _check(lib.ora_gauss_info(C.byref(pin.s), C.byref(pin.c), C.byref(pin.o), int(i), out.ctypes.data),
            "gauss_info")
     return dict(valid=bool(out[0]), px=out[1], py=out[2], conic=out[3:6], sigma2=out[6:9],
-                sigma=out[9], d=out[10], eps=out[11], rgb=out[12:15], bbox=out[15:19].astype(int))
+                sigma=out[9], d=out[10], eps=out[11], rgb=out[12:15], bbox=out[15:19].astype(int),
+                nrm=out[19:22], S=out[22:24], scale_filtered=out[24:26])
 
 
 def id_validity(scene, cam, ref, ids, opts=None):
