@@ -379,6 +379,35 @@ def paper_shaped_extra(R, N, sg):
     return res
 
 
+def geometry_2dges_extra(R, N, sg, scene, cams):
+    """2D-GES (Sec. 6.4): the headline orbit with the 3D Gaussians replaced by
+    2D ones (their first two axes) as one batch graph; and the geometry maps
+    (Eq. 10-12) of one 1080p view against the plain render, both kinds."""
+    import numpy as np
+    flat = scene.subset()
+    flat.g_scale = np.ascontiguousarray(flat.g_scale[:, :2])
+    g2 = R.GESScene.from_arrays(flat)
+    b = R.GESBatch([g2], cams)
+    ms = _time(lambda: (b.launch(), b.sync()), 5)
+    b.profile(reset=True)
+    _time(lambda: (b.launch(), b.sync()), 5, warm=0)
+    prof = b.profile()
+    b.close()
+    frags = [N.ges_count_fragments(g2.handle, R.camera_struct(cams[k]), R.opts_struct(None))
+             for k in range(0, len(cams), 16)]
+    res = {"workload": f"orbit-{len(cams)}-views-1080p-1M-surfels-300k-2d-gaussians",
+           "frames_per_s_2d": len(cams) / (ms / 1e3),
+           "kernel_ms_per_frame_2d": {k: prof[k][0] / prof[k][1] / len(cams) for k in prof},
+           "gauss_terms_per_frame_2d": float(np.mean([f[1] for f in frags]))}
+    g3 = R.GESScene.from_arrays(scene)
+    for name, g in (("3d", g3), ("2d", g2)):
+        res[f"view_ms_render_{name}"] = _time(lambda: R.render(g, cams[0], with_aux=False), 10)
+        res[f"view_ms_render_geom_{name}"] = _time(lambda: R.render_geom(g, cams[0]), 10)
+    g2.close()
+    g3.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -496,6 +525,7 @@ def main():
         extras["msaa_4x"] = msaa_extra(R, N, gs, cams)
         extras["mip_ges"] = mip_extra(R, N, gs, cams)
         extras["paper_shaped"] = paper_shaped_extra(R, N, sg)
+        extras["geometry_2dges"] = geometry_2dges_extra(R, N, sg, scene, cams)
     if rank != 0:
         return
     # roofline of the dominant kernel (largest share of device time); one

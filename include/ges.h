@@ -95,6 +95,14 @@ typedef struct ges_scene ges_scene;   /* opaque */
  * rotations, scales and opacities use attr_dtype, SH coefficients sh_dtype.
  *   s_pos [N,3]  s_rot [N,4] (w,x,y,z)  s_scale [N,2]  s_sh [N,K,3]
  *   g_pos [M,3]  g_rot [M,4] (w,x,y,z)  g_scale [M,3]  g_opac [M]  g_sh [M,K,3]
+ *   gauss_dim: 3 (or 0) for 3D Gaussians; 2 for the 2D Gaussians of 2D-GES
+ *     (Sec. 6.4): g_scale is then [M,2], each Gaussian a planar splat in the
+ *     plane of its rotation's first two axes, evaluated at the ray-splat hit
+ *     with its planar depth and the object-space EWA filter of Eq. 17-18 (size
+ *     lowpass: scales s_k S_k, opacity sigma/(S1 S2), S_k from the diagonal of
+ *     I + lowpass J^-1 J^-T); eps_i = eps_factor/2 (s1 + s2).  The 3D filter
+ *     and GES_FILTER_MIP do not apply to them; the backward pass and
+ *     ges_render_noalloc return GES_ERR_UNSUPPORTED for them.
  *   g_filter3d [M] float32 or NULL: Mip-GES 3D filter variance per Gaussian
  *     (Sec. 6.1, Mip-Splatting's world-space filter; see ges_compute_filter3d).
  *     Rendering uses Sigma3 + v I = R diag(s^2 + v) R^T and scales the opacity
@@ -111,6 +119,7 @@ typedef struct {
     const float *g_pos;
     const void *g_rot, *g_scale, *g_opac, *g_sh;
     const float *g_filter3d;
+    int32_t gauss_dim;            /* 3 (0 reads as 3) or 2 */
 } ges_scene_desc;
 
 /* Pinhole camera; width, height in [1, 16384]; fx, fy > 0; znear > 0. */
@@ -212,6 +221,21 @@ GES_API ges_status ges_render(ges_scene *scene, const ges_camera *cam, float *ou
  * (defaults); samples other than 1 or 4 is GES_ERR_INVALID_ARG. */
 GES_API ges_status ges_render_ex(ges_scene *scene, const ges_camera *cam, const ges_render_opts *opts,
                          float *out_rgb, float *out_depth, int32_t *out_surfel_id, float *aux);
+
+/* The render of ges_render_ex plus the geometry maps of Sec. 6.4 (Eq. 10-12),
+ * camera space: out_normal_s [3,H,W] the surfel normal N_s (of the nearest
+ * covered sample's surfel, facing the camera; 0 where no surfel covers),
+ * out_depth_smooth [H,W] D_smooth = (W_s D_s + D_G)/(W_s + W_G) and
+ * out_normal_smooth [3,H,W] N_smooth = (W_s N_s + N_G)/(W_s + W_G), with
+ * D_G = sum alpha_i d_i and N_G = sum alpha_i n_i over the depth-tested
+ * Gaussians, and W_s = 1 where a surfel covers the pixel, 0 elsewhere (where
+ * both weights are 0: D_smooth = +inf, N_smooth = 0); out_dg [H,W] and out_ng
+ * [3,H,W] are D_G and N_G.  d_i, n_i: centre depth and smallest-scale axis for
+ * 3D Gaussians, planar depth and splat normal for 2D ones; normals face the
+ * camera and are not renormalised.  Every output but out_rgb may be NULL. */
+GES_API ges_status ges_render_geom(ges_scene *scene, const ges_camera *cam, const ges_render_opts *opts,
+                                   float *out_rgb, float *out_depth, float *out_normal_s, float *out_depth_smooth,
+                                   float *out_normal_smooth, float *out_dg, float *out_ng);
 
 /* Gradients of L = sum(dL_drgb * C) for the joint stage (Sec. 4.2): Gaussian
  * position, rotation (through the normalisation), scale, opacity and SH, and

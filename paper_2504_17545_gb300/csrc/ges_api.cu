@@ -80,6 +80,7 @@ struct ges_scene {
     DevBuf hist, base, vcount;     // local binning
     DevBuf status;                 // ST_WORDS per view slot
     DevBuf filt;                   // ges_compute_filter3d: cameras + one scratch word
+    DevBuf g_aux;                  // Gaussian side data (2D Gaussians, geometry maps)
     unsigned *status_host = nullptr;
     int status_slots = 0;
     int64_t tiles_cap = 0;
@@ -107,6 +108,8 @@ ges_status check_desc(const ges_scene_desc *d)
         return fail(GES_ERR_INVALID_ARG, "surfel attribute pointer is NULL");
     if (d->n_gaussians > 0 && (!d->g_pos || !d->g_rot || !d->g_scale || !d->g_opac || !d->g_sh))
         return fail(GES_ERR_INVALID_ARG, "Gaussian attribute pointer is NULL");
+    if (d->gauss_dim != 0 && d->gauss_dim != 2 && d->gauss_dim != 3)
+        return fail(GES_ERR_INVALID_ARG, "gauss_dim %d is not 2 or 3", d->gauss_dim);
     return GES_OK;
 }
 
@@ -126,7 +129,7 @@ void set_view(ges_scene *s)
     const ges_scene_desc &d = s->desc;
     s->view = SceneView{d.n_surfels, d.n_gaussians, d.sh_degree, d.attr_dtype, d.sh_dtype,
                         d.s_pos, d.s_rot, d.s_scale, d.s_sh, d.g_pos, d.g_rot, d.g_scale, d.g_opac, d.g_sh,
-                        d.g_filter3d};
+                        d.g_filter3d, d.gauss_dim == 2 ? 2 : 3};
 }
 
 bool finite_all(const float *v, int n)
@@ -190,6 +193,7 @@ ges_status make_opts(const ges_render_opts *o, OptParams &O)
     O.surfel_r = std::sqrt(o->surfel_r2);
     O.mode = o->mode;
     O.samples = o->samples;
+    O.geo = 0;
     O.filter = o->filter;
     return GES_OK;
 }
@@ -251,6 +255,7 @@ ViewScratch scratch_of(ges_scene *s, int slot)
     X.hist = (unsigned *)s->hist.p;
     X.base = (unsigned *)s->base.p;
     X.vcount = (unsigned *)s->vcount.p;
+    X.g_aux = (float4 *)s->g_aux.p;
     return X;
 }
 
@@ -292,7 +297,7 @@ void prof_collect(ges_scene *s, int first_ev, const char *const *names, int n)
 // slot; on list overflow grow the lists and repeat.
 ges_status render_views(ges_scene *const *scenes, const CamParams *cams, const int32_t *scene_of_view, int n,
                         const OptParams &O, float *const *rgb, float *const *depth, int32_t *const *ids,
-                        float *const *auxs)
+                        float *const *auxs, const float *const *geo_maps = nullptr)
 {
     ges_scene *s0 = scenes[scene_of_view[0]];
     cudaStream_t st = s0->stream;
@@ -302,6 +307,11 @@ ges_status render_views(ges_scene *const *scenes, const CamParams *cams, const i
             ges_scene *s = scenes[scene_of_view[v]];
             ges_status r = ensure_scratch(s, (int64_t)cams[v].tiles_x * cams[v].tiles_y, s == s0 ? n : 1, st);
             if (r != GES_OK) return r;
+            // side data: 2D Gaussians always, 3D ones for the geometry maps
+            if (s->view.gdim == 2 || O.geo) {
+                cudaError_t e = s->g_aux.ensure((size_t)std::max<int64_t>(s->desc.n_gaussians, 1) * 32);
+                if (e != cudaSuccess) return cuda_fail(e, "scratch allocation (Gaussian side data)");
+            }
         }
         if (s0->status_slots < n) {
             ges_status r = ensure_scratch(s0, 1, n, st);
@@ -319,7 +329,7 @@ ges_status render_views(ges_scene *const *scenes, const CamParams *cams, const i
             X.status = (unsigned *)s0->status.p + (size_t)v * ST_WORDS;
             cudaError_t e = launch_forward(s->view, cams[v], O, X, rgb[v], depth ? depth[v] : nullptr,
                                            ids ? ids[v] : nullptr, auxs ? auxs[v] : nullptr, st,
-                                           prof ? s0->ev.data() + 8 + 5 * v : nullptr);
+                                           prof ? s0->ev.data() + 8 + 5 * v : nullptr, geo_maps);
             if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
         }
         GES_CUDA(cudaMemcpyAsync(s0->status_host, s0->status.p, (size_t)n * ST_WORDS * 4, cudaMemcpyDeviceToHost, st));
@@ -405,7 +415,7 @@ ges_status ges_destroy_scene(ges_scene *s)
     cudaStreamSynchronize(s->stream);
     DevBuf *bufs[] = {&s->s_rec, &s->s_rgb, &s->g_rec, &s->s_vis, &s->g_vis, &s->s_cnt, &s->g_cnt, &s->s_off,
                       &s->g_off, &s->s_cur, &s->g_cur, &s->s_list, &s->g_list, &s->hist, &s->base,
-                      &s->vcount, &s->status, &s->filt};
+                      &s->vcount, &s->status, &s->filt, &s->g_aux};
     for (DevBuf *b : bufs) b->release();
     if (s->status_host) cudaFreeHost(s->status_host);
     for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
@@ -438,6 +448,25 @@ ges_status ges_render_ex(ges_scene *s, const ges_camera *cam, const ges_render_o
     return render_views(&s, &C, &zero, 1, O, rgb, dep, ids, aux1);
 }
 
+ges_status ges_render_geom(ges_scene *s, const ges_camera *cam, const ges_render_opts *opts, float *out_rgb,
+                           float *out_depth, float *out_normal_s, float *out_depth_smooth, float *out_normal_smooth,
+                           float *out_dg, float *out_ng)
+{
+    if (!s) return fail(GES_ERR_INVALID_ARG, "scene is NULL");
+    if (!out_rgb) return fail(GES_ERR_INVALID_ARG, "out_rgb is NULL");
+    CamParams C;
+    OptParams O;
+    ges_status r = make_cam(cam, C);
+    if (r != GES_OK) return r;
+    if ((r = make_opts(opts, O)) != GES_OK) return r;
+    O.geo = 1;
+    const int32_t zero = 0;
+    float *rgb[1] = {out_rgb};
+    float *dep[1] = {out_depth};
+    const float *maps[5] = {out_normal_s, out_depth_smooth, out_normal_smooth, out_dg, out_ng};
+    return render_views(&s, &C, &zero, 1, O, rgb, dep, nullptr, nullptr, maps);
+}
+
 ges_status ges_render(ges_scene *s, const ges_camera *cam, float *out_rgb, float *out_depth)
 {
     return ges_render_ex(s, cam, nullptr, out_rgb, out_depth, nullptr, nullptr);
@@ -451,6 +480,7 @@ ges_status ges_render_backward(ges_scene *s, const ges_camera *cam, const ges_re
     if (!grads) return fail(GES_ERR_INVALID_ARG, "grads is NULL");
     if (!dL_drgb || !out_rgb || !out_depth || !surfel_id || !aux)
         return fail(GES_ERR_INVALID_ARG, "backward needs dL_drgb, out_rgb, out_depth, surfel_id and aux");
+    if (s->view.gdim == 2) return fail(GES_ERR_UNSUPPORTED, "the backward pass covers 3D Gaussians only");
     CamParams C;
     OptParams O;
     ges_status r = make_cam(cam, C);
@@ -499,6 +529,7 @@ ges_status ges_count_fragments(ges_scene *s, const ges_camera *cam, const ges_re
     if ((r = make_opts(opts, O)) != GES_OK) return r;
     for (int attempt = 0; attempt < 4; ++attempt) {
         if ((r = ensure_scratch(s, (int64_t)C.tiles_x * C.tiles_y, 1, s->stream)) != GES_OK) return r;
+        if (s->view.gdim == 2) GES_CUDA(s->g_aux.ensure((size_t)std::max<int64_t>(s->desc.n_gaussians, 1) * 32));
         ViewScratch X = scratch_of(s, 0);
         GES_CUDA(cudaMemsetAsync(X.status, 0, ST_WORDS * 4, s->stream));
         cudaError_t e = launch_count(s->view, C, O, X, s->stream);
@@ -653,6 +684,7 @@ size_t batch_layout(ges_batch *b, const std::vector<SceneView> &S, const std::ve
         X.hist = (unsigned *)take((size_t)P * ((T + 1) / 2) * 4);
         X.base = (unsigned *)take((size_t)P * T * 4);
         X.vcount = (unsigned *)take((size_t)P * 4);
+        X.g_aux = S[v].gdim == 2 ? (float4 *)take(M * 32) : nullptr;
         X.status = b->d_status + (size_t)v * ST_WORDS;
     }
     return off;
@@ -686,6 +718,8 @@ ges_status ges_batch_create(ges_scene *const *scenes, const ges_camera *cams, co
         S[v] = scenes[scene_of_view[v]]->view;
         if (O.mode == GES_MODE_GAUSSIANS_ONLY) S[v].N = 0;
         if (O.mode == GES_MODE_SURFELS_ONLY) S[v].M = 0;
+        if (S[v].gdim != S[0].gdim)
+            return fail(GES_ERR_UNSUPPORTED, "a batch renders scenes of one Gaussian kind (view %d differs)", v);
     }
     ges_batch *b = new (std::nothrow) ges_batch();
     if (!b) return fail(GES_ERR_OOM, "host allocation failed");
@@ -740,7 +774,7 @@ ges_status ges_batch_create(ges_scene *const *scenes, const ges_camera *cams, co
         // resident raster CTAs per SM: the 4-sample kernel is built for one fewer
         for (int per_sm : {O.samples == 4 ? 3 : 4, O.samples == 4 ? 4 : 5}) {
             batch_layout(b, S, C, R, (unsigned char *)b->arena);
-            BatchPlan P{n_views, 0, 0, 0, 0, sms * per_sm};
+            BatchPlan P{n_views, 0, 0, 0, 0, sms * per_sm, S[0].gdim};
             for (int v = 0; v < n_views; ++v) {
                 P.total_tiles += b->views[v].T;
                 P.total_prep += b->views[v].B.Ps + b->views[v].B.Pg;
@@ -956,6 +990,9 @@ extern "C" GES_API ges_status ges_render_noalloc(const ges_scene_desc *desc, con
     OptParams O;
     if ((r = make_cam(cam, C)) != GES_OK) return r;
     if ((r = make_opts(opts, O)) != GES_OK) return r;
+    if (desc->gauss_dim == 2)
+        return fail(GES_ERR_UNSUPPORTED, "ges_render_noalloc renders 3D Gaussians only (its fixed array has no room "
+                                         "for the side data of 2D Gaussians)");
     if (desc->n_surfels > kNaMaxSurfels || desc->n_gaussians > kNaMaxGaussians)
         return fail(GES_ERR_CAPACITY, "ges_render_noalloc: at most %lld surfels and %lld Gaussians (got %lld, %lld)",
                     (long long)kNaMaxSurfels, (long long)kNaMaxGaussians, (long long)desc->n_surfels,

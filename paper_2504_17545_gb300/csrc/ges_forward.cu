@@ -70,14 +70,41 @@ namespace {
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
-__device__ __forceinline__ void store_rec(float4 *dst, const void *rec)
+// A 64-byte record as four float4 stores, built from its fields (no
+// reinterpretation of the local copy).
+__device__ __forceinline__ void store_rec(float4 *dst, const SurfelRec &r)
 {
-    const float4 *src = reinterpret_cast<const float4 *>(rec);
-    dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2]; dst[3] = src[3];
+    dst[0] = make_float4(r.ur, r.vr, r.iz0, r.gu);
+    dst[1] = make_float4(r.gv, r.au, r.av, r.a0);
+    dst[2] = make_float4(r.bu, r.bv, r.b0, r.izmax);
+    dst[3] = make_float4(__int_as_float(r.id), __uint_as_float(r.bb_lo), __uint_as_float(r.bb_hi), r.pad);
+}
+
+// The first three quarters of a staged Gaussian record (what alpha, the depth
+// key and the colour need).
+__device__ __forceinline__ GaussRec gauss_rec3(float4 a, float4 b, float4 c)
+{
+    GaussRec g;
+    g.px = a.x; g.py = a.y; g.pxl = a.z; g.pyl = a.w;
+    g.la = b.x; g.lb = b.y; g.lc = b.z; g.sigma = b.w;
+    g.key = c.x; g.r = c.y; g.g = c.z; g.b = c.w;
+    g.id = 0; g.bb_lo = 0u; g.bb_hi = 0u; g.pad = 0.f;
+    return g;
+}
+
+__device__ __forceinline__ void store_rec(float4 *dst, const GaussRec &r)
+{
+    dst[0] = make_float4(r.px, r.py, r.pxl, r.pyl);
+    dst[1] = make_float4(r.la, r.lb, r.lc, r.sigma);
+    dst[2] = make_float4(r.key, r.r, r.g, r.b);
+    dst[3] = make_float4(__int_as_float(r.id), __uint_as_float(r.bb_lo), __uint_as_float(r.bb_hi), r.pad);
 }
 
 // Set up primitive i of the given kind; on success write its record and
 // return its pixel bbox.
+// kGd: the scene's Gaussian kind (a template argument, so that each kernel
+// carries only its own set-up code)
+template <int kGd>
 __device__ __forceinline__ bool setup_and_store(const SceneView &S, const CamParams &C, const OptParams &O,
                                                 const ViewScratch &X, bool surf, int64_t i, int &x0, int &y0,
                                                 int &x1, int &y1)
@@ -87,15 +114,21 @@ __device__ __forceinline__ bool setup_and_store(const SceneView &S, const CamPar
         surfel_setup(S, C, O, i, o);
         if (!o.valid_quat) atomicOr(X.status + ST_FLAGS, FLAG_BADQ);
         if (!o.visible) return false;
-        store_rec(X.s_rec + 4 * i, &o.rec);
+        store_rec(X.s_rec + 4 * i, o.rec);
         X.s_rgb[i] = make_float4(o.rgb[0], o.rgb[1], o.rgb[2], 0.f);
         x0 = o.x0; y0 = o.y0; x1 = o.x1; y1 = o.y1;
     } else {
         GaussOut o;
-        gauss_setup(S, C, O, i, o);
+        if (kGd == 2) gauss2d_setup(S, C, O, i, o);
+        else gauss_setup(S, C, O, i, o);
         if (!o.valid_quat) atomicOr(X.status + ST_FLAGS, FLAG_BADQ);
         if (!o.visible) return false;
-        store_rec(X.g_rec + 4 * i, &o.rec);
+        if (kGd == 2) store_rec(X.g_rec + 4 * i, o.drec);
+        else store_rec(X.g_rec + 4 * i, o.rec);
+        if (kGd == 2 || O.geo) {
+            X.g_aux[2 * i] = o.aux[0];
+            X.g_aux[2 * i + 1] = o.aux[1];
+        }
         x0 = o.x0; y0 = o.y0; x1 = o.x1; y1 = o.y1;
     }
     return true;
@@ -106,6 +139,7 @@ __device__ __forceinline__ bool setup_and_store(const SceneView &S, const CamPar
 
 // CTA c of a view: its range of primitives.  hist: ceil(T/2) shared words
 // (two 16-bit counters each); vcnt: a shared counter.
+template <int kGd>
 __device__ __forceinline__ void prep_local_body(const SceneView &S, const CamParams &C, const OptParams &O,
                                                 const ViewScratch &X, const LocalBins &B, int c, unsigned *hist,
                                                 unsigned &vcnt)
@@ -122,7 +156,7 @@ __device__ __forceinline__ void prep_local_body(const SceneView &S, const CamPar
     for (int64_t i0 = beg; i0 < end; i0 += kPrepThreads) {
         const int64_t i = i0 + threadIdx.x;
         int x0 = 0, y0 = 0, x1 = -1, y1 = -1;
-        const bool vis = i < end && setup_and_store(S, C, O, X, surf, i, x0, y0, x1, y1);
+        const bool vis = i < end && setup_and_store<kGd>(S, C, O, X, surf, i, x0, y0, x1, y1);
         const unsigned m = __ballot_sync(0xffffffffu, vis);
         if (m) {
             const int leader = __ffs(m) - 1;
@@ -149,12 +183,13 @@ __device__ __forceinline__ void prep_local_body(const SceneView &S, const CamPar
     }
 }
 
+template <int kGd>
 __global__ void __launch_bounds__(kPrepThreads, 2) k_prep_local(SceneView S, CamParams C, OptParams O,
                                                                 ViewScratch X, LocalBins B)
 {
     extern __shared__ unsigned hist[];
     __shared__ unsigned vcnt;
-    prep_local_body(S, C, O, X, B, blockIdx.x, hist, vcnt);
+    prep_local_body<kGd>(S, C, O, X, B, blockIdx.x, hist, vcnt);
 }
 
 __device__ __forceinline__ unsigned hist_get(const unsigned *row, int t)
@@ -245,13 +280,14 @@ __device__ __forceinline__ void append_visible(bool vis, int64_t i, unsigned *co
     if (vis) list[base + __popc(m & ((1u << lane) - 1u))] = (int)i;
 }
 
+template <int kGd>
 __global__ void __launch_bounds__(256) k_prep_atomic(SceneView S, CamParams C, OptParams O, ViewScratch X,
                                                      int n_sblocks)
 {
     const bool surf = (int)blockIdx.x < n_sblocks;
     const int64_t i = (int64_t)(surf ? blockIdx.x : blockIdx.x - n_sblocks) * 256 + threadIdx.x;
     int x0 = 0, y0 = 0, x1 = -1, y1 = -1;
-    const bool vis = i < (surf ? S.N : S.M) && setup_and_store(S, C, O, X, surf, i, x0, y0, x1, y1);
+    const bool vis = i < (surf ? S.N : S.M) && setup_and_store<kGd>(S, C, O, X, surf, i, x0, y0, x1, y1);
     if (vis) {
         int *cnt = surf ? X.s_cnt : X.g_cnt;
         for (int ty = y0 / kTile; ty <= y1 / kTile; ++ty)
@@ -348,15 +384,52 @@ __device__ __forceinline__ void stage_rec(float4 (*st)[kChunk], const float4 *re
     st[0][slot] = r0; st[1][slot] = r1; st[2][slot] = r2; st[3][slot] = r3;
 }
 
+// shared planes of one staged Gaussian: the record, plus its side data
+// (both words for 2D Gaussians, the first for 3D ones with geometry)
+template <int kG, bool kGeo>
+__host__ __device__ constexpr int gauss_planes() { return kG == 2 ? 6 : (kGeo ? 5 : 4); }
+
+template <int kG, bool kGeo>
+__device__ __forceinline__ void stage_gauss(float4 (*st)[kChunk], const ViewScratch &X, int id, int slot)
+{
+    stage_rec(st, X.g_rec, id, slot);
+    if (gauss_planes<kG, kGeo>() > 4) st[4][slot] = X.g_aux[2 * (int64_t)id];
+    if (gauss_planes<kG, kGeo>() > 5) st[5][slot] = X.g_aux[2 * (int64_t)id + 1];
+}
+
+// Surfel normal from its record, camera space, facing the camera: the record's
+// 1/z = iz0 + gu (u - ur) + gv (v - vr) equals (n . ray)/(n . P), so
+// m = (gu fx, gv fy, iz0 - gu (ur - cx) - gv (vr - cy)) = n / (n . P).
+__device__ __forceinline__ void surfel_normal(const float4 *rec, int id, const CamParams &C, float *nrm)
+{
+    const float4 r0 = rec[4 * (int64_t)id], r1 = rec[4 * (int64_t)id + 1];
+    const float mx = r0.w * C.fx, my = r1.x * C.fy;
+    const float mz = r0.z - r0.w * (r0.x - C.cx) - r1.x * (r0.y - C.cy);
+    const float inv = -rsqrtf(fmaf(mx, mx, fmaf(my, my, mz * mz)));
+    nrm[0] = mx * inv; nrm[1] = my * inv; nrm[2] = mz * inv;
+}
+
+// Geometry outputs of a render (Sec. 6.4, Eq. 10-12); any may be null.
+struct GeoMaps {
+    float *ns;            // [3,H,W] surfel normal (0 where no surfel)
+    float *dsm;           // [H,W] D_smooth
+    float *nsm;           // [3,H,W] N_smooth
+    float *dg;            // [H,W] D_G
+    float *ng;            // [3,H,W] N_G
+};
+
 // One 16x16 tile.  ss/sgs: shared staging for surfel and Gaussian records,
 // structure-of-arrays (one float4 plane per 16-byte quarter): consecutive
 // threads store consecutive 16 B, and a warp reading one record gets a
 // broadcast.  kS surfel samples per pixel: 1 (the centre) or 4 (the 2x2 grid
 // at +-0.25 px, 4x multisampling of Sec. 5; the Gaussians stay at the centre).
-template <int kS>
+// kG: 3D Gaussians (EWA splats) or 2D Gaussians of 2D-GES (ray-splat hit,
+// planar depth).  kGeo: also the geometry maps of Eq. 10-12.
+template <int kS, int kG, bool kGeo>
 __device__ __forceinline__ void raster_tile(const ViewScratch &X, const CamParams &C, const OptParams &O,
                                             float *__restrict__ out_rgb, float *__restrict__ out_depth,
-                                            int32_t *__restrict__ out_id, float *__restrict__ aux, int tile,
+                                            int32_t *__restrict__ out_id, float *__restrict__ aux,
+                                            const GeoMaps &geo, int tile,
                                             float4 (*ss)[kChunk], float4 (*sgs)[kChunk])
 {
     const int tx = tile % C.tiles_x, ty = tile / C.tiles_x;
@@ -376,7 +449,7 @@ __device__ __forceinline__ void raster_tile(const ViewScratch &X, const CamParam
 
     // first chunk of both lists together: one round trip, one barrier
     if (s0 + t < s1) stage_rec(ss, X.s_rec, X.s_list[s0 + t], t);
-    if (g0 + t < g1) stage_rec(sgs, X.g_rec, X.g_list[g0 + t], t);
+    if (g0 + t < g1) stage_gauss<kG, kGeo>(sgs, X, X.g_list[g0 + t], t);
     __syncthreads();
 
     // ---------------- pass 1: surfel z-buffer ----------------
@@ -468,13 +541,14 @@ __device__ __forceinline__ void raster_tile(const ViewScratch &X, const CamParam
 
     // ---------------- pass 2: Gaussians (Eq. 2-4) ----------------
     long long acc_r = 0, acc_g = 0, acc_b = 0, acc_w = 0;
+    long long acc_d = 0, acc_nx = 0, acc_ny = 0, acc_nz = 0;   // D_G, N_G (kGeo)
     // no Gaussian with key >= max over the warp's pixels of D_s can pass the depth test there
     const float wmaxD = __uint_as_float(__reduce_max_sync(0xffffffffu, in_img ? __float_as_uint(Ds) : 0u));
     const float amin32 = O.alpha_min * 4294967296.f;
     for (int base = g0; base < g1; base += kChunk) {
         if (base != g0) {
             __syncthreads();
-            if (base + t < g1) stage_rec(sgs, X.g_rec, X.g_list[base + t], t);
+            if (base + t < g1) stage_gauss<kG, kGeo>(sgs, X, X.g_list[base + t], t);
             __syncthreads();
         }
         const int n = min(kChunk, g1 - base);
@@ -484,26 +558,52 @@ __device__ __forceinline__ void raster_tile(const ViewScratch &X, const CamParam
                 bool keep = false;
                 if (j < n) {
                     const float4 r3 = sgs[3][j];
+                    // 3D: key = d - eps; 2D: the smallest planar depth (1/izmax) - eps
+                    const float key = kG == 2 ? 1.f / sgs[2][j].w - r3.w : sgs[2][j].x;
                     keep = box_overlap(__float_as_uint(r3.y), __float_as_uint(r3.z), wx0, wy0, wx1, wy1) &&
-                           sgs[2][j].x < wmaxD;
+                           key < wmaxD;
                 }
                 unsigned mask = __ballot_sync(0xffffffffu, keep);
                 while (mask) {
                     const int jj = j0 + __ffs(mask) - 1;
                     mask &= mask - 1;
-                    GaussRec g;
-                    *reinterpret_cast<float4 *>(&g.px) = sgs[0][jj];
-                    *reinterpret_cast<float4 *>(&g.la) = sgs[1][jj];
-                    *reinterpret_cast<float4 *>(&g.key) = sgs[2][jj];
-                    float e;
-                    const float a = gauss_alpha(g, u, v, e);
+                    float a, depth, cr, cg, cb, ok;
+                    float4 side = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (kG == 2) {
+                        const float4 r0 = sgs[0][jj], r1 = sgs[1][jj], r2 = sgs[2][jj];
+                        const float4 x0 = sgs[4][jj];
+                        side = sgs[5][jj];
+                        const float du = u - r0.x, dv = v - r0.y;
+                        const float iz = fmaf(r0.w, du, fmaf(r1.x, dv, r0.z));
+                        const float A = fmaf(r1.y, du, fmaf(r1.z, dv, r1.w));
+                        const float B = fmaf(r2.x, du, fmaf(r2.y, dv, r2.z));
+                        depth = __frcp_rn(iz);
+                        // rho = (a'^2 + b'^2)/r^2; alpha = 2^(log2 sigma' + log2(alpha_min/sigma') rho)
+                        const float rho = fmaf(A, A, B * B) * (depth * depth);
+                        a = ex2_approx(fmaf(side.w, rho, x0.w));
+                        cr = x0.x; cg = x0.y; cb = x0.z;
+                        ok = (iz > 0.f && iz < C.izn && depth - sgs[3][jj].w < Ds) ? 1.f : 0.f;
+                    } else {
+                        const GaussRec g = gauss_rec3(sgs[0][jj], sgs[1][jj], sgs[2][jj]);
+                        float e;
+                        a = gauss_alpha(g, u, v, e);
+                        cr = g.r; cg = g.g; cb = g.b;
+                        ok = g.key < Ds ? 1.f : 0.f;
+                        if (kGeo) { side = sgs[4][jj]; depth = side.w; }
+                    }
                     // alpha * 2^32 is exact scaling: the clamp decision equals alpha >= alpha_min
                     const float a32 = a * 4294967296.f;
-                    if (in_img && a32 >= amin32 && g.key < Ds) {
+                    if (in_img && a32 >= amin32 && ok != 0.f) {
                         acc_w += __float2ll_rn(a32);
-                        acc_r += __float2ll_rn(a32 * g.r);
-                        acc_g += __float2ll_rn(a32 * g.g);
-                        acc_b += __float2ll_rn(a32 * g.b);
+                        acc_r += __float2ll_rn(a32 * cr);
+                        acc_g += __float2ll_rn(a32 * cg);
+                        acc_b += __float2ll_rn(a32 * cb);
+                        if (kGeo) {
+                            acc_d += __float2ll_rn(a32 * depth);
+                            acc_nx += __float2ll_rn(a32 * side.x);
+                            acc_ny += __float2ll_rn(a32 * side.y);
+                            acc_nz += __float2ll_rn(a32 * side.z);
+                        }
                     }
                 }
             }
@@ -534,19 +634,40 @@ __device__ __forceinline__ void raster_tile(const ViewScratch &X, const CamParam
         for (int k = 0; k < kS; ++k) out_id[k * HW + pix] = bid[k] != 0x7fffffff ? bid[k] : -1;
     }
     if (aux) aux[pix] = WG;
+    if (kGeo) {
+        // Eq. 10-12 with W_s = 1 where a surfel covers the pixel, 0 elsewhere
+        float ns[3] = {0.f, 0.f, 0.f};
+        const bool covered = bmax > 0.f;
+        if (covered) {
+            // the nearest sample's surfel (lowest id on a tie)
+            int w = 0x7fffffff;
+#pragma unroll
+            for (int k = 0; k < kS; ++k)
+                if (best[k] == bmax && bid[k] < w) w = bid[k];
+            surfel_normal(X.s_rec, w, C, ns);
+        }
+        const float DG = __ll2float_rn(acc_d) * k32;
+        const float NG[3] = {__ll2float_rn(acc_nx) * k32, __ll2float_rn(acc_ny) * k32, __ll2float_rn(acc_nz) * k32};
+        const float ws = covered ? 1.f : 0.f, wt = ws + WG;
+        if (geo.dg) geo.dg[pix] = DG;
+        if (geo.dsm) geo.dsm[pix] = wt > 0.f ? ((covered ? Ds : 0.f) + DG) / wt : INFINITY;
+        for (int c = 0; c < 3; ++c) {
+            if (geo.ns) geo.ns[c * HW + pix] = ns[c];
+            if (geo.ng) geo.ng[c * HW + pix] = NG[c];
+            if (geo.nsm) geo.nsm[c * HW + pix] = wt > 0.f ? (ws * ns[c] + NG[c]) / wt : 0.f;
+        }
+    }
 }
 
-template <int kS>
-__global__ void __launch_bounds__(kRasterThreads, kS == 1 ? 5 : 4) k_raster(ViewScratch X, CamParams C, OptParams O,
-                                                           float *__restrict__ out_rgb,
-                                                           float *__restrict__ out_depth,
-                                                           int32_t *__restrict__ out_id,
-                                                           float *__restrict__ aux)
+template <int kS, int kG, bool kGeo>
+__global__ void __launch_bounds__(kRasterThreads, kS == 1 && kG == 3 && !kGeo ? 5 : 4)
+    k_raster(ViewScratch X, CamParams C, OptParams O, float *__restrict__ out_rgb, float *__restrict__ out_depth,
+             int32_t *__restrict__ out_id, float *__restrict__ aux, GeoMaps geo)
 {
     __shared__ float4 ss[4][kChunk];
-    __shared__ float4 sgs[4][kChunk];
+    __shared__ float4 sgs[gauss_planes<kG, kGeo>()][kChunk];
     if (X.status[ST_FLAGS] & (FLAG_SOVF | FLAG_GOVF)) return;
-    raster_tile<kS>(X, C, O, out_rgb, out_depth, out_id, aux, blockIdx.x, ss, sgs);
+    raster_tile<kS, kG, kGeo>(X, C, O, out_rgb, out_depth, out_id, aux, geo, blockIdx.x, ss, sgs);
 }
 
 // ---------------------------------------------------------------------------
@@ -572,6 +693,7 @@ __device__ __forceinline__ void load_view(const BatchView *V, int v, BatchView &
     for (int k = threadIdx.x; k < (int)(sizeof(BatchView) / 4); k += blockDim.x) d[k] = src[k];
 }
 
+template <int kGd>
 __global__ void __launch_bounds__(kPrepThreads, 2) k_bprep(const BatchView *V, int n, OptParams O,
                                                           unsigned long long *t0)
 {
@@ -588,7 +710,7 @@ __global__ void __launch_bounds__(kPrepThreads, 2) k_bprep(const BatchView *V, i
     __syncthreads();
     load_view(V, sv, bv);
     __syncthreads();
-    prep_local_body(bv.S, bv.C, O, bv.X, bv.B, blockIdx.x - bv.prep_base, hist, vcnt);
+    prep_local_body<kGd>(bv.S, bv.C, O, bv.X, bv.B, blockIdx.x - bv.prep_base, hist, vcnt);
 }
 
 __global__ void __launch_bounds__(256) k_bcolscan(const BatchView *V, int n)
@@ -630,12 +752,12 @@ __global__ void __launch_bounds__(kFillThreads) k_bfill(const BatchView *V, int 
 // Persistent raster over the (view, tile) items of the whole batch: each CTA
 // takes the next item from a counter until none is left, so uneven views
 // balance across the GPU.
-template <int kS>
-__global__ void __launch_bounds__(kRasterThreads, kS == 1 ? 5 : 4) k_braster(const BatchView *V, int n, OptParams O,
+template <int kS, int kG>
+__global__ void __launch_bounds__(kRasterThreads, kS == 1 && kG == 3 ? 5 : 4) k_braster(const BatchView *V, int n, OptParams O,
                                                             unsigned *counter, int total)
 {
     __shared__ float4 ss[4][kChunk];
-    __shared__ float4 sgs[4][kChunk];
+    __shared__ float4 sgs[gauss_planes<kG, false>()][kChunk];
     __shared__ __align__(16) unsigned char bv_raw[sizeof(BatchView)];
     BatchView &bv = *reinterpret_cast<BatchView *>(bv_raw);
     __shared__ int item, sv;
@@ -654,7 +776,8 @@ __global__ void __launch_bounds__(kRasterThreads, kS == 1 ? 5 : 4) k_braster(con
         }
         __syncthreads();
         if (!(bv.X.status[ST_FLAGS] & (FLAG_SOVF | FLAG_GOVF)))
-            raster_tile<kS>(bv.X, bv.C, O, bv.rgb, bv.depth, nullptr, nullptr, it - bv.tile_base, ss, sgs);
+            raster_tile<kS, kG, false>(bv.X, bv.C, O, bv.rgb, bv.depth, nullptr, nullptr, GeoMaps{}, it - bv.tile_base,
+                                       ss, sgs);
         __syncthreads();
         // per-view completion time: the CTA that finishes the view's last tile stamps it
         if (threadIdx.x == 0 && atomicAdd(bv.X.status + ST_RETIRED, 1u) + 1u == (unsigned)bv.T)
@@ -671,8 +794,12 @@ cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const Opt
     auto mark = [&](int k) { if (ev) cudaEventRecordWithFlags(ev[k], st, cudaEventRecordExternal); };
     mark(0);
     if (P.total_prep > 0)
-        k_bprep<<<P.total_prep, kPrepThreads, local_bins_smem(P.max_T, false), st>>>(
-            d_views, P.n, O, reinterpret_cast<unsigned long long *>(work_counter + 2));
+    {
+        unsigned long long *t0 = reinterpret_cast<unsigned long long *>(work_counter + 2);
+        const size_t sm = local_bins_smem(P.max_T, false);
+        if (P.gdim == 2) k_bprep<2><<<P.total_prep, kPrepThreads, sm, st>>>(d_views, P.n, O, t0);
+        else k_bprep<3><<<P.total_prep, kPrepThreads, sm, st>>>(d_views, P.n, O, t0);
+    }
     mark(1);
     if (P.total_colscan > 0) k_bcolscan<<<dim3(P.total_colscan, 2), 256, 0, st>>>(d_views, P.n);
     k_bscan<<<2 * P.n, 1024, 0, st>>>(d_views);
@@ -680,10 +807,12 @@ cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const Opt
     if (P.total_prep > 0)
         k_bfill<<<P.total_prep, kFillThreads, local_bins_smem(P.max_T, true), st>>>(d_views, P.n);
     mark(3);
-    if (O.samples == 4)
-        k_braster<4><<<P.raster_ctas, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
-    else
-        k_braster<1><<<P.raster_ctas, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
+    // P.gdim: the Gaussian kind shared by all scenes of the batch
+    const unsigned grid = P.raster_ctas;
+    if (O.samples == 4 && P.gdim == 2) k_braster<4, 2><<<grid, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
+    else if (O.samples == 4) k_braster<4, 3><<<grid, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
+    else if (P.gdim == 2) k_braster<1, 2><<<grid, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
+    else k_braster<1, 3><<<grid, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
     mark(4);
     return cudaGetLastError();
 }
@@ -693,11 +822,11 @@ size_t local_bins_smem(int T, bool fill) { return fill ? (size_t)T * 4 : (size_t
 cudaError_t prepare_forward_kernels()
 {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_prep_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)local_bins_smem(kLocalMaxTiles, false))) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(k_bprep, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)local_bins_smem(kLocalMaxTiles, false))) != cudaSuccess)
+    const int hs = (int)local_bins_smem(kLocalMaxTiles, false);
+    if ((e = cudaFuncSetAttribute(k_prep_local<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_prep_local<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_bprep<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_bprep<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess)
         return e;
     if ((e = cudaFuncSetAttribute(k_fill_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)local_bins_smem(kLocalMaxTiles, true))) != cudaSuccess)
@@ -723,11 +852,17 @@ cudaError_t launch_binning(const SceneView &S, const CamParams &C, const OptPara
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         B = plan_local_bins(Sv.N, Sv.M, sms);
-        if (B.Ps + B.Pg > 0)
-            k_prep_local<<<B.Ps + B.Pg, kPrepThreads, local_bins_smem(T, false), st>>>(Sv, C, O, X, B);
+        if (B.Ps + B.Pg > 0) {
+            const size_t sm = local_bins_smem(T, false);
+            if (Sv.gdim == 2) k_prep_local<2><<<B.Ps + B.Pg, kPrepThreads, sm, st>>>(Sv, C, O, X, B);
+            else k_prep_local<3><<<B.Ps + B.Pg, kPrepThreads, sm, st>>>(Sv, C, O, X, B);
+        }
     } else {
         const int nsb = (int)((Sv.N + 255) / 256), ngb = (int)((Sv.M + 255) / 256);
-        if (nsb + ngb > 0) k_prep_atomic<<<nsb + ngb, 256, 0, st>>>(Sv, C, O, X, nsb);
+        if (nsb + ngb > 0) {
+            if (Sv.gdim == 2) k_prep_atomic<2><<<nsb + ngb, 256, 0, st>>>(Sv, C, O, X, nsb);
+            else k_prep_atomic<3><<<nsb + ngb, 256, 0, st>>>(Sv, C, O, X, nsb);
+        }
     }
     if (ev) cudaEventRecord(ev[1], st);
     if (local && B.Ps + B.Pg > 0) k_colscan<<<dim3((T + 31) / 32, 2), 256, 0, st>>>(X, T, B);
@@ -745,7 +880,7 @@ cudaError_t launch_binning(const SceneView &S, const CamParams &C, const OptPara
 // Exact work counts of one view: every (sample, surfel) fragment inside the
 // opaque disc in front of the near plane, and every (pixel, Gaussian) pair
 // with alpha >= alpha_min, over the full tile lists (no culling).
-__global__ void __launch_bounds__(256) k_count(ViewScratch X, CamParams C, OptParams O)
+__global__ void __launch_bounds__(256) k_count(SceneView S, ViewScratch X, CamParams C, OptParams O)
 {
     __shared__ float4 st[4][256];
     __shared__ unsigned red[2][8];
@@ -781,10 +916,19 @@ __global__ void __launch_bounds__(256) k_count(ViewScratch X, CamParams C, OptPa
                         const float B = fmaf(r2.x, du, fmaf(r2.y, dv, r2.z));
                         ns += (fmaf(A, A, fmaf(B, B, -iz * iz)) <= 0.f && iz > 0.f && iz < C.izn) ? 1u : 0u;
                     }
+                } else if (S.gdim == 2) {
+                    const float4 r0 = st[0][j], r1 = st[1][j], r2 = st[2][j];
+                    const int id = __float_as_int(st[3][j].x);
+                    const float4 x0 = X.g_aux[2 * (int64_t)id], x1 = X.g_aux[2 * (int64_t)id + 1];
+                    const float du = u - r0.x, dv = v - r0.y;
+                    const float iz = fmaf(r0.w, du, fmaf(r1.x, dv, r0.z));
+                    const float A = fmaf(r1.y, du, fmaf(r1.z, dv, r1.w));
+                    const float B = fmaf(r2.x, du, fmaf(r2.y, dv, r2.z));
+                    const float z = __frcp_rn(iz);
+                    const float a = ex2_approx(fmaf(x1.w, fmaf(A, A, B * B) * (z * z), x0.w));
+                    ng += (iz > 0.f && iz < C.izn && a >= O.alpha_min) ? 1u : 0u;
                 } else {
-                    GaussRec g;
-                    *reinterpret_cast<float4 *>(&g.px) = st[0][j];
-                    *reinterpret_cast<float4 *>(&g.la) = st[1][j];
+                    const GaussRec g = gauss_rec3(st[0][j], st[1][j], make_float4(0.f, 0.f, 0.f, 0.f));
                     float e;
                     ng += gauss_alpha(g, u, v, e) >= O.alpha_min ? 1u : 0u;
                 }
@@ -806,16 +950,31 @@ __global__ void __launch_bounds__(256) k_count(ViewScratch X, CamParams C, OptPa
 }
 }  // namespace
 
+namespace {
+template <int kS, int kG>
+void launch_raster(const ViewScratch &X, const CamParams &C, const OptParams &O, float *out_rgb, float *out_depth,
+                   int32_t *out_id, float *aux, const GeoMaps &geo, cudaStream_t st)
+{
+    const unsigned grid = C.tiles_x * C.tiles_y;
+    if (O.geo) k_raster<kS, kG, true><<<grid, kRasterThreads, 0, st>>>(X, C, O, out_rgb, out_depth, out_id, aux, geo);
+    else k_raster<kS, kG, false><<<grid, kRasterThreads, 0, st>>>(X, C, O, out_rgb, out_depth, out_id, aux, geo);
+}
+}  // namespace
+
 cudaError_t launch_forward(const SceneView &S, const CamParams &C, const OptParams &O, const ViewScratch &X,
                            float *out_rgb, float *out_depth, int32_t *out_id, float *aux, cudaStream_t st,
-                           cudaEvent_t *ev)
+                           cudaEvent_t *ev, const float *const *geo_maps)
 {
     cudaError_t e = launch_binning(S, C, O, X, st, ev);
     if (e != cudaSuccess) return e;
-    if (O.samples == 4)
-        k_raster<4><<<C.tiles_x * C.tiles_y, kRasterThreads, 0, st>>>(X, C, O, out_rgb, out_depth, out_id, aux);
-    else
-        k_raster<1><<<C.tiles_x * C.tiles_y, kRasterThreads, 0, st>>>(X, C, O, out_rgb, out_depth, out_id, aux);
+    GeoMaps geo{};
+    if (geo_maps) geo = GeoMaps{const_cast<float *>(geo_maps[0]), const_cast<float *>(geo_maps[1]),
+                                const_cast<float *>(geo_maps[2]), const_cast<float *>(geo_maps[3]),
+                                const_cast<float *>(geo_maps[4])};
+    if (O.samples == 4 && S.gdim == 2) launch_raster<4, 2>(X, C, O, out_rgb, out_depth, out_id, aux, geo, st);
+    else if (O.samples == 4) launch_raster<4, 3>(X, C, O, out_rgb, out_depth, out_id, aux, geo, st);
+    else if (S.gdim == 2) launch_raster<1, 2>(X, C, O, out_rgb, out_depth, out_id, aux, geo, st);
+    else launch_raster<1, 3>(X, C, O, out_rgb, out_depth, out_id, aux, geo, st);
     if (ev) cudaEventRecord(ev[4], st);
     return cudaGetLastError();
 }
@@ -890,7 +1049,7 @@ cudaError_t launch_count(const SceneView &S, const CamParams &C, const OptParams
 {
     cudaError_t e = launch_binning(S, C, O, X, st, nullptr);
     if (e != cudaSuccess) return e;
-    k_count<<<C.tiles_x * C.tiles_y, 256, 0, st>>>(X, C, O);
+    k_count<<<C.tiles_x * C.tiles_y, 256, 0, st>>>(S, X, C, O);
     return cudaGetLastError();
 }
 

@@ -50,6 +50,7 @@ struct OptParams {
     int mode;
     int samples;          // surfel samples per pixel: 1 or 4
     int filter;           // GES_FILTER_EWA or GES_FILTER_MIP
+    int geo;              // 1: the render also produces the geometry maps (Sec. 6.4)
 };
 
 struct SceneView {
@@ -60,6 +61,7 @@ struct SceneView {
     const float *g_pos;
     const void *g_rot, *g_scale, *g_opac, *g_sh;
     const float *g_filt3;     // Mip-GES 3D filter variance [M], or null
+    int gdim;                 // 3: 3D Gaussians; 2: 2D Gaussians of 2D-GES (g_scale [M,2])
 };
 
 // Scratch of one view (device pointers owned by the scene).
@@ -79,6 +81,10 @@ struct ViewScratch {
     unsigned *hist = nullptr;    // [P][ceil(T/2)] packed 16-bit per-CTA tile counts
     unsigned *base = nullptr;    // [P][T] per-CTA start inside each tile's list
     unsigned *vcount = nullptr;  // [P] visible primitives per CTA
+    // [M][2] side data of each Gaussian, written when the render needs it:
+    // 2D Gaussians (rgb, log2 sigma'), (normal, log2(alpha_min / sigma'));
+    // 3D Gaussians with geometry outputs (normal, centre depth), unused
+    float4 *g_aux = nullptr;
 };
 
 // Number of preprocess CTAs for local binning and the size of their ranges.
@@ -102,6 +108,7 @@ struct BatchPlan {
     int n;                                   // views
     int total_tiles, total_prep, total_colscan, max_T;
     int raster_ctas;                         // persistent raster grid
+    int gdim;                                // Gaussian kind of every scene (2 or 3; 0 reads as 3)
 };
 cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const OptParams &O, unsigned *work_counter,
                          cudaStream_t st, cudaEvent_t *ev /* 5 events or nullptr */);
@@ -115,9 +122,11 @@ cudaError_t prepare_forward_kernels();   // once per device: large dynamic share
 // ---------------------------------------------------------------------------
 // host launchers (ges_forward.cu / ges_backward.cu)
 
+// geo_maps: null, or 5 device pointers (each may be null): N_s [3,H,W],
+// D_smooth [H,W], N_smooth [3,H,W], D_G [H,W], N_G [3,H,W]; with O.geo set.
 cudaError_t launch_forward(const SceneView &S, const CamParams &C, const OptParams &O, const ViewScratch &X,
                            float *out_rgb, float *out_depth, int32_t *out_id, float *aux, cudaStream_t st,
-                           cudaEvent_t *ev /* 5 events or nullptr */);
+                           cudaEvent_t *ev /* 5 events or nullptr */, const float *const *geo_maps = nullptr);
 
 cudaError_t launch_count(const SceneView &S, const CamParams &C, const OptParams &O, const ViewScratch &X,
                          cudaStream_t st);
@@ -389,7 +398,8 @@ __device__ __forceinline__ unsigned pack_xy(int x, int y) { return (unsigned)x |
 //   A    = a0  + au du + av dv          a * invz / r   (a, b: disc coordinates
 //   B    = b0  + bu du + bv dv          b * invz / r    scaled by s1, s2)
 // The pixel is inside the opaque disc iff invz > 0 and A^2 + B^2 <= invz^2.
-struct SurfelRec {
+// (16-byte aligned: it is moved as four float4)
+struct __align__(16) SurfelRec {
     float ur, vr, iz0, gu;
     float gv, au, av, a0;
     float bu, bv, b0, izmax;      // izmax: largest 1/z over the disc (culling)
@@ -397,7 +407,7 @@ struct SurfelRec {
     unsigned bb_lo, bb_hi;        // pixel bbox (x | y << 16), inclusive
     float pad;
 };
-static_assert(sizeof(SurfelRec) == 64, "surfel record is 64 B");
+static_assert(sizeof(SurfelRec) == 64 && alignof(SurfelRec) == 16, "surfel record is 64 B, 16-aligned");
 
 // Gaussian raster record (64 B).  alpha(u,v) = sigma * 2^-(y0^2 + y1^2) with
 // y0 = la dx, y1 = lb dx + lc dy, dx = (u - px) - pxl (projected centre in
@@ -406,7 +416,7 @@ static_assert(sizeof(SurfelRec) == 64, "surfel record is 64 B");
 // q = dx^T Sigma2^-1 dx = (a dx)^2 + (b dx + c dy)^2.  This sum of squares
 // stays accurate far from the centre of elongated Gaussians, where the
 // expanded quadratic form cancels.  Depth test: key = d - eps < D_s.
-struct GaussRec {
+struct __align__(16) GaussRec {
     float px, py, pxl, pyl;
     float la, lb, lc, sigma;
     float key, r, g, b;
@@ -414,7 +424,7 @@ struct GaussRec {
     unsigned bb_lo, bb_hi;
     float pad;
 };
-static_assert(sizeof(GaussRec) == 64, "Gaussian record is 64 B");
+static_assert(sizeof(GaussRec) == 64 && alignof(GaussRec) == 16, "Gaussian record is 64 B, 16-aligned");
 
 struct SurfelOut {
     bool valid_quat;
@@ -436,44 +446,27 @@ __device__ __forceinline__ void pixel_span(float a, float b, int n, int &lo, int
     lo = (int)fl; hi = (int)fh;
 }
 
-// Per-surfel set-up for the view (Sec. 3: disc placed by scale, rotation,
-// translation; opaque extent of Sec. 4.1).  Produces the raster record, the
-// colour (Eq. 1) and a conservative pixel bbox.
-__device__ __forceinline__ void surfel_setup(const SceneView &S, const CamParams &C, const OptParams &O,
-                                             int64_t i, SurfelOut &o)
+// Raster record of a planar disc a^2 + b^2 <= r^2 (a, b in units of the scales
+// s1, s2 along the camera-space axes tu, tv; normal n; centre P in
+// double-float): affine forms of 1/z and of (a/r)/z, (b/r)/z around a
+// reference pixel, the largest 1/z over the disc, and a conservative pixel
+// bbox widened by pad.  False when no part of it can be on screen.
+struct DiscOut {
+    SurfelRec rec;
+    int x0, y0, x1, y1;
+};
+
+__device__ __forceinline__ bool disc_setup(const CamParams &C, const df *P, const float *tu, const float *tv,
+                                           const float *n, float s1, float s2, float r, float pad, int id,
+                                           DiscOut &o)
 {
-    o.visible = false;
-    o.valid_quat = true;
-    const float px = __ldg(S.s_pos + 3 * i), py = __ldg(S.s_pos + 3 * i + 1), pz = __ldg(S.s_pos + 3 * i + 2);
-    float q[4], R[9];
-    for (int k = 0; k < 4; ++k) q[k] = load_attr(S.s_rot, 4 * i + k, S.attr_dtype);
-    if (!quat_to_rot(q[0], q[1], q[2], q[3], R, nullptr, nullptr)) { o.valid_quat = false; return; }
-    const float s1 = load_attr(S.s_scale, 2 * i, S.attr_dtype), s2 = load_attr(S.s_scale, 2 * i + 1, S.attr_dtype);
-    // view direction for the SH colour: from the surfel centre to the camera
-    {
-        float vx = C.ocam[0] - px, vy = C.ocam[1] - py, vz = C.ocam[2] - pz;
-        float L = sqrtf(vx * vx + vy * vy + vz * vz);
-        float il = L > 0.f ? 1.f / L : 0.f;
-        o.dir[0] = vx * il; o.dir[1] = vy * il; o.dir[2] = vz * il;
-    }
-    if (!(s1 > 0.f && s2 > 0.f && isfinite(s1) && isfinite(s2))) return;
-    // camera-space frame (float) and centre (double-float)
-    float tu[3], tv[3], n[3];
-    for (int r = 0; r < 3; ++r) {
-        tu[r] = C.R[3 * r] * R[0] + C.R[3 * r + 1] * R[3] + C.R[3 * r + 2] * R[6];
-        tv[r] = C.R[3 * r] * R[1] + C.R[3 * r + 1] * R[4] + C.R[3 * r + 2] * R[7];
-        n[r] = C.R[3 * r] * R[2] + C.R[3 * r + 1] * R[5] + C.R[3 * r + 2] * R[8];
-    }
-    df P[3];
-    for (int r = 0; r < 3; ++r) P[r] = df_dot3_plus(C.R + 3 * r, px, py, pz, C.t[r]);
     const float Ph[3] = {P[0].hi, P[1].hi, P[2].hi};
     const float nP = fmaf(n[0], Ph[0], fmaf(n[1], Ph[1], n[2] * Ph[2])) +
                      (n[0] * P[0].lo + n[1] * P[1].lo + n[2] * P[2].lo);
-    if (!(nP != 0.f) || !isfinite(nP)) return;
-    const float r = O.surfel_r;
+    if (!(nP != 0.f) || !isfinite(nP)) return false;
     const float ez = r * sqrtf(s1 * tu[2] * s1 * tu[2] + s2 * tv[2] * s2 * tv[2]);
     const float zmax = Ph[2] + ez, zmin = Ph[2] - ez;
-    if (!(zmax > C.znear * (1.f - 1e-5f) - 1e-6f)) return;
+    if (!(zmax > C.znear * (1.f - 1e-5f) - 1e-6f)) return false;
 
     // --- affine coefficients (see SurfelRec) ---
     const float inP = 1.f / nP;
@@ -590,7 +583,7 @@ __device__ __forceinline__ void surfel_setup(const SceneView &S, const CamParams
                 ++np;
             }
         }
-        if (np == 0) return;
+        if (np == 0) return false;
         for (int k = 0; k < np; ++k) {
             float izk = 1.f / poly[k][2];
             float u = C.fx * poly[k][0] * izk + C.cx, v = C.fy * poly[k][1] * izk + C.cy;
@@ -599,18 +592,55 @@ __device__ __forceinline__ void surfel_setup(const SceneView &S, const CamParams
         // one pixel of slack for the float projection of the clipped polygon
         umin -= 1.f; vmin -= 1.f; umax += 1.f; vmax += 1.f;
     }
-    // with 4 samples a pixel is touched when a sample at +-0.25 px from its
-    // centre falls inside: widen the interval of centres by that much
-    if (O.samples == 4) { umin -= 0.25f; vmin -= 0.25f; umax += 0.25f; vmax += 0.25f; }
+    // widen the interval of pixel centres by pad (4x multisampling: a pixel is
+    // touched when a sample at +-0.25 px from its centre falls inside)
+    umin -= pad; vmin -= pad; umax += pad; vmax += pad;
     int x0, x1, y0, y1;
     pixel_span(fmaxf(umin, -1e6f), fminf(umax, 1e6f), C.W, x0, x1);
     pixel_span(fmaxf(vmin, -1e6f), fminf(vmax, 1e6f), C.H, y0, y1);
-    if (x0 > x1 || y0 > y1) return;
+    if (x0 > x1 || y0 > y1) return false;
     o.x0 = x0; o.x1 = x1; o.y0 = y0; o.y1 = y1;
 
     float izmax = zmin > C.znear ? (1.f / zmin) * (1.f + 4e-6f) : C.izn * (1.f + 4e-6f);
-    o.rec = SurfelRec{ur, vr, iz0, gu, gv, au, av, a0, bu, bv, b0, izmax, (int)i,
+    o.rec = SurfelRec{ur, vr, iz0, gu, gv, au, av, a0, bu, bv, b0, izmax, id,
                       pack_xy(x0, y0), pack_xy(x1, y1), 0.f};
+    return true;
+}
+
+// Per-surfel set-up for the view (Sec. 3: disc placed by scale, rotation,
+// translation; opaque extent of Sec. 4.1).  Produces the raster record, the
+// colour (Eq. 1) and a conservative pixel bbox.
+__device__ __forceinline__ void surfel_setup(const SceneView &S, const CamParams &C, const OptParams &O,
+                                             int64_t i, SurfelOut &o)
+{
+    o.visible = false;
+    o.valid_quat = true;
+    const float px = __ldg(S.s_pos + 3 * i), py = __ldg(S.s_pos + 3 * i + 1), pz = __ldg(S.s_pos + 3 * i + 2);
+    float q[4], R[9];
+    for (int k = 0; k < 4; ++k) q[k] = load_attr(S.s_rot, 4 * i + k, S.attr_dtype);
+    if (!quat_to_rot(q[0], q[1], q[2], q[3], R, nullptr, nullptr)) { o.valid_quat = false; return; }
+    const float s1 = load_attr(S.s_scale, 2 * i, S.attr_dtype), s2 = load_attr(S.s_scale, 2 * i + 1, S.attr_dtype);
+    // view direction for the SH colour: from the surfel centre to the camera
+    {
+        float vx = C.ocam[0] - px, vy = C.ocam[1] - py, vz = C.ocam[2] - pz;
+        float L = sqrtf(vx * vx + vy * vy + vz * vz);
+        float il = L > 0.f ? 1.f / L : 0.f;
+        o.dir[0] = vx * il; o.dir[1] = vy * il; o.dir[2] = vz * il;
+    }
+    if (!(s1 > 0.f && s2 > 0.f && isfinite(s1) && isfinite(s2))) return;
+    // camera-space frame (float) and centre (double-float)
+    float tu[3], tv[3], n[3];
+    for (int r = 0; r < 3; ++r) {
+        tu[r] = C.R[3 * r] * R[0] + C.R[3 * r + 1] * R[3] + C.R[3 * r + 2] * R[6];
+        tv[r] = C.R[3 * r] * R[1] + C.R[3 * r + 1] * R[4] + C.R[3 * r + 2] * R[7];
+        n[r] = C.R[3 * r] * R[2] + C.R[3 * r + 1] * R[5] + C.R[3 * r + 2] * R[8];
+    }
+    df P[3];
+    for (int r = 0; r < 3; ++r) P[r] = df_dot3_plus(C.R + 3 * r, px, py, pz, C.t[r]);
+    DiscOut d;
+    if (!disc_setup(C, P, tu, tv, n, s1, s2, O.surfel_r, O.samples == 4 ? 0.25f : 0.f, (int)i, d)) return;
+    o.rec = d.rec;
+    o.x0 = d.x0; o.y0 = d.y0; o.x1 = d.x1; o.y1 = d.y1;
     const int K = (S.deg + 1) * (S.deg + 1);
     float Y[16];
     sh_basis(K, o.dir[0], o.dir[1], o.dir[2], Y);
@@ -632,6 +662,10 @@ struct GaussOut {
     float se[3];              // axis lengths after the 3D filter (= s without it)
     float n0, n1, det0;       // Sigma2 before the screen filter: diagonal and determinant
     int x0, y0, x1, y1;
+    // 2D Gaussians: a disc record (SurfelRec layout, eps in its last word)
+    // instead of rec; both kinds: side data for g_aux
+    SurfelRec drec;
+    float4 aux[2];
 };
 
 // Per-Gaussian set-up (Eq. 4: projected covariance and centre; 1/255 clamp
@@ -746,6 +780,95 @@ __device__ __forceinline__ void gauss_setup(const SceneView &S, const CamParams 
     sh_basis(K, o.dir[0], o.dir[1], o.dir[2], Y);
     sh_colour(S.g_sh, i, K, S.sh_dtype, Y, o.rgb, o.raw);
     o.rec.r = o.rgb[0]; o.rec.g = o.rgb[1]; o.rec.b = o.rgb[2];
+    if (O.geo) {
+        // geometry (Sec. 6.4): d_i = centre depth, n_i = the axis of the smallest
+        // scale, camera space, facing the camera
+        int km = 0;
+        for (int k = 1; k < 3; ++k)
+            if (fabsf(o.s[k]) < fabsf(o.s[km])) km = k;
+        float nc[3];
+        for (int r = 0; r < 3; ++r)
+            nc[r] = C.R[3 * r] * o.R[km] + C.R[3 * r + 1] * o.R[3 + km] + C.R[3 * r + 2] * o.R[6 + km];
+        const float fl = (nc[0] * x + nc[1] * y + nc[2] * z) > 0.f ? -1.f : 1.f;
+        o.aux[0] = make_float4(fl * nc[0], fl * nc[1], fl * nc[2], z);
+        o.aux[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    o.visible = true;
+}
+
+// 2D Gaussian of 2D-GES (Sec. 6.4): a splat in the plane of its rotation's
+// first two axes, opacity sigma exp(-(a^2 + b^2)/2) at the ray-splat hit (a, b
+// in scale units), planar depth for the depth test.  The screen-space EWA
+// filter of size lowpass is back-projected into object space (Eq. 17-18):
+// with J the Jacobian of local unit coordinates -> pixels at the centre, the
+// scales become s_k S_k and the opacity sigma / (S1 S2), with
+// S_k = sqrt(1 + lowpass ((J^T J)^-1)_kk) (the diagonal of I + lowpass J^-1 J^-T).
+// The support alpha >= alpha_min is the disc of radius r = sqrt(2 ln(sigma'/alpha_min))
+// in filtered units, so the record is a disc record (disc_setup) and
+// alpha = 2^(log2 sigma' + log2(alpha_min/sigma') rho), rho = (a'^2 + b'^2)/r^2.
+__device__ __forceinline__ void gauss2d_setup(const SceneView &S, const CamParams &C, const OptParams &O,
+                                              int64_t i, GaussOut &o)
+{
+    o.visible = false;
+    o.valid_quat = true;
+    const float px = __ldg(S.g_pos + 3 * i), py = __ldg(S.g_pos + 3 * i + 1), pz = __ldg(S.g_pos + 3 * i + 2);
+    float q[4];
+    for (int k = 0; k < 4; ++k) q[k] = load_attr(S.g_rot, 4 * i + k, S.attr_dtype);
+    if (!quat_to_rot(q[0], q[1], q[2], q[3], o.R, o.qn, &o.qnorm)) { o.valid_quat = false; return; }
+    const float s0 = load_attr(S.g_scale, 2 * i, S.attr_dtype), s1 = load_attr(S.g_scale, 2 * i + 1, S.attr_dtype);
+    o.s[0] = s0; o.s[1] = s1; o.s[2] = 0.f;
+    const float sigma = load_attr(S.g_opac, i, S.attr_dtype);
+    o.sigma0 = sigma;
+    {
+        float vx = C.ocam[0] - px, vy = C.ocam[1] - py, vz = C.ocam[2] - pz;
+        float L = sqrtf(vx * vx + vy * vy + vz * vz);
+        float il = L > 0.f ? 1.f / L : 0.f;
+        o.dir[0] = vx * il; o.dir[1] = vy * il; o.dir[2] = vz * il;
+        o.dist = L;
+    }
+    if (!(sigma >= O.alpha_min)) return;            // sigma' <= sigma
+    if (!(s0 > 0.f && s1 > 0.f && isfinite(s0) && isfinite(s1))) return;
+    float tu[3], tv[3], n[3];
+    for (int r = 0; r < 3; ++r) {
+        tu[r] = C.R[3 * r] * o.R[0] + C.R[3 * r + 1] * o.R[3] + C.R[3 * r + 2] * o.R[6];
+        tv[r] = C.R[3 * r] * o.R[1] + C.R[3 * r + 1] * o.R[4] + C.R[3 * r + 2] * o.R[7];
+        n[r] = C.R[3 * r] * o.R[2] + C.R[3 * r + 1] * o.R[5] + C.R[3 * r + 2] * o.R[8];
+    }
+    df P[3];
+    for (int r = 0; r < 3; ++r) P[r] = df_dot3_plus(C.R + 3 * r, px, py, pz, C.t[r]);
+    if (!(P[2].hi > C.znear || (P[2].hi == C.znear && P[2].lo > 0.f))) return;
+    // object-space filter
+    const float x = P[0].hi, y = P[1].hi, z = P[2].hi, iz = 1.f / z;
+    const float j00 = C.fx * iz, j02 = -C.fx * x * iz * iz, j11 = C.fy * iz, j12 = -C.fy * y * iz * iz;
+    const float J00 = s0 * (j00 * tu[0] + j02 * tu[2]), J01 = s1 * (j00 * tv[0] + j02 * tv[2]);
+    const float J10 = s0 * (j11 * tu[1] + j12 * tu[2]), J11 = s1 * (j11 * tv[1] + j12 * tv[2]);
+    const float dJ = J00 * J11 - J01 * J10;         // det(J^T J) = det(J)^2
+    const float det = dJ * dJ;
+    if (!(det > 0.f) || !isfinite(det)) return;
+    const float M00 = J00 * J00 + J10 * J10, M11 = J01 * J01 + J11 * J11;
+    const float S1 = sqrtf(1.f + O.lowpass * M11 / det), S2 = sqrtf(1.f + O.lowpass * M00 / det);
+    const float sigp = sigma / (S1 * S2);
+    if (!(sigp >= O.alpha_min)) return;
+    const float r = sqrtf(2.f * logf(sigp / O.alpha_min));
+    if (!(r > 0.f)) return;
+    DiscOut d;
+    if (!disc_setup(C, P, tu, tv, n, s0 * S1, s1 * S2, r, 0.f, (int)i, d)) return;
+    float eps;
+    if (O.eps_mode == GES_EPS_ADAPTIVE) eps = O.eps_factor * 0.5f * (s0 + s1);
+    else if (O.eps_mode == GES_EPS_ZERO) eps = 0.f;
+    else eps = O.eps_value;
+    o.drec = d.rec;
+    o.drec.pad = eps;
+    o.x0 = d.x0; o.y0 = d.y0; o.x1 = d.x1; o.y1 = d.y1;
+    const float nP = n[0] * x + n[1] * y + n[2] * z;
+    const float fl = nP > 0.f ? -1.f : 1.f;
+    const int K = (S.deg + 1) * (S.deg + 1);
+    float Y[16];
+    sh_basis(K, o.dir[0], o.dir[1], o.dir[2], Y);
+    sh_colour(S.g_sh, i, K, S.sh_dtype, Y, o.rgb, o.raw);
+    const float lsig = log2f(sigp);
+    o.aux[0] = make_float4(o.rgb[0], o.rgb[1], o.rgb[2], lsig);
+    o.aux[1] = make_float4(fl * n[0], fl * n[1], fl * n[2], log2f(O.alpha_min) - lsig);
     o.visible = true;
 }
 

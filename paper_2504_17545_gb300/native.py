@@ -35,7 +35,7 @@ class ges_scene_desc(C.Structure):
                 ("attr_dtype", C.c_int32), ("sh_dtype", C.c_int32),
                 ("s_pos", C.c_void_p), ("s_rot", C.c_void_p), ("s_scale", C.c_void_p), ("s_sh", C.c_void_p),
                 ("g_pos", C.c_void_p), ("g_rot", C.c_void_p), ("g_scale", C.c_void_p), ("g_opac", C.c_void_p),
-                ("g_sh", C.c_void_p), ("g_filter3d", C.c_void_p)]
+                ("g_sh", C.c_void_p), ("g_filter3d", C.c_void_p), ("gauss_dim", C.c_int32)]
 
 
 class ges_camera(C.Structure):
@@ -81,6 +81,7 @@ _SIGS = {
     "ges_render": (C.c_int, [C.c_void_p, _P(ges_camera), C.c_void_p, C.c_void_p]),
     "ges_render_ex": (C.c_int, [C.c_void_p, _P(ges_camera), _P(ges_render_opts), C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.c_void_p]),
+    "ges_render_geom": (C.c_int, [C.c_void_p, _P(ges_camera), _P(ges_render_opts)] + [C.c_void_p] * 7),
     "ges_render_backward": (C.c_int, [C.c_void_p, _P(ges_camera), _P(ges_render_opts), C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_void_p, _P(ges_grads)]),
     "ges_render_batch": (C.c_int, [_P(C.c_void_p), _P(ges_camera), _P(C.c_int32), C.c_int32,
@@ -172,6 +173,13 @@ def ges_render(scene, cam: ges_camera, out_rgb: int, out_depth: int):
 def ges_render_ex(scene, cam: ges_camera, opts, out_rgb: int, out_depth: int, out_id: int, aux: int):
     _check(load().ges_render_ex(scene, C.byref(cam), C.byref(opts) if opts is not None else None,
                                 C.c_void_p(out_rgb), C.c_void_p(out_depth), C.c_void_p(out_id), C.c_void_p(aux)))
+
+
+def ges_render_geom(scene, cam: ges_camera, opts, out_rgb: int, out_depth: int, out_ns: int, out_dsm: int,
+                    out_nsm: int, out_dg: int, out_ng: int):
+    _check(load().ges_render_geom(scene, C.byref(cam), C.byref(opts) if opts is not None else None,
+                                  *[C.c_void_p(p) for p in (out_rgb, out_depth, out_ns, out_dsm, out_nsm,
+                                                             out_dg, out_ng)]))
 
 
 def ges_render_backward(scene, cam: ges_camera, opts, dL_drgb: int, out_rgb: int, out_depth: int,

@@ -69,6 +69,8 @@ class GESScene:
             raise TypeError("surfel and Gaussian SH must share one dtype")
         if self.t["s_pos"].dtype != torch.float32 or self.t["g_pos"].dtype != torch.float32:
             raise TypeError("positions are float32")
+        gs = self.t["g_scale"]
+        self.gauss_dim = 2 if gs.dim() == 2 and gs.shape[1] == 2 else 3
         self.attr_dtype = _DTYPES[attr]
         self.sh_dtype = _DTYPES[self.t["s_sh"].dtype]
         self._desc = self._make_desc()
@@ -110,6 +112,7 @@ class GESScene:
         d = N.ges_scene_desc()
         d.n_surfels, d.n_gaussians = self.n_surfels, self.n_gaussians
         d.sh_degree, d.attr_dtype, d.sh_dtype = self.sh_degree, self.attr_dtype, self.sh_dtype
+        d.gauss_dim = self.gauss_dim
         for k in _SCENE_KEYS:
             setattr(d, k, self.t[k].data_ptr() if self.t[k].numel() else None)
         f3 = getattr(self, "g_filter3d", None)
@@ -176,6 +179,22 @@ def render(scene: GESScene, cam, opts: Optional[dict] = None, with_aux: bool = T
     scene.bind_stream()
     N.ges_render_ex(scene.handle, c, o, rgb.data_ptr(), depth.data_ptr(),
                     sid.data_ptr() if sid is not None else 0, aux.data_ptr() if aux is not None else 0)
+    return out
+
+
+def render_geom(scene: GESScene, cam, opts: Optional[dict] = None):
+    """Render plus the geometry maps of Sec. 6.4 (Eq. 10-12), camera space:
+    dict(rgb, depth, ns [3,H,W], dsmooth [H,W], nsmooth [3,H,W], dg [H,W],
+    ng [3,H,W])."""
+    c = camera_struct(cam)
+    dev = scene.t["s_pos"].device
+    H, W = c.height, c.width
+    e = lambda *shape: torch.empty(shape, device=dev, dtype=torch.float32)
+    out = dict(rgb=e(3, H, W), depth=e(H, W), ns=e(3, H, W), dsmooth=e(H, W), nsmooth=e(3, H, W),
+               dg=e(H, W), ng=e(3, H, W))
+    scene.bind_stream()
+    N.ges_render_geom(scene.handle, c, opts_struct(opts),
+                      *[out[k].data_ptr() for k in ("rgb", "depth", "ns", "dsmooth", "nsmooth", "dg", "ng")])
     return out
 
 

@@ -5,7 +5,8 @@ as ambiguous (competing depths within 1e-6 relative, a disc rim within 1e-5
 relative of r^2, a near-plane or grazing fragment; with 4 samples, at any
 sample of the pixel); at flagged pixels the GPU's
 id must still be an acceptable answer (``oracle.id_validity``).  Depth must
-match to ``depth_rel`` where the ids match; colour to ``col_tol`` max abs per
+match to ``depth_rel + DEPTH_GRAZE / |cos|`` where the ids match (cos: between
+the ray and the winning disc's normal); colour to ``col_tol`` max abs per
 channel where the ids match and no Gaussian sits on the 1/255 clamp or the
 depth-test threshold.
 """
@@ -19,6 +20,10 @@ COL_TOL = 2e-4       # spec colour tolerance for FP32 work
 # final reciprocal 1u, and 16-bit quaternions renormalised in float32 a few u
 # more; over millions of pixels the worst case reaches ~20u (u = 2^-24).
 DEPTH_REL = 2e-6
+# depth z = (n.P)/(n.d): the float32 plane normal carries a few u per
+# component, so the relative error of n.d (and of z) grows as 1/|cos| of the
+# angle between the ray and the disc normal; 4e-7 ~ 6u covers it
+DEPTH_GRAZE = 4e-7
 
 
 def compare(scene, cam, gpu, ref, opts=None, col_tol=COL_TOL, depth_rel=DEPTH_REL, check_ids=True):
@@ -40,9 +45,27 @@ def compare(scene, cam, gpu, ref, opts=None, col_tol=COL_TOL, depth_rel=DEPTH_RE
     if hit.ndim == 3:
         hit = hit.any(0)
     cov = same & hit & ~amb_id     # grazing/rim/tie pixels: depth is ill-conditioned
+    out["depth_excess"] = 0.0
     if cov.any():
         rel = np.abs(depth[cov] - ref["depth"][cov]) / ref["depth"][cov]
         out["depth_rel_max"] = float(rel.max())
+        # per-pixel bound DEPTH_REL + DEPTH_GRAZE/|cos| (cos at the winner of
+        # each sample, the smallest over the samples)
+        jj, ii = np.nonzero(cov)
+        rid = ref["id"] if ref["id"].ndim == 3 else ref["id"][None]
+        cmin = np.full(jj.size, np.inf)
+        for k in range(rid.shape[0]):
+            sid = rid[k][jj, ii]
+            m = sid >= 0
+            if m.any():
+                _, _, nd, ok = oracle.surfel_eval(scene, cam, ii[m], jj[m], sid[m], opts)
+                c = np.where(ok != 0, np.abs(nd), 0.0)
+                cm = cmin[m]
+                cmin[m] = np.minimum(cm, c)
+        bound = depth_rel + DEPTH_GRAZE / np.maximum(cmin, 1e-30)
+        w = int(np.argmax(rel / bound))
+        out["depth_excess"] = float(rel[w] / bound[w])
+        out["depth_worst"] = dict(px=int(ii[w]), py=int(jj[w]), rel=float(rel[w]), cos=float(cmin[w]))
     else:
         out["depth_rel_max"] = 0.0
     out["depth_inf_ok"] = bool(np.all(np.isinf(depth[same & ~hit])))
@@ -52,5 +75,35 @@ def compare(scene, cam, gpu, ref, opts=None, col_tol=COL_TOL, depth_rel=DEPTH_RE
     out["masked_frac"] = float((amb_id | amb_col).mean())
     out["compared_px"] = int(ok.sum())
     out["pass"] = (out.get("id_mismatch_unmasked", 0) == 0 and out.get("id_invalid", 0) == 0 and
-                   out["depth_rel_max"] <= depth_rel and out["depth_inf_ok"] and out["col_max"] <= col_tol)
+                   out["depth_excess"] <= 1.0 and out["depth_inf_ok"] and out["col_max"] <= col_tol)
+    return out
+
+
+GEO_NORMAL_TOL = 2e-4   # abs, per component (unit normals in float32, alpha-weighted sums)
+GEO_DEPTH_REL = 2e-5    # relative (alpha-weighted depths accumulated in 2^-32 fixed point)
+
+
+def compare_geom(gpu, ref_geo, ref, col_tol=COL_TOL):
+    """Geometry maps (N_s, D_G, N_G, D_smooth, N_smooth) at pixels the oracle
+    did not flag (id or colour ambiguity): D_G, N_G to an absolute tolerance
+    scaled by W_G (their terms are alpha-weighted), D_smooth relative,
+    normals absolute."""
+    amb = ref_geo["amb"] != 0
+    ok = ~amb
+    out = {}
+    g = {k: gpu[k].detach().cpu().numpy().astype(np.float64) for k in ("ns", "dg", "ng", "dsmooth", "nsmooth")}
+    out["ns_max"] = float(np.abs(g["ns"] - ref_geo["ns"])[:, ok].max()) if ok.any() else 0.0
+    scale = np.maximum(1.0, ref["wg"])
+    dg_ref = ref_geo["dg"]
+    out["dg_max_rel"] = float((np.abs(g["dg"] - dg_ref) / (scale * np.maximum(1.0, np.abs(dg_ref))))[ok].max())
+    out["ng_max"] = float((np.abs(g["ng"] - ref_geo["ng"]) / scale)[:, ok].max())
+    fin = ok & np.isfinite(ref_geo["dsmooth"])
+    out["dsmooth_inf_ok"] = bool(np.array_equal(np.isinf(g["dsmooth"][ok]), np.isinf(ref_geo["dsmooth"][ok])))
+    out["dsmooth_max_rel"] = float((np.abs(g["dsmooth"][fin] - ref_geo["dsmooth"][fin]) /
+                                    ref_geo["dsmooth"][fin]).max()) if fin.any() else 0.0
+    out["nsmooth_max"] = float(np.abs(g["nsmooth"] - ref_geo["nsmooth"])[:, ok].max()) if ok.any() else 0.0
+    out["compared_px"] = int(ok.sum())
+    out["pass"] = (out["ns_max"] <= GEO_NORMAL_TOL and out["ng_max"] <= GEO_NORMAL_TOL and
+                   out["nsmooth_max"] <= GEO_NORMAL_TOL and out["dg_max_rel"] <= GEO_DEPTH_REL and
+                   out["dsmooth_max_rel"] <= GEO_DEPTH_REL and out["dsmooth_inf_ok"])
     return out

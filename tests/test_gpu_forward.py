@@ -1,4 +1,5 @@
 """GPU forward render vs the FP64 oracle, through the C ABI."""
+import json
 import math
 
 import numpy as np
@@ -28,7 +29,7 @@ def _render(R, scene, cam, opts=None, **kw):
 
 
 def _assert(res):
-    assert res["pass"], res
+    assert res["pass"], json.dumps(res, default=str)
 
 
 def test_parity_workload_128(R):

@@ -1,6 +1,7 @@
 """Mip-GES (Sec. 6.1) on the GPU vs the FP64 oracle: the 3D filter variance
 from training cameras, the filtered forward pass, its backward, the batch
 graph."""
+import json
 import math
 
 import numpy as np
@@ -27,7 +28,7 @@ def R():
 
 
 def _assert(res):
-    assert res["pass"], res
+    assert res["pass"], json.dumps(res, default=str)
 
 
 def _ring(n, W, H, r=2.8, fov=55.0):

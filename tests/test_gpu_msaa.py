@@ -1,5 +1,6 @@
 """4x multisampled surfel pass (Sec. 5) on the GPU vs the FP64 oracle: per
 sample ids, the resolved colour and depth, the backward, the batch graph."""
+import json
 import numpy as np
 import pytest
 
@@ -24,7 +25,7 @@ def R():
 
 
 def _assert(res):
-    assert res["pass"], res
+    assert res["pass"], json.dumps(res, default=str)
 
 
 def test_msaa_parity_workload_128(R):
