@@ -21,8 +21,13 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libges.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# --fmad=false: no implicit multiply-add contraction.  Without it the code
+# generator may fuse a*b + c differently in each kernel that inlines the same
+# set-up code (prep of the per-view path, of the batch graph, of the backward),
+# so their results could differ in the last bit; the hot loops call fmaf
+# explicitly and keep their FMAs.
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
-              "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
+              "--expt-relaxed-constexpr", "--fmad=false", "-I", INCLUDE, "-I", CSRC]
 
 
 def nvcc() -> str:
