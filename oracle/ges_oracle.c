@@ -71,6 +71,8 @@ typedef struct {
     int32_t filter;      /* 0: fixed EWA dilation Sigma2 + lowpass I (3DGS, basic GES);
                             1: Mip-GES screen filter: the same dilation with the opacity
                                scaled by sqrt(|Sigma2| / |Sigma2 + lowpass I|) (Sec. 6.1) */
+    double tol_disc_graze;   /* rim band at a fragment whose ray meets the disc at cosine c:
+                                tol_disc_rel (1 + tol_disc_graze / max(|c|, tol_graze)) */
 } ora_opts;
 
 enum { ORA_OK = 0, ORA_BAD_ARG = 1, ORA_BAD_QUAT = 2, ORA_NOMEM = 3 };
@@ -218,6 +220,16 @@ typedef struct {
 
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+/* Relative width of the disc-rim ambiguity band for a fragment whose ray
+   meets the disc plane at cosine nd.  The fragment's in-plane coordinates are
+   conditioned like its depth, z = (n.P)/(n.d), by 1/|cos|, so any float32
+   evaluation's rim decision is uncertain in a band that widens at grazing
+   incidence; below tol_graze the pixel is flagged as grazing anyway. */
+static double disc_band(const ora_opts *o, double nd)
+{
+    return o->tol_disc_rel * (1.0 + o->tol_disc_graze / fmax(fabs(nd), o->tol_graze));
+}
+
 /* Conservative pixel rectangle of the disc a^2 + b^2 <= r^2 of a planar frame
    (camera-space centre pc, axes tu, tv, scales s1, s2): the disc lies inside
    the rectangle pc +- r s1 tu +- r s2 tv; clip it to z >= znear, project the
@@ -279,7 +291,7 @@ static int surfel_setup(const ora_scene *S, const ora_camera *c, const ora_opts 
        z >= znear, project its vertices, pad by one pixel. */
     sf->x0 = 1; sf->x1 = 0; sf->y0 = 1; sf->y1 = 0;
     if (!sf->valid) return 1;
-    disc_rect(c, sf, sqrt(o->surfel_r2 * (1.0 + 2.0 * o->tol_disc_rel)));
+    disc_rect(c, sf, sqrt(o->surfel_r2 * (1.0 + 2.0 * o->tol_disc_rel * (1.0 + o->tol_disc_graze / o->tol_graze))));
     return 1;
 }
 
@@ -614,7 +626,7 @@ static void zbuffer_sample(const ora_scene *S, const ora_camera *c, const ora_op
         double z, rho, nd;
         if (!surfel_hit(sf, d, &z, &rho, &nd)) continue;
         if (!(z > c->znear)) continue;
-        if (fabs(rho - r2) <= o->tol_disc_rel * r2) zband = fmin(zband, z);
+        if (fabs(rho - r2) <= disc_band(o, nd) * r2) zband = fmin(zband, z);
         if (!(rho <= r2)) continue;
         if (fabs(z - c->znear) <= o->tol_depth_rel * fmax(1.0, c->znear)) *amb |= AMB_ID;
         if (z < z1 || (z == z1 && s < best)) {
@@ -625,7 +637,7 @@ static void zbuffer_sample(const ora_scene *S, const ora_camera *c, const ora_op
         }
     }
     if (second >= 0 && (z2 - z1) <= o->tol_depth_rel * z1) *amb |= AMB_ID;
-    if (best >= 0 && fabs(rho1 - r2) <= o->tol_disc_rel * r2) *amb |= AMB_ID;
+    if (best >= 0 && fabs(rho1 - r2) <= disc_band(o, nd1) * r2) *amb |= AMB_ID;
     if (best >= 0 && fabs(nd1) < o->tol_graze) *amb |= AMB_ID;
     if (zband < INFINITY && (best < 0 || zband <= z1 * (1.0 + o->tol_depth_rel))) *amb |= AMB_ID;
     *best_out = best;
@@ -880,11 +892,12 @@ int ora_surfel_eval(const ora_scene *S, const ora_camera *c, const ora_opts *o, 
    ids and valid are [samples, H, W])?  The exact answer
    is the lexicographic min of (z, index) over surfels whose fragment is inside
    its disc in front of the near plane; where fragments sit within the bands
-   (disc rim |rho - r2| <= tol_disc r2, depth gap <= tol_depth z) several
+   (disc rim |rho - r2| <= band r2 with the band of disc_band, depth gap
+   <= tol_depth z) several
    answers are correct.  A surfel s is acceptable iff its fragment is inside
    its disc up to the rim band and in front of the near plane up to the depth
    band, and no surfel clearly in front of it (z_t < z_s (1 - tol_depth)) is
-   clearly inside its own disc (rho_t < r2 (1 - tol_disc)).  -1 is acceptable
+   clearly inside its own disc (rho_t < r2 (1 - band)).  -1 is acceptable
    iff no surfel is clearly inside.  Grazing fragments (|cos| < tol_graze)
    count as inside up to the band, like rim fragments. */
 int ora_check_ids(const ora_scene *S, const ora_camera *c, const ora_opts *o, const int32_t *ids,
@@ -896,7 +909,7 @@ int ora_check_ids(const ora_scene *S, const ora_camera *c, const ora_opts *o, co
     if (st != ORA_OK) { prep_free(&P); return st; }
     const int W = c->width, H = c->height, nsamp = o->samples == 4 ? 4 : 1;
     const int64_t HW = (int64_t)W * H;
-    const double r2 = o->surfel_r2, td = o->tol_depth_rel, tr = o->tol_disc_rel;
+    const double r2 = o->surfel_r2, td = o->tol_depth_rel;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int jk = 0; jk < H * nsamp; ++jk) {
         const int j = jk % H, smp = jk / H;
@@ -911,7 +924,7 @@ int ora_check_ids(const ora_scene *S, const ora_camera *c, const ora_opts *o, co
                 if (s >= S->n_surfels || !P.sf[s].valid) { valid[pix] = 0; continue; }
                 double rho, nd;
                 if (!surfel_hit(&P.sf[s], d, &zs, &rho, &nd) || !(zs > c->znear * (1.0 - td)) ||
-                    !(rho <= r2 * (1.0 + tr) || fabs(nd) < o->tol_graze)) { valid[pix] = 0; continue; }
+                    !(rho <= r2 * (1.0 + disc_band(o, nd)) || fabs(nd) < o->tol_graze)) { valid[pix] = 0; continue; }
             }
             const int64_t cell = (int64_t)(j / ORA_CELL) * P.rs.cx + i / ORA_CELL;
             for (int64_t t = P.rs.off[cell]; t < P.rs.off[cell + 1] && ok; ++t) {
@@ -922,7 +935,7 @@ int ora_check_ids(const ora_scene *S, const ora_camera *c, const ora_opts *o, co
                 if (!surfel_hit(sf, d, &z, &rho, &nd)) continue;
                 if (!(z > c->znear * (1.0 + td))) continue;
                 if (!(z < zs * (1.0 - td))) continue;
-                if (rho < r2 * (1.0 - tr) && fabs(nd) >= o->tol_graze) ok = 0;
+                if (rho < r2 * (1.0 - disc_band(o, nd)) && fabs(nd) >= o->tol_graze) ok = 0;
             }
             valid[pix] = (uint8_t)ok;
         }
@@ -954,10 +967,10 @@ int ora_touching(const ora_scene *S, const ora_camera *c, const ora_opts *o, con
                 if (!flag[(int64_t)j * W + i]) continue;
                 const int nsamp = o->samples == 4 ? 4 : 1;
                 for (int k = 0; k < nsamp && !s_touch[s]; ++k) {
-                    double d[3], z, rho;
+                    double d[3], z, rho, nd;
                     sample_ray(c, nsamp, i, j, k, d);
-                    if (surfel_hit(sf, d, &z, &rho, NULL) && z > c->znear &&
-                        rho <= o->surfel_r2 * (1.0 + o->tol_disc_rel)) s_touch[s] = 1;
+                    if (surfel_hit(sf, d, &z, &rho, &nd) && z > c->znear &&
+                        rho <= o->surfel_r2 * (1.0 + disc_band(o, nd))) s_touch[s] = 1;
                 }
                 if (s_touch[s]) break;
             }

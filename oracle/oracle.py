@@ -27,7 +27,7 @@ _lib = None
 DEFAULT_OPTS = dict(eps_mode=0, eps_value=0.1, eps_factor=5.0, lowpass=0.3,
                     alpha_min=1.0 / 255.0, surfel_r2=2.0 * math.log(255.0), mode=0,
                     tol_depth_rel=1e-6, tol_disc_rel=1e-5, tol_graze=1e-3, tol_alpha=1e-5,
-                    tol_gdepth_rel=2e-6, samples=1, filter=0)
+                    tol_gdepth_rel=2e-6, samples=1, filter=0, tol_disc_graze=0.1)
 
 
 class _Scene(C.Structure):
@@ -48,7 +48,7 @@ class _Opts(C.Structure):
                 ("lowpass", C.c_double), ("alpha_min", C.c_double), ("surfel_r2", C.c_double),
                 ("mode", C.c_int32), ("tol_depth_rel", C.c_double), ("tol_disc_rel", C.c_double),
                 ("tol_graze", C.c_double), ("tol_alpha", C.c_double), ("tol_gdepth_rel", C.c_double),
-                ("samples", C.c_int32), ("filter", C.c_int32)]
+                ("samples", C.c_int32), ("filter", C.c_int32), ("tol_disc_graze", C.c_double)]
 
 
 def build(force: bool = False) -> str:
