@@ -1253,6 +1253,330 @@ int ora_backward(const ora_scene *S, const ora_camera *c, const ora_opts *o, int
     return ORA_OK;
 }
 
+/* ------------------------------------------------------------------------ */
+/* translucent surfels (Sec. 4.1, Eq. 6-7): the differentiable surfel render  */
+/* of the coarse stage.                                                        */
+/* alpha_i = min(1, w_i G(a, b)), G = exp(-(a^2 + b^2)/2) at the ray-plane hit */
+/* (a, b in scale units), clamped to 0 where min(alpha_i, G) < 1/255.  The     */
+/* rasterisation follows 2DGS: front-to-back alpha blending in the order of    */
+/* the surfel centres' camera depths (ties: lower index first), stopping once  */
+/* the transmittance falls below 1e-4 after a blend; C += T bg at the end.     */
+/* With front_first (the w_i >= 30 regime), each pixel blends its frontmost    */
+/* covering surfel (least depth at the pixel, ties: lower index) first and the */
+/* others in the sorted order.                                                 */
+
+#define ORA_T_STOP 1e-4
+
+typedef struct { int64_t s; double zc, z, a, G, rho; } tcontrib;
+
+static int tcontrib_cmp(const void *pa, const void *pb)
+{
+    const tcontrib *a = pa, *b = pb;
+    if (a->zc < b->zc) return -1;
+    if (a->zc > b->zc) return 1;
+    return (a->s > b->s) - (a->s < b->s);
+}
+
+/* Contributors of pixel (i, j) in blending order; returns their number, or -1
+   when out of memory.  *list is grown with realloc.  amb gets AMB_COLOR where
+   a decision sits within the bands (cut-off, blend order, front choice, near
+   plane, grazing). */
+static int64_t tcollect(const ora_scene *S, const ora_camera *c, const ora_opts *o, const prep_t *P, int culled,
+                        const double *w, int front_first, int i, int j, tcontrib **list, int64_t *cap,
+                        uint8_t *amb)
+{
+    double d[3];
+    pixel_ray(c, i, j, d);
+    const double amin = o->alpha_min;
+    int64_t n = 0, lo = 0, hi = S->n_surfels;
+    if (culled) {
+        const int64_t cell = (int64_t)(j / ORA_CELL) * P->rs.cx + i / ORA_CELL;
+        lo = P->rs.off[cell]; hi = P->rs.off[cell + 1];
+    }
+    for (int64_t t = lo; t < hi; ++t) {
+        const int64_t s = culled ? P->rs.idx[t] : t;
+        const surf_t *sf = &P->sf[s];
+        if (!sf->valid) continue;
+        if (culled && (i < sf->x0 || i > sf->x1 || j < sf->y0 || j > sf->y1)) continue;
+        double z, rho, nd;
+        if (!surfel_hit(sf, d, &z, &rho, &nd)) continue;
+        if (!(z > c->znear)) continue;
+        const double G = exp(-0.5 * rho), a = fmin(1.0, w[s] * G);
+        const double m = fmin(a, G);
+        if (fabs(m - amin) <= o->tol_alpha) *amb |= AMB_COLOR;
+        if (!(m >= amin)) continue;
+        if (fabs(nd) < o->tol_graze || fabs(z - c->znear) <= o->tol_depth_rel * fmax(1.0, c->znear)) *amb |= AMB_COLOR;
+        if (n == *cap) {
+            int64_t nc = *cap ? 2 * *cap : 64;
+            tcontrib *nl = realloc(*list, sizeof(tcontrib) * (size_t)nc);
+            if (!nl) return -1;
+            *list = nl; *cap = nc;
+        }
+        (*list)[n++] = (tcontrib){s, sf->pc[2], z, a, G, rho};
+    }
+    qsort(*list, (size_t)n, sizeof(tcontrib), tcontrib_cmp);
+    for (int64_t k = 1; k < n; ++k)
+        if ((*list)[k].zc - (*list)[k - 1].zc <= o->tol_depth_rel * fabs((*list)[k].zc)) *amb |= AMB_COLOR;
+    if (front_first && n > 1) {
+        int64_t f = 0;
+        for (int64_t k = 1; k < n; ++k)
+            if ((*list)[k].z < (*list)[f].z || ((*list)[k].z == (*list)[f].z && (*list)[k].s < (*list)[f].s)) f = k;
+        for (int64_t k = 0; k < n; ++k)
+            if (k != f && (*list)[k].z - (*list)[f].z <= o->tol_depth_rel * (*list)[f].z) *amb |= AMB_COLOR;
+        tcontrib fr = (*list)[f];
+        memmove(*list + 1, *list, sizeof(tcontrib) * (size_t)f);
+        (*list)[0] = fr;
+    }
+    return n;
+}
+
+int ora_render_translucent(const ora_scene *S, const ora_camera *c, const ora_opts *o, const double *w,
+                           int front_first, int culled, int nthreads, double *rgb, double *T_out,
+                           int32_t *front, int32_t *nblend, uint8_t *amb)
+{
+    if (!check_args(S, c, o) || !w) return ORA_BAD_ARG;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    prep_t P;
+    int st = prepare(S, c, o, culled, &P);
+    if (st != ORA_OK) { prep_free(&P); return st; }
+    const int W = c->width, H = c->height;
+    const int64_t HW = (int64_t)W * H;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(|:bad)
+    for (int j = 0; j < H; ++j) {
+        tcontrib *list = NULL;
+        int64_t cap = 0;
+        for (int i = 0; i < W; ++i) {
+            const int64_t pix = (int64_t)j * W + i;
+            uint8_t a8 = 0;
+            const int64_t n = tcollect(S, c, o, &P, culled, w, front_first, i, j, &list, &cap, &a8);
+            if (n < 0) { bad = 1; break; }
+            double C[3] = {0, 0, 0}, T = 1.0;
+            int32_t nb = 0;
+            for (int64_t k = 0; k < n; ++k) {
+                const tcontrib *e = &list[k];
+                for (int ch = 0; ch < 3; ++ch) C[ch] += P.sf[e->s].rgb[ch] * e->a * T;
+                T *= 1.0 - e->a;
+                ++nb;
+                if (fabs(T - ORA_T_STOP) <= 1e-6 * ORA_T_STOP) a8 |= AMB_COLOR;
+                if (T < ORA_T_STOP) break;
+            }
+            for (int ch = 0; ch < 3; ++ch) rgb[ch * HW + pix] = C[ch] + T * c->bg[ch];
+            T_out[pix] = T;
+            /* the frontmost contributor (least depth at the pixel) */
+            int64_t f = -1;
+            double fz = INFINITY;
+            for (int64_t k = 0; k < n; ++k)
+                if (list[k].z < fz || (list[k].z == fz && list[k].s < f)) { f = list[k].s; fz = list[k].z; }
+            front[pix] = (int32_t)f;
+            nblend[pix] = nb;
+            amb[pix] = a8;
+        }
+        free(list);
+    }
+    prep_free(&P);
+    return bad ? ORA_NOMEM : ORA_OK;
+}
+
+/* Covering score (Sec. 4.1, pruning): the number of pixels at which each
+   surfel is the frontmost contributor of the translucent render. */
+int ora_covering_counts(const ora_scene *S, const ora_camera *c, const ora_opts *o, const double *w,
+                        int64_t *counts)
+{
+    if (!check_args(S, c, o) || !w) return ORA_BAD_ARG;
+    const int64_t HW = (int64_t)c->width * c->height;
+    double *rgb = malloc(sizeof(double) * 3 * (size_t)HW), *T = malloc(sizeof(double) * (size_t)HW);
+    int32_t *fr = malloc(sizeof(int32_t) * (size_t)HW), *nb = malloc(sizeof(int32_t) * (size_t)HW);
+    uint8_t *amb = malloc((size_t)HW);
+    int st = ORA_NOMEM;
+    if (rgb && T && fr && nb && amb) st = ora_render_translucent(S, c, o, w, 1, 1, 0, rgb, T, fr, nb, amb);
+    if (st == ORA_OK) {
+        memset(counts, 0, sizeof(int64_t) * (size_t)(S->n_surfels > 0 ? S->n_surfels : 0));
+        for (int64_t p = 0; p < HW; ++p)
+            if (fr[p] >= 0) ++counts[fr[p]];
+    }
+    free(rgb); free(T); free(fr); free(nb); free(amb);
+    return st;
+}
+
+/* Gradients of L = sum(dL_drgb * C) of the translucent render with respect to
+   surfel position, rotation (through the normalisation), scales, w and SH.
+   With T_i the transmittance before contributor i, S_{i+1} the colour seen
+   behind it (S = c a + (1 - a) S, ending in bg): dC/dc_i = a_i T_i,
+   dC/da_i = T_i (c_i - S_{i+1}); where w G < 1: da/dw = G, da/drho = -w G / 2,
+   rho = a^2 + b^2; the hit coordinate a = ((z d - P).U)/s1 with
+   z = (N.P)/(N.d) gives da/dP = ((U.d)/(N.d) N - U)/s1, da/dU = (z d - P)/s1,
+   da/dN = (U.d)(P - z d)/((N.d) s1), da/ds1 = -a/s1 (b likewise with V, s2).
+   The cut-off, the order and the early stop are piecewise constant. */
+int ora_backward_translucent(const ora_scene *S, const ora_camera *c, const ora_opts *o, const double *w,
+                             int front_first, int nthreads, const double *dL_drgb, double *gs_pos,
+                             double *gs_rot, double *gs_scale, double *gs_w, double *gs_sh)
+{
+    if (!check_args(S, c, o) || !w) return ORA_BAD_ARG;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    prep_t P;
+    int st = prepare(S, c, o, 1, &P);
+    if (st != ORA_OK) { prep_free(&P); return st; }
+    const int W = c->width, H = c->height;
+    const int64_t HW = (int64_t)W * H, N = S->n_surfels;
+    const int K = (S->sh_degree + 1) * (S->sh_degree + 1);
+    /* per surfel, camera space: gP(3) gU(3) gV(3) gN(3) gs1 gs2 gw gc(3) = 18 */
+    double *acc = calloc((size_t)(N > 0 ? N : 1) * 18, sizeof(double));
+    if (!acc) { prep_free(&P); return ORA_NOMEM; }
+    int bad = 0;
+    /* rows are summed serially per row block to keep the result deterministic */
+    for (int j = 0; j < H && !bad; ++j) {
+        tcontrib *list = NULL;
+        int64_t cap = 0;
+        for (int i = 0; i < W; ++i) {
+            const int64_t pix = (int64_t)j * W + i;
+            uint8_t a8 = 0;
+            const int64_t n = tcollect(S, c, o, &P, 1, w, front_first, i, j, &list, &cap, &a8);
+            if (n < 0) { bad = 1; break; }
+            int64_t nb = 0;
+            double T = 1.0;
+            for (int64_t k = 0; k < n; ++k) {
+                T *= 1.0 - list[k].a;
+                ++nb;
+                if (T < ORA_T_STOP) break;
+            }
+            const double g[3] = {dL_drgb[pix], dL_drgb[HW + pix], dL_drgb[2 * HW + pix]};
+            /* transmittances before each blended contributor */
+            double *Tb = malloc(sizeof(double) * (size_t)(nb > 0 ? nb : 1));
+            if (!Tb) { bad = 1; break; }
+            T = 1.0;
+            for (int64_t k = 0; k < nb; ++k) { Tb[k] = T; T *= 1.0 - list[k].a; }
+            double Sb[3] = {c->bg[0], c->bg[1], c->bg[2]};
+            double d[3];
+            pixel_ray(c, i, j, d);
+            for (int64_t k = nb - 1; k >= 0; --k) {
+                const tcontrib *e = &list[k];
+                const surf_t *sf = &P.sf[e->s];
+                double *A = acc + 18 * e->s;
+                double dLda = 0.0;
+                for (int ch = 0; ch < 3; ++ch) {
+                    A[15 + ch] += e->a * Tb[k] * g[ch];
+                    dLda += Tb[k] * (sf->rgb[ch] - Sb[ch]) * g[ch];
+                }
+                for (int ch = 0; ch < 3; ++ch) Sb[ch] = sf->rgb[ch] * e->a + (1.0 - e->a) * Sb[ch];
+                if (!(w[e->s] * e->G < 1.0)) continue;        /* alpha clamped at 1: no gradient */
+                A[14] += dLda * e->G;
+                const double dLdrho = dLda * (-0.5 * w[e->s] * e->G);
+                /* local coordinates and their derivatives */
+                const double Nd = dot3(sf->n, d), Ud = dot3(sf->tu, d), Vd = dot3(sf->tv, d);
+                const double z = e->z;
+                double X[3];
+                for (int q = 0; q < 3; ++q) X[q] = z * d[q] - sf->pc[q];
+                const double a = dot3(X, sf->tu) / sf->s1, b = dot3(X, sf->tv) / sf->s2;
+                const double dLa = dLdrho * 2.0 * a, dLb = dLdrho * 2.0 * b;
+                for (int q = 0; q < 3; ++q) {
+                    A[q] += dLa * ((Ud / Nd) * sf->n[q] - sf->tu[q]) / sf->s1 +
+                            dLb * ((Vd / Nd) * sf->n[q] - sf->tv[q]) / sf->s2;
+                    A[3 + q] += dLa * X[q] / sf->s1;
+                    A[6 + q] += dLb * X[q] / sf->s2;
+                    A[9 + q] += dLa * Ud * (-X[q]) / (Nd * sf->s1) + dLb * Vd * (-X[q]) / (Nd * sf->s2);
+                }
+                A[12] += dLa * (-a / sf->s1);
+                A[13] += dLb * (-b / sf->s2);
+            }
+            free(Tb);
+        }
+        free(list);
+    }
+    if (bad) { free(acc); prep_free(&P); return ORA_NOMEM; }
+    double Rc[9];
+    cam_rot(c, Rc);
+    for (int64_t s = 0; s < N; ++s) {
+        const double *A = acc + 18 * s;
+        double *gp = gs_pos + 3 * s;
+        double R[9], qn[4], qnorm;
+        for (int q = 0; q < 3; ++q) gp[q] = Rc[q] * A[0] + Rc[3 + q] * A[1] + Rc[6 + q] * A[2];
+        for (int q = 0; q < 4; ++q) gs_rot[4 * s + q] = 0.0;
+        gs_scale[2 * s] = A[12]; gs_scale[2 * s + 1] = A[13];
+        gs_w[s] = A[14];
+        memset(gs_sh + (int64_t)3 * K * s, 0, sizeof(double) * 3 * (size_t)K);
+        const surf_t *sf = &P.sf[s];
+        if (!sf->valid || !quat_rot(S->s_rot + 4 * s, R, qn, &qnorm)) continue;
+        /* U = Rc R e_x, V = Rc R e_y, N = Rc R e_z:  dL/dR[:,k] = Rc^T g */
+        double GR[9];
+        for (int q = 0; q < 3; ++q) {
+            GR[3 * q] = Rc[q] * A[3] + Rc[3 + q] * A[4] + Rc[6 + q] * A[5];
+            GR[3 * q + 1] = Rc[q] * A[6] + Rc[3 + q] * A[7] + Rc[6 + q] * A[8];
+            GR[3 * q + 2] = Rc[q] * A[9] + Rc[3 + q] * A[10] + Rc[6 + q] * A[11];
+        }
+        double wq = qn[0], qx = qn[1], qy = qn[2], qz = qn[3];
+        double dR[4][9] = {
+            {0, -2*qz, 2*qy, 2*qz, 0, -2*qx, -2*qy, 2*qx, 0},
+            {0, 2*qy, 2*qz, 2*qy, -4*qx, -2*wq, 2*qz, 2*wq, -4*qx},
+            {-4*qy, 2*qx, 2*wq, 2*qx, 0, 2*qz, -2*wq, 2*qz, -4*qy},
+            {-4*qz, -2*wq, 2*qx, 2*wq, -4*qz, 2*qy, 2*qx, 2*qy, 0},
+        };
+        double gqn[4];
+        for (int a = 0; a < 4; ++a) {
+            double acc2 = 0.0;
+            for (int k = 0; k < 9; ++k) acc2 += GR[k] * dR[a][k];
+            gqn[a] = acc2;
+        }
+        double pr = gqn[0]*wq + gqn[1]*qx + gqn[2]*qy + gqn[3]*qz;
+        for (int a = 0; a < 4; ++a) gs_rot[4 * s + a] = (gqn[a] - pr * qn[a]) / qnorm;
+        /* colour -> SH and position (through the view direction) */
+        double ocam[3], v[3];
+        cam_centre(c, ocam);
+        for (int q = 0; q < 3; ++q) v[q] = ocam[q] - S->s_pos[3 * s + q];
+        sh_backward(S->sh_degree, S->s_sh + (int64_t)3 * K * s, sf->dir, sqrt(dot3(v, v)), sf->raw, A + 15,
+                    gs_sh + (int64_t)3 * K * s, gp);
+    }
+    free(acc);
+    prep_free(&P);
+    return ORA_OK;
+}
+
+/* Contribution score of each Gaussian (Sec. 4.2, Eq. 9), for pruning:
+   s_i = max over the pixels where Gaussian i contributes (clamp and depth
+   test passed) of c_max alpha_i / (W_s + W_G), c_max its largest colour
+   channel, W_s = 1; 0 where it contributes nowhere. */
+int ora_contribution(const ora_scene *S, const ora_camera *c, const ora_opts *o, double *score)
+{
+    if (!check_args(S, c, o)) return ORA_BAD_ARG;
+    const int W = c->width, H = c->height;
+    const int64_t HW = (int64_t)W * H, M = S->n_gaussians;
+    double *rgb = malloc(sizeof(double) * 3 * (size_t)HW), *Ds = malloc(sizeof(double) * (size_t)HW);
+    double *WG = malloc(sizeof(double) * (size_t)HW);
+    int32_t *sid = malloc(sizeof(int32_t) * (size_t)HW * (o->samples == 4 ? 4 : 1));
+    uint8_t *amb = malloc((size_t)HW);
+    if (!rgb || !Ds || !WG || !sid || !amb) { free(rgb); free(Ds); free(WG); free(sid); free(amb); return ORA_NOMEM; }
+    int st = ora_render(S, c, o, 1, 0, rgb, Ds, sid, WG, amb, NULL);
+    prep_t P;
+    if (st == ORA_OK) st = prepare(S, c, o, 1, &P);
+    else memset(&P, 0, sizeof P);
+    if (st == ORA_OK) {
+#pragma omp parallel for schedule(dynamic, 64)
+        for (int64_t k = 0; k < M; ++k) {
+            const gauss_t *g = &P.gs[k];
+            double best = 0.0;
+            if (g->valid) {
+                const double cm = fmax(g->rgb[0], fmax(g->rgb[1], g->rgb[2]));
+                for (int j = g->y0; j <= g->y1; ++j)
+                    for (int i = g->x0; i <= g->x1; ++i) {
+                        const int64_t pix = (int64_t)j * W + i;
+                        double gd;
+                        const double a = gauss_eval(c, g, i, j, &gd, NULL);
+                        if (!(a >= o->alpha_min) || !(gd < Ds[pix] + g->eps)) continue;
+                        best = fmax(best, cm * a / (1.0 + WG[pix]));
+                    }
+            }
+            score[k] = best;
+        }
+    }
+    prep_free(&P);
+    free(rgb); free(Ds); free(WG); free(sid); free(amb);
+    return st;
+}
+
 /* Mip-GES 3D filter variance per Gaussian (Sec. 6.1, Mip-Splatting's world-space
    filter): v_i = s3d / nu_i^2 with nu_i the highest sampling rate at which the
    training cameras see the centre, nu = max(fx, fy) / z over the cameras whose

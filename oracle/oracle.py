@@ -81,6 +81,12 @@ def load():
         lib.ora_count_fragments.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_void_p, C.c_void_p]
         lib.ora_filter3d.argtypes = [P(_Scene), C.c_void_p, C.c_int, C.c_double, C.c_void_p]
         lib.ora_render_geom.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_int, C.c_int] + [C.c_void_p] * 6
+        lib.ora_render_translucent.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_void_p, C.c_int, C.c_int,
+                                               C.c_int] + [C.c_void_p] * 5
+        lib.ora_backward_translucent.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_void_p, C.c_int, C.c_int,
+                                                 C.c_void_p] + [C.c_void_p] * 5
+        lib.ora_covering_counts.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_void_p, C.c_void_p]
+        lib.ora_contribution.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_void_p]
         _lib = lib
     return _lib
 
@@ -149,6 +155,62 @@ def render_geom(scene, cam, opts=None, culled: bool = True, nthreads: int = 0):
     st = lib.ora_render_geom(C.byref(pin.s), C.byref(pin.c), C.byref(pin.o), int(culled), int(nthreads),
                              *[out[k].ctypes.data for k in ("ns", "dg", "ng", "dsmooth", "nsmooth", "amb")])
     _check(st, "render_geom")
+    return out
+
+
+def render_translucent(scene, cam, w, front_first: bool = True, opts=None, culled: bool = True, nthreads: int = 0):
+    """FP64 translucent-surfel render (Sec. 4.1, Eq. 6-7) with the opacity
+    modulating parameters w [N]: rgb [3,H,W], T [H,W] (final transmittance),
+    front [H,W] (frontmost contributing surfel, -1), nblend [H,W] (surfels
+    blended), amb [H,W] (bit 2: a decision within the bands)."""
+    lib = load()
+    pin = _Pinned(scene, cam, opts)
+    ww = _d(w)
+    assert ww.shape == (scene.n_surfels,)
+    H, W = cam.height, cam.width
+    out = dict(rgb=np.empty((3, H, W)), T=np.empty((H, W)), front=np.empty((H, W), np.int32),
+               nblend=np.empty((H, W), np.int32), amb=np.empty((H, W), np.uint8))
+    st = lib.ora_render_translucent(C.byref(pin.s), C.byref(pin.c), C.byref(pin.o), ww.ctypes.data, int(front_first),
+                                    int(culled), int(nthreads),
+                                    *[out[k].ctypes.data for k in ("rgb", "T", "front", "nblend", "amb")])
+    _check(st, "render_translucent")
+    return out
+
+
+def backward_translucent(scene, cam, w, dL_drgb, front_first: bool = True, opts=None, nthreads: int = 0):
+    """Analytic FP64 gradients of sum(dL_drgb * C) of the translucent render:
+    s_pos [N,3], s_rot [N,4], s_scale [N,2], s_w [N], s_sh [N,K,3]."""
+    lib = load()
+    pin = _Pinned(scene, cam, opts)
+    ww = _d(w)
+    g = _d(dL_drgb)
+    N, K = scene.n_surfels, (scene.sh_degree + 1) ** 2
+    out = dict(s_pos=np.empty((N, 3)), s_rot=np.empty((N, 4)), s_scale=np.empty((N, 2)), s_w=np.empty((N,)),
+               s_sh=np.empty((N, K, 3)))
+    st = lib.ora_backward_translucent(C.byref(pin.s), C.byref(pin.c), C.byref(pin.o), ww.ctypes.data,
+                                      int(front_first), int(nthreads), g.ctypes.data,
+                                      *[out[k].ctypes.data for k in ("s_pos", "s_rot", "s_scale", "s_w", "s_sh")])
+    _check(st, "backward_translucent")
+    return out
+
+
+def covering_counts(scene, cam, w, opts=None):
+    """Pixels at which each surfel is the frontmost contributor (Sec. 4.1)."""
+    lib = load()
+    pin = _Pinned(scene, cam, opts)
+    ww = _d(w)
+    out = np.empty(scene.n_surfels, np.int64)
+    _check(lib.ora_covering_counts(C.byref(pin.s), C.byref(pin.c), C.byref(pin.o), ww.ctypes.data, out.ctypes.data),
+           "covering_counts")
+    return out
+
+
+def contribution(scene, cam, opts=None):
+    """Contribution score of each Gaussian (Sec. 4.2, Eq. 9)."""
+    lib = load()
+    pin = _Pinned(scene, cam, opts)
+    out = np.empty(scene.n_gaussians)
+    _check(lib.ora_contribution(C.byref(pin.s), C.byref(pin.c), C.byref(pin.o), out.ctypes.data), "contribution")
     return out
 
 
