@@ -201,6 +201,54 @@ GES_API ges_status ges_scene_update(ges_scene *scene, const ges_scene_desc *desc
 GES_API ges_status ges_compute_filter3d(ges_scene *scene, const ges_camera *cams, int32_t n_cams, float s3d,
                                         float *out_var);
 
+/* Translucent-surfel render of the coarse stage (Sec. 4.1, Eq. 6-7): surfel i
+ * has opacity alpha = min(1, w[i] G(a, b)), G = exp(-(a^2 + b^2)/2) at the
+ * ray-plane hit (a, b in scale units), zero where min(alpha, G) < alpha_min;
+ * surfels are alpha-blended front to back in the order of their centres'
+ * camera depths (ties: lower index), the pixel's frontmost contributor (least
+ * depth at the pixel) first when front_first != 0 (the w >= 30 regime), and
+ * blending stops once the transmittance falls below 1e-4 after a blend;
+ * C = sum c alpha T + T bg.  Gaussians are not rendered.  w: DEVICE float [N],
+ * w >= 0 (0: never contributes).  Outputs (DEVICE): out_rgb [3,H,W]; out_T,
+ * out_Tlast [H,W] (final transmittance, transmittance before the last blended
+ * surfel), out_front, out_last [H,W] int32 (frontmost contributor or -1; list
+ * position after the last blended surfel), all needed by the backward and
+ * each may otherwise be NULL; out_cover [N] int32 or NULL: set to the number
+ * of pixels where each surfel is the frontmost contributor (the covering
+ * score of Sec. 4.1 for this view).  Needs samples = 1 and surfel_r2 >=
+ * 2 ln(1/alpha_min) (GES_ERR_INVALID_ARG otherwise). */
+GES_API ges_status ges_render_translucent(ges_scene *scene, const ges_camera *cam, const ges_render_opts *opts,
+                                          const float *w, int32_t front_first, float *out_rgb, float *out_T,
+                                          int32_t *out_front, int32_t *out_last, float *out_Tlast,
+                                          int32_t *out_cover);
+
+/* Gradient outputs of the translucent backward (DEVICE, float32, overwritten):
+ * s_pos [N,3], s_rot [N,4], s_scale [N,2], s_w [N], s_sh [N,K,3]; any may be NULL. */
+typedef struct {
+    float *s_pos, *s_rot, *s_scale, *s_w, *s_sh;
+} ges_tgrads;
+
+/* Gradients of L = sum(dL_drgb * C) of ges_render_translucent with respect to
+ * surfel position, rotation (through the normalisation), scales, w and SH;
+ * out_T, out_front, out_last, out_Tlast are that call's outputs for the same
+ * scene arrays, camera, options, w and front_first.  The cut-off, the order
+ * and the early stop pass no gradient.  Deterministic: per-surfel sums are
+ * accumulated in 64-bit fixed point scaled by the largest |dL_drgb|. */
+GES_API ges_status ges_render_translucent_backward(ges_scene *scene, const ges_camera *cam,
+                                                   const ges_render_opts *opts, const float *w, int32_t front_first,
+                                                   const float *dL_drgb, const float *out_T, const int32_t *out_front,
+                                                   const int32_t *out_last, const float *out_Tlast,
+                                                   const ges_tgrads *grads);
+
+/* Contribution score of each Gaussian (Sec. 4.2, Eq. 9), for pruning:
+ * out_score [M] (DEVICE) = max over the pixels where the Gaussian contributes
+ * (1/255 clamp and depth test passed) of c_max alpha / (W_s + W_G), c_max its
+ * largest colour channel, W_s = 1; 0 where it contributes nowhere.  out_depth
+ * and aux are D_s and W_G of a ges_render_ex call with the same scene arrays,
+ * camera and options (samples = 1). */
+GES_API ges_status ges_contribution_scores(ges_scene *scene, const ges_camera *cam, const ges_render_opts *opts,
+                                           const float *out_depth, const float *aux, float *out_score);
+
 /* Release the scene and its scratch (synchronises its stream first).
  * NULL is accepted and ignored. */
 GES_API ges_status ges_destroy_scene(ges_scene *scene);

@@ -81,6 +81,7 @@ struct ges_scene {
     DevBuf status;                 // ST_WORDS per view slot
     DevBuf filt;                   // ges_compute_filter3d: cameras + one scratch word
     DevBuf g_aux;                  // Gaussian side data (2D Gaussians, geometry maps)
+    DevBuf t_side, t_keys, t_acc;  // translucent render: surfel frames, sort keys, gradient sums
     unsigned *status_host = nullptr;
     int status_slots = 0;
     int64_t tiles_cap = 0;
@@ -415,7 +416,7 @@ ges_status ges_destroy_scene(ges_scene *s)
     cudaStreamSynchronize(s->stream);
     DevBuf *bufs[] = {&s->s_rec, &s->s_rgb, &s->g_rec, &s->s_vis, &s->g_vis, &s->s_cnt, &s->g_cnt, &s->s_off,
                       &s->g_off, &s->s_cur, &s->g_cur, &s->s_list, &s->g_list, &s->hist, &s->base,
-                      &s->vcount, &s->status, &s->filt, &s->g_aux};
+                      &s->vcount, &s->status, &s->filt, &s->g_aux, &s->t_side, &s->t_keys, &s->t_acc};
     for (DevBuf *b : bufs) b->release();
     if (s->status_host) cudaFreeHost(s->status_host);
     for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
@@ -565,6 +566,118 @@ ges_status ges_compute_filter3d(ges_scene *s, const ges_camera *cams, int32_t n_
     GES_CUDA(cudaMemcpyAsync(base, C.data(), cam_bytes, cudaMemcpyHostToDevice, s->stream));
     cudaError_t e = launch_filter3d(s->view, (const CamParams *)base, n_cams, s3d, out_var,
                                     (unsigned *)(base + word_at), s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    GES_CUDA(cudaStreamSynchronize(s->stream));
+    return GES_OK;
+}
+
+namespace {
+// scratch and checks shared by the translucent calls
+ges_status translucent_setup(ges_scene *s, const ges_camera *cam, const ges_render_opts *opts, const float *w,
+                             CamParams &C, OptParams &O, ViewScratch &X)
+{
+    if (!s) return fail(GES_ERR_INVALID_ARG, "scene is NULL");
+    if (!w && s->desc.n_surfels > 0) return fail(GES_ERR_INVALID_ARG, "w is NULL");
+    ges_status r = make_cam(cam, C);
+    if (r != GES_OK) return r;
+    if ((r = make_opts(opts, O)) != GES_OK) return r;
+    // the records' disc must hold the whole support G >= alpha_min
+    if (O.surfel_r2 < -2.f * logf(O.alpha_min) * (1.f - 1e-6f))
+        return fail(GES_ERR_INVALID_ARG, "the translucent render needs surfel_r2 >= 2 ln(1/alpha_min)");
+    if (O.samples != 1) return fail(GES_ERR_INVALID_ARG, "the translucent render samples pixel centres only");
+    const int64_t N = std::max<int64_t>(s->desc.n_surfels, 1);
+    if ((r = ensure_scratch(s, (int64_t)C.tiles_x * C.tiles_y, 1, s->stream)) != GES_OK) return r;
+    cudaError_t e;
+    if ((e = s->t_side.ensure((size_t)N * 64)) || (e = s->t_keys.ensure((size_t)s->s_cap * 8)))
+        return cuda_fail(e, "scratch allocation (translucent)");
+    X = scratch_of(s, 0);
+    X.s_tside = (float4 *)s->t_side.p;
+    return GES_OK;
+}
+
+// status check after a translucent launch; true when the lists overflowed (grown, retry)
+ges_status translucent_status(ges_scene *s, bool &retry)
+{
+    retry = false;
+    GES_CUDA(cudaMemcpyAsync(s->status_host, s->status.p, ST_WORDS * 4, cudaMemcpyDeviceToHost, s->stream));
+    GES_CUDA(cudaStreamSynchronize(s->stream));
+    const unsigned *w = s->status_host;
+    if (w[ST_FLAGS] & FLAG_BADQ) return fail(GES_ERR_INVALID_ARG, "a rotation quaternion has zero norm or is not finite");
+    if (w[ST_FLAGS] & FLAG_SOVF) {
+        s->s_cap = std::max<int64_t>(s->s_cap * 2, (int64_t)(w[ST_SPAIRS] * 1.25) + 1024);
+        retry = true;
+    }
+    return GES_OK;
+}
+}  // namespace
+
+ges_status ges_render_translucent(ges_scene *s, const ges_camera *cam, const ges_render_opts *opts, const float *w,
+                                  int32_t front_first, float *out_rgb, float *out_T, int32_t *out_front,
+                                  int32_t *out_last, float *out_Tlast, int32_t *out_cover)
+{
+    if (!out_rgb) return fail(GES_ERR_INVALID_ARG, "out_rgb is NULL");
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        CamParams C;
+        OptParams O;
+        ViewScratch X;
+        ges_status r = translucent_setup(s, cam, opts, w, C, O, X);
+        if (r != GES_OK) return r;
+        GES_CUDA(cudaMemsetAsync(X.status, 0, ST_WORDS * 4, s->stream));
+        if (out_cover && s->desc.n_surfels > 0)
+            GES_CUDA(cudaMemsetAsync(out_cover, 0, sizeof(int32_t) * (size_t)s->desc.n_surfels, s->stream));
+        cudaError_t e = launch_translucent(s->view, C, O, X, w, front_first != 0, (unsigned long long *)s->t_keys.p,
+                                           out_rgb, out_T, out_front, out_last, out_Tlast, out_cover, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+        bool retry;
+        if ((r = translucent_status(s, retry)) != GES_OK) return r;
+        if (!retry) return GES_OK;
+    }
+    return fail(GES_ERR_INTERNAL, "tile lists kept overflowing after growing them");
+}
+
+ges_status ges_render_translucent_backward(ges_scene *s, const ges_camera *cam, const ges_render_opts *opts,
+                                           const float *w, int32_t front_first, const float *dL_drgb,
+                                           const float *out_T, const int32_t *out_front, const int32_t *out_last,
+                                           const float *out_Tlast, const ges_tgrads *grads)
+{
+    if (!grads) return fail(GES_ERR_INVALID_ARG, "grads is NULL");
+    if (!dL_drgb || !out_T || !out_front || !out_last || !out_Tlast)
+        return fail(GES_ERR_INVALID_ARG, "the backward needs dL_drgb and the forward's T, front, last and Tlast");
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        CamParams C;
+        OptParams O;
+        ViewScratch X;
+        ges_status r = translucent_setup(s, cam, opts, w, C, O, X);
+        if (r != GES_OK) return r;
+        const int64_t N = std::max<int64_t>(s->desc.n_surfels, 1);
+        GES_CUDA(s->t_acc.ensure((size_t)N * 18 * 8 + 16));
+        GES_CUDA(cudaMemsetAsync(X.status, 0, ST_WORDS * 4, s->stream));
+        long long *acc = (long long *)s->t_acc.p;
+        cudaError_t e = launch_translucent_backward(s->view, C, O, X, w, front_first != 0,
+                                                    (unsigned long long *)s->t_keys.p, dL_drgb, out_T, out_front,
+                                                    out_last, out_Tlast, acc, (unsigned *)(acc + (size_t)N * 18),
+                                                    grads->s_pos, grads->s_rot, grads->s_scale, grads->s_w,
+                                                    grads->s_sh, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+        bool retry;
+        if ((r = translucent_status(s, retry)) != GES_OK) return r;
+        if (!retry) return GES_OK;
+    }
+    return fail(GES_ERR_INTERNAL, "tile lists kept overflowing after growing them");
+}
+
+ges_status ges_contribution_scores(ges_scene *s, const ges_camera *cam, const ges_render_opts *opts,
+                                   const float *out_depth, const float *aux, float *out_score)
+{
+    if (!s) return fail(GES_ERR_INVALID_ARG, "scene is NULL");
+    if (!out_depth || !aux || (!out_score && s->desc.n_gaussians > 0))
+        return fail(GES_ERR_INVALID_ARG, "contribution scores need depth, aux and out_score");
+    CamParams C;
+    OptParams O;
+    ges_status r = make_cam(cam, C);
+    if (r != GES_OK) return r;
+    if ((r = make_opts(opts, O)) != GES_OK) return r;
+    cudaError_t e = launch_contribution(s->view, C, O, out_depth, aux, out_score, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     GES_CUDA(cudaStreamSynchronize(s->stream));
     return GES_OK;

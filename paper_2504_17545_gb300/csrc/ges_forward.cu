@@ -104,7 +104,7 @@ __device__ __forceinline__ void store_rec(float4 *dst, const GaussRec &r)
 // return its pixel bbox.
 // kGd: the scene's Gaussian kind (a template argument, so that each kernel
 // carries only its own set-up code)
-template <int kGd>
+template <int kGd, bool kTr = false>
 __device__ __forceinline__ bool setup_and_store(const SceneView &S, const CamParams &C, const OptParams &O,
                                                 const ViewScratch &X, bool surf, int64_t i, int &x0, int &y0,
                                                 int &x1, int &y1)
@@ -116,6 +116,13 @@ __device__ __forceinline__ bool setup_and_store(const SceneView &S, const CamPar
         if (!o.visible) return false;
         store_rec(X.s_rec + 4 * i, o.rec);
         X.s_rgb[i] = make_float4(o.rgb[0], o.rgb[1], o.rgb[2], 0.f);
+        if (kTr) {
+            float4 *f = X.s_tside + 4 * i;
+            f[0] = make_float4(o.P[0], o.P[1], o.P[2], o.s1);
+            f[1] = make_float4(o.U[0], o.U[1], o.U[2], o.s2);
+            f[2] = make_float4(o.V[0], o.V[1], o.V[2], 0.f);
+            f[3] = make_float4(o.N[0], o.N[1], o.N[2], 0.f);
+        }
         x0 = o.x0; y0 = o.y0; x1 = o.x1; y1 = o.y1;
     } else {
         GaussOut o;
@@ -139,7 +146,7 @@ __device__ __forceinline__ bool setup_and_store(const SceneView &S, const CamPar
 
 // CTA c of a view: its range of primitives.  hist: ceil(T/2) shared words
 // (two 16-bit counters each); vcnt: a shared counter.
-template <int kGd>
+template <int kGd, bool kTr = false>
 __device__ __forceinline__ void prep_local_body(const SceneView &S, const CamParams &C, const OptParams &O,
                                                 const ViewScratch &X, const LocalBins &B, int c, unsigned *hist,
                                                 unsigned &vcnt)
@@ -156,7 +163,7 @@ __device__ __forceinline__ void prep_local_body(const SceneView &S, const CamPar
     for (int64_t i0 = beg; i0 < end; i0 += kPrepThreads) {
         const int64_t i = i0 + threadIdx.x;
         int x0 = 0, y0 = 0, x1 = -1, y1 = -1;
-        const bool vis = i < end && setup_and_store<kGd>(S, C, O, X, surf, i, x0, y0, x1, y1);
+        const bool vis = i < end && setup_and_store<kGd, kTr>(S, C, O, X, surf, i, x0, y0, x1, y1);
         const unsigned m = __ballot_sync(0xffffffffu, vis);
         if (m) {
             const int leader = __ffs(m) - 1;
@@ -183,13 +190,13 @@ __device__ __forceinline__ void prep_local_body(const SceneView &S, const CamPar
     }
 }
 
-template <int kGd>
+template <int kGd, bool kTr = false>
 __global__ void __launch_bounds__(kPrepThreads, 2) k_prep_local(SceneView S, CamParams C, OptParams O,
                                                                 ViewScratch X, LocalBins B)
 {
     extern __shared__ unsigned hist[];
     __shared__ unsigned vcnt;
-    prep_local_body<kGd>(S, C, O, X, B, blockIdx.x, hist, vcnt);
+    prep_local_body<kGd, kTr>(S, C, O, X, B, blockIdx.x, hist, vcnt);
 }
 
 __device__ __forceinline__ unsigned hist_get(const unsigned *row, int t)
@@ -280,14 +287,14 @@ __device__ __forceinline__ void append_visible(bool vis, int64_t i, unsigned *co
     if (vis) list[base + __popc(m & ((1u << lane) - 1u))] = (int)i;
 }
 
-template <int kGd>
+template <int kGd, bool kTr = false>
 __global__ void __launch_bounds__(256) k_prep_atomic(SceneView S, CamParams C, OptParams O, ViewScratch X,
                                                      int n_sblocks)
 {
     const bool surf = (int)blockIdx.x < n_sblocks;
     const int64_t i = (int64_t)(surf ? blockIdx.x : blockIdx.x - n_sblocks) * 256 + threadIdx.x;
     int x0 = 0, y0 = 0, x1 = -1, y1 = -1;
-    const bool vis = i < (surf ? S.N : S.M) && setup_and_store<kGd>(S, C, O, X, surf, i, x0, y0, x1, y1);
+    const bool vis = i < (surf ? S.N : S.M) && setup_and_store<kGd, kTr>(S, C, O, X, surf, i, x0, y0, x1, y1);
     if (vis) {
         int *cnt = surf ? X.s_cnt : X.g_cnt;
         for (int ty = y0 / kTile; ty <= y1 / kTile; ++ty)
@@ -825,6 +832,7 @@ cudaError_t prepare_forward_kernels()
     const int hs = (int)local_bins_smem(kLocalMaxTiles, false);
     if ((e = cudaFuncSetAttribute(k_prep_local<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(k_prep_local<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_prep_local<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(k_bprep<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(k_bprep<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess)
         return e;
@@ -835,7 +843,6 @@ cudaError_t prepare_forward_kernels()
                                 (int)local_bins_smem(kLocalMaxTiles, true));
 }
 
-namespace {
 // preprocess + binning of one view (everything before the raster)
 cudaError_t launch_binning(const SceneView &S, const CamParams &C, const OptParams &O, const ViewScratch &X,
                            cudaStream_t st, cudaEvent_t *ev)
@@ -854,13 +861,15 @@ cudaError_t launch_binning(const SceneView &S, const CamParams &C, const OptPara
         B = plan_local_bins(Sv.N, Sv.M, sms);
         if (B.Ps + B.Pg > 0) {
             const size_t sm = local_bins_smem(T, false);
-            if (Sv.gdim == 2) k_prep_local<2><<<B.Ps + B.Pg, kPrepThreads, sm, st>>>(Sv, C, O, X, B);
+            if (X.s_tside) k_prep_local<3, true><<<B.Ps + B.Pg, kPrepThreads, sm, st>>>(Sv, C, O, X, B);
+            else if (Sv.gdim == 2) k_prep_local<2><<<B.Ps + B.Pg, kPrepThreads, sm, st>>>(Sv, C, O, X, B);
             else k_prep_local<3><<<B.Ps + B.Pg, kPrepThreads, sm, st>>>(Sv, C, O, X, B);
         }
     } else {
         const int nsb = (int)((Sv.N + 255) / 256), ngb = (int)((Sv.M + 255) / 256);
         if (nsb + ngb > 0) {
-            if (Sv.gdim == 2) k_prep_atomic<2><<<nsb + ngb, 256, 0, st>>>(Sv, C, O, X, nsb);
+            if (X.s_tside) k_prep_atomic<3, true><<<nsb + ngb, 256, 0, st>>>(Sv, C, O, X, nsb);
+            else if (Sv.gdim == 2) k_prep_atomic<2><<<nsb + ngb, 256, 0, st>>>(Sv, C, O, X, nsb);
             else k_prep_atomic<3><<<nsb + ngb, 256, 0, st>>>(Sv, C, O, X, nsb);
         }
     }
@@ -877,6 +886,7 @@ cudaError_t launch_binning(const SceneView &S, const CamParams &C, const OptPara
     return cudaGetLastError();
 }
 
+namespace {
 // Exact work counts of one view: every (sample, surfel) fragment inside the
 // opaque disc in front of the near plane, and every (pixel, Gaussian) pair
 // with alpha >= alpha_min, over the full tile lists (no culling).

@@ -85,6 +85,9 @@ struct ViewScratch {
     // 2D Gaussians (rgb, log2 sigma'), (normal, log2(alpha_min / sigma'));
     // 3D Gaussians with geometry outputs (normal, centre depth), unused
     float4 *g_aux = nullptr;
+    // [N][4] camera-space frame of each surfel for the translucent render:
+    // (P, s1), (U, s2), (V, -), (N, -); written when non-null
+    float4 *s_tside = nullptr;
 };
 
 // Number of preprocess CTAs for local binning and the size of their ranges.
@@ -121,6 +124,30 @@ cudaError_t prepare_forward_kernels();   // once per device: large dynamic share
 
 // ---------------------------------------------------------------------------
 // host launchers (ges_forward.cu / ges_backward.cu)
+
+// Preprocess and binning of one view (the tile lists, before any raster);
+// ev: 4 events or null.  With X.s_tside set, surfels also export their
+// camera-space frame (translucent render).
+cudaError_t launch_binning(const SceneView &S, const CamParams &C, const OptParams &O, const ViewScratch &X,
+                           cudaStream_t st, cudaEvent_t *ev);
+
+// Translucent-surfel render (Sec. 4.1) of one view: binning of the surfels
+// (X.s_tside must be set), per-tile sort, blend.  keys: one 64-bit word per
+// tile-list entry.  cover (or null): per-surfel counts of frontmost pixels, added.
+cudaError_t launch_translucent(const SceneView &S, const CamParams &C, const OptParams &O, const ViewScratch &X,
+                               const float *w, bool front_first, unsigned long long *keys, float *out_rgb,
+                               float *out_T, int32_t *out_front, int32_t *out_last, float *out_Tlast, int32_t *cover,
+                               cudaStream_t st);
+// Its backward: acc [N][18] 64-bit words and gmax (one word) are scratch.
+cudaError_t launch_translucent_backward(const SceneView &S, const CamParams &C, const OptParams &O,
+                                        const ViewScratch &X, const float *w, bool front_first,
+                                        unsigned long long *keys, const float *dL, const float *in_T,
+                                        const int32_t *in_front, const int32_t *in_last, const float *in_Tlast,
+                                        long long *acc, unsigned *gmax, float *g_pos, float *g_rot, float *g_scale,
+                                        float *g_w, float *g_sh, cudaStream_t st);
+// Gaussian contribution scores (Eq. 9) from a render's depth (D_s) and aux (W_G).
+cudaError_t launch_contribution(const SceneView &S, const CamParams &C, const OptParams &O, const float *depth,
+                                const float *aux, float *score, cudaStream_t st);
 
 // geo_maps: null, or 5 device pointers (each may be null): N_s [3,H,W],
 // D_smooth [H,W], N_smooth [3,H,W], D_G [H,W], N_G [3,H,W]; with O.geo set.
@@ -432,6 +459,8 @@ struct SurfelOut {
     SurfelRec rec;
     float rgb[3], raw[3], dir[3];
     int x0, y0, x1, y1;
+    // camera-space frame (for the translucent render's backward)
+    float P[3], U[3], V[3], N[3], s1, s2;
 };
 
 // Conservative pixel range [lo, hi] of centres (i + 0.5) inside [a, b], clamped.
@@ -639,6 +668,8 @@ __device__ __forceinline__ void surfel_setup(const SceneView &S, const CamParams
     for (int r = 0; r < 3; ++r) P[r] = df_dot3_plus(C.R + 3 * r, px, py, pz, C.t[r]);
     DiscOut d;
     if (!disc_setup(C, P, tu, tv, n, s1, s2, O.surfel_r, O.samples == 4 ? 0.25f : 0.f, (int)i, d)) return;
+    for (int k = 0; k < 3; ++k) { o.P[k] = P[k].hi; o.U[k] = tu[k]; o.V[k] = tv[k]; o.N[k] = n[k]; }
+    o.s1 = s1; o.s2 = s2;
     o.rec = d.rec;
     o.x0 = d.x0; o.y0 = d.y0; o.x1 = d.x1; o.y1 = d.y1;
     const int K = (S.deg + 1) * (S.deg + 1);

@@ -54,6 +54,10 @@ class ges_grads(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("g_pos", "g_rot", "g_scale", "g_opac", "g_sh", "s_sh")]
 
 
+class ges_tgrads(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("s_pos", "s_rot", "s_scale", "s_w", "s_sh")]
+
+
 class ges_stats(C.Structure):
     _fields_ = [("visible_surfels", C.c_int64), ("visible_gaussians", C.c_int64),
                 ("surfel_tile_pairs", C.c_int64), ("gauss_tile_pairs", C.c_int64),
@@ -82,6 +86,11 @@ _SIGS = {
     "ges_render_ex": (C.c_int, [C.c_void_p, _P(ges_camera), _P(ges_render_opts), C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.c_void_p]),
     "ges_render_geom": (C.c_int, [C.c_void_p, _P(ges_camera), _P(ges_render_opts)] + [C.c_void_p] * 7),
+    "ges_render_translucent": (C.c_int, [C.c_void_p, _P(ges_camera), _P(ges_render_opts), C.c_void_p, C.c_int32]
+                               + [C.c_void_p] * 6),
+    "ges_render_translucent_backward": (C.c_int, [C.c_void_p, _P(ges_camera), _P(ges_render_opts), C.c_void_p,
+                                                  C.c_int32] + [C.c_void_p] * 5 + [_P(ges_tgrads)]),
+    "ges_contribution_scores": (C.c_int, [C.c_void_p, _P(ges_camera), _P(ges_render_opts)] + [C.c_void_p] * 3),
     "ges_render_backward": (C.c_int, [C.c_void_p, _P(ges_camera), _P(ges_render_opts), C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_void_p, _P(ges_grads)]),
     "ges_render_batch": (C.c_int, [_P(C.c_void_p), _P(ges_camera), _P(C.c_int32), C.c_int32,
@@ -180,6 +189,27 @@ def ges_render_geom(scene, cam: ges_camera, opts, out_rgb: int, out_depth: int, 
     _check(load().ges_render_geom(scene, C.byref(cam), C.byref(opts) if opts is not None else None,
                                   *[C.c_void_p(p) for p in (out_rgb, out_depth, out_ns, out_dsm, out_nsm,
                                                              out_dg, out_ng)]))
+
+
+def ges_render_translucent(scene, cam: ges_camera, opts, w: int, front_first: bool, out_rgb: int, out_T: int,
+                           out_front: int, out_last: int, out_Tlast: int, out_cover: int):
+    _check(load().ges_render_translucent(scene, C.byref(cam), C.byref(opts) if opts is not None else None,
+                                         C.c_void_p(w), int(bool(front_first)),
+                                         *[C.c_void_p(p) for p in (out_rgb, out_T, out_front, out_last, out_Tlast,
+                                                                    out_cover)]))
+
+
+def ges_render_translucent_backward(scene, cam: ges_camera, opts, w: int, front_first: bool, dL: int, T: int,
+                                    front: int, last: int, Tlast: int, grads: "ges_tgrads"):
+    _check(load().ges_render_translucent_backward(scene, C.byref(cam), C.byref(opts) if opts is not None else None,
+                                                  C.c_void_p(w), int(bool(front_first)),
+                                                  *[C.c_void_p(p) for p in (dL, T, front, last, Tlast)],
+                                                  C.byref(grads)))
+
+
+def ges_contribution_scores(scene, cam: ges_camera, opts, depth: int, aux: int, out: int):
+    _check(load().ges_contribution_scores(scene, C.byref(cam), C.byref(opts) if opts is not None else None,
+                                          C.c_void_p(depth), C.c_void_p(aux), C.c_void_p(out)))
 
 
 def ges_render_backward(scene, cam: ges_camera, opts, dL_drgb: int, out_rgb: int, out_depth: int,

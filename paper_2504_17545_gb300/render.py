@@ -198,6 +198,61 @@ def render_geom(scene: GESScene, cam, opts: Optional[dict] = None):
     return out
 
 
+def render_translucent(scene: GESScene, cam, w: torch.Tensor, front_first: bool = True, opts: Optional[dict] = None,
+                       cover: bool = False):
+    """Translucent-surfel render of the coarse stage (Sec. 4.1, Eq. 6-7) with
+    the opacity modulating parameters w [N] (float32 CUDA tensor): dict(rgb
+    [3,H,W], T, front, last, Tlast [H,W]; cover [N] int32 when ``cover``)."""
+    c = camera_struct(cam)
+    dev = scene.t["s_pos"].device
+    H, W = c.height, c.width
+    wt = w.contiguous().float()
+    out = dict(rgb=torch.empty((3, H, W), device=dev), T=torch.empty((H, W), device=dev),
+               front=torch.empty((H, W), device=dev, dtype=torch.int32),
+               last=torch.empty((H, W), device=dev, dtype=torch.int32), Tlast=torch.empty((H, W), device=dev))
+    if cover:
+        out["cover"] = torch.empty((scene.n_surfels,), device=dev, dtype=torch.int32)
+    scene.bind_stream()
+    N.ges_render_translucent(scene.handle, c, opts_struct(opts), wt.data_ptr() if wt.numel() else 0, front_first,
+                             *[out[k].data_ptr() for k in ("rgb", "T", "front", "last", "Tlast")],
+                             out["cover"].data_ptr() if cover and scene.n_surfels else 0)
+    out["w"] = wt
+    return out
+
+
+def render_translucent_backward(scene: GESScene, cam, w: torch.Tensor, fwd: dict, dL_drgb: torch.Tensor,
+                                front_first: bool = True, opts: Optional[dict] = None):
+    """Gradients of sum(dL_drgb * C) of the translucent render: s_pos, s_rot,
+    s_scale, s_w, s_sh (float32)."""
+    c = camera_struct(cam)
+    dev = scene.t["s_pos"].device
+    n, K = scene.n_surfels, (scene.sh_degree + 1) ** 2
+    g = {"s_pos": torch.empty((n, 3), device=dev), "s_rot": torch.empty((n, 4), device=dev),
+         "s_scale": torch.empty((n, 2), device=dev), "s_w": torch.empty((n,), device=dev),
+         "s_sh": torch.empty((n, K, 3), device=dev)}
+    gr = N.ges_tgrads()
+    for k in ("s_pos", "s_rot", "s_scale", "s_w", "s_sh"):
+        setattr(gr, k, g[k].data_ptr() if g[k].numel() else None)
+    wt = w.contiguous().float()
+    dl = dL_drgb.contiguous().float()
+    scene.bind_stream()
+    N.ges_render_translucent_backward(scene.handle, c, opts_struct(opts), wt.data_ptr() if wt.numel() else 0,
+                                      front_first, dl.data_ptr(), fwd["T"].data_ptr(), fwd["front"].data_ptr(),
+                                      fwd["last"].data_ptr(), fwd["Tlast"].data_ptr(), gr)
+    return g
+
+
+def contribution_scores(scene: GESScene, cam, fwd: dict, opts: Optional[dict] = None) -> torch.Tensor:
+    """Contribution score of each Gaussian (Sec. 4.2, Eq. 9) from a render's
+    depth and aux outputs."""
+    c = camera_struct(cam)
+    out = torch.empty((scene.n_gaussians,), device=scene.t["g_pos"].device)
+    scene.bind_stream()
+    N.ges_contribution_scores(scene.handle, c, opts_struct(opts), fwd["depth"].data_ptr(), fwd["aux"].data_ptr(),
+                              out.data_ptr() if out.numel() else 0)
+    return out
+
+
 def render_backward(scene: GESScene, cam, fwd: dict, dL_drgb: torch.Tensor, opts: Optional[dict] = None):
     """Gradients of sum(dL_drgb * C) (Sec. 4.2); returns a dict of float32 tensors."""
     c = camera_struct(cam)
