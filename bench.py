@@ -408,6 +408,32 @@ def geometry_2dges_extra(R, N, sg, scene, cams):
     return res
 
 
+def translucent_extra(R, N, scene, cams):
+    """Coarse stage (Sec. 4.1): the translucent-surfel render of the 1M
+    surfels at 1080p, forward and forward + backward, per view, in the two
+    regimes (w in [0.1, 30) with the sorted order; w in [30, 255] front first);
+    and the Gaussian contribution scores (Eq. 9) of one view."""
+    import numpy as np
+    import torch
+    sc = scene.subset(g_idx=np.zeros(0, int))
+    gs = R.GESScene.from_arrays(sc)
+    res = {"workload": "1080p-1M-surfels-translucent"}
+    rng = np.random.default_rng(0)
+    for name, lo, hi, ff in (("early", 0.1, 30.0, False), ("late", 30.0, 255.0, True)):
+        w = torch.as_tensor(rng.uniform(lo, hi, sc.n_surfels), dtype=torch.float32, device="cuda")
+        fwd = R.render_translucent(gs, cams[0], w, ff)
+        g = torch.sign(fwd["rgb"] - 0.5) / fwd["rgb"].numel()
+        res[f"{name}_fwd_ms"] = _time(lambda: R.render_translucent(gs, cams[0], w, ff), 5)
+        res[f"{name}_fwd_bwd_ms"] = _time(
+            lambda: R.render_translucent_backward(gs, cams[0], w, R.render_translucent(gs, cams[0], w, ff), g, ff), 5)
+    gs.close()
+    g3 = R.GESScene.from_arrays(scene)
+    out = R.render(g3, cams[0])
+    res["contribution_scores_ms"] = _time(lambda: R.contribution_scores(g3, cams[0], out), 5)
+    g3.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -526,6 +552,7 @@ def main():
         extras["mip_ges"] = mip_extra(R, N, gs, cams)
         extras["paper_shaped"] = paper_shaped_extra(R, N, sg)
         extras["geometry_2dges"] = geometry_2dges_extra(R, N, sg, scene, cams)
+        extras["translucent_coarse"] = translucent_extra(R, N, scene, cams)
     if rank != 0:
         return
     # roofline of the dominant kernel (largest share of device time); one
