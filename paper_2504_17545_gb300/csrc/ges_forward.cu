@@ -111,18 +111,11 @@ __device__ __forceinline__ bool setup_and_store(const SceneView &S, const CamPar
 {
     if (surf) {
         SurfelOut o;
-        surfel_setup(S, C, O, i, o);
+        surfel_setup(S, C, O, i, o, kTr ? X.s_tside + 4 * i : nullptr);
         if (!o.valid_quat) atomicOr(X.status + ST_FLAGS, FLAG_BADQ);
         if (!o.visible) return false;
         store_rec(X.s_rec + 4 * i, o.rec);
         X.s_rgb[i] = make_float4(o.rgb[0], o.rgb[1], o.rgb[2], 0.f);
-        if (kTr) {
-            float4 *f = X.s_tside + 4 * i;
-            f[0] = make_float4(o.P[0], o.P[1], o.P[2], o.s1);
-            f[1] = make_float4(o.U[0], o.U[1], o.U[2], o.s2);
-            f[2] = make_float4(o.V[0], o.V[1], o.V[2], 0.f);
-            f[3] = make_float4(o.N[0], o.N[1], o.N[2], 0.f);
-        }
         x0 = o.x0; y0 = o.y0; x1 = o.x1; y1 = o.y1;
     } else {
         GaussOut o;

@@ -459,8 +459,6 @@ struct SurfelOut {
     SurfelRec rec;
     float rgb[3], raw[3], dir[3];
     int x0, y0, x1, y1;
-    // camera-space frame (for the translucent render's backward)
-    float P[3], U[3], V[3], N[3], s1, s2;
 };
 
 // Conservative pixel range [lo, hi] of centres (i + 0.5) inside [a, b], clamped.
@@ -639,8 +637,10 @@ __device__ __forceinline__ bool disc_setup(const CamParams &C, const df *P, cons
 // Per-surfel set-up for the view (Sec. 3: disc placed by scale, rotation,
 // translation; opaque extent of Sec. 4.1).  Produces the raster record, the
 // colour (Eq. 1) and a conservative pixel bbox.
+// tside (translucent render only; null elsewhere, which removes the stores):
+// the camera-space frame (P, s1), (U, s2), (V, -), (N, -) of a visible surfel.
 __device__ __forceinline__ void surfel_setup(const SceneView &S, const CamParams &C, const OptParams &O,
-                                             int64_t i, SurfelOut &o)
+                                             int64_t i, SurfelOut &o, float4 *tside = nullptr)
 {
     o.visible = false;
     o.valid_quat = true;
@@ -668,8 +668,12 @@ __device__ __forceinline__ void surfel_setup(const SceneView &S, const CamParams
     for (int r = 0; r < 3; ++r) P[r] = df_dot3_plus(C.R + 3 * r, px, py, pz, C.t[r]);
     DiscOut d;
     if (!disc_setup(C, P, tu, tv, n, s1, s2, O.surfel_r, O.samples == 4 ? 0.25f : 0.f, (int)i, d)) return;
-    for (int k = 0; k < 3; ++k) { o.P[k] = P[k].hi; o.U[k] = tu[k]; o.V[k] = tv[k]; o.N[k] = n[k]; }
-    o.s1 = s1; o.s2 = s2;
+    if (tside) {
+        tside[0] = make_float4(P[0].hi, P[1].hi, P[2].hi, s1);
+        tside[1] = make_float4(tu[0], tu[1], tu[2], s2);
+        tside[2] = make_float4(tv[0], tv[1], tv[2], 0.f);
+        tside[3] = make_float4(n[0], n[1], n[2], 0.f);
+    }
     o.rec = d.rec;
     o.x0 = d.x0; o.y0 = d.y0; o.x1 = d.x1; o.y1 = d.y1;
     const int K = (S.deg + 1) * (S.deg + 1);
