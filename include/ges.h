@@ -360,6 +360,8 @@ typedef struct {
     int32_t raster_ctas_per_sm;    /* chosen persistent raster occupancy */
     int32_t candidates;            /* configurations timed by the autotuner */
     double tuned_ms;               /* best measured time of one launch */
+    int64_t h2d_bytes;             /* host->device bytes of one launch (the view table) */
+    int64_t d2h_bytes;             /* device->host bytes of one launch (status words) */
 } ges_batch_info;
 
 GES_API ges_status ges_batch_create(ges_scene *const *scenes, const ges_camera *cams, const int32_t *scene_of_view,

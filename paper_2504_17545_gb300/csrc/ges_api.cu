@@ -945,6 +945,8 @@ ges_status ges_batch_create(ges_scene *const *scenes, const ges_camera *cams, co
     b->info.n_views = n_views;
     b->info.candidates = cand;
     b->info.tuned_ms = best_ms;
+    b->info.h2d_bytes = (int64_t)(sizeof(BatchView) * n_views);
+    b->info.d2h_bytes = (int64_t)(status_words * 4);
 #undef BATCH_CUDA
     // one checked launch with the chosen configuration
     cudaGraphLaunch(b->exec, b->stream);
