@@ -329,7 +329,8 @@ def msaa_extra(R, N, gs, cams):
                                 "frac": ops / sec / alu_peak() if sec else None,
                                 "units_per_launch": {"sample_fragments": len(cams) * sfrag,
                                                      "gauss_terms": len(cams) * gterm}},
-            "autotuned": {"prims_per_cta": info.prims_per_cta, "raster_ctas_per_sm": info.raster_ctas_per_sm}}
+            "autotuned": {"prims_per_cta": info.prims_per_cta, "raster_ctas_per_sm": info.raster_ctas_per_sm,
+                                 "raster": "pipelined" if info.raster_pipelined else "classic"}}
 
 
 def mip_extra(R, N, gs, cams):
@@ -355,7 +356,8 @@ def mip_extra(R, N, gs, cams):
             "filter3d_ms": t_f3, "filter3d_cameras": len(cams),
             "kernel_ms_per_frame": {k: prof[k][0] / prof[k][1] / len(cams) for k in prof},
             "gauss_terms_per_frame": float(np.mean([f[1] for f in frags])),
-            "autotuned": {"prims_per_cta": info.prims_per_cta, "raster_ctas_per_sm": info.raster_ctas_per_sm}}
+            "autotuned": {"prims_per_cta": info.prims_per_cta, "raster_ctas_per_sm": info.raster_ctas_per_sm,
+                                 "raster": "pipelined" if info.raster_pipelined else "classic"}}
 
 
 def paper_shaped_extra(R, N, sg):
@@ -598,8 +600,9 @@ def main():
     sec = top_ms / top_launches / 1e3
     if top == "raster":
         ops = n_views * (OPS_PER_SURFEL_FRAGMENT * sfrag + OPS_PER_GAUSS_TERM * gterm)
-        roof = {"bound": "alu", "kernel": "k_braster", "achieved": ops / sec / 1e12, "peak": alu_peak() / 1e12,
-                "unit": "TFLOP/s", "frac": ops / sec / alu_peak(), "traffic": ncu_traffic("k_braster", n_views),
+        rk = "k_braster_pipe" if info.raster_pipelined else "k_braster"
+        roof = {"bound": "alu", "kernel": rk, "achieved": ops / sec / 1e12, "peak": alu_peak() / 1e12,
+                "unit": "TFLOP/s", "frac": ops / sec / alu_peak(), "traffic": ncu_traffic(rk, n_views),
                 "peak_source": "152 SMs x 128 FP32 lanes x max SM clock",
                 "units_per_launch": {"surfel_fragments": n_views * sfrag, "gauss_terms": n_views * gterm}}
     else:
@@ -618,7 +621,8 @@ def main():
                    "n_gaussians": scene.n_gaussians, "views_per_step": n_views,
                    "l2": "inputs 332 MB > 129 MB L2, no flush", "parallelism": f"replicas{world}",
                    "launch": f"one CUDA graph per step (5 kernels over all {n_views} views)",
-                   "autotuned": {"prims_per_cta": info.prims_per_cta, "raster_ctas_per_sm": info.raster_ctas_per_sm}},
+                   "autotuned": {"prims_per_cta": info.prims_per_cta, "raster_ctas_per_sm": info.raster_ctas_per_sm,
+                                 "raster": "pipelined" if info.raster_pipelined else "classic"}},
         "roofline": roof,
         "frame_roofline": {"bound": "hbm", "algorithmic_bytes_per_frame": float(np.mean(frame_b)),
                            "achieved": frame_achieved, "peak": peak, "frac": frame_achieved / peak, "unit": "GB/s"},

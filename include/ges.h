@@ -348,7 +348,13 @@ GES_API ges_status ges_count_fragments(ges_scene *scene, const ges_camera *cam, 
  * ges_batch_create renders every view once through the scene's own path to
  * size the tile lists (x1.5 headroom), allocates the batch's own scratch,
  * then autotunes the primitives per preprocess CTA and the persistent raster
- * grid by timing each candidate graph, and keeps the fastest.  Pointers
+ * grid by timing each candidate graph, and keeps the fastest.  The raster
+ * kind comes from the environment variable GES_BATCH_RASTER: classic (the
+ * default; CTAs stage each chunk of records together), pipelined (a producer
+ * warp gathers the records with bulk asynchronous copies into a ring of
+ * shared-memory stages that the pixel warps consume without CTA-wide
+ * barriers), or auto (time both).  Both give bitwise-identical images.
+ * Pointers
  * (scenes' arrays, outputs) are baked into the graph and must stay valid
  * until ges_batch_destroy.  Images must have at most 32768 tiles of 16x16
  * (otherwise GES_ERR_UNSUPPORTED; ges_render_batch has no such limit).
@@ -362,6 +368,8 @@ typedef struct {
     double tuned_ms;               /* best measured time of one launch */
     int64_t h2d_bytes;             /* host->device bytes of one launch (the view table) */
     int64_t d2h_bytes;             /* device->host bytes of one launch (status words) */
+    int32_t raster_pipelined;      /* 1: the pipelined raster (producer warp, bulk copies) was chosen */
+    int32_t reserved;
 } ges_batch_info;
 
 GES_API ges_status ges_batch_create(ges_scene *const *scenes, const ges_camera *cams, const int32_t *scene_of_view,

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -883,11 +884,25 @@ ges_status ges_batch_create(ges_scene *const *scenes, const ges_camera *cams, co
     // autotune: capture a graph per candidate, time it, keep the fastest
     float best_ms = 1e30f;
     int cand = 0;
+    // raster candidates (pipelined?, resident CTAs per SM); the 4-sample
+    // kernels are built for one CTA fewer.  GES_BATCH_RASTER selects the kind:
+    // classic (the default: CTA-staged, measured faster on every workload
+    // tried), pipelined, or auto (time both)
+    struct RasterCand { int pipe, per_sm; };
+    std::vector<RasterCand> rc;
+    {
+        const char *env = std::getenv("GES_BATCH_RASTER");
+        const bool use_pipe = env && (std::strcmp(env, "pipelined") == 0 || std::strcmp(env, "auto") == 0);
+        const bool use_classic = !env || std::strcmp(env, "pipelined") != 0;
+        const int d = O.samples == 4 ? 1 : 0;
+        if (use_classic) rc.insert(rc.end(), {{0, 4 - d}, {0, 5 - d}});
+        if (use_pipe) rc.insert(rc.end(), {{1, 3 - d}, {1, 4 - d}});
+    }
     for (int64_t R : kR) {
-        // resident raster CTAs per SM: the 4-sample kernel is built for one fewer
-        for (int per_sm : {O.samples == 4 ? 3 : 4, O.samples == 4 ? 4 : 5}) {
+        for (const RasterCand &cnd : rc) {
+            const int per_sm = cnd.per_sm;
             batch_layout(b, S, C, R, (unsigned char *)b->arena);
-            BatchPlan P{n_views, 0, 0, 0, 0, sms * per_sm, S[0].gdim};
+            BatchPlan P{n_views, 0, 0, 0, 0, sms * per_sm, S[0].gdim, cnd.pipe};
             for (int v = 0; v < n_views; ++v) {
                 P.total_tiles += b->views[v].T;
                 P.total_prep += b->views[v].B.Ps + b->views[v].B.Pg;
@@ -934,6 +949,7 @@ ges_status ges_batch_create(ges_scene *const *scenes, const ges_camera *cams, co
                 b->exec = ex;
                 b->info.prims_per_cta = (int32_t)R;
                 b->info.raster_ctas_per_sm = per_sm;
+                b->info.raster_pipelined = cnd.pipe;
             } else {
                 cudaGraphExecDestroy(ex);
             }
@@ -1003,6 +1019,10 @@ ges_status ges_batch_sync(ges_batch *b)
         }
         if (i >= 0) { b->profile.ms[i] += ms; b->profile.launches[i] += 1; }
     }
+    // word 4 after the views' status: a wait of the pipelined raster gave up
+    // (1: a consumer warp, 2: the producer warp)
+    if (const unsigned pw = b->h_status[(size_t)b->n * ST_WORDS + 4])
+        return fail(GES_ERR_INTERNAL, "the pipelined raster's waits gave up (code %u)", pw);
     for (int v = 0; v < b->n; ++v) {
         const unsigned *w = b->h_status + (size_t)v * ST_WORDS;
         if (w[ST_FLAGS] & FLAG_BADQ)

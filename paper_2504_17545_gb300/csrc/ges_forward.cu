@@ -418,203 +418,229 @@ struct GeoMaps {
     float *ng;            // [3,H,W] N_G
 };
 
-// One 16x16 tile.  ss/sgs: shared staging for surfel and Gaussian records,
-// structure-of-arrays (one float4 plane per 16-byte quarter): consecutive
-// threads store consecutive 16 B, and a warp reading one record gets a
-// broadcast.  kS surfel samples per pixel: 1 (the centre) or 4 (the 2x2 grid
-// at +-0.25 px, 4x multisampling of Sec. 5; the Gaussians stay at the centre).
-// kG: 3D Gaussians (EWA splats) or 2D Gaussians of 2D-GES (ray-splat hit,
-// planar depth).  kGeo: also the geometry maps of Eq. 10-12.
-template <int kS, int kG, bool kGeo>
-__device__ __forceinline__ void raster_tile(const ViewScratch &X, const CamParams &C, const OptParams &O,
-                                            float *__restrict__ out_rgb, float *__restrict__ out_depth,
-                                            int32_t *__restrict__ out_id, float *__restrict__ aux,
-                                            const GeoMaps &geo, int tile,
-                                            float4 (*ss)[kChunk], float4 (*sgs)[kChunk])
-{
-    const int tx = tile % C.tiles_x, ty = tile / C.tiles_x;
-    const unsigned warp = threadIdx.x >> 5, lane = lane_id();
-    const int wx0 = tx * kTile + (warp & 1) * kWarpW, wy0 = ty * kTile + (warp >> 1) * kWarpH;
-    const bool wactive = wx0 < C.W && wy0 < C.H;        // warp-uniform
-    const int wx1 = min(wx0 + kWarpW - 1, C.W - 1), wy1 = min(wy0 + kWarpH - 1, C.H - 1);
-    const int px = wx0 + (int)(lane & 7), py = wy0 + (int)(lane >> 3);
-    const bool in_img = px < C.W && py < C.H;
-    const float u = px + 0.5f, v = py + 0.5f;
-    // sample k sits at (us + 0.5 (k & 1), vs + 0.5 (k >> 1))
-    const float us = kS == 4 ? px + 0.25f : u, vs = kS == 4 ? py + 0.25f : v;
-    const bool do_s = O.mode != GES_MODE_GAUSSIANS_ONLY, do_g = O.mode != GES_MODE_SURFELS_ONLY;
-    const int s0 = do_s ? X.s_off[tile] : 0, s1 = do_s ? X.s_off[tile + 1] : 0;
-    const int g0 = do_g ? X.g_off[tile] : 0, g1 = do_g ? X.g_off[tile + 1] : 0;
-    const int t = threadIdx.x;
+// Staged records as seen by the per-pixel loops: plane p (16-byte quarter) of
+// record j.  SoaRecs: one float4 plane per quarter (the per-view raster's
+// staging: consecutive threads store consecutive 16 B, and a warp reading one
+// record gets a broadcast).  SlotRecs: records in slots of kSlot bytes, as the
+// bulk copies of the pipelined raster leave them (kSlot / 16 odd, so the 8
+// lanes of a quarter warp reading 8 consecutive slots hit 8 different 16-byte
+// bank groups).
+template <int kPlanes>
+struct SoaRecs {
+    const float4 (*st)[kChunk];
+    __device__ __forceinline__ float4 operator()(int p, int j) const { return st[p][j]; }
+};
+template <int kSlot>
+struct SlotRecs {
+    const unsigned char *base;
+    __device__ __forceinline__ float4 operator()(int p, int j) const
+    {
+        return *reinterpret_cast<const float4 *>(base + j * kSlot + 16 * p);
+    }
+};
 
-    // first chunk of both lists together: one round trip, one barrier
-    if (s0 + t < s1) stage_rec(ss, X.s_rec, X.s_list[s0 + t], t);
-    if (g0 + t < g1) stage_gauss<kG, kGeo>(sgs, X, X.g_list[g0 + t], t);
-    __syncthreads();
+// The 8x4 pixel block of one warp inside a 16x16 tile, and its lane's pixel.
+// kS surfel samples per pixel: 1 (the centre) or 4 (the 2x2 grid at +-0.25
+// px, 4x multisampling of Sec. 5; the Gaussians stay at the centre).
+template <int kS>
+struct WarpBlock {
+    int wx0, wy0, wx1, wy1, px, py;
+    bool wactive, in_img;
+    float u, v, us, vs;    // pixel centre; sample k sits at (us + 0.5 (k & 1), vs + 0.5 (k >> 1))
+    __device__ __forceinline__ WarpBlock(const CamParams &C, int tile, unsigned warp, unsigned lane)
+    {
+        const int tx = tile % C.tiles_x, ty = tile / C.tiles_x;
+        wx0 = tx * kTile + (warp & 1) * kWarpW;
+        wy0 = ty * kTile + (warp >> 1) * kWarpH;
+        wactive = wx0 < C.W && wy0 < C.H;        // warp-uniform
+        wx1 = min(wx0 + kWarpW - 1, C.W - 1);
+        wy1 = min(wy0 + kWarpH - 1, C.H - 1);
+        px = wx0 + (int)(lane & 7);
+        py = wy0 + (int)(lane >> 3);
+        in_img = px < C.W && py < C.H;
+        u = px + 0.5f;
+        v = py + 0.5f;
+        us = kS == 4 ? px + 0.25f : u;
+        vs = kS == 4 ? py + 0.25f : v;
+    }
+};
 
-    // ---------------- pass 1: surfel z-buffer ----------------
-    // A warp skips a surfel whose bbox misses its 8x4 block, or whose largest
-    // 1/z over the disc (izmax) is below every 1/z its pixels already hold
-    // (it cannot win anywhere in the block).  Survivors are tested two at a
-    // time; the lexicographic (depth, id) min does not depend on the order.
-    float best[kS];                          // per sample: 1/z of the nearest hit (0: none)
+// Pass 1 state of one lane: per sample the 1/z of the nearest hit (0: none)
+// and its surfel id; wmin: the smallest 'best' over the warp's samples.
+template <int kS>
+struct SurfelZ {
+    float best[kS];
     int bid[kS];
+    float wmin;
+    __device__ __forceinline__ void init(bool in_img)
+    {
 #pragma unroll
-    for (int k = 0; k < kS; ++k) { best[k] = in_img ? 0.f : INFINITY; bid[k] = 0x7fffffff; }
-    float wmin = 0.f;                        // smallest 'best' over the warp's samples
-    for (int base = s0; base < s1; base += kChunk) {
-        if (base != s0) {
-            __syncthreads();
-            if (base + t < s1) stage_rec(ss, X.s_rec, X.s_list[base + t], t);
-            __syncthreads();
+        for (int k = 0; k < kS; ++k) { best[k] = in_img ? 0.f : INFINITY; bid[k] = 0x7fffffff; }
+        wmin = 0.f;
+    }
+};
+
+// Pass 1 over n staged surfel records.  A warp skips a surfel whose bbox
+// misses its 8x4 block, or whose largest 1/z over the disc (izmax) is below
+// every 1/z its pixels already hold (it cannot win anywhere in the block).
+// Survivors are tested two at a time; the lexicographic (depth, id) min does
+// not depend on the order.
+template <int kS, class Recs>
+__device__ __forceinline__ void surfel_pass(const Recs &R, int n, const WarpBlock<kS> &B, float izn, unsigned lane,
+                                            SurfelZ<kS> &z)
+{
+    for (int j0 = 0; j0 < n; j0 += 32) {
+        const int j = j0 + (int)lane;
+        bool keep = false;
+        if (j < n) {
+            const float4 r3 = R(3, j);
+            keep = box_overlap(__float_as_uint(r3.y), __float_as_uint(r3.z), B.wx0, B.wy0, B.wx1, B.wy1) &&
+                   R(2, j).w >= z.wmin;
         }
-        const int n = min(kChunk, s1 - base);
-        if (wactive) {
-            for (int j0 = 0; j0 < n; j0 += 32) {
-                const int j = j0 + (int)lane;
-                bool keep = false;
-                if (j < n) {
-                    const float4 r3 = ss[3][j];
-                    keep = box_overlap(__float_as_uint(r3.y), __float_as_uint(r3.z), wx0, wy0, wx1, wy1) &&
-                           ss[2][j].w >= wmin;
-                }
-                unsigned mask = __ballot_sync(0xffffffffu, keep);
-                while (mask) {
-                    const int ja = j0 + __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    const bool two = mask != 0u;
-                    const int jb = two ? j0 + __ffs(mask) - 1 : ja;
-                    if (two) mask &= mask - 1;
-                    const float4 a2 = ss[2][ja], b2 = ss[2][jb];
-                    const float4 a0 = ss[0][ja], a1 = ss[1][ja], b0 = ss[0][jb], b1 = ss[1][jb];
-                    const int ida = __float_as_int(ss[3][ja].x), idb = __float_as_int(ss[3][jb].x);
+        unsigned mask = __ballot_sync(0xffffffffu, keep);
+        while (mask) {
+            const int ja = j0 + __ffs(mask) - 1;
+            mask &= mask - 1;
+            const bool two = mask != 0u;
+            const int jb = two ? j0 + __ffs(mask) - 1 : ja;
+            if (two) mask &= mask - 1;
+            const float4 a2 = R(2, ja), b2 = R(2, jb);
+            const float4 a0 = R(0, ja), a1 = R(1, ja), b0 = R(0, jb), b1 = R(1, jb);
+            const int ida = __float_as_int(R(3, ja).x), idb = __float_as_int(R(3, jb).x);
 #pragma unroll
-                    for (int k = 0; k < kS; ++k) {
-                        const float uk = us + 0.5f * (k & 1), vk = vs + 0.5f * (k >> 1);
-                        const float dua = uk - a0.x, dva = vk - a0.y, dub = uk - b0.x, dvb = vk - b0.y;
-                        const float iza = fmaf(a0.w, dua, fmaf(a1.x, dva, a0.z));
-                        const float izb = fmaf(b0.w, dub, fmaf(b1.x, dvb, b0.z));
-                        const float Aa = fmaf(a1.y, dua, fmaf(a1.z, dva, a1.w));
-                        const float Ab = fmaf(b1.y, dub, fmaf(b1.z, dvb, b1.w));
-                        const float Ba = fmaf(a2.x, dua, fmaf(a2.y, dva, a2.z));
-                        const float Bb = fmaf(b2.x, dub, fmaf(b2.y, dvb, b2.z));
-                        const float qa = fmaf(Aa, Aa, fmaf(Ba, Ba, -iza * iza));
-                        const float qb = fmaf(Ab, Ab, fmaf(Bb, Bb, -izb * izb));
-                        const bool ina = qa <= 0.f && iza < C.izn, inb = qb <= 0.f && izb < C.izn && two;
-                        if (ina && (iza > best[k] || (iza == best[k] && ida < bid[k]))) { best[k] = iza; bid[k] = ida; }
-                        if (inb && (izb > best[k] || (izb == best[k] && idb < bid[k]))) { best[k] = izb; bid[k] = idb; }
-                    }
-                }
-                // the warp's depth bound is refreshed once per group of 32
-                // entries: per-survivor refreshes and re-checks cost more
-                // instructions than they cull
-                float bmin = best[0];
-#pragma unroll
-                for (int k = 1; k < kS; ++k) bmin = fminf(bmin, best[k]);
-                wmin = __uint_as_float(__reduce_min_sync(0xffffffffu, __float_as_uint(bmin)));
+            for (int k = 0; k < kS; ++k) {
+                const float uk = B.us + 0.5f * (k & 1), vk = B.vs + 0.5f * (k >> 1);
+                const float dua = uk - a0.x, dva = vk - a0.y, dub = uk - b0.x, dvb = vk - b0.y;
+                const float iza = fmaf(a0.w, dua, fmaf(a1.x, dva, a0.z));
+                const float izb = fmaf(b0.w, dub, fmaf(b1.x, dvb, b0.z));
+                const float Aa = fmaf(a1.y, dua, fmaf(a1.z, dva, a1.w));
+                const float Ab = fmaf(b1.y, dub, fmaf(b1.z, dvb, b1.w));
+                const float Ba = fmaf(a2.x, dua, fmaf(a2.y, dva, a2.z));
+                const float Bb = fmaf(b2.x, dub, fmaf(b2.y, dvb, b2.z));
+                const float qa = fmaf(Aa, Aa, fmaf(Ba, Ba, -iza * iza));
+                const float qb = fmaf(Ab, Ab, fmaf(Bb, Bb, -izb * izb));
+                const bool ina = qa <= 0.f && iza < izn, inb = qb <= 0.f && izb < izn && two;
+                if (ina && (iza > z.best[k] || (iza == z.best[k] && ida < z.bid[k]))) { z.best[k] = iza; z.bid[k] = ida; }
+                if (inb && (izb > z.best[k] || (izb == z.best[k] && idb < z.bid[k]))) { z.best[k] = izb; z.bid[k] = idb; }
             }
         }
-    }
-    // resolve: C_s is the mean of the samples' colours (background where a
-    // sample hits nothing), D_s the nearest sample's depth
-    float bmax = best[0];
+        // the warp's depth bound is refreshed once per group of 32 entries:
+        // per-survivor refreshes and re-checks cost more instructions than
+        // they cull
+        float bmin = z.best[0];
 #pragma unroll
-    for (int k = 1; k < kS; ++k) bmax = fmaxf(bmax, best[k]);
-    const float Ds = bmax > 0.f ? 1.f / bmax : INFINITY;
-    float Cs[3];
+        for (int k = 1; k < kS; ++k) bmin = fminf(bmin, z.best[k]);
+        z.wmin = __uint_as_float(__reduce_min_sync(0xffffffffu, __float_as_uint(bmin)));
+    }
+}
+
+// Resolve of pass 1: C_s is the mean of the samples' colours (background
+// where a sample hits nothing), D_s the nearest sample's depth.
+template <int kS>
+__device__ __forceinline__ void surfel_resolve(const SurfelZ<kS> &z, bool in_img, const float4 *__restrict__ s_rgb,
+                                               const float *bg, float &bmax, float &Ds, float *Cs)
+{
+    bmax = z.best[0];
+#pragma unroll
+    for (int k = 1; k < kS; ++k) bmax = fmaxf(bmax, z.best[k]);
+    Ds = bmax > 0.f ? 1.f / bmax : INFINITY;
     if (kS == 1) {
-        Cs[0] = C.bg[0]; Cs[1] = C.bg[1]; Cs[2] = C.bg[2];
-        if (bid[0] != 0x7fffffff) {
-            const float4 c = X.s_rgb[bid[0]];
+        Cs[0] = bg[0]; Cs[1] = bg[1]; Cs[2] = bg[2];
+        if (z.bid[0] != 0x7fffffff) {
+            const float4 c = s_rgb[z.bid[0]];
             Cs[0] = c.x; Cs[1] = c.y; Cs[2] = c.z;
         }
     } else {
         float sr = 0.f, sgc = 0.f, sb = 0.f;
 #pragma unroll
         for (int k = 0; k < kS; ++k) {
-            float4 c = make_float4(C.bg[0], C.bg[1], C.bg[2], 0.f);
-            if (in_img && bid[k] != 0x7fffffff) c = X.s_rgb[bid[k]];
+            float4 c = make_float4(bg[0], bg[1], bg[2], 0.f);
+            if (in_img && z.bid[k] != 0x7fffffff) c = s_rgb[z.bid[k]];
             sr += c.x; sgc += c.y; sb += c.z;
         }
         Cs[0] = sr * (1.f / kS); Cs[1] = sgc * (1.f / kS); Cs[2] = sb * (1.f / kS);
     }
+}
 
-    // ---------------- pass 2: Gaussians (Eq. 2-4) ----------------
-    long long acc_r = 0, acc_g = 0, acc_b = 0, acc_w = 0;
-    long long acc_d = 0, acc_nx = 0, acc_ny = 0, acc_nz = 0;   // D_G, N_G (kGeo)
-    // no Gaussian with key >= max over the warp's pixels of D_s can pass the depth test there
-    const float wmaxD = __uint_as_float(__reduce_max_sync(0xffffffffu, in_img ? __float_as_uint(Ds) : 0u));
-    const float amin32 = O.alpha_min * 4294967296.f;
-    for (int base = g0; base < g1; base += kChunk) {
-        if (base != g0) {
-            __syncthreads();
-            if (base + t < g1) stage_gauss<kG, kGeo>(sgs, X, X.g_list[base + t], t);
-            __syncthreads();
+// Pass 2 sums of one lane, in 64-bit fixed point (units of 2^-32).
+struct GaussAcc {
+    long long r = 0, g = 0, b = 0, w = 0;
+    long long d = 0, nx = 0, ny = 0, nz = 0;   // D_G, N_G (geometry maps)
+};
+
+// Pass 2 over n staged Gaussian records (Eq. 2-4).  No Gaussian with key >=
+// wmaxD (the max over the warp's pixels of D_s) can pass the depth test there.
+template <int kS, int kG, bool kGeo, class Recs>
+__device__ __forceinline__ void gauss_pass(const Recs &R, int n, const WarpBlock<kS> &B, float Ds, float wmaxD,
+                                           float amin32, float izn, unsigned lane, GaussAcc &acc)
+{
+    for (int j0 = 0; j0 < n; j0 += 32) {
+        const int j = j0 + (int)lane;
+        bool keep = false;
+        if (j < n) {
+            const float4 r3 = R(3, j);
+            // 3D: key = d - eps; 2D: the smallest planar depth (1/izmax) - eps
+            const float key = kG == 2 ? 1.f / R(2, j).w - r3.w : R(2, j).x;
+            keep = box_overlap(__float_as_uint(r3.y), __float_as_uint(r3.z), B.wx0, B.wy0, B.wx1, B.wy1) &&
+                   key < wmaxD;
         }
-        const int n = min(kChunk, g1 - base);
-        if (wactive) {
-            for (int j0 = 0; j0 < n; j0 += 32) {
-                const int j = j0 + (int)lane;
-                bool keep = false;
-                if (j < n) {
-                    const float4 r3 = sgs[3][j];
-                    // 3D: key = d - eps; 2D: the smallest planar depth (1/izmax) - eps
-                    const float key = kG == 2 ? 1.f / sgs[2][j].w - r3.w : sgs[2][j].x;
-                    keep = box_overlap(__float_as_uint(r3.y), __float_as_uint(r3.z), wx0, wy0, wx1, wy1) &&
-                           key < wmaxD;
-                }
-                unsigned mask = __ballot_sync(0xffffffffu, keep);
-                while (mask) {
-                    const int jj = j0 + __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    float a, depth, cr, cg, cb, ok;
-                    float4 side = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (kG == 2) {
-                        const float4 r0 = sgs[0][jj], r1 = sgs[1][jj], r2 = sgs[2][jj];
-                        const float4 x0 = sgs[4][jj];
-                        side = sgs[5][jj];
-                        const float du = u - r0.x, dv = v - r0.y;
-                        const float iz = fmaf(r0.w, du, fmaf(r1.x, dv, r0.z));
-                        const float A = fmaf(r1.y, du, fmaf(r1.z, dv, r1.w));
-                        const float B = fmaf(r2.x, du, fmaf(r2.y, dv, r2.z));
-                        depth = __frcp_rn(iz);
-                        // rho = (a'^2 + b'^2)/r^2; alpha = 2^(log2 sigma' + log2(alpha_min/sigma') rho)
-                        const float rho = fmaf(A, A, B * B) * (depth * depth);
-                        a = ex2_approx(fmaf(side.w, rho, x0.w));
-                        cr = x0.x; cg = x0.y; cb = x0.z;
-                        ok = (iz > 0.f && iz < C.izn && depth - sgs[3][jj].w < Ds) ? 1.f : 0.f;
-                    } else {
-                        const GaussRec g = gauss_rec3(sgs[0][jj], sgs[1][jj], sgs[2][jj]);
-                        float e;
-                        a = gauss_alpha(g, u, v, e);
-                        cr = g.r; cg = g.g; cb = g.b;
-                        ok = g.key < Ds ? 1.f : 0.f;
-                        if (kGeo) { side = sgs[4][jj]; depth = side.w; }
-                    }
-                    // alpha * 2^32 is exact scaling: the clamp decision equals alpha >= alpha_min
-                    const float a32 = a * 4294967296.f;
-                    if (in_img && a32 >= amin32 && ok != 0.f) {
-                        acc_w += __float2ll_rn(a32);
-                        acc_r += __float2ll_rn(a32 * cr);
-                        acc_g += __float2ll_rn(a32 * cg);
-                        acc_b += __float2ll_rn(a32 * cb);
-                        if (kGeo) {
-                            acc_d += __float2ll_rn(a32 * depth);
-                            acc_nx += __float2ll_rn(a32 * side.x);
-                            acc_ny += __float2ll_rn(a32 * side.y);
-                            acc_nz += __float2ll_rn(a32 * side.z);
-                        }
-                    }
+        unsigned mask = __ballot_sync(0xffffffffu, keep);
+        while (mask) {
+            const int jj = j0 + __ffs(mask) - 1;
+            mask &= mask - 1;
+            float a, depth, cr, cg, cb, ok;
+            float4 side = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (kG == 2) {
+                const float4 r0 = R(0, jj), r1 = R(1, jj), r2 = R(2, jj);
+                const float4 x0 = R(4, jj);
+                side = R(5, jj);
+                const float du = B.u - r0.x, dv = B.v - r0.y;
+                const float iz = fmaf(r0.w, du, fmaf(r1.x, dv, r0.z));
+                const float A = fmaf(r1.y, du, fmaf(r1.z, dv, r1.w));
+                const float Bq = fmaf(r2.x, du, fmaf(r2.y, dv, r2.z));
+                depth = __frcp_rn(iz);
+                // rho = (a'^2 + b'^2)/r^2; alpha = 2^(log2 sigma' + log2(alpha_min/sigma') rho)
+                const float rho = fmaf(A, A, Bq * Bq) * (depth * depth);
+                a = ex2_approx(fmaf(side.w, rho, x0.w));
+                cr = x0.x; cg = x0.y; cb = x0.z;
+                ok = (iz > 0.f && iz < izn && depth - R(3, jj).w < Ds) ? 1.f : 0.f;
+            } else {
+                const GaussRec g = gauss_rec3(R(0, jj), R(1, jj), R(2, jj));
+                float e;
+                a = gauss_alpha(g, B.u, B.v, e);
+                cr = g.r; cg = g.g; cb = g.b;
+                ok = g.key < Ds ? 1.f : 0.f;
+                if (kGeo) { side = R(4, jj); depth = side.w; }
+            }
+            // alpha * 2^32 is exact scaling: the clamp decision equals alpha >= alpha_min
+            const float a32 = a * 4294967296.f;
+            if (B.in_img && a32 >= amin32 && ok != 0.f) {
+                acc.w += __float2ll_rn(a32);
+                acc.r += __float2ll_rn(a32 * cr);
+                acc.g += __float2ll_rn(a32 * cg);
+                acc.b += __float2ll_rn(a32 * cb);
+                if (kGeo) {
+                    acc.d += __float2ll_rn(a32 * depth);
+                    acc.nx += __float2ll_rn(a32 * side.x);
+                    acc.ny += __float2ll_rn(a32 * side.y);
+                    acc.nz += __float2ll_rn(a32 * side.z);
                 }
             }
         }
     }
-    if (!in_img) return;
+}
 
-    // ---------------- composite (Eq. 5) ----------------
+// Composite (Eq. 5) of one pixel and its outputs.
+template <int kS, bool kGeo>
+__device__ __forceinline__ void composite_store(const CamParams &C, const OptParams &O, const ViewScratch &X,
+                                                const WarpBlock<kS> &B, const SurfelZ<kS> &z, float bmax, float Ds,
+                                                const float *Cs, const GaussAcc &acc, float *__restrict__ out_rgb,
+                                                float *__restrict__ out_depth, int32_t *__restrict__ out_id,
+                                                float *__restrict__ aux, const GeoMaps &geo)
+{
     const float k32 = 2.3283064365386963e-10f;   // 2^-32
-    const float WG = __ll2float_rn(acc_w) * k32;
-    const float CG[3] = {__ll2float_rn(acc_r) * k32, __ll2float_rn(acc_g) * k32, __ll2float_rn(acc_b) * k32};
+    const float WG = __ll2float_rn(acc.w) * k32;
+    const float CG[3] = {__ll2float_rn(acc.r) * k32, __ll2float_rn(acc.g) * k32, __ll2float_rn(acc.b) * k32};
     float out[3];
     if (O.mode == GES_MODE_FULL) {
         const float inv = 1.f / (1.f + WG);
@@ -624,14 +650,14 @@ __device__ __forceinline__ void raster_tile(const ViewScratch &X, const CamParam
     } else {
         for (int c = 0; c < 3; ++c) out[c] = WG > 0.f ? CG[c] / WG : C.bg[c];
     }
-    const int64_t HW = (int64_t)C.W * C.H, pix = (int64_t)py * C.W + px;
+    const int64_t HW = (int64_t)C.W * C.H, pix = (int64_t)B.py * C.W + B.px;
     out_rgb[pix] = out[0];
     out_rgb[HW + pix] = out[1];
     out_rgb[2 * HW + pix] = out[2];
     if (out_depth) out_depth[pix] = Ds;
     if (out_id) {
 #pragma unroll
-        for (int k = 0; k < kS; ++k) out_id[k * HW + pix] = bid[k] != 0x7fffffff ? bid[k] : -1;
+        for (int k = 0; k < kS; ++k) out_id[k * HW + pix] = z.bid[k] != 0x7fffffff ? z.bid[k] : -1;
     }
     if (aux) aux[pix] = WG;
     if (kGeo) {
@@ -643,11 +669,11 @@ __device__ __forceinline__ void raster_tile(const ViewScratch &X, const CamParam
             int w = 0x7fffffff;
 #pragma unroll
             for (int k = 0; k < kS; ++k)
-                if (best[k] == bmax && bid[k] < w) w = bid[k];
+                if (z.best[k] == bmax && z.bid[k] < w) w = z.bid[k];
             surfel_normal(X.s_rec, w, C, ns);
         }
-        const float DG = __ll2float_rn(acc_d) * k32;
-        const float NG[3] = {__ll2float_rn(acc_nx) * k32, __ll2float_rn(acc_ny) * k32, __ll2float_rn(acc_nz) * k32};
+        const float DG = __ll2float_rn(acc.d) * k32;
+        const float NG[3] = {__ll2float_rn(acc.nx) * k32, __ll2float_rn(acc.ny) * k32, __ll2float_rn(acc.nz) * k32};
         const float ws = covered ? 1.f : 0.f, wt = ws + WG;
         if (geo.dg) geo.dg[pix] = DG;
         if (geo.dsm) geo.dsm[pix] = wt > 0.f ? ((covered ? Ds : 0.f) + DG) / wt : INFINITY;
@@ -657,6 +683,62 @@ __device__ __forceinline__ void raster_tile(const ViewScratch &X, const CamParam
             if (geo.nsm) geo.nsm[c * HW + pix] = wt > 0.f ? (ws * ns[c] + NG[c]) / wt : 0.f;
         }
     }
+}
+
+// One 16x16 tile with the CTA's shared staging (ss/sgs, structure of arrays):
+// all 8 warps stage a chunk of records together, then each warp runs its
+// 8x4 block over it.  kG: 3D Gaussians (EWA splats) or 2D Gaussians of
+// 2D-GES (ray-splat hit, planar depth).  kGeo: also the geometry maps of
+// Eq. 10-12.
+template <int kS, int kG, bool kGeo>
+__device__ __forceinline__ void raster_tile(const ViewScratch &X, const CamParams &C, const OptParams &O,
+                                            float *__restrict__ out_rgb, float *__restrict__ out_depth,
+                                            int32_t *__restrict__ out_id, float *__restrict__ aux,
+                                            const GeoMaps &geo, int tile,
+                                            float4 (*ss)[kChunk], float4 (*sgs)[kChunk])
+{
+    const unsigned warp = threadIdx.x >> 5, lane = lane_id();
+    const WarpBlock<kS> B(C, tile, warp, lane);
+    const bool do_s = O.mode != GES_MODE_GAUSSIANS_ONLY, do_g = O.mode != GES_MODE_SURFELS_ONLY;
+    const int s0 = do_s ? X.s_off[tile] : 0, s1 = do_s ? X.s_off[tile + 1] : 0;
+    const int g0 = do_g ? X.g_off[tile] : 0, g1 = do_g ? X.g_off[tile + 1] : 0;
+    const int t = threadIdx.x;
+
+    // first chunk of both lists together: one round trip, one barrier
+    if (s0 + t < s1) stage_rec(ss, X.s_rec, X.s_list[s0 + t], t);
+    if (g0 + t < g1) stage_gauss<kG, kGeo>(sgs, X, X.g_list[g0 + t], t);
+    __syncthreads();
+
+    // ---------------- pass 1: surfel z-buffer ----------------
+    SurfelZ<kS> z;
+    z.init(B.in_img);
+    const SoaRecs<4> RS{ss};
+    for (int base = s0; base < s1; base += kChunk) {
+        if (base != s0) {
+            __syncthreads();
+            if (base + t < s1) stage_rec(ss, X.s_rec, X.s_list[base + t], t);
+            __syncthreads();
+        }
+        if (B.wactive) surfel_pass<kS>(RS, min(kChunk, s1 - base), B, C.izn, lane, z);
+    }
+    float bmax, Ds, Cs[3];
+    surfel_resolve<kS>(z, B.in_img, X.s_rgb, C.bg, bmax, Ds, Cs);
+
+    // ---------------- pass 2: Gaussians (Eq. 2-4) ----------------
+    GaussAcc acc;
+    const float wmaxD = __uint_as_float(__reduce_max_sync(0xffffffffu, B.in_img ? __float_as_uint(Ds) : 0u));
+    const float amin32 = O.alpha_min * 4294967296.f;
+    const SoaRecs<gauss_planes<kG, kGeo>()> RG{sgs};
+    for (int base = g0; base < g1; base += kChunk) {
+        if (base != g0) {
+            __syncthreads();
+            if (base + t < g1) stage_gauss<kG, kGeo>(sgs, X, X.g_list[base + t], t);
+            __syncthreads();
+        }
+        if (B.wactive) gauss_pass<kS, kG, kGeo>(RG, min(kChunk, g1 - base), B, Ds, wmaxD, amin32, C.izn, lane, acc);
+    }
+    if (!B.in_img) return;
+    composite_store<kS, kGeo>(C, O, X, B, z, bmax, Ds, Cs, acc, out_rgb, out_depth, out_id, aux, geo);
 }
 
 template <int kS, int kG, bool kGeo>
@@ -785,6 +867,245 @@ __global__ void __launch_bounds__(kRasterThreads, kS == 1 && kG == 3 ? 5 : 4) k_
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Pipelined persistent raster (warp-specialised).  One producer warp takes
+// (view, tile) items from the counter and gathers each tile's records with
+// bulk asynchronous copies (cp.async.bulk, 64 B per record plus the 2D
+// Gaussians' 32 B of side data) into a ring of shared-memory stages; each
+// stage holds one chunk of one list and a header (view, tile, kind, count,
+// first/last chunk).  Eight consumer warps, one 8x4 block of the tile each,
+// walk the stages in order: pass 1 over the surfel stages, the resolve after
+// the last one, pass 2 over the Gaussian stages, the composite after the last.
+// A stage's "full" mbarrier completes when the producer has armed it and its
+// copies have landed; its "empty" mbarrier when all eight consumers are done
+// with it.  No CTA-wide barrier is left in the loop: a warp that finishes its
+// block early moves on to the next tile's stages while the others finish.
+// The per-pixel arithmetic is the per-view raster's (the same functions), so
+// the images are bitwise identical.
+//
+// Every wait is bounded: a wait that sees the CTA's abort flag or runs for
+// about a second gives up, records the failure in the batch's status words
+// and the warp leaves its loop; the producer first waits (bounded) for the
+// copies it has issued.
+
+constexpr int kPipeC = 128;                    // records per stage
+constexpr int kPipeStages = 4;
+constexpr int kPipeConsumers = 8;              // warps, one 8x4 block each
+constexpr int kPipeThreads = 32 * (kPipeConsumers + 1);
+enum : int { PK_SURFEL = 0, PK_GAUSS = 1, PK_END = 2 };
+enum : int { PF_FIRST = 1, PF_LAST = 2 };
+
+// bytes per record slot: 64 B record (+32 B side data for 2D Gaussians),
+// padded to an odd number of 16-byte units
+template <int kG>
+__host__ __device__ constexpr int pipe_slot() { return kG == 2 ? 112 : 80; }
+template <int kG>
+__host__ __device__ constexpr int pipe_ring_bytes() { return kPipeStages * kPipeC * pipe_slot<kG>(); }
+
+struct PipeHdr {
+    int view, tile, kind, n, flags, pad[3];
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(unsigned bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    return ok != 0u;
+}
+// Bounded wait for the phase of the given parity: false when the CTA's abort
+// flag is set or after about a second.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, const volatile int *abort)
+{
+    unsigned long long t0 = 0ull;
+    for (unsigned it = 0; it < (1u << 28); ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort) return false;
+        if ((it & 63u) == 63u) {
+            const unsigned long long t = global_timer_ns();
+            if (t0 == 0ull) t0 = t;
+            else if (t - t0 > 1000000000ull) return false;
+        }
+    }
+    return false;
+}
+// Global -> shared bulk copy completing on an mbarrier (both addresses 16-byte
+// aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned bytes, unsigned bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+template <int kS, int kG>
+__global__ void __launch_bounds__(kPipeThreads, kS == 1 ? 4 : 3)
+    k_braster_pipe(const BatchView *__restrict__ V, int n, OptParams O, unsigned *counter, int total)
+{
+    extern __shared__ __align__(128) unsigned char ring[];
+    __shared__ __align__(8) unsigned long long full[kPipeStages], empty[kPipeStages];
+    __shared__ PipeHdr hdr[kPipeStages];
+    __shared__ int abort_flag;
+    constexpr int kSlot = pipe_slot<kG>();
+    const unsigned warp = threadIdx.x >> 5, lane = lane_id();
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kPipeStages; ++s) {
+            mbar_init(smem_u32(&full[s]), 1u);
+            mbar_init(smem_u32(&empty[s]), (unsigned)kPipeConsumers);
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const volatile int *abort_p = &abort_flag;
+    auto give_up = [&](unsigned code) {
+        abort_flag = 1;
+        atomicOr(counter + 4, code);
+    };
+
+    if (warp == kPipeConsumers) {
+        // ---------------- producer ----------------
+        int stage = 0;
+        unsigned lap = 0;
+        bool ok = true;
+        // claim the next stage (bounded wait for its consumers), arm it
+        auto claim = [&](const PipeHdr &h, unsigned bytes) -> bool {
+            bool w = true;
+            if (lane == 0) w = mbar_wait(smem_u32(&empty[stage]), (lap & 1u) ^ 1u, abort_p);
+            w = __shfl_sync(0xffffffffu, w, 0);
+            if (!w) return false;
+            if (lane == 0) {
+                hdr[stage] = h;
+                mbar_arrive_tx(smem_u32(&full[stage]), bytes);
+            }
+            __syncwarp();
+            return true;
+        };
+        auto advance = [&]() {
+            if (++stage == kPipeStages) { stage = 0; ++lap; }
+        };
+        const bool do_s = O.mode != GES_MODE_GAUSSIANS_ONLY, do_g = O.mode != GES_MODE_SURFELS_ONLY;
+        while (ok) {
+            int item = 0, v = 0;
+            if (lane == 0) {
+                item = (int)atomicAdd(counter, 1u);
+                if (item < total) v = find_view(n, item, [&](int k) { return V[k].tile_base; });
+            }
+            item = __shfl_sync(0xffffffffu, item, 0);
+            v = __shfl_sync(0xffffffffu, v, 0);
+            if (item >= total) break;
+            const BatchView &bv = V[v];
+            if (*(volatile unsigned *)(bv.X.status + ST_FLAGS) & (FLAG_SOVF | FLAG_GOVF)) continue;
+            const int tile = item - bv.tile_base;
+            for (int kind = PK_SURFEL; kind <= PK_GAUSS && ok; ++kind) {
+                const bool on = kind == PK_SURFEL ? do_s : do_g;
+                const int *off = kind == PK_SURFEL ? bv.X.s_off : bv.X.g_off;
+                const int *list = kind == PK_SURFEL ? bv.X.s_list : bv.X.g_list;
+                const float4 *rec = kind == PK_SURFEL ? bv.X.s_rec : bv.X.g_rec;
+                const int a = on ? off[tile] : 0, b = on ? off[tile + 1] : 0;
+                const int nch = max(1, (b - a + kPipeC - 1) / kPipeC);
+                const unsigned per = (kind == PK_GAUSS && kG == 2) ? 96u : 64u;
+                for (int c = 0; c < nch; ++c) {
+                    const int cnt = max(0, min(kPipeC, b - a - c * kPipeC));
+                    const PipeHdr h{v, tile, kind, cnt, (c == 0 ? PF_FIRST : 0) | (c == nch - 1 ? PF_LAST : 0),
+                                    {0, 0, 0}};
+                    if (!claim(h, per * (unsigned)cnt)) { ok = false; break; }
+                    const unsigned dst0 = smem_u32(ring) + (unsigned)(stage * kPipeC * kSlot);
+                    const unsigned bar = smem_u32(&full[stage]);
+                    for (int j = (int)lane; j < cnt; j += 32) {
+                        const int id = list[a + c * kPipeC + j];
+                        bulk_g2s(dst0 + (unsigned)(j * kSlot), rec + 4 * (int64_t)id, 64u, bar);
+                        if (kind == PK_GAUSS && kG == 2)
+                            bulk_g2s(dst0 + (unsigned)(j * kSlot + 64), bv.X.g_aux + 2 * (int64_t)id, 32u, bar);
+                    }
+                    advance();
+                }
+            }
+        }
+        if (ok) {
+            ok = claim(PipeHdr{0, 0, PK_END, 0, 0, {0, 0, 0}}, 0u);
+            if (ok) advance();
+        }
+        if (!ok) {
+            if (lane == 0) give_up(2u);
+            // wait (bounded) for the copies this warp has issued: every
+            // stage's latest armed phase completes once its copies land
+            if (lane == 0) {
+                const volatile int never = 0;
+                for (int k = 0; k < kPipeStages; ++k) {
+                    // stage s was last armed in lap (s < stage ? lap : lap - 1)
+                    if (k >= stage && lap == 0u) continue;
+                    const unsigned l = k < stage ? lap : lap - 1u;
+                    mbar_wait(smem_u32(&full[k]), l & 1u, &never);
+                }
+            }
+        }
+        return;
+    }
+
+    // ---------------- consumers ----------------
+    int stage = 0;
+    unsigned lap = 0;
+    SurfelZ<kS> z;
+    z.init(false);
+    GaussAcc acc;
+    float bmax = 0.f, Ds = INFINITY, Cs[3] = {0.f, 0.f, 0.f}, wmaxD = 0.f;
+    const float amin32 = O.alpha_min * 4294967296.f;
+    for (;;) {
+        const bool got = mbar_wait(smem_u32(&full[stage]), lap & 1u, abort_p);
+        if (!__all_sync(0xffffffffu, got)) {
+            if (lane == 0) give_up(1u);
+            break;
+        }
+        const PipeHdr h = hdr[stage];
+        if (h.kind == PK_END) break;
+        const BatchView &bv = V[h.view];
+        const WarpBlock<kS> B(bv.C, h.tile, warp, lane);
+        const SlotRecs<kSlot> R{ring + stage * kPipeC * kSlot};
+        if (h.kind == PK_SURFEL) {
+            if (h.flags & PF_FIRST) z.init(B.in_img);
+            if (B.wactive) surfel_pass<kS>(R, h.n, B, bv.C.izn, lane, z);
+            if (h.flags & PF_LAST) {
+                surfel_resolve<kS>(z, B.in_img, bv.X.s_rgb, bv.C.bg, bmax, Ds, Cs);
+                wmaxD = __uint_as_float(__reduce_max_sync(0xffffffffu, B.in_img ? __float_as_uint(Ds) : 0u));
+                acc = GaussAcc();
+            }
+        } else {
+            if (B.wactive) gauss_pass<kS, kG, false>(R, h.n, B, Ds, wmaxD, amin32, bv.C.izn, lane, acc);
+            if (h.flags & PF_LAST) {
+                if (B.in_img)
+                    composite_store<kS, false>(bv.C, O, bv.X, B, z, bmax, Ds, Cs, acc, bv.rgb, bv.depth, nullptr,
+                                               nullptr, GeoMaps{});
+                // per-view completion time: the warp that finishes the view's last block stamps it
+                if (lane == 0 &&
+                    atomicAdd(bv.X.status + ST_RETIRED, 1u) + 1u == (unsigned)(kPipeConsumers * bv.T))
+                    *reinterpret_cast<unsigned long long *>(bv.X.status + ST_TDONE) = global_timer_ns();
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&empty[stage]));
+        if (++stage == kPipeStages) { stage = 0; ++lap; }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const OptParams &O, unsigned *work_counter,
@@ -809,7 +1130,18 @@ cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const Opt
     mark(3);
     // P.gdim: the Gaussian kind shared by all scenes of the batch
     const unsigned grid = P.raster_ctas;
-    if (O.samples == 4 && P.gdim == 2) k_braster<4, 2><<<grid, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
+    if (P.pipe) {
+        const size_t rb2 = pipe_ring_bytes<2>(), rb3 = pipe_ring_bytes<3>();
+        if (O.samples == 4 && P.gdim == 2)
+            k_braster_pipe<4, 2><<<grid, kPipeThreads, rb2, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
+        else if (O.samples == 4)
+            k_braster_pipe<4, 3><<<grid, kPipeThreads, rb3, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
+        else if (P.gdim == 2)
+            k_braster_pipe<1, 2><<<grid, kPipeThreads, rb2, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
+        else
+            k_braster_pipe<1, 3><<<grid, kPipeThreads, rb3, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
+    }
+    else if (O.samples == 4 && P.gdim == 2) k_braster<4, 2><<<grid, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
     else if (O.samples == 4) k_braster<4, 3><<<grid, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
     else if (P.gdim == 2) k_braster<1, 2><<<grid, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
     else k_braster<1, 3><<<grid, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
@@ -831,6 +1163,15 @@ cudaError_t prepare_forward_kernels()
         return e;
     if ((e = cudaFuncSetAttribute(k_fill_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)local_bins_smem(kLocalMaxTiles, true))) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_braster_pipe<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  pipe_ring_bytes<3>())) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_braster_pipe<4, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  pipe_ring_bytes<3>())) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_braster_pipe<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  pipe_ring_bytes<2>())) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_braster_pipe<4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  pipe_ring_bytes<2>())) != cudaSuccess)
         return e;
     return cudaFuncSetAttribute(k_bfill, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)local_bins_smem(kLocalMaxTiles, true));

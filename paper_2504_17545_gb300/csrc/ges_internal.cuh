@@ -112,6 +112,7 @@ struct BatchPlan {
     int total_tiles, total_prep, total_colscan, max_T;
     int raster_ctas;                         // persistent raster grid
     int gdim;                                // Gaussian kind of every scene (2 or 3; 0 reads as 3)
+    int pipe;                                // raster: 0 CTA-staged, 1 pipelined (producer warp + ring)
 };
 cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const OptParams &O, unsigned *work_counter,
                          cudaStream_t st, cudaEvent_t *ev /* 5 events or nullptr */);

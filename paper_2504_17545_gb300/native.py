@@ -67,7 +67,7 @@ class ges_stats(C.Structure):
 class ges_batch_info(C.Structure):
     _fields_ = [("n_views", C.c_int32), ("prims_per_cta", C.c_int32), ("raster_ctas_per_sm", C.c_int32),
                 ("candidates", C.c_int32), ("tuned_ms", C.c_double), ("h2d_bytes", C.c_int64),
-                ("d2h_bytes", C.c_int64)]
+                ("d2h_bytes", C.c_int64), ("raster_pipelined", C.c_int32), ("reserved", C.c_int32)]
 
 
 class ges_profile(C.Structure):
