@@ -34,32 +34,87 @@ __device__ __forceinline__ float warp_sum(float x)
 
 
 struct GLoop {
-    float px, py, pxl, pyl, la, lb, lc, sigma, key, r, g, b, ia, ib, ic;
+    float px, py, pxl, pyl, la, lb, lc, sigma, key, r, g, b;
     int x0, y0, x1, y1;
 };
+
+// n zeros from dst (16-byte stores when dst is 16-byte aligned and n % 4 == 0)
+__device__ __forceinline__ void store_zeros(float *dst, int n)
+{
+    if (((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) && (n & 3) == 0) {
+        float4 *d4 = reinterpret_cast<float4 *>(dst);
+        for (int k = 0; k < n / 4; ++k) d4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        for (int k = 0; k < n; ++k) dst[k] = 0.f;
+    }
+}
+
+// SH coefficient gradients of one primitive: dst[3k + c] = Y_k gc_c, zero for
+// the channels whose unclamped colour raw_c is not positive (raw null: no
+// gate).  A thread writes 3K consecutive floats, in 16-byte stores where the
+// row allows it (fewer, fuller memory transactions than scalar stores).
+__device__ __forceinline__ void store_sh_grad(float *dst, int K, const float *Y, const float *gc, const float *raw)
+{
+    float g[3];
+    for (int c = 0; c < 3; ++c) g[c] = (raw == nullptr || raw[c] > 0.f) ? gc[c] : 0.f;
+    if (((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) && ((3 * K) & 3) == 0) {
+        // 3K = 4 m: float4 number q holds entries 4q .. 4q + 3, i.e. basis
+        // functions (4q + e) / 3 and channels (4q + e) % 3
+        float4 *d4 = reinterpret_cast<float4 *>(dst);
+        for (int q = 0; q < (3 * K) / 4; ++q) {
+            float v[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int idx = 4 * q + e;
+                v[e] = Y[idx / 3] * g[idx % 3];
+            }
+            d4[q] = make_float4(v[0], v[1], v[2], v[3]);
+        }
+    } else {
+        for (int k = 0; k < K; ++k)
+            for (int c = 0; c < 3; ++c) dst[3 * k + c] = Y[k] * g[c];
+    }
+}
+
+// Per pixel, what every Gaussian term there needs: P = (k g, k g.C) with
+// k = 1/(1+W_G) (Eq. 5; 1/W_G in the Gaussians-only mode) and g = dL/dC.
+// Pixels with W_G = 0 get zeros: no Gaussian contributes there.
+__global__ void __launch_bounds__(256) k_pixgrad(int64_t HW, bool gmode, const float *__restrict__ dL,
+                                                const float *__restrict__ rgb, const float *__restrict__ aux,
+                                                float4 *__restrict__ P)
+{
+    const int64_t pix = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (pix >= HW) return;
+    const float W = __ldg(aux + pix);
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (W > 0.f) {
+        const float kk = gmode ? 1.f / W : 1.f / (1.f + W);
+        const float g0 = __ldg(dL + pix), g1 = __ldg(dL + HW + pix), g2 = __ldg(dL + 2 * HW + pix);
+        const float C0 = __ldg(rgb + pix), C1 = __ldg(rgb + HW + pix), C2 = __ldg(rgb + 2 * HW + pix);
+        p = make_float4(kk * g0, kk * g1, kk * g2, kk * (g0 * C0 + g1 * C1 + g2 * C2));
+    }
+    P[pix] = p;
+}
 
 // One pixel of one Gaussian: add its 2D-level gradients to acc (dc(3),
 // dsigma, dpx, dpy, dia, dib, dic).  Same alpha and depth test as the forward.
 __device__ __forceinline__ void gauss_pixel(const GLoop &s, int x, int y, const CamParams &C, const OptParams &O,
-                                            bool gmode, const float *__restrict__ dL,
-                                            const float *__restrict__ rgb, const float *__restrict__ depth,
-                                            const float *__restrict__ aux, float *acc)
+                                            const float4 *__restrict__ P, const float *__restrict__ depth,
+                                            float *acc)
 {
-    const int64_t HW = (int64_t)C.W * C.H, pix = (int64_t)y * C.W + x;
+    const int64_t pix = (int64_t)y * C.W + x;
     GaussRec g;
     g.px = s.px; g.py = s.py; g.pxl = s.pxl; g.pyl = s.pyl;
     g.la = s.la; g.lb = s.lb; g.lc = s.lc; g.sigma = s.sigma;
     float e;
     const float a = gauss_alpha(g, x + 0.5f, y + 0.5f, e);
     if (!(a >= O.alpha_min) || !(s.key < __ldg(depth + pix))) return;
-    const float W = __ldg(aux + pix);
-    const float kk = gmode ? 1.f / W : 1.f / (1.f + W);
-    const float g0 = __ldg(dL + pix), g1 = __ldg(dL + HW + pix), g2 = __ldg(dL + 2 * HW + pix);
-    const float C0 = __ldg(rgb + pix), C1 = __ldg(rgb + HW + pix), C2 = __ldg(rgb + 2 * HW + pix);
-    acc[0] += a * kk * g0;
-    acc[1] += a * kk * g1;
-    acc[2] += a * kk * g2;
-    const float dLda = kk * (g0 * (s.r - C0) + g1 * (s.g - C1) + g2 * (s.b - C2));
+    const float4 p = __ldg(P + pix);
+    acc[0] += a * p.x;
+    acc[1] += a * p.y;
+    acc[2] += a * p.z;
+    // dL/dalpha = k g.(c_i - C)
+    const float dLda = fmaf(s.r, p.x, fmaf(s.g, p.y, s.b * p.z)) - p.w;
     acc[3] += dLda * e;
     const float dLdq = -0.5f * dLda * a;
     const float dx = (x + 0.5f - s.px) - s.pxl, dy = (y + 0.5f - s.py) - s.pyl;
@@ -78,62 +133,103 @@ __device__ __forceinline__ void gauss_pixel(const GLoop &s, int x, int y, const 
 __device__ __forceinline__ float shfl_f(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 __device__ __forceinline__ int shfl_i(int v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
-__global__ void __launch_bounds__(256) k_gauss_bwd(SceneView S, CamParams C, OptParams O,
-                                                  const float *__restrict__ dL, const float *__restrict__ rgb,
-                                                  const float *__restrict__ depth, const float *__restrict__ aux,
-                                                  ges_grads G)
+// Gaussian backward in three launches.  k_gbwd_rec sets every Gaussian up
+// with the forward's device function and stores its raster record (an empty
+// bbox when it is not drawn).  k_gbwd_sweep: one thread per Gaussian, the
+// warp sweeps its 32 Gaussians' pixel bboxes one Gaussian at a time (one
+// pixel per lane, rows read coalesced) and reduces the per-lane partial sums
+// with a fixed butterfly into the owning lane, which stores its 9 sums; this
+// latency-bound loop runs light on registers, at full occupancy.
+// k_gbwd_chain runs the chain rule per Gaussian from those sums (set-up
+// recomputed).  The summation order is fixed, so the result is deterministic.
+__global__ void __launch_bounds__(256) k_gbwd_rec(SceneView S, CamParams C, OptParams O, float4 *__restrict__ rec)
 {
     const int64_t gi = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (gi >= S.M) return;
+    GaussOut o;
+    o.visible = false;
+    if (O.mode != GES_MODE_SURFELS_ONLY) gauss_setup(S, C, O, gi, o);
+    float4 *d = rec + 4 * gi;
+    if (!o.visible) {
+        // empty bbox: x0 = 1 > x1 = 0
+        d[3] = make_float4(0.f, __uint_as_float(1u), __uint_as_float(0u), 0.f);
+        return;
+    }
+    d[0] = make_float4(o.rec.px, o.rec.py, o.rec.pxl, o.rec.pyl);
+    d[1] = make_float4(o.rec.la, o.rec.lb, o.rec.lc, o.rec.sigma);
+    d[2] = make_float4(o.rec.key, o.rec.r, o.rec.g, o.rec.b);
+    d[3] = make_float4(0.f, __uint_as_float(o.rec.bb_lo), __uint_as_float(o.rec.bb_hi), 0.f);
+}
+
+__global__ void __launch_bounds__(256, 4) k_gbwd_sweep(int64_t M, CamParams C, OptParams O,
+                                                      const float4 *__restrict__ rec, const float4 *__restrict__ P,
+                                                      const float *__restrict__ depth, float *__restrict__ sums)
+{
+    const int64_t gi = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const int64_t g0 = gi - (threadIdx.x & 31);      // the warp's first Gaussian
     const int lane = threadIdx.x & 31;
-    const bool gmode = O.mode == GES_MODE_GAUSSIANS_ONLY;
-    // 1) set-up (the forward's definition), keep only what the sweep needs
-    GLoop s;
     bool vis = false;
-    if (gi < S.M && O.mode != GES_MODE_SURFELS_ONLY) {
-        GaussOut o;
-        gauss_setup(S, C, O, gi, o);
-        vis = o.visible;
-        if (vis) {
-            s = GLoop{o.rec.px, o.rec.py, o.rec.pxl, o.rec.pyl, o.rec.la, o.rec.lb, o.rec.lc, o.rec.sigma,
-                      o.rec.key, o.rec.r, o.rec.g, o.rec.b, o.ia, o.ib, o.ic, o.x0, o.y0, o.x1, o.y1};
-        }
+    if (gi < M) {
+        const float4 r3 = __ldg(rec + 4 * gi + 3);
+        const unsigned lo = __float_as_uint(r3.y), hi = __float_as_uint(r3.z);
+        vis = (lo & 0xffff) <= (hi & 0xffff) && (lo >> 16) <= (hi >> 16);
     }
     float acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    // 2) the whole warp sweeps one Gaussian's pixels at a time (rows are read
-    //    coalesced), then reduces with a fixed butterfly
     unsigned big = __ballot_sync(0xffffffffu, vis);
     while (big) {
         const int j = __ffs(big) - 1;
         big &= big - 1;
+        // Gaussian g0 + j: every lane reads the same record (a broadcast, from L1)
+        const float4 *rj = rec + 4 * (g0 + j);
+        const float4 r0 = __ldg(rj), r1 = __ldg(rj + 1), r2 = __ldg(rj + 2), r3 = __ldg(rj + 3);
         GLoop t;
-        t.px = shfl_f(s.px, j); t.py = shfl_f(s.py, j); t.pxl = shfl_f(s.pxl, j); t.pyl = shfl_f(s.pyl, j);
-        t.la = shfl_f(s.la, j); t.lb = shfl_f(s.lb, j); t.lc = shfl_f(s.lc, j); t.sigma = shfl_f(s.sigma, j);
-        t.key = shfl_f(s.key, j); t.r = shfl_f(s.r, j); t.g = shfl_f(s.g, j); t.b = shfl_f(s.b, j);
-        t.ia = shfl_f(s.ia, j); t.ib = shfl_f(s.ib, j); t.ic = shfl_f(s.ic, j);
-        t.x0 = shfl_i(s.x0, j); t.y0 = shfl_i(s.y0, j); t.x1 = shfl_i(s.x1, j); t.y1 = shfl_i(s.y1, j);
+        t.px = r0.x; t.py = r0.y; t.pxl = r0.z; t.pyl = r0.w;
+        t.la = r1.x; t.lb = r1.y; t.lc = r1.z; t.sigma = r1.w;
+        t.key = r2.x; t.r = r2.y; t.g = r2.z; t.b = r2.w;
+        const unsigned lo = __float_as_uint(r3.y), hi = __float_as_uint(r3.z);
+        t.x0 = lo & 0xffff; t.y0 = lo >> 16; t.x1 = hi & 0xffff; t.y1 = hi >> 16;
         const int w = t.x1 - t.x0 + 1, n = w * (t.y1 - t.y0 + 1);
         float part[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        for (int k = lane; k < n; k += 32) gauss_pixel(t, t.x0 + k % w, t.y0 + k / w, C, O, gmode, dL, rgb, depth, aux, part);
+        // pixel k of the bbox, row-major: row k / w and column k - w row.  The
+        // quotient from a float reciprocal is within one of the exact one for
+        // every bbox of an image of at most 16384^2 (k exact in float below
+        // 2^24; beyond, w >= 32), and the two fix-ups make it exact, so no
+        // integer division runs per pixel
+        const float iw = 1.f / (float)w;
+        for (int k = lane; k < n; k += 32) {
+            int r = (int)(((float)k + 0.5f) * iw);
+            r -= (r * w > k) ? 1 : 0;
+            r += ((r + 1) * w <= k) ? 1 : 0;
+            gauss_pixel(t, t.x0 + (k - r * w), t.y0 + r, C, O, P, depth, part);
+        }
         for (int c = 0; c < 9; ++c) {
             const float v = warp_sum(part[c]);
             if (lane == j) acc[c] = v;
         }
     }
+    if (gi < M)
+        for (int c = 0; c < 9; ++c) sums[(int64_t)c * M + gi] = acc[c];
+}
+
+__global__ void __launch_bounds__(256) k_gbwd_chain(SceneView S, CamParams C, OptParams O,
+                                                   const float *__restrict__ sums, ges_grads G)
+{
+    const int64_t gi = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (gi >= S.M) return;
     const int K = (S.deg + 1) * (S.deg + 1);
-    // 3) chain rule for this lane's Gaussian (set-up recomputed: fewer live registers in the sweep)
     GaussOut o;
     o.visible = false;
-    if (vis) gauss_setup(S, C, O, gi, o);
+    if (O.mode != GES_MODE_SURFELS_ONLY) gauss_setup(S, C, O, gi, o);
     if (!o.visible) {
         if (G.g_pos) for (int a = 0; a < 3; ++a) G.g_pos[3 * gi + a] = 0.f;
         if (G.g_rot) for (int a = 0; a < 4; ++a) G.g_rot[4 * gi + a] = 0.f;
         if (G.g_scale) for (int a = 0; a < 3; ++a) G.g_scale[3 * gi + a] = 0.f;
         if (G.g_opac) G.g_opac[gi] = 0.f;
-        if (G.g_sh) for (int a = 0; a < 3 * K; ++a) G.g_sh[3 * K * gi + a] = 0.f;
+        if (G.g_sh) store_zeros(G.g_sh + 3 * K * gi, 3 * K);
         return;
     }
-    const float *my = acc;
+    float my[9];
+    for (int c = 0; c < 9; ++c) my[c] = __ldg(sums + (int64_t)c * S.M + gi);
     const float *dc = my;
     float gp[3] = {0.f, 0.f, 0.f};
     // colour -> SH coefficients and position (through the view direction)
@@ -147,10 +243,10 @@ __global__ void __launch_bounds__(256) k_gauss_bwd(SceneView S, CamParams C, Opt
         for (int k = 0; k < K; ++k) {
             float sh[3];
             for (int c = 0; c < 3; ++c) sh[c] = load_attr(S.g_sh, 3 * K * gi + 3 * k + c, S.sh_dtype);
-            if (G.g_sh) for (int c = 0; c < 3; ++c) G.g_sh[3 * K * gi + 3 * k + c] = Y[k] * gc[c];
             const float w = sh[0] * gc[0] + sh[1] * gc[1] + sh[2] * gc[2];
             for (int a = 0; a < 3; ++a) gd[a] += w * dY[k][a];
         }
+        if (G.g_sh) store_sh_grad(G.g_sh + 3 * K * gi, K, Y, gc, nullptr);
         if (o.dist > 0.f) {
             const float pr = gd[0] * o.dir[0] + gd[1] * o.dir[1] + gd[2] * o.dir[2];
             for (int a = 0; a < 3; ++a) gp[a] -= (gd[a] - pr * o.dir[a]) / o.dist;
@@ -248,74 +344,117 @@ __global__ void __launch_bounds__(256) k_gauss_bwd(SceneView S, CamParams C, Opt
         for (int a = 0; a < 4; ++a) G.g_rot[4 * gi + a] = (gq[a] - pr * o.qn[a]) / o.qnorm;
 }
 
-__global__ void __launch_bounds__(256) k_surfel_bwd(SceneView S, CamParams C, OptParams O,
-                                                   const float *__restrict__ dL, const int32_t *__restrict__ sid,
-                                                   const float *__restrict__ aux, float *__restrict__ g_sh)
+// largest |x| (non-negative floats order like their bit patterns)
+__global__ void __launch_bounds__(256) k_absmax(const float *__restrict__ x, int64_t n, unsigned *out)
 {
-    const int64_t si = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    const int lane = threadIdx.x & 31;
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(x[i]));
+    for (int d = 16; d >= 1; d >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, d));
+    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(out, __float_as_uint(m));
+}
+
+// Surfel colour gradients, scatter form: dL/dc_s = sum over the samples s won
+// of k g / samples (k = 1/(1+W_G), or 1 with surfels only).  One thread per
+// pixel adds the term of each distinct winner among its samples to that
+// surfel's three sums, in 64-bit fixed point (units of gmax 2^-30, so one
+// term stays within 2^30): integer sums are exact, so the result does not
+// depend on the order of the atomics.
+__global__ void __launch_bounds__(256) k_surfel_scatter(int64_t N, CamParams C, OptParams O,
+                                                       const float *__restrict__ dL, const int32_t *__restrict__ sid,
+                                                       const float *__restrict__ aux,
+                                                       const unsigned *__restrict__ gmax_bits, long long *acc)
+{
     const int64_t HW = (int64_t)C.W * C.H;
+    const int64_t pix = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (pix >= HW) return;
+    const float gmax = __uint_as_float(*gmax_bits);
+    if (!(gmax > 0.f)) return;
+    const float g[3] = {__ldg(dL + pix), __ldg(dL + HW + pix), __ldg(dL + 2 * HW + pix)};
+    if (g[0] == 0.f && g[1] == 0.f && g[2] == 0.f) return;
+    const float scale = 1073741824.f / gmax;   // 2^30 / max |dL/dC|
     const bool full = O.mode == GES_MODE_FULL;
-    SurfelOut o;
-    o.visible = false;
-    if (si < S.N && O.mode != GES_MODE_GAUSSIANS_ONLY) surfel_setup(S, C, O, si, o);
-    const bool vis = o.visible;
-    int x0 = 0, y0 = 0, x1 = -1, y1 = -1;
-    if (vis) { x0 = o.x0; y0 = o.y0; x1 = o.x1; y1 = o.y1; }
-    float acc[3] = {0.f, 0.f, 0.f};
-    // dL/dc_s = sum over the samples s won of k g / samples (k = 1/(1+W_G),
-    // or 1 with surfels only); the warp sweeps one surfel's bbox at a time
-    unsigned big = __ballot_sync(0xffffffffu, vis);
-    while (big) {
-        const int j = __ffs(big) - 1;
-        big &= big - 1;
-        const int bx0 = shfl_i(x0, j), by0 = shfl_i(y0, j), bx1 = shfl_i(x1, j), by1 = shfl_i(y1, j);
-        const int32_t want = (int32_t)(si - lane + j);
-        const int w = bx1 - bx0 + 1, n = w * (by1 - by0 + 1);
-        float part[3] = {0.f, 0.f, 0.f};
-        for (int k = lane; k < n; k += 32) {
-            const int64_t pix = (int64_t)(by0 + k / w) * C.W + bx0 + k % w;
-            // with 4 samples each won sample carries a quarter of the pixel
-            int won = 0;
-            for (int q = 0; q < O.samples; ++q) won += __ldg(sid + q * HW + pix) == want;
-            if (won == 0) continue;
-            const float kk = (full ? 1.f / (1.f + __ldg(aux + pix)) : 1.f) * (float)won / (float)O.samples;
-            part[0] += kk * __ldg(dL + pix);
-            part[1] += kk * __ldg(dL + HW + pix);
-            part[2] += kk * __ldg(dL + 2 * HW + pix);
-        }
+    int32_t w[4];
+    for (int q = 0; q < O.samples; ++q) w[q] = __ldg(sid + q * HW + pix);
+    for (int q = 0; q < O.samples; ++q) {
+        const int32_t s = w[q];
+        if (s < 0 || (int64_t)s >= N) continue;
+        bool seen = false;
+        for (int r = 0; r < q; ++r) seen |= w[r] == s;
+        if (seen) continue;
+        // with 4 samples each won sample carries a quarter of the pixel
+        int won = 0;
+        for (int r = 0; r < O.samples; ++r) won += w[r] == s;
+        const float kk = (full ? 1.f / (1.f + __ldg(aux + pix)) : 1.f) * (float)won / (float)O.samples;
+        unsigned long long *a = reinterpret_cast<unsigned long long *>(acc + 3 * (int64_t)s);
         for (int c = 0; c < 3; ++c) {
-            const float v = warp_sum(part[c]);
-            if (lane == j) acc[c] = v;
+            const long long v = __float2ll_rn(kk * g[c] * scale);
+            if (v != 0) atomicAdd(a + c, (unsigned long long)v);
         }
     }
+}
+
+// Per surfel: the colour sums -> SH coefficients through Eq. 1 (zero where
+// the unclamped colour is not positive).  The view direction and the colour
+// are recomputed with the forward's functions, so the clamp gate is the
+// forward's.  A surfel that won no sample gets zeros.
+__global__ void __launch_bounds__(256) k_surfel_sh(SceneView S, CamParams C, const long long *__restrict__ acc,
+                                                  const unsigned *__restrict__ gmax_bits, float *__restrict__ g_sh)
+{
+    const int64_t si = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (si >= S.N) return;
     const int K = (S.deg + 1) * (S.deg + 1);
     float *out = g_sh + (int64_t)3 * K * si;
-    if (!vis) {
-        for (int a = 0; a < 3 * K; ++a) out[a] = 0.f;
+    const long long a0 = acc[3 * si], a1 = acc[3 * si + 1], a2 = acc[3 * si + 2];
+    if (a0 == 0 && a1 == 0 && a2 == 0) {
+        store_zeros(out, 3 * K);
         return;
     }
-    float Y[16];
-    sh_basis(K, o.dir[0], o.dir[1], o.dir[2], Y);
-    for (int k = 0; k < K; ++k)
-        for (int c = 0; c < 3; ++c) out[3 * k + c] = o.raw[c] > 0.f ? Y[k] * acc[c] : 0.f;
+    const float unit = __uint_as_float(*gmax_bits) * 9.31322574615478516e-10f;   // gmax 2^-30
+    const float gc[3] = {__ll2float_rn(a0) * unit, __ll2float_rn(a1) * unit, __ll2float_rn(a2) * unit};
+    float dir[3], L, Y[16], rgb[3], raw[3];
+    view_dir(C, __ldg(S.s_pos + 3 * si), __ldg(S.s_pos + 3 * si + 1), __ldg(S.s_pos + 3 * si + 2), dir, L);
+    sh_basis(K, dir[0], dir[1], dir[2], Y);
+    sh_colour(S.s_sh, si, K, S.sh_dtype, Y, rgb, raw);
+    store_sh_grad(out, K, Y, gc, raw);
 }
 
 }  // namespace
 
+cudaError_t launch_absmax(const float *x, int64_t n, unsigned *out, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess || n <= 0) return e;
+    k_absmax<<<152 * 4, 256, 0, st>>>(x, n, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_backward(const SceneView &S, const CamParams &C, const OptParams &O, const float *dL_drgb,
                             const float *out_rgb, const float *out_depth, const int32_t *surfel_id,
-                            const float *aux, const ges_grads &G, unsigned *status, cudaStream_t st,
-                            cudaEvent_t *ev)
+                            const float *aux, const ges_grads &G, long long *s_acc, unsigned *gmax,
+                            float4 *pixg, float4 *g_rec, float *g_sums, cudaStream_t st, cudaEvent_t *ev)
 {
-    (void)status;
     if (ev) cudaEventRecord(ev[0], st);
-    if (S.M > 0)
-        k_gauss_bwd<<<(unsigned)((S.M + 255) / 256), 256, 0, st>>>(S, C, O, dL_drgb, out_rgb, out_depth, aux, G);
+    if (S.M > 0) {
+        const int64_t HW = (int64_t)C.W * C.H;
+        k_pixgrad<<<(unsigned)((HW + 255) / 256), 256, 0, st>>>(HW, O.mode == GES_MODE_GAUSSIANS_ONLY, dL_drgb,
+                                                                out_rgb, aux, pixg);
+        const unsigned nb = (unsigned)((S.M + 255) / 256);
+        k_gbwd_rec<<<nb, 256, 0, st>>>(S, C, O, g_rec);
+        k_gbwd_sweep<<<nb, 256, 0, st>>>(S.M, C, O, g_rec, pixg, out_depth, g_sums);
+        k_gbwd_chain<<<nb, 256, 0, st>>>(S, C, O, g_sums, G);
+    }
     if (ev) cudaEventRecord(ev[1], st);
-    if (S.N > 0 && G.s_sh)
-        k_surfel_bwd<<<(unsigned)((S.N + 255) / 256), 256, 0, st>>>(S, C, O, dL_drgb, surfel_id, aux, G.s_sh);
+    if (S.N > 0 && G.s_sh) {
+        cudaError_t e = cudaMemsetAsync(s_acc, 0, sizeof(long long) * 3 * (size_t)S.N, st);
+        if (e != cudaSuccess) return e;
+        const int64_t HW = (int64_t)C.W * C.H;
+        if ((e = launch_absmax(dL_drgb, 3 * HW, gmax, st)) != cudaSuccess) return e;
+        if (O.mode != GES_MODE_GAUSSIANS_ONLY)
+            k_surfel_scatter<<<(unsigned)((HW + 255) / 256), 256, 0, st>>>(S.N, C, O, dL_drgb, surfel_id, aux, gmax,
+                                                                           s_acc);
+        k_surfel_sh<<<(unsigned)((S.N + 255) / 256), 256, 0, st>>>(S, C, s_acc, gmax, G.s_sh);
+    }
     if (ev) cudaEventRecord(ev[2], st);
     return cudaGetLastError();
 }

@@ -163,10 +163,16 @@ cudaError_t launch_count(const SceneView &S, const CamParams &C, const OptParams
 cudaError_t launch_filter3d(const SceneView &S, const CamParams *d_cams, int n_cams, float s3d, float *out,
                             unsigned *d_vmax, cudaStream_t st);
 
+// Scratch: s_acc 3 N 64-bit words (surfel colour sums), gmax one word,
+// pixg H W float4 (per-pixel terms of the Gaussian gradients), g_rec M
+// 64-byte records, g_sums 9 M floats (per-Gaussian sums of the sweep).
 cudaError_t launch_backward(const SceneView &S, const CamParams &C, const OptParams &O, const float *dL_drgb,
                             const float *out_rgb, const float *out_depth, const int32_t *surfel_id,
-                            const float *aux, const ges_grads &G, unsigned *status, cudaStream_t st,
+                            const float *aux, const ges_grads &G, long long *s_acc, unsigned *gmax,
+                            float4 *pixg, float4 *g_rec, float *g_sums, cudaStream_t st,
                             cudaEvent_t *ev /* 3 events or nullptr */);
+// *out = the bit pattern of max |x[i]| over n floats (0 for none); zeroes it first.
+cudaError_t launch_absmax(const float *x, int64_t n, unsigned *out, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // device helpers
@@ -454,6 +460,17 @@ struct __align__(16) GaussRec {
 };
 static_assert(sizeof(GaussRec) == 64 && alignof(GaussRec) == 16, "Gaussian record is 64 B, 16-aligned");
 
+// Eq. 1's view direction: the unit vector from the primitive's centre to the
+// camera, and their distance (zero direction at distance 0).  The one
+// definition used by the set-up and by the backward passes.
+__device__ __forceinline__ void view_dir(const CamParams &C, float px, float py, float pz, float *dir, float &L)
+{
+    const float vx = C.ocam[0] - px, vy = C.ocam[1] - py, vz = C.ocam[2] - pz;
+    L = sqrtf(vx * vx + vy * vy + vz * vz);
+    const float il = L > 0.f ? 1.f / L : 0.f;
+    dir[0] = vx * il; dir[1] = vy * il; dir[2] = vz * il;
+}
+
 struct SurfelOut {
     bool valid_quat;
     bool visible;
@@ -652,10 +669,8 @@ __device__ __forceinline__ void surfel_setup(const SceneView &S, const CamParams
     const float s1 = load_attr(S.s_scale, 2 * i, S.attr_dtype), s2 = load_attr(S.s_scale, 2 * i + 1, S.attr_dtype);
     // view direction for the SH colour: from the surfel centre to the camera
     {
-        float vx = C.ocam[0] - px, vy = C.ocam[1] - py, vz = C.ocam[2] - pz;
-        float L = sqrtf(vx * vx + vy * vy + vz * vz);
-        float il = L > 0.f ? 1.f / L : 0.f;
-        o.dir[0] = vx * il; o.dir[1] = vy * il; o.dir[2] = vz * il;
+        float L;
+        view_dir(C, px, py, pz, o.dir, L);
     }
     if (!(s1 > 0.f && s2 > 0.f && isfinite(s1) && isfinite(s2))) return;
     // camera-space frame (float) and centre (double-float)
@@ -733,13 +748,7 @@ __device__ __forceinline__ void gauss_setup(const SceneView &S, const CamParams 
             }
         }
     }
-    {
-        float vx = C.ocam[0] - px, vy = C.ocam[1] - py, vz = C.ocam[2] - pz;
-        float L = sqrtf(vx * vx + vy * vy + vz * vz);
-        float il = L > 0.f ? 1.f / L : 0.f;
-        o.dir[0] = vx * il; o.dir[1] = vy * il; o.dir[2] = vz * il;
-        o.dist = L;
-    }
+    view_dir(C, px, py, pz, o.dir, o.dist);
     // alpha <= sigma k3 k2 <= sigma k3 < alpha_min everywhere
     if (!(sigma * o.k3 >= O.alpha_min)) return;
     df t[3];
@@ -855,13 +864,7 @@ __device__ __forceinline__ void gauss2d_setup(const SceneView &S, const CamParam
     o.s[0] = s0; o.s[1] = s1; o.s[2] = 0.f;
     const float sigma = load_attr(S.g_opac, i, S.attr_dtype);
     o.sigma0 = sigma;
-    {
-        float vx = C.ocam[0] - px, vy = C.ocam[1] - py, vz = C.ocam[2] - pz;
-        float L = sqrtf(vx * vx + vy * vy + vz * vz);
-        float il = L > 0.f ? 1.f / L : 0.f;
-        o.dir[0] = vx * il; o.dir[1] = vy * il; o.dir[2] = vz * il;
-        o.dist = L;
-    }
+    view_dir(C, px, py, pz, o.dir, o.dist);
     if (!(sigma >= O.alpha_min)) return;            // sigma' <= sigma
     if (!(s0 > 0.f && s1 > 0.f && isfinite(s0) && isfinite(s1))) return;
     float tu[3], tv[3], n[3];

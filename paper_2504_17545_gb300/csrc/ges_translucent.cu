@@ -238,16 +238,6 @@ __global__ void __launch_bounds__(kRasterThreads, 4)
     if (cover && has_front) atomicAdd(cover + fid, 1);
 }
 
-// largest |dL/dC| (non-negative floats order like their bit patterns)
-__global__ void __launch_bounds__(256) k_tgmax(const float *__restrict__ g, int64_t n, unsigned *gmax)
-{
-    float m = 0.f;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        m = fmaxf(m, fabsf(g[i]));
-    for (int d = 16; d >= 1; d >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, d));
-    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(gmax, __float_as_uint(m));
-}
-
 __device__ __forceinline__ float warp_sum(float x)
 {
     for (int d = 16; d >= 1; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
@@ -572,9 +562,7 @@ cudaError_t launch_translucent_backward(const SceneView &S, const CamParams &C, 
     k_tsort<<<T, 256, 0, st>>>(X.s_off, keys, X.s_list, X.status);
     if ((e = cudaMemsetAsync(acc, 0, sizeof(long long) * kTAcc * (size_t)(S.N > 0 ? S.N : 1), st)) != cudaSuccess)
         return e;
-    if ((e = cudaMemsetAsync(gmax, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
-    const int64_t n = 3 * (int64_t)C.W * C.H;
-    k_tgmax<<<152 * 4, 256, 0, st>>>(dL, n, gmax);
+    if ((e = launch_absmax(dL, 3 * (int64_t)C.W * C.H, gmax, st)) != cudaSuccess) return e;
     if (front_first) k_tbwd<true><<<T, kRasterThreads, 0, st>>>(X, C, Os, w, dL, in_T, in_front, in_last, in_Tlast, gmax, acc);
     else k_tbwd<false><<<T, kRasterThreads, 0, st>>>(X, C, Os, w, dL, in_T, in_front, in_last, in_Tlast, gmax, acc);
     if (S.N > 0)
