@@ -32,11 +32,67 @@ __device__ __forceinline__ float warp_sum(float x)
     return x;
 }
 
+// Sums the 9 values v over the warp and stores total c at dst[c * stride].
+// A halving exchange: at each of the xor-16, 8, 4, 2 steps a lane keeps one
+// part of its values (by its lane bit) and adds the partner's copy of that
+// part, sending the other part (5, 3, 2 and 1 shuffles; missing slots are
+// zero); a last xor-1 step completes the sum.  Lane l then holds total
+// (l & 16 ? 5 : 0) + (l & 8 ? 3 : 0) + (l & 4 ? 2 : 0) + (l & 2 ? 1 : 0)
+// where that index addresses a real slot at every step; the even lane of the
+// pair stores it.  12 shuffles instead of 45 for nine butterflies, and a
+// fixed order, so the result is deterministic.
+__device__ __forceinline__ void warp_reduce9_store(const float *v, int lane, float *dst, int64_t stride)
+{
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+    float k1[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const float lo = v[i], hi = i + 5 < 9 ? v[i + 5] : 0.f;
+        k1[i] = (b4 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b4 ? lo : hi, 16);
+    }
+    float k2[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float lo = k1[i], hi = i + 3 < 5 ? k1[i + 3] : 0.f;
+        k2[i] = (b3 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b3 ? lo : hi, 8);
+    }
+    float k3[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float lo = k2[i], hi = i + 2 < 3 ? k2[i + 2] : 0.f;
+        k3[i] = (b2 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b2 ? lo : hi, 4);
+    }
+    float k4 = (b1 ? k3[1] : k3[0]) + __shfl_xor_sync(0xffffffffu, b1 ? k3[0] : k3[1], 2);
+    k4 += __shfl_xor_sync(0xffffffffu, k4, 1);
+    const int s2 = (b2 ? 2 : 0) + (b1 ? 1 : 0);     // slot in k2
+    const int s1 = (b3 ? 3 : 0) + s2;               // slot in k1
+    const int idx = (b4 ? 5 : 0) + s1;              // value index
+    if ((lane & 1) == 0 && s2 < 3 && s1 < 5 && idx < 9) dst[idx * stride] = k4;
+}
+
 
 struct GLoop {
     float px, py, pxl, pyl, la, lb, lc, sigma, key, r, g, b;
     int x0, y0, x1, y1;
 };
+
+// gd = sum_k (SH_k . gc) grad Y_k at the unit direction dir: the SH row is
+// read in index order and the basis gradients are those of sh_basis_grad
+// (compile-time K: no per-k array in local memory).
+template <int K>
+__device__ __forceinline__ void sh_weighted_grad(const void *sh, int64_t i, int dtype, const float *gc,
+                                                 const float *dir, float *gd)
+{
+    float dY[K][3];
+    sh_basis_grad(K, dir[0], dir[1], dir[2], dY);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float c[3];
+        for (int q = 0; q < 3; ++q) c[q] = load_attr(sh, (int64_t)3 * K * i + 3 * k + q, dtype);
+        const float w = c[0] * gc[0] + c[1] * gc[1] + c[2] * gc[2];
+        for (int a = 0; a < 3; ++a) gd[a] += w * dY[k][a];
+    }
+}
 
 // n zeros from dst (16-byte stores when dst is 16-byte aligned and n % 4 == 0)
 __device__ __forceinline__ void store_zeros(float *dst, int n)
@@ -174,7 +230,8 @@ __global__ void __launch_bounds__(256, 4) k_gbwd_sweep(int64_t M, CamParams C, O
         const unsigned lo = __float_as_uint(r3.y), hi = __float_as_uint(r3.z);
         vis = (lo & 0xffff) <= (hi & 0xffff) && (lo >> 16) <= (hi >> 16);
     }
-    float acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (gi < M && !vis)
+        for (int c = 0; c < 9; ++c) sums[(int64_t)c * M + gi] = 0.f;
     unsigned big = __ballot_sync(0xffffffffu, vis);
     while (big) {
         const int j = __ffs(big) - 1;
@@ -202,16 +259,11 @@ __global__ void __launch_bounds__(256, 4) k_gbwd_sweep(int64_t M, CamParams C, O
             r += ((r + 1) * w <= k) ? 1 : 0;
             gauss_pixel(t, t.x0 + (k - r * w), t.y0 + r, C, O, P, depth, part);
         }
-        for (int c = 0; c < 9; ++c) {
-            const float v = warp_sum(part[c]);
-            if (lane == j) acc[c] = v;
-        }
+        warp_reduce9_store(part, lane, sums + g0 + j, M);
     }
-    if (gi < M)
-        for (int c = 0; c < 9; ++c) sums[(int64_t)c * M + gi] = acc[c];
 }
 
-__global__ void __launch_bounds__(256) k_gbwd_chain(SceneView S, CamParams C, OptParams O,
+__global__ void __launch_bounds__(256, 3) k_gbwd_chain(SceneView S, CamParams C, OptParams O,
                                                    const float *__restrict__ sums, ges_grads G)
 {
     const int64_t gi = (int64_t)blockIdx.x * 256 + threadIdx.x;
@@ -234,17 +286,16 @@ __global__ void __launch_bounds__(256) k_gbwd_chain(SceneView S, CamParams C, Op
     float gp[3] = {0.f, 0.f, 0.f};
     // colour -> SH coefficients and position (through the view direction)
     {
-        float Y[16], dY[16][3];
+        float Y[16];
         sh_basis(K, o.dir[0], o.dir[1], o.dir[2], Y);
-        sh_basis_grad(K, o.dir[0], o.dir[1], o.dir[2], dY);
         float gc[3];
         for (int c = 0; c < 3; ++c) gc[c] = o.raw[c] > 0.f ? dc[c] : 0.f;
         float gd[3] = {0.f, 0.f, 0.f};
-        for (int k = 0; k < K; ++k) {
-            float sh[3];
-            for (int c = 0; c < 3; ++c) sh[c] = load_attr(S.g_sh, 3 * K * gi + 3 * k + c, S.sh_dtype);
-            const float w = sh[0] * gc[0] + sh[1] * gc[1] + sh[2] * gc[2];
-            for (int a = 0; a < 3; ++a) gd[a] += w * dY[k][a];
+        switch (K) {
+        case 16: sh_weighted_grad<16>(S.g_sh, gi, S.sh_dtype, gc, o.dir, gd); break;
+        case 9: sh_weighted_grad<9>(S.g_sh, gi, S.sh_dtype, gc, o.dir, gd); break;
+        case 4: sh_weighted_grad<4>(S.g_sh, gi, S.sh_dtype, gc, o.dir, gd); break;
+        default: break;   // degree 0: the colour does not depend on the direction
         }
         if (G.g_sh) store_sh_grad(G.g_sh + 3 * K * gi, K, Y, gc, nullptr);
         if (o.dist > 0.f) {
@@ -340,8 +391,16 @@ __global__ void __launch_bounds__(256) k_gbwd_chain(SceneView S, CamParams C, Op
     gq[3] = 2.f * (-2.f * qz * GR[0][0] - w * GR[0][1] + qx * GR[0][2] + w * GR[1][0] - 2.f * qz * GR[1][1] +
                    qy * GR[1][2] + qx * GR[2][0] + qy * GR[2][1]);
     const float pr = gq[0] * w + gq[1] * qx + gq[2] * qy + gq[3] * qz;
-    if (G.g_rot)
-        for (int a = 0; a < 4; ++a) G.g_rot[4 * gi + a] = (gq[a] - pr * o.qn[a]) / o.qnorm;
+    if (G.g_rot) {
+        const float4 r4 = make_float4((gq[0] - pr * o.qn[0]) / o.qnorm, (gq[1] - pr * o.qn[1]) / o.qnorm,
+                                      (gq[2] - pr * o.qn[2]) / o.qnorm, (gq[3] - pr * o.qn[3]) / o.qnorm);
+        if ((reinterpret_cast<uintptr_t>(G.g_rot) & 15u) == 0) {
+            reinterpret_cast<float4 *>(G.g_rot)[gi] = r4;
+        } else {
+            G.g_rot[4 * gi] = r4.x; G.g_rot[4 * gi + 1] = r4.y;
+            G.g_rot[4 * gi + 2] = r4.z; G.g_rot[4 * gi + 3] = r4.w;
+        }
+    }
 }
 
 // largest |x| (non-negative floats order like their bit patterns)
