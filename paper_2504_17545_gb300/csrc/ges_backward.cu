@@ -26,111 +26,10 @@ namespace ges {
 
 namespace {
 
-__device__ __forceinline__ float warp_sum(float x)
-{
-    for (int d = 16; d >= 1; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
-    return x;
-}
-
-// Sums the 9 values v over the warp and stores total c at dst[c * stride].
-// A halving exchange: at each of the xor-16, 8, 4, 2 steps a lane keeps one
-// part of its values (by its lane bit) and adds the partner's copy of that
-// part, sending the other part (5, 3, 2 and 1 shuffles; missing slots are
-// zero); a last xor-1 step completes the sum.  Lane l then holds total
-// (l & 16 ? 5 : 0) + (l & 8 ? 3 : 0) + (l & 4 ? 2 : 0) + (l & 2 ? 1 : 0)
-// where that index addresses a real slot at every step; the even lane of the
-// pair stores it.  12 shuffles instead of 45 for nine butterflies, and a
-// fixed order, so the result is deterministic.
-__device__ __forceinline__ void warp_reduce9_store(const float *v, int lane, float *dst, int64_t stride)
-{
-    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
-    float k1[5];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-        const float lo = v[i], hi = i + 5 < 9 ? v[i + 5] : 0.f;
-        k1[i] = (b4 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b4 ? lo : hi, 16);
-    }
-    float k2[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const float lo = k1[i], hi = i + 3 < 5 ? k1[i + 3] : 0.f;
-        k2[i] = (b3 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b3 ? lo : hi, 8);
-    }
-    float k3[2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const float lo = k2[i], hi = i + 2 < 3 ? k2[i + 2] : 0.f;
-        k3[i] = (b2 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b2 ? lo : hi, 4);
-    }
-    float k4 = (b1 ? k3[1] : k3[0]) + __shfl_xor_sync(0xffffffffu, b1 ? k3[0] : k3[1], 2);
-    k4 += __shfl_xor_sync(0xffffffffu, k4, 1);
-    const int s2 = (b2 ? 2 : 0) + (b1 ? 1 : 0);     // slot in k2
-    const int s1 = (b3 ? 3 : 0) + s2;               // slot in k1
-    const int idx = (b4 ? 5 : 0) + s1;              // value index
-    if ((lane & 1) == 0 && s2 < 3 && s1 < 5 && idx < 9) dst[idx * stride] = k4;
-}
-
-
 struct GLoop {
     float px, py, pxl, pyl, la, lb, lc, sigma, key, r, g, b;
     int x0, y0, x1, y1;
 };
-
-// gd = sum_k (SH_k . gc) grad Y_k at the unit direction dir: the SH row is
-// read in index order and the basis gradients are those of sh_basis_grad
-// (compile-time K: no per-k array in local memory).
-template <int K>
-__device__ __forceinline__ void sh_weighted_grad(const void *sh, int64_t i, int dtype, const float *gc,
-                                                 const float *dir, float *gd)
-{
-    float dY[K][3];
-    sh_basis_grad(K, dir[0], dir[1], dir[2], dY);
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        float c[3];
-        for (int q = 0; q < 3; ++q) c[q] = load_attr(sh, (int64_t)3 * K * i + 3 * k + q, dtype);
-        const float w = c[0] * gc[0] + c[1] * gc[1] + c[2] * gc[2];
-        for (int a = 0; a < 3; ++a) gd[a] += w * dY[k][a];
-    }
-}
-
-// n zeros from dst (16-byte stores when dst is 16-byte aligned and n % 4 == 0)
-__device__ __forceinline__ void store_zeros(float *dst, int n)
-{
-    if (((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) && (n & 3) == 0) {
-        float4 *d4 = reinterpret_cast<float4 *>(dst);
-        for (int k = 0; k < n / 4; ++k) d4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    } else {
-        for (int k = 0; k < n; ++k) dst[k] = 0.f;
-    }
-}
-
-// SH coefficient gradients of one primitive: dst[3k + c] = Y_k gc_c, zero for
-// the channels whose unclamped colour raw_c is not positive (raw null: no
-// gate).  A thread writes 3K consecutive floats, in 16-byte stores where the
-// row allows it (fewer, fuller memory transactions than scalar stores).
-__device__ __forceinline__ void store_sh_grad(float *dst, int K, const float *Y, const float *gc, const float *raw)
-{
-    float g[3];
-    for (int c = 0; c < 3; ++c) g[c] = (raw == nullptr || raw[c] > 0.f) ? gc[c] : 0.f;
-    if (((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) && ((3 * K) & 3) == 0) {
-        // 3K = 4 m: float4 number q holds entries 4q .. 4q + 3, i.e. basis
-        // functions (4q + e) / 3 and channels (4q + e) % 3
-        float4 *d4 = reinterpret_cast<float4 *>(dst);
-        for (int q = 0; q < (3 * K) / 4; ++q) {
-            float v[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int idx = 4 * q + e;
-                v[e] = Y[idx / 3] * g[idx % 3];
-            }
-            d4[q] = make_float4(v[0], v[1], v[2], v[3]);
-        }
-    } else {
-        for (int k = 0; k < K; ++k)
-            for (int c = 0; c < 3; ++c) dst[3 * k + c] = Y[k] * g[c];
-    }
-}
 
 // Per pixel, what every Gaussian term there needs: P = (k g, k g.C) with
 // k = 1/(1+W_G) (Eq. 5; 1/W_G in the Gaussians-only mode) and g = dL/dC.
@@ -186,8 +85,6 @@ __device__ __forceinline__ void gauss_pixel(const GLoop &s, int x, int y, const 
     acc[8] += dLdq * dy * dy;
 }
 
-__device__ __forceinline__ float shfl_f(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
-__device__ __forceinline__ int shfl_i(int v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
 // Gaussian backward in three launches.  k_gbwd_rec sets every Gaussian up
 // with the forward's device function and stores its raster record (an empty
@@ -259,7 +156,8 @@ __global__ void __launch_bounds__(256, 4) k_gbwd_sweep(int64_t M, CamParams C, O
             r += ((r + 1) * w <= k) ? 1 : 0;
             gauss_pixel(t, t.x0 + (k - r * w), t.y0 + r, C, O, P, depth, part);
         }
-        warp_reduce9_store(part, lane, sums + g0 + j, M);
+        float *dst = sums + g0 + j;
+        warp_reduce_scatter<9>(part, lane, [&](int c, float tot) { dst[(int64_t)c * M] = tot; });
     }
 }
 

@@ -911,6 +911,104 @@ __device__ __forceinline__ void gauss2d_setup(const SceneView &S, const CamParam
     o.visible = true;
 }
 
+// Sums NV <= 32 per-lane values over the warp and hands total i to exactly
+// one lane, as f(i, total).  A halving exchange: at the xor-16, 8, 4, 2 and 1
+// steps a lane keeps the lower or the upper part of its slots (by its lane
+// bit), adds the partner's copy of that part and sends the other part
+// (ceil(n/2) shuffles per step, missing slots zero): 20 shuffles for 18
+// values instead of 90 for 18 butterflies.  The order is fixed, so the
+// result is deterministic.
+template <int NV, class F>
+__device__ __forceinline__ void warp_reduce_scatter(const float *v, int lane, F f)
+{
+    constexpr int n1 = (NV + 1) / 2, n2 = (n1 + 1) / 2, n3 = (n2 + 1) / 2, n4 = (n3 + 1) / 2;
+    static_assert(NV >= 1 && NV <= 32, "1 to 32 values");
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2, b0 = lane & 1;
+    float a1[n1], a2[n2], a3[n3], a4[n4];
+#pragma unroll
+    for (int i = 0; i < n1; ++i) {
+        const float lo = v[i], hi = i + n1 < NV ? v[i + n1] : 0.f;
+        a1[i] = (b4 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b4 ? lo : hi, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < n2; ++i) {
+        const float lo = a1[i], hi = i + n2 < n1 ? a1[i + n2] : 0.f;
+        a2[i] = (b3 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b3 ? lo : hi, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < n3; ++i) {
+        const float lo = a2[i], hi = i + n3 < n2 ? a2[i + n3] : 0.f;
+        a3[i] = (b2 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b2 ? lo : hi, 4);
+    }
+#pragma unroll
+    for (int i = 0; i < n4; ++i) {
+        const float lo = a3[i], hi = i + n4 < n3 ? a3[i + n4] : 0.f;
+        a4[i] = (b1 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b1 ? lo : hi, 2);
+    }
+    const float lo = a4[0], hi = n4 > 1 ? a4[n4 - 1] : 0.f;
+    const float tot = (b0 ? hi : lo) + __shfl_xor_sync(0xffffffffu, b0 ? lo : hi, 1);
+    // the slot this lane ends with, level by level
+    const int s4 = b0 ? 1 : 0, s3 = (b1 ? n4 : 0) + s4, s2 = (b2 ? n3 : 0) + s3;
+    const int s1 = (b3 ? n2 : 0) + s2, s0 = (b4 ? n1 : 0) + s1;
+    if (s4 < n4 && s3 < n3 && s2 < n2 && s1 < n1 && s0 < NV) f(s0, tot);
+}
+
+// gd = sum_k (SH_k . gc) grad Y_k at the unit direction dir: the SH row is
+// read in index order and the basis gradients are those of sh_basis_grad
+// (compile-time K: no per-k array in local memory).
+template <int K>
+__device__ __forceinline__ void sh_weighted_grad(const void *sh, int64_t i, int dtype, const float *gc,
+                                                 const float *dir, float *gd)
+{
+    float dY[K][3];
+    sh_basis_grad(K, dir[0], dir[1], dir[2], dY);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float c[3];
+        for (int q = 0; q < 3; ++q) c[q] = load_attr(sh, (int64_t)3 * K * i + 3 * k + q, dtype);
+        const float w = c[0] * gc[0] + c[1] * gc[1] + c[2] * gc[2];
+        for (int a = 0; a < 3; ++a) gd[a] += w * dY[k][a];
+    }
+}
+
+// n zeros from dst (16-byte stores when dst is 16-byte aligned and n % 4 == 0)
+__device__ __forceinline__ void store_zeros(float *dst, int n)
+{
+    if (((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) && (n & 3) == 0) {
+        float4 *d4 = reinterpret_cast<float4 *>(dst);
+        for (int k = 0; k < n / 4; ++k) d4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        for (int k = 0; k < n; ++k) dst[k] = 0.f;
+    }
+}
+
+// SH coefficient gradients of one primitive: dst[3k + c] = Y_k gc_c, zero for
+// the channels whose unclamped colour raw_c is not positive (raw null: no
+// gate).  A thread writes 3K consecutive floats, in 16-byte stores where the
+// row allows it (fewer, fuller memory transactions than scalar stores).
+__device__ __forceinline__ void store_sh_grad(float *dst, int K, const float *Y, const float *gc, const float *raw)
+{
+    float g[3];
+    for (int c = 0; c < 3; ++c) g[c] = (raw == nullptr || raw[c] > 0.f) ? gc[c] : 0.f;
+    if (((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) && ((3 * K) & 3) == 0) {
+        // 3K = 4 m: float4 number q holds entries 4q .. 4q + 3, i.e. basis
+        // functions (4q + e) / 3 and channels (4q + e) % 3
+        float4 *d4 = reinterpret_cast<float4 *>(dst);
+        for (int q = 0; q < (3 * K) / 4; ++q) {
+            float v[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int idx = 4 * q + e;
+                v[e] = Y[idx / 3] * g[idx % 3];
+            }
+            d4[q] = make_float4(v[0], v[1], v[2], v[3]);
+        }
+    } else {
+        for (int k = 0; k < K; ++k)
+            for (int c = 0; c < 3; ++c) dst[3 * k + c] = Y[k] * g[c];
+    }
+}
+
 // Eq. 4 at pixel centre (u, v): the one definition used by forward and backward.
 __device__ __forceinline__ float gauss_alpha(const GaussRec &g, float u, float v, float &e)
 {

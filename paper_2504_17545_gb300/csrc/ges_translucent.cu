@@ -238,12 +238,6 @@ __global__ void __launch_bounds__(kRasterThreads, 4)
     if (cover && has_front) atomicAdd(cover + fid, 1);
 }
 
-__device__ __forceinline__ float warp_sum(float x)
-{
-    for (int d = 16; d >= 1; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
-    return x;
-}
-
 // the 18 per-(pixel, surfel) gradient terms: gP(3) gU(3) gV(3) gN(3) gs1 gs2 gw gc(3), camera space
 __device__ __forceinline__ void t_terms(const float4 *fr, float a, float G, float wv, float T, float iz,
                                         const float *g, const float *cS, const float *col, float u, float v,
@@ -368,8 +362,12 @@ __global__ void __launch_bounds__(kRasterThreads, 2)
             if (!__any_sync(0xffffffffu, contrib)) continue;
             if (!contrib)
                 for (int k = 0; k < kTAcc; ++k) terms[k] = 0.f;
-            for (int k = 0; k < kTAcc; ++k) terms[k] = warp_sum(terms[k]);
-            if (lane == 0) t_add(acc, id, terms, scale);
+            // the warp's 18 sums, each added by the lane that ends up holding it
+            unsigned long long *ak = reinterpret_cast<unsigned long long *>(acc + (int64_t)kTAcc * id);
+            warp_reduce_scatter<kTAcc>(terms, (int)lane, [&](int k, float tot) {
+                const float x = tot * scale;
+                if (x != 0.f) atomicAdd(ak + k, (unsigned long long)__float2ll_rn(x));
+            });
         }
     }
     // the frontmost surfel, blended first (T = 1)
@@ -400,6 +398,17 @@ __global__ void __launch_bounds__(256) k_tfinal(SceneView S, CamParams C, const 
     float A[kTAcc];
     for (int k = 0; k < kTAcc; ++k) A[k] = (float)acc[(int64_t)kTAcc * i + k] * inv;
     const int K = (S.deg + 1) * (S.deg + 1);
+    bool any = false;
+    for (int k = 0; k < kTAcc; ++k) any |= A[k] != 0.f;
+    if (!any) {
+        // no pixel sent a gradient: zeros, without reading the SH row
+        if (g_pos) for (int a = 0; a < 3; ++a) g_pos[3 * i + a] = 0.f;
+        if (g_scale) { g_scale[2 * i] = 0.f; g_scale[2 * i + 1] = 0.f; }
+        if (g_w) g_w[i] = 0.f;
+        if (g_rot) for (int a = 0; a < 4; ++a) g_rot[4 * i + a] = 0.f;
+        if (g_sh) store_zeros(g_sh + 3 * K * i, 3 * K);
+        return;
+    }
     float q[4], R[9], qn[4], qnorm;
     for (int k = 0; k < 4; ++k) q[k] = load_attr(S.s_rot, 4 * i + k, S.attr_dtype);
     const bool okq = quat_to_rot(q[0], q[1], q[2], q[3], R, qn, &qnorm);
@@ -408,30 +417,22 @@ __global__ void __launch_bounds__(256) k_tfinal(SceneView S, CamParams C, const 
     if (g_scale) { g_scale[2 * i] = A[12]; g_scale[2 * i + 1] = A[13]; }
     if (g_w) g_w[i] = A[14];
     // colour -> SH coefficients and position (through the view direction)
-    const float px = __ldg(S.s_pos + 3 * i), py = __ldg(S.s_pos + 3 * i + 1), pz = __ldg(S.s_pos + 3 * i + 2);
-    float dir[3];
-    float dist;
-    {
-        const float vx = C.ocam[0] - px, vy = C.ocam[1] - py, vz = C.ocam[2] - pz;
-        dist = sqrtf(vx * vx + vy * vy + vz * vz);
-        const float il = dist > 0.f ? 1.f / dist : 0.f;
-        dir[0] = vx * il; dir[1] = vy * il; dir[2] = vz * il;
-    }
-    float Y[16], dY[16][3];
+    float dir[3], dist;
+    view_dir(C, __ldg(S.s_pos + 3 * i), __ldg(S.s_pos + 3 * i + 1), __ldg(S.s_pos + 3 * i + 2), dir, dist);
+    float Y[16];
     sh_basis(K, dir[0], dir[1], dir[2], Y);
-    sh_basis_grad(K, dir[0], dir[1], dir[2], dY);
     float rgb[3], raw[3];
     sh_colour(S.s_sh, i, K, S.sh_dtype, Y, rgb, raw);
     float gc[3];
     for (int c = 0; c < 3; ++c) gc[c] = raw[c] > 0.f ? A[15 + c] : 0.f;
     float gd[3] = {0.f, 0.f, 0.f};
-    for (int k = 0; k < K; ++k) {
-        float sh[3];
-        for (int c = 0; c < 3; ++c) sh[c] = load_attr(S.s_sh, 3 * K * i + 3 * k + c, S.sh_dtype);
-        if (g_sh) for (int c = 0; c < 3; ++c) g_sh[3 * K * i + 3 * k + c] = Y[k] * gc[c];
-        const float wsum = sh[0] * gc[0] + sh[1] * gc[1] + sh[2] * gc[2];
-        for (int a = 0; a < 3; ++a) gd[a] += wsum * dY[k][a];
+    switch (K) {
+    case 16: sh_weighted_grad<16>(S.s_sh, i, S.sh_dtype, gc, dir, gd); break;
+    case 9: sh_weighted_grad<9>(S.s_sh, i, S.sh_dtype, gc, dir, gd); break;
+    case 4: sh_weighted_grad<4>(S.s_sh, i, S.sh_dtype, gc, dir, gd); break;
+    default: break;   // degree 0: the colour does not depend on the direction
     }
+    if (g_sh) store_sh_grad(g_sh + 3 * K * i, K, Y, gc, nullptr);
     if (dist > 0.f) {
         const float pr = gd[0] * dir[0] + gd[1] * dir[1] + gd[2] * dir[2];
         for (int a = 0; a < 3; ++a) gp[a] -= (gd[a] - pr * dir[a]) / dist;
