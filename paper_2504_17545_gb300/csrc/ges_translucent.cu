@@ -99,23 +99,36 @@ __global__ void __launch_bounds__(256) k_tsort(const int *__restrict__ off, unsi
 // Returns true where it contributes (min(alpha, G) >= alpha_min, hit in
 // front of the near plane); alpha, om = 1 - alpha (accurate near alpha = 1),
 // G and 1/z come back.
-__device__ __forceinline__ bool t_alpha(const float4 &r0, const float4 &r1, const float4 &r2, float w, float u,
-                                        float v, const CamParams &C, const OptParams &O, float &alpha, float &om,
-                                        float &G, float &iz)
+__device__ __forceinline__ bool t_hit(const float4 &r0, const float4 &r1, const float4 &r2, float u, float v,
+                                      const CamParams &C, float &iz, float &q)
 {
     const float du = u - r0.x, dv = v - r0.y;
     iz = fmaf(r0.w, du, fmaf(r1.x, dv, r0.z));
     const float A = fmaf(r1.y, du, fmaf(r1.z, dv, r1.w));
     const float B = fmaf(r2.x, du, fmaf(r2.y, dv, r2.z));
-    const float q = fmaf(A, A, B * B);
-    if (!(w > 0.f) || !(iz > 0.f && iz < C.izn && q <= iz * iz)) return false;   // outside the 1/255 disc
+    q = fmaf(A, A, B * B);
+    return iz > 0.f && iz < C.izn && q <= iz * iz;   // inside the 1/255 disc
+}
+// log w of a surfel, computed once per staged entry (-inf for w <= 0: never drawn)
+__device__ __forceinline__ float t_logw(float w) { return w > 0.f ? logf(w) : -INFINITY; }
+__device__ __forceinline__ bool t_opacity(float q, float iz, float lw, const OptParams &O, float &alpha, float &om,
+                                          float &G)
+{
+    if (!(lw > -INFINITY)) return false;
     const float rho = O.surfel_r2 * q / (iz * iz);
     const float e = -0.5f * rho;
     G = expf(e);
-    const float lw = logf(w), x = lw + e;                           // w G = exp(x)
+    const float x = lw + e;                         // w G = exp(x)
     if (x >= 0.f) { alpha = 1.f; om = 0.f; }
     else { om = -expm1f(x); alpha = 1.f - om; }
     return fminf(alpha, G) >= O.alpha_min;
+}
+__device__ __forceinline__ bool t_alpha(const float4 &r0, const float4 &r1, const float4 &r2, float lw, float u,
+                                        float v, const CamParams &C, const OptParams &O, float &alpha, float &om,
+                                        float &G, float &iz)
+{
+    float q;
+    return t_hit(r0, r1, r2, u, v, C, iz, q) && t_opacity(q, iz, lw, O, alpha, om, G);
 }
 
 __device__ __forceinline__ float shfl_f(float v, int s) { return __shfl_sync(0xffffffffu, v, s); }
@@ -131,6 +144,7 @@ __global__ void __launch_bounds__(kRasterThreads, 4)
     __shared__ int sid[kRasterThreads];
     __shared__ unsigned sbb[2][kRasterThreads];
     __shared__ float sizmax[kRasterThreads];
+    __shared__ float slw[kRasterThreads];        // log w
     if (X.status[ST_FLAGS] & FLAG_SOVF) return;
     const int tile = blockIdx.x, tx = tile % C.tiles_x, ty = tile / C.tiles_x;
     const unsigned warp = threadIdx.x >> 5, lane = lane_idx();
@@ -151,7 +165,9 @@ __global__ void __launch_bounds__(kRasterThreads, 4)
             sbb[0][t] = __float_as_uint(r3.y); sbb[1][t] = __float_as_uint(r3.z);
             sizmax[t] = rp[2].w;
             const float4 c = X.s_rgb[id];
-            sx[t] = make_float4(c.x, c.y, c.z, w[id]);
+            const float wi = w[id];
+            sx[t] = make_float4(c.x, c.y, c.z, wi);
+            slw[t] = t_logw(wi);
             sid[t] = id;
         }
     };
@@ -178,10 +194,14 @@ __global__ void __launch_bounds__(kRasterThreads, 4)
             while (mask) {
                 const int jj = j0 + __ffs(mask) - 1;
                 mask &= mask - 1;
-                float a, om, G, iz;
-                if (in_img && t_alpha(ss[0][jj], ss[1][jj], ss[2][jj], sx[jj].w, u, v, C, O, a, om, G, iz)) {
+                // only a hit that would win needs its opacity (the exp and the cut)
+                float a, om, G, iz, q;
+                if (in_img && t_hit(ss[0][jj], ss[1][jj], ss[2][jj], u, v, C, iz, q)) {
                     const int id = sid[jj];
-                    if (iz > best || (iz == best && id < fid)) { best = iz; fid = id; }
+                    if ((iz > best || (iz == best && id < fid)) && t_opacity(q, iz, slw[jj], O, a, om, G)) {
+                        best = iz;
+                        fid = id;
+                    }
                 }
             }
             wmin = __uint_as_float(__reduce_min_sync(0xffffffffu, __float_as_uint(best)));
@@ -196,7 +216,7 @@ __global__ void __launch_bounds__(kRasterThreads, 4)
     if (kFront && has_front && !done) {
         const float4 *rp = X.s_rec + 4 * (int64_t)fid;
         float a, om, G, iz;
-        t_alpha(rp[0], rp[1], rp[2], w[fid], u, v, C, O, a, om, G, iz);
+        t_alpha(rp[0], rp[1], rp[2], t_logw(w[fid]), u, v, C, O, a, om, G, iz);
         const float4 c = X.s_rgb[fid];
         Cr += c.x * a * T; Cg += c.y * a * T; Cb += c.z * a * T;
         Tlast = T;
@@ -217,7 +237,7 @@ __global__ void __launch_bounds__(kRasterThreads, 4)
             const int id = sid[j];
             if (kFront && id == fid) continue;
             float a, om, G, iz;
-            if (!t_alpha(ss[0][j], ss[1][j], ss[2][j], sx[j].w, u, v, C, O, a, om, G, iz)) continue;
+            if (!t_alpha(ss[0][j], ss[1][j], ss[2][j], slw[j], u, v, C, O, a, om, G, iz)) continue;
             const float4 c = sx[j];
             Cr += c.x * a * T; Cg += c.y * a * T; Cb += c.z * a * T;
             Tlast = T;
@@ -285,7 +305,7 @@ __device__ __forceinline__ void t_add(long long *acc, int id, const float *terms
 }
 
 template <bool kFront>
-__global__ void __launch_bounds__(kRasterThreads, 2)
+__global__ void __launch_bounds__(kRasterThreads, 3)
     k_tbwd(ViewScratch X, CamParams C, OptParams O, const float *__restrict__ w, const float *__restrict__ dL,
            const float *__restrict__ in_T, const int32_t *__restrict__ in_front, const int32_t *__restrict__ in_last,
            const float *__restrict__ in_Tlast, const unsigned *gmax_bits, long long *acc)
@@ -294,6 +314,7 @@ __global__ void __launch_bounds__(kRasterThreads, 2)
     __shared__ float4 sx[kRasterThreads];
     __shared__ int sid[kRasterThreads];
     __shared__ unsigned sbb[2][kRasterThreads];
+    __shared__ float slw[kRasterThreads];        // log w
     __shared__ int s_maxlast;
     if (X.status[ST_FLAGS] & FLAG_SOVF) return;
     const float gmax = __uint_as_float(*gmax_bits);
@@ -332,7 +353,9 @@ __global__ void __launch_bounds__(kRasterThreads, 2)
             const float4 r3 = rp[3];
             sbb[0][t] = __float_as_uint(r3.y); sbb[1][t] = __float_as_uint(r3.z);
             const float4 c = X.s_rgb[id];
-            sx[t] = make_float4(c.x, c.y, c.z, w[id]);
+            const float wi = w[id];
+            sx[t] = make_float4(c.x, c.y, c.z, wi);
+            slw[t] = t_logw(wi);
             sid[t] = id;
         }
         __syncthreads();
@@ -349,7 +372,7 @@ __global__ void __launch_bounds__(kRasterThreads, 2)
             bool contrib = false;
             float a = 0.f, om = 1.f, G = 0.f, iz = 1.f;
             if (in_img && pos < mylast && !(kFront && id == myfront) &&
-                t_alpha(ss[0][j], ss[1][j], ss[2][j], sx[j].w, u, v, C, O, a, om, G, iz)) {
+                t_alpha(ss[0][j], ss[1][j], ss[2][j], slw[j], u, v, C, O, a, om, G, iz)) {
                 contrib = true;
                 // T before this contributor: stored for the last one, else T_after / (1 - alpha)
                 const float Ti = !first_seen ? Tl : Tc / om;
@@ -374,7 +397,7 @@ __global__ void __launch_bounds__(kRasterThreads, 2)
     if (kFront && in_img && myfront >= 0) {
         const float4 *rp = X.s_rec + 4 * (int64_t)myfront;
         float a, om, G, iz;
-        if (t_alpha(rp[0], rp[1], rp[2], w[myfront], u, v, C, O, a, om, G, iz)) {
+        if (t_alpha(rp[0], rp[1], rp[2], t_logw(w[myfront]), u, v, C, O, a, om, G, iz)) {
             const float4 c = X.s_rgb[myfront];
             const float col[3] = {c.x, c.y, c.z};
             float terms[kTAcc];
