@@ -76,8 +76,8 @@ __device__ __forceinline__ void store_rec(float4 *dst, const SurfelRec &r)
 {
     dst[0] = make_float4(r.ur, r.vr, r.iz0, r.gu);
     dst[1] = make_float4(r.gv, r.au, r.av, r.a0);
-    dst[2] = make_float4(r.bu, r.bv, r.b0, r.izmax);
-    dst[3] = make_float4(__int_as_float(r.id), __uint_as_float(r.bb_lo), __uint_as_float(r.bb_hi), r.pad);
+    dst[2] = make_float4(r.bu, r.bv, r.b0, __int_as_float(r.id));
+    dst[3] = make_float4(r.izmax, __uint_as_float(r.bb_lo), __uint_as_float(r.bb_hi), r.pad);
 }
 
 // The first three quarters of a staged Gaussian record (what alpha, the depth
@@ -493,9 +493,9 @@ __device__ __forceinline__ void surfel_pass(const Recs &R, int n, const WarpBloc
         const int j = j0 + (int)lane;
         bool keep = false;
         if (j < n) {
-            const float4 r3 = R(3, j);
+            const float4 r3 = R(3, j);     // (izmax, bbox, -)
             keep = box_overlap(__float_as_uint(r3.y), __float_as_uint(r3.z), B.wx0, B.wy0, B.wx1, B.wy1) &&
-                   R(2, j).w >= z.wmin;
+                   r3.x >= z.wmin;
         }
         unsigned mask = __ballot_sync(0xffffffffu, keep);
         while (mask) {
@@ -506,7 +506,7 @@ __device__ __forceinline__ void surfel_pass(const Recs &R, int n, const WarpBloc
             if (two) mask &= mask - 1;
             const float4 a2 = R(2, ja), b2 = R(2, jb);
             const float4 a0 = R(0, ja), a1 = R(1, ja), b0 = R(0, jb), b1 = R(1, jb);
-            const int ida = __float_as_int(R(3, ja).x), idb = __float_as_int(R(3, jb).x);
+            const int ida = __float_as_int(a2.w), idb = __float_as_int(b2.w);
 #pragma unroll
             for (int k = 0; k < kS; ++k) {
                 const float uk = B.us + 0.5f * (k & 1), vk = B.vs + 0.5f * (k >> 1);
@@ -579,8 +579,9 @@ __device__ __forceinline__ void gauss_pass(const Recs &R, int n, const WarpBlock
         bool keep = false;
         if (j < n) {
             const float4 r3 = R(3, j);
-            // 3D: key = d - eps; 2D: the smallest planar depth (1/izmax) - eps
-            const float key = kG == 2 ? 1.f / R(2, j).w - r3.w : R(2, j).x;
+            // 3D: key = d - eps (kept with the bbox); 2D: the smallest planar
+            // depth (1/izmax) - eps
+            const float key = kG == 2 ? 1.f / r3.x - r3.w : r3.w;
             keep = box_overlap(__float_as_uint(r3.y), __float_as_uint(r3.z), B.wx0, B.wy0, B.wx1, B.wy1) &&
                    key < wmaxD;
         }
@@ -1262,7 +1263,7 @@ __global__ void __launch_bounds__(256) k_count(SceneView S, ViewScratch X, CamPa
                     }
                 } else if (S.gdim == 2) {
                     const float4 r0 = st[0][j], r1 = st[1][j], r2 = st[2][j];
-                    const int id = __float_as_int(st[3][j].x);
+                    const int id = __float_as_int(st[2][j].w);
                     const float4 x0 = X.g_aux[2 * (int64_t)id], x1 = X.g_aux[2 * (int64_t)id + 1];
                     const float du = u - r0.x, dv = v - r0.y;
                     const float iz = fmaf(r0.w, du, fmaf(r1.x, dv, r0.z));

@@ -432,12 +432,15 @@ __device__ __forceinline__ unsigned pack_xy(int x, int y) { return (unsigned)x |
 //   A    = a0  + au du + av dv          a * invz / r   (a, b: disc coordinates
 //   B    = b0  + bu du + bv dv          b * invz / r    scaled by s1, s2)
 // The pixel is inside the opaque disc iff invz > 0 and A^2 + B^2 <= invz^2.
-// (16-byte aligned: it is moved as four float4)
+// (16-byte aligned: it is moved as four float4.)  The first three quarters
+// hold what a coverage test reads (the id with the coefficients); the last
+// one what the culling reads.
 struct __align__(16) SurfelRec {
     float ur, vr, iz0, gu;
     float gv, au, av, a0;
-    float bu, bv, b0, izmax;      // izmax: largest 1/z over the disc (culling)
+    float bu, bv, b0;
     int id;
+    float izmax;                  // largest 1/z over the disc (culling)
     unsigned bb_lo, bb_hi;        // pixel bbox (x | y << 16), inclusive
     float pad;
 };
@@ -647,7 +650,7 @@ __device__ __forceinline__ bool disc_setup(const CamParams &C, const df *P, cons
     o.x0 = x0; o.x1 = x1; o.y0 = y0; o.y1 = y1;
 
     float izmax = zmin > C.znear ? (1.f / zmin) * (1.f + 4e-6f) : C.izn * (1.f + 4e-6f);
-    o.rec = SurfelRec{ur, vr, iz0, gu, gv, au, av, a0, bu, bv, b0, izmax, id,
+    o.rec = SurfelRec{ur, vr, iz0, gu, gv, au, av, a0, bu, bv, b0, id, izmax,
                       pack_xy(x0, y0), pack_xy(x1, y1), 0.f};
     return true;
 }
@@ -819,7 +822,7 @@ __device__ __forceinline__ void gauss_setup(const SceneView &S, const CamParams 
     o.rec.sigma = sigma; o.rec.key = key;
     o.rec.id = (int)i;
     o.rec.bb_lo = pack_xy(x0, y0); o.rec.bb_hi = pack_xy(x1, y1);
-    o.rec.pad = 0.f;
+    o.rec.pad = key;              // the culling reads key with the bbox
     const int K = (S.deg + 1) * (S.deg + 1);
     float Y[16];
     sh_basis(K, o.dir[0], o.dir[1], o.dir[2], Y);

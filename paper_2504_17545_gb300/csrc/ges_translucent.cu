@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kRasterThreads, 4)
             ss[0][t] = rp[0]; ss[1][t] = rp[1]; ss[2][t] = rp[2];
             const float4 r3 = rp[3];
             sbb[0][t] = __float_as_uint(r3.y); sbb[1][t] = __float_as_uint(r3.z);
-            sizmax[t] = rp[2].w;
+            sizmax[t] = r3.x;
             const float4 c = X.s_rgb[id];
             const float wi = w[id];
             sx[t] = make_float4(c.x, c.y, c.z, wi);
