@@ -519,7 +519,8 @@ __device__ __forceinline__ void surfel_pass(const Recs &R, int n, const WarpBloc
                 const float Bb = fmaf(b2.x, dub, fmaf(b2.y, dvb, b2.z));
                 const float qa = fmaf(Aa, Aa, fmaf(Ba, Ba, -iza * iza));
                 const float qb = fmaf(Ab, Ab, fmaf(Bb, Bb, -izb * izb));
-                const bool ina = qa <= 0.f && iza < izn, inb = qb <= 0.f && izb < izn && two;
+                // with one survivor left b is a again: testing it twice is harmless
+                const bool ina = qa <= 0.f && iza < izn, inb = qb <= 0.f && izb < izn;
                 if (ina && (iza > z.best[k] || (iza == z.best[k] && ida < z.bid[k]))) { z.best[k] = iza; z.bid[k] = ida; }
                 if (inb && (izb > z.best[k] || (izb == z.best[k] && idb < z.bid[k]))) { z.best[k] = izb; z.bid[k] = idb; }
             }
