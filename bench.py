@@ -436,6 +436,40 @@ def translucent_extra(R, N, scene, cams):
     return res
 
 
+def run_case(args):
+    """One secondary workload alone, --warmup untimed and --steps timed
+    iterations, for profiler captures: the training step (forward + backward
+    at 1600x1060, 500k + 500k) or the translucent coarse-stage render
+    (forward + backward at 1080p, 1M surfels, early w)."""
+    import numpy as np
+    import torch
+    import scenegen as sg
+    from paper_2504_17545_gb300 import render as R
+    if args.case == "train_step":
+        scene, cams = sg.config_scene(3)
+        gs = R.GESScene.from_arrays(scene)
+        fwd = R.render(gs, cams[0])
+        g = torch.sign(fwd["rgb"] - torch.rand_like(fwd["rgb"])) / fwd["rgb"].numel()
+
+        def step():
+            out = R.render(gs, cams[0])
+            R.render_backward(gs, cams[0], out, g)
+    else:
+        scene, cams = sg.config_scene(1)
+        sc = scene.subset(g_idx=np.zeros(0, int))
+        gs = R.GESScene.from_arrays(sc)
+        w = torch.as_tensor(np.random.default_rng(0).uniform(0.1, 30.0, sc.n_surfels), dtype=torch.float32,
+                            device="cuda")
+        fwd = R.render_translucent(gs, cams[0], w, False)
+        g = torch.sign(fwd["rgb"] - 0.5) / fwd["rgb"].numel()
+
+        def step():
+            R.render_translucent_backward(gs, cams[0], w, R.render_translucent(gs, cams[0], w, False), g, False)
+    ms = _time(step, max(1, args.steps), warm=max(0, args.warmup))
+    gs.close()
+    print(json.dumps({"case": args.case, "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -446,12 +480,18 @@ def main():
     ap.add_argument("--views", type=int, default=N_VIEWS,
                     help="orbit views per step (the workload is 64; fewer only for profiling captures)")
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--case", default="orbit", choices=["orbit", "train_step", "translucent"],
+                    help="orbit: the benchmark; train_step / translucent: run that secondary workload "
+                         "--steps times and print its timing (for profiler captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.case != "orbit" and args.impl == "ours":
+        run_case(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
