@@ -167,9 +167,15 @@ __global__ void __launch_bounds__(256, 3) k_gbwd_chain(SceneView S, CamParams C,
     const int64_t gi = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (gi >= S.M) return;
     const int K = (S.deg + 1) * (S.deg + 1);
+    unsigned bits = 0u;
+    for (int c = 0; c < 9; ++c) bits |= __float_as_uint(__ldg(sums + (int64_t)c * S.M + gi)) & 0x7fffffffu;
+    const bool any = bits != 0u;
+    // every gradient is linear in the nine sums: a Gaussian that passed the
+    // cut and the depth test nowhere (not drawn, or hidden) gets zeros without
+    // its set-up
     GaussOut o;
     o.visible = false;
-    if (O.mode != GES_MODE_SURFELS_ONLY) gauss_setup(S, C, O, gi, o);
+    if (any && O.mode != GES_MODE_SURFELS_ONLY) gauss_setup(S, C, O, gi, o);
     if (!o.visible) {
         if (G.g_pos) for (int a = 0; a < 3; ++a) G.g_pos[3 * gi + a] = 0.f;
         if (G.g_rot) for (int a = 0; a < 4; ++a) G.g_rot[4 * gi + a] = 0.f;
@@ -179,7 +185,7 @@ __global__ void __launch_bounds__(256, 3) k_gbwd_chain(SceneView S, CamParams C,
         return;
     }
     float my[9];
-    for (int c = 0; c < 9; ++c) my[c] = __ldg(sums + (int64_t)c * S.M + gi);
+    for (int c = 0; c < 9; ++c) my[c] = sums[(int64_t)c * S.M + gi];
     const float *dc = my;
     float gp[3] = {0.f, 0.f, 0.f};
     // colour -> SH coefficients and position (through the view direction)

@@ -111,20 +111,33 @@ __device__ __forceinline__ bool setup_and_store(const SceneView &S, const CamPar
 {
     if (surf) {
         SurfelOut o;
-        surfel_setup(S, C, O, i, o, kTr ? X.s_tside + 4 * i : nullptr);
+        // the record goes out before the colour is evaluated: its registers
+        // are free again for the SH row
+        surfel_geom(S, C, O, i, o, kTr ? X.s_tside + 4 * i : nullptr);
         if (!o.valid_quat) atomicOr(X.status + ST_FLAGS, FLAG_BADQ);
         if (!o.visible) return false;
         store_rec(X.s_rec + 4 * i, o.rec);
+        surfel_colour(S, i, o);
         X.s_rgb[i] = make_float4(o.rgb[0], o.rgb[1], o.rgb[2], 0.f);
         x0 = o.x0; y0 = o.y0; x1 = o.x1; y1 = o.y1;
     } else {
         GaussOut o;
         if (kGd == 2) gauss2d_setup(S, C, O, i, o);
-        else gauss_setup(S, C, O, i, o);
+        else gauss_geom(S, C, O, i, o);
         if (!o.valid_quat) atomicOr(X.status + ST_FLAGS, FLAG_BADQ);
         if (!o.visible) return false;
-        if (kGd == 2) store_rec(X.g_rec + 4 * i, o.drec);
-        else store_rec(X.g_rec + 4 * i, o.rec);
+        if (kGd == 2) {
+            store_rec(X.g_rec + 4 * i, o.drec);
+        } else {
+            // three quarters of the record before the colour is evaluated
+            float4 *dst = X.g_rec + 4 * i;
+            dst[0] = make_float4(o.rec.px, o.rec.py, o.rec.pxl, o.rec.pyl);
+            dst[1] = make_float4(o.rec.la, o.rec.lb, o.rec.lc, o.rec.sigma);
+            dst[3] = make_float4(__int_as_float(o.rec.id), __uint_as_float(o.rec.bb_lo),
+                                 __uint_as_float(o.rec.bb_hi), o.rec.pad);
+            gauss_colour(S, i, o);
+            dst[2] = make_float4(o.rec.key, o.rec.r, o.rec.g, o.rec.b);
+        }
         if (kGd == 2 || O.geo) {
             X.g_aux[2 * i] = o.aux[0];
             X.g_aux[2 * i + 1] = o.aux[1];

@@ -660,8 +660,9 @@ __device__ __forceinline__ bool disc_setup(const CamParams &C, const df *P, cons
 // colour (Eq. 1) and a conservative pixel bbox.
 // tside (translucent render only; null elsewhere, which removes the stores):
 // the camera-space frame (P, s1), (U, s2), (V, -), (N, -) of a visible surfel.
-__device__ __forceinline__ void surfel_setup(const SceneView &S, const CamParams &C, const OptParams &O,
-                                             int64_t i, SurfelOut &o, float4 *tside = nullptr)
+// surfel_geom: everything but the colour (visible: drawn somewhere).
+__device__ __forceinline__ void surfel_geom(const SceneView &S, const CamParams &C, const OptParams &O,
+                                            int64_t i, SurfelOut &o, float4 *tside = nullptr)
 {
     o.visible = false;
     o.valid_quat = true;
@@ -695,11 +696,24 @@ __device__ __forceinline__ void surfel_setup(const SceneView &S, const CamParams
     }
     o.rec = d.rec;
     o.x0 = d.x0; o.y0 = d.y0; o.x1 = d.x1; o.y1 = d.y1;
+    o.visible = true;
+}
+
+// The colour of a surfel set up by surfel_geom (Eq. 1 at o.dir).
+__device__ __forceinline__ void surfel_colour(const SceneView &S, int64_t i, SurfelOut &o)
+{
     const int K = (S.deg + 1) * (S.deg + 1);
     float Y[16];
     sh_basis(K, o.dir[0], o.dir[1], o.dir[2], Y);
     sh_colour(S.s_sh, i, K, S.sh_dtype, Y, o.rgb, o.raw);
-    o.visible = true;
+}
+
+// Geometry and colour.
+__device__ __forceinline__ void surfel_setup(const SceneView &S, const CamParams &C, const OptParams &O,
+                                             int64_t i, SurfelOut &o, float4 *tside = nullptr)
+{
+    surfel_geom(S, C, O, i, o, tside);
+    if (o.visible) surfel_colour(S, i, o);
 }
 
 struct GaussOut {
@@ -728,8 +742,9 @@ struct GaussOut {
 // sqrt(s^2 + v) and scales the opacity by prod |s_j| / sqrt(s_j^2 + v); the
 // screen filter (GES_FILTER_MIP) scales it by sqrt(|Sigma2'| / |Sigma2' + lowpass I|),
 // Sigma2' the projected covariance before the dilation.
-__device__ __forceinline__ void gauss_setup(const SceneView &S, const CamParams &C, const OptParams &O,
-                                            int64_t i, GaussOut &o)
+// gauss_geom: everything but the colour (visible: drawn somewhere).
+__device__ __forceinline__ void gauss_geom(const SceneView &S, const CamParams &C, const OptParams &O,
+                                           int64_t i, GaussOut &o)
 {
     o.visible = false;
     o.valid_quat = true;
@@ -823,11 +838,6 @@ __device__ __forceinline__ void gauss_setup(const SceneView &S, const CamParams 
     o.rec.id = (int)i;
     o.rec.bb_lo = pack_xy(x0, y0); o.rec.bb_hi = pack_xy(x1, y1);
     o.rec.pad = key;              // the culling reads key with the bbox
-    const int K = (S.deg + 1) * (S.deg + 1);
-    float Y[16];
-    sh_basis(K, o.dir[0], o.dir[1], o.dir[2], Y);
-    sh_colour(S.g_sh, i, K, S.sh_dtype, Y, o.rgb, o.raw);
-    o.rec.r = o.rgb[0]; o.rec.g = o.rgb[1]; o.rec.b = o.rgb[2];
     if (O.geo) {
         // geometry (Sec. 6.4): d_i = centre depth, n_i = the axis of the smallest
         // scale, camera space, facing the camera
@@ -842,6 +852,25 @@ __device__ __forceinline__ void gauss_setup(const SceneView &S, const CamParams 
         o.aux[1] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     o.visible = true;
+}
+
+// The colour of a Gaussian set up by gauss_geom (Eq. 1 at o.dir), also into
+// its record.
+__device__ __forceinline__ void gauss_colour(const SceneView &S, int64_t i, GaussOut &o)
+{
+    const int K = (S.deg + 1) * (S.deg + 1);
+    float Y[16];
+    sh_basis(K, o.dir[0], o.dir[1], o.dir[2], Y);
+    sh_colour(S.g_sh, i, K, S.sh_dtype, Y, o.rgb, o.raw);
+    o.rec.r = o.rgb[0]; o.rec.g = o.rgb[1]; o.rec.b = o.rgb[2];
+}
+
+// Geometry and colour.
+__device__ __forceinline__ void gauss_setup(const SceneView &S, const CamParams &C, const OptParams &O,
+                                            int64_t i, GaussOut &o)
+{
+    gauss_geom(S, C, O, i, o);
+    if (o.visible) gauss_colour(S, i, o);
 }
 
 // 2D Gaussian of 2D-GES (Sec. 6.4): a splat in the plane of its rotation's
