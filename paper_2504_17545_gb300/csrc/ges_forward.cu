@@ -859,14 +859,18 @@ __global__ void __launch_bounds__(kRasterThreads, kS == 1 && kG == 3 ? 5 : 4) k_
     BatchView &bv = *reinterpret_cast<BatchView *>(bv_raw);
     __shared__ int item, sv;
     int cur_v = -1;
+    if (threadIdx.x == 0) {
+        item = (int)atomicAdd(counter, 1u);
+        if (item < total) sv = find_view(n, item, [&](int k) { return V[k].tile_base; });
+    }
     for (;;) {
-        if (threadIdx.x == 0) {
-            item = (int)atomicAdd(counter, 1u);
-            if (item < total) sv = find_view(n, item, [&](int k) { return V[k].tile_base; });
-        }
         __syncthreads();
         const int it = item;
         if (it >= total) break;
+        // the next item is taken now and used after this tile: the atomic's
+        // round trip overlaps the raster instead of holding the CTA at a barrier
+        int nxt = 0;
+        if (threadIdx.x == 0) nxt = (int)atomicAdd(counter, 1u);
         if (sv != cur_v) {
             cur_v = sv;
             load_view(V, cur_v, bv);
@@ -876,9 +880,13 @@ __global__ void __launch_bounds__(kRasterThreads, kS == 1 && kG == 3 ? 5 : 4) k_
             raster_tile<kS, kG, false>(bv.X, bv.C, O, bv.rgb, bv.depth, nullptr, nullptr, GeoMaps{}, it - bv.tile_base,
                                        ss, sgs);
         __syncthreads();
-        // per-view completion time: the CTA that finishes the view's last tile stamps it
-        if (threadIdx.x == 0 && atomicAdd(bv.X.status + ST_RETIRED, 1u) + 1u == (unsigned)bv.T)
-            *reinterpret_cast<unsigned long long *>(bv.X.status + ST_TDONE) = global_timer_ns();
+        if (threadIdx.x == 0) {
+            // per-view completion time: the CTA that finishes the view's last tile stamps it
+            if (atomicAdd(bv.X.status + ST_RETIRED, 1u) + 1u == (unsigned)bv.T)
+                *reinterpret_cast<unsigned long long *>(bv.X.status + ST_TDONE) = global_timer_ns();
+            item = nxt;
+            if (nxt < total) sv = find_view(n, nxt, [&](int k) { return V[k].tile_base; });
+        }
     }
 }
 
