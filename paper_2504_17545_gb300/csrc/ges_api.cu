@@ -206,7 +206,7 @@ ges_status ensure_scratch(ges_scene *s, int64_t T, int slots, cudaStream_t st)
     const int64_t N = std::max<int64_t>(s->desc.n_surfels, 1), M = std::max<int64_t>(s->desc.n_gaussians, 1);
     cudaError_t e;
     if ((e = s->s_rec.ensure(N * 64)) || (e = s->s_rgb.ensure(N * 16)) || (e = s->g_rec.ensure(M * 64)) ||
-        (e = s->s_vis.ensure(N * 4)) || (e = s->g_vis.ensure(M * 4)))
+        (e = s->s_vis.ensure(N * 16)) || (e = s->g_vis.ensure(M * 16)))
         return cuda_fail(e, "scratch allocation (records)");
     if (T > s->tiles_cap) {
         const int64_t Tc = T;
@@ -795,8 +795,8 @@ size_t batch_layout(ges_batch *b, const std::vector<SceneView> &S, const std::ve
         X.s_rec = (float4 *)take(N * 64);
         X.s_rgb = (float4 *)take(N * 16);
         X.g_rec = (float4 *)take(M * 64);
-        X.s_vis = (int *)take(N * 4);
-        X.g_vis = (int *)take(M * 4);
+        X.s_vis = (int *)take(N * 16);   // 16-byte segment entries (local bins)
+        X.g_vis = (int *)take(M * 16);
         X.s_cnt = (int *)take((T + 1) * 4);
         X.g_cnt = (int *)take((T + 1) * 4);
         X.s_off = (int *)take((T + 1) * 4);

@@ -165,7 +165,10 @@ __device__ __forceinline__ void prep_local_body(const SceneView &S, const CamPar
     for (int w = threadIdx.x; w < words; w += kPrepThreads) hist[w] = 0u;
     if (threadIdx.x == 0) vcnt = 0u;
     __syncthreads();
-    int *seg = (surf ? X.s_vis : X.g_vis) + beg;
+    // the CTA's segment of visible primitives: (id, bbox lo, bbox hi) per
+    // entry, so that the fill reads its entries contiguously instead of
+    // gathering each record's bbox
+    int4 *seg = reinterpret_cast<int4 *>(surf ? X.s_vis : X.g_vis) + beg;
     for (int64_t i0 = beg; i0 < end; i0 += kPrepThreads) {
         const int64_t i = i0 + threadIdx.x;
         int x0 = 0, y0 = 0, x1 = -1, y1 = -1;
@@ -176,7 +179,9 @@ __device__ __forceinline__ void prep_local_body(const SceneView &S, const CamPar
             unsigned b = 0;
             if ((int)lane_id() == leader) b = atomicAdd(&vcnt, (unsigned)__popc(m));
             b = __shfl_sync(0xffffffffu, b, leader);
-            if (vis) seg[b + __popc(m & ((1u << lane_id()) - 1u))] = (int)i;
+            if (vis)
+                seg[b + __popc(m & ((1u << lane_id()) - 1u))] =
+                    make_int4((int)i, (int)pack_xy(x0, y0), (int)pack_xy(x1, y1), 0);
         }
         if (vis) {
             const int tx0 = x0 / kTile, tx1 = x1 / kTile, ty0 = y0 / kTile, ty1 = y1 / kTile;
@@ -257,14 +262,13 @@ __device__ __forceinline__ void fill_local_body(const ViewScratch &X, int T, int
     for (int t = threadIdx.x; t < T; t += kFillThreads) cur[t] = (unsigned)off[t] + brow[t];
     __syncthreads();
     const int64_t beg = (int64_t)(surf ? c : c - B.Ps) * (surf ? B.Rs : B.Rg);
-    const int *seg = (surf ? X.s_vis : X.g_vis) + beg;
-    const float4 *rec = surf ? X.s_rec : X.g_rec;
+    const int4 *seg = reinterpret_cast<const int4 *>(surf ? X.s_vis : X.g_vis) + beg;
     int *list = surf ? X.s_list : X.g_list;
     const unsigned n = X.vcount[c];
     for (unsigned k = threadIdx.x; k < n; k += kFillThreads) {
-        const int id = seg[k];
-        const float4 r3 = rec[4 * (int64_t)id + 3];
-        const unsigned lo = __float_as_uint(r3.y), hi = __float_as_uint(r3.z);
+        const int4 e = seg[k];
+        const int id = e.x;
+        const unsigned lo = (unsigned)e.y, hi = (unsigned)e.z;
         const int tx0 = (lo & 0xffff) / kTile, ty0 = (lo >> 16) / kTile;
         const int tx1 = (hi & 0xffff) / kTile, ty1 = (hi >> 16) / kTile;
         for (int ty = ty0; ty <= ty1; ++ty)

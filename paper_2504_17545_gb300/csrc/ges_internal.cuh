@@ -69,7 +69,10 @@ struct ViewScratch {
     float4 *s_rec;        // [N][4]  surfel raster records
     float4 *s_rgb;        // [N]     surfel colours
     float4 *g_rec;        // [M][4]  Gaussian raster records
-    int *s_vis, *g_vis;   // visible primitives (per-CTA segments with local bins)
+    // visible primitives: with local bins, per-CTA segments of 16-byte entries
+    // (id, bbox lo, bbox hi, -), 16 B per primitive; with atomic binning one
+    // id per entry
+    int *s_vis, *g_vis;
     int *s_cnt, *g_cnt;   // [T]     per-tile counts (zero between renders)
     int *s_off, *g_off;   // [T+1]   exclusive offsets
     int *s_cur, *g_cur;   // [T]     fill cursors (atomic binning)
