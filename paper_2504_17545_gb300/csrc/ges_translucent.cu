@@ -230,20 +230,27 @@ __global__ void __launch_bounds__(kRasterThreads, 4)
         __syncthreads();
         const int n = min(kRasterThreads, s1 - base);
         if (!wactive) continue;
-        for (int j = 0; j < n; ++j) {
+        // groups of 32 entries: the lanes test the block overlap of one entry
+        // each, then the warp walks the overlapping ones in list order
+        for (int j0 = 0; j0 < n; j0 += 32) {
             if (__all_sync(0xffffffffu, done)) break;
-            if (!overlap(j)) continue;
-            if (done) continue;
-            const int id = sid[j];
-            if (kFront && id == fid) continue;
-            float a, om, G, iz;
-            if (!t_alpha(ss[0][j], ss[1][j], ss[2][j], slw[j], u, v, C, O, a, om, G, iz)) continue;
-            const float4 c = sx[j];
-            Cr += c.x * a * T; Cg += c.y * a * T; Cb += c.z * a * T;
-            Tlast = T;
-            T *= om;
-            last = base - s0 + j + 1;
-            done = T < kTStop;
+            unsigned mask = __ballot_sync(0xffffffffu, j0 + (int)lane < n && overlap(j0 + (int)lane));
+            while (mask) {
+                if (__all_sync(0xffffffffu, done)) break;
+                const int j = j0 + __ffs(mask) - 1;
+                mask &= mask - 1;
+                if (done) continue;
+                const int id = sid[j];
+                if (kFront && id == fid) continue;
+                float a, om, G, iz;
+                if (!t_alpha(ss[0][j], ss[1][j], ss[2][j], slw[j], u, v, C, O, a, om, G, iz)) continue;
+                const float4 c = sx[j];
+                Cr += c.x * a * T; Cg += c.y * a * T; Cb += c.z * a * T;
+                Tlast = T;
+                T *= om;
+                last = base - s0 + j + 1;
+                done = T < kTStop;
+            }
         }
     }
     if (!in_img) return;
@@ -361,36 +368,47 @@ __global__ void __launch_bounds__(kRasterThreads, 3)
         __syncthreads();
         if (!wactive) continue;
         const int n = min(kRasterThreads, nl - cbase);
-        for (int j = n - 1; j >= 0; --j) {
-            const unsigned lo = sbb[0][j], hi = sbb[1][j];
-            if (!((lo & 0xffff) <= (unsigned)wx1 && (hi & 0xffff) >= (unsigned)wx0 && (lo >> 16) <= (unsigned)wy1 &&
-                  (hi >> 16) >= (unsigned)wy0))
-                continue;
-            const int pos = cbase + j;             // position in the tile list
-            const int id = sid[j];
-            float terms[kTAcc];
-            bool contrib = false;
-            float a = 0.f, om = 1.f, G = 0.f, iz = 1.f;
-            if (in_img && pos < mylast && !(kFront && id == myfront) &&
-                t_alpha(ss[0][j], ss[1][j], ss[2][j], slw[j], u, v, C, O, a, om, G, iz)) {
-                contrib = true;
-                // T before this contributor: stored for the last one, else T_after / (1 - alpha)
-                const float Ti = !first_seen ? Tl : Tc / om;
-                first_seen = true;
-                const float col[3] = {sx[j].x, sx[j].y, sx[j].z};
-                t_terms(X.s_tside + 4 * (int64_t)id, a, G, sx[j].w, Ti, iz, g, S, col, u, v, C, terms);
-                for (int ch = 0; ch < 3; ++ch) S[ch] = col[ch] * a + om * S[ch];
-                Tc = Ti;
+        // groups of 32 entries from the end: the lanes test the block overlap
+        // of one entry each, then the warp walks the overlapping ones backwards
+        for (int j0 = ((n - 1) >> 5) << 5; j0 >= 0; j0 -= 32) {
+            const int jl = j0 + (int)lane;
+            bool ov = false;
+            if (jl < n) {
+                const unsigned lo = sbb[0][jl], hi = sbb[1][jl];
+                ov = (lo & 0xffff) <= (unsigned)wx1 && (hi & 0xffff) >= (unsigned)wx0 && (lo >> 16) <= (unsigned)wy1 &&
+                     (hi >> 16) >= (unsigned)wy0;
             }
-            if (!__any_sync(0xffffffffu, contrib)) continue;
-            if (!contrib)
-                for (int k = 0; k < kTAcc; ++k) terms[k] = 0.f;
-            // the warp's 18 sums, each added by the lane that ends up holding it
-            unsigned long long *ak = reinterpret_cast<unsigned long long *>(acc + (int64_t)kTAcc * id);
-            warp_reduce_scatter<kTAcc>(terms, (int)lane, [&](int k, float tot) {
-                const float x = tot * scale;
-                if (x != 0.f) atomicAdd(ak + k, (unsigned long long)__float2ll_rn(x));
-            });
+            unsigned mask = __ballot_sync(0xffffffffu, ov);
+            while (mask) {
+                const int hb = 31 - __clz(mask);
+                mask &= ~(1u << hb);
+                const int j = j0 + hb;
+                const int pos = cbase + j;             // position in the tile list
+                const int id = sid[j];
+                float terms[kTAcc];
+                bool contrib = false;
+                float a = 0.f, om = 1.f, G = 0.f, iz = 1.f;
+                if (in_img && pos < mylast && !(kFront && id == myfront) &&
+                    t_alpha(ss[0][j], ss[1][j], ss[2][j], slw[j], u, v, C, O, a, om, G, iz)) {
+                    contrib = true;
+                    // T before this contributor: stored for the last one, else T_after / (1 - alpha)
+                    const float Ti = !first_seen ? Tl : Tc / om;
+                    first_seen = true;
+                    const float col[3] = {sx[j].x, sx[j].y, sx[j].z};
+                    t_terms(X.s_tside + 4 * (int64_t)id, a, G, sx[j].w, Ti, iz, g, S, col, u, v, C, terms);
+                    for (int ch = 0; ch < 3; ++ch) S[ch] = col[ch] * a + om * S[ch];
+                    Tc = Ti;
+                }
+                if (!__any_sync(0xffffffffu, contrib)) continue;
+                if (!contrib)
+                    for (int k = 0; k < kTAcc; ++k) terms[k] = 0.f;
+                // the warp's 18 sums, each added by the lane that ends up holding it
+                unsigned long long *ak = reinterpret_cast<unsigned long long *>(acc + (int64_t)kTAcc * id);
+                warp_reduce_scatter<kTAcc>(terms, (int)lane, [&](int k, float tot) {
+                    const float x = tot * scale;
+                    if (x != 0.f) atomicAdd(ak + k, (unsigned long long)__float2ll_rn(x));
+                });
+            }
         }
     }
     // the frontmost surfel, blended first (T = 1)
