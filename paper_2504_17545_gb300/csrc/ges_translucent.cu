@@ -57,17 +57,20 @@ __global__ void __launch_bounds__(256) k_tkeys(const int *__restrict__ list, con
 // Ascending bitonic sort of a[0..n) (m = the next power of two); pairs whose
 // upper index is >= n are skipped, which equals padding with +infinity
 // because every compare-exchange moves the smaller key to the lower index.
+// (k, h, j are powers of two: the pair index splits with shifts and masks.)
 __device__ __forceinline__ void bitonic(unsigned long long *a, int n, int m)
 {
     for (int k = 2; k <= m; k <<= 1) {
+        const int lh = __ffs(k) - 2;              // log2(k / 2)
         for (int p = threadIdx.x; p < m / 2; p += blockDim.x) {
-            const int h = k >> 1, i = (p / h) * k + (p % h), l = i ^ (k - 1);
+            const int i = ((p >> lh) << (lh + 1)) + (p & ((1 << lh) - 1)), l = i ^ (k - 1);
             if (l < n && a[i] > a[l]) { const unsigned long long t = a[i]; a[i] = a[l]; a[l] = t; }
         }
         __syncthreads();
         for (int j = k >> 2; j >= 1; j >>= 1) {
+            const int lj = __ffs(j) - 1;
             for (int p = threadIdx.x; p < m / 2; p += blockDim.x) {
-                const int i = (p / j) * 2 * j + (p % j), l = i + j;
+                const int i = ((p >> lj) << (lj + 1)) + (p & (j - 1)), l = i + j;
                 if (l < n && a[i] > a[l]) { const unsigned long long t = a[i]; a[i] = a[l]; a[l] = t; }
             }
             __syncthreads();
