@@ -491,19 +491,21 @@ ges_status ges_render_backward(ges_scene *s, const ges_camera *cam, const ges_re
     if ((r = make_opts(opts, O)) != GES_OK) return r;
     const bool prof = s->prof;
     if (prof && (r = ensure_events(s, 8)) != GES_OK) return r;
-    // scratch: surfel sums + one word | per-pixel terms | Gaussian records | Gaussian sums
+    // scratch: surfel sums + one word | per-pixel terms | Gaussian records | Gaussian sums |
+    // chain-rule words
     const int64_t N = std::max<int64_t>(s->desc.n_surfels, 1), M = std::max<int64_t>(s->desc.n_gaussians, 1);
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t pix_off = up((size_t)N * 3 * 8 + 16);
     const size_t rec_off = pix_off + up((size_t)C.W * C.H * 16);
     const size_t sum_off = rec_off + up((size_t)M * 64);
-    GES_CUDA(s->t_acc.ensure(sum_off + (size_t)M * 9 * 4));
+    const size_t chain_off = sum_off + up((size_t)M * 9 * 4);
+    GES_CUDA(s->t_acc.ensure(chain_off + (size_t)M * kBwdChainWords * 4));
     unsigned char *base = (unsigned char *)s->t_acc.p;
     long long *acc = (long long *)base;
     cudaError_t e = launch_backward(s->view, C, O, dL_drgb, out_rgb, out_depth, surfel_id, aux, *grads, acc,
                                     (unsigned *)(acc + (size_t)N * 3), (float4 *)(base + pix_off),
-                                    (float4 *)(base + rec_off), (float *)(base + sum_off), s->stream,
-                                    prof ? s->ev.data() : nullptr);
+                                    (float4 *)(base + rec_off), (float *)(base + sum_off),
+                                    (float *)(base + chain_off), s->stream, prof ? s->ev.data() : nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "backward launch");
     GES_CUDA(cudaStreamSynchronize(s->stream));
     if (prof) prof_collect(s, 0, kBwdNames, 2);

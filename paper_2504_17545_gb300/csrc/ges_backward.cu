@@ -95,7 +95,51 @@ __device__ __forceinline__ void gauss_pixel(const GLoop &s, int x, int y, const 
 // latency-bound loop runs light on registers, at full occupancy.
 // k_gbwd_chain runs the chain rule per Gaussian from those sums (set-up
 // recomputed).  The summation order is fixed, so the result is deterministic.
-__global__ void __launch_bounds__(256) k_gbwd_rec(SceneView S, CamParams C, OptParams O, float4 *__restrict__ rec)
+// What the chain rule needs of a Gaussian's set-up, kept by k_gbwd_rec as
+// kChainWords structure-of-arrays words (word f of Gaussian i at f M + i) so
+// that k_gbwd_chain does not set it up again.
+constexpr int kChainWords = kBwdChainWords;
+static_assert(kChainWords == 40, "chain words");
+__device__ __forceinline__ void chain_put(const GaussOut &o, float *w, int64_t M, int64_t i)
+{
+    float v[kChainWords];
+    int f = 0;
+    for (int k = 0; k < 9; ++k) v[f++] = o.R[k];
+    for (int k = 0; k < 4; ++k) v[f++] = o.qn[k];
+    v[f++] = o.qnorm;
+    for (int k = 0; k < 3; ++k) v[f++] = o.s[k];
+    for (int k = 0; k < 3; ++k) v[f++] = o.se[k];
+    v[f++] = o.k3; v[f++] = o.k2; v[f++] = o.sigma0;
+    v[f++] = o.tx; v[f++] = o.ty; v[f++] = o.tz;
+    v[f++] = o.ia; v[f++] = o.ib; v[f++] = o.ic;
+    v[f++] = o.S2b; v[f++] = o.n0; v[f++] = o.n1; v[f++] = o.det0;
+    for (int k = 0; k < 3; ++k) v[f++] = o.dir[k];
+    v[f++] = o.dist;
+    for (int k = 0; k < 3; ++k) v[f++] = o.raw[k];
+    for (int k = 0; k < kChainWords; ++k) w[(int64_t)k * M + i] = v[k];
+}
+__device__ __forceinline__ void chain_get(GaussOut &o, const float *__restrict__ w, int64_t M, int64_t i)
+{
+    float v[kChainWords];
+    for (int k = 0; k < kChainWords; ++k) v[k] = __ldg(w + (int64_t)k * M + i);
+    int f = 0;
+    for (int k = 0; k < 9; ++k) o.R[k] = v[f++];
+    for (int k = 0; k < 4; ++k) o.qn[k] = v[f++];
+    o.qnorm = v[f++];
+    for (int k = 0; k < 3; ++k) o.s[k] = v[f++];
+    for (int k = 0; k < 3; ++k) o.se[k] = v[f++];
+    o.k3 = v[f++]; o.k2 = v[f++]; o.sigma0 = v[f++];
+    o.tx = v[f++]; o.ty = v[f++]; o.tz = v[f++];
+    o.ia = v[f++]; o.ib = v[f++]; o.ic = v[f++];
+    o.S2b = v[f++]; o.n0 = v[f++]; o.n1 = v[f++]; o.det0 = v[f++];
+    for (int k = 0; k < 3; ++k) o.dir[k] = v[f++];
+    o.dist = v[f++];
+    for (int k = 0; k < 3; ++k) o.raw[k] = v[f++];
+    o.visible = true;
+}
+
+__global__ void __launch_bounds__(256) k_gbwd_rec(SceneView S, CamParams C, OptParams O, float4 *__restrict__ rec,
+                                                 float *__restrict__ chain)
 {
     const int64_t gi = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (gi >= S.M) return;
@@ -112,6 +156,7 @@ __global__ void __launch_bounds__(256) k_gbwd_rec(SceneView S, CamParams C, OptP
     d[1] = make_float4(o.rec.la, o.rec.lb, o.rec.lc, o.rec.sigma);
     d[2] = make_float4(o.rec.key, o.rec.r, o.rec.g, o.rec.b);
     d[3] = make_float4(0.f, __uint_as_float(o.rec.bb_lo), __uint_as_float(o.rec.bb_hi), 0.f);
+    chain_put(o, chain, S.M, gi);
 }
 
 __global__ void __launch_bounds__(256, 4) k_gbwd_sweep(int64_t M, CamParams C, OptParams O,
@@ -144,16 +189,10 @@ __global__ void __launch_bounds__(256, 4) k_gbwd_sweep(int64_t M, CamParams C, O
         t.x0 = lo & 0xffff; t.y0 = lo >> 16; t.x1 = hi & 0xffff; t.y1 = hi >> 16;
         const int w = t.x1 - t.x0 + 1, n = w * (t.y1 - t.y0 + 1);
         float part[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        // pixel k of the bbox, row-major: row k / w and column k - w row.  The
-        // quotient from a float reciprocal is within one of the exact one for
-        // every bbox of an image of at most 16384^2 (k exact in float below
-        // 2^24; beyond, w >= 32), and the two fix-ups make it exact, so no
-        // integer division runs per pixel
+        // pixel k of the bbox, row-major (no integer division per pixel)
         const float iw = 1.f / (float)w;
         for (int k = lane; k < n; k += 32) {
-            int r = (int)(((float)k + 0.5f) * iw);
-            r -= (r * w > k) ? 1 : 0;
-            r += ((r + 1) * w <= k) ? 1 : 0;
+            const int r = bbox_row(k, w, iw);
             gauss_pixel(t, t.x0 + (k - r * w), t.y0 + r, C, O, P, depth, part);
         }
         float *dst = sums + g0 + j;
@@ -162,7 +201,8 @@ __global__ void __launch_bounds__(256, 4) k_gbwd_sweep(int64_t M, CamParams C, O
 }
 
 __global__ void __launch_bounds__(256, 3) k_gbwd_chain(SceneView S, CamParams C, OptParams O,
-                                                   const float *__restrict__ sums, ges_grads G)
+                                                   const float *__restrict__ sums,
+                                                   const float *__restrict__ chain, ges_grads G)
 {
     const int64_t gi = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (gi >= S.M) return;
@@ -171,11 +211,12 @@ __global__ void __launch_bounds__(256, 3) k_gbwd_chain(SceneView S, CamParams C,
     for (int c = 0; c < 9; ++c) bits |= __float_as_uint(__ldg(sums + (int64_t)c * S.M + gi)) & 0x7fffffffu;
     const bool any = bits != 0u;
     // every gradient is linear in the nine sums: a Gaussian that passed the
-    // cut and the depth test nowhere (not drawn, or hidden) gets zeros without
-    // its set-up
+    // cut and the depth test nowhere (not drawn, or hidden) gets zeros; the
+    // others read what k_gbwd_rec kept of their set-up (nonzero sums imply
+    // it was drawn)
     GaussOut o;
     o.visible = false;
-    if (any && O.mode != GES_MODE_SURFELS_ONLY) gauss_setup(S, C, O, gi, o);
+    if (any && O.mode != GES_MODE_SURFELS_ONLY) chain_get(o, chain, S.M, gi);
     if (!o.visible) {
         if (G.g_pos) for (int a = 0; a < 3; ++a) G.g_pos[3 * gi + a] = 0.f;
         if (G.g_rot) for (int a = 0; a < 4; ++a) G.g_rot[4 * gi + a] = 0.f;
@@ -395,7 +436,8 @@ cudaError_t launch_absmax(const float *x, int64_t n, unsigned *out, cudaStream_t
 cudaError_t launch_backward(const SceneView &S, const CamParams &C, const OptParams &O, const float *dL_drgb,
                             const float *out_rgb, const float *out_depth, const int32_t *surfel_id,
                             const float *aux, const ges_grads &G, long long *s_acc, unsigned *gmax,
-                            float4 *pixg, float4 *g_rec, float *g_sums, cudaStream_t st, cudaEvent_t *ev)
+                            float4 *pixg, float4 *g_rec, float *g_sums, float *g_chain, cudaStream_t st,
+                            cudaEvent_t *ev)
 {
     if (ev) cudaEventRecord(ev[0], st);
     if (S.M > 0) {
@@ -403,9 +445,9 @@ cudaError_t launch_backward(const SceneView &S, const CamParams &C, const OptPar
         k_pixgrad<<<(unsigned)((HW + 255) / 256), 256, 0, st>>>(HW, O.mode == GES_MODE_GAUSSIANS_ONLY, dL_drgb,
                                                                 out_rgb, aux, pixg);
         const unsigned nb = (unsigned)((S.M + 255) / 256);
-        k_gbwd_rec<<<nb, 256, 0, st>>>(S, C, O, g_rec);
+        k_gbwd_rec<<<nb, 256, 0, st>>>(S, C, O, g_rec, g_chain);
         k_gbwd_sweep<<<nb, 256, 0, st>>>(S.M, C, O, g_rec, pixg, out_depth, g_sums);
-        k_gbwd_chain<<<nb, 256, 0, st>>>(S, C, O, g_sums, G);
+        k_gbwd_chain<<<nb, 256, 0, st>>>(S, C, O, g_sums, g_chain, G);
     }
     if (ev) cudaEventRecord(ev[1], st);
     if (S.N > 0 && G.s_sh) {

@@ -168,11 +168,13 @@ cudaError_t launch_filter3d(const SceneView &S, const CamParams *d_cams, int n_c
 
 // Scratch: s_acc 3 N 64-bit words (surfel colour sums), gmax one word,
 // pixg H W float4 (per-pixel terms of the Gaussian gradients), g_rec M
-// 64-byte records, g_sums 9 M floats (per-Gaussian sums of the sweep).
+// 64-byte records, g_sums 9 M floats (per-Gaussian sums of the sweep),
+// g_chain kBwdChainWords M floats (what the chain rule needs of each set-up).
+constexpr int kBwdChainWords = 40;
 cudaError_t launch_backward(const SceneView &S, const CamParams &C, const OptParams &O, const float *dL_drgb,
                             const float *out_rgb, const float *out_depth, const int32_t *surfel_id,
                             const float *aux, const ges_grads &G, long long *s_acc, unsigned *gmax,
-                            float4 *pixg, float4 *g_rec, float *g_sums, cudaStream_t st,
+                            float4 *pixg, float4 *g_rec, float *g_sums, float *g_chain, cudaStream_t st,
                             cudaEvent_t *ev /* 3 events or nullptr */);
 // *out = the bit pattern of max |x[i]| over n floats (0 for none); zeroes it first.
 cudaError_t launch_absmax(const float *x, int64_t n, unsigned *out, cudaStream_t st);
@@ -944,6 +946,18 @@ __device__ __forceinline__ void gauss2d_setup(const SceneView &S, const CamParam
     o.aux[0] = make_float4(o.rgb[0], o.rgb[1], o.rgb[2], lsig);
     o.aux[1] = make_float4(fl * n[0], fl * n[1], fl * n[2], log2f(O.alpha_min) - lsig);
     o.visible = true;
+}
+
+// Row of pixel k of a w-wide bbox walked row-major (k / w) without an integer
+// division: the quotient from the float reciprocal iw = 1/w is within one of
+// the exact one for every bbox of an image of at most 16384^2 (k exact in
+// float below 2^24; beyond, w >= 32), and the two fix-ups make it exact.
+__device__ __forceinline__ int bbox_row(int k, int w, float iw)
+{
+    int r = (int)(((float)k + 0.5f) * iw);
+    r -= (r * w > k) ? 1 : 0;
+    r += ((r + 1) * w <= k) ? 1 : 0;
+    return r;
 }
 
 // Sums NV <= 32 per-lane values over the warp and hands total i to exactly

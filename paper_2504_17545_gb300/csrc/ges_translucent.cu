@@ -539,8 +539,10 @@ __global__ void __launch_bounds__(256) k_contrib(SceneView S, CamParams C, OptPa
             x0a = make_float4(shfl_f(o.aux[0].x, j), shfl_f(o.aux[0].y, j), shfl_f(o.aux[0].z, j), shfl_f(o.aux[0].w, j));
             x1a = make_float4(shfl_f(o.aux[1].x, j), shfl_f(o.aux[1].y, j), shfl_f(o.aux[1].z, j), shfl_f(o.aux[1].w, j));
             const float cm = fmaxf(x0a.x, fmaxf(x0a.y, x0a.z));
+            const float ibw = 1.f / (float)bw;
             for (int k = lane; k < n; k += 32) {
-                const int xx = x0 + k % bw, yy = y0 + k / bw;
+                const int rk = bbox_row(k, bw, ibw);
+                const int xx = x0 + (k - rk * bw), yy = y0 + rk;
                 const float du = xx + 0.5f - r[0].x, dv = yy + 0.5f - r[0].y;
                 const float iz = fmaf(r[0].w, du, fmaf(r[1].x, dv, r[0].z));
                 const float A = fmaf(r[1].y, du, fmaf(r[1].z, dv, r[1].w));
@@ -557,8 +559,10 @@ __global__ void __launch_bounds__(256) k_contrib(SceneView S, CamParams C, OptPa
             g.pyl = shfl_f(o.rec.pyl, j); g.la = shfl_f(o.rec.la, j); g.lb = shfl_f(o.rec.lb, j);
             g.lc = shfl_f(o.rec.lc, j); g.sigma = shfl_f(o.rec.sigma, j); g.key = shfl_f(o.rec.key, j);
             const float cm = fmaxf(shfl_f(o.rec.r, j), fmaxf(shfl_f(o.rec.g, j), shfl_f(o.rec.b, j)));
+            const float ibw = 1.f / (float)bw;
             for (int k = lane; k < n; k += 32) {
-                const int xx = x0 + k % bw, yy = y0 + k / bw;
+                const int rk = bbox_row(k, bw, ibw);
+                const int xx = x0 + (k - rk * bw), yy = y0 + rk;
                 float e;
                 const float a = gauss_alpha(g, xx + 0.5f, yy + 0.5f, e);
                 const int64_t p = (int64_t)yy * W + xx;
