@@ -421,6 +421,16 @@ GES_API const char *ges_last_error_message(void);
 /* ABI version of this header. */
 GES_API int32_t ges_version(void);
 
+/* Self-test of the bounded wait that the pipelined batch raster uses on its
+ * shared-memory mbarriers (no fault is involved: the wait gives up by design).
+ * One warp waits on a barrier that another warp completes, then on one that
+ * nothing completes, which must give up after limit_ms (1..10000) of device
+ * time.  out[0] = 1 when the first wait returned completed; out[1] = 1 when
+ * the second gave up; out[2] = how long it waited, in microseconds.  Uses the
+ * current device and stream 0; synchronises.  GES_ERR_INVALID_ARG for a NULL
+ * out or a limit outside the range. */
+GES_API ges_status ges_selftest_wait_timeout(int32_t limit_ms, int64_t *out);
+
 #ifdef __cplusplus
 }
 #endif

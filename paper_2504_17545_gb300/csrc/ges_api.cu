@@ -721,6 +721,28 @@ ges_status ges_get_profile(ges_scene *s, ges_profile *out)
     return GES_OK;
 }
 
+ges_status ges_selftest_wait_timeout(int32_t limit_ms, int64_t *out)
+{
+    if (!out) return fail(GES_ERR_INVALID_ARG, "out is NULL");
+    if (limit_ms < 1 || limit_ms > 10000) return fail(GES_ERR_INVALID_ARG, "limit_ms %d not in [1,10000]", limit_ms);
+    int dev = 0;
+    GES_CUDA(cudaGetDevice(&dev));
+    ges_status r = check_device(&dev);
+    if (r != GES_OK) return r;
+    unsigned *d = nullptr;
+    GES_CUDA(cudaMalloc(&d, 4 * sizeof(unsigned)));
+    unsigned h[4] = {0u, 0u, 0u, 0u};
+    cudaError_t e = cudaMemset(d, 0, sizeof h);
+    if (e == cudaSuccess) e = launch_wait_selftest((unsigned long long)limit_ms * 1000000ull, d, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof h, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "wait self-test");
+    out[0] = h[0];
+    out[1] = h[1];
+    out[2] = (int64_t)((((unsigned long long)h[3] << 32) | h[2]) / 1000ull);
+    return GES_OK;
+}
+
 const char *ges_last_error_message(void) { return g_err.c_str(); }
 
 int32_t ges_version(void) { return 1; }

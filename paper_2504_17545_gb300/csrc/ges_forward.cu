@@ -92,14 +92,6 @@ __device__ __forceinline__ GaussRec gauss_rec3(float4 a, float4 b, float4 c)
     return g;
 }
 
-__device__ __forceinline__ void store_rec(float4 *dst, const GaussRec &r)
-{
-    dst[0] = make_float4(r.px, r.py, r.pxl, r.pyl);
-    dst[1] = make_float4(r.la, r.lb, r.lc, r.sigma);
-    dst[2] = make_float4(r.key, r.r, r.g, r.b);
-    dst[3] = make_float4(__int_as_float(r.id), __uint_as_float(r.bb_lo), __uint_as_float(r.bb_hi), r.pad);
-}
-
 // Set up primitive i of the given kind; on success write its record and
 // return its pixel bbox.
 // kGd: the scene's Gaussian kind (a template argument, so that each kernel
@@ -959,8 +951,10 @@ __device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity)
     return ok != 0u;
 }
 // Bounded wait for the phase of the given parity: false when the CTA's abort
-// flag is set or after about a second.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, const volatile int *abort)
+// flag is set, after limit_ns of %globaltimer time (about a second by
+// default) or after 2^28 polls, whichever comes first.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, const volatile int *abort,
+                                          unsigned long long limit_ns = 1000000000ull)
 {
     unsigned long long t0 = 0ull;
     for (unsigned it = 0; it < (1u << 28); ++it) {
@@ -969,11 +963,40 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, const v
         if ((it & 63u) == 63u) {
             const unsigned long long t = global_timer_ns();
             if (t0 == 0ull) t0 = t;
-            else if (t - t0 > 1000000000ull) return false;
+            else if (t - t0 > limit_ns) return false;
         }
     }
     return false;
 }
+
+// Self-test of the bounded wait (the one the pipelined raster uses), with no
+// fault involved: warp 0 waits on an mbarrier that completes (one arrival by
+// warp 1 first), then on one that nothing arrives at, which must give up after
+// limit_ns.  out: [completed wait ok, idle wait gave up, its duration in ns (2 words)].
+__global__ void __launch_bounds__(64) k_wait_selftest(unsigned long long limit_ns, unsigned *out)
+{
+    __shared__ __align__(8) unsigned long long bars[2];
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bars[0]), 1u);
+        mbar_init(smem_u32(&bars[1]), 1u);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 32) mbar_arrive(smem_u32(&bars[0]));
+    if (threadIdx.x == 0) {
+        const bool ok = mbar_wait(smem_u32(&bars[0]), 0u, &abort_flag, limit_ns);
+        const unsigned long long t0 = global_timer_ns();
+        const bool idle = mbar_wait(smem_u32(&bars[1]), 0u, &abort_flag, limit_ns);
+        const unsigned long long dt = global_timer_ns() - t0;
+        out[0] = ok ? 1u : 0u;
+        out[1] = idle ? 0u : 1u;
+        out[2] = (unsigned)(dt & 0xffffffffull);
+        out[3] = (unsigned)(dt >> 32);
+    }
+}
+
 // Global -> shared bulk copy completing on an mbarrier (both addresses 16-byte
 // aligned, size a multiple of 16).
 __device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned bytes, unsigned bar)
@@ -1173,6 +1196,12 @@ cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const Opt
     else if (P.gdim == 2) k_braster<1, 2><<<grid, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
     else k_braster<1, 3><<<grid, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
     mark(4);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(unsigned long long limit_ns, unsigned *d_out, cudaStream_t st)
+{
+    k_wait_selftest<<<1, 64, 0, st>>>(limit_ns, d_out);
     return cudaGetLastError();
 }
 

@@ -125,6 +125,8 @@ constexpr int kFillThreads = 1024;
 LocalBins plan_local_bins(int64_t N, int64_t M, int num_sms);
 size_t local_bins_smem(int T, bool fill);
 cudaError_t prepare_forward_kernels();   // once per device: large dynamic shared memory
+// Self-test of the pipelined raster's bounded mbarrier wait (4 device words out).
+cudaError_t launch_wait_selftest(unsigned long long limit_ns, unsigned *d_out, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // host launchers (ges_forward.cu / ges_backward.cu)

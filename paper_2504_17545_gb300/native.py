@@ -115,6 +115,7 @@ _SIGS = {
     "ges_get_profile": (C.c_int, [C.c_void_p, _P(ges_profile)]),
     "ges_last_error_message": (C.c_char_p, []),
     "ges_version": (C.c_int32, []),
+    "ges_selftest_wait_timeout": (C.c_int, [C.c_int32, _P(C.c_int64)]),
 }
 
 _lib = None
@@ -252,6 +253,13 @@ def ges_last_error_message() -> str:
 
 def ges_version() -> int:
     return int(load().ges_version())
+
+
+def ges_selftest_wait_timeout(limit_ms: int):
+    """(completed wait ok, idle wait gave up, its duration in microseconds)."""
+    out = (C.c_int64 * 3)()
+    _check(load().ges_selftest_wait_timeout(int(limit_ms), out))
+    return bool(out[0]), bool(out[1]), int(out[2])
 
 
 def ges_count_fragments(scene, cam: ges_camera, opts):

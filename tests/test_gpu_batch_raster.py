@@ -129,3 +129,21 @@ def test_batch_raster_auto_times_both_kinds(R, monkeypatch):
     assert (b.rgb[0] == single["rgb"]).all() and (b.depth[0] == single["depth"]).all()
     b.close()
     gs.close()
+
+
+def test_bounded_mbarrier_wait_gives_up(R):
+    """The pipelined raster's shared-memory waits are bounded: on a barrier
+    that nothing completes, the wait returns after its limit (device time)
+    and the GPU stays usable.  No fault is involved."""
+    from paper_2504_17545_gb300 import native as N
+    ok, gave_up, us = N.ges_selftest_wait_timeout(50)
+    assert ok and gave_up, (ok, gave_up, us)
+    assert 50_000 <= us < 5_000_000, us
+    # the context still works
+    scene, cams = sg.config_scene(0)
+    gs = R.GESScene.from_arrays(scene)
+    out = R.render(gs, cams[0])
+    assert out["rgb"].isfinite().all()
+    gs.close()
+    with pytest.raises(N.GesError):
+        N.ges_selftest_wait_timeout(0)
