@@ -715,14 +715,6 @@ __device__ __forceinline__ void surfel_colour(const SceneView &S, int64_t i, Sur
     sh_colour(S.s_sh, i, K, S.sh_dtype, Y, o.rgb, o.raw);
 }
 
-// Geometry and colour.
-__device__ __forceinline__ void surfel_setup(const SceneView &S, const CamParams &C, const OptParams &O,
-                                             int64_t i, SurfelOut &o, float4 *tside = nullptr)
-{
-    surfel_geom(S, C, O, i, o, tside);
-    if (o.visible) surfel_colour(S, i, o);
-}
-
 struct GaussOut {
     bool valid_quat;
     bool visible;
