@@ -175,3 +175,28 @@ def test_contribution_scores_match_oracle(R):
     keep = ~gt
     assert keep.mean() > 0.75 and (ref[keep] > 0).sum() > 100
     np.testing.assert_allclose(got[keep], ref[keep], rtol=2e-4, atol=1e-6)
+
+
+def test_translucent_nonpositive_w_are_never_drawn(R):
+    """w <= 0 (or a zero weight left by pruning) gives alpha = 0 everywhere:
+    such surfels are never blended, never frontmost and get no gradient."""
+    import torch
+    sc, cam, w = _scene_w("cfg0", 11)
+    rng = np.random.default_rng(12)
+    off = rng.random(sc.n_surfels) < 0.3
+    w = w.copy()
+    w[off] = np.where(rng.random(off.sum()) < 0.5, 0.0, -1.0)
+    gs, out = _run(R, sc, cam, w, True, cover=True)
+    ref = oracle.render_translucent(sc, cam, w, True)
+    res = _fwd_compare(out, ref)
+    assert res["pass"], json.dumps(res)
+    front = out["front"].cpu().numpy()
+    assert not off[front[front >= 0]].any()
+    assert (out["cover"].cpu().numpy()[off] == 0).all()
+    g = torch.as_tensor(np.random.default_rng(13).standard_normal((3, cam.height, cam.width)), dtype=torch.float32,
+                        device="cuda")
+    wt = torch.as_tensor(w, dtype=torch.float32, device="cuda")
+    gr = R.render_translucent_backward(gs, cam, wt, out, g, True)
+    for k in ("s_pos", "s_rot", "s_scale", "s_w", "s_sh"):
+        assert (gr[k].cpu().numpy()[off] == 0).all(), k
+    gs.close()
