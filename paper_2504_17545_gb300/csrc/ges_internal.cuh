@@ -942,6 +942,27 @@ __device__ __forceinline__ void gauss2d_setup(const SceneView &S, const CamParam
     o.visible = true;
 }
 
+// float -> int64 rounded to nearest (ties to even) for the fixed-point sums,
+// on the FP32 and integer pipes (the library's int64 conversion runs on the
+// FP64 pipe, which GB300 has little of: it limited the Gaussian pass).
+// x is first clamped to +-2^41, the range the sums are built for (a term of
+// 2^41 units of 2^-32 is 512, where alpha <= 1 and colours of a few units
+// are the method's range); inside it the result equals __float2ll_rn(x)
+// exactly: x = h 2^20 + l with h = rint(x 2^-20) and |l| <= 2^19 both exact
+// in float, each rounded to an integer by adding 1.5 2^23 (where the float
+// spacing is 1) and reading the bits.  NaN saturates to the upper bound.
+__device__ __forceinline__ long long f2ll_rn_sat(float x)
+{
+    x = fminf(fmaxf(x, -2199023255552.f), 2199023255552.f);   // +-2^41
+    const float M = 12582912.f;                        // 1.5 2^23
+    const float t = fmaf(x, 9.5367431640625e-07f, M);  // x 2^-20 + M, rounded to an integer
+    const float h = t - M;                             // that integer, exactly
+    const float l = fmaf(-h, 1048576.f, x);            // x - h 2^20, exactly
+    const int hi = __float_as_int(t) - __float_as_int(M);
+    const int li = __float_as_int(l + M) - __float_as_int(M);
+    return (long long)hi * 1048576LL + li;
+}
+
 // Row of pixel k of a w-wide bbox walked row-major (k / w) without an integer
 // division: the quotient from the float reciprocal iw = 1/w is within one of
 // the exact one for every bbox of an image of at most 16384^2 (k exact in
