@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(256) k_surfel_scatter(int64_t N, CamParams C, 
         const float kk = (full ? 1.f / (1.f + __ldg(aux + pix)) : 1.f) * (float)won / (float)O.samples;
         unsigned long long *a = reinterpret_cast<unsigned long long *>(acc + 3 * (int64_t)s);
         for (int c = 0; c < 3; ++c) {
-            const long long v = f2ll_rn_sat(kk * g[c] * scale);   // |v| <= 2^30
+            const long long v = f2ll_rn(kk * g[c] * scale);   // |v| <= 2^30
             if (v != 0) atomicAdd(a + c, (unsigned long long)v);
         }
     }

@@ -624,17 +624,17 @@ __device__ __forceinline__ void gauss_pass(const Recs &R, int n, const WarpBlock
                 if (kGeo) { side = R(4, jj); depth = side.w; }
             }
             // alpha * 2^32 is exact scaling: the clamp decision equals alpha >= alpha_min
-            const float a32 = a * 4294967296.f;
+            const float a32 = fminf(a * 4294967296.f, kAlpha32Max);
             if (B.in_img && a32 >= amin32 && ok != 0.f) {
-                acc.w += f2ll_rn_sat(a32);
-                acc.r += f2ll_rn_sat(a32 * cr);
-                acc.g += f2ll_rn_sat(a32 * cg);
-                acc.b += f2ll_rn_sat(a32 * cb);
+                acc.w += f2ll_rn(a32);
+                acc.r += f2ll_rn(a32 * cr);
+                acc.g += f2ll_rn(a32 * cg);
+                acc.b += f2ll_rn(a32 * cb);
                 if (kGeo) {
                     acc.d += __float2ll_rn(a32 * depth);
-                    acc.nx += f2ll_rn_sat(a32 * side.x);
-                    acc.ny += f2ll_rn_sat(a32 * side.y);
-                    acc.nz += f2ll_rn_sat(a32 * side.z);
+                    acc.nx += f2ll_rn(a32 * side.x);
+                    acc.ny += f2ll_rn(a32 * side.y);
+                    acc.nz += f2ll_rn(a32 * side.z);
                 }
             }
         }

@@ -251,6 +251,14 @@ __device__ __forceinline__ unsigned long long global_timer_ns()
     return t;
 }
 
+// Range of the Gaussian pass's fixed-point terms (units of 2^-32): alpha 2^32
+// is capped at 2^33 and a Gaussian's colour in its record at kColourMax, so
+// every term alpha 2^32 c stays below 2^41 and converts exactly (f2ll_rn).
+// Both caps lie far outside the method's range (alpha <= 1, colours of a few
+// units).
+constexpr float kColourMax = 256.f;
+constexpr float kAlpha32Max = 8589934592.f;   // 2^33
+
 __device__ __forceinline__ float ex2_approx(float x)
 {
     float y;
@@ -854,14 +862,15 @@ __device__ __forceinline__ void gauss_geom(const SceneView &S, const CamParams &
 }
 
 // The colour of a Gaussian set up by gauss_geom (Eq. 1 at o.dir), also into
-// its record.
+// its record (at most kColourMax there).
 __device__ __forceinline__ void gauss_colour(const SceneView &S, int64_t i, GaussOut &o)
 {
     const int K = (S.deg + 1) * (S.deg + 1);
     float Y[16];
     sh_basis(K, o.dir[0], o.dir[1], o.dir[2], Y);
     sh_colour(S.g_sh, i, K, S.sh_dtype, Y, o.rgb, o.raw);
-    o.rec.r = o.rgb[0]; o.rec.g = o.rgb[1]; o.rec.b = o.rgb[2];
+    o.rec.r = fminf(o.rgb[0], kColourMax); o.rec.g = fminf(o.rgb[1], kColourMax);
+    o.rec.b = fminf(o.rgb[2], kColourMax);
 }
 
 // Geometry and colour.
@@ -937,23 +946,21 @@ __device__ __forceinline__ void gauss2d_setup(const SceneView &S, const CamParam
     sh_basis(K, o.dir[0], o.dir[1], o.dir[2], Y);
     sh_colour(S.g_sh, i, K, S.sh_dtype, Y, o.rgb, o.raw);
     const float lsig = log2f(sigp);
-    o.aux[0] = make_float4(o.rgb[0], o.rgb[1], o.rgb[2], lsig);
+    o.aux[0] = make_float4(fminf(o.rgb[0], kColourMax), fminf(o.rgb[1], kColourMax), fminf(o.rgb[2], kColourMax),
+                           lsig);
     o.aux[1] = make_float4(fl * n[0], fl * n[1], fl * n[2], log2f(O.alpha_min) - lsig);
     o.visible = true;
 }
 
 // float -> int64 rounded to nearest (ties to even) for the fixed-point sums,
 // on the FP32 and integer pipes (the library's int64 conversion runs on the
-// FP64 pipe, which GB300 has little of: it limited the Gaussian pass).
-// x is first clamped to +-2^41, the range the sums are built for (a term of
-// 2^41 units of 2^-32 is 512, where alpha <= 1 and colours of a few units
-// are the method's range); inside it the result equals __float2ll_rn(x)
-// exactly: x = h 2^20 + l with h = rint(x 2^-20) and |l| <= 2^19 both exact
-// in float, each rounded to an integer by adding 1.5 2^23 (where the float
-// spacing is 1) and reading the bits.  NaN saturates to the upper bound.
-__device__ __forceinline__ long long f2ll_rn_sat(float x)
+// FP64 pipe, which GB300 has little of: it limited the Gaussian pass).  For
+// |x| < 2^42 the result equals __float2ll_rn(x) exactly: x = h 2^20 + l with
+// h = rint(x 2^-20) and |l| <= 2^19 both exact in float, each rounded to an
+// integer by adding 1.5 2^23 (where the float spacing is 1) and reading the
+// bits.  Callers keep their terms inside that range (see kColourMax).
+__device__ __forceinline__ long long f2ll_rn(float x)
 {
-    x = fminf(fmaxf(x, -2199023255552.f), 2199023255552.f);   // +-2^41
     const float M = 12582912.f;                        // 1.5 2^23
     const float t = fmaf(x, 9.5367431640625e-07f, M);  // x 2^-20 + M, rounded to an integer
     const float h = t - M;                             // that integer, exactly
