@@ -1058,7 +1058,7 @@ ges_status ges_batch_sync(ges_batch *b)
     // word 4 after the views' status: a wait of the pipelined raster gave up
     // (1: a consumer warp, 2: the producer warp)
     if (const unsigned pw = b->h_status[(size_t)b->n * ST_WORDS + 4])
-        return fail(GES_ERR_INTERNAL, "the pipelined raster's waits gave up (code %u)", pw);
+        return fail(GES_ERR_TIMEOUT, "the pipelined raster's waits gave up (code %u)", pw);
     for (int v = 0; v < b->n; ++v) {
         const unsigned *w = b->h_status + (size_t)v * ST_WORDS;
         if (w[ST_FLAGS] & FLAG_BADQ)
