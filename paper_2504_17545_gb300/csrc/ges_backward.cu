@@ -3,15 +3,19 @@
 // scale, opacity and SH coefficients, and surfel SH coefficients (surfel
 // geometry is fixed in that stage and gets none).
 //
-// Gather form, no atomics: one thread per primitive.  Each thread sets its
-// primitive up with the same device function as the forward pass (so the alpha
-// and depth-test decisions are bit-identical); then the warp sweeps its 32
-// primitives' pixel bboxes one primitive at a time, one pixel per lane (rows
-// read coalesced), and reduces the per-lane partial sums with a fixed
-// butterfly into the owning lane.  Finally each thread runs the chain rule for
-// its own primitive.  The summation order is fixed, so the result is
-// deterministic.  (Sweeping each footprint in its own lane was measured slower:
+// Gaussians, gather form without atomics, in three launches: k_gbwd_rec sets
+// every Gaussian up with the forward's device function (so the alpha and
+// depth-test decisions are bit-identical) and keeps its record and what the
+// chain rule needs; k_gbwd_sweep has each warp sweep its 32 Gaussians' pixel
+// bboxes one Gaussian at a time, one pixel per lane (rows read coalesced),
+// against per-pixel terms k_pixgrad prepared, and reduce the nine per-lane
+// partial sums in a fixed order; k_gbwd_chain runs the chain rule per
+// Gaussian.  (Sweeping each footprint in its own lane was measured slower:
 // scattered rows, long dependent loops.)
+// Surfels, scatter form: one thread per pixel adds its term to the winning
+// surfel's sums in 64-bit fixed point (exact, so the order of the atomics
+// does not matter), then one thread per surfel runs the SH chain.  Every sum
+// has a fixed value, so the result is deterministic.
 //
 // Per (Gaussian i, pixel) that passes the clamp and the depth test, with
 // k = 1/(1+W_G) (Eq. 5; 1/W_G in the Gaussians-only mode) and g = dL/dC:
