@@ -18,8 +18,9 @@
 //                stopping once T < 1e-4 after a blend; C += T bg;
 //   k_tbwd       per pixel in reverse order, dC/dc = alpha T and
 //                dC/dalpha = T (c - S_behind), chained to the surfel's camera-
-//                space frame; the warp sums each entry's terms with a fixed
-//                butterfly and adds them as 64-bit fixed point, so the result
+//                space frame; the warp reduces each entry's 18 terms in a
+//                fixed order (a halving reduce-scatter) and the lanes holding
+//                the totals add them as 64-bit fixed point, so the result
 //                does not depend on the order of the atomics;
 //   k_tfinal     per surfel: fixed point -> float, camera -> world, rotation
 //                through the quaternion's normalisation, colour -> SH.
