@@ -458,8 +458,9 @@ def run_case(args):
     """One secondary workload alone, --warmup untimed and --steps timed
     iterations, for profiler captures: the training step (forward + backward
     at 1600x1060, 500k + 500k), the translucent coarse-stage render (forward +
-    backward at 1080p, 1M surfels, early w) or the paper-shaped mix (0.2M
-    surfels + 2.5M Gaussians, 8 orbit views at 1080p as one batch graph)."""
+    backward at 1080p, 1M surfels, early w), the paper-shaped mix (0.2M
+    surfels + 2.5M Gaussians, 8 orbit views at 1080p as one batch graph) or
+    the 4x multisampled orbit (--views views of the 1080p orbit, one graph)."""
     import numpy as np
     import torch
     import scenegen as sg
@@ -473,6 +474,14 @@ def run_case(args):
         def step():
             out = R.render(gs, cams[0])
             R.render_backward(gs, cams[0], out, g)
+    elif args.case == "msaa":
+        scene, cams = sg.config_scene(1)
+        gs = R.GESScene.from_arrays(scene)
+        batch = R.GESBatch([gs], cams[:max(1, min(args.views, len(cams)))], opts=dict(samples=4))
+
+        def step():
+            batch.launch()
+            batch.sync()
     elif args.case == "paper_shaped":
         scene, cams = sg.config_scene(100)
         gs = R.GESScene.from_arrays(scene)
@@ -507,8 +516,8 @@ def main():
     ap.add_argument("--views", type=int, default=N_VIEWS,
                     help="orbit views per step (the workload is 64; fewer only for profiling captures)")
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
-    ap.add_argument("--case", default="orbit", choices=["orbit", "train_step", "translucent", "paper_shaped"],
-                    help="orbit: the benchmark; train_step / translucent / paper_shaped: run that secondary "
+    ap.add_argument("--case", default="orbit", choices=["orbit", "train_step", "translucent", "paper_shaped", "msaa"],
+                    help="orbit: the benchmark; train_step / translucent / paper_shaped / msaa: run that secondary "
                          "workload --steps times and print its timing (for profiler captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
