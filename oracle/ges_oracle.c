@@ -1365,11 +1365,15 @@ int ora_render_translucent(const ora_scene *S, const ora_camera *c, const ora_op
             }
             for (int ch = 0; ch < 3; ++ch) rgb[ch * HW + pix] = C[ch] + T * c->bg[ch];
             T_out[pix] = T;
-            /* the frontmost contributor (least depth at the pixel) */
+            /* the frontmost contributor (least depth at the pixel); another
+               contributor within the depth band of it makes the choice
+               ambiguous (either is a correct answer in finite precision) */
             int64_t f = -1;
             double fz = INFINITY;
             for (int64_t k = 0; k < n; ++k)
                 if (list[k].z < fz || (list[k].z == fz && list[k].s < f)) { f = list[k].s; fz = list[k].z; }
+            for (int64_t k = 0; k < n; ++k)
+                if (list[k].s != f && list[k].z - fz <= o->tol_depth_rel * fz) a8 |= AMB_ID;
             front[pix] = (int32_t)f;
             nblend[pix] = nb;
             amb[pix] = a8;
