@@ -14,7 +14,7 @@ import numpy as np
 
 import oracle
 
-COL_TOL = 2e-4       # spec colour tolerance for FP32 work
+COL_TOL = 2e-4       # colour tolerance of the FP32 path (absolute, per channel)
 # GPU depth = 1/(iz0 + gu du + gv dv): iz0 carries the rounding of the
 # double-float centre and of its reciprocal (~3u), the affine step ~2u, the
 # final reciprocal 1u, and 16-bit quaternions renormalised in float32 a few u
