@@ -848,12 +848,15 @@ __device__ __forceinline__ void gauss_geom(const SceneView &S, const CamParams &
     if (O.geo) {
         // geometry (Sec. 6.4): d_i = centre depth, n_i = the axis of the smallest
         // scale, camera space, facing the camera
-        int km = 0;
-        for (int k = 1; k < 3; ++k)
-            if (fabsf(o.s[k]) < fabsf(o.s[km])) km = k;
+        // (the column is selected, not indexed: a run-time index into o.s or
+        // o.R would keep those arrays, and the set-up around them, in local
+        // memory)
+        const float a0 = fabsf(o.s[0]), a1 = fabsf(o.s[1]), a2 = fabsf(o.s[2]);
+        const int km = a1 < a0 ? (a2 < a1 ? 2 : 1) : (a2 < a0 ? 2 : 0);
+        float ax[3];
+        for (int r = 0; r < 3; ++r) ax[r] = km == 0 ? o.R[3 * r] : (km == 1 ? o.R[3 * r + 1] : o.R[3 * r + 2]);
         float nc[3];
-        for (int r = 0; r < 3; ++r)
-            nc[r] = C.R[3 * r] * o.R[km] + C.R[3 * r + 1] * o.R[3 + km] + C.R[3 * r + 2] * o.R[6 + km];
+        for (int r = 0; r < 3; ++r) nc[r] = C.R[3 * r] * ax[0] + C.R[3 * r + 1] * ax[1] + C.R[3 * r + 2] * ax[2];
         const float fl = (nc[0] * x + nc[1] * y + nc[2] * z) > 0.f ? -1.f : 1.f;
         o.aux[0] = make_float4(fl * nc[0], fl * nc[1], fl * nc[2], z);
         o.aux[1] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1056,15 +1059,17 @@ __device__ __forceinline__ void store_zeros(float *dst, int n)
 // SH coefficient gradients of one primitive: dst[3k + c] = Y_k gc_c, zero for
 // the channels whose unclamped colour raw_c is not positive (raw null: no
 // gate).  A thread writes 3K consecutive floats, in 16-byte stores where the
-// row allows it (fewer, fuller memory transactions than scalar stores).
-__device__ __forceinline__ void store_sh_grad(float *dst, int K, const float *Y, const float *gc, const float *raw)
+// row allows it (fewer, fuller memory transactions than scalar stores).  K is
+// a template parameter so that every index into Y and g is a constant: a
+// run-time index would put both arrays in local memory.
+template <int K>
+__device__ __forceinline__ void store_sh_grad_k(float *dst, const float *Y, const float *g)
 {
-    float g[3];
-    for (int c = 0; c < 3; ++c) g[c] = (raw == nullptr || raw[c] > 0.f) ? gc[c] : 0.f;
-    if (((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) && ((3 * K) & 3) == 0) {
+    if (((3 * K) & 3) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
         // 3K = 4 m: float4 number q holds entries 4q .. 4q + 3, i.e. basis
         // functions (4q + e) / 3 and channels (4q + e) % 3
         float4 *d4 = reinterpret_cast<float4 *>(dst);
+#pragma unroll
         for (int q = 0; q < (3 * K) / 4; ++q) {
             float v[4];
 #pragma unroll
@@ -1075,8 +1080,21 @@ __device__ __forceinline__ void store_sh_grad(float *dst, int K, const float *Y,
             d4[q] = make_float4(v[0], v[1], v[2], v[3]);
         }
     } else {
+#pragma unroll
         for (int k = 0; k < K; ++k)
+#pragma unroll
             for (int c = 0; c < 3; ++c) dst[3 * k + c] = Y[k] * g[c];
+    }
+}
+__device__ __forceinline__ void store_sh_grad(float *dst, int K, const float *Y, const float *gc, const float *raw)
+{
+    float g[3];
+    for (int c = 0; c < 3; ++c) g[c] = (raw == nullptr || raw[c] > 0.f) ? gc[c] : 0.f;
+    switch (K) {
+    case 16: store_sh_grad_k<16>(dst, Y, g); break;
+    case 9: store_sh_grad_k<9>(dst, Y, g); break;
+    case 4: store_sh_grad_k<4>(dst, Y, g); break;
+    default: store_sh_grad_k<1>(dst, Y, g); break;
     }
 }
 
