@@ -67,6 +67,33 @@ def test_two_discs_blend_in_centre_depth_order(oracle_lib):
         np.testing.assert_allclose(out["rgb"], want, rtol=0, atol=1e-14)
 
 
+def test_front_choice_is_ambiguous_only_within_the_depth_band(oracle_lib):
+    """The frontmost contributor (least depth at the pixel) is a unique answer
+    only when no other contributor lies within the depth band of it.  Two
+    coplanar discs tie everywhere they overlap, which is flagged in both blend
+    orders.  With one disc clearly nearer it is the front surfel, and the
+    front choice adds no flag."""
+    cam = ident_cam(40, 40, 40.0)
+    c0, c1 = (0.9, 0.1, 0.1), (0.1, 0.1, 0.9)
+    w = np.array([0.8, 0.6])
+    tie = _discs([2.0, 2.0], [0.1, 0.12], [c0, c1], pos_xy=[[0.01, 0.0], [0.0, 0.01]])
+    for ff in (False, True):
+        out = oracle_lib.render_translucent(tie, cam, w, front_first=ff)
+        both = out["nblend"] == 2
+        assert both.sum() > 50
+        assert np.all(out["amb"][both] != 0)
+        if not ff:
+            assert np.all((out["amb"][both] & 1) != 0)
+    near = _discs([2.0, 1.5], [0.1, 0.12], [c0, c1], pos_xy=[[0.01, 0.0], [0.0, 0.01]])
+    for ff in (False, True):
+        out = oracle_lib.render_translucent(near, cam, w, front_first=ff)
+        both = out["nblend"] == 2
+        clear = both & (out["amb"] == 0)
+        assert clear.sum() > 0.8 * both.sum() > 40
+        assert np.all(out["front"][both] == 1)
+        assert np.all((out["amb"][both] & 1) == 0)
+
+
 def test_front_first_moves_the_nearest_fragment(oracle_lib):
     """A large tilted disc whose centre is behind a small fronto-parallel one
     but whose fragment is in front of it at some pixels: with front_first it
