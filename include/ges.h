@@ -260,7 +260,9 @@ GES_API ges_status ges_set_stream(ges_scene *scene, void *stream);
 /* Both passes of Sec. 3 and the composite of Eq. 5 for one camera.
  * out_rgb [3,H,W] and out_depth [H,W] (D_s, +inf where no surfel) are device
  * buffers.  Returns after the stream has completed the render (the call
- * checks the device status word). */
+ * checks the device status word).  Any image size: up to 32768 tiles of
+ * 16x16 pixels the binning counts in shared memory, above that with global
+ * counters (same results). */
 GES_API ges_status ges_render(ges_scene *scene, const ges_camera *cam, float *out_rgb, float *out_depth);
 
 /* As ges_render with options and two optional outputs: out_surfel_id
