@@ -798,7 +798,7 @@ size_t batch_layout(ges_batch *b, const std::vector<SceneView> &S, const std::ve
 {
     size_t off = 0;
     auto take = [&](size_t bytes) { unsigned char *p = base ? base + off : nullptr; off = align256(off + bytes); return p; };
-    int prep_base = 0, tile_base = 0, col_base = 0;
+    int prep_base = 0, tile_base = 0, col_base = 0, sprep_base = 0, gprep_base = 0;
     for (int v = 0; v < b->n; ++v) {
         BatchView &bv = b->views[v];
         const int64_t N = std::max<int64_t>(S[v].N, 1), M = std::max<int64_t>(S[v].M, 1);
@@ -811,9 +811,13 @@ size_t batch_layout(ges_batch *b, const std::vector<SceneView> &S, const std::ve
         bv.T = T;
         bv.tile_base = tile_base;
         bv.prep_base = prep_base;
+        bv.sprep_base = sprep_base;
+        bv.gprep_base = gprep_base;
         bv.colscan_base = col_base;
         tile_base += T;
         prep_base += B.Ps + B.Pg;
+        sprep_base += B.Ps;
+        gprep_base += B.Pg;
         col_base += (T + 31) / 32;
         ViewScratch &X = bv.X;
         X.s_rec = (float4 *)take(N * 64);
@@ -938,10 +942,12 @@ ges_status ges_batch_create(ges_scene *const *scenes, const ges_camera *cams, co
         for (const RasterCand &cnd : rc) {
             const int per_sm = cnd.per_sm;
             batch_layout(b, S, C, R, (unsigned char *)b->arena);
-            BatchPlan P{n_views, 0, 0, 0, 0, sms * per_sm, S[0].gdim, cnd.pipe};
+            BatchPlan P{n_views, 0, 0, 0, 0, 0, 0, sms * per_sm, S[0].gdim, cnd.pipe};
             for (int v = 0; v < n_views; ++v) {
                 P.total_tiles += b->views[v].T;
                 P.total_prep += b->views[v].B.Ps + b->views[v].B.Pg;
+                P.total_sprep += b->views[v].B.Ps;
+                P.total_gprep += b->views[v].B.Pg;
                 P.total_colscan += (b->views[v].T + 31) / 32;
                 P.max_T = std::max(P.max_T, b->views[v].T);
             }

@@ -144,13 +144,15 @@ __device__ __forceinline__ bool setup_and_store(const SceneView &S, const CamPar
 
 // CTA c of a view: its range of primitives.  hist: ceil(T/2) shared words
 // (two 16-bit counters each); vcnt: a shared counter.
-template <int kGd, bool kTr = false>
+// kKind: 0 both kinds (CTA c < B.Ps: surfels), 1 surfel ranges only, 2
+// Gaussian ranges only (a launch per kind gives each its own registers)
+template <int kGd, bool kTr = false, int kKind = 0>
 __device__ __forceinline__ void prep_local_body(const SceneView &S, const CamParams &C, const OptParams &O,
                                                 const ViewScratch &X, const LocalBins &B, int c, unsigned *hist,
                                                 unsigned &vcnt)
 {
     const int T = C.tiles_x * C.tiles_y, words = (T + 1) >> 1;
-    const bool surf = c < B.Ps;
+    const bool surf = kKind == 1 ? true : (kKind == 2 ? false : c < B.Ps);
     const int64_t R = surf ? B.Rs : B.Rg, n = surf ? S.N : S.M;
     const int64_t beg = (int64_t)(surf ? c : c - B.Ps) * R;
     const int64_t end = beg + R < n ? beg + R : n;
@@ -786,7 +788,11 @@ __device__ __forceinline__ void load_view(const BatchView *V, int v, BatchView &
     for (int k = threadIdx.x; k < (int)(sizeof(BatchView) / 4); k += blockDim.x) d[k] = src[k];
 }
 
-template <int kGd>
+// Preprocess of all views, one launch per primitive kind (kKind 1: the
+// surfel ranges, 2: the Gaussian ranges); CTA x of the launch is range
+// x - base(view) of its kind.  The two set-ups need different registers, and
+// a kernel per kind keeps the one from spilling for the other.
+template <int kGd, int kKind>
 __global__ void __launch_bounds__(kPrepThreads, 2) k_bprep(const BatchView *V, int n, OptParams O,
                                                           unsigned long long *t0)
 {
@@ -798,12 +804,13 @@ __global__ void __launch_bounds__(kPrepThreads, 2) k_bprep(const BatchView *V, i
     if (threadIdx.x == 0) {
         // the first CTA to start stamps the batch's start time (t0 is zeroed per launch)
         atomicCAS(t0, 0ull, global_timer_ns());
-        sv = find_view(n, blockIdx.x, [&](int k) { return V[k].prep_base; });
+        sv = find_view(n, blockIdx.x, [&](int k) { return kKind == 1 ? V[k].sprep_base : V[k].gprep_base; });
     }
     __syncthreads();
     load_view(V, sv, bv);
     __syncthreads();
-    prep_local_body<kGd>(bv.S, bv.C, O, bv.X, bv.B, blockIdx.x - bv.prep_base, hist, vcnt);
+    const int c = kKind == 1 ? (int)blockIdx.x - bv.sprep_base : bv.B.Ps + (int)blockIdx.x - bv.gprep_base;
+    prep_local_body<kGd, false, kKind>(bv.S, bv.C, O, bv.X, bv.B, c, hist, vcnt);
 }
 
 __global__ void __launch_bounds__(256) k_bcolscan(const BatchView *V, int n)
@@ -1164,12 +1171,17 @@ cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const Opt
     // ev (5 events or null): recorded as graph event nodes when captured
     auto mark = [&](int k) { if (ev) cudaEventRecordWithFlags(ev[k], st, cudaEventRecordExternal); };
     mark(0);
-    if (P.total_prep > 0)
     {
         unsigned long long *t0 = reinterpret_cast<unsigned long long *>(work_counter + 2);
         const size_t sm = local_bins_smem(P.max_T, false);
-        if (P.gdim == 2) k_bprep<2><<<P.total_prep, kPrepThreads, sm, st>>>(d_views, P.n, O, t0);
-        else k_bprep<3><<<P.total_prep, kPrepThreads, sm, st>>>(d_views, P.n, O, t0);
+        if (P.total_sprep > 0) {
+            if (P.gdim == 2) k_bprep<2, 1><<<P.total_sprep, kPrepThreads, sm, st>>>(d_views, P.n, O, t0);
+            else k_bprep<3, 1><<<P.total_sprep, kPrepThreads, sm, st>>>(d_views, P.n, O, t0);
+        }
+        if (P.total_gprep > 0) {
+            if (P.gdim == 2) k_bprep<2, 2><<<P.total_gprep, kPrepThreads, sm, st>>>(d_views, P.n, O, t0);
+            else k_bprep<3, 2><<<P.total_gprep, kPrepThreads, sm, st>>>(d_views, P.n, O, t0);
+        }
     }
     mark(1);
     if (P.total_colscan > 0) k_bcolscan<<<dim3(P.total_colscan, 2), 256, 0, st>>>(d_views, P.n);
@@ -1214,8 +1226,10 @@ cudaError_t prepare_forward_kernels()
     if ((e = cudaFuncSetAttribute(k_prep_local<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(k_prep_local<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(k_prep_local<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(k_bprep<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(k_bprep<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess)
+        (e = cudaFuncSetAttribute(k_bprep<3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_bprep<3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_bprep<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_bprep<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess)
         return e;
     if ((e = cudaFuncSetAttribute(k_fill_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)local_bins_smem(kLocalMaxTiles, true))) != cudaSuccess)

@@ -109,10 +109,12 @@ struct BatchView {
     LocalBins B;
     float *rgb, *depth;
     int T, tile_base, prep_base, colscan_base;
+    int sprep_base, gprep_base;   // first CTA of the view's surfel / Gaussian ranges in their own launches
 };
 struct BatchPlan {
     int n;                                   // views
     int total_tiles, total_prep, total_colscan, max_T;
+    int total_sprep, total_gprep;            // preprocess CTAs of the surfel and the Gaussian launch
     int raster_ctas;                         // persistent raster grid
     int gdim;                                // Gaussian kind of every scene (2 or 3; 0 reads as 3)
     int pipe;                                // raster: 0 CTA-staged, 1 pipelined (producer warp + ring)
