@@ -1211,7 +1211,7 @@ extern "C" GES_API ges_status ges_render_noalloc(const ges_scene_desc *desc, con
     GES_CUDA(cudaMemsetAsync(X.status, 0, ST_WORDS * 4, st));
     SceneView S{desc->n_surfels, desc->n_gaussians, desc->sh_degree, desc->attr_dtype, desc->sh_dtype,
                 desc->s_pos, desc->s_rot, desc->s_scale, desc->s_sh, desc->g_pos, desc->g_rot, desc->g_scale,
-                desc->g_opac, desc->g_sh, desc->g_filter3d};
+                desc->g_opac, desc->g_sh, desc->g_filter3d, 3};
     cudaError_t e = launch_forward(S, C, O, X, out_rgb, out_depth, out_surfel_id, aux, st, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     unsigned w[ST_WORDS];
