@@ -95,14 +95,37 @@ OPS_PER_SURFEL_FRAGMENT = 20
 OPS_PER_GAUSS_TERM = 13
 
 
-def alu_peak():
-    """FP32 lane-instructions per second: 152 SMs x 128 FP32 lanes x the
-    maximum SM clock (MEASURED_PEAKS.json, else 2070 MHz)."""
+def sm_count():
+    """(SMs of the current device, where the number comes from): the device
+    properties when a GPU is visible, else GB300's 152."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count), "device"
+    except Exception:
+        pass
+    return 152, "GB300 nominal"
+
+
+def max_sm_mhz():
     mhz = 2070.0
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         mhz = float(json.load(open(p)).get("sm_max_mhz", mhz))
-    return 152 * 128 * mhz * 1e6
+    return mhz
+
+
+def alu_peak(sms=None):
+    """FP32 lane-instructions per second: SMs x 128 FP32 lanes x the maximum
+    SM clock (MEASURED_PEAKS.json, else 2070 MHz)."""
+    if sms is None:
+        sms = sm_count()[0]
+    return sms * 128 * max_sm_mhz() * 1e6
+
+
+def alu_peak_source():
+    sms, src = sm_count()
+    return f"{sms} SMs ({src}) x 128 FP32 lanes x {max_sm_mhz():.0f} MHz max SM clock"
 
 
 # the sources that define the batch graph's kernels (k_bprep, k_braster and
@@ -122,14 +145,24 @@ def ncu_traffic(kernel, n_views):
     """DRAM bytes of one launch of `kernel` over n_views views, from the
     committed ncu record (taken on a smaller batch of the same views and
     scaled by the views processed), or None when the kernel sources changed
-    since it was taken."""
+    since it was taken.  `kernel` may name several records (a phase made of
+    several launches, e.g. the preprocess of each primitive kind), which are
+    summed; None if any of them is missing or stale."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p)).get(kernel)
-    if not d or d.get("source_digest") != source_digest():
-        return None
-    return float(d["dram_bytes_per_view"]) * n_views
+    rec = json.load(open(p))
+    total = 0.0
+    for k in ((kernel,) if isinstance(kernel, str) else tuple(kernel)):
+        d = rec.get(k)
+        if not d or d.get("source_digest") != source_digest():
+            return None
+        total += float(d["dram_bytes_per_view"]) * n_views
+    return total
+
+
+# the batch preprocess: one launch over the surfel ranges, one over the Gaussian ranges
+PREP_KERNELS = ("k_bprep<3,1>", "k_bprep<3,2>")
 
 
 def algorithmic_bytes(n_s, n_g, s_vis, g_vis, hw, attr_bytes=4, sh_bytes=4, deg=3):
@@ -181,6 +214,42 @@ def cpu_baseline_sample(scene, cams):
     dt = time.perf_counter() - t0
     return {"value": n / dt, "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"{n} full 1080p orbit views (of 64), FP64, OpenMP over all host cores"}
+
+
+def storage_precision_cost(R, sg, views=(0, 8)):
+    """What FP16 / BF16 attribute and SH storage costs in accuracy, per view:
+    the renders of the batched workload (16 views at 1264x832, 2M surfels +
+    500k Gaussians) stored in FP32, FP16 and BF16, each against the FP64
+    oracle's render of the FP32-source scene (views 0 and 8).  Reported: max,
+    99.9th percentile and mean absolute colour error over all pixels, and the
+    fraction of surfel ids that differ where the oracle flags no ambiguity.
+    The kernel's own accuracy (against the oracle fed the same dequantised
+    values) is the parity tests' business; this is the cost of the storage.
+    Part of the CPU-baseline leg: the oracle runs on the host cores."""
+    import numpy as np
+    import torch
+    import oracle
+    oracle.build()
+    scene, cams = sg.config_scene(2)
+    refs = {v: oracle.render(scene, cams[v]) for v in views}
+    res = {"workload": "16x1264x832-2M-surfels-500k-gaussians", "views": list(views),
+           "reference": "FP64 oracle on the FP32-source scene"}
+    for name, dt in (("fp32", torch.float32), ("fp16", torch.float16), ("bf16", torch.bfloat16)):
+        gs = R.GESScene.from_arrays(scene, attr_dtype=dt, sh_dtype=dt)
+        per = []
+        for v in views:
+            out = R.render(gs, cams[v])
+            torch.cuda.synchronize()
+            ref = refs[v]
+            err = np.abs(out["rgb"].cpu().numpy().astype(np.float64) - ref["rgb"])
+            unm = (ref["amb"] & 1) == 0
+            per.append({"view": v, "colour_max_abs": float(err.max()),
+                        "colour_p99_9_abs": float(np.percentile(err, 99.9)),
+                        "colour_mean_abs": float(err.mean()),
+                        "id_mismatch_frac": float((out["id"].cpu().numpy() != ref["id"])[unm].mean())})
+        gs.close()
+        res[name] = per
+    return res
 
 
 def reduce_max_over_ranks(ms: float, dist, device) -> float:
@@ -334,7 +403,7 @@ def msaa_extra(R, N, gs, cams):
                                 "units_per_launch": {"sample_fragments": len(cams) * sfrag,
                                                      "gauss_terms": len(cams) * gterm}},
             "autotuned": {"prims_per_cta": info.prims_per_cta, "raster_ctas_per_sm": info.raster_ctas_per_sm,
-                                 "raster": "pipelined" if info.raster_pipelined else "classic"}}
+                                 "tile": f"{info.tile_w}x{info.tile_h}"}}
 
 
 def mip_extra(R, N, gs, cams):
@@ -361,7 +430,7 @@ def mip_extra(R, N, gs, cams):
             "kernel_ms_per_frame": {k: prof[k][0] / prof[k][1] / len(cams) for k in prof},
             "gauss_terms_per_frame": float(np.mean([f[1] for f in frags])),
             "autotuned": {"prims_per_cta": info.prims_per_cta, "raster_ctas_per_sm": info.raster_ctas_per_sm,
-                                 "raster": "pipelined" if info.raster_pipelined else "classic"}}
+                                 "tile": f"{info.tile_w}x{info.tile_h}"}}
 
 
 def orbit_2160p_extra(R, N, gs, cams):
@@ -681,15 +750,15 @@ def main():
     sec = top_ms / top_launches / 1e3
     if top == "raster":
         ops = n_views * (OPS_PER_SURFEL_FRAGMENT * sfrag + OPS_PER_GAUSS_TERM * gterm)
-        rk = "k_braster_pipe" if info.raster_pipelined else "k_braster"
+        rk = "k_braster"
         roof = {"bound": "alu", "kernel": rk, "achieved": ops / sec / 1e12, "peak": alu_peak() / 1e12,
                 "unit": "TFLOP/s", "frac": ops / sec / alu_peak(), "traffic": ncu_traffic(rk, n_views),
-                "peak_source": "152 SMs x 128 FP32 lanes x max SM clock",
+                "peak_source": alu_peak_source(),
                 "units_per_launch": {"surfel_fragments": n_views * sfrag, "gauss_terms": n_views * gterm}}
     else:
         bpl = n_views * float(np.mean(prep_b))
         roof = {"bound": "hbm", "kernel": "k_bprep", "achieved": bpl / sec / 1e9, "peak": peak,
-                "unit": "GB/s", "frac": bpl / sec / 1e9 / peak, "traffic": ncu_traffic("k_bprep", n_views),
+                "unit": "GB/s", "frac": bpl / sec / 1e9 / peak, "traffic": ncu_traffic(PREP_KERNELS, n_views),
                 "peak_source": peak_src}
     prep_ms, prep_n = prof.get("preprocess", (0.0, 1))
     prep_gbs = n_views * float(np.mean(prep_b)) / (prep_ms / prep_n / 1e3) / 1e9 if prep_ms > 0 else None
@@ -706,14 +775,14 @@ def main():
                    "l2": "inputs 332 MB > 129 MB L2, no flush", "parallelism": f"replicas{world}",
                    "launch": f"one CUDA graph per step ({kernels_per_step} kernels over all {n_views} views)",
                    "autotuned": {"prims_per_cta": info.prims_per_cta, "raster_ctas_per_sm": info.raster_ctas_per_sm,
-                                 "raster": "pipelined" if info.raster_pipelined else "classic"}},
+                                 "tile": f"{info.tile_w}x{info.tile_h}"}},
         "roofline": roof,
         "frame_roofline": {"bound": "hbm", "algorithmic_bytes_per_frame": float(np.mean(frame_b)),
                            "achieved": frame_achieved, "peak": peak, "frac": frame_achieved / peak, "unit": "GB/s"},
         "preprocess_roofline": {"bound": "hbm", "kernel": "k_bprep", "achieved": prep_gbs, "peak": peak,
                                 "frac": prep_gbs / peak if prep_gbs else None, "unit": "GB/s",
                                 "algorithmic_bytes_per_launch": n_views * float(np.mean(prep_b)),
-                                "traffic": ncu_traffic("k_bprep", n_views)},
+                                "traffic": ncu_traffic(PREP_KERNELS, n_views)},
         "kernel_ms_per_frame": {k: prof[k][0] / prof[k][1] / n_views for k in names},
         "clocks": clocks,
         "e2e": e2e,
@@ -722,6 +791,8 @@ def main():
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline_sample(scene, cams)
+        if "batched_precision" in extras:
+            extras["batched_precision"]["err_vs_fp64_oracle"] = storage_precision_cost(R, sg)
     print(json.dumps(line), flush=True)
     batch.close()
     gs.close()

@@ -350,12 +350,7 @@ GES_API ges_status ges_count_fragments(ges_scene *scene, const ges_camera *cam, 
  * ges_batch_create renders every view once through the scene's own path to
  * size the tile lists (x1.5 headroom), allocates the batch's own scratch,
  * then autotunes the primitives per preprocess CTA and the persistent raster
- * grid by timing each candidate graph, and keeps the fastest.  The raster
- * kind comes from the environment variable GES_BATCH_RASTER: classic (the
- * default; CTAs stage each chunk of records together), pipelined (a producer
- * warp gathers the records with bulk asynchronous copies into a ring of
- * shared-memory stages that the pixel warps consume without CTA-wide
- * barriers), or auto (time both).  Both give bitwise-identical images.
+ * grid by timing each candidate graph, and keeps the fastest.
  * Pointers
  * (scenes' arrays, outputs) are baked into the graph and must stay valid
  * until ges_batch_destroy.  Images must have at most 32768 tiles of 16x16
@@ -370,8 +365,7 @@ typedef struct {
     double tuned_ms;               /* best measured time of one launch */
     int64_t h2d_bytes;             /* host->device bytes of one launch (the view table) */
     int64_t d2h_bytes;             /* device->host bytes of one launch (status words) */
-    int32_t raster_pipelined;      /* 1: the pipelined raster (producer warp, bulk copies) was chosen */
-    int32_t reserved;
+    int32_t tile_w, tile_h;        /* binning tile of the chosen configuration, pixels */
 } ges_batch_info;
 
 GES_API ges_status ges_batch_create(ges_scene *const *scenes, const ges_camera *cams, const int32_t *scene_of_view,
@@ -422,16 +416,6 @@ GES_API const char *ges_last_error_message(void);
 
 /* ABI version of this header. */
 GES_API int32_t ges_version(void);
-
-/* Self-test of the bounded wait that the pipelined batch raster uses on its
- * shared-memory mbarriers (no fault is involved: the wait gives up by design).
- * One warp waits on a barrier that another warp completes, then on one that
- * nothing completes, which must give up after limit_ms (1..10000) of device
- * time.  out[0] = 1 when the first wait returned completed; out[1] = 1 when
- * the second gave up; out[2] = how long it waited, in microseconds.  Uses the
- * current device and stream 0; synchronises.  GES_ERR_INVALID_ARG for a NULL
- * out or a limit outside the range. */
-GES_API ges_status ges_selftest_wait_timeout(int32_t limit_ms, int64_t *out);
 
 #ifdef __cplusplus
 }

@@ -721,28 +721,6 @@ ges_status ges_get_profile(ges_scene *s, ges_profile *out)
     return GES_OK;
 }
 
-ges_status ges_selftest_wait_timeout(int32_t limit_ms, int64_t *out)
-{
-    if (!out) return fail(GES_ERR_INVALID_ARG, "out is NULL");
-    if (limit_ms < 1 || limit_ms > 10000) return fail(GES_ERR_INVALID_ARG, "limit_ms %d not in [1,10000]", limit_ms);
-    int dev = 0;
-    GES_CUDA(cudaGetDevice(&dev));
-    ges_status r = check_device(&dev);
-    if (r != GES_OK) return r;
-    unsigned *d = nullptr;
-    GES_CUDA(cudaMalloc(&d, 4 * sizeof(unsigned)));
-    unsigned h[4] = {0u, 0u, 0u, 0u};
-    cudaError_t e = cudaMemset(d, 0, sizeof h);
-    if (e == cudaSuccess) e = launch_wait_selftest((unsigned long long)limit_ms * 1000000ull, d, 0);
-    if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof h, cudaMemcpyDeviceToHost);
-    cudaFree(d);
-    if (e != cudaSuccess) return cuda_fail(e, "wait self-test");
-    out[0] = h[0];
-    out[1] = h[1];
-    out[2] = (int64_t)((((unsigned long long)h[3] << 32) | h[2]) / 1000ull);
-    return GES_OK;
-}
-
 const char *ges_last_error_message(void) { return g_err.c_str(); }
 
 int32_t ges_version(void) { return 1; }
@@ -924,25 +902,14 @@ ges_status ges_batch_create(ges_scene *const *scenes, const ges_camera *cams, co
     // autotune: capture a graph per candidate, time it, keep the fastest
     float best_ms = 1e30f;
     int cand = 0;
-    // raster candidates (pipelined?, resident CTAs per SM); the 4-sample
-    // kernels are built for one CTA fewer.  GES_BATCH_RASTER selects the kind:
-    // classic (the default: CTA-staged, measured faster on every workload
-    // tried), pipelined, or auto (time both)
-    struct RasterCand { int pipe, per_sm; };
-    std::vector<RasterCand> rc;
-    {
-        const char *env = std::getenv("GES_BATCH_RASTER");
-        const bool use_pipe = env && (std::strcmp(env, "pipelined") == 0 || std::strcmp(env, "auto") == 0);
-        const bool use_classic = !env || std::strcmp(env, "pipelined") != 0;
-        const int d = O.samples == 4 ? 1 : 0;
-        if (use_classic) rc.insert(rc.end(), {{0, 4 - d}, {0, 5 - d}});
-        if (use_pipe) rc.insert(rc.end(), {{1, 3 - d}, {1, 4 - d}});
-    }
+    // raster candidates: resident CTAs per SM (the 4-sample kernels are built
+    // for one CTA fewer)
+    const int d = O.samples == 4 ? 1 : 0;
+    const int kPerSm[] = {4 - d, 5 - d};
     for (int64_t R : kR) {
-        for (const RasterCand &cnd : rc) {
-            const int per_sm = cnd.per_sm;
+        for (const int per_sm : kPerSm) {
             batch_layout(b, S, C, R, (unsigned char *)b->arena);
-            BatchPlan P{n_views, 0, 0, 0, 0, 0, 0, sms * per_sm, S[0].gdim, cnd.pipe};
+            BatchPlan P{n_views, 0, 0, 0, 0, 0, 0, sms * per_sm, S[0].gdim};
             for (int v = 0; v < n_views; ++v) {
                 P.total_tiles += b->views[v].T;
                 P.total_prep += b->views[v].B.Ps + b->views[v].B.Pg;
@@ -991,7 +958,8 @@ ges_status ges_batch_create(ges_scene *const *scenes, const ges_camera *cams, co
                 b->exec = ex;
                 b->info.prims_per_cta = (int32_t)R;
                 b->info.raster_ctas_per_sm = per_sm;
-                b->info.raster_pipelined = cnd.pipe;
+                b->info.tile_w = kTile;
+                b->info.tile_h = kTile;
             } else {
                 cudaGraphExecDestroy(ex);
             }
@@ -1061,10 +1029,6 @@ ges_status ges_batch_sync(ges_batch *b)
         }
         if (i >= 0) { b->profile.ms[i] += ms; b->profile.launches[i] += 1; }
     }
-    // word 4 after the views' status: a wait of the pipelined raster gave up
-    // (1: a consumer warp, 2: the producer warp)
-    if (const unsigned pw = b->h_status[(size_t)b->n * ST_WORDS + 4])
-        return fail(GES_ERR_TIMEOUT, "the pipelined raster's waits gave up (code %u)", pw);
     for (int v = 0; v < b->n; ++v) {
         const unsigned *w = b->h_status + (size_t)v * ST_WORDS;
         if (w[ST_FLAGS] & FLAG_BADQ)

@@ -430,24 +430,12 @@ struct GeoMaps {
 };
 
 // Staged records as seen by the per-pixel loops: plane p (16-byte quarter) of
-// record j.  SoaRecs: one float4 plane per quarter (the per-view raster's
-// staging: consecutive threads store consecutive 16 B, and a warp reading one
-// record gets a broadcast).  SlotRecs: records in slots of kSlot bytes, as the
-// bulk copies of the pipelined raster leave them (kSlot / 16 odd, so the 8
-// lanes of a quarter warp reading 8 consecutive slots hit 8 different 16-byte
-// bank groups).
+// record j, one float4 plane per quarter (consecutive threads store
+// consecutive 16 B, and a warp reading one record gets a broadcast).
 template <int kPlanes>
 struct SoaRecs {
     const float4 (*st)[kChunk];
     __device__ __forceinline__ float4 operator()(int p, int j) const { return st[p][j]; }
-};
-template <int kSlot>
-struct SlotRecs {
-    const unsigned char *base;
-    __device__ __forceinline__ float4 operator()(int p, int j) const
-    {
-        return *reinterpret_cast<const float4 *>(base + j * kSlot + 16 * p);
-    }
 };
 
 // The 8x4 pixel block of one warp inside a 16x16 tile, and its lane's pixel.
@@ -894,275 +882,6 @@ __global__ void __launch_bounds__(kRasterThreads, kS == 1 && kG == 3 ? 5 : 4) k_
 }
 
 
-// ---------------------------------------------------------------------------
-// Pipelined persistent raster (warp-specialised).  One producer warp takes
-// (view, tile) items from the counter and gathers each tile's records with
-// bulk asynchronous copies (cp.async.bulk, 64 B per record plus the 2D
-// Gaussians' 32 B of side data) into a ring of shared-memory stages; each
-// stage holds one chunk of one list and a header (view, tile, kind, count,
-// first/last chunk).  Eight consumer warps, one 8x4 block of the tile each,
-// walk the stages in order: pass 1 over the surfel stages, the resolve after
-// the last one, pass 2 over the Gaussian stages, the composite after the last.
-// A stage's "full" mbarrier completes when the producer has armed it and its
-// copies have landed; its "empty" mbarrier when all eight consumers are done
-// with it.  No CTA-wide barrier is left in the loop: a warp that finishes its
-// block early moves on to the next tile's stages while the others finish.
-// The per-pixel arithmetic is the per-view raster's (the same functions), so
-// the images are bitwise identical.
-//
-// Every wait is bounded: a wait that sees the CTA's abort flag or runs for
-// about a second gives up, records the failure in the batch's status words
-// and the warp leaves its loop; the producer first waits (bounded) for the
-// copies it has issued.
-
-constexpr int kPipeC = 128;                    // records per stage
-constexpr int kPipeStages = 4;
-constexpr int kPipeConsumers = 8;              // warps, one 8x4 block each
-constexpr int kPipeThreads = 32 * (kPipeConsumers + 1);
-enum : int { PK_SURFEL = 0, PK_GAUSS = 1, PK_END = 2 };
-enum : int { PF_FIRST = 1, PF_LAST = 2 };
-
-// bytes per record slot: 64 B record (+32 B side data for 2D Gaussians),
-// padded to an odd number of 16-byte units
-template <int kG>
-__host__ __device__ constexpr int pipe_slot() { return kG == 2 ? 112 : 80; }
-template <int kG>
-__host__ __device__ constexpr int pipe_ring_bytes() { return kPipeStages * kPipeC * pipe_slot<kG>(); }
-
-struct PipeHdr {
-    int view, tile, kind, n, flags, pad[3];
-};
-
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(unsigned bar)
-{
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_tx(unsigned bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(ok)
-                 : "r"(bar), "r"(parity)
-                 : "memory");
-    return ok != 0u;
-}
-// Bounded wait for the phase of the given parity: false when the CTA's abort
-// flag is set, after limit_ns of %globaltimer time (about a second by
-// default) or after 2^28 polls, whichever comes first.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, const volatile int *abort,
-                                          unsigned long long limit_ns = 1000000000ull)
-{
-    unsigned long long t0 = 0ull;
-    for (unsigned it = 0; it < (1u << 28); ++it) {
-        if (mbar_try(bar, parity)) return true;
-        if (*abort) return false;
-        if ((it & 63u) == 63u) {
-            const unsigned long long t = global_timer_ns();
-            if (t0 == 0ull) t0 = t;
-            else if (t - t0 > limit_ns) return false;
-        }
-    }
-    return false;
-}
-
-// Self-test of the bounded wait (the one the pipelined raster uses), with no
-// fault involved: warp 0 waits on an mbarrier that completes (one arrival by
-// warp 1 first), then on one that nothing arrives at, which must give up after
-// limit_ns.  out: [completed wait ok, idle wait gave up, its duration in ns (2 words)].
-__global__ void __launch_bounds__(64) k_wait_selftest(unsigned long long limit_ns, unsigned *out)
-{
-    __shared__ __align__(8) unsigned long long bars[2];
-    __shared__ int abort_flag;
-    if (threadIdx.x == 0) {
-        mbar_init(smem_u32(&bars[0]), 1u);
-        mbar_init(smem_u32(&bars[1]), 1u);
-        abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    if (threadIdx.x == 32) mbar_arrive(smem_u32(&bars[0]));
-    if (threadIdx.x == 0) {
-        const bool ok = mbar_wait(smem_u32(&bars[0]), 0u, &abort_flag, limit_ns);
-        const unsigned long long t0 = global_timer_ns();
-        const bool idle = mbar_wait(smem_u32(&bars[1]), 0u, &abort_flag, limit_ns);
-        const unsigned long long dt = global_timer_ns() - t0;
-        out[0] = ok ? 1u : 0u;
-        out[1] = idle ? 0u : 1u;
-        out[2] = (unsigned)(dt & 0xffffffffull);
-        out[3] = (unsigned)(dt >> 32);
-    }
-}
-
-// Global -> shared bulk copy completing on an mbarrier (both addresses 16-byte
-// aligned, size a multiple of 16).
-__device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned bytes, unsigned bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-
-template <int kS, int kG>
-__global__ void __launch_bounds__(kPipeThreads, kS == 1 ? 4 : 3)
-    k_braster_pipe(const BatchView *__restrict__ V, int n, OptParams O, unsigned *counter, int total)
-{
-    extern __shared__ __align__(128) unsigned char ring[];
-    __shared__ __align__(8) unsigned long long full[kPipeStages], empty[kPipeStages];
-    __shared__ PipeHdr hdr[kPipeStages];
-    __shared__ int abort_flag;
-    constexpr int kSlot = pipe_slot<kG>();
-    const unsigned warp = threadIdx.x >> 5, lane = lane_id();
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < kPipeStages; ++s) {
-            mbar_init(smem_u32(&full[s]), 1u);
-            mbar_init(smem_u32(&empty[s]), (unsigned)kPipeConsumers);
-        }
-        abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    const volatile int *abort_p = &abort_flag;
-    auto give_up = [&](unsigned code) {
-        abort_flag = 1;
-        atomicOr(counter + 4, code);
-    };
-
-    if (warp == kPipeConsumers) {
-        // ---------------- producer ----------------
-        int stage = 0;
-        unsigned lap = 0;
-        bool ok = true;
-        // claim the next stage (bounded wait for its consumers), arm it
-        auto claim = [&](const PipeHdr &h, unsigned bytes) -> bool {
-            bool w = true;
-            if (lane == 0) w = mbar_wait(smem_u32(&empty[stage]), (lap & 1u) ^ 1u, abort_p);
-            w = __shfl_sync(0xffffffffu, w, 0);
-            if (!w) return false;
-            if (lane == 0) {
-                hdr[stage] = h;
-                mbar_arrive_tx(smem_u32(&full[stage]), bytes);
-            }
-            __syncwarp();
-            return true;
-        };
-        auto advance = [&]() {
-            if (++stage == kPipeStages) { stage = 0; ++lap; }
-        };
-        const bool do_s = O.mode != GES_MODE_GAUSSIANS_ONLY, do_g = O.mode != GES_MODE_SURFELS_ONLY;
-        while (ok) {
-            int item = 0, v = 0;
-            if (lane == 0) {
-                item = (int)atomicAdd(counter, 1u);
-                if (item < total) v = find_view(n, item, [&](int k) { return V[k].tile_base; });
-            }
-            item = __shfl_sync(0xffffffffu, item, 0);
-            v = __shfl_sync(0xffffffffu, v, 0);
-            if (item >= total) break;
-            const BatchView &bv = V[v];
-            if (*(volatile unsigned *)(bv.X.status + ST_FLAGS) & (FLAG_SOVF | FLAG_GOVF)) continue;
-            const int tile = item - bv.tile_base;
-            for (int kind = PK_SURFEL; kind <= PK_GAUSS && ok; ++kind) {
-                const bool on = kind == PK_SURFEL ? do_s : do_g;
-                const int *off = kind == PK_SURFEL ? bv.X.s_off : bv.X.g_off;
-                const int *list = kind == PK_SURFEL ? bv.X.s_list : bv.X.g_list;
-                const float4 *rec = kind == PK_SURFEL ? bv.X.s_rec : bv.X.g_rec;
-                const int a = on ? off[tile] : 0, b = on ? off[tile + 1] : 0;
-                const int nch = max(1, (b - a + kPipeC - 1) / kPipeC);
-                const unsigned per = (kind == PK_GAUSS && kG == 2) ? 96u : 64u;
-                for (int c = 0; c < nch; ++c) {
-                    const int cnt = max(0, min(kPipeC, b - a - c * kPipeC));
-                    const PipeHdr h{v, tile, kind, cnt, (c == 0 ? PF_FIRST : 0) | (c == nch - 1 ? PF_LAST : 0),
-                                    {0, 0, 0}};
-                    if (!claim(h, per * (unsigned)cnt)) { ok = false; break; }
-                    const unsigned dst0 = smem_u32(ring) + (unsigned)(stage * kPipeC * kSlot);
-                    const unsigned bar = smem_u32(&full[stage]);
-                    for (int j = (int)lane; j < cnt; j += 32) {
-                        const int id = list[a + c * kPipeC + j];
-                        bulk_g2s(dst0 + (unsigned)(j * kSlot), rec + 4 * (int64_t)id, 64u, bar);
-                        if (kind == PK_GAUSS && kG == 2)
-                            bulk_g2s(dst0 + (unsigned)(j * kSlot + 64), bv.X.g_aux + 2 * (int64_t)id, 32u, bar);
-                    }
-                    advance();
-                }
-            }
-        }
-        if (ok) {
-            ok = claim(PipeHdr{0, 0, PK_END, 0, 0, {0, 0, 0}}, 0u);
-            if (ok) advance();
-        }
-        if (!ok) {
-            if (lane == 0) give_up(2u);
-            // wait (bounded) for the copies this warp has issued: every
-            // stage's latest armed phase completes once its copies land
-            if (lane == 0) {
-                const volatile int never = 0;
-                for (int k = 0; k < kPipeStages; ++k) {
-                    // stage s was last armed in lap (s < stage ? lap : lap - 1)
-                    if (k >= stage && lap == 0u) continue;
-                    const unsigned l = k < stage ? lap : lap - 1u;
-                    mbar_wait(smem_u32(&full[k]), l & 1u, &never);
-                }
-            }
-        }
-        return;
-    }
-
-    // ---------------- consumers ----------------
-    int stage = 0;
-    unsigned lap = 0;
-    SurfelZ<kS> z;
-    z.init(false);
-    GaussAcc acc;
-    float bmax = 0.f, Ds = INFINITY, Cs[3] = {0.f, 0.f, 0.f}, wmaxD = 0.f;
-    const float amin32 = O.alpha_min * 4294967296.f;
-    for (;;) {
-        const bool got = mbar_wait(smem_u32(&full[stage]), lap & 1u, abort_p);
-        if (!__all_sync(0xffffffffu, got)) {
-            if (lane == 0) give_up(1u);
-            break;
-        }
-        const PipeHdr h = hdr[stage];
-        if (h.kind == PK_END) break;
-        const BatchView &bv = V[h.view];
-        const WarpBlock<kS> B(bv.C, h.tile, warp, lane);
-        const SlotRecs<kSlot> R{ring + stage * kPipeC * kSlot};
-        if (h.kind == PK_SURFEL) {
-            if (h.flags & PF_FIRST) z.init(B.in_img);
-            if (B.wactive) surfel_pass<kS>(R, h.n, B, bv.C.izn, lane, z);
-            if (h.flags & PF_LAST) {
-                surfel_resolve<kS>(z, B.in_img, bv.X.s_rgb, bv.C.bg, bmax, Ds, Cs);
-                wmaxD = __uint_as_float(__reduce_max_sync(0xffffffffu, B.in_img ? __float_as_uint(Ds) : 0u));
-                acc = GaussAcc();
-            }
-        } else {
-            if (B.wactive) gauss_pass<kS, kG, false>(R, h.n, B, Ds, wmaxD, amin32, bv.C.izn, lane, acc);
-            if (h.flags & PF_LAST) {
-                if (B.in_img)
-                    composite_store<kS, false>(bv.C, O, bv.X, B, z, bmax, Ds, Cs, acc, bv.rgb, bv.depth, nullptr,
-                                               nullptr, GeoMaps{});
-                // per-view completion time: the warp that finishes the view's last block stamps it
-                if (lane == 0 &&
-                    atomicAdd(bv.X.status + ST_RETIRED, 1u) + 1u == (unsigned)(kPipeConsumers * bv.T))
-                    *reinterpret_cast<unsigned long long *>(bv.X.status + ST_TDONE) = global_timer_ns();
-            }
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&empty[stage]));
-        if (++stage == kPipeStages) { stage = 0; ++lap; }
-    }
-}
-
 }  // namespace
 
 cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const OptParams &O, unsigned *work_counter,
@@ -1192,28 +911,11 @@ cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const Opt
     mark(3);
     // P.gdim: the Gaussian kind shared by all scenes of the batch
     const unsigned grid = P.raster_ctas;
-    if (P.pipe) {
-        const size_t rb2 = pipe_ring_bytes<2>(), rb3 = pipe_ring_bytes<3>();
-        if (O.samples == 4 && P.gdim == 2)
-            k_braster_pipe<4, 2><<<grid, kPipeThreads, rb2, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
-        else if (O.samples == 4)
-            k_braster_pipe<4, 3><<<grid, kPipeThreads, rb3, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
-        else if (P.gdim == 2)
-            k_braster_pipe<1, 2><<<grid, kPipeThreads, rb2, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
-        else
-            k_braster_pipe<1, 3><<<grid, kPipeThreads, rb3, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
-    }
-    else if (O.samples == 4 && P.gdim == 2) k_braster<4, 2><<<grid, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
+    if (O.samples == 4 && P.gdim == 2) k_braster<4, 2><<<grid, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
     else if (O.samples == 4) k_braster<4, 3><<<grid, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
     else if (P.gdim == 2) k_braster<1, 2><<<grid, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
     else k_braster<1, 3><<<grid, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
     mark(4);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_wait_selftest(unsigned long long limit_ns, unsigned *d_out, cudaStream_t st)
-{
-    k_wait_selftest<<<1, 64, 0, st>>>(limit_ns, d_out);
     return cudaGetLastError();
 }
 
@@ -1233,15 +935,6 @@ cudaError_t prepare_forward_kernels()
         return e;
     if ((e = cudaFuncSetAttribute(k_fill_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)local_bins_smem(kLocalMaxTiles, true))) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(k_braster_pipe<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  pipe_ring_bytes<3>())) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(k_braster_pipe<4, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  pipe_ring_bytes<3>())) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(k_braster_pipe<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  pipe_ring_bytes<2>())) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(k_braster_pipe<4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  pipe_ring_bytes<2>())) != cudaSuccess)
         return e;
     return cudaFuncSetAttribute(k_bfill, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)local_bins_smem(kLocalMaxTiles, true));

@@ -117,7 +117,6 @@ struct BatchPlan {
     int total_sprep, total_gprep;            // preprocess CTAs of the surfel and the Gaussian launch
     int raster_ctas;                         // persistent raster grid
     int gdim;                                // Gaussian kind of every scene (2 or 3; 0 reads as 3)
-    int pipe;                                // raster: 0 CTA-staged, 1 pipelined (producer warp + ring)
 };
 cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const OptParams &O, unsigned *work_counter,
                          cudaStream_t st, cudaEvent_t *ev /* 5 events or nullptr */);
@@ -127,8 +126,6 @@ constexpr int kFillThreads = 1024;
 LocalBins plan_local_bins(int64_t N, int64_t M, int num_sms);
 size_t local_bins_smem(int T, bool fill);
 cudaError_t prepare_forward_kernels();   // once per device: large dynamic shared memory
-// Self-test of the pipelined raster's bounded mbarrier wait (4 device words out).
-cudaError_t launch_wait_selftest(unsigned long long limit_ns, unsigned *d_out, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // host launchers (ges_forward.cu / ges_backward.cu)

@@ -67,7 +67,7 @@ class ges_stats(C.Structure):
 class ges_batch_info(C.Structure):
     _fields_ = [("n_views", C.c_int32), ("prims_per_cta", C.c_int32), ("raster_ctas_per_sm", C.c_int32),
                 ("candidates", C.c_int32), ("tuned_ms", C.c_double), ("h2d_bytes", C.c_int64),
-                ("d2h_bytes", C.c_int64), ("raster_pipelined", C.c_int32), ("reserved", C.c_int32)]
+                ("d2h_bytes", C.c_int64), ("tile_w", C.c_int32), ("tile_h", C.c_int32)]
 
 
 class ges_profile(C.Structure):
@@ -115,7 +115,6 @@ _SIGS = {
     "ges_get_profile": (C.c_int, [C.c_void_p, _P(ges_profile)]),
     "ges_last_error_message": (C.c_char_p, []),
     "ges_version": (C.c_int32, []),
-    "ges_selftest_wait_timeout": (C.c_int, [C.c_int32, _P(C.c_int64)]),
 }
 
 _lib = None
@@ -253,13 +252,6 @@ def ges_last_error_message() -> str:
 
 def ges_version() -> int:
     return int(load().ges_version())
-
-
-def ges_selftest_wait_timeout(limit_ms: int):
-    """(completed wait ok, idle wait gave up, its duration in microseconds)."""
-    out = (C.c_int64 * 3)()
-    _check(load().ges_selftest_wait_timeout(int(limit_ms), out))
-    return bool(out[0]), bool(out[1]), int(out[2])
 
 
 def ges_count_fragments(scene, cam: ges_camera, opts):

@@ -10,6 +10,9 @@ the ray and the winning disc's normal); colour to ``col_tol`` max abs per
 channel where the ids match and no Gaussian sits on the 1/255 clamp or the
 depth-test threshold.
 """
+import json
+import os
+
 import numpy as np
 
 import oracle
@@ -26,7 +29,26 @@ DEPTH_REL = 2e-6
 DEPTH_GRAZE = 4e-7
 
 
-def compare(scene, cam, gpu, ref, opts=None, col_tol=COL_TOL, depth_rel=DEPTH_REL, check_ids=True):
+# Bound on the fraction of pixels the oracle flags as ambiguous (excluded from
+# the comparison): a parity test that masks more than this compares too
+# little to count.  The workloads' own fractions are well below it (0.1-0.7 %
+# at 1080p); the small hand-built scenes that aim at ties and grazing discs
+# pass their own bound.
+MASKED_MAX = 0.02
+
+
+def log_result(name, res):
+    """Append one comparison's summary to the file named by GES_PARITY_LOG
+    (unset: nothing is written)."""
+    path = os.environ.get("GES_PARITY_LOG")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps(dict(test=os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0], what=name,
+                                    **{k: v for k, v in res.items() if not isinstance(v, dict)})) + "\n")
+
+
+def compare(scene, cam, gpu, ref, opts=None, col_tol=COL_TOL, depth_rel=DEPTH_REL, check_ids=True,
+            max_masked=MASKED_MAX):
     rgb = gpu["rgb"].detach().cpu().numpy().astype(np.float64)
     depth = gpu["depth"].detach().cpu().numpy().astype(np.float64)
     out = {}
@@ -75,7 +97,9 @@ def compare(scene, cam, gpu, ref, opts=None, col_tol=COL_TOL, depth_rel=DEPTH_RE
     out["masked_frac"] = float((amb_id | amb_col).mean())
     out["compared_px"] = int(ok.sum())
     out["pass"] = (out.get("id_mismatch_unmasked", 0) == 0 and out.get("id_invalid", 0) == 0 and
-                   out["depth_excess"] <= 1.0 and out["depth_inf_ok"] and out["col_max"] <= col_tol)
+                   out["depth_excess"] <= 1.0 and out["depth_inf_ok"] and out["col_max"] <= col_tol and
+                   out["masked_frac"] <= max_masked)
+    log_result("render", out)
     return out
 
 
@@ -103,7 +127,10 @@ def compare_geom(gpu, ref_geo, ref, col_tol=COL_TOL):
                                     ref_geo["dsmooth"][fin]).max()) if fin.any() else 0.0
     out["nsmooth_max"] = float(np.abs(g["nsmooth"] - ref_geo["nsmooth"])[:, ok].max()) if ok.any() else 0.0
     out["compared_px"] = int(ok.sum())
+    out["masked_frac"] = float(amb.mean())
     out["pass"] = (out["ns_max"] <= GEO_NORMAL_TOL and out["ng_max"] <= GEO_NORMAL_TOL and
                    out["nsmooth_max"] <= GEO_NORMAL_TOL and out["dg_max_rel"] <= GEO_DEPTH_REL and
-                   out["dsmooth_max_rel"] <= GEO_DEPTH_REL and out["dsmooth_inf_ok"])
+                   out["dsmooth_max_rel"] <= GEO_DEPTH_REL and out["dsmooth_inf_ok"] and
+                   out["masked_frac"] <= MASKED_MAX)
+    log_result("geometry", out)
     return out

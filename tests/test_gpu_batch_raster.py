@@ -1,9 +1,7 @@
-"""The batch graph's two raster kinds: CTA-staged, and pipelined (a producer
-warp gathers each tile's records with bulk asynchronous copies into a ring of
-shared-memory stages guarded by mbarriers; eight pixel warps consume them
-without CTA-wide barriers).  Both must give bitwise the per-view render's
-images, for every render mode, sample count and Gaussian kind, with empty,
-ragged and multi-stage tile lists."""
+"""The batch graph (every phase one launch over all views, persistent raster
+over (view, tile) items): bitwise the per-view render's images, for every
+render mode, sample count and Gaussian kind, with empty, ragged and long tile
+lists; and the timed 1080p orbit path itself against the oracle."""
 import numpy as np
 import pytest
 
@@ -12,8 +10,6 @@ from test_gpu_2dges import _small2d
 from test_gpu_forward import _small
 
 pytestmark = pytest.mark.gpu
-
-KINDS = ["classic", "pipelined"]
 
 
 @pytest.fixture(scope="module")
@@ -33,39 +29,34 @@ def _views():
             sg.look_at((0.1, 0.05, -0.6), (0, 0.1, 1), (0, 1, 0), 97, 61, 95.0)]
 
 
-def _check(R, scenes, views, sov, opts, kind, reps=2):
+def _check(R, scenes, views, sov, opts, reps=2):
     b = R.GESBatch(scenes, views, sov, opts=opts)
-    assert b.info().raster_pipelined == (1 if kind == "pipelined" else 0)
+    assert (b.info().tile_w, b.info().tile_h) == (16, 16)
     for rep in range(reps):
         b.launch()
         b.sync()
         for v in range(len(views)):
             single = R.render(scenes[sov[v]], views[v], opts, with_aux=False)
-            assert (b.rgb[v] == single["rgb"]).all(), (kind, rep, v)
-            assert (b.depth[v] == single["depth"]).all(), (kind, rep, v)
+            assert (b.rgb[v] == single["rgb"]).all(), (rep, v)
+            assert (b.depth[v] == single["depth"]).all(), (rep, v)
     b.close()
 
 
-@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("opts", [None, dict(mode=1), dict(mode=2), dict(samples=4)])
-def test_batch_raster_equals_single_views(R, monkeypatch, kind, opts):
-    monkeypatch.setenv("GES_BATCH_RASTER", kind)
+def test_batch_raster_equals_single_views(R, opts):
     scene, cams = sg.config_scene(0)
     other = _small(91, 2000, 6000)
     empty = other.subset(s_idx=np.zeros(0, int), g_idx=np.zeros(0, int))
     gs = [R.GESScene.from_arrays(x) for x in (scene, other, empty)]
     views = [cams[0]] + _views() + [cams[0]]
     sov = [0, 1, 0, 1, 0, 1, 2]
-    _check(R, gs, views, sov, opts, kind)
+    _check(R, gs, views, sov, opts)
     for g in gs:
         g.close()
 
 
-@pytest.mark.parametrize("kind", KINDS)
-def test_batch_raster_long_tile_lists(R, monkeypatch, kind):
-    """Thousands of entries per tile: many stages (128 records each) and
-    chunks (256) per tile, so the ring wraps inside one tile."""
-    monkeypatch.setenv("GES_BATCH_RASTER", kind)
+def test_batch_raster_long_tile_lists(R):
+    """Thousands of entries per tile: many staged chunks (256 records) per tile."""
     dense = _small(92, 30000, 30000)
     gs = R.GESScene.from_arrays(dense)
     views = [sg.look_at((0, 0, -2.5), (0, 0, 0), (0, 1, 0), 48, 40, 60.0),
@@ -76,77 +67,57 @@ def test_batch_raster_long_tile_lists(R, monkeypatch, kind):
         gs_stats.append(gs.stats())
     # the lists really are long: over 1000 entries per tile on average
     assert min(s.surfel_tile_pairs / (s.tiles_x * s.tiles_y) for s in gs_stats) > 1000
-    _check(R, [gs], views, [0, 0], None, kind)
+    _check(R, [gs], views, [0, 0], None)
     gs.close()
 
 
-@pytest.mark.parametrize("kind", KINDS)
-def test_batch_raster_2d_gaussians(R, monkeypatch, kind):
-    monkeypatch.setenv("GES_BATCH_RASTER", kind)
+def test_batch_raster_2d_gaussians(R):
     ga, gb = R.GESScene.from_arrays(_small2d(93, 2000, 6000)), R.GESScene.from_arrays(_small2d(94, 500, 3000))
     views = _views()[:3]
     for opts in (None, dict(samples=4)):
-        _check(R, [ga, gb], views, [0, 1, 0], opts, kind, reps=1)
+        _check(R, [ga, gb], views, [0, 1, 0], opts, reps=1)
     ga.close()
     gb.close()
 
 
-def test_batch_raster_kinds_agree_on_the_1080p_orbit(R, monkeypatch):
-    """Four views of the 1M-surfel / 300k-Gaussian 1080p orbit through both
-    kinds: identical images, and identical to the per-view render."""
+def test_timed_orbit_path_matches_oracle(R):
+    """The benchmark's own path: a batch graph over views of the 1M-surfel /
+    300k-Gaussian 1080p orbit.  One view against the oracle directly (colour
+    and depth; the batch keeps no id map), every view bitwise equal to its
+    per-view render, and the per-view completion stamps sane."""
+    import oracle
+    from parity import compare
     scene, cams = sg.config_scene(1)
     gs = R.GESScene.from_arrays(scene)
     views = [cams[k] for k in (0, 16, 33, 50)]
-    imgs = {}
-    for kind in KINDS:
-        monkeypatch.setenv("GES_BATCH_RASTER", kind)
-        b = R.GESBatch([gs], views)
-        assert b.info().raster_pipelined == (1 if kind == "pipelined" else 0)
-        b.launch()
-        b.sync()
-        imgs[kind] = [(b.rgb[v].clone(), b.depth[v].clone()) for v in range(len(views))]
-        t = b.view_times()
-        assert all(0.0 < x < 1000.0 for x in t), t
-        b.close()
-    single = R.render(gs, views[2], with_aux=False)
+    b = R.GESBatch([gs], views)
+    b.launch()
+    b.sync()
+    t = b.view_times()
+    assert all(0.0 < x < 1000.0 for x in t), t
     for v in range(len(views)):
-        assert (imgs["classic"][v][0] == imgs["pipelined"][v][0]).all(), v
-        assert (imgs["classic"][v][1] == imgs["pipelined"][v][1]).all(), v
-    assert (imgs["pipelined"][2][0] == single["rgb"]).all() and (imgs["pipelined"][2][1] == single["depth"]).all()
+        single = R.render(gs, views[v], with_aux=False)
+        assert (b.rgb[v] == single["rgb"]).all() and (b.depth[v] == single["depth"]).all(), v
+    ref = oracle.render(scene, views[2])
+    res = compare(scene, views[2], dict(rgb=b.rgb[2], depth=b.depth[2]), ref, check_ids=False)
+    assert res["pass"], res
+    assert res["masked_frac"] < 0.01
+    b.close()
     gs.close()
 
 
-def test_batch_raster_auto_times_both_kinds(R, monkeypatch):
-    monkeypatch.setenv("GES_BATCH_RASTER", "auto")
+def test_batch_autotuner_candidates(R):
     scene, cams = sg.config_scene(0)
     gs = R.GESScene.from_arrays(scene)
     b = R.GESBatch([gs], [cams[0]])
-    # 5 preprocess ranges x (2 classic + 2 pipelined) raster shapes
-    assert b.info().candidates == 20
+    # 5 preprocess ranges x 2 raster occupancies
+    assert b.info().candidates == 10
     b.launch()
     b.sync()
     single = R.render(gs, cams[0], with_aux=False)
     assert (b.rgb[0] == single["rgb"]).all() and (b.depth[0] == single["depth"]).all()
     b.close()
     gs.close()
-
-
-def test_bounded_mbarrier_wait_gives_up(R):
-    """The pipelined raster's shared-memory waits are bounded: on a barrier
-    that nothing completes, the wait returns after its limit (device time)
-    and the GPU stays usable.  No fault is involved."""
-    from paper_2504_17545_gb300 import native as N
-    ok, gave_up, us = N.ges_selftest_wait_timeout(50)
-    assert ok and gave_up, (ok, gave_up, us)
-    assert 50_000 <= us < 5_000_000, us
-    # the context still works
-    scene, cams = sg.config_scene(0)
-    gs = R.GESScene.from_arrays(scene)
-    out = R.render(gs, cams[0])
-    assert out["rgb"].isfinite().all()
-    gs.close()
-    with pytest.raises(N.GesError):
-        N.ges_selftest_wait_timeout(0)
 
 
 def test_batch_2160p_orbit_view_matches_oracle(R):

@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import scenegen as sg
-from parity import COL_TOL
+from parity import COL_TOL, log_result
 
 pytestmark = pytest.mark.gpu
 
@@ -48,8 +48,10 @@ def _fwd_compare(gpu, ref):
     res = dict(col_max=float(np.abs(rgb - ref["rgb"])[:, ok].max()),
                T_max=float(np.abs(gpu["T"].cpu().numpy() - ref["T"])[ok].max()),
                front_mismatch=int((gpu["front"].cpu().numpy() != ref["front"])[ok].sum()),
-               compared=int(ok.sum()))
-    res["pass"] = res["col_max"] <= COL_TOL and res["T_max"] <= COL_TOL and res["front_mismatch"] == 0
+               compared=int(ok.sum()), masked_frac=float(1.0 - ok.mean()))
+    res["pass"] = (res["col_max"] <= COL_TOL and res["T_max"] <= COL_TOL and res["front_mismatch"] == 0 and
+                   res["masked_frac"] <= 0.1)
+    log_result("translucent", res)
     return res
 
 
