@@ -301,7 +301,18 @@ GES_API ges_status ges_render_backward(ges_scene *scene, const ges_camera *cam, 
  * (host arrays) and writes out_rgb[v] [3,H_v,W_v] and out_depth[v] [H_v,W_v]
  * (host arrays of device pointers; out_depth entries may be NULL).  All
  * scenes must live on the same device; the batch runs on the stream of
- * scenes[0].  Per-view semantics are exactly those of ges_render_ex. */
+ * scenes[scene_of_view[0]] and the call returns when it is done.  Per-view
+ * semantics are exactly those of ges_render_ex.
+ *
+ * The views render as one batch graph (see ges_batch_create) kept on the
+ * first view's scene: the first call with a given set of image sizes,
+ * scenes (primitive counts, kinds, storage types) and options builds it,
+ * which renders every view once on the per-view path; later calls with the
+ * same set rewrite its view table (cameras, outputs, attribute pointers) and
+ * replay it.  Its memory is held until that scene is destroyed or a call
+ * with another set replaces it.  Views above 32768 tiles of 16x16, or scenes
+ * of both Gaussian kinds in one call, take one launch sequence per view
+ * instead. */
 GES_API ges_status ges_render_batch(ges_scene *const *scenes, const ges_camera *cams, const int32_t *scene_of_view,
                             int32_t n_views, const ges_render_opts *opts,
                             float *const *out_rgb, float *const *out_depth);
@@ -354,7 +365,7 @@ GES_API ges_status ges_count_fragments(ges_scene *scene, const ges_camera *cam, 
  * Pointers
  * (scenes' arrays, outputs) are baked into the graph and must stay valid
  * until ges_batch_destroy.  Images must have at most 32768 tiles of 16x16
- * (otherwise GES_ERR_UNSUPPORTED; ges_render_batch has no such limit).
+ * (otherwise GES_ERR_UNSUPPORTED; ges_render_batch renders such views one by one).
  * out_depth may be NULL (no depth output) or have NULL entries. */
 typedef struct ges_batch ges_batch;
 typedef struct {

@@ -68,6 +68,8 @@ struct DevBuf {
 const char *kFwdNames[4] = {"preprocess", "scan", "fill", "raster"};
 const char *kBwdNames[2] = {"gauss_bwd", "surfel_bwd"};
 
+void batch_release(ges_batch *b);
+
 }  // namespace
 
 struct ges_scene {
@@ -84,6 +86,10 @@ struct ges_scene {
     DevBuf g_aux;                  // Gaussian side data (2D Gaussians, geometry maps)
     DevBuf t_side, t_keys;         // translucent render: surfel frames, sort keys
     DevBuf t_acc;                  // backward passes: 64-bit fixed-point gradient sums + one word
+    // ges_render_batch's batch graph (views of this and other scenes, with
+    // this scene the first view's), kept while the calls keep the same key
+    ges_batch *bcache = nullptr;
+    std::vector<int64_t> bkey;
     unsigned *status_host = nullptr;
     int status_slots = 0;
     int64_t tiles_cap = 0;
@@ -365,6 +371,10 @@ ges_status render_views(ges_scene *const *scenes, const CamParams *cams, const i
     return fail(GES_ERR_INTERNAL, "tile lists kept overflowing after growing them");
 }
 
+ges_status render_batch_engine(ges_scene *const *scenes, const std::vector<CamParams> &C, const ges_camera *cams,
+                               const int32_t *sov, int n, const OptParams &O, const ges_render_opts *opts,
+                               float *const *out_rgb, float *const *out_depth);
+
 }  // namespace
 
 extern "C" {
@@ -420,6 +430,7 @@ ges_status ges_destroy_scene(ges_scene *s)
                       &s->g_off, &s->s_cur, &s->g_cur, &s->s_list, &s->g_list, &s->hist, &s->base,
                       &s->vcount, &s->status, &s->filt, &s->g_aux, &s->t_side, &s->t_keys, &s->t_acc};
     for (DevBuf *b : bufs) b->release();
+    if (s->bcache) batch_release(s->bcache);
     if (s->status_host) cudaFreeHost(s->status_host);
     for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
     delete s;
@@ -531,6 +542,15 @@ ges_status ges_render_batch(ges_scene *const *scenes, const ges_camera *cams, co
     }
     for (int k = 0; k <= max_scene; ++k)
         if (!scenes[k]) return fail(GES_ERR_INVALID_ARG, "scenes[%d] is NULL", k);
+    // the batch graph, unless a view is beyond its local binning or the
+    // scenes mix Gaussian kinds: then one launch sequence per view
+    bool engine = true;
+    for (int v = 0; v < n_views; ++v) {
+        if ((int64_t)C[v].tiles_x * C[v].tiles_y > kLocalMaxTiles) engine = false;
+        if (scenes[scene_of_view[v]]->view.gdim != scenes[scene_of_view[0]]->view.gdim) engine = false;
+    }
+    if (engine)
+        return render_batch_engine(scenes, C, cams, scene_of_view, n_views, O, opts, out_rgb, out_depth);
     return render_views(scenes, C.data(), scene_of_view, n_views, O, out_rgb, out_depth, nullptr, nullptr);
 }
 
@@ -826,9 +846,12 @@ size_t batch_layout(ges_batch *b, const std::vector<SceneView> &S, const std::ve
 
 extern "C" {
 
-ges_status ges_batch_create(ges_scene *const *scenes, const ges_camera *cams, const int32_t *scene_of_view,
-                            int32_t n_views, const ges_render_opts *opts, float *const *out_rgb,
-                            float *const *out_depth, ges_batch **out)
+// tune: time the candidate configurations and keep the fastest; otherwise
+// take the one most workloads pick (8192 primitives per preprocess CTA, the
+// most resident raster CTAs)
+static ges_status batch_create(ges_scene *const *scenes, const ges_camera *cams, const int32_t *scene_of_view,
+                               int32_t n_views, const ges_render_opts *opts, float *const *out_rgb,
+                               float *const *out_depth, ges_batch **out, bool tune)
 {
     if (!out) return fail(GES_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -893,7 +916,9 @@ ges_status ges_batch_create(ges_scene *const *scenes, const ges_camera *cams, co
         b->views[v].depth = out_depth ? out_depth[v] : nullptr;
     }
     // arena sized for the smallest primitives-per-CTA tried (most histogram rows)
-    const int64_t kR[] = {4096, 8192, 16384, 32768, 60000};
+    const int64_t kRall[] = {4096, 8192, 16384, 32768, 60000}, kRone[] = {8192};
+    const int64_t *kR = tune ? kRall : kRone;
+    const int nR = tune ? 5 : 1;
     const size_t bytes = batch_layout(b, S, C, kR[0], nullptr);
     BATCH_CUDA(cudaMalloc(&b->arena, bytes));
     int sms = 152;
@@ -905,9 +930,11 @@ ges_status ges_batch_create(ges_scene *const *scenes, const ges_camera *cams, co
     // raster candidates: resident CTAs per SM (the 4-sample kernels are built
     // for one CTA fewer)
     const int d = O.samples == 4 ? 1 : 0;
-    const int kPerSm[] = {4 - d, 5 - d};
-    for (int64_t R : kR) {
-        for (const int per_sm : kPerSm) {
+    const int kPerSm[] = {5 - d, 4 - d};
+    for (int ri = 0; ri < nR; ++ri) {
+        const int64_t R = kR[ri];
+        for (int pi = 0; pi < (tune ? 2 : 1); ++pi) {
+            const int per_sm = kPerSm[pi];
             batch_layout(b, S, C, R, (unsigned char *)b->arena);
             BatchPlan P{n_views, 0, 0, 0, 0, 0, 0, sms * per_sm, S[0].gdim};
             for (int v = 0; v < n_views; ++v) {
@@ -985,6 +1012,13 @@ ges_status ges_batch_create(ges_scene *const *scenes, const ges_camera *cams, co
         *out = nullptr;
     }
     return r;
+}
+
+ges_status ges_batch_create(ges_scene *const *scenes, const ges_camera *cams, const int32_t *scene_of_view,
+                            int32_t n_views, const ges_render_opts *opts, float *const *out_rgb,
+                            float *const *out_depth, ges_batch **out)
+{
+    return batch_create(scenes, cams, scene_of_view, n_views, opts, out_rgb, out_depth, out, true);
 }
 
 ges_status ges_batch_set_camera(ges_batch *b, int32_t view, const ges_camera *cam)
@@ -1076,6 +1110,77 @@ ges_status ges_batch_destroy(ges_batch *b)
 }
 
 }  // extern "C"
+
+namespace {
+
+// ges_render_batch through a batch graph kept on the first view's scene.  The
+// key is what the graph bakes in: the views' image sizes, the scenes'
+// primitive counts, kinds and storage types, and the options.  With the same
+// key the call only rewrites the view table (cameras, outputs, attribute
+// pointers) and replays the graph; otherwise (or when the tile lists of the
+// kept graph overflow for new cameras) it builds a new one, without tuning.
+ges_status render_batch_engine(ges_scene *const *scenes, const std::vector<CamParams> &C, const ges_camera *cams,
+                               const int32_t *sov, int n, const OptParams &O, const ges_render_opts *opts,
+                               float *const *out_rgb, float *const *out_depth)
+{
+    ges_scene *own = scenes[sov[0]];
+    std::vector<int64_t> key{n};
+    {
+        int32_t w[sizeof(OptParams) / 4];
+        std::memcpy(w, &O, sizeof w);
+        key.insert(key.end(), w, w + sizeof(OptParams) / 4);
+    }
+    for (int v = 0; v < n; ++v) {
+        const SceneView &S = scenes[sov[v]]->view;
+        key.insert(key.end(), {(int64_t)sov[v], S.N, S.M, S.gdim, S.deg, S.attr_dtype, S.sh_dtype,
+                               (int64_t)(S.g_filt3 != nullptr), C[v].W, C[v].H,
+                               (int64_t)(out_depth && out_depth[v])});
+    }
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if (own->bcache && own->bkey == key) {
+            ges_batch *b = own->bcache;
+            for (int v = 0; v < n; ++v) {
+                SceneView S = scenes[sov[v]]->view;
+                if (O.mode == GES_MODE_GAUSSIANS_ONLY) S.N = 0;
+                if (O.mode == GES_MODE_SURFELS_ONLY) S.M = 0;
+                b->views[v].S = S;
+                b->views[v].C = C[v];
+                b->views[v].rgb = out_rgb[v];
+                b->views[v].depth = out_depth ? out_depth[v] : nullptr;
+            }
+            std::memcpy(b->h_table, b->views.data(), sizeof(BatchView) * n);
+            ges_status r = ges_batch_launch(b, own->stream);
+            if (r == GES_OK) r = ges_batch_sync(b);
+            if (r != GES_ERR_CAPACITY) {
+                if (r == GES_OK)
+                    for (int v = 0; v < n; ++v) {
+                        const unsigned *w = b->h_status + (size_t)v * ST_WORDS;
+                        ges_stats &st = scenes[sov[v]]->stats;
+                        st.visible_surfels = w[ST_SVIS];
+                        st.visible_gaussians = w[ST_GVIS];
+                        st.surfel_tile_pairs = w[ST_SPAIRS];
+                        st.gauss_tile_pairs = w[ST_GPAIRS];
+                        st.tiles_x = C[v].tiles_x;
+                        st.tiles_y = C[v].tiles_y;
+                    }
+                return r;
+            }
+        }
+        if (own->bcache) batch_release(own->bcache);
+        own->bcache = nullptr;
+        own->bkey.clear();
+        // a new graph; its creation renders every view once and checks it
+        ges_batch *b = nullptr;
+        ges_status r = batch_create(scenes, cams, sov, n, opts, out_rgb, out_depth, &b, false);
+        if (r != GES_OK) return r;
+        own->bcache = b;
+        own->bkey = key;
+        return GES_OK;
+    }
+    return fail(GES_ERR_INTERNAL, "batch render kept overflowing its tile lists");
+}
+
+}  // namespace
 
 // ---------------------------------------------------------------------------
 // ges_render_noalloc: the forward render with every intermediate buffer in one

@@ -36,12 +36,17 @@ def test_alu_peak_is_lanes_times_clock():
     p = os.path.join(bench.ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         mhz = float(json.load(open(p)).get("sm_max_mhz", mhz))
-    assert bench.alu_peak() == pytest.approx(152 * 128 * mhz * 1e6)
+    # without a GPU the SM count is GB300's; with one, the device's
+    sms, src = bench.sm_count()
+    assert (sms, src) == (152, "GB300 nominal") or src == "device"
+    assert bench.alu_peak() == pytest.approx(sms * 128 * mhz * 1e6)
+    assert bench.alu_peak(100) == pytest.approx(100 * 128 * mhz * 1e6)
+    assert f"{sms} SMs" in bench.alu_peak_source()
 
 
 def test_ncu_traffic_follows_the_sources(monkeypatch):
     rec = json.load(open(os.path.join(bench.ROOT, "profiles", "ncu_traffic.json")))
-    for k in ("k_bprep", "k_braster"):
+    for k in ("k_braster",) + tuple(n for n in bench.PREP_KERNELS if n in rec):
         assert rec[k]["views_in_capture"] >= 1 and rec[k]["dram_bytes_per_view"] > 0
     digest = bench.source_digest()
     assert len(digest) == 16
@@ -49,6 +54,8 @@ def test_ncu_traffic_follows_the_sources(monkeypatch):
         # scaled by the views of the launch
         t1, t64 = bench.ncu_traffic("k_braster", 1), bench.ncu_traffic("k_braster", 64)
         assert t64 == pytest.approx(64 * t1)
+    # a phase of several launches needs all of their records
+    assert bench.ncu_traffic(("k_braster", "no_such_kernel"), 64) is None
     # any change to the kernel sources drops the number
     monkeypatch.setattr(bench, "source_digest", lambda: "0" * 16)
     assert bench.ncu_traffic("k_braster", 64) is None

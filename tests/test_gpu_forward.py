@@ -50,9 +50,11 @@ def test_parity_ragged_and_modes(R, mode):
     scene = _small(31)
     cams = [sg.look_at((0.2, 0.3, -2.8), (0, 0, 0), (0, 1, 0), 203, 141, 55.0),
             sg.look_at((0.1, 0.05, -0.6), (0, 0.1, 1), (0, 1, 0), 97, 61, 95.0)]   # inside the scene
-    for cam in cams:
+    # the camera inside the scene sees near-plane and grazing discs: more of
+    # its pixels are ambiguous (about 3 %) than at the workloads' views
+    for cam, mm in zip(cams, (0.02, 0.06)):
         ref = oracle.render(scene, cam, dict(mode=mode))
-        _assert(compare(scene, cam, _render(R, scene, cam, dict(mode=mode)), ref, dict(mode=mode)))
+        _assert(compare(scene, cam, _render(R, scene, cam, dict(mode=mode)), ref, dict(mode=mode), max_masked=mm))
 
 
 @pytest.mark.parametrize("opts", [dict(eps_mode=1), dict(eps_mode=2, eps_value=0.1), dict(lowpass=0.1)])
@@ -184,6 +186,36 @@ def test_batch_equals_single_views(R):
         assert (rgb == single["rgb"]).all() and (depth == single["depth"]).all()
     ga.close()
     gb.close()
+
+
+def test_render_batch_reuses_its_graph_and_rebuilds_when_needed(R):
+    """ges_render_batch keeps a batch graph: a first call builds it, a call
+    with the same image sizes and scenes replays it with new cameras, a
+    camera whose tile lists no longer fit rebuilds it, and other image sizes
+    rebuild it too; every result bitwise equal to the per-view render."""
+    scene = _small(37, 20000, 20000)
+    gs = R.GESScene.from_arrays(scene)
+    away = [sg.look_at((0, 0, -3), (0, 0, -10), (0, 1, 0), 320, 240, 60.0),
+            sg.look_at((0.4, 0, -3), (0.4, 0, -10), (0, 1, 0), 160, 120, 60.0)]
+    toward = [sg.look_at((0, 0, -2.2), (0, 0, 0), (0, 1, 0), 320, 240, 60.0),
+              sg.look_at((0.4, 0.2, -2.0), (0, 0, 0), (0, 1, 0), 160, 120, 70.0)]
+
+    def check(views):
+        outs = R.render_batch([gs], views)
+        for v, (rgb, depth) in enumerate(outs):
+            single = R.render(gs, views[v], with_aux=False)
+            assert (rgb == single["rgb"]).all() and (depth == single["depth"]).all(), v
+
+    # the lists of a graph built for the away cameras (no tile entries: the
+    # 65536 of headroom) cannot hold the toward view's entries
+    R.render(gs, toward[0], with_aux=False)
+    assert gs.stats().surfel_tile_pairs > 65536
+    check(away)                   # built for cameras that see nothing
+    check(toward)                 # its lists overflow: rebuilt
+    check(toward)                 # replayed
+    check(away)                   # replayed with other cameras
+    check(toward[:1])             # other sizes: rebuilt
+    gs.close()
 
 
 def test_stats_count_visible_primitives(R):

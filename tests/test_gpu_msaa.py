@@ -47,9 +47,11 @@ def test_msaa_parity_ragged_and_modes(R, mode):
     opts = dict(mode=mode, samples=4)
     cams = [sg.look_at((0.2, 0.3, -2.8), (0, 0, 0), (0, 1, 0), 203, 141, 55.0),
             sg.look_at((0.1, 0.05, -0.6), (0, 0.1, 1), (0, 1, 0), 97, 61, 95.0)]   # inside the scene
-    for cam in cams:
+    # the camera inside the scene sees near-plane and grazing discs, and a
+    # pixel is ambiguous when any of its 4 samples is (about 5 %)
+    for cam, mm in zip(cams, (0.02, 0.08)):
         ref = oracle.render(scene, cam, opts)
-        _assert(compare(scene, cam, _render(R, scene, cam, opts), ref, opts))
+        _assert(compare(scene, cam, _render(R, scene, cam, opts), ref, opts, max_masked=mm))
 
 
 def test_msaa_parity_1080p_orbit_camera(R):
