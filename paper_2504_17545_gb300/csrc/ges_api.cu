@@ -148,6 +148,15 @@ bool finite_all(const float *v, int n)
     return true;
 }
 
+// Binning tiles of 2^tsx x 2^tsy pixels for the camera's image.
+void set_tiles(CamParams &C, int tsx, int tsy)
+{
+    C.tsx = tsx;
+    C.tsy = tsy;
+    C.tiles_x = (C.W + (1 << tsx) - 1) >> tsx;
+    C.tiles_y = (C.H + (1 << tsy) - 1) >> tsy;
+}
+
 ges_status make_cam(const ges_camera *c, CamParams &C)
 {
     if (!c) return fail(GES_ERR_INVALID_ARG, "camera is NULL");
@@ -173,8 +182,7 @@ ges_status make_cam(const ges_camera *c, CamParams &C)
     C.izn = 1.f / c->znear;
     for (int k = 0; k < 3; ++k) C.bg[k] = c->bg[k];
     C.W = c->width; C.H = c->height;
-    C.tiles_x = (c->width + kTile - 1) / kTile;
-    C.tiles_y = (c->height + kTile - 1) / kTile;
+    set_tiles(C, kTileShift, kTileShift);
     return GES_OK;
 }
 
@@ -767,6 +775,7 @@ struct ges_batch {
     cudaEvent_t phase[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // event nodes in the graph
     ges_batch_info info{};
     ges_profile profile{};
+    int tsx = kTileShift, tsy = kTileShift;   // binning tile of the chosen configuration
 };
 
 namespace {
@@ -900,9 +909,45 @@ static ges_status batch_create(ges_scene *const *scenes, const ges_camera *cams,
             batch_release(b);
             return r;
         }
-        b->s_cap[v] = (int64_t)(sc->stats.surfel_tile_pairs * 1.5) + 65536;
-        b->g_cap[v] = (int64_t)(sc->stats.gauss_tile_pairs * 1.5) + 65536;
+        // other tile shapes than the per-view path's 16x16 give other counts
+        // (a candidate whose lists overflow is dropped)
+        const double head = tune ? 2.0 : 1.5;
+        b->s_cap[v] = (int64_t)(sc->stats.surfel_tile_pairs * head) + 65536;
+        b->g_cap[v] = (int64_t)(sc->stats.gauss_tile_pairs * head) + 65536;
     }
+    // tile shapes tried (log2 width, log2 height): all when tuning, unless
+    // GES_BATCH_TILE names one ("16x16", "32x8" or "8x32"); 16x16 otherwise
+    std::vector<std::pair<int, int>> shapes{{kTileShift, kTileShift}};
+    if (tune) {
+        shapes = {{4, 4}, {5, 3}, {3, 5}};
+        if (const char *env = std::getenv("GES_BATCH_TILE")) {
+            if (!std::strcmp(env, "16x16")) shapes = {{4, 4}};
+            else if (!std::strcmp(env, "32x8")) shapes = {{5, 3}};
+            else if (!std::strcmp(env, "8x32")) shapes = {{3, 5}};
+        }
+    }
+    {
+        std::vector<std::pair<int, int>> ok;
+        for (const auto &sh : shapes) {
+            bool fits = true;
+            for (int v = 0; v < n_views; ++v) {
+                CamParams c = C[v];
+                set_tiles(c, sh.first, sh.second);
+                fits = fits && (int64_t)c.tiles_x * c.tiles_y <= kLocalMaxTiles;
+            }
+            if (fits) ok.push_back(sh);
+        }
+        if (ok.empty()) {
+            batch_release(b);
+            return fail(GES_ERR_UNSUPPORTED, "no tile shape keeps every view within %d tiles", kLocalMaxTiles);
+        }
+        shapes = ok;
+    }
+    auto shaped = [&](const std::pair<int, int> &sh) {
+        std::vector<CamParams> c = C;
+        for (CamParams &x : c) set_tiles(x, sh.first, sh.second);
+        return c;
+    };
     BATCH_CUDA(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
     BATCH_CUDA(cudaEventCreate(&b->done));
     for (cudaEvent_t &ev : b->phase) BATCH_CUDA(cudaEventCreate(&ev));
@@ -919,7 +964,8 @@ static ges_status batch_create(ges_scene *const *scenes, const ges_camera *cams,
     const int64_t kRall[] = {4096, 8192, 16384, 32768, 60000}, kRone[] = {8192};
     const int64_t *kR = tune ? kRall : kRone;
     const int nR = tune ? 5 : 1;
-    const size_t bytes = batch_layout(b, S, C, kR[0], nullptr);
+    size_t bytes = 0;
+    for (const auto &sh : shapes) bytes = std::max(bytes, batch_layout(b, S, shaped(sh), kR[0], nullptr));
     BATCH_CUDA(cudaMalloc(&b->arena, bytes));
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
@@ -931,11 +977,13 @@ static ges_status batch_create(ges_scene *const *scenes, const ges_camera *cams,
     // for one CTA fewer)
     const int d = O.samples == 4 ? 1 : 0;
     const int kPerSm[] = {5 - d, 4 - d};
+    for (const auto &sh : shapes)
     for (int ri = 0; ri < nR; ++ri) {
+        const std::vector<CamParams> Cs = shaped(sh);
         const int64_t R = kR[ri];
         for (int pi = 0; pi < (tune ? 2 : 1); ++pi) {
             const int per_sm = kPerSm[pi];
-            batch_layout(b, S, C, R, (unsigned char *)b->arena);
+            batch_layout(b, S, Cs, R, (unsigned char *)b->arena);
             BatchPlan P{n_views, 0, 0, 0, 0, 0, 0, sms * per_sm, S[0].gdim};
             for (int v = 0; v < n_views; ++v) {
                 P.total_tiles += b->views[v].T;
@@ -979,21 +1027,31 @@ static ges_status batch_create(ges_scene *const *scenes, const ges_camera *cams,
             }
             ++cand;
             ms /= 3.f;
-            if (ms < best_ms) {
+            // a candidate whose tile lists overflowed skipped its raster: not a timing
+            bool overflow = false;
+            for (int v = 0; v < n_views; ++v)
+                overflow = overflow || (b->h_status[(size_t)v * ST_WORDS + ST_FLAGS] & (FLAG_SOVF | FLAG_GOVF));
+            if (!overflow && ms < best_ms) {
                 best_ms = ms;
                 if (b->exec) cudaGraphExecDestroy(b->exec);
                 b->exec = ex;
                 b->info.prims_per_cta = (int32_t)R;
                 b->info.raster_ctas_per_sm = per_sm;
-                b->info.tile_w = kTile;
-                b->info.tile_h = kTile;
+                b->tsx = sh.first;
+                b->tsy = sh.second;
+                b->info.tile_w = 1 << sh.first;
+                b->info.tile_h = 1 << sh.second;
             } else {
                 cudaGraphExecDestroy(ex);
             }
         }
     }
+    if (!b->exec) {
+        batch_release(b);
+        return fail(GES_ERR_CAPACITY, "every configuration overflowed the batch's tile lists");
+    }
     // the table the chosen graph reads: rebuild it for that candidate
-    batch_layout(b, S, C, b->info.prims_per_cta, (unsigned char *)b->arena);
+    batch_layout(b, S, shaped({b->tsx, b->tsy}), b->info.prims_per_cta, (unsigned char *)b->arena);
     std::memcpy(b->h_table, b->views.data(), sizeof(BatchView) * n_views);
     b->info.n_views = n_views;
     b->info.candidates = cand;
@@ -1028,6 +1086,7 @@ ges_status ges_batch_set_camera(ges_batch *b, int32_t view, const ges_camera *ca
     CamParams C;
     ges_status r = make_cam(cam, C);
     if (r != GES_OK) return r;
+    set_tiles(C, b->tsx, b->tsy);
     if (C.W != b->views[view].C.W || C.H != b->views[view].C.H)
         return fail(GES_ERR_INVALID_ARG, "view %d: image size must stay %dx%d", view, b->views[view].C.W,
                     b->views[view].C.H);
@@ -1145,6 +1204,7 @@ ges_status render_batch_engine(ges_scene *const *scenes, const std::vector<CamPa
                 if (O.mode == GES_MODE_SURFELS_ONLY) S.M = 0;
                 b->views[v].S = S;
                 b->views[v].C = C[v];
+                set_tiles(b->views[v].C, b->tsx, b->tsy);
                 b->views[v].rgb = out_rgb[v];
                 b->views[v].depth = out_depth ? out_depth[v] : nullptr;
             }

@@ -178,7 +178,7 @@ __device__ __forceinline__ void prep_local_body(const SceneView &S, const CamPar
                     make_int4((int)i, (int)pack_xy(x0, y0), (int)pack_xy(x1, y1), 0);
         }
         if (vis) {
-            const int tx0 = x0 / kTile, tx1 = x1 / kTile, ty0 = y0 / kTile, ty1 = y1 / kTile;
+            const int tx0 = x0 >> C.tsx, tx1 = x1 >> C.tsx, ty0 = y0 >> C.tsy, ty1 = y1 >> C.tsy;
             for (int ty = ty0; ty <= ty1; ++ty)
                 for (int tx = tx0; tx <= tx1; ++tx) {
                     const int t = ty * C.tiles_x + tx;
@@ -246,8 +246,8 @@ __global__ void __launch_bounds__(256) k_colscan(ViewScratch X, int T, LocalBins
     colscan_body(X, T, B, blockIdx.x, blockIdx.y == 0, part);
 }
 
-__device__ __forceinline__ void fill_local_body(const ViewScratch &X, int T, int tiles_x, const LocalBins &B, int c,
-                                                unsigned *cur)
+__device__ __forceinline__ void fill_local_body(const ViewScratch &X, int T, int tiles_x, int tsx, int tsy,
+                                                const LocalBins &B, int c, unsigned *cur)
 {
     if (X.status[ST_FLAGS] & (FLAG_SOVF | FLAG_GOVF)) return;
     const bool surf = c < B.Ps;
@@ -263,17 +263,18 @@ __device__ __forceinline__ void fill_local_body(const ViewScratch &X, int T, int
         const int4 e = seg[k];
         const int id = e.x;
         const unsigned lo = (unsigned)e.y, hi = (unsigned)e.z;
-        const int tx0 = (lo & 0xffff) / kTile, ty0 = (lo >> 16) / kTile;
-        const int tx1 = (hi & 0xffff) / kTile, ty1 = (hi >> 16) / kTile;
+        const int tx0 = (int)(lo & 0xffff) >> tsx, ty0 = (int)(lo >> 16) >> tsy;
+        const int tx1 = (int)(hi & 0xffff) >> tsx, ty1 = (int)(hi >> 16) >> tsy;
         for (int ty = ty0; ty <= ty1; ++ty)
             for (int tx = tx0; tx <= tx1; ++tx) list[atomicAdd(cur + ty * tiles_x + tx, 1u)] = id;
     }
 }
 
-__global__ void __launch_bounds__(kFillThreads) k_fill_local(ViewScratch X, int T, int tiles_x, LocalBins B)
+__global__ void __launch_bounds__(kFillThreads) k_fill_local(ViewScratch X, int T, int tiles_x, int tsx, int tsy,
+                                                             LocalBins B)
 {
     extern __shared__ unsigned cur[];    // T cursors
-    fill_local_body(X, T, tiles_x, B, blockIdx.x, cur);
+    fill_local_body(X, T, tiles_x, tsx, tsy, B, blockIdx.x, cur);
 }
 
 // ---------------------------------------------------------------------------
@@ -301,29 +302,29 @@ __global__ void __launch_bounds__(256) k_prep_atomic(SceneView S, CamParams C, O
     const bool vis = i < (surf ? S.N : S.M) && setup_and_store<kGd, kTr>(S, C, O, X, surf, i, x0, y0, x1, y1);
     if (vis) {
         int *cnt = surf ? X.s_cnt : X.g_cnt;
-        for (int ty = y0 / kTile; ty <= y1 / kTile; ++ty)
-            for (int tx = x0 / kTile; tx <= x1 / kTile; ++tx) atomicAdd(cnt + ty * C.tiles_x + tx, 1);
+        for (int ty = y0 >> C.tsy; ty <= y1 >> C.tsy; ++ty)
+            for (int tx = x0 >> C.tsx; tx <= x1 >> C.tsx; ++tx) atomicAdd(cnt + ty * C.tiles_x + tx, 1);
     }
     append_visible(vis, i, X.status + (surf ? ST_SVIS : ST_GVIS), surf ? X.s_vis : X.g_vis);
 }
 
-__device__ __forceinline__ void fill_one(const float4 *rec, int id, int tiles_x, int *cur, int *list)
+__device__ __forceinline__ void fill_one(const float4 *rec, int id, int tiles_x, int tsx, int tsy, int *cur, int *list)
 {
     const float4 r3 = rec[4 * (int64_t)id + 3];
     const unsigned lo = __float_as_uint(r3.y), hi = __float_as_uint(r3.z);
     const int x0 = lo & 0xffff, y0 = lo >> 16, x1 = hi & 0xffff, y1 = hi >> 16;
-    for (int ty = y0 / kTile; ty <= y1 / kTile; ++ty)
-        for (int tx = x0 / kTile; tx <= x1 / kTile; ++tx) list[atomicAdd(cur + ty * tiles_x + tx, 1)] = id;
+    for (int ty = y0 >> tsy; ty <= y1 >> tsy; ++ty)
+        for (int tx = x0 >> tsx; tx <= x1 >> tsx; ++tx) list[atomicAdd(cur + ty * tiles_x + tx, 1)] = id;
 }
 
-__global__ void __launch_bounds__(256) k_fill_atomic(ViewScratch X, int tiles_x)
+__global__ void __launch_bounds__(256) k_fill_atomic(ViewScratch X, int tiles_x, int tsx, int tsy)
 {
     if (X.status[ST_FLAGS] & (FLAG_SOVF | FLAG_GOVF)) return;
     const unsigned ns = X.status[ST_SVIS], ng = X.status[ST_GVIS];
     const unsigned stride = gridDim.x * blockDim.x;
     for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < ns + ng; k += stride) {
-        if (k < ns) fill_one(X.s_rec, X.s_vis[k], tiles_x, X.s_cur, X.s_list);
-        else fill_one(X.g_rec, X.g_vis[k - ns], tiles_x, X.g_cur, X.g_list);
+        if (k < ns) fill_one(X.s_rec, X.s_vis[k], tiles_x, tsx, tsy, X.s_cur, X.s_list);
+        else fill_one(X.g_rec, X.g_vis[k - ns], tiles_x, tsx, tsy, X.g_cur, X.g_list);
     }
 }
 
@@ -448,9 +449,11 @@ struct WarpBlock {
     float u, v, us, vs;    // pixel centre; sample k sits at (us + 0.5 (k & 1), vs + 0.5 (k >> 1))
     __device__ __forceinline__ WarpBlock(const CamParams &C, int tile, unsigned warp, unsigned lane)
     {
+        // the 8 warps' 8x4 blocks fill the tile row by row
         const int tx = tile % C.tiles_x, ty = tile / C.tiles_x;
-        wx0 = tx * kTile + (warp & 1) * kWarpW;
-        wy0 = ty * kTile + (warp >> 1) * kWarpH;
+        const int wpr = 1 << (C.tsx - 3);          // blocks per tile row
+        wx0 = (tx << C.tsx) + (int)(warp & (unsigned)(wpr - 1)) * kWarpW;
+        wy0 = (ty << C.tsy) + (int)(warp >> (C.tsx - 3)) * kWarpH;
         wactive = wx0 < C.W && wy0 < C.H;        // warp-uniform
         wx1 = min(wx0 + kWarpW - 1, C.W - 1);
         wy1 = min(wy0 + kWarpH - 1, C.H - 1);
@@ -834,7 +837,7 @@ __global__ void __launch_bounds__(kFillThreads) k_bfill(const BatchView *V, int 
     __syncthreads();
     load_view(V, sv, bv);
     __syncthreads();
-    fill_local_body(bv.X, bv.T, bv.C.tiles_x, bv.B, blockIdx.x - bv.prep_base, cur);
+    fill_local_body(bv.X, bv.T, bv.C.tiles_x, bv.C.tsx, bv.C.tsy, bv.B, blockIdx.x - bv.prep_base, cur);
 }
 
 // Persistent raster over the (view, tile) items of the whole batch: each CTA
@@ -975,9 +978,9 @@ cudaError_t launch_binning(const SceneView &S, const CamParams &C, const OptPara
     k_scan<<<2, 1024, 0, st>>>(X, T);
     if (ev) cudaEventRecord(ev[2], st);
     if (local) {
-        if (B.Ps + B.Pg > 0) k_fill_local<<<B.Ps + B.Pg, kFillThreads, local_bins_smem(T, true), st>>>(X, T, C.tiles_x, B);
+        if (B.Ps + B.Pg > 0) k_fill_local<<<B.Ps + B.Pg, kFillThreads, local_bins_smem(T, true), st>>>(X, T, C.tiles_x, C.tsx, C.tsy, B);
     } else {
-        k_fill_atomic<<<152 * 8, 256, 0, st>>>(X, C.tiles_x);
+        k_fill_atomic<<<152 * 8, 256, 0, st>>>(X, C.tiles_x, C.tsx, C.tsy);
     }
     if (ev) cudaEventRecord(ev[3], st);
     return cudaGetLastError();
@@ -994,7 +997,7 @@ __global__ void __launch_bounds__(256) k_count(SceneView S, ViewScratch X, CamPa
     if (X.status[ST_FLAGS] & (FLAG_SOVF | FLAG_GOVF)) return;
     const int tile = blockIdx.x, t = threadIdx.x;
     const int tx = tile % C.tiles_x, ty = tile / C.tiles_x;
-    const int px = tx * kTile + (t & 15), py = ty * kTile + (t >> 4);
+    const int px = (tx << C.tsx) + (t & ((1 << C.tsx) - 1)), py = (ty << C.tsy) + (t >> C.tsx);
     const bool in_img = px < C.W && py < C.H;
     const float u = px + 0.5f, v = py + 0.5f;
     unsigned ns = 0, ng = 0;

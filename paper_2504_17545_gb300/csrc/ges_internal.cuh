@@ -15,9 +15,12 @@
 
 namespace ges {
 
-constexpr int kTile = 16;               // binning tile edge (pixels)
+constexpr int kTile = 16;               // default binning tile edge (pixels): 16x16
+constexpr int kTileShift = 4;           // log2 kTile
 constexpr int kRasterThreads = 256;     // 8 warps, each an 8x4 pixel block
 constexpr int kWarpW = 8, kWarpH = 4;
+// A binning tile holds the 8 warps' blocks: 2^tsx x 2^tsy pixels with
+// tsx + tsy = 8 and tsx in [3, 6] (8x32, 16x16, 32x8, 64x4).
 
 // status word layout (uint32 words)
 enum : int {
@@ -42,6 +45,7 @@ struct CamParams {
     float znear, izn;     // z_near and 1/z_near
     float bg[3];
     int W, H, tiles_x, tiles_y;
+    int tsx, tsy;         // log2 of the binning tile's width and height
 };
 
 struct OptParams {

@@ -29,9 +29,10 @@ def _views():
             sg.look_at((0.1, 0.05, -0.6), (0, 0.1, 1), (0, 1, 0), 97, 61, 95.0)]
 
 
-def _check(R, scenes, views, sov, opts, reps=2):
+def _check(R, scenes, views, sov, opts, reps=2, shape=None):
     b = R.GESBatch(scenes, views, sov, opts=opts)
-    assert (b.info().tile_w, b.info().tile_h) == (16, 16)
+    if shape is not None:
+        assert f"{b.info().tile_w}x{b.info().tile_h}" == shape
     for rep in range(reps):
         b.launch()
         b.sync()
@@ -106,12 +107,34 @@ def test_timed_orbit_path_matches_oracle(R):
     gs.close()
 
 
+@pytest.mark.parametrize("shape", ["16x16", "32x8", "8x32"])
+def test_batch_tile_shapes_equal_single_views(R, monkeypatch, shape):
+    """Every binning tile shape the autotuner tries gives bitwise the per-view
+    (16x16) render, with ragged, tiny and empty views, 4 samples and 2D
+    Gaussians: the shape moves work between CTAs, never the arithmetic."""
+    monkeypatch.setenv("GES_BATCH_TILE", shape)
+    scene, cams = sg.config_scene(0)
+    other = _small(95, 2000, 6000)
+    empty = other.subset(s_idx=np.zeros(0, int), g_idx=np.zeros(0, int))
+    gs = [R.GESScene.from_arrays(x) for x in (scene, other, empty)]
+    views = [cams[0]] + _views() + [cams[0]]
+    sov = [0, 1, 0, 1, 0, 1, 2]
+    for opts in (None, dict(samples=4)):
+        _check(R, gs, views, sov, opts, reps=1, shape=shape)
+    for g in gs:
+        g.close()
+    g2 = R.GESScene.from_arrays(_small2d(96, 2000, 6000))
+    _check(R, [g2], _views()[:3], [0, 0, 0], None, reps=1, shape=shape)
+    g2.close()
+
+
 def test_batch_autotuner_candidates(R):
     scene, cams = sg.config_scene(0)
     gs = R.GESScene.from_arrays(scene)
     b = R.GESBatch([gs], [cams[0]])
-    # 5 preprocess ranges x 2 raster occupancies
-    assert b.info().candidates == 10
+    # 3 tile shapes x 5 preprocess ranges x 2 raster occupancies
+    assert b.info().candidates == 30
+    assert f"{b.info().tile_w}x{b.info().tile_h}" in ("16x16", "32x8", "8x32")
     b.launch()
     b.sync()
     single = R.render(gs, cams[0], with_aux=False)
