@@ -776,6 +776,8 @@ struct ges_batch {
     ges_batch_info info{};
     ges_profile profile{};
     int tsx = kTileShift, tsy = kTileShift;   // binning tile of the chosen configuration
+    int2 *d_map = nullptr;                 // preprocess CTA -> (view, CTA of the view), both launches
+    size_t map_cap = 0;                    // entries
 };
 
 namespace {
@@ -789,6 +791,7 @@ void batch_release(ges_batch *b)
         if (e) cudaEventDestroy(e);
     if (b->stream) cudaStreamDestroy(b->stream);
     if (b->arena) cudaFree(b->arena);
+    if (b->d_map) cudaFree(b->d_map);
     if (b->d_table) cudaFree(b->d_table);
     if (b->d_status) cudaFree(b->d_status);
     if (b->h_table) cudaFreeHost(b->h_table);
@@ -849,6 +852,51 @@ size_t batch_layout(ges_batch *b, const std::vector<SceneView> &S, const std::ve
         X.status = b->d_status + (size_t)v * ST_WORDS;
     }
     return off;
+}
+
+// The preprocess launches' CTA order: views of one scene (same arrays and
+// counts) take each primitive range one after another, so only the first of
+// them reads the range's attributes from HBM; surfel CTAs first, then the
+// Gaussian ones (their own launch).  Uploads the map; P gets its pointers.
+cudaError_t upload_prep_map(ges_batch *b, BatchPlan &P)
+{
+    std::vector<int2> m;
+    m.reserve((size_t)P.total_sprep + P.total_gprep);
+    std::vector<int> done(b->n, 0);
+    std::vector<std::vector<int>> groups;
+    for (int v = 0; v < b->n; ++v) {
+        if (done[v]) continue;
+        std::vector<int> g{v};
+        done[v] = 1;
+        const SceneView &a = b->views[v].S;
+        for (int w = v + 1; w < b->n; ++w) {
+            const SceneView &c = b->views[w].S;
+            if (!done[w] && c.s_pos == a.s_pos && c.g_pos == a.g_pos && c.N == a.N && c.M == a.M &&
+                b->views[w].B.Ps == b->views[v].B.Ps && b->views[w].B.Pg == b->views[v].B.Pg) {
+                g.push_back(w);
+                done[w] = 1;
+            }
+        }
+        groups.push_back(g);
+    }
+    for (int kind = 0; kind < 2; ++kind)
+        for (const std::vector<int> &g : groups) {
+            const LocalBins &B = b->views[g[0]].B;
+            const int n = kind == 0 ? B.Ps : B.Pg;
+            for (int c = 0; c < n; ++c)
+                for (int v : g) m.push_back(make_int2(v, kind == 0 ? c : B.Ps + c));
+        }
+    if (m.size() > b->map_cap) {
+        if (b->d_map) cudaFree(b->d_map);
+        b->d_map = nullptr;
+        b->map_cap = 0;
+        cudaError_t e = cudaMalloc(&b->d_map, std::max<size_t>(m.size(), 1) * sizeof(int2));
+        if (e != cudaSuccess) return e;
+        b->map_cap = std::max<size_t>(m.size(), 1);
+    }
+    P.smap = b->d_map;
+    P.gmap = b->d_map + P.total_sprep;
+    return m.empty() ? cudaSuccess : cudaMemcpy(b->d_map, m.data(), m.size() * sizeof(int2), cudaMemcpyHostToDevice);
 }
 
 }  // namespace
@@ -984,7 +1032,7 @@ static ges_status batch_create(ges_scene *const *scenes, const ges_camera *cams,
         for (int pi = 0; pi < (tune ? 2 : 1); ++pi) {
             const int per_sm = kPerSm[pi];
             batch_layout(b, S, Cs, R, (unsigned char *)b->arena);
-            BatchPlan P{n_views, 0, 0, 0, 0, 0, 0, sms * per_sm, S[0].gdim};
+            BatchPlan P{n_views, 0, 0, 0, 0, 0, 0, sms * per_sm, S[0].gdim, nullptr, nullptr};
             for (int v = 0; v < n_views; ++v) {
                 P.total_tiles += b->views[v].T;
                 P.total_prep += b->views[v].B.Ps + b->views[v].B.Pg;
@@ -994,6 +1042,7 @@ static ges_status batch_create(ges_scene *const *scenes, const ges_camera *cams,
                 P.max_T = std::max(P.max_T, b->views[v].T);
             }
             std::memcpy(b->h_table, b->views.data(), sizeof(BatchView) * n_views);
+            BATCH_CUDA(upload_prep_map(b, P));
             cudaGraph_t g = nullptr;
             cudaGraphExec_t ex = nullptr;
             BATCH_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
@@ -1050,9 +1099,17 @@ static ges_status batch_create(ges_scene *const *scenes, const ges_camera *cams,
         batch_release(b);
         return fail(GES_ERR_CAPACITY, "every configuration overflowed the batch's tile lists");
     }
-    // the table the chosen graph reads: rebuild it for that candidate
+    // the table and the CTA map the chosen graph reads: rebuild them for that candidate
     batch_layout(b, S, shaped({b->tsx, b->tsy}), b->info.prims_per_cta, (unsigned char *)b->arena);
     std::memcpy(b->h_table, b->views.data(), sizeof(BatchView) * n_views);
+    {
+        BatchPlan P{};
+        for (int v = 0; v < n_views; ++v) {
+            P.total_sprep += b->views[v].B.Ps;
+            P.total_gprep += b->views[v].B.Pg;
+        }
+        BATCH_CUDA(upload_prep_map(b, P));
+    }
     b->info.n_views = n_views;
     b->info.candidates = cand;
     b->info.tuned_ms = best_ms;

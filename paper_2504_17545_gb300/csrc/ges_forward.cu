@@ -780,28 +780,27 @@ __device__ __forceinline__ void load_view(const BatchView *V, int v, BatchView &
 }
 
 // Preprocess of all views, one launch per primitive kind (kKind 1: the
-// surfel ranges, 2: the Gaussian ranges); CTA x of the launch is range
-// x - base(view) of its kind.  The two set-ups need different registers, and
-// a kernel per kind keeps the one from spilling for the other.
+// surfel ranges, 2: the Gaussian ranges); CTA x of the launch takes the view
+// and the range of map[x].  The two set-ups need different registers, and a
+// kernel per kind keeps the one from spilling for the other.
 template <int kGd, int kKind>
-__global__ void __launch_bounds__(kPrepThreads, 2) k_bprep(const BatchView *V, int n, OptParams O,
-                                                          unsigned long long *t0)
+__global__ void __launch_bounds__(kPrepThreads, 2) k_bprep(const BatchView *V, const int2 *__restrict__ map,
+                                                          OptParams O, unsigned long long *t0)
 {
     extern __shared__ unsigned hist[];
     __shared__ unsigned vcnt;
     __shared__ __align__(16) unsigned char bv_raw[sizeof(BatchView)];
     BatchView &bv = *reinterpret_cast<BatchView *>(bv_raw);
-    __shared__ int sv;
+    __shared__ int2 sm;
     if (threadIdx.x == 0) {
         // the first CTA to start stamps the batch's start time (t0 is zeroed per launch)
         atomicCAS(t0, 0ull, global_timer_ns());
-        sv = find_view(n, blockIdx.x, [&](int k) { return kKind == 1 ? V[k].sprep_base : V[k].gprep_base; });
+        sm = map[blockIdx.x];
     }
     __syncthreads();
-    load_view(V, sv, bv);
+    load_view(V, sm.x, bv);
     __syncthreads();
-    const int c = kKind == 1 ? (int)blockIdx.x - bv.sprep_base : bv.B.Ps + (int)blockIdx.x - bv.gprep_base;
-    prep_local_body<kGd, false, kKind>(bv.S, bv.C, O, bv.X, bv.B, c, hist, vcnt);
+    prep_local_body<kGd, false, kKind>(bv.S, bv.C, O, bv.X, bv.B, sm.y, hist, vcnt);
 }
 
 __global__ void __launch_bounds__(256) k_bcolscan(const BatchView *V, int n)
@@ -897,12 +896,12 @@ cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const Opt
         unsigned long long *t0 = reinterpret_cast<unsigned long long *>(work_counter + 2);
         const size_t sm = local_bins_smem(P.max_T, false);
         if (P.total_sprep > 0) {
-            if (P.gdim == 2) k_bprep<2, 1><<<P.total_sprep, kPrepThreads, sm, st>>>(d_views, P.n, O, t0);
-            else k_bprep<3, 1><<<P.total_sprep, kPrepThreads, sm, st>>>(d_views, P.n, O, t0);
+            if (P.gdim == 2) k_bprep<2, 1><<<P.total_sprep, kPrepThreads, sm, st>>>(d_views, P.smap, O, t0);
+            else k_bprep<3, 1><<<P.total_sprep, kPrepThreads, sm, st>>>(d_views, P.smap, O, t0);
         }
         if (P.total_gprep > 0) {
-            if (P.gdim == 2) k_bprep<2, 2><<<P.total_gprep, kPrepThreads, sm, st>>>(d_views, P.n, O, t0);
-            else k_bprep<3, 2><<<P.total_gprep, kPrepThreads, sm, st>>>(d_views, P.n, O, t0);
+            if (P.gdim == 2) k_bprep<2, 2><<<P.total_gprep, kPrepThreads, sm, st>>>(d_views, P.gmap, O, t0);
+            else k_bprep<3, 2><<<P.total_gprep, kPrepThreads, sm, st>>>(d_views, P.gmap, O, t0);
         }
     }
     mark(1);

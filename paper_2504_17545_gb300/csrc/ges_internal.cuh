@@ -121,6 +121,10 @@ struct BatchPlan {
     int total_sprep, total_gprep;            // preprocess CTAs of the surfel and the Gaussian launch
     int raster_ctas;                         // persistent raster grid
     int gdim;                                // Gaussian kind of every scene (2 or 3; 0 reads as 3)
+    // (view, CTA of the view) of each CTA of the surfel / Gaussian preprocess
+    // launch: the views of one scene take the same primitive range one after
+    // another, so all but the first read its attributes from L2
+    const int2 *smap, *gmap;
 };
 cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const OptParams &O, unsigned *work_counter,
                          cudaStream_t st, cudaEvent_t *ev /* 5 events or nullptr */);
