@@ -23,11 +23,24 @@ _lib = None
 
 # Paper defaults: eps_i = 5 * mean axis length (Sec. 5), 1/255 clamp (Sec. 3),
 # opaque extent 2 ln 255 (Sec. 4.1), 3DGS's fixed screen low-pass 0.3.
-# The tol_* entries are the ambiguity bands of the parity tests.
+# The tol_* entries are the ambiguity bands of the parity tests, each the
+# float32 error bound of the quantity it guards (u = 2^-24):
+#   tol_disc_rel, tol_disc_graze  a fragment's a^2 + b^2 against r^2: the
+#       disc forms' coefficients (6u each, three terms of at most 3 times the
+#       rim's 1/z) and evaluation, 2 (20u + 20u + 20u) = 120u, plus the frame's
+#       rounding eps_f = 20u in the plane, 2 eps_f = 40u: 160u <= 1e-5; the
+#       frame's tilt moves the fragment in the plane by 2 eps_f / |cos| =
+#       2.4e-6 / |cos| = 1e-5 x 0.24 / |cos| (0.25 taken)
+#   tol_depth_rel  two fragments ordered by depth: each 1/z within 26u (its
+#       coefficients and evaluation), 52u = 3.1e-6 (3.5e-6 taken)
+#   tol_gdepth_rel  a Gaussian's key d - eps against D_s: 2u and 28u, 30u = 1.8e-6
+#   tol_alpha  alpha at the 1/255 cut: q = y0^2 + y1^2 within 26u relative,
+#       alpha within 9e-6 relative, 3.4e-8 absolute at the cut (1e-5 taken)
+#   tol_graze  |cos| below which a fragment is grazing outright
 DEFAULT_OPTS = dict(eps_mode=0, eps_value=0.1, eps_factor=5.0, lowpass=0.3,
                     alpha_min=1.0 / 255.0, surfel_r2=2.0 * math.log(255.0), mode=0,
-                    tol_depth_rel=1e-6, tol_disc_rel=1e-5, tol_graze=1e-3, tol_alpha=1e-5,
-                    tol_gdepth_rel=2e-6, samples=1, filter=0, tol_disc_graze=0.1)
+                    tol_depth_rel=3.5e-6, tol_disc_rel=1e-5, tol_graze=1e-3, tol_alpha=1e-5,
+                    tol_gdepth_rel=2e-6, samples=1, filter=0, tol_disc_graze=0.25)
 
 
 class _Scene(C.Structure):

@@ -18,14 +18,14 @@ import numpy as np
 import oracle
 
 COL_TOL = 2e-4       # colour tolerance of the FP32 path (absolute, per channel)
-# GPU depth = 1/(iz0 + gu du + gv dv): iz0 carries the rounding of the
-# double-float centre and of its reciprocal (~3u), the affine step ~2u, the
-# final reciprocal 1u, and 16-bit quaternions renormalised in float32 a few u
-# more; over millions of pixels the worst case reaches ~20u (u = 2^-24).
+# GPU depth = 1/(iz0 + gu du + gv dv): the three coefficients carry at most
+# 6u each (u = 2^-24; formed from the float32 frame and the double-float
+# centre), the three terms are at most 1.5 times 1/z at a pixel of the disc,
+# the two FMAs add 2u and the reciprocal 2u: 6u x 4 + 2u + 2u = 28u = 1.7e-6.
 DEPTH_REL = 2e-6
-# depth z = (n.P)/(n.d): the float32 plane normal carries a few u per
-# component, so the relative error of n.d (and of z) grows as 1/|cos| of the
-# angle between the ray and the disc normal; 4e-7 ~ 6u covers it
+# The frame's rounding (eps_f = 20u) tilts the plane about the centre; at a
+# pixel theta (at most ~0.3 rad for the discs here) from the centre's ray the
+# depth moves by eps_f theta / |cos| = 6u / |cos| = 3.6e-7 / |cos|.
 DEPTH_GRAZE = 4e-7
 
 
