@@ -1054,17 +1054,154 @@ static void sh_backward(int deg, const double *sh, const double *dir, double dis
     }
 }
 
+/* Rotation gradient: columns GR[:,k] = dL/d(R e_k) -> dL/dq through the
+   normalised quaternion qhat = q/|q| and R(qhat). */
+static void rot_backward(const double *GR, const double *qn, double qnorm, double *g_q)
+{
+    double w = qn[0], qx = qn[1], qy = qn[2], qz = qn[3];
+    double dR[4][9] = {
+        {0, -2*qz, 2*qy, 2*qz, 0, -2*qx, -2*qy, 2*qx, 0},
+        {0, 2*qy, 2*qz, 2*qy, -4*qx, -2*w, 2*qz, 2*w, -4*qx},
+        {-4*qy, 2*qx, 2*w, 2*qx, 0, 2*qz, -2*w, 2*qz, -4*qy},
+        {-4*qz, -2*w, 2*qx, 2*w, -4*qz, 2*qy, 2*qx, 2*qy, 0},
+    };
+    double gqn[4];
+    for (int a = 0; a < 4; ++a) {
+        double acc = 0.0;
+        for (int k = 0; k < 9; ++k) acc += GR[k] * dR[a][k];
+        gqn[a] = acc;
+    }
+    double pr = gqn[0]*w + gqn[1]*qx + gqn[2]*qy + gqn[3]*qz;
+    for (int a = 0; a < 4; ++a) g_q[a] = (gqn[a] - pr * qn[a]) / qnorm;
+}
+
+/* 2D Gaussian of 2D-GES (Sec. 6.4, Eq. 17-18), one primitive.  At a pixel
+   whose ray d meets the splat plane at z = (N.t)/(N.d), X = z d - t,
+   a = X.U / f1, b = X.V / f2 (U, V, N the camera-space frame, t the centre,
+   f_k = s_k S_k the filtered scales), alpha = sigma0 / (S1 S2) exp(-(a^2 + b^2)/2).
+   The per-pixel part gives dL/d(t, U, V, N, f1, f2, sigma); the object-space
+   filter S1 = sqrt(1 + r M11/det M), S2 = sqrt(1 + r M00/det M) with M = J^T J,
+   J = Jp(t) [s1 U, s2 V], then passes it on to t, U, V and s.  The depth test
+   and the clamp are indicators (no gradient), eps_i included. */
+static void gauss2d_backward(const ora_scene *S, const ora_camera *c, const ora_opts *o, const gauss_t *g,
+                             int64_t gi, const double *dL_drgb, const double *rgb, const double *Ds,
+                             const double *WG, const double *Rc, double *gp, double *g_rot, double *g_scale,
+                             double *g_opac, double *g_sh)
+{
+    const int W = c->width;
+    const int64_t HW = (int64_t)W * c->height;
+    const int K = (S->sh_degree + 1) * (S->sh_degree + 1);
+    const surf_t *f = &g->geo;
+    double dc[3] = {0, 0, 0}, dsig = 0.0, gt[3] = {0, 0, 0}, gU[3] = {0, 0, 0}, gV[3] = {0, 0, 0};
+    double gN[3] = {0, 0, 0}, gf1 = 0.0, gf2 = 0.0;
+    for (int j = g->y0; j <= g->y1; ++j)
+        for (int i = g->x0; i <= g->x1; ++i) {
+            const int64_t pix = (int64_t)j * W + i;
+            double d[3];
+            pixel_ray(c, i, j, d);
+            const double Nd = dot3(f->n, d);
+            if (Nd == 0.0) continue;
+            const double z = dot3(f->n, f->pc) / Nd;
+            if (!(z > c->znear)) continue;
+            double X[3];
+            for (int q = 0; q < 3; ++q) X[q] = z * d[q] - f->pc[q];
+            const double a = dot3(X, f->tu) / f->s1, b = dot3(X, f->tv) / f->s2;
+            const double e = exp(-0.5 * (a*a + b*b)), al = g->sigma * e;
+            if (!(al >= o->alpha_min) || !(z < Ds[pix] + g->eps)) continue;
+            const double k = o->mode == 0 ? 1.0 / (1.0 + WG[pix]) : 1.0 / WG[pix];
+            double gdotcC = 0.0;
+            for (int ch = 0; ch < 3; ++ch) {
+                const double gch = dL_drgb[ch * HW + pix];
+                dc[ch] += al * k * gch;
+                gdotcC += gch * (g->rgb[ch] - rgb[ch * HW + pix]);
+            }
+            const double dLda = k * gdotcC;
+            dsig += dLda * e;
+            const double dLdrho = dLda * al * (-0.5);
+            const double dLa = dLdrho * 2.0 * a, dLb = dLdrho * 2.0 * b;
+            const double Ud = dot3(f->tu, d), Vd = dot3(f->tv, d);
+            /* dz/dt = N/Nd, dz/dN = -X/Nd, dX/dt = d (dz/dt)^T - I */
+            for (int q = 0; q < 3; ++q) {
+                gt[q] += dLa * ((Ud / Nd) * f->n[q] - f->tu[q]) / f->s1 +
+                         dLb * ((Vd / Nd) * f->n[q] - f->tv[q]) / f->s2;
+                gU[q] += dLa * X[q] / f->s1;
+                gV[q] += dLb * X[q] / f->s2;
+                gN[q] += -(dLa * Ud / f->s1 + dLb * Vd / f->s2) * X[q] / Nd;
+            }
+            gf1 += dLa * (-a / f->s1);
+            gf2 += dLb * (-b / f->s2);
+        }
+    const double *s = S->g_scale + 2*gi;
+    /* colour -> SH and position (through the view direction) */
+    sh_backward(S->sh_degree, S->g_sh + (int64_t)3*K*gi, g->dir, g->dist, g->raw, dc, g_sh, gp);
+    /* sigma = sigma0 / (S1 S2), f_k = s_k S_k */
+    *g_opac = dsig / (g->S1 * g->S2);
+    const double gS1 = gf1 * s[0] - dsig * g->sigma / g->S1, gS2 = gf2 * s[1] - dsig * g->sigma / g->S2;
+    double gs0 = gf1 * g->S1, gs1 = gf2 * g->S2;
+    /* rebuild J = Jp [s1 U, s2 V] and M = J^T J */
+    const double x = g->t[0], y = g->t[1], z = g->t[2];
+    const double Jp[6] = {c->fx / z, 0.0, -c->fx * x / (z*z), 0.0, c->fy / z, -c->fy * y / (z*z)};
+    double JU[2], JV[2], J[4];
+    for (int a = 0; a < 2; ++a) {
+        JU[a] = dot3(Jp + 3*a, f->tu);
+        JV[a] = dot3(Jp + 3*a, f->tv);
+        J[2*a] = s[0] * JU[a];
+        J[2*a + 1] = s[1] * JV[a];
+    }
+    const double M00 = J[0]*J[0] + J[2]*J[2], M01 = J[0]*J[1] + J[2]*J[3], M11 = J[1]*J[1] + J[3]*J[3];
+    const double det = M00 * M11 - M01 * M01, r = o->lowpass, d2 = det * det;
+    /* S1^2 = 1 + r M11/det, S2^2 = 1 + r M00/det */
+    const double h1 = gS1 * r / (2.0 * g->S1), h2 = gS2 * r / (2.0 * g->S2);
+    const double gM00 = h1 * (-M11 * M11 / d2) + h2 * (-M01 * M01 / d2);
+    const double gM11 = h1 * (-M01 * M01 / d2) + h2 * (-M00 * M00 / d2);
+    const double gM01 = h1 * (2.0 * M11 * M01 / d2) + h2 * (2.0 * M00 * M01 / d2);
+    /* M = J^T J */
+    double gJ[4];
+    gJ[0] = 2.0 * J[0] * gM00 + J[1] * gM01;
+    gJ[2] = 2.0 * J[2] * gM00 + J[3] * gM01;
+    gJ[1] = J[0] * gM01 + 2.0 * J[1] * gM11;
+    gJ[3] = J[2] * gM01 + 2.0 * J[3] * gM11;
+    /* J[a][0] = s1 (Jp_a . U), J[a][1] = s2 (Jp_a . V) */
+    double gJp[6];
+    for (int a = 0; a < 2; ++a) {
+        gs0 += gJ[2*a] * JU[a];
+        gs1 += gJ[2*a + 1] * JV[a];
+        for (int q = 0; q < 3; ++q) {
+            gU[q] += s[0] * gJ[2*a] * Jp[3*a + q];
+            gV[q] += s[1] * gJ[2*a + 1] * Jp[3*a + q];
+            gJp[3*a + q] = s[0] * gJ[2*a] * f->tu[q] + s[1] * gJ[2*a + 1] * f->tv[q];
+        }
+    }
+    g_scale[0] = gs0;
+    g_scale[1] = gs1;
+    /* Jp(t) -> t */
+    gt[0] += gJp[2] * (-c->fx / (z*z));
+    gt[1] += gJp[5] * (-c->fy / (z*z));
+    gt[2] += gJp[0] * (-c->fx / (z*z)) + gJp[2] * (2.0 * c->fx * x / (z*z*z))
+           + gJp[4] * (-c->fy / (z*z)) + gJp[5] * (2.0 * c->fy * y / (z*z*z));
+    /* t = Rc p + tc; U, V, N = Rc R e_k:  world gradients through Rc^T */
+    double GR[9];
+    for (int q = 0; q < 3; ++q) {
+        gp[q] += Rc[q]*gt[0] + Rc[3 + q]*gt[1] + Rc[6 + q]*gt[2];
+        GR[3*q] = Rc[q]*gU[0] + Rc[3 + q]*gU[1] + Rc[6 + q]*gU[2];
+        GR[3*q + 1] = Rc[q]*gV[0] + Rc[3 + q]*gV[1] + Rc[6 + q]*gV[2];
+        GR[3*q + 2] = Rc[q]*gN[0] + Rc[3 + q]*gN[1] + Rc[6 + q]*gN[2];
+    }
+    rot_backward(GR, g->qn, g->qnorm, g_rot);
+}
+
 int ora_backward(const ora_scene *S, const ora_camera *c, const ora_opts *o, int nthreads,
                  const double *dL_drgb,
                  double *gg_pos, double *gg_rot, double *gg_scale, double *gg_opac, double *gg_sh,
                  double *gs_sh)
 {
-    if (!check_args(S, c, o) || S->gauss_dim == 2) return ORA_BAD_ARG;   /* 3D Gaussians only */
+    if (!check_args(S, c, o)) return ORA_BAD_ARG;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #endif
     const int W = c->width, H = c->height;
     const int64_t HW = (int64_t)W * H, N = S->n_surfels, M = S->n_gaussians;
+    const int D = S->gauss_dim == 2 ? 2 : 3;
     const int K = (S->sh_degree + 1) * (S->sh_degree + 1);
     double *rgb = malloc(sizeof(double) * 3 * (size_t)HW), *Ds = malloc(sizeof(double) * (size_t)HW);
     double *WG = malloc(sizeof(double) * (size_t)HW);
@@ -1106,7 +1243,7 @@ int ora_backward(const ora_scene *S, const ora_camera *c, const ora_opts *o, int
 
     memset(gg_pos, 0, sizeof(double) * 3 * (size_t)M);
     memset(gg_rot, 0, sizeof(double) * 4 * (size_t)M);
-    memset(gg_scale, 0, sizeof(double) * 3 * (size_t)M);
+    memset(gg_scale, 0, sizeof(double) * D * (size_t)M);
     memset(gg_opac, 0, sizeof(double) * (size_t)M);
     memset(gg_sh, 0, sizeof(double) * 3 * (size_t)K * (size_t)M);
     if (o->mode != 1) {
@@ -1114,6 +1251,11 @@ int ora_backward(const ora_scene *S, const ora_camera *c, const ora_opts *o, int
         for (int64_t gi = 0; gi < M; ++gi) {
             const gauss_t *g = &P.gs[gi];
             if (!g->valid) continue;
+            if (g->dim == 2) {
+                gauss2d_backward(S, c, o, g, gi, dL_drgb, rgb, Ds, WG, Rc, gg_pos + 3*gi, gg_rot + 4*gi,
+                                 gg_scale + 2*gi, gg_opac + gi, gg_sh + (int64_t)3*K*gi);
+                continue;
+            }
             /* 2D-level gradients summed over the Gaussian's pixels */
             double dc[3] = {0, 0, 0}, dsig = 0, dpx = 0, dpy = 0, dca = 0, dcb = 0, dcc = 0;
             for (int j = g->y0; j <= g->y1; ++j) {
@@ -1229,23 +1371,7 @@ int ora_backward(const ora_scene *S, const ora_camera *c, const ora_opts *o, int
                 if (v3 != 0.0 && s[b] != 0.0) gs += dk3 * g->k3 * v3 / (s[b] * g->se[b] * g->se[b]);
                 gg_scale[3*gi + b] = gs;
             }
-            /* R(qhat): partial derivatives of each entry w.r.t. (w,x,y,z) */
-            double w = g->qn[0], qx = g->qn[1], qy = g->qn[2], qz = g->qn[3];
-            double dR[4][9] = {
-                {0, -2*qz, 2*qy, 2*qz, 0, -2*qx, -2*qy, 2*qx, 0},
-                {0, 2*qy, 2*qz, 2*qy, -4*qx, -2*w, 2*qz, 2*w, -4*qx},
-                {-4*qy, 2*qx, 2*w, 2*qx, 0, 2*qz, -2*w, 2*qz, -4*qy},
-                {-4*qz, -2*w, 2*qx, 2*w, -4*qz, 2*qy, 2*qx, 2*qy, 0},
-            };
-            double gqn[4];
-            for (int a = 0; a < 4; ++a) {
-                double acc = 0.0;
-                for (int k = 0; k < 9; ++k) acc += GR[k] * dR[a][k];
-                gqn[a] = acc;
-            }
-            /* qhat = q/|q|:  dL/dq = (gqn - qhat (qhat . gqn)) / |q| */
-            double pr = gqn[0]*w + gqn[1]*qx + gqn[2]*qy + gqn[3]*qz;
-            for (int a = 0; a < 4; ++a) gg_rot[4*gi + a] = (gqn[a] - pr * g->qn[a]) / g->qnorm;
+            rot_backward(GR, g->qn, g->qnorm, gg_rot + 4*gi);
         }
     }
     prep_free(&P);

@@ -228,14 +228,15 @@ def contribution(scene, cam, opts=None):
 
 
 def backward(scene, cam, dL_drgb, opts=None, nthreads: int = 0):
-    """Analytic FP64 gradients of sum(dL_drgb * C)."""
+    """Analytic FP64 gradients of sum(dL_drgb * C); g_scale is [M, 3] for 3D
+    Gaussians and [M, 2] for the 2D Gaussians of 2D-GES (Sec. 6.4)."""
     lib = load()
     pin = _Pinned(scene, cam, opts)
     K = (scene.sh_degree + 1) ** 2
     M, N = scene.n_gaussians, scene.n_surfels
     g = _d(dL_drgb)
     assert g.shape == (3, cam.height, cam.width)
-    out = dict(g_pos=np.empty((M, 3)), g_rot=np.empty((M, 4)), g_scale=np.empty((M, 3)),
+    out = dict(g_pos=np.empty((M, 3)), g_rot=np.empty((M, 4)), g_scale=np.empty((M, pin.s.gauss_dim)),
                g_opac=np.empty((M,)), g_sh=np.empty((M, K, 3)), s_sh=np.empty((N, K, 3)))
     st = lib.ora_backward(C.byref(pin.s), C.byref(pin.c), C.byref(pin.o), int(nthreads), g.ctypes.data,
                           *[out[k].ctypes.data for k in ("g_pos", "g_rot", "g_scale", "g_opac", "g_sh", "s_sh")])

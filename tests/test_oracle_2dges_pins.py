@@ -251,3 +251,85 @@ def test_2d_eps_uses_two_axes(oracle_lib):
     sc = _splat_scene([0.0, 0.0, 2.0], [1.0, 0, 0, 0], [0.03, 0.05], 0.5)
     info = oracle_lib.gauss_info(sc, cam, 0)
     np.testing.assert_allclose(info["eps"], gold["eps_factor"]["value"] / 2.0 * 0.08, rtol=1e-15)
+
+
+# ---------------------------------------------- backward (Sec. 6.4, FD)
+
+def _flat_crop(seed, **kw):
+    sc, cam = sg.crop_scene(seed, **kw)
+    sc = f64(sc)
+    sc.g_scale = np.ascontiguousarray(sc.g_scale[:, :2])
+    return sc, cam
+
+
+@pytest.mark.parametrize("opts", [dict(mode=0), dict(mode=2), dict(mode=0, lowpass=1.0, samples=4)])
+def test_2d_backward_matches_central_differences(opts):
+    """Every gradient of the 2D-GES backward (through the ray-splat hit, the
+    object-space filter factors S_k of Eq. 17-18 and the view direction of the
+    SH colour) against central differences of the FP64 render, wherever no
+    alpha cut or depth test flips inside the step."""
+    import oracle as O
+    sc, cam = _flat_crop(11)
+    rng = np.random.default_rng(12)
+    g = rng.standard_normal((3, cam.height, cam.width))
+    grads = O.backward(sc, cam, g, opts)
+    base = O.render(sc, cam, opts, nthreads=1)
+    assert grads["g_scale"].shape == (sc.n_gaussians, 2)
+    assert base["ncontrib"].sum() > 200
+
+    def loss(o):
+        out = O.render(sc, cam, opts, nthreads=1)
+        return float(np.sum(out["rgb"] * g)), out
+
+    n_checked = {}
+    for arr_name in ("g_pos", "g_rot", "g_scale", "g_opac", "g_sh", "s_sh"):
+        arr = getattr(sc, arr_name)
+        flat = arr.reshape(-1)
+        idx = range(flat.size) if flat.size <= 160 else rng.choice(flat.size, 160, replace=False)
+        gmax = np.abs(grads[arr_name]).max()
+        for k in idx:
+            h = 1e-6 * (abs(flat[k]) if arr_name == "g_scale" else max(1.0, abs(flat[k])))
+            old = flat[k]
+            flat[k] = old + h
+            lp, op = loss(opts)
+            flat[k] = old - h
+            lm, om = loss(opts)
+            flat[k] = old
+            if not (np.array_equal(op["ncontrib"], om["ncontrib"]) and np.array_equal(op["id"], om["id"])
+                    and np.array_equal(op["ncontrib"], base["ncontrib"])):
+                continue
+            fd = (lp - lm) / (2 * h)
+            an = grads[arr_name].reshape(-1)[k]
+            assert abs(fd - an) <= 2e-5 * abs(an) + 1e-6 * gmax + 1e-9, (arr_name, k, fd, an)
+            n_checked[arr_name] = n_checked.get(arr_name, 0) + (abs(an) > 1e-3 * gmax)
+    # each kind of gradient is checked where it is not negligible
+    assert all(n_checked.get(k, 0) >= 10 for k in ("g_pos", "g_rot", "g_scale", "g_opac", "g_sh")), n_checked
+
+
+def test_2d_backward_filter_factor_chain_on_a_sub_pixel_splat():
+    """A splat far below a pixel is almost all filter: f_k = s_k S_k tends to
+    sqrt(r) times the pixel footprint, so dL/ds_k is small while the opacity
+    gradient carries the 1/(S1 S2) factor.  Checked by central differences on
+    one tilted, off-axis splat where S1, S2 differ from 1 by a factor of
+    several, so a dropped S-term or a swapped M00/M11 shows at once."""
+    import oracle as O
+    cam = sg.look_at((0.0, 0.0, -3.0), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 48, 40, 60.0)
+    q = np.array([0.9, 0.3, -0.25, 0.2])
+    q /= np.linalg.norm(q)
+    sc = f64(_splat_scene([0.35, -0.2, 0.1], q, [0.012, 0.004], 0.8))
+    g = np.random.default_rng(3).standard_normal((3, cam.height, cam.width))
+    opts = dict(lowpass=0.5)
+    info = O.gauss_info(sc, cam, 0, opts)
+    gr = O.backward(sc, cam, g, opts)
+    for name, k in (("g_scale", 0), ("g_scale", 1), ("g_opac", 0), ("g_pos", 0), ("g_pos", 2), ("g_rot", 1)):
+        flat = getattr(sc, name).reshape(-1)
+        h = 1e-7 if name != "g_scale" else 1e-5 * flat[k]
+        old = flat[k]
+        flat[k] = old + h
+        lp = float(np.sum(O.render(sc, cam, opts)["rgb"] * g))
+        flat[k] = old - h
+        lm = float(np.sum(O.render(sc, cam, opts)["rgb"] * g))
+        flat[k] = old
+        fd = (lp - lm) / (2 * h)
+        np.testing.assert_allclose(gr[name].reshape(-1)[k], fd, rtol=2e-6, atol=1e-10, err_msg=f"{name}[{k}]")
+    assert info["valid"] and min(info["S"]) > 2.0 and info["S"][1] > 1.5 * info["S"][0], info["S"]
