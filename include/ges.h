@@ -101,8 +101,8 @@ typedef struct ges_scene ges_scene;   /* opaque */
  *     with its planar depth and the object-space EWA filter of Eq. 17-18 (size
  *     lowpass: scales s_k S_k, opacity sigma/(S1 S2), S_k from the diagonal of
  *     I + lowpass J^-1 J^-T); eps_i = eps_factor/2 (s1 + s2).  The 3D filter
- *     and GES_FILTER_MIP do not apply to them; the backward pass and
- *     ges_render_noalloc return GES_ERR_UNSUPPORTED for them.
+ *     and GES_FILTER_MIP do not apply to them; ges_render_noalloc returns
+ *     GES_ERR_UNSUPPORTED for them.
  *   g_filter3d [M] float32 or NULL: Mip-GES 3D filter variance per Gaussian
  *     (Sec. 6.1, Mip-Splatting's world-space filter; see ges_compute_filter3d).
  *     Rendering uses Sigma3 + v I = R diag(s^2 + v) R^T and scales the opacity
@@ -148,9 +148,9 @@ typedef struct {
 } ges_render_opts;
 
 /* Gradient outputs (DEVICE pointers, float32, overwritten, not accumulated).
- * Shapes follow the inputs: g_pos [M,3], g_rot [M,4], g_scale [M,3],
- * g_opac [M], g_sh [M,K,3], s_sh [N,K,3].  Any pointer may be NULL to skip
- * that group. */
+ * Shapes follow the inputs: g_pos [M,3], g_rot [M,4], g_scale [M,3] ([M,2]
+ * for 2D Gaussians), g_opac [M], g_sh [M,K,3], s_sh [N,K,3].  Any pointer may
+ * be NULL to skip that group. */
 typedef struct {
     float *g_pos, *g_rot, *g_scale, *g_opac, *g_sh, *s_sh;
 } ges_grads;
@@ -289,7 +289,8 @@ GES_API ges_status ges_render_geom(ges_scene *scene, const ges_camera *cam, cons
 
 /* Gradients of L = sum(dL_drgb * C) for the joint stage (Sec. 4.2): Gaussian
  * position, rotation (through the normalisation), scale, opacity and SH, and
- * surfel SH.  out_rgb, out_depth, surfel_id and aux must be the outputs of a
+ * surfel SH.  For 2D Gaussians (Sec. 6.4) the chain runs through the
+ * ray-splat hit and the object-space filter factors S1, S2 of Eq. 17-18.  out_rgb, out_depth, surfel_id and aux must be the outputs of a
  * ges_render_ex call with the same scene arrays, camera and options.  The
  * depth-test indicator and the 1/255 clamp are piecewise constant and pass no
  * gradient.  Results are deterministic (no floating-point atomics). */

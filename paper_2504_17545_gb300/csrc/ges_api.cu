@@ -502,7 +502,6 @@ ges_status ges_render_backward(ges_scene *s, const ges_camera *cam, const ges_re
     if (!grads) return fail(GES_ERR_INVALID_ARG, "grads is NULL");
     if (!dL_drgb || !out_rgb || !out_depth || !surfel_id || !aux)
         return fail(GES_ERR_INVALID_ARG, "backward needs dL_drgb, out_rgb, out_depth, surfel_id and aux");
-    if (s->view.gdim == 2) return fail(GES_ERR_UNSUPPORTED, "the backward pass covers 3D Gaussians only");
     CamParams C;
     OptParams O;
     ges_status r = make_cam(cam, C);
@@ -516,8 +515,8 @@ ges_status ges_render_backward(ges_scene *s, const ges_camera *cam, const ges_re
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t pix_off = up((size_t)N * 3 * 8 + 16);
     const size_t rec_off = pix_off + up((size_t)C.W * C.H * 16);
-    const size_t sum_off = rec_off + up((size_t)M * 64);
-    const size_t chain_off = sum_off + up((size_t)M * 9 * 4);
+    const size_t sum_off = rec_off + up((size_t)M * kBwdRecBytes);
+    const size_t chain_off = sum_off + up((size_t)M * kBwdSums * 4);
     GES_CUDA(s->t_acc.ensure(chain_off + (size_t)M * kBwdChainWords * 4));
     unsigned char *base = (unsigned char *)s->t_acc.p;
     long long *acc = (long long *)base;

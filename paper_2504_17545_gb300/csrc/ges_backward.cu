@@ -24,6 +24,20 @@
 // then q -> (projected centre, conic) -> Sigma2 -> (Sigma3 -> s, r) and
 // (Jacobian, centre -> p), and c_i -> SH and p through the view direction.
 // Surfel s: dL/dc_s = sum over pixels won by s of k g, then SH.
+//
+// 2D Gaussians of 2D-GES (Sec. 6.4, Eq. 17-18) take the same three launches
+// with their own per-pixel term and chain rule.  At a pixel whose ray d meets
+// the splat plane at depth z = (N.t)/(N.d), X = z d - t = f1 a U + f2 b V
+// (t the camera-space centre, U, V, N the frame, f_k = s_k S_k the filtered
+// scales), alpha = sigma' exp(-(a^2 + b^2)/2), sigma' = sigma/(S1 S2).  With
+// rho' = dL/d(a^2 + b^2) = -alpha dL/dalpha / 2, every hit gradient is a
+// linear combination of seven moments, so the sweep sums those and the
+// chain kernel combines them (U.d/N.d = (a f1 + U.t)/(N.t), likewise V):
+//   sum rho' {a, b, a^2, ab, b^2, a r2, b r2},  r2 = a^2 + b^2,
+// kept in units of the support radius r (a = r a_n), with dc and
+// sum dL/dalpha alpha.  From the hit they pass through S1, S2 (functions of
+// the Jacobian J = Jp(t) [s1 U, s2 V]) to t, U, V and s, then to position and
+// rotation.
 #include "ges_internal.cuh"
 
 namespace ges {
@@ -89,6 +103,42 @@ __device__ __forceinline__ void gauss_pixel(const GLoop &s, int x, int y, const 
     acc[8] += dLdq * dy * dy;
 }
 
+// One pixel of one 2D Gaussian: the forward's alpha, clamp and depth test
+// from the disc record (r0..r2: forms of 1/z and of a/(r z), b/(r z) around
+// the reference pixel; r3.w = eps; cl: the clamped colour and log2 sigma';
+// side.w = log2(alpha_min / sigma')), then acc += dc(3), dL/dalpha alpha and
+// the seven moments of rho' (a_n = a/r, b_n = b/r).
+__device__ __forceinline__ void gauss2d_pixel(const float4 *q, int x, int y, const CamParams &C, const OptParams &O,
+                                              const float4 *__restrict__ P, const float *__restrict__ depth,
+                                              float *acc)
+{
+    const int64_t pix = (int64_t)y * C.W + x;
+    const float4 r0 = q[0], r1 = q[1], r2 = q[2], r3 = q[3], cl = q[4], side = q[5];
+    const float du = (x + 0.5f) - r0.x, dv = (y + 0.5f) - r0.y;
+    const float iz = fmaf(r0.w, du, fmaf(r1.x, dv, r0.z));
+    const float A = fmaf(r1.y, du, fmaf(r1.z, dv, r1.w));
+    const float Bq = fmaf(r2.x, du, fmaf(r2.y, dv, r2.z));
+    const float z = __frcp_rn(iz);
+    const float rho = fmaf(A, A, Bq * Bq) * (z * z);
+    const float a = ex2_approx(fmaf(side.w, rho, cl.w));
+    if (!(iz > 0.f && iz < C.izn && z - r3.w < __ldg(depth + pix))) return;
+    if (!(fminf(a * 4294967296.f, kAlpha32Max) >= O.alpha_min * 4294967296.f)) return;
+    const float4 p = __ldg(P + pix);
+    acc[0] += a * p.x;
+    acc[1] += a * p.y;
+    acc[2] += a * p.z;
+    const float dLda = fmaf(cl.x, p.x, fmaf(cl.y, p.y, cl.z * p.z)) - p.w;
+    acc[3] += dLda * a;
+    const float rp = -0.5f * dLda * a;
+    const float an = A * z, bn = Bq * z, r2n = fmaf(an, an, bn * bn);
+    acc[4] += rp * an;
+    acc[5] += rp * bn;
+    acc[6] += rp * an * an;
+    acc[7] += rp * an * bn;
+    acc[8] += rp * bn * bn;
+    acc[9] += rp * an * r2n;
+    acc[10] += rp * bn * r2n;
+}
 
 // Gaussian backward in three launches.  k_gbwd_rec sets every Gaussian up
 // with the forward's device function and stores its raster record (an empty
@@ -163,44 +213,146 @@ __global__ void __launch_bounds__(256) k_gbwd_rec(SceneView S, CamParams C, OptP
     chain_put(o, chain, S.M, gi);
 }
 
+// 2D Gaussians: what the chain rule needs, kChainWords2 words per Gaussian
+// in the same structure-of-arrays layout.
+constexpr int kChainWords2 = 30;
+static_assert(kChainWords2 <= kBwdChainWords, "chain words");
+__device__ __forceinline__ void chain2_put(const GaussOut &o, float *w, int64_t M, int64_t i)
+{
+    float v[kChainWords2];
+    int f = 0;
+    for (int k = 0; k < 9; ++k) v[f++] = o.R[k];
+    for (int k = 0; k < 4; ++k) v[f++] = o.qn[k];
+    v[f++] = o.qnorm;
+    v[f++] = o.s[0]; v[f++] = o.s[1];
+    v[f++] = o.S1; v[f++] = o.S2; v[f++] = o.rsup; v[f++] = o.sigma0;
+    v[f++] = o.tx; v[f++] = o.ty; v[f++] = o.tz;
+    for (int k = 0; k < 3; ++k) v[f++] = o.dir[k];
+    v[f++] = o.dist;
+    for (int k = 0; k < 3; ++k) v[f++] = o.raw[k];
+    for (int k = 0; k < kChainWords2; ++k) w[(int64_t)k * M + i] = v[k];
+}
+
+__global__ void __launch_bounds__(256) k_gbwd_rec2(SceneView S, CamParams C, OptParams O, float4 *__restrict__ rec,
+                                                  float *__restrict__ chain)
+{
+    const int64_t gi = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (gi >= S.M) return;
+    GaussOut o;
+    o.visible = false;
+    if (O.mode != GES_MODE_SURFELS_ONLY) gauss2d_setup(S, C, O, gi, o);
+    float4 *d = rec + 6 * gi;
+    if (!o.visible) {
+        d[3] = make_float4(0.f, __uint_as_float(1u), __uint_as_float(0u), 0.f);
+        return;
+    }
+    const SurfelRec &r = o.drec;
+    d[0] = make_float4(r.ur, r.vr, r.iz0, r.gu);
+    d[1] = make_float4(r.gv, r.au, r.av, r.a0);
+    d[2] = make_float4(r.bu, r.bv, r.b0, __int_as_float(r.id));
+    d[3] = make_float4(r.izmax, __uint_as_float(r.bb_lo), __uint_as_float(r.bb_hi), r.pad);
+    d[4] = o.aux[0];
+    d[5] = o.aux[1];
+    chain2_put(o, chain, S.M, gi);
+}
+
+// kG 3: 4-quarter EWA records, 9 sums; kG 2: 6-quarter disc records (the
+// record and its two side words), 11 sums.
+template <int kG>
 __global__ void __launch_bounds__(256, 4) k_gbwd_sweep(int64_t M, CamParams C, OptParams O,
                                                       const float4 *__restrict__ rec, const float4 *__restrict__ P,
                                                       const float *__restrict__ depth, float *__restrict__ sums)
 {
+    constexpr int kQ = kG == 2 ? 6 : 4, kNV = kG == 2 ? 11 : 9;
     const int64_t gi = (int64_t)blockIdx.x * 256 + threadIdx.x;
     const int64_t g0 = gi - (threadIdx.x & 31);      // the warp's first Gaussian
     const int lane = threadIdx.x & 31;
     bool vis = false;
     if (gi < M) {
-        const float4 r3 = __ldg(rec + 4 * gi + 3);
+        const float4 r3 = __ldg(rec + kQ * gi + 3);
         const unsigned lo = __float_as_uint(r3.y), hi = __float_as_uint(r3.z);
         vis = (lo & 0xffff) <= (hi & 0xffff) && (lo >> 16) <= (hi >> 16);
     }
     if (gi < M && !vis)
-        for (int c = 0; c < 9; ++c) sums[(int64_t)c * M + gi] = 0.f;
+        for (int c = 0; c < kNV; ++c) sums[(int64_t)c * M + gi] = 0.f;
     unsigned big = __ballot_sync(0xffffffffu, vis);
     while (big) {
         const int j = __ffs(big) - 1;
         big &= big - 1;
         // Gaussian g0 + j: every lane reads the same record (a broadcast, from L1)
-        const float4 *rj = rec + 4 * (g0 + j);
-        const float4 r0 = __ldg(rj), r1 = __ldg(rj + 1), r2 = __ldg(rj + 2), r3 = __ldg(rj + 3);
+        const float4 *rj = rec + kQ * (g0 + j);
+        float4 q[kQ];
+#pragma unroll
+        for (int k = 0; k < kQ; ++k) q[k] = __ldg(rj + k);
+        const unsigned lo = __float_as_uint(q[3].y), hi = __float_as_uint(q[3].z);
+        const int x0 = lo & 0xffff, y0 = lo >> 16, x1 = hi & 0xffff, y1 = hi >> 16;
         GLoop t;
-        t.px = r0.x; t.py = r0.y; t.pxl = r0.z; t.pyl = r0.w;
-        t.la = r1.x; t.lb = r1.y; t.lc = r1.z; t.sigma = r1.w;
-        t.key = r2.x; t.r = r2.y; t.g = r2.z; t.b = r2.w;
-        const unsigned lo = __float_as_uint(r3.y), hi = __float_as_uint(r3.z);
-        t.x0 = lo & 0xffff; t.y0 = lo >> 16; t.x1 = hi & 0xffff; t.y1 = hi >> 16;
-        const int w = t.x1 - t.x0 + 1, n = w * (t.y1 - t.y0 + 1);
-        float part[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        if (kG == 3) {
+            t.px = q[0].x; t.py = q[0].y; t.pxl = q[0].z; t.pyl = q[0].w;
+            t.la = q[1].x; t.lb = q[1].y; t.lc = q[1].z; t.sigma = q[1].w;
+            t.key = q[2].x; t.r = q[2].y; t.g = q[2].z; t.b = q[2].w;
+            t.x0 = x0; t.y0 = y0; t.x1 = x1; t.y1 = y1;
+        }
+        const int w = x1 - x0 + 1, n = w * (y1 - y0 + 1);
+        float part[kNV];
+#pragma unroll
+        for (int c = 0; c < kNV; ++c) part[c] = 0.f;
         // pixel k of the bbox, row-major (no integer division per pixel)
         const float iw = 1.f / (float)w;
         for (int k = lane; k < n; k += 32) {
             const int r = bbox_row(k, w, iw);
-            gauss_pixel(t, t.x0 + (k - r * w), t.y0 + r, C, O, P, depth, part);
+            if (kG == 2) gauss2d_pixel(q, x0 + (k - r * w), y0 + r, C, O, P, depth, part);
+            else gauss_pixel(t, x0 + (k - r * w), y0 + r, C, O, P, depth, part);
         }
         float *dst = sums + g0 + j;
-        warp_reduce_scatter<9>(part, lane, [&](int c, float tot) { dst[(int64_t)c * M] = tot; });
+        warp_reduce_scatter<kNV>(part, lane, [&](int c, float tot) { dst[(int64_t)c * M] = tot; });
+    }
+}
+
+// Colour -> SH coefficients (stored) and position through the view direction
+// (added to gp).
+__device__ __forceinline__ void colour_grad(const SceneView &S, int64_t gi, int K, const GaussOut &o,
+                                            const float *dc, const ges_grads &G, float *gp)
+{
+    float Y[16];
+    sh_basis(K, o.dir[0], o.dir[1], o.dir[2], Y);
+    float gc[3];
+    for (int c = 0; c < 3; ++c) gc[c] = o.raw[c] > 0.f ? dc[c] : 0.f;
+    float gd[3] = {0.f, 0.f, 0.f};
+    switch (K) {
+    case 16: sh_weighted_grad<16>(S.g_sh, gi, S.sh_dtype, gc, o.dir, gd); break;
+    case 9: sh_weighted_grad<9>(S.g_sh, gi, S.sh_dtype, gc, o.dir, gd); break;
+    case 4: sh_weighted_grad<4>(S.g_sh, gi, S.sh_dtype, gc, o.dir, gd); break;
+    default: break;   // degree 0: the colour does not depend on the direction
+    }
+    if (G.g_sh) store_sh_grad(G.g_sh + 3 * K * gi, K, Y, gc, nullptr);
+    if (o.dist > 0.f) {
+        const float pr = gd[0] * o.dir[0] + gd[1] * o.dir[1] + gd[2] * o.dir[2];
+        for (int a = 0; a < 3; ++a) gp[a] -= (gd[a] - pr * o.dir[a]) / o.dist;
+    }
+}
+
+// dL/dR (GR[a][b] = dL/dR_ab) -> R(qhat) -> qhat -> q (through the
+// normalisation), stored as the four floats of g_rot[gi].
+__device__ __forceinline__ void rot_grad(const float (*GR)[3], const GaussOut &o, float *g_rot, int64_t gi)
+{
+    const float w = o.qn[0], qx = o.qn[1], qy = o.qn[2], qz = o.qn[3];
+    float gq[4];
+    gq[0] = 2.f * (-qz * GR[0][1] + qy * GR[0][2] + qz * GR[1][0] - qx * GR[1][2] - qy * GR[2][0] + qx * GR[2][1]);
+    gq[1] = 2.f * (qy * GR[0][1] + qz * GR[0][2] + qy * GR[1][0] - 2.f * qx * GR[1][1] - w * GR[1][2] +
+                   qz * GR[2][0] + w * GR[2][1] - 2.f * qx * GR[2][2]);
+    gq[2] = 2.f * (-2.f * qy * GR[0][0] + qx * GR[0][1] + w * GR[0][2] + qx * GR[1][0] + qz * GR[1][2] -
+                   w * GR[2][0] + qz * GR[2][1] - 2.f * qy * GR[2][2]);
+    gq[3] = 2.f * (-2.f * qz * GR[0][0] - w * GR[0][1] + qx * GR[0][2] + w * GR[1][0] - 2.f * qz * GR[1][1] +
+                   qy * GR[1][2] + qx * GR[2][0] + qy * GR[2][1]);
+    const float pr = gq[0] * w + gq[1] * qx + gq[2] * qy + gq[3] * qz;
+    const float4 r4 = make_float4((gq[0] - pr * o.qn[0]) / o.qnorm, (gq[1] - pr * o.qn[1]) / o.qnorm,
+                                  (gq[2] - pr * o.qn[2]) / o.qnorm, (gq[3] - pr * o.qn[3]) / o.qnorm);
+    if ((reinterpret_cast<uintptr_t>(g_rot) & 15u) == 0) {
+        reinterpret_cast<float4 *>(g_rot)[gi] = r4;
+    } else {
+        g_rot[4 * gi] = r4.x; g_rot[4 * gi + 1] = r4.y;
+        g_rot[4 * gi + 2] = r4.z; g_rot[4 * gi + 3] = r4.w;
     }
 }
 
@@ -233,25 +385,7 @@ __global__ void __launch_bounds__(256, 3) k_gbwd_chain(SceneView S, CamParams C,
     for (int c = 0; c < 9; ++c) my[c] = sums[(int64_t)c * S.M + gi];
     const float *dc = my;
     float gp[3] = {0.f, 0.f, 0.f};
-    // colour -> SH coefficients and position (through the view direction)
-    {
-        float Y[16];
-        sh_basis(K, o.dir[0], o.dir[1], o.dir[2], Y);
-        float gc[3];
-        for (int c = 0; c < 3; ++c) gc[c] = o.raw[c] > 0.f ? dc[c] : 0.f;
-        float gd[3] = {0.f, 0.f, 0.f};
-        switch (K) {
-        case 16: sh_weighted_grad<16>(S.g_sh, gi, S.sh_dtype, gc, o.dir, gd); break;
-        case 9: sh_weighted_grad<9>(S.g_sh, gi, S.sh_dtype, gc, o.dir, gd); break;
-        case 4: sh_weighted_grad<4>(S.g_sh, gi, S.sh_dtype, gc, o.dir, gd); break;
-        default: break;   // degree 0: the colour does not depend on the direction
-        }
-        if (G.g_sh) store_sh_grad(G.g_sh + 3 * K * gi, K, Y, gc, nullptr);
-        if (o.dist > 0.f) {
-            const float pr = gd[0] * o.dir[0] + gd[1] * o.dir[1] + gd[2] * o.dir[2];
-            for (int a = 0; a < 3; ++a) gp[a] -= (gd[a] - pr * o.dir[a]) / o.dist;
-        }
-    }
+    colour_grad(S, gi, K, o, dc, G, gp);
     // my[3] is dL/dsigma with sigma = sigma0 k3 k2 (the Mip-GES factors, 1 without them)
     if (G.g_opac) G.g_opac[gi] = my[3] * o.k3 * o.k2;
     // conic Q = Sigma2^-1:  dL/dSigma2 = -Q GQ Q with GQ = [[dia, dib/2], [dib/2, dic]]
@@ -329,27 +463,121 @@ __global__ void __launch_bounds__(256, 3) k_gbwd_chain(SceneView S, CamParams C,
         }
     }
     if (G.g_scale) for (int b = 0; b < 3; ++b) G.g_scale[3 * gi + b] = gsc[b];
-    // R(qhat) -> qhat -> q (through the normalisation)
-    const float w = o.qn[0], qx = o.qn[1], qy = o.qn[2], qz = o.qn[3];
-    float gq[4];
-    gq[0] = 2.f * (-qz * GR[0][1] + qy * GR[0][2] + qz * GR[1][0] - qx * GR[1][2] - qy * GR[2][0] + qx * GR[2][1]);
-    gq[1] = 2.f * (qy * GR[0][1] + qz * GR[0][2] + qy * GR[1][0] - 2.f * qx * GR[1][1] - w * GR[1][2] +
-                   qz * GR[2][0] + w * GR[2][1] - 2.f * qx * GR[2][2]);
-    gq[2] = 2.f * (-2.f * qy * GR[0][0] + qx * GR[0][1] + w * GR[0][2] + qx * GR[1][0] + qz * GR[1][2] -
-                   w * GR[2][0] + qz * GR[2][1] - 2.f * qy * GR[2][2]);
-    gq[3] = 2.f * (-2.f * qz * GR[0][0] - w * GR[0][1] + qx * GR[0][2] + w * GR[1][0] - 2.f * qz * GR[1][1] +
-                   qy * GR[1][2] + qx * GR[2][0] + qy * GR[2][1]);
-    const float pr = gq[0] * w + gq[1] * qx + gq[2] * qy + gq[3] * qz;
-    if (G.g_rot) {
-        const float4 r4 = make_float4((gq[0] - pr * o.qn[0]) / o.qnorm, (gq[1] - pr * o.qn[1]) / o.qnorm,
-                                      (gq[2] - pr * o.qn[2]) / o.qnorm, (gq[3] - pr * o.qn[3]) / o.qnorm);
-        if ((reinterpret_cast<uintptr_t>(G.g_rot) & 15u) == 0) {
-            reinterpret_cast<float4 *>(G.g_rot)[gi] = r4;
-        } else {
-            G.g_rot[4 * gi] = r4.x; G.g_rot[4 * gi + 1] = r4.y;
-            G.g_rot[4 * gi + 2] = r4.z; G.g_rot[4 * gi + 3] = r4.w;
-        }
+    if (G.g_rot) rot_grad(GR, o, G.g_rot, gi);
+}
+
+// 2D Gaussians: the chain rule from the 11 sums of the sweep (dc, dL/dalpha
+// alpha, the seven moments of rho') and the kept set-up words.
+__global__ void __launch_bounds__(256, 3) k_gbwd_chain2(SceneView S, CamParams C, OptParams O,
+                                                    const float *__restrict__ sums,
+                                                    const float *__restrict__ chain, ges_grads G)
+{
+    const int64_t gi = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (gi >= S.M) return;
+    const int K = (S.deg + 1) * (S.deg + 1);
+    float my[11];
+    unsigned bits = 0u;
+    for (int c = 0; c < 11; ++c) {
+        my[c] = __ldg(sums + (int64_t)c * S.M + gi);
+        bits |= __float_as_uint(my[c]) & 0x7fffffffu;
     }
+    if (bits == 0u || O.mode == GES_MODE_SURFELS_ONLY) {
+        if (G.g_pos) for (int a = 0; a < 3; ++a) G.g_pos[3 * gi + a] = 0.f;
+        if (G.g_rot) for (int a = 0; a < 4; ++a) G.g_rot[4 * gi + a] = 0.f;
+        if (G.g_scale) for (int a = 0; a < 2; ++a) G.g_scale[2 * gi + a] = 0.f;
+        if (G.g_opac) G.g_opac[gi] = 0.f;
+        if (G.g_sh) store_zeros(G.g_sh + 3 * K * gi, 3 * K);
+        return;
+    }
+    GaussOut o;
+    float v[kChainWords2];
+    for (int k = 0; k < kChainWords2; ++k) v[k] = __ldg(chain + (int64_t)k * S.M + gi);
+    int f = 0;
+    for (int k = 0; k < 9; ++k) o.R[k] = v[f++];
+    for (int k = 0; k < 4; ++k) o.qn[k] = v[f++];
+    o.qnorm = v[f++];
+    const float s0 = v[f++], s1 = v[f++];
+    const float S1 = v[f++], S2 = v[f++], r = v[f++], sigma0 = v[f++];
+    const float x = v[f++], y = v[f++], z = v[f++];
+    for (int k = 0; k < 3; ++k) o.dir[k] = v[f++];
+    o.dist = v[f++];
+    for (int k = 0; k < 3; ++k) o.raw[k] = v[f++];
+
+    float gp[3] = {0.f, 0.f, 0.f};
+    colour_grad(S, gi, K, o, my, G, gp);
+    // sigma' = sigma0 / (S1 S2): dalpha/dsigma' = alpha / sigma'
+    const float sigp = sigma0 / (S1 * S2);
+    const float dsig = my[3] / sigp;
+    if (G.g_opac) G.g_opac[gi] = dsig / (S1 * S2);
+    // moments in filtered units (a = r a_n)
+    const float r2 = r * r, r3 = r2 * r;
+    const float Sa = r * my[4], Sb = r * my[5], Saa = r2 * my[6], Sab = r2 * my[7], Sbb = r2 * my[8];
+    const float Sar = r3 * my[9], Sbr = r3 * my[10];
+    // camera-space frame, as the set-up forms it
+    float U[3], V[3], N[3];
+    for (int q = 0; q < 3; ++q) {
+        U[q] = C.R[3 * q] * o.R[0] + C.R[3 * q + 1] * o.R[3] + C.R[3 * q + 2] * o.R[6];
+        V[q] = C.R[3 * q] * o.R[1] + C.R[3 * q + 1] * o.R[4] + C.R[3 * q + 2] * o.R[7];
+        N[q] = C.R[3 * q] * o.R[2] + C.R[3 * q + 1] * o.R[5] + C.R[3 * q + 2] * o.R[8];
+    }
+    const float f1 = s0 * S1, f2 = s1 * S2;
+    const float Ut = U[0] * x + U[1] * y + U[2] * z, Vt = V[0] * x + V[1] * y + V[2] * z;
+    const float Nt = N[0] * x + N[1] * y + N[2] * z;
+    const float cu = Ut / f1, cv = Vt / f2, k2 = 2.f / Nt;
+    // sums of w = 2 rho' (a U.d/f1 + b V.d/f2) / N.d, and of w a, w b
+    const float Sw = k2 * (Saa + Sbb + cu * Sa + cv * Sb);
+    const float Swa = k2 * (Sar + cu * Saa + cv * Sab);
+    const float Swb = k2 * (Sbr + cu * Sab + cv * Sbb);
+    float gt[3], gU[3], gV[3], gN[3];
+    for (int q = 0; q < 3; ++q) {
+        gt[q] = N[q] * Sw - U[q] * (2.f * Sa / f1) - V[q] * (2.f * Sb / f2);
+        gU[q] = 2.f * (Saa * U[q] + (f2 / f1) * Sab * V[q]);
+        gV[q] = 2.f * ((f1 / f2) * Sab * U[q] + Sbb * V[q]);
+        gN[q] = -(f1 * Swa * U[q] + f2 * Swb * V[q]);
+    }
+    const float gf1 = -2.f * Saa / f1, gf2 = -2.f * Sbb / f2;
+    // f_k = s_k S_k and sigma' = sigma0 / (S1 S2)
+    const float gS1 = gf1 * s0 - dsig * sigp / S1, gS2 = gf2 * s1 - dsig * sigp / S2;
+    float gs0 = gf1 * S1, gs1 = gf2 * S2;
+    // S1^2 = 1 + lowpass M11/det, S2^2 = 1 + lowpass M00/det with M = J^T J,
+    // J = Jp(t) [s1 U, s2 V]; in the ratios p1 = M11/det, p2 = M00/det, m = M01/det
+    const float iz = 1.f / z;
+    const float j00 = C.fx * iz, j02 = -C.fx * x * iz * iz, j11 = C.fy * iz, j12 = -C.fy * y * iz * iz;
+    const float JU0 = j00 * U[0] + j02 * U[2], JU1 = j11 * U[1] + j12 * U[2];
+    const float JV0 = j00 * V[0] + j02 * V[2], JV1 = j11 * V[1] + j12 * V[2];
+    const float J00 = s0 * JU0, J01 = s1 * JV0, J10 = s0 * JU1, J11 = s1 * JV1;
+    const float dJ = J00 * J11 - J01 * J10;
+    const float idet = 1.f / (dJ * dJ);
+    const float M00 = J00 * J00 + J10 * J10, M11 = J01 * J01 + J11 * J11, M01 = J00 * J01 + J10 * J11;
+    const float p1 = M11 * idet, p2 = M00 * idet, m = M01 * idet;
+    const float h1 = gS1 * O.lowpass / (2.f * S1), h2 = gS2 * O.lowpass / (2.f * S2);
+    const float gM00 = -h1 * p1 * p1 - h2 * m * m;
+    const float gM11 = -h1 * m * m - h2 * p2 * p2;
+    const float gM01 = 2.f * m * (h1 * p1 + h2 * p2);
+    const float gJ00 = 2.f * J00 * gM00 + J01 * gM01, gJ10 = 2.f * J10 * gM00 + J11 * gM01;
+    const float gJ01 = J00 * gM01 + 2.f * J01 * gM11, gJ11 = J10 * gM01 + 2.f * J11 * gM11;
+    gs0 += gJ00 * JU0 + gJ10 * JU1;
+    gs1 += gJ01 * JV0 + gJ11 * JV1;
+    gU[0] += s0 * gJ00 * j00; gU[1] += s0 * gJ10 * j11; gU[2] += s0 * (gJ00 * j02 + gJ10 * j12);
+    gV[0] += s1 * gJ01 * j00; gV[1] += s1 * gJ11 * j11; gV[2] += s1 * (gJ01 * j02 + gJ11 * j12);
+    // Jp(t) -> t: dL/dJp row a = s1 gJ_a0 U + s2 gJ_a1 V (the non-zero entries)
+    const float gj00 = s0 * gJ00 * U[0] + s1 * gJ01 * V[0], gj02 = s0 * gJ00 * U[2] + s1 * gJ01 * V[2];
+    const float gj11 = s0 * gJ10 * U[1] + s1 * gJ11 * V[1], gj12 = s0 * gJ10 * U[2] + s1 * gJ11 * V[2];
+    gt[0] += gj02 * (-C.fx * iz * iz);
+    gt[1] += gj12 * (-C.fy * iz * iz);
+    gt[2] += gj00 * (-C.fx * iz * iz) + gj02 * (2.f * C.fx * x * iz * iz * iz) + gj11 * (-C.fy * iz * iz) +
+             gj12 * (2.f * C.fy * y * iz * iz * iz);
+    if (G.g_scale) { G.g_scale[2 * gi] = gs0; G.g_scale[2 * gi + 1] = gs1; }
+    // t = Rc p + tc; U, V, N = Rc R e_k: world gradients through Rc^T
+    float GR[3][3];
+    for (int a = 0; a < 3; ++a) {
+        gp[a] += C.R[a] * gt[0] + C.R[3 + a] * gt[1] + C.R[6 + a] * gt[2];
+        GR[a][0] = C.R[a] * gU[0] + C.R[3 + a] * gU[1] + C.R[6 + a] * gU[2];
+        GR[a][1] = C.R[a] * gV[0] + C.R[3 + a] * gV[1] + C.R[6 + a] * gV[2];
+        GR[a][2] = C.R[a] * gN[0] + C.R[3 + a] * gN[1] + C.R[6 + a] * gN[2];
+    }
+    if (G.g_pos) for (int a = 0; a < 3; ++a) G.g_pos[3 * gi + a] = gp[a];
+    if (G.g_rot) rot_grad(GR, o, G.g_rot, gi);
 }
 
 // largest |x| (non-negative floats order like their bit patterns)
@@ -449,9 +677,15 @@ cudaError_t launch_backward(const SceneView &S, const CamParams &C, const OptPar
         k_pixgrad<<<(unsigned)((HW + 255) / 256), 256, 0, st>>>(HW, O.mode == GES_MODE_GAUSSIANS_ONLY, dL_drgb,
                                                                 out_rgb, aux, pixg);
         const unsigned nb = (unsigned)((S.M + 255) / 256);
-        k_gbwd_rec<<<nb, 256, 0, st>>>(S, C, O, g_rec, g_chain);
-        k_gbwd_sweep<<<nb, 256, 0, st>>>(S.M, C, O, g_rec, pixg, out_depth, g_sums);
-        k_gbwd_chain<<<nb, 256, 0, st>>>(S, C, O, g_sums, g_chain, G);
+        if (S.gdim == 2) {
+            k_gbwd_rec2<<<nb, 256, 0, st>>>(S, C, O, g_rec, g_chain);
+            k_gbwd_sweep<2><<<nb, 256, 0, st>>>(S.M, C, O, g_rec, pixg, out_depth, g_sums);
+            k_gbwd_chain2<<<nb, 256, 0, st>>>(S, C, O, g_sums, g_chain, G);
+        } else {
+            k_gbwd_rec<<<nb, 256, 0, st>>>(S, C, O, g_rec, g_chain);
+            k_gbwd_sweep<3><<<nb, 256, 0, st>>>(S.M, C, O, g_rec, pixg, out_depth, g_sums);
+            k_gbwd_chain<<<nb, 256, 0, st>>>(S, C, O, g_sums, g_chain, G);
+        }
     }
     if (ev) cudaEventRecord(ev[1], st);
     if (S.N > 0 && G.s_sh) {

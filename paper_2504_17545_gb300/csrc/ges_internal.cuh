@@ -177,9 +177,11 @@ cudaError_t launch_filter3d(const SceneView &S, const CamParams *d_cams, int n_c
 
 // Scratch: s_acc 3 N 64-bit words (surfel colour sums), gmax one word,
 // pixg H W float4 (per-pixel terms of the Gaussian gradients), g_rec M
-// 64-byte records, g_sums 9 M floats (per-Gaussian sums of the sweep),
-// g_chain kBwdChainWords M floats (what the chain rule needs of each set-up).
-constexpr int kBwdChainWords = 40;
+// records of kBwdRecBytes, g_sums kBwdSums M floats (per-Gaussian sums of the
+// sweep), g_chain kBwdChainWords M floats (what the chain rule needs of each
+// set-up).  The sizes cover both Gaussian kinds (3D: 64-byte records, 9 sums;
+// 2D: 96-byte records, 11 sums).
+constexpr int kBwdChainWords = 40, kBwdRecBytes = 96, kBwdSums = 11;
 cudaError_t launch_backward(const SceneView &S, const CamParams &C, const OptParams &O, const float *dL_drgb,
                             const float *out_rgb, const float *out_depth, const int32_t *surfel_id,
                             const float *aux, const ges_grads &G, long long *s_acc, unsigned *gmax,
@@ -748,6 +750,9 @@ struct GaussOut {
     // instead of rec; both kinds: side data for g_aux
     SurfelRec drec;
     float4 aux[2];
+    // 2D Gaussians, for the backward pass: object-space filter factors S1, S2
+    // and the support radius in filtered units (tx, ty, tz: the centre)
+    float S1, S2, rsup;
 };
 
 // Per-Gaussian set-up (Eq. 4: projected covariance and centre; 1/255 clamp
@@ -940,6 +945,8 @@ __device__ __forceinline__ void gauss2d_setup(const SceneView &S, const CamParam
     if (!(sigp >= O.alpha_min)) return;
     const float r = sqrtf(2.f * logf(sigp / O.alpha_min));
     if (!(r > 0.f)) return;
+    o.tx = x; o.ty = y; o.tz = z;
+    o.S1 = S1; o.S2 = S2; o.rsup = r;
     DiscOut d;
     if (!disc_setup(C, P, tu, tv, n, s0 * S1, s1 * S2, r, 0.f, (int)i, d)) return;
     float eps;

@@ -254,13 +254,14 @@ def contribution_scores(scene: GESScene, cam, fwd: dict, opts: Optional[dict] = 
 
 
 def render_backward(scene: GESScene, cam, fwd: dict, dL_drgb: torch.Tensor, opts: Optional[dict] = None):
-    """Gradients of sum(dL_drgb * C) (Sec. 4.2); returns a dict of float32 tensors."""
+    """Gradients of sum(dL_drgb * C) (Sec. 4.2); returns a dict of float32
+    tensors (g_scale [M,2] for the 2D Gaussians of 2D-GES)."""
     c = camera_struct(cam)
     dev = scene.t["s_pos"].device
     g = {
         "g_pos": torch.empty((scene.n_gaussians, 3), device=dev),
         "g_rot": torch.empty((scene.n_gaussians, 4), device=dev),
-        "g_scale": torch.empty((scene.n_gaussians, 3), device=dev),
+        "g_scale": torch.empty((scene.n_gaussians, scene.gauss_dim), device=dev),
         "g_opac": torch.empty((scene.n_gaussians,), device=dev),
         "g_sh": torch.empty(tuple(scene.t["g_sh"].shape), device=dev),
         "s_sh": torch.empty(tuple(scene.t["s_sh"].shape), device=dev),

@@ -150,15 +150,3 @@ def test_2d_batch_graph_equals_single_views(R):
     ga.close()
     gb.close()
     g3.close()
-
-
-def test_2d_backward_is_unsupported(R):
-    torch = pytest.importorskip("torch")
-    from paper_2504_17545_gb300 import native as N
-    scene, cam = sg.crop_scene(7)
-    gs = R.GESScene.from_arrays(_flat(scene))
-    fwd = R.render(gs, cam)
-    with pytest.raises(N.GesError) as ei:
-        R.render_backward(gs, cam, fwd, torch.ones_like(fwd["rgb"]))
-    assert ei.value.status == N.GES_ERR_UNSUPPORTED
-    gs.close()
