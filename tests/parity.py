@@ -31,9 +31,11 @@ DEPTH_GRAZE = 4e-7
 
 # Bound on the fraction of pixels the oracle flags as ambiguous (excluded from
 # the comparison): a parity test that masks more than this compares too
-# little to count.  The workloads' own fractions are well below it (0.1-0.7 %
-# at 1080p); the small hand-built scenes that aim at ties and grazing discs
-# pass their own bound.
+# little to count.  With the bands derived from the float32 error model the
+# 1080p orbit views flag 0.9-1.6 % (mostly neighbouring surfels of one
+# surface whose fragment depths agree within 3.5e-6); the small hand-built
+# scenes that aim at ties and grazing discs, and the cameras inside the
+# scene, pass their own bounds.
 MASKED_MAX = 0.02
 
 

@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 import scenegen as sg
-from parity import compare
+from parity import MASKED_MAX, compare
 from test_gpu_backward import _check, _grads_gpu
 from test_gpu_forward import _render, _small
 
@@ -116,7 +116,7 @@ def test_mip_parity_1080p_orbit_camera(R):
         ref = oracle.render(scene, cams[k], MIP)
         res = compare(scene, cams[k], R.render(gs, cams[k], MIP), ref, MIP)
         _assert(res)
-        assert res["masked_frac"] < 0.01
+        assert res["masked_frac"] <= MASKED_MAX
     gs.close()
 
 
