@@ -73,6 +73,8 @@ typedef struct {
                                scaled by sqrt(|Sigma2| / |Sigma2 + lowpass I|) (Sec. 6.1) */
     double tol_disc_graze;   /* rim band at a fragment whose ray meets the disc at cosine c:
                                 tol_disc_rel (1 + tol_disc_graze / max(|c|, tol_graze)) */
+    double tol_centre_rel;   /* translucent blend order: two surfel centres' camera depths
+                                closer than this (relative) may be ordered either way */
 } ora_opts;
 
 enum { ORA_OK = 0, ORA_BAD_ARG = 1, ORA_BAD_QUAT = 2, ORA_NOMEM = 3 };
@@ -1442,7 +1444,7 @@ static int64_t tcollect(const ora_scene *S, const ora_camera *c, const ora_opts 
     }
     qsort(*list, (size_t)n, sizeof(tcontrib), tcontrib_cmp);
     for (int64_t k = 1; k < n; ++k)
-        if ((*list)[k].zc - (*list)[k - 1].zc <= o->tol_depth_rel * fabs((*list)[k].zc)) *amb |= AMB_COLOR;
+        if ((*list)[k].zc - (*list)[k - 1].zc <= o->tol_centre_rel * fabs((*list)[k].zc)) *amb |= AMB_COLOR;
     if (front_first && n > 1) {
         int64_t f = 0;
         for (int64_t k = 1; k < n; ++k)

@@ -37,10 +37,14 @@ _lib = None
 #   tol_alpha  alpha at the 1/255 cut: q = y0^2 + y1^2 within 26u relative,
 #       alpha within 9e-6 relative, 3.4e-8 absolute at the cut (1e-5 taken)
 #   tol_graze  |cos| below which a fragment is grazing outright
+#   tol_centre_rel  the translucent render's blend order: a centre's camera
+#       depth is the double-float transform rounded once (within u of the
+#       exact value), and rounding keeps order, so two centres can only swap
+#       into a tie when they lie within 2u = 1.2e-7 of each other
 DEFAULT_OPTS = dict(eps_mode=0, eps_value=0.1, eps_factor=5.0, lowpass=0.3,
                     alpha_min=1.0 / 255.0, surfel_r2=2.0 * math.log(255.0), mode=0,
                     tol_depth_rel=3.5e-6, tol_disc_rel=1e-5, tol_graze=1e-3, tol_alpha=1e-5,
-                    tol_gdepth_rel=2e-6, samples=1, filter=0, tol_disc_graze=0.25)
+                    tol_gdepth_rel=2e-6, samples=1, filter=0, tol_disc_graze=0.25, tol_centre_rel=1.2e-7)
 
 
 class _Scene(C.Structure):
@@ -61,7 +65,8 @@ class _Opts(C.Structure):
                 ("lowpass", C.c_double), ("alpha_min", C.c_double), ("surfel_r2", C.c_double),
                 ("mode", C.c_int32), ("tol_depth_rel", C.c_double), ("tol_disc_rel", C.c_double),
                 ("tol_graze", C.c_double), ("tol_alpha", C.c_double), ("tol_gdepth_rel", C.c_double),
-                ("samples", C.c_int32), ("filter", C.c_int32), ("tol_disc_graze", C.c_double)]
+                ("samples", C.c_int32), ("filter", C.c_int32), ("tol_disc_graze", C.c_double),
+                ("tol_centre_rel", C.c_double)]
 
 
 def build(force: bool = False) -> str:

@@ -251,7 +251,9 @@ __global__ void __launch_bounds__(256) k_gbwd_rec2(SceneView S, CamParams C, Opt
     d[1] = make_float4(r.gv, r.au, r.av, r.a0);
     d[2] = make_float4(r.bu, r.bv, r.b0, __int_as_float(r.id));
     d[3] = make_float4(r.izmax, __uint_as_float(r.bb_lo), __uint_as_float(r.bb_hi), r.pad);
-    d[4] = o.aux[0];
+    // float colours (the forward record carries them in 2^-16 units)
+    d[4] = make_float4(fminf(o.rgb[0], kColourMax), fminf(o.rgb[1], kColourMax), fminf(o.rgb[2], kColourMax),
+                       o.aux[0].w);
     d[5] = o.aux[1];
     chain2_put(o, chain, S.M, gi);
 }

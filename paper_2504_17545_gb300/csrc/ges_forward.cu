@@ -128,7 +128,7 @@ __device__ __forceinline__ bool setup_and_store(const SceneView &S, const CamPar
             dst[3] = make_float4(__int_as_float(o.rec.id), __uint_as_float(o.rec.bb_lo),
                                  __uint_as_float(o.rec.bb_hi), o.rec.pad);
             gauss_colour(S, i, o);
-            dst[2] = make_float4(o.rec.key, o.rec.r, o.rec.g, o.rec.b);
+            dst[2] = make_float4(o.rec.key, colour_q(o.rec.r), colour_q(o.rec.g), colour_q(o.rec.b));
         }
         if (kGd == 2 || O.geo) {
             X.g_aux[2 * i] = o.aux[0];
@@ -565,7 +565,16 @@ __device__ __forceinline__ void surfel_resolve(const SurfelZ<kS> &z, bool in_img
     }
 }
 
-// Pass 2 sums of one lane, in 64-bit fixed point (units of 2^-32).
+// alpha 2^32 (an exact integer below 2^34) times a record colour (2^-16
+// units, below 2^25): the exact product, units of 2^-48.
+__device__ __forceinline__ unsigned long long mul_q(long long A, unsigned c)
+{
+    const unsigned lo = (unsigned)A, hi = (unsigned)((unsigned long long)A >> 32);
+    return (unsigned long long)lo * c + ((unsigned long long)(hi * c) << 32);
+}
+
+// Pass 2 sums of one lane, in 64-bit fixed point: W_G and the geometry sums
+// in units of 2^-32, the colour sums in units of 2^-48.
 struct GaussAcc {
     long long r = 0, g = 0, b = 0, w = 0;
     long long d = 0, nx = 0, ny = 0, nz = 0;   // D_G, N_G (geometry maps)
@@ -592,7 +601,8 @@ __device__ __forceinline__ void gauss_pass(const Recs &R, int n, const WarpBlock
         while (mask) {
             const int jj = j0 + __ffs(mask) - 1;
             mask &= mask - 1;
-            float a, depth, cr, cg, cb, ok;
+            float a, depth, ok;
+            unsigned cr, cg, cb;   // record colours, 2^-16 units
             float4 side = make_float4(0.f, 0.f, 0.f, 0.f);
             if (kG == 2) {
                 const float4 r0 = R(0, jj), r1 = R(1, jj), r2 = R(2, jj);
@@ -606,23 +616,25 @@ __device__ __forceinline__ void gauss_pass(const Recs &R, int n, const WarpBlock
                 // rho = (a'^2 + b'^2)/r^2; alpha = 2^(log2 sigma' + log2(alpha_min/sigma') rho)
                 const float rho = fmaf(A, A, Bq * Bq) * (depth * depth);
                 a = ex2_approx(fmaf(side.w, rho, x0.w));
-                cr = x0.x; cg = x0.y; cb = x0.z;
+                cr = __float_as_uint(x0.x); cg = __float_as_uint(x0.y); cb = __float_as_uint(x0.z);
                 ok = (iz > 0.f && iz < izn && depth - R(3, jj).w < Ds) ? 1.f : 0.f;
             } else {
                 const GaussRec g = gauss_rec3(R(0, jj), R(1, jj), R(2, jj));
                 float e;
                 a = gauss_alpha(g, B.u, B.v, e);
-                cr = g.r; cg = g.g; cb = g.b;
+                cr = __float_as_uint(g.r); cg = __float_as_uint(g.g); cb = __float_as_uint(g.b);
                 ok = g.key < Ds ? 1.f : 0.f;
                 if (kGeo) { side = R(4, jj); depth = side.w; }
             }
             // alpha * 2^32 is exact scaling: the clamp decision equals alpha >= alpha_min
             const float a32 = fminf(a * 4294967296.f, kAlpha32Max);
             if (B.in_img && a32 >= amin32 && ok != 0.f) {
-                acc.w += f2ll_rn(a32);
-                acc.r += f2ll_rn(a32 * cr);
-                acc.g += f2ll_rn(a32 * cg);
-                acc.b += f2ll_rn(a32 * cb);
+                // one exact conversion; the colour terms are integer products
+                const long long A = f2ll_rn(a32);
+                acc.w += A;
+                acc.r += (long long)mul_q(A, cr);
+                acc.g += (long long)mul_q(A, cg);
+                acc.b += (long long)mul_q(A, cb);
                 if (kGeo) {
                     acc.d += __float2ll_rn(a32 * depth);
                     acc.nx += f2ll_rn(a32 * side.x);
@@ -643,8 +655,9 @@ __device__ __forceinline__ void composite_store(const CamParams &C, const OptPar
                                                 float *__restrict__ aux, const GeoMaps &geo)
 {
     const float k32 = 2.3283064365386963e-10f;   // 2^-32
+    const float k48 = 3.5527136788005009e-15f;   // 2^-48
     const float WG = __ll2float_rn(acc.w) * k32;
-    const float CG[3] = {__ll2float_rn(acc.r) * k32, __ll2float_rn(acc.g) * k32, __ll2float_rn(acc.b) * k32};
+    const float CG[3] = {__ll2float_rn(acc.r) * k48, __ll2float_rn(acc.g) * k48, __ll2float_rn(acc.b) * k48};
     float out[3];
     if (O.mode == GES_MODE_FULL) {
         const float inv = 1.f / (1.f + WG);

@@ -260,13 +260,26 @@ __device__ __forceinline__ unsigned long long global_timer_ns()
     return t;
 }
 
-// Range of the Gaussian pass's fixed-point terms (units of 2^-32): alpha 2^32
-// is capped at 2^33 and a Gaussian's colour in its record at kColourMax, so
-// every term alpha 2^32 c stays below 2^41 and converts exactly (f2ll_rn).
-// Both caps lie far outside the method's range (alpha <= 1, colours of a few
+// Range of the Gaussian pass's fixed-point terms: alpha 2^32 (an exact
+// integer once alpha >= 1/255) is capped at 2^33 and converted exactly
+// (f2ll_rn) into W_G's sum (units of 2^-32); a Gaussian's colour sits in its
+// raster record as an integer of 2^-16 units, capped at kColourMax, and the
+// colour sums add the exact integer products (units of 2^-48).  The sums are
+// therefore exact while sum alpha < 2^31 and sum alpha c < 2^15 per pixel and
+// channel, far outside the method's range (alpha <= 1, colours of a few
 // units).
 constexpr float kColourMax = 256.f;
 constexpr float kAlpha32Max = 8589934592.f;   // 2^33
+constexpr float kColourScale = 65536.f;       // 2^16
+
+#ifdef __CUDACC__
+// A record colour: min(c, kColourMax) in 2^-16 units, rounded to nearest,
+// carried in a float word.  Colours are >= 0 (Eq. 1's clamp).
+__device__ __forceinline__ float colour_q(float c)
+{
+    return __uint_as_float(__float2uint_rn(fminf(c, kColourMax) * kColourScale));
+}
+#endif
 
 __device__ __forceinline__ float ex2_approx(float x)
 {
@@ -963,8 +976,7 @@ __device__ __forceinline__ void gauss2d_setup(const SceneView &S, const CamParam
     sh_basis(K, o.dir[0], o.dir[1], o.dir[2], Y);
     sh_colour(S.g_sh, i, K, S.sh_dtype, Y, o.rgb, o.raw);
     const float lsig = log2f(sigp);
-    o.aux[0] = make_float4(fminf(o.rgb[0], kColourMax), fminf(o.rgb[1], kColourMax), fminf(o.rgb[2], kColourMax),
-                           lsig);
+    o.aux[0] = make_float4(colour_q(o.rgb[0]), colour_q(o.rgb[1]), colour_q(o.rgb[2]), lsig);
     o.aux[1] = make_float4(fl * n[0], fl * n[1], fl * n[2], log2f(O.alpha_min) - lsig);
     o.visible = true;
 }

@@ -539,7 +539,9 @@ __global__ void __launch_bounds__(256) k_contrib(SceneView S, CamParams C, OptPa
             }
             x0a = make_float4(shfl_f(o.aux[0].x, j), shfl_f(o.aux[0].y, j), shfl_f(o.aux[0].z, j), shfl_f(o.aux[0].w, j));
             x1a = make_float4(shfl_f(o.aux[1].x, j), shfl_f(o.aux[1].y, j), shfl_f(o.aux[1].z, j), shfl_f(o.aux[1].w, j));
-            const float cm = fmaxf(x0a.x, fmaxf(x0a.y, x0a.z));
+            // the colour as a float (the side word carries it in 2^-16 units)
+            const float cm = fminf(fmaxf(shfl_f(o.rgb[0], j), fmaxf(shfl_f(o.rgb[1], j), shfl_f(o.rgb[2], j))),
+                                   kColourMax);
             const float ibw = 1.f / (float)bw;
             for (int k = lane; k < n; k += 32) {
                 const int rk = bbox_row(k, bw, ibw);

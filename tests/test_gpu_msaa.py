@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 import scenegen as sg
-from parity import compare
+from parity import MASKED_MAX, compare
 from test_gpu_backward import _check, _grads_gpu
 from test_gpu_forward import _render, _small
 
@@ -63,7 +63,7 @@ def test_msaa_parity_1080p_orbit_camera(R):
     out = R.render(gs, cams[8], MS)
     res = compare(scene, cams[8], out, ref, MS)
     _assert(res)
-    assert res["masked_frac"] < 0.02
+    assert res["masked_frac"] <= MASKED_MAX
     gs.close()
 
 
