@@ -222,7 +222,10 @@ def storage_precision_cost(R, sg, views=(0, 8)):
     500k Gaussians) stored in FP32, FP16 and BF16, each against the FP64
     oracle's render of the FP32-source scene (views 0 and 8).  Reported: max,
     99.9th percentile and mean absolute colour error over all pixels, and the
-    fraction of surfel ids that differ where the oracle flags no ambiguity.
+    fraction of surfel ids that differ where the oracle flags no ambiguity;
+    and the same colour figures over the pixels the oracle flags as neither
+    id- nor colour-ambiguous (several answers are right at the others, so
+    there even FP32 storage differs by a whole surfel colour).
     The kernel's own accuracy (against the oracle fed the same dequantised
     values) is the parity tests' business; this is the cost of the storage.
     Part of the CPU-baseline leg: the oracle runs on the host cores."""
@@ -243,10 +246,16 @@ def storage_precision_cost(R, sg, views=(0, 8)):
             ref = refs[v]
             err = np.abs(out["rgb"].cpu().numpy().astype(np.float64) - ref["rgb"])
             unm = (ref["amb"] & 1) == 0
+            clear = ref["amb"] == 0
+            ec = err[:, clear]
             per.append({"view": v, "colour_max_abs": float(err.max()),
                         "colour_p99_9_abs": float(np.percentile(err, 99.9)),
                         "colour_mean_abs": float(err.mean()),
-                        "id_mismatch_frac": float((out["id"].cpu().numpy() != ref["id"])[unm].mean())})
+                        "id_mismatch_frac": float((out["id"].cpu().numpy() != ref["id"])[unm].mean()),
+                        "unflagged_frac": float(clear.mean()),
+                        "unflagged_colour_max_abs": float(ec.max()),
+                        "unflagged_colour_p99_9_abs": float(np.percentile(ec, 99.9)),
+                        "unflagged_colour_mean_abs": float(ec.mean())})
         gs.close()
         res[name] = per
     return res
@@ -283,7 +292,8 @@ def _time(fn, iters, warm=2):
 
 def train_step_extra(R, N, sg):
     """Forward + backward on the training-step workload: 1600x1060, 500k
-    surfels + 500k Gaussians, FP32, L1 loss gradient against a target."""
+    surfels + 500k Gaussians, FP32, L1 loss gradient against a target; then
+    the same with the Gaussians as 2D splats (2D-GES, their first two axes)."""
     import torch
     scene, cams = sg.config_scene(3)
     gs = R.GESScene.from_arrays(scene)
@@ -303,8 +313,16 @@ def train_step_extra(R, N, sg):
     fwd_ms = _time(f, 10)
     fb_ms = _time(fb, 10)
     gs.close()
+    # the same step with the Gaussians as the 2D splats of 2D-GES (Sec. 6.4)
+    flat = scene.subset()
+    flat.g_scale = flat.g_scale[:, :2].copy()
+    gs = R.GESScene.from_arrays(flat)
+    fwd2_ms = _time(f, 10)
+    fb2_ms = _time(fb, 10)
+    gs.close()
     return {"workload": "1600x1060-500k-surfels-500k-gaussians-fp32", "fwd_ms_per_view": fwd_ms,
-            "fwd_bwd_ms_per_view": fb_ms, "bwd_ms_per_view": fb_ms - fwd_ms}
+            "fwd_bwd_ms_per_view": fb_ms, "bwd_ms_per_view": fb_ms - fwd_ms,
+            "fwd_ms_per_view_2d": fwd2_ms, "fwd_bwd_ms_per_view_2d": fb2_ms, "bwd_ms_per_view_2d": fb2_ms - fwd2_ms}
 
 
 def batched_extra(R, N, sg):
@@ -372,9 +390,8 @@ def uneven_extra(R, N, sg):
             "render_batch_mpix_per_s": px / (ms_rb / 1e3) / 1e6,
             "per_view_loop_mpix_per_s": px / (ms_loop / 1e3) / 1e6,
             "graph_ms": ms_graph, "per_scene_completion": per_scene,
-            "autotuned": {"prims_per_cta": info.prims_per_cta,
-                                                "raster_ctas_per_sm": info.raster_ctas_per_sm,
-                                                "candidates": info.candidates}}
+            "autotuned": {"prims_per_cta": info.prims_per_cta, "raster_ctas_per_sm": info.raster_ctas_per_sm,
+                          "tile": f"{info.tile_w}x{info.tile_h}", "candidates": info.candidates}}
 
 
 def msaa_extra(R, N, gs, cams):
@@ -451,7 +468,8 @@ def orbit_2160p_extra(R, N, gs, cams):
     b.close()
     return {"workload": "orbit-64-views-2160p-1M-surfels-300k-gaussians", "frames_per_s": len(big) / (ms / 1e3),
             "kernel_ms_per_frame": {k: prof[k][0] / prof[k][1] / len(big) for k in prof},
-            "autotuned": {"prims_per_cta": info.prims_per_cta, "raster_ctas_per_sm": info.raster_ctas_per_sm}}
+            "autotuned": {"prims_per_cta": info.prims_per_cta, "raster_ctas_per_sm": info.raster_ctas_per_sm,
+                          "tile": f"{info.tile_w}x{info.tile_h}"}}
 
 
 def paper_shaped_extra(R, N, sg):
