@@ -775,8 +775,10 @@ struct ges_batch {
     ges_batch_info info{};
     ges_profile profile{};
     int tsx = kTileShift, tsy = kTileShift;   // binning tile of the chosen configuration
-    int2 *d_map = nullptr;                 // preprocess CTA -> (view, CTA of the view), both launches
-    size_t map_cap = 0;                    // entries
+    // the maps the graph reads: preprocess CTA -> (view, CTA of the view) of
+    // both launches, the colour pass's work items and view groups
+    unsigned char *d_map = nullptr;
+    size_t map_bytes = 0;                  // capacity
 };
 
 namespace {
@@ -857,12 +859,41 @@ size_t batch_layout(ges_batch *b, const std::vector<SceneView> &S, const std::ve
 // counts) take each primitive range one after another, so only the first of
 // them reads the range's attributes from HBM; surfel CTAs first, then the
 // Gaussian ones (their own launch).  Uploads the map; P gets its pointers.
+// Bytes of the maps (see ges_batch::d_map) for n_prep preprocess CTAs,
+// n_items colour items and n views; the parts start 16-byte aligned.
+size_t map_layout(size_t n_prep, size_t n_items, size_t n, size_t *off_items, size_t *off_gview)
+{
+    const size_t a = (n_prep * sizeof(int2) + 15) & ~(size_t)15;
+    const size_t b = a + n_items * sizeof(int4);
+    if (off_items) *off_items = a;
+    if (off_gview) *off_gview = b;
+    return b + n * sizeof(int);
+}
+
+// Grow the map buffer to at least bytes.  Only before a graph is kept: a
+// captured graph holds the buffer's address.
+cudaError_t reserve_map(ges_batch *b, size_t bytes)
+{
+    if (bytes <= b->map_bytes) return cudaSuccess;
+    if (b->exec) return cudaErrorInvalidValue;
+    if (b->d_map) cudaFree(b->d_map);
+    b->d_map = nullptr;
+    b->map_bytes = 0;
+    cudaError_t e = cudaMalloc(&b->d_map, bytes);
+    if (e == cudaSuccess) b->map_bytes = bytes;
+    return e;
+}
+
+// Colour items of one primitive kind of a group: one per kColourThreads primitives.
+size_t colour_items(int64_t n) { return (size_t)((n + kColourThreads - 1) / kColourThreads); }
+
+// The preprocess CTA maps (views of one scene take the same range one after
+// another) and the colour pass's work list (one item per kColourThreads
+// primitives of a kind per view group), uploaded for the current layout.
 cudaError_t upload_prep_map(ges_batch *b, BatchPlan &P)
 {
-    std::vector<int2> m;
-    m.reserve((size_t)P.total_sprep + P.total_gprep);
-    std::vector<int> done(b->n, 0);
     std::vector<std::vector<int>> groups;
+    std::vector<int> done(b->n, 0);
     for (int v = 0; v < b->n; ++v) {
         if (done[v]) continue;
         std::vector<int> g{v};
@@ -870,7 +901,8 @@ cudaError_t upload_prep_map(ges_batch *b, BatchPlan &P)
         const SceneView &a = b->views[v].S;
         for (int w = v + 1; w < b->n; ++w) {
             const SceneView &c = b->views[w].S;
-            if (!done[w] && c.s_pos == a.s_pos && c.g_pos == a.g_pos && c.N == a.N && c.M == a.M &&
+            if (!done[w] && c.s_pos == a.s_pos && c.g_pos == a.g_pos && c.s_sh == a.s_sh && c.g_sh == a.g_sh &&
+                c.N == a.N && c.M == a.M && c.deg == a.deg && c.sh_dtype == a.sh_dtype &&
                 b->views[w].B.Ps == b->views[v].B.Ps && b->views[w].B.Pg == b->views[v].B.Pg) {
                 g.push_back(w);
                 done[w] = 1;
@@ -878,6 +910,8 @@ cudaError_t upload_prep_map(ges_batch *b, BatchPlan &P)
         }
         groups.push_back(g);
     }
+    std::vector<int2> m;
+    m.reserve((size_t)P.total_sprep + P.total_gprep);
     for (int kind = 0; kind < 2; ++kind)
         for (const std::vector<int> &g : groups) {
             const LocalBins &B = b->views[g[0]].B;
@@ -885,17 +919,32 @@ cudaError_t upload_prep_map(ges_batch *b, BatchPlan &P)
             for (int c = 0; c < n; ++c)
                 for (int v : g) m.push_back(make_int2(v, kind == 0 ? c : B.Ps + c));
         }
-    if (m.size() > b->map_cap) {
-        if (b->d_map) cudaFree(b->d_map);
-        b->d_map = nullptr;
-        b->map_cap = 0;
-        cudaError_t e = cudaMalloc(&b->d_map, std::max<size_t>(m.size(), 1) * sizeof(int2));
-        if (e != cudaSuccess) return e;
-        b->map_cap = std::max<size_t>(m.size(), 1);
+    std::vector<int4> items;
+    std::vector<int> gview;
+    for (const std::vector<int> &g : groups) {
+        const int gofs = (int)gview.size();
+        gview.insert(gview.end(), g.begin(), g.end());
+        const SceneView &S0 = b->views[g[0]].S;
+        for (int kind = 0; kind < 2; ++kind) {
+            const int64_t n = kind == 0 ? S0.N : S0.M;
+            for (int64_t f = 0; f < n; f += kColourThreads)
+                items.push_back(make_int4(kind, gofs, (int)g.size(), (int)f));
+        }
     }
-    P.smap = b->d_map;
-    P.gmap = b->d_map + P.total_sprep;
-    return m.empty() ? cudaSuccess : cudaMemcpy(b->d_map, m.data(), m.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    size_t oi = 0, og = 0;
+    const size_t bytes = map_layout(m.size(), items.size(), gview.size(), &oi, &og);
+    cudaError_t e = reserve_map(b, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) return e;
+    std::vector<unsigned char> h(bytes, 0);
+    if (!m.empty()) std::memcpy(h.data(), m.data(), m.size() * sizeof(int2));
+    if (!items.empty()) std::memcpy(h.data() + oi, items.data(), items.size() * sizeof(int4));
+    if (!gview.empty()) std::memcpy(h.data() + og, gview.data(), gview.size() * sizeof(int));
+    P.smap = reinterpret_cast<const int2 *>(b->d_map);
+    P.gmap = P.smap + P.total_sprep;
+    P.cmap = reinterpret_cast<const int4 *>(b->d_map + oi);
+    P.gview = reinterpret_cast<const int *>(b->d_map + og);
+    P.total_colour = (int)items.size();
+    return cudaMemcpy(b->d_map, h.data(), bytes, cudaMemcpyHostToDevice);
 }
 
 }  // namespace
@@ -1014,6 +1063,16 @@ static ges_status batch_create(ges_scene *const *scenes, const ges_camera *cams,
     size_t bytes = 0;
     for (const auto &sh : shapes) bytes = std::max(bytes, batch_layout(b, S, shaped(sh), kR[0], nullptr));
     BATCH_CUDA(cudaMalloc(&b->arena, bytes));
+    {
+        // the maps of the candidate with the most preprocess CTAs (a kept
+        // graph holds the buffer's address, so it never moves afterwards)
+        size_t n_prep = 0, n_items = 0;
+        for (int v = 0; v < n_views; ++v) {
+            n_prep += (size_t)((S[v].N + kR[0] - 1) / kR[0] + (S[v].M + kR[0] - 1) / kR[0]);
+            n_items += colour_items(S[v].N) + colour_items(S[v].M);
+        }
+        BATCH_CUDA(reserve_map(b, map_layout(n_prep, n_items, (size_t)n_views, nullptr, nullptr) + 16));
+    }
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
 
@@ -1247,7 +1306,14 @@ ges_status render_batch_engine(ges_scene *const *scenes, const std::vector<CamPa
     }
     for (int v = 0; v < n; ++v) {
         const SceneView &S = scenes[sov[v]]->view;
-        key.insert(key.end(), {(int64_t)sov[v], S.N, S.M, S.gdim, S.deg, S.attr_dtype, S.sh_dtype,
+        // the first view whose scene arrays are the same: the graph's colour
+        // pass evaluates such views together
+        int grp = v;
+        for (int w = 0; w < v; ++w) {
+            const SceneView &T = scenes[sov[w]]->view;
+            if (T.s_pos == S.s_pos && T.g_pos == S.g_pos && T.s_sh == S.s_sh && T.g_sh == S.g_sh) { grp = w; break; }
+        }
+        key.insert(key.end(), {(int64_t)sov[v], (int64_t)grp, S.N, S.M, S.gdim, S.deg, S.attr_dtype, S.sh_dtype,
                                (int64_t)(S.g_filt3 != nullptr), C[v].W, C[v].H,
                                (int64_t)(out_depth && out_depth[v])});
     }

@@ -96,7 +96,9 @@ __device__ __forceinline__ GaussRec gauss_rec3(float4 a, float4 b, float4 c)
 // return its pixel bbox.
 // kGd: the scene's Gaussian kind (a template argument, so that each kernel
 // carries only its own set-up code)
-template <int kGd, bool kTr = false>
+// kCol false: leave the colour (Eq. 1) to the batch's colour pass; only the
+// geometry is set up and stored here.
+template <int kGd, bool kTr = false, bool kCol = true>
 __device__ __forceinline__ bool setup_and_store(const SceneView &S, const CamParams &C, const OptParams &O,
                                                 const ViewScratch &X, bool surf, int64_t i, int &x0, int &y0,
                                                 int &x1, int &y1)
@@ -109,12 +111,14 @@ __device__ __forceinline__ bool setup_and_store(const SceneView &S, const CamPar
         if (!o.valid_quat) atomicOr(X.status + ST_FLAGS, FLAG_BADQ);
         if (!o.visible) return false;
         store_rec(X.s_rec + 4 * i, o.rec);
-        surfel_colour(S, i, o);
-        X.s_rgb[i] = make_float4(o.rgb[0], o.rgb[1], o.rgb[2], 0.f);
+        if (kCol) {
+            surfel_colour(S, i, o);
+            X.s_rgb[i] = make_float4(o.rgb[0], o.rgb[1], o.rgb[2], 0.f);
+        }
         x0 = o.x0; y0 = o.y0; x1 = o.x1; y1 = o.y1;
     } else {
         GaussOut o;
-        if (kGd == 2) gauss2d_setup(S, C, O, i, o);
+        if (kGd == 2) gauss2d_setup(S, C, O, i, o, kCol);
         else gauss_geom(S, C, O, i, o);
         if (!o.valid_quat) atomicOr(X.status + ST_FLAGS, FLAG_BADQ);
         if (!o.visible) return false;
@@ -127,8 +131,12 @@ __device__ __forceinline__ bool setup_and_store(const SceneView &S, const CamPar
             dst[1] = make_float4(o.rec.la, o.rec.lb, o.rec.lc, o.rec.sigma);
             dst[3] = make_float4(__int_as_float(o.rec.id), __uint_as_float(o.rec.bb_lo),
                                  __uint_as_float(o.rec.bb_hi), o.rec.pad);
-            gauss_colour(S, i, o);
-            dst[2] = make_float4(o.rec.key, colour_q(o.rec.r), colour_q(o.rec.g), colour_q(o.rec.b));
+            if (kCol) {
+                gauss_colour(S, i, o);
+                dst[2] = make_float4(o.rec.key, colour_q(o.rec.r), colour_q(o.rec.g), colour_q(o.rec.b));
+            } else {
+                reinterpret_cast<float *>(dst + 2)[0] = o.rec.key;
+            }
         }
         if (kGd == 2 || O.geo) {
             X.g_aux[2 * i] = o.aux[0];
@@ -146,7 +154,7 @@ __device__ __forceinline__ bool setup_and_store(const SceneView &S, const CamPar
 // (two 16-bit counters each); vcnt: a shared counter.
 // kKind: 0 both kinds (CTA c < B.Ps: surfels), 1 surfel ranges only, 2
 // Gaussian ranges only (a launch per kind gives each its own registers)
-template <int kGd, bool kTr = false, int kKind = 0>
+template <int kGd, bool kTr = false, int kKind = 0, bool kCol = true>
 __device__ __forceinline__ void prep_local_body(const SceneView &S, const CamParams &C, const OptParams &O,
                                                 const ViewScratch &X, const LocalBins &B, int c, unsigned *hist,
                                                 unsigned &vcnt)
@@ -166,7 +174,7 @@ __device__ __forceinline__ void prep_local_body(const SceneView &S, const CamPar
     for (int64_t i0 = beg; i0 < end; i0 += kPrepThreads) {
         const int64_t i = i0 + threadIdx.x;
         int x0 = 0, y0 = 0, x1 = -1, y1 = -1;
-        const bool vis = i < end && setup_and_store<kGd, kTr>(S, C, O, X, surf, i, x0, y0, x1, y1);
+        const bool vis = i < end && setup_and_store<kGd, kTr, kCol>(S, C, O, X, surf, i, x0, y0, x1, y1);
         const unsigned m = __ballot_sync(0xffffffffu, vis);
         if (m) {
             const int leader = __ffs(m) - 1;
@@ -813,7 +821,65 @@ __global__ void __launch_bounds__(kPrepThreads, 2) k_bprep(const BatchView *V, c
     __syncthreads();
     load_view(V, sm.x, bv);
     __syncthreads();
-    prep_local_body<kGd, false, kKind>(bv.S, bv.C, O, bv.X, bv.B, sm.y, hist, vcnt);
+    prep_local_body<kGd, false, kKind, false>(bv.S, bv.C, O, bv.X, bv.B, sm.y, hist, vcnt);
+}
+
+// Colour pass of the batch (Eq. 1): one thread per primitive of one kind,
+// for every view of its view group (the views of one scene).  The SH row and
+// the position are read once; per view, the direction from the centre to that
+// view's camera, the basis and the colour are evaluated with the same
+// operations, in the same order, as the inline set-up of the per-view path,
+// so both paths store bit-identical colours.  Surfels: the view's colour
+// array; 3D Gaussians: the three colour words of the view's raster record;
+// 2D Gaussians: the colour words of the first side word (both in 2^-16
+// units).  Primitives a view does not draw get colours that nothing reads.
+template <int K, int kGd>
+__device__ __forceinline__ void colour_views(const BatchView *V, const int *__restrict__ gview, int gofs, int gn,
+                                             bool surf, int64_t i, const SceneView &S)
+{
+    const float *pos = surf ? S.s_pos : S.g_pos;
+    const float px = __ldg(pos + 3 * i), py = __ldg(pos + 3 * i + 1), pz = __ldg(pos + 3 * i + 2);
+    float c[3 * K];
+    load_sh_row<K>(surf ? S.s_sh : S.g_sh, i, S.sh_dtype, c);
+    for (int k = 0; k < gn; ++k) {
+        const BatchView *bv = V + __ldg(gview + gofs + k);
+        float dir[3], L;
+        view_dir(bv->C, px, py, pz, dir, L);
+        float Y[16];
+        sh_basis(K, dir[0], dir[1], dir[2], Y);
+        float r = 0.5f, g = 0.5f, b = 0.5f;
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            r = fmaf(c[3 * q], Y[q], r);
+            g = fmaf(c[3 * q + 1], Y[q], g);
+            b = fmaf(c[3 * q + 2], Y[q], b);
+        }
+        r = fmaxf(r, 0.f); g = fmaxf(g, 0.f); b = fmaxf(b, 0.f);
+        if (surf) {
+            bv->X.s_rgb[i] = make_float4(r, g, b, 0.f);
+        } else {
+            float *w = kGd == 2 ? reinterpret_cast<float *>(bv->X.g_aux + 2 * i)
+                                : reinterpret_cast<float *>(bv->X.g_rec + 4 * i + 2) + 1;
+            w[0] = colour_q(r); w[1] = colour_q(g); w[2] = colour_q(b);
+        }
+    }
+}
+
+template <int kGd>
+__global__ void __launch_bounds__(kColourThreads) k_bcolour(const BatchView *V, const int4 *__restrict__ items,
+                                                            const int *__restrict__ gview)
+{
+    const int4 it = items[blockIdx.x];
+    const bool surf = it.x == 0;
+    const SceneView &S = V[__ldg(gview + it.y)].S;
+    const int64_t i = (int64_t)it.w + threadIdx.x;
+    if (i >= (surf ? S.N : S.M)) return;
+    switch ((S.deg + 1) * (S.deg + 1)) {
+    case 16: colour_views<16, kGd>(V, gview, it.y, it.z, surf, i, S); break;
+    case 9: colour_views<9, kGd>(V, gview, it.y, it.z, surf, i, S); break;
+    case 4: colour_views<4, kGd>(V, gview, it.y, it.z, surf, i, S); break;
+    default: colour_views<1, kGd>(V, gview, it.y, it.z, surf, i, S); break;
+    }
 }
 
 __global__ void __launch_bounds__(256) k_bcolscan(const BatchView *V, int n)
@@ -915,6 +981,10 @@ cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const Opt
         if (P.total_gprep > 0) {
             if (P.gdim == 2) k_bprep<2, 2><<<P.total_gprep, kPrepThreads, sm, st>>>(d_views, P.gmap, O, t0);
             else k_bprep<3, 2><<<P.total_gprep, kPrepThreads, sm, st>>>(d_views, P.gmap, O, t0);
+        }
+        if (P.total_colour > 0) {
+            if (P.gdim == 2) k_bcolour<2><<<P.total_colour, kColourThreads, 0, st>>>(d_views, P.cmap, P.gview);
+            else k_bcolour<3><<<P.total_colour, kColourThreads, 0, st>>>(d_views, P.cmap, P.gview);
         }
     }
     mark(1);

@@ -125,7 +125,14 @@ struct BatchPlan {
     // launch: the views of one scene take the same primitive range one after
     // another, so all but the first read its attributes from L2
     const int2 *smap, *gmap;
+    // colour pass: per CTA (kind: 0 surfels / 1 Gaussians, first entry of its
+    // view group in gview, views in the group, first primitive); gview lists
+    // the views of each group of views that share one scene
+    const int4 *cmap;
+    const int *gview;
+    int total_colour;
 };
+constexpr int kColourThreads = 256;   // primitives per colour-pass CTA
 cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const OptParams &O, unsigned *work_counter,
                          cudaStream_t st, cudaEvent_t *ev /* 5 events or nullptr */);
 LocalBins plan_local_bins_per_cta(int64_t N, int64_t M, int64_t prims_per_cta);
@@ -919,8 +926,10 @@ __device__ __forceinline__ void gauss_setup(const SceneView &S, const CamParams 
 // The support alpha >= alpha_min is the disc of radius r = sqrt(2 ln(sigma'/alpha_min))
 // in filtered units, so the record is a disc record (disc_setup) and
 // alpha = 2^(log2 sigma' + log2(alpha_min/sigma') rho), rho = (a'^2 + b'^2)/r^2.
+// colour false: the side word's colour is left at 0 for a later pass (the
+// batch evaluates the colours of all views of a scene in one kernel).
 __device__ __forceinline__ void gauss2d_setup(const SceneView &S, const CamParams &C, const OptParams &O,
-                                              int64_t i, GaussOut &o)
+                                              int64_t i, GaussOut &o, bool colour = true)
 {
     o.visible = false;
     o.valid_quat = true;
@@ -971,12 +980,16 @@ __device__ __forceinline__ void gauss2d_setup(const SceneView &S, const CamParam
     o.x0 = d.x0; o.y0 = d.y0; o.x1 = d.x1; o.y1 = d.y1;
     const float nP = n[0] * x + n[1] * y + n[2] * z;
     const float fl = nP > 0.f ? -1.f : 1.f;
-    const int K = (S.deg + 1) * (S.deg + 1);
-    float Y[16];
-    sh_basis(K, o.dir[0], o.dir[1], o.dir[2], Y);
-    sh_colour(S.g_sh, i, K, S.sh_dtype, Y, o.rgb, o.raw);
     const float lsig = log2f(sigp);
-    o.aux[0] = make_float4(colour_q(o.rgb[0]), colour_q(o.rgb[1]), colour_q(o.rgb[2]), lsig);
+    if (colour) {
+        const int K = (S.deg + 1) * (S.deg + 1);
+        float Y[16];
+        sh_basis(K, o.dir[0], o.dir[1], o.dir[2], Y);
+        sh_colour(S.g_sh, i, K, S.sh_dtype, Y, o.rgb, o.raw);
+        o.aux[0] = make_float4(colour_q(o.rgb[0]), colour_q(o.rgb[1]), colour_q(o.rgb[2]), lsig);
+    } else {
+        o.aux[0] = make_float4(0.f, 0.f, 0.f, lsig);
+    }
     o.aux[1] = make_float4(fl * n[0], fl * n[1], fl * n[2], log2f(O.alpha_min) - lsig);
     o.visible = true;
 }
