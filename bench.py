@@ -161,8 +161,9 @@ def ncu_traffic(kernel, n_views):
     return total
 
 
-# the batch preprocess: one launch over the surfel ranges, one over the Gaussian ranges
-PREP_KERNELS = ("k_bprep<3,1>", "k_bprep<3,2>")
+# the batch preprocess: one launch over the surfel ranges, one over the
+# Gaussian ranges, and the colour pass over all views of the scene
+PREP_KERNELS = ("k_bprep<3,1>", "k_bprep<3,2>", "k_bcolour<3>")
 
 
 def algorithmic_bytes(n_s, n_g, s_vis, g_vis, hw, attr_bytes=4, sh_bytes=4, deg=3):
@@ -789,8 +790,9 @@ def main():
     prep_gbs = n_views * float(np.mean(prep_b)) / (prep_ms / prep_n / 1e3) / 1e9 if prep_ms > 0 else None
     frame_achieved = float(np.mean(frame_b)) * frames / world / (ms / 1e3) / 1e9
     # kernels of one graph replay: a preprocess launch per primitive kind
-    # present, then the column scan, the scan, the fill and the raster
-    kernels_per_step = (scene.n_surfels > 0) + (scene.n_gaussians > 0) + 4
+    # present, the colour pass, then the column scan, the scan, the fill and
+    # the raster
+    kernels_per_step = (scene.n_surfels > 0) + (scene.n_gaussians > 0) + (scene.n_surfels + scene.n_gaussians > 0) + 4
     line = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",

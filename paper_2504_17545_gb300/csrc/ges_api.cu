@@ -771,7 +771,7 @@ struct ges_batch {
     cudaStream_t stream = nullptr;         // capture / tuning stream
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t done = nullptr;
-    cudaEvent_t phase[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // event nodes in the graph
+    cudaEvent_t phase[7] = {};             // event nodes in the graph (phase boundaries, colour pass)
     ges_batch_info info{};
     ges_profile profile{};
     int tsx = kTileShift, tsy = kTileShift;   // binning tile of the chosen configuration
@@ -1224,10 +1224,12 @@ ges_status ges_batch_sync(ges_batch *b)
     if (!b) return fail(GES_ERR_INVALID_ARG, "batch is NULL");
     GES_CUDA(cudaEventSynchronize(b->done));
     // per-phase device time of the last launch (graph event nodes)
-    static const char *names[4] = {"preprocess", "scan", "fill", "raster"};
-    for (int k = 0; k < 4; ++k) {
+    // the colour pass runs inside the preprocess phase; its own time is reported beside it
+    static const char *names[5] = {"preprocess", "scan", "fill", "raster", "colour_in_preprocess"};
+    for (int k = 0; k < 5; ++k) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, b->phase[k], b->phase[k + 1]) != cudaSuccess) continue;
+        cudaEvent_t a = k < 4 ? b->phase[k] : b->phase[5], z = k < 4 ? b->phase[k + 1] : b->phase[6];
+        if (cudaEventElapsedTime(&ms, a, z) != cudaSuccess) continue;
         int i = -1;
         for (int j = 0; j < b->profile.n; ++j)
             if (std::strncmp(b->profile.names[j], names[k], 23) == 0) i = j;

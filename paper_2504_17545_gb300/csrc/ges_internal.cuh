@@ -133,8 +133,11 @@ struct BatchPlan {
     int total_colour;
 };
 constexpr int kColourThreads = 256;   // primitives per colour-pass CTA
+constexpr int kColourViews = 64;      // views whose camera centres a colour-pass CTA stages at a time
+// ev: 7 events recorded as graph event nodes (phase boundaries 0-4, the
+// colour pass's start and end 5-6) or nullptr.
 cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const OptParams &O, unsigned *work_counter,
-                         cudaStream_t st, cudaEvent_t *ev /* 5 events or nullptr */);
+                         cudaStream_t st, cudaEvent_t *ev);
 LocalBins plan_local_bins_per_cta(int64_t N, int64_t M, int64_t prims_per_cta);
 constexpr int kPrepThreads = 512;
 constexpr int kFillThreads = 1024;
@@ -510,12 +513,17 @@ static_assert(sizeof(GaussRec) == 64 && alignof(GaussRec) == 16, "Gaussian recor
 // Eq. 1's view direction: the unit vector from the primitive's centre to the
 // camera, and their distance (zero direction at distance 0).  The one
 // definition used by the set-up and by the backward passes.
-__device__ __forceinline__ void view_dir(const CamParams &C, float px, float py, float pz, float *dir, float &L)
+__device__ __forceinline__ void view_dir_o(float ox, float oy, float oz, float px, float py, float pz, float *dir,
+                                           float &L)
 {
-    const float vx = C.ocam[0] - px, vy = C.ocam[1] - py, vz = C.ocam[2] - pz;
+    const float vx = ox - px, vy = oy - py, vz = oz - pz;
     L = sqrtf(vx * vx + vy * vy + vz * vz);
     const float il = L > 0.f ? 1.f / L : 0.f;
     dir[0] = vx * il; dir[1] = vy * il; dir[2] = vz * il;
+}
+__device__ __forceinline__ void view_dir(const CamParams &C, float px, float py, float pz, float *dir, float &L)
+{
+    view_dir_o(C.ocam[0], C.ocam[1], C.ocam[2], px, py, pz, dir, L);
 }
 
 struct SurfelOut {
