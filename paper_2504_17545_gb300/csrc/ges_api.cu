@@ -772,6 +772,7 @@ struct ges_batch {
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t done = nullptr;
     cudaEvent_t phase[7] = {};             // event nodes in the graph (phase boundaries, colour pass)
+    bool colour_pass = false;              // the kept graph has a colour pass (events 5-6 recorded)
     ges_batch_info info{};
     ges_profile profile{};
     int tsx = kTileShift, tsy = kTileShift;   // binning tile of the chosen configuration
@@ -921,7 +922,12 @@ cudaError_t upload_prep_map(ges_batch *b, BatchPlan &P)
         }
     std::vector<int4> items;
     std::vector<int> gview;
+    // a colour pass only pays when some scene has several views: otherwise
+    // the set-up evaluates each colour where it reads the primitive anyway
+    size_t maxg = 0;
+    for (const std::vector<int> &g : groups) maxg = std::max(maxg, g.size());
     for (const std::vector<int> &g : groups) {
+        if (maxg < 2) break;
         const int gofs = (int)gview.size();
         gview.insert(gview.end(), g.begin(), g.end());
         const SceneView &S0 = b->views[g[0]].S;
@@ -944,6 +950,7 @@ cudaError_t upload_prep_map(ges_batch *b, BatchPlan &P)
     P.cmap = reinterpret_cast<const int4 *>(b->d_map + oi);
     P.gview = reinterpret_cast<const int *>(b->d_map + og);
     P.total_colour = (int)items.size();
+    b->colour_pass = P.total_colour > 0;
     return cudaMemcpy(b->d_map, h.data(), bytes, cudaMemcpyHostToDevice);
 }
 
@@ -1226,10 +1233,13 @@ ges_status ges_batch_sync(ges_batch *b)
     // per-phase device time of the last launch (graph event nodes)
     // the colour pass runs inside the preprocess phase; its own time is reported beside it
     static const char *names[5] = {"preprocess", "scan", "fill", "raster", "colour_in_preprocess"};
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < (b->colour_pass ? 5 : 4); ++k) {
         float ms = 0.f;
         cudaEvent_t a = k < 4 ? b->phase[k] : b->phase[5], z = k < 4 ? b->phase[k + 1] : b->phase[6];
-        if (cudaEventElapsedTime(&ms, a, z) != cudaSuccess) continue;
+        if (cudaEventElapsedTime(&ms, a, z) != cudaSuccess) {
+            cudaGetLastError();   // a failed query must not surface at the next launch
+            continue;
+        }
         int i = -1;
         for (int j = 0; j < b->profile.n; ++j)
             if (std::strncmp(b->profile.names[j], names[k], 23) == 0) i = j;

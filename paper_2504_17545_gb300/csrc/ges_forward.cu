@@ -803,8 +803,10 @@ __device__ __forceinline__ void load_view(const BatchView *V, int v, BatchView &
 // Preprocess of all views, one launch per primitive kind (kKind 1: the
 // surfel ranges, 2: the Gaussian ranges); CTA x of the launch takes the view
 // and the range of map[x].  The two set-ups need different registers, and a
-// kernel per kind keeps the one from spilling for the other.
-template <int kGd, int kKind>
+// kernel per kind keeps the one from spilling for the other.  kCol: the
+// colours too (a batch whose scenes each have one view; otherwise the colour
+// pass evaluates them for all views of a scene at once).
+template <int kGd, int kKind, bool kCol>
 __global__ void __launch_bounds__(kPrepThreads, 2) k_bprep(const BatchView *V, const int2 *__restrict__ map,
                                                           OptParams O, unsigned long long *t0)
 {
@@ -821,7 +823,7 @@ __global__ void __launch_bounds__(kPrepThreads, 2) k_bprep(const BatchView *V, c
     __syncthreads();
     load_view(V, sm.x, bv);
     __syncthreads();
-    prep_local_body<kGd, false, kKind, false>(bv.S, bv.C, O, bv.X, bv.B, sm.y, hist, vcnt);
+    prep_local_body<kGd, false, kKind, kCol>(bv.S, bv.C, O, bv.X, bv.B, sm.y, hist, vcnt);
 }
 
 // Colour pass of the batch (Eq. 1): one thread per primitive of one kind,
@@ -993,13 +995,20 @@ cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const Opt
     {
         unsigned long long *t0 = reinterpret_cast<unsigned long long *>(work_counter + 2);
         const size_t sm = local_bins_smem(P.max_T, false);
+        const bool col = P.total_colour > 0;   // colours in the colour pass, not in the set-up
         if (P.total_sprep > 0) {
-            if (P.gdim == 2) k_bprep<2, 1><<<P.total_sprep, kPrepThreads, sm, st>>>(d_views, P.smap, O, t0);
-            else k_bprep<3, 1><<<P.total_sprep, kPrepThreads, sm, st>>>(d_views, P.smap, O, t0);
+            const unsigned g = P.total_sprep;
+            if (P.gdim == 2 && col) k_bprep<2, 1, false><<<g, kPrepThreads, sm, st>>>(d_views, P.smap, O, t0);
+            else if (P.gdim == 2) k_bprep<2, 1, true><<<g, kPrepThreads, sm, st>>>(d_views, P.smap, O, t0);
+            else if (col) k_bprep<3, 1, false><<<g, kPrepThreads, sm, st>>>(d_views, P.smap, O, t0);
+            else k_bprep<3, 1, true><<<g, kPrepThreads, sm, st>>>(d_views, P.smap, O, t0);
         }
         if (P.total_gprep > 0) {
-            if (P.gdim == 2) k_bprep<2, 2><<<P.total_gprep, kPrepThreads, sm, st>>>(d_views, P.gmap, O, t0);
-            else k_bprep<3, 2><<<P.total_gprep, kPrepThreads, sm, st>>>(d_views, P.gmap, O, t0);
+            const unsigned g = P.total_gprep;
+            if (P.gdim == 2 && col) k_bprep<2, 2, false><<<g, kPrepThreads, sm, st>>>(d_views, P.gmap, O, t0);
+            else if (P.gdim == 2) k_bprep<2, 2, true><<<g, kPrepThreads, sm, st>>>(d_views, P.gmap, O, t0);
+            else if (col) k_bprep<3, 2, false><<<g, kPrepThreads, sm, st>>>(d_views, P.gmap, O, t0);
+            else k_bprep<3, 2, true><<<g, kPrepThreads, sm, st>>>(d_views, P.gmap, O, t0);
         }
         if (P.total_colour > 0) {
             // (a second graph branch beside the scans and the fill measured 0.3 % faster: not kept)
@@ -1035,10 +1044,14 @@ cudaError_t prepare_forward_kernels()
     if ((e = cudaFuncSetAttribute(k_prep_local<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(k_prep_local<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(k_prep_local<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(k_bprep<3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(k_bprep<3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(k_bprep<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(k_bprep<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess)
+        (e = cudaFuncSetAttribute(k_bprep<3, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_bprep<3, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_bprep<2, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_bprep<2, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_bprep<3, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_bprep<3, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_bprep<2, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_bprep<2, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, hs)) != cudaSuccess)
         return e;
     if ((e = cudaFuncSetAttribute(k_fill_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)local_bins_smem(kLocalMaxTiles, true))) != cudaSuccess)

@@ -127,7 +127,8 @@ struct BatchPlan {
     const int2 *smap, *gmap;
     // colour pass: per CTA (kind: 0 surfels / 1 Gaussians, first entry of its
     // view group in gview, views in the group, first primitive); gview lists
-    // the views of each group of views that share one scene
+    // the views of each group of views that share one scene.  total_colour 0
+    // (no scene with several views): the set-up evaluates the colours
     const int4 *cmap;
     const int *gview;
     int total_colour;
