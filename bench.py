@@ -143,11 +143,14 @@ def source_digest():
 
 def ncu_traffic(kernel, n_views):
     """DRAM bytes of one launch of `kernel` over n_views views, from the
-    committed ncu record (taken on a smaller batch of the same views and
-    scaled by the views processed), or None when the kernel sources changed
-    since it was taken.  `kernel` may name several records (a phase made of
-    several launches, e.g. the preprocess of each primitive kind), which are
-    summed; None if any of them is missing or stale."""
+    committed ncu record (taken on a smaller batch of the same views), or
+    None when the kernel sources changed since it was taken.  A record scales
+    with the views processed (dram_bytes_per_view), or, where the kernel reads
+    a scene's attributes once for all of its views, holds those reads per
+    batch and the writes per view (read_bytes_per_batch,
+    write_bytes_per_view).  `kernel` may name several records (a phase made
+    of several launches, e.g. the preprocess of each primitive kind and the
+    colour pass), which are summed; None if any of them is missing or stale."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
@@ -157,7 +160,10 @@ def ncu_traffic(kernel, n_views):
         d = rec.get(k)
         if not d or d.get("source_digest") != source_digest():
             return None
-        total += float(d["dram_bytes_per_view"]) * n_views
+        if "read_bytes_per_batch" in d:
+            total += float(d["read_bytes_per_batch"]) + float(d["write_bytes_per_view"]) * n_views
+        else:
+            total += float(d["dram_bytes_per_view"]) * n_views
     return total
 
 

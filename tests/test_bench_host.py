@@ -47,13 +47,20 @@ def test_alu_peak_is_lanes_times_clock():
 def test_ncu_traffic_follows_the_sources(monkeypatch):
     rec = json.load(open(os.path.join(bench.ROOT, "profiles", "ncu_traffic.json")))
     for k in ("k_braster",) + tuple(n for n in bench.PREP_KERNELS if n in rec):
-        assert rec[k]["views_in_capture"] >= 1 and rec[k]["dram_bytes_per_view"] > 0
+        assert rec[k]["views_in_capture"] >= 1
+        assert rec[k].get("dram_bytes_per_view", 0) > 0 or rec[k]["write_bytes_per_view"] > 0
     digest = bench.source_digest()
     assert len(digest) == 16
     if rec["k_braster"]["source_digest"] == digest:
         # scaled by the views of the launch
         t1, t64 = bench.ncu_traffic("k_braster", 1), bench.ncu_traffic("k_braster", 64)
         assert t64 == pytest.approx(64 * t1)
+    # reads once per batch, writes per view
+    fake = {"k_x": {"read_bytes_per_batch": 100.0, "write_bytes_per_view": 10.0, "source_digest": digest,
+                    "views_in_capture": 4}}
+    monkeypatch.setattr(bench.json, "load", lambda f: fake)
+    assert bench.ncu_traffic("k_x", 64) == pytest.approx(100.0 + 640.0)
+    monkeypatch.undo()
     # a phase of several launches needs all of their records
     assert bench.ncu_traffic(("k_braster", "no_such_kernel"), 64) is None
     # any change to the kernel sources drops the number
