@@ -167,3 +167,42 @@ def test_batch_2160p_orbit_view_matches_oracle(R):
     assert (b.rgb[1] == single1["rgb"]).all() and (b.depth[1] == single1["depth"]).all()
     b.close()
     gs.close()
+
+
+@pytest.mark.parametrize("deg,dtype", [(0, "float32"), (1, "float32"), (2, "float16"), (3, "bfloat16")])
+def test_batch_colour_pass_sh_degrees_and_storage(R, deg, dtype):
+    """The batch's colour pass (Eq. 1 for all views of a scene, one SH read
+    per primitive) stores the same bits as the inline colour of the per-view
+    path, for every SH degree and storage type."""
+    import torch
+    sc = sg.random_scene(95, 1500, 4000, n_objects=5, box=1.0, sphere_r=(0.3, 0.6), plane_side=(0.6, 1.2),
+                         surfel_scale=(0.03, 0.1), gauss_logscale=(-3.8, 0.4), sh_degree=deg)
+    dt = getattr(torch, dtype)
+    gs = R.GESScene.from_arrays(sc, attr_dtype=dt, sh_dtype=dt)
+    _check(R, [gs], _views()[:3], [0, 0, 0], None, reps=1)
+    gs.close()
+
+
+def test_batch_colour_pass_groups_views_by_scene_arrays(R):
+    """Views are grouped for the colour pass by the arrays their scenes view:
+    two scene handles on the same tensors share one group, a scene with the
+    same positions but other SH does not; ges_render_batch rebuilds its kept
+    graph when the grouping of the same view pattern changes."""
+    import torch
+    sc = _small(96, 1500, 4000)
+    ga = R.GESScene.from_arrays(sc)
+    gb = R.GESScene(sc.sh_degree, **ga.t)                     # the same tensors
+    t = dict(ga.t)
+    t["s_sh"] = (t["s_sh"] * 0.5).contiguous()
+    t["g_sh"] = (t["g_sh"] - 0.1).contiguous()
+    gc = R.GESScene(sc.sh_degree, **t)                       # same positions, other colours
+    views = _views()[:3]
+    _check(R, [ga, gb, gc], views + views[:2], [0, 1, 2, 0, 2], None, reps=1)
+    for scenes in ([ga, gb], [ga, gc], [ga, gb]):
+        outs = R.render_batch(scenes, views[:2], [0, 1])
+        torch.cuda.synchronize()
+        for v in range(2):
+            single = R.render(scenes[v], views[v], with_aux=False)
+            assert (outs[v][0] == single["rgb"]).all() and (outs[v][1] == single["depth"]).all(), v
+    for g in (ga, gb, gc):
+        g.close()
