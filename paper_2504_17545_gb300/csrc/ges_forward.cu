@@ -573,16 +573,10 @@ __device__ __forceinline__ void surfel_resolve(const SurfelZ<kS> &z, bool in_img
     }
 }
 
-// alpha 2^32 (an exact integer below 2^34) times a record colour (2^-16
-// units, below 2^25): the exact product, units of 2^-48.
-__device__ __forceinline__ unsigned long long mul_q(long long A, unsigned c)
-{
-    const unsigned lo = (unsigned)A, hi = (unsigned)((unsigned long long)A >> 32);
-    return (unsigned long long)lo * c + ((unsigned long long)(hi * c) << 32);
-}
-
-// Pass 2 sums of one lane, in 64-bit fixed point: W_G and the geometry sums
-// in units of 2^-32, the colour sums in units of 2^-48.
+// Pass 2 sums of one lane, in 64-bit fixed point: W_G in units of 2^-30
+// (each alpha rounded once to that grid), the colour sums in units of 2^-46
+// (that alpha times the record colour in 2^-16 units, an exact integer
+// product), the geometry sums in units of 2^-32.
 struct GaussAcc {
     long long r = 0, g = 0, b = 0, w = 0;
     long long d = 0, nx = 0, ny = 0, nz = 0;   // D_G, N_G (geometry maps)
@@ -637,12 +631,13 @@ __device__ __forceinline__ void gauss_pass(const Recs &R, int n, const WarpBlock
             // alpha * 2^32 is exact scaling: the clamp decision equals alpha >= alpha_min
             const float a32 = fminf(a * 4294967296.f, kAlpha32Max);
             if (B.in_img && a32 >= amin32 && ok != 0.f) {
-                // one exact conversion; the colour terms are integer products
-                const long long A = f2ll_rn(a32);
+                // alpha on the 2^-30 grid (alpha <= 2: below 2^31), one conversion;
+                // the colour terms are exact 32 x 32 -> 64-bit products
+                const unsigned A = __float2uint_rn(fminf(a, 2.f) * 1073741824.f);
                 acc.w += A;
-                acc.r += (long long)mul_q(A, cr);
-                acc.g += (long long)mul_q(A, cg);
-                acc.b += (long long)mul_q(A, cb);
+                acc.r += (long long)((unsigned long long)A * cr);
+                acc.g += (long long)((unsigned long long)A * cg);
+                acc.b += (long long)((unsigned long long)A * cb);
                 if (kGeo) {
                     acc.d += __float2ll_rn(a32 * depth);
                     acc.nx += f2ll_rn(a32 * side.x);
@@ -663,9 +658,10 @@ __device__ __forceinline__ void composite_store(const CamParams &C, const OptPar
                                                 float *__restrict__ aux, const GeoMaps &geo)
 {
     const float k32 = 2.3283064365386963e-10f;   // 2^-32
-    const float k48 = 3.5527136788005009e-15f;   // 2^-48
-    const float WG = __ll2float_rn(acc.w) * k32;
-    const float CG[3] = {__ll2float_rn(acc.r) * k48, __ll2float_rn(acc.g) * k48, __ll2float_rn(acc.b) * k48};
+    const float k30 = 9.3132257461547852e-10f;   // 2^-30
+    const float k46 = 1.4210854715202004e-14f;   // 2^-46
+    const float WG = __ll2float_rn(acc.w) * k30;
+    const float CG[3] = {__ll2float_rn(acc.r) * k46, __ll2float_rn(acc.g) * k46, __ll2float_rn(acc.b) * k46};
     float out[3];
     if (O.mode == GES_MODE_FULL) {
         const float inv = 1.f / (1.f + WG);

@@ -271,14 +271,15 @@ __device__ __forceinline__ unsigned long long global_timer_ns()
     return t;
 }
 
-// Range of the Gaussian pass's fixed-point terms: alpha 2^32 (an exact
-// integer once alpha >= 1/255) is capped at 2^33 and converted exactly
-// (f2ll_rn) into W_G's sum (units of 2^-32); a Gaussian's colour sits in its
-// raster record as an integer of 2^-16 units, capped at kColourMax, and the
-// colour sums add the exact integer products (units of 2^-48).  The sums are
-// therefore exact while sum alpha < 2^31 and sum alpha c < 2^15 per pixel and
-// channel, far outside the method's range (alpha <= 1, colours of a few
-// units).
+// Range of the Gaussian pass's fixed-point terms: each alpha >= alpha_min,
+// capped at 2, is rounded once to the 2^-30 grid (an unsigned 32-bit
+// integer) and added into W_G's sum; a Gaussian's colour sits in its raster
+// record as an integer of 2^-16 units, capped at kColourMax, and the colour
+// sums add the exact 64-bit products of the two (units of 2^-46).  The sums
+// are therefore exact and order independent while sum alpha < 2^33 and
+// sum alpha c < 2^17 per pixel and channel, far outside the method's range
+// (alpha <= 1, colours of a few units).  The geometry maps' sums keep alpha
+// 2^32 (kAlpha32Max) for their own terms.
 constexpr float kColourMax = 256.f;
 constexpr float kAlpha32Max = 8589934592.f;   // 2^33
 constexpr float kColourScale = 65536.f;       // 2^16
