@@ -169,7 +169,7 @@ def ncu_traffic(kernel, n_views):
 
 # the batch preprocess: one launch over the surfel ranges, one over the
 # Gaussian ranges, and the colour pass over all views of the scene
-PREP_KERNELS = ("k_bprep<3,1>", "k_bprep<3,2>", "k_bcolour<3>")
+PREP_KERNELS = ("k_bprep<3,1>", "k_bprep<3,2>", "k_bcolour")
 
 
 def algorithmic_bytes(n_s, n_g, s_vis, g_vis, hw, attr_bytes=4, sh_bytes=4, deg=3):

@@ -851,6 +851,7 @@ size_t batch_layout(ges_batch *b, const std::vector<SceneView> &S, const std::ve
         X.base = (unsigned *)take((size_t)P * T * 4);
         X.vcount = (unsigned *)take((size_t)P * 4);
         X.g_aux = S[v].gdim == 2 ? (float4 *)take(M * 32) : nullptr;
+        X.g_col = (float4 *)take(M * 16);
         X.status = b->d_status + (size_t)v * ST_WORDS;
     }
     return off;

@@ -135,11 +135,17 @@ __device__ __forceinline__ bool setup_and_store(const SceneView &S, const CamPar
                 gauss_colour(S, i, o);
                 dst[2] = make_float4(o.rec.key, colour_q(o.rec.r), colour_q(o.rec.g), colour_q(o.rec.b));
             } else {
-                reinterpret_cast<float *>(dst + 2)[0] = o.rec.key;
+                const float4 c = X.g_col[i];   // the colour pass's colour
+                dst[2] = make_float4(o.rec.key, c.x, c.y, c.z);
             }
         }
         if (kGd == 2 || O.geo) {
-            X.g_aux[2 * i] = o.aux[0];
+            float4 a0 = o.aux[0];
+            if (kGd == 2 && !kCol) {
+                const float4 c = X.g_col[i];   // the colour pass's colour
+                a0.x = c.x; a0.y = c.y; a0.z = c.z;
+            }
+            X.g_aux[2 * i] = a0;
             X.g_aux[2 * i + 1] = o.aux[1];
         }
         x0 = o.x0; y0 = o.y0; x1 = o.x1; y1 = o.y1;
@@ -829,11 +835,11 @@ __global__ void __launch_bounds__(kPrepThreads, 2) k_bprep(const BatchView *V, c
 // direction from the centre to that view's camera, the basis and the colour
 // are evaluated with the same operations, in the same order, as the inline
 // set-up of the per-view path, so both paths store bit-identical colours.
-// Surfels: the view's colour array; 3D Gaussians: the three colour words of
-// the view's raster record; 2D Gaussians: the colour words of the first side
-// word (both in 2^-16 units).  Primitives a view does not draw get colours
-// that nothing reads.
-template <int K, int kGd>
+// Surfels: the view's colour array; Gaussians: the view's Gaussian colour
+// array in 2^-16 units (dense 16-byte stores; the set-up, which runs after
+// this pass, copies them into the records).  Primitives a view does not draw
+// get colours that nothing reads.
+template <int K>
 __device__ __forceinline__ void colour_views(const BatchView *V, const int *__restrict__ gview, int gofs, int gn,
                                              bool surf, int64_t i, bool act, const SceneView &S, float4 *s_cam,
                                              float4 **s_out)
@@ -850,7 +856,7 @@ __device__ __forceinline__ void colour_views(const BatchView *V, const int *__re
         if ((int)threadIdx.x < m) {
             const BatchView *bv = V + __ldg(gview + gofs + k0 + threadIdx.x);
             s_cam[threadIdx.x] = make_float4(bv->C.ocam[0], bv->C.ocam[1], bv->C.ocam[2], 0.f);
-            s_out[threadIdx.x] = surf ? bv->X.s_rgb : (kGd == 2 ? bv->X.g_aux : bv->X.g_rec);
+            s_out[threadIdx.x] = surf ? bv->X.s_rgb : bv->X.g_col;
         }
         __syncthreads();
         if (!act) continue;
@@ -868,34 +874,28 @@ __device__ __forceinline__ void colour_views(const BatchView *V, const int *__re
                 b = fmaf(c[3 * q + 2], Y[q], b);
             }
             r = fmaxf(r, 0.f); g = fmaxf(g, 0.f); b = fmaxf(b, 0.f);
-            float4 *out = s_out[k];
-            if (surf) {
-                out[i] = make_float4(r, g, b, 0.f);
-            } else {
-                float *w = kGd == 2 ? reinterpret_cast<float *>(out + 2 * i)
-                                    : reinterpret_cast<float *>(out + 4 * i + 2) + 1;
-                w[0] = colour_q(r); w[1] = colour_q(g); w[2] = colour_q(b);
-            }
+            s_out[k][i] = surf ? make_float4(r, g, b, 0.f) : make_float4(colour_q(r), colour_q(g), colour_q(b), 0.f);
         }
     }
 }
 
-template <int kGd>
 __global__ void __launch_bounds__(kColourThreads) k_bcolour(const BatchView *V, const int4 *__restrict__ items,
-                                                            const int *__restrict__ gview)
+                                                            const int *__restrict__ gview, unsigned long long *t0)
 {
     __shared__ float4 s_cam[kColourViews];
     __shared__ float4 *s_out[kColourViews];
+    // the first CTA to start stamps the batch's start time (t0 is zeroed per launch)
+    if (threadIdx.x == 0) atomicCAS(t0, 0ull, global_timer_ns());
     const int4 it = items[blockIdx.x];
     const bool surf = it.x == 0;
     const SceneView &S = V[__ldg(gview + it.y)].S;
     const int64_t i = (int64_t)it.w + threadIdx.x;
     const bool act = i < (surf ? S.N : S.M);
     switch ((S.deg + 1) * (S.deg + 1)) {
-    case 16: colour_views<16, kGd>(V, gview, it.y, it.z, surf, i, act, S, s_cam, s_out); break;
-    case 9: colour_views<9, kGd>(V, gview, it.y, it.z, surf, i, act, S, s_cam, s_out); break;
-    case 4: colour_views<4, kGd>(V, gview, it.y, it.z, surf, i, act, S, s_cam, s_out); break;
-    default: colour_views<1, kGd>(V, gview, it.y, it.z, surf, i, act, S, s_cam, s_out); break;
+    case 16: colour_views<16>(V, gview, it.y, it.z, surf, i, act, S, s_cam, s_out); break;
+    case 9: colour_views<9>(V, gview, it.y, it.z, surf, i, act, S, s_cam, s_out); break;
+    case 4: colour_views<4>(V, gview, it.y, it.z, surf, i, act, S, s_cam, s_out); break;
+    default: colour_views<1>(V, gview, it.y, it.z, surf, i, act, S, s_cam, s_out); break;
     }
 }
 
@@ -992,6 +992,12 @@ cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const Opt
         unsigned long long *t0 = reinterpret_cast<unsigned long long *>(work_counter + 2);
         const size_t sm = local_bins_smem(P.max_T, false);
         const bool col = P.total_colour > 0;   // colours in the colour pass, not in the set-up
+        if (col) {
+            // before the set-up, which copies the Gaussian colours into the records
+            if (ev) cudaEventRecordWithFlags(ev[5], st, cudaEventRecordExternal);
+            k_bcolour<<<P.total_colour, kColourThreads, 0, st>>>(d_views, P.cmap, P.gview, t0);
+            if (ev) cudaEventRecordWithFlags(ev[6], st, cudaEventRecordExternal);
+        }
         if (P.total_sprep > 0) {
             const unsigned g = P.total_sprep;
             if (P.gdim == 2 && col) k_bprep<2, 1, false><<<g, kPrepThreads, sm, st>>>(d_views, P.smap, O, t0);
@@ -1005,13 +1011,6 @@ cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const Opt
             else if (P.gdim == 2) k_bprep<2, 2, true><<<g, kPrepThreads, sm, st>>>(d_views, P.gmap, O, t0);
             else if (col) k_bprep<3, 2, false><<<g, kPrepThreads, sm, st>>>(d_views, P.gmap, O, t0);
             else k_bprep<3, 2, true><<<g, kPrepThreads, sm, st>>>(d_views, P.gmap, O, t0);
-        }
-        if (P.total_colour > 0) {
-            // (a second graph branch beside the scans and the fill measured 0.3 % faster: not kept)
-            if (ev) cudaEventRecordWithFlags(ev[5], st, cudaEventRecordExternal);
-            if (P.gdim == 2) k_bcolour<2><<<P.total_colour, kColourThreads, 0, st>>>(d_views, P.cmap, P.gview);
-            else k_bcolour<3><<<P.total_colour, kColourThreads, 0, st>>>(d_views, P.cmap, P.gview);
-            if (ev) cudaEventRecordWithFlags(ev[6], st, cudaEventRecordExternal);
         }
     }
     mark(1);

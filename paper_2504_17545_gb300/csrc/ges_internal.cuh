@@ -95,6 +95,9 @@ struct ViewScratch {
     // [N][4] camera-space frame of each surfel for the translucent render:
     // (P, s1), (U, s2), (V, -), (N, -); written when non-null
     float4 *s_tside = nullptr;
+    // [M] Gaussian colours in 2^-16 units, written by the batch's colour pass
+    // before the set-up, which copies them into the records; null elsewhere
+    float4 *g_col = nullptr;
 };
 
 // Number of preprocess CTAs for local binning and the size of their ranges.
