@@ -389,6 +389,13 @@ GES_API ges_status ges_batch_create(ges_scene *const *scenes, const ges_camera *
  * is in flight (after ges_batch_sync). */
 GES_API ges_status ges_batch_set_camera(ges_batch *batch, int32_t view, const ges_camera *cam);
 
+/* Also write the surfel id map out_surfel_id [samples,H,W] (z-buffer winner of
+ * each sample, -1 where none) and aux [H,W] (W_G of Eq. 3) of one view in the
+ * following launches, as ges_render_ex does; DEVICE pointers owned by the
+ * caller, either may be NULL (not written).  Call it when no launch of this
+ * batch is in flight. */
+GES_API ges_status ges_batch_set_id_output(ges_batch *batch, int32_t view, int32_t *out_surfel_id, float *aux);
+
 /* Enqueue one replay of the batch's graph on `stream` (cudaStream_t). */
 GES_API ges_status ges_batch_launch(ges_batch *batch, void *stream);
 

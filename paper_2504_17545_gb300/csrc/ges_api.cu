@@ -1063,6 +1063,8 @@ static ges_status batch_create(ges_scene *const *scenes, const ges_camera *cams,
     for (int v = 0; v < n_views; ++v) {
         b->views[v].rgb = out_rgb[v];
         b->views[v].depth = out_depth ? out_depth[v] : nullptr;
+        b->views[v].id = nullptr;
+        b->views[v].aux = nullptr;
     }
     // arena sized for the smallest primitives-per-CTA tried (most histogram rows)
     const int64_t kRall[] = {4096, 8192, 16384, 32768, 60000}, kRone[] = {8192};
@@ -1215,6 +1217,17 @@ ges_status ges_batch_set_camera(ges_batch *b, int32_t view, const ges_camera *ca
                     b->views[view].C.H);
     b->views[view].C = C;
     b->h_table[view].C = C;
+    return GES_OK;
+}
+
+ges_status ges_batch_set_id_output(ges_batch *b, int32_t view, int32_t *out_surfel_id, float *aux)
+{
+    if (!b) return fail(GES_ERR_INVALID_ARG, "batch is NULL");
+    if (view < 0 || view >= b->n) return fail(GES_ERR_INVALID_ARG, "view %d out of range", view);
+    b->views[view].id = out_surfel_id;
+    b->views[view].aux = aux;
+    b->h_table[view].id = out_surfel_id;
+    b->h_table[view].aux = aux;
     return GES_OK;
 }
 

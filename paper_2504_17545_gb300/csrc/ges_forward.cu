@@ -966,7 +966,7 @@ __global__ void __launch_bounds__(kRasterThreads, kS == 1 && kG == 3 ? 5 : 4) k_
         }
         __syncthreads();
         if (!(bv.X.status[ST_FLAGS] & (FLAG_SOVF | FLAG_GOVF)))
-            raster_tile<kS, kG, false>(bv.X, bv.C, O, bv.rgb, bv.depth, nullptr, nullptr, GeoMaps{}, it - bv.tile_base,
+            raster_tile<kS, kG, false>(bv.X, bv.C, O, bv.rgb, bv.depth, bv.id, bv.aux, GeoMaps{}, it - bv.tile_base,
                                        ss, sgs);
         __syncthreads();
         if (threadIdx.x == 0) {

@@ -115,6 +115,8 @@ struct BatchView {
     ViewScratch X;
     LocalBins B;
     float *rgb, *depth;
+    int32_t *id;          // surfel id map [samples,H,W] or null (ges_batch_set_id_output)
+    float *aux;           // W_G [H,W] or null
     int T, tile_base, prep_base, colscan_base;
     int sprep_base, gprep_base;   // first CTA of the view's surfel / Gaussian ranges in their own launches
 };

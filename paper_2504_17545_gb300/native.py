@@ -104,6 +104,7 @@ _SIGS = {
     "ges_batch_create": (C.c_int, [_P(C.c_void_p), _P(ges_camera), _P(C.c_int32), C.c_int32,
                                    _P(ges_render_opts), _P(C.c_void_p), _P(C.c_void_p), _P(C.c_void_p)]),
     "ges_batch_set_camera": (C.c_int, [C.c_void_p, C.c_int32, _P(ges_camera)]),
+    "ges_batch_set_id_output": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "ges_batch_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ges_batch_sync": (C.c_int, [C.c_void_p]),
     "ges_batch_get_info": (C.c_int, [C.c_void_p, _P(ges_batch_info)]),
@@ -281,6 +282,10 @@ def ges_batch_create(scenes, cams, scene_of_view, opts, out_rgb, out_depth):
 
 def ges_batch_set_camera(batch, view: int, cam: ges_camera):
     _check(load().ges_batch_set_camera(batch, int(view), C.byref(cam)))
+
+
+def ges_batch_set_id_output(batch, view: int, out_surfel_id: int, aux: int):
+    _check(load().ges_batch_set_id_output(batch, int(view), out_surfel_id or None, aux or None))
 
 
 def ges_batch_launch(batch, stream: int):

@@ -347,6 +347,15 @@ class GESBatch:
     def set_camera(self, view: int, cam):
         N.ges_batch_set_camera(self.handle, view, camera_struct(cam))
 
+    def set_id_output(self, view: int, out_id: Optional[torch.Tensor], aux: Optional[torch.Tensor] = None):
+        """Also write view ``view``'s surfel id map (int32 [samples,H,W]) and
+        W_G (float32 [H,W]) in the following launches (None: not written).
+        The tensors must stay alive while they are set."""
+        self._id_keep = getattr(self, "_id_keep", {})
+        self._id_keep[view] = (out_id, aux)
+        N.ges_batch_set_id_output(self.handle, view, out_id.data_ptr() if out_id is not None else 0,
+                                  aux.data_ptr() if aux is not None else 0)
+
     def info(self):
         return N.ges_batch_get_info(self.handle)
 

@@ -83,26 +83,42 @@ def test_batch_raster_2d_gaussians(R):
 
 def test_timed_orbit_path_matches_oracle(R):
     """The benchmark's own path: a batch graph over views of the 1M-surfel /
-    300k-Gaussian 1080p orbit.  One view against the oracle directly (colour
-    and depth; the batch keeps no id map), every view bitwise equal to its
-    per-view render, and the per-view completion stamps sane."""
+    300k-Gaussian 1080p orbit.  One view against the oracle directly (colour,
+    depth and the surfel id map the batch writes when asked), every view
+    bitwise equal to its per-view render (ids and W_G too where written), and
+    the per-view completion stamps sane."""
+    import torch
     import oracle
     from parity import MASKED_MAX, compare
     scene, cams = sg.config_scene(1)
     gs = R.GESScene.from_arrays(scene)
     views = [cams[k] for k in (0, 16, 33, 50)]
     b = R.GESBatch([gs], views)
+    ids = {v: torch.empty((views[v].height, views[v].width), dtype=torch.int32, device="cuda") for v in (1, 2)}
+    aux = torch.empty((views[2].height, views[2].width), device="cuda")
+    b.set_id_output(1, ids[1])
+    b.set_id_output(2, ids[2], aux)
     b.launch()
     b.sync()
     t = b.view_times()
     assert all(0.0 < x < 1000.0 for x in t), t
     for v in range(len(views)):
-        single = R.render(gs, views[v], with_aux=False)
+        single = R.render(gs, views[v], with_aux=True)
         assert (b.rgb[v] == single["rgb"]).all() and (b.depth[v] == single["depth"]).all(), v
+        if v in ids:
+            assert (ids[v] == single["id"]).all(), v
+        if v == 2:
+            assert (aux == single["aux"]).all()
     ref = oracle.render(scene, views[2])
-    res = compare(scene, views[2], dict(rgb=b.rgb[2], depth=b.depth[2]), ref, check_ids=False)
+    res = compare(scene, views[2], dict(rgb=b.rgb[2], depth=b.depth[2], id=ids[2]), ref)
     assert res["pass"], res
     assert res["masked_frac"] <= MASKED_MAX
+    # switched off again: the next launch leaves the arrays alone
+    b.set_id_output(1, None)
+    ids[1].fill_(-7)
+    b.launch()
+    b.sync()
+    assert (ids[1] == -7).all()
     b.close()
     gs.close()
 
