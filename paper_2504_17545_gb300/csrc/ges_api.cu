@@ -780,6 +780,9 @@ struct ges_batch {
     // both launches, the colour pass's work items and view groups
     unsigned char *d_map = nullptr;
     size_t map_bytes = 0;                  // capacity
+    BatchPlan plan{};                      // of the kept graph
+    OptParams opt{};
+    bool ids = false;                      // the kept graph's raster writes id maps / W_G where asked
 };
 
 namespace {
@@ -861,6 +864,25 @@ size_t batch_layout(ges_batch *b, const std::vector<SceneView> &S, const std::ve
 // counts) take each primitive range one after another, so only the first of
 // them reads the range's attributes from HBM; surfel CTAs first, then the
 // Gaussian ones (their own launch).  Uploads the map; P gets its pointers.
+// Capture one replay of the batch (table upload, status reset, the kernels of
+// launch_batch, status read-back) as an executable graph.
+cudaError_t capture_exec(ges_batch *b, const BatchPlan &P, const OptParams &O, bool ids, cudaGraphExec_t *out)
+{
+    const size_t status_words = (size_t)b->n * ST_WORDS + 16;
+    cudaGraph_t g = nullptr;
+    *out = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaMemcpyAsync(b->d_table, b->h_table, sizeof(BatchView) * b->n, cudaMemcpyHostToDevice, b->stream);
+    cudaMemsetAsync(b->d_status, 0, status_words * 4, b->stream);
+    launch_batch(b->d_table, P, O, b->d_status + (size_t)b->n * ST_WORDS, b->stream, b->phase, ids);
+    cudaMemcpyAsync(b->h_status, b->d_status, status_words * 4, cudaMemcpyDeviceToHost, b->stream);
+    if ((e = cudaStreamEndCapture(b->stream, &g)) != cudaSuccess) return e;
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return e;
+}
+
 // Bytes of the maps (see ges_batch::d_map) for n_prep preprocess CTAs,
 // n_items colour items and n views; the parts start 16-byte aligned.
 size_t map_layout(size_t n_prep, size_t n_items, size_t n, size_t *off_items, size_t *off_gview)
@@ -1111,16 +1133,8 @@ static ges_status batch_create(ges_scene *const *scenes, const ges_camera *cams,
             }
             std::memcpy(b->h_table, b->views.data(), sizeof(BatchView) * n_views);
             BATCH_CUDA(upload_prep_map(b, P));
-            cudaGraph_t g = nullptr;
             cudaGraphExec_t ex = nullptr;
-            BATCH_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-            cudaMemcpyAsync(b->d_table, b->h_table, sizeof(BatchView) * n_views, cudaMemcpyHostToDevice, b->stream);
-            cudaMemsetAsync(b->d_status, 0, status_words * 4, b->stream);
-            launch_batch(b->d_table, P, O, b->d_status + (size_t)n_views * ST_WORDS, b->stream, b->phase);
-            cudaMemcpyAsync(b->h_status, b->d_status, status_words * 4, cudaMemcpyDeviceToHost, b->stream);
-            BATCH_CUDA(cudaStreamEndCapture(b->stream, &g));
-            e = cudaGraphInstantiate(&ex, g, 0);
-            cudaGraphDestroy(g);
+            e = capture_exec(b, P, O, false, &ex);
             if (e != cudaSuccess) {
                 batch_release(b);
                 return cuda_fail(e, "cudaGraphInstantiate");
@@ -1158,6 +1172,7 @@ static ges_status batch_create(ges_scene *const *scenes, const ges_camera *cams,
                 b->tsy = sh.second;
                 b->info.tile_w = 1 << sh.first;
                 b->info.tile_h = 1 << sh.second;
+                b->plan = P;
             } else {
                 cudaGraphExecDestroy(ex);
             }
@@ -1178,6 +1193,7 @@ static ges_status batch_create(ges_scene *const *scenes, const ges_camera *cams,
         }
         BATCH_CUDA(upload_prep_map(b, P));
     }
+    b->opt = O;
     b->info.n_views = n_views;
     b->info.candidates = cand;
     b->info.tuned_ms = best_ms;
@@ -1228,6 +1244,19 @@ ges_status ges_batch_set_id_output(ges_batch *b, int32_t view, int32_t *out_surf
     b->views[view].aux = aux;
     b->h_table[view].id = out_surfel_id;
     b->h_table[view].aux = aux;
+    // the raster that writes them is a kernel of its own (the timed one keeps
+    // its registers): re-capture the graph when the need for it changes
+    bool want = false;
+    for (int v = 0; v < b->n; ++v) want = want || b->views[v].id || b->views[v].aux;
+    if (want != b->ids) {
+        if (b->done) GES_CUDA(cudaEventSynchronize(b->done));
+        cudaGraphExec_t ex = nullptr;
+        cudaError_t e = capture_exec(b, b->plan, b->opt, want, &ex);
+        if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+        cudaGraphExecDestroy(b->exec);
+        b->exec = ex;
+        b->ids = want;
+    }
     return GES_OK;
 }
 

@@ -938,7 +938,7 @@ __global__ void __launch_bounds__(kFillThreads) k_bfill(const BatchView *V, int 
 // Persistent raster over the (view, tile) items of the whole batch: each CTA
 // takes the next item from a counter until none is left, so uneven views
 // balance across the GPU.
-template <int kS, int kG>
+template <int kS, int kG, bool kIds>
 __global__ void __launch_bounds__(kRasterThreads, kS == 1 && kG == 3 ? 5 : 4) k_braster(const BatchView *V, int n, OptParams O,
                                                             unsigned *counter, int total)
 {
@@ -966,7 +966,8 @@ __global__ void __launch_bounds__(kRasterThreads, kS == 1 && kG == 3 ? 5 : 4) k_
         }
         __syncthreads();
         if (!(bv.X.status[ST_FLAGS] & (FLAG_SOVF | FLAG_GOVF)))
-            raster_tile<kS, kG, false>(bv.X, bv.C, O, bv.rgb, bv.depth, bv.id, bv.aux, GeoMaps{}, it - bv.tile_base,
+            raster_tile<kS, kG, false>(bv.X, bv.C, O, bv.rgb, bv.depth, kIds ? bv.id : nullptr,
+                                       kIds ? bv.aux : nullptr, GeoMaps{}, it - bv.tile_base,
                                        ss, sgs);
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -983,7 +984,7 @@ __global__ void __launch_bounds__(kRasterThreads, kS == 1 && kG == 3 ? 5 : 4) k_
 }  // namespace
 
 cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const OptParams &O, unsigned *work_counter,
-                         cudaStream_t st, cudaEvent_t *ev)
+                         cudaStream_t st, cudaEvent_t *ev, bool ids)
 {
     // ev (7 events or null): recorded as graph event nodes when captured
     auto mark = [&](int k) { if (ev) cudaEventRecordWithFlags(ev[k], st, cudaEventRecordExternal); };
@@ -1022,10 +1023,18 @@ cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const Opt
     mark(3);
     // P.gdim: the Gaussian kind shared by all scenes of the batch
     const unsigned grid = P.raster_ctas;
-    if (O.samples == 4 && P.gdim == 2) k_braster<4, 2><<<grid, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
-    else if (O.samples == 4) k_braster<4, 3><<<grid, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
-    else if (P.gdim == 2) k_braster<1, 2><<<grid, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
-    else k_braster<1, 3><<<grid, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles);
+    const int kind = (O.samples == 4 ? 2 : 0) + (P.gdim == 2 ? 1 : 0);
+    auto go = [&](auto kern) { kern<<<grid, kRasterThreads, 0, st>>>(d_views, P.n, O, work_counter, P.total_tiles); };
+    switch (kind + (ids ? 4 : 0)) {
+    case 0: go(k_braster<1, 3, false>); break;
+    case 1: go(k_braster<1, 2, false>); break;
+    case 2: go(k_braster<4, 3, false>); break;
+    case 3: go(k_braster<4, 2, false>); break;
+    case 4: go(k_braster<1, 3, true>); break;
+    case 5: go(k_braster<1, 2, true>); break;
+    case 6: go(k_braster<4, 3, true>); break;
+    default: go(k_braster<4, 2, true>); break;
+    }
     mark(4);
     return cudaGetLastError();
 }

@@ -142,8 +142,10 @@ constexpr int kColourThreads = 256;   // primitives per colour-pass CTA
 constexpr int kColourViews = 64;      // views whose camera centres a colour-pass CTA stages at a time
 // ev: 7 events recorded as graph event nodes (phase boundaries 0-4, the
 // colour pass's start and end 5-6) or nullptr.
+// ids: the raster also writes the views' id maps and W_G where BatchView
+// points to them (a raster kernel of its own).
 cudaError_t launch_batch(const BatchView *d_views, const BatchPlan &P, const OptParams &O, unsigned *work_counter,
-                         cudaStream_t st, cudaEvent_t *ev);
+                         cudaStream_t st, cudaEvent_t *ev, bool ids);
 LocalBins plan_local_bins_per_cta(int64_t N, int64_t M, int64_t prims_per_cta);
 constexpr int kPrepThreads = 512;
 constexpr int kFillThreads = 1024;
