@@ -65,6 +65,10 @@ def test_null_handles():
     assert lib.ges_get_stats(None, None) == N.GES_ERR_INVALID_ARG
     assert lib.ges_render_batch(None, None, None, 0, None, None, None) == N.GES_ERR_INVALID_ARG
     assert lib.ges_default_opts(None) == N.GES_ERR_INVALID_ARG
+    assert lib.ges_batch_set_camera(None, 0, None) == N.GES_ERR_INVALID_ARG
+    assert lib.ges_batch_set_id_output(None, 0, None, None) == N.GES_ERR_INVALID_ARG
+    assert "batch is NULL" in N.ges_last_error_message()
+    assert lib.ges_batch_launch(None, None) == N.GES_ERR_INVALID_ARG
 
 
 def test_without_a_device_creation_fails_cleanly():
