@@ -222,3 +222,15 @@ def test_batch_colour_pass_groups_views_by_scene_arrays(R):
             assert (outs[v][0] == single["rgb"]).all() and (outs[v][1] == single["depth"]).all(), v
     for g in (ga, gb, gc):
         g.close()
+
+
+def test_batch_colour_pass_more_views_than_one_staging_round(R):
+    """A scene with 70 views: the colour pass stages the views' camera centres
+    64 at a time, so a second round covers the last 6; every view's image
+    equals its per-view render."""
+    sc = _small(97, 800, 2000)
+    gs = R.GESScene.from_arrays(sc)
+    views = [sg.look_at((2.6 * np.sin(a), 0.3 * np.cos(3 * a), -2.6 * np.cos(a)), (0, 0, 0), (0, 1, 0), 40, 24, 55.0)
+             for a in np.linspace(0.0, 2.0 * np.pi, 70, endpoint=False)]
+    _check(R, [gs], views, [0] * 70, None, reps=1)
+    gs.close()
