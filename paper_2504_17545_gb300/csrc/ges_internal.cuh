@@ -727,11 +727,12 @@ __device__ __forceinline__ void surfel_geom(const SceneView &S, const CamParams 
 {
     o.visible = false;
     o.valid_quat = true;
+    // every attribute load is issued before the first use (one round trip)
     const float px = __ldg(S.s_pos + 3 * i), py = __ldg(S.s_pos + 3 * i + 1), pz = __ldg(S.s_pos + 3 * i + 2);
     float q[4], R[9];
     for (int k = 0; k < 4; ++k) q[k] = load_attr(S.s_rot, 4 * i + k, S.attr_dtype);
-    if (!quat_to_rot(q[0], q[1], q[2], q[3], R, nullptr, nullptr)) { o.valid_quat = false; return; }
     const float s1 = load_attr(S.s_scale, 2 * i, S.attr_dtype), s2 = load_attr(S.s_scale, 2 * i + 1, S.attr_dtype);
+    if (!quat_to_rot(q[0], q[1], q[2], q[3], R, nullptr, nullptr)) { o.valid_quat = false; return; }
     // view direction for the SH colour: from the surfel centre to the camera
     {
         float L;
@@ -804,12 +805,13 @@ __device__ __forceinline__ void gauss_geom(const SceneView &S, const CamParams &
 {
     o.visible = false;
     o.valid_quat = true;
+    // every attribute load is issued before the first use (one round trip)
     const float px = __ldg(S.g_pos + 3 * i), py = __ldg(S.g_pos + 3 * i + 1), pz = __ldg(S.g_pos + 3 * i + 2);
     float q[4];
     for (int k = 0; k < 4; ++k) q[k] = load_attr(S.g_rot, 4 * i + k, S.attr_dtype);
-    if (!quat_to_rot(q[0], q[1], q[2], q[3], o.R, o.qn, &o.qnorm)) { o.valid_quat = false; return; }
     for (int k = 0; k < 3; ++k) o.s[k] = load_attr(S.g_scale, 3 * i + k, S.attr_dtype);
     float sigma = load_attr(S.g_opac, i, S.attr_dtype);
+    if (!quat_to_rot(q[0], q[1], q[2], q[3], o.R, o.qn, &o.qnorm)) { o.valid_quat = false; return; }
     o.sigma0 = sigma;
     o.k3 = 1.f; o.k2 = 1.f;
     o.se[0] = o.s[0]; o.se[1] = o.s[1]; o.se[2] = o.s[2];
