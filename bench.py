@@ -204,7 +204,7 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "views_per_step": 1, "resolution": "1920x1080"},
             "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} full 1080p orbit views, FP64, OpenMP over all host cores"},
+                             "sample": f"{args.steps} full 1080p orbit view{'' if args.steps == 1 else 's'} (one per step), FP64, OpenMP over all host cores"},
             "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
