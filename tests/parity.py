@@ -23,10 +23,15 @@ COL_TOL = 2e-4       # colour tolerance of the FP32 path (absolute, per channel)
 # centre), the three terms are at most 1.5 times 1/z at a pixel of the disc,
 # the two FMAs add 2u and the reciprocal 2u: 6u x 4 + 2u + 2u = 28u = 1.7e-6.
 DEPTH_REL = 2e-6
-# The frame's rounding (eps_f = 20u) tilts the plane about the centre; at a
-# pixel theta (at most ~0.3 rad for the discs here) from the centre's ray the
-# depth moves by eps_f theta / |cos| = 6u / |cos| = 3.6e-7 / |cos|.
+# The frame's rounding (normal n off by at most eps_f = 20u) tilts the plane
+# about the centre P: the hit X = t d moves in depth by eps_f |X - P| /
+# (|X| |cos|) relative (t = n.P / n.d, and d / n.d = X / n.P).  For discs small
+# against their distance |X - P| / |X| <= 0.3: 6u / |cos| = 3.6e-7 / |cos|.
+# Larger ratios (a disc reaching past the camera from a centre behind it) scale
+# the term; the ratio is bounded by sqrt(rho) s_max / z (rho = a^2 + b^2 at X,
+# z its depth).
 DEPTH_GRAZE = 4e-7
+GRAZE_RATIO = 0.3
 
 
 # Bound on the fraction of pixels the oracle flags as ambiguous (excluded from
@@ -79,15 +84,19 @@ def compare(scene, cam, gpu, ref, opts=None, col_tol=COL_TOL, depth_rel=DEPTH_RE
         jj, ii = np.nonzero(cov)
         rid = ref["id"] if ref["id"].ndim == 3 else ref["id"][None]
         cmin = np.full(jj.size, np.inf)
+        gmax = np.zeros(jj.size)      # max over the samples of max(ratio, 0.3) / |cos|
+        smax = np.abs(np.asarray(scene.s_scale, np.float64)).max(1) if scene.n_surfels else np.zeros(0)
         for k in range(rid.shape[0]):
             sid = rid[k][jj, ii]
             m = sid >= 0
             if m.any():
-                _, _, nd, ok = oracle.surfel_eval(scene, cam, ii[m], jj[m], sid[m], opts)
+                zk, rho, nd, ok = oracle.surfel_eval(scene, cam, ii[m], jj[m], sid[m], opts)
                 c = np.where(ok != 0, np.abs(nd), 0.0)
-                cm = cmin[m]
-                cmin[m] = np.minimum(cm, c)
-        bound = depth_rel + DEPTH_GRAZE / np.maximum(cmin, 1e-30)
+                cmin[m] = np.minimum(cmin[m], c)
+                ratio = np.sqrt(np.maximum(rho, 0.0)) * smax[sid[m]] / np.maximum(zk, 1e-30)
+                g = np.maximum(ratio, GRAZE_RATIO) / np.maximum(c, 1e-30)
+                gmax[m] = np.maximum(gmax[m], g)
+        bound = depth_rel + (DEPTH_GRAZE / GRAZE_RATIO) * gmax
         w = int(np.argmax(rel / bound))
         out["depth_excess"] = float(rel[w] / bound[w])
         out["depth_worst"] = dict(px=int(ii[w]), py=int(jj[w]), rel=float(rel[w]), cos=float(cmin[w]))

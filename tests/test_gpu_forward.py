@@ -106,6 +106,40 @@ def test_empty_and_degenerate_inputs(R):
     _assert(compare(sc, cam, _render(R, sc, cam), ref))
 
 
+def test_discs_at_and_behind_the_camera(R):
+    """Discs the random scenes rarely hold, each driving a branch of the
+    surfel set-up (Sec. 3; Sec. 4.1's opaque extent r): a disc whose centre
+    is behind the camera and whose far point at 0.9 r is behind the near
+    plane too (the forms evaluated at the image centre); one whose centre is
+    behind the camera but whose far point is in front (reference pixel at
+    that point); both reaching through the near plane, so their bboxes come
+    from the near-clipped rectangle; a disc crossing the near plane at an
+    angle; one wholly behind the camera; one seen edge-on."""
+    import camera_discs as cd
+    cam, base = cd.camera(), cd.background()
+    zn = cam.znear
+    discs = cd.walls()
+    ez = [cd.depth_extent(d) for d in discs]
+    zc = [d[0][2] for d in discs]
+    # the set-up's branch conditions, restated
+    assert zc[0] + ez[0] > zn and zc[0] + 0.9 * ez[0] <= 1.01 * zn
+    assert zc[1] < 0.5 * ez[1] + zn and zc[1] + 0.9 * ez[1] > 1.01 * zn and zc[1] - ez[1] < zn
+    assert zc[2] + ez[2] < zn
+    sc = cd.with_discs(base, discs, 37)
+    ref = oracle.render(sc, cam)
+    _assert(compare(sc, cam, _render(R, sc, cam), ref, max_masked=0.1))
+    n0 = base.n_surfels
+    won = (ref["amb"] & 1) == 0
+    assert (won & (ref["id"] == n0)).sum() > 50 and (won & (ref["id"] == n0 + 1)).sum() > 50
+    assert not (ref["id"] == n0 + 2).any()
+    tilt = cd.tilted()
+    assert tilt[0][0][2] - cd.depth_extent(tilt[0]) < zn
+    sc = cd.with_discs(base, tilt, 38)
+    ref = oracle.render(sc, cam)
+    _assert(compare(sc, cam, _render(R, sc, cam), ref, max_masked=0.1))
+    assert (((ref["amb"] & 1) == 0) & (ref["id"] == n0)).sum() > 50
+
+
 def test_zero_norm_quaternion_is_invalid_argument(R):
     from paper_2504_17545_gb300 import native as N
     sc = _small(34, 30, 30)

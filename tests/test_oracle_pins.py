@@ -228,6 +228,32 @@ def test_culled_equals_brute_force_bitwise(oracle_lib, seed):
                 np.testing.assert_array_equal(a[k], b[k], err_msg=f"{k} mode={mode}")
 
 
+def test_discs_at_and_behind_the_camera_brute_force_and_closed_form(oracle_lib):
+    """Discs reaching through the near plane from behind the camera, one
+    wholly behind it and one edge-on: the culled render equals brute force
+    bitwise, and where the wall in the plane x = 0.05 wins, its depth is the
+    ray-plane hit z = 0.05 fx / (u + 1/2 - cx) (a pixel ray (du, dv, 1)
+    meets x = 0.05 at t = 0.05 / du)."""
+    import camera_discs as cd
+    cam, base = cd.camera(), cd.background()
+    n0 = base.n_surfels
+    for discs, seed in ((cd.walls(), 37), (cd.tilted(), 38)):
+        sc = cd.with_discs(base, discs, seed)
+        a = oracle_lib.render(sc, cam, culled=True)
+        b = oracle_lib.render(sc, cam, culled=False)
+        for k in a:
+            np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    sc = cd.with_discs(base, cd.walls(), 37)
+    a = oracle_lib.render(sc, cam)
+    jj, ii = np.nonzero(a["id"] == n0)
+    assert jj.size > 1000
+    z = 0.05 * cam.fx / (ii + 0.5 - cam.cx)
+    # the scene is float32: the plane sits at float32(0.05), the frame at float32 rounding
+    np.testing.assert_allclose(a["depth"][jj, ii], z, rtol=1e-6)
+    assert not (a["id"] == n0 + 2).any()           # wholly behind the camera
+    assert not (a["id"] == n0 + 3).any()           # edge-on: no area on screen
+
+
 def test_culled_equals_brute_force_parity_workload(oracle_lib):
     sc, cams = sg.config_scene(0)
     a = oracle_lib.render(sc, cams[0], culled=True)
