@@ -54,6 +54,19 @@ def test_msaa_parity_ragged_and_modes(R, mode):
         _assert(compare(scene, cam, _render(R, scene, cam, opts), ref, opts, max_masked=mm))
 
 
+def test_msaa_discs_at_and_behind_the_camera(R):
+    """The hand-placed discs at and behind the camera (near-clipped bboxes
+    widened by the quarter-pixel sample offset, forms at the image centre or
+    at the far point) with 4 samples per pixel."""
+    import camera_discs as cd
+    cam, base = cd.camera(), cd.background()
+    for discs, seed in ((cd.walls(), 37), (cd.tilted(), 38)):
+        sc = cd.with_discs(base, discs, seed)
+        ref = oracle.render(sc, cam, MS)
+        _assert(compare(sc, cam, _render(R, sc, cam, MS), ref, MS, max_masked=0.1))
+        assert (ref["id"] == base.n_surfels).any(0).sum() > 50
+
+
 def test_msaa_parity_1080p_orbit_camera(R):
     """The 1M-surfel / 300k-Gaussian 1080p workload with 4 samples, one full
     frame of the orbit."""

@@ -67,6 +67,25 @@ def test_translucent_forward_matches_oracle(R, kind, seed, ff):
     assert res["compared"] > 0.9 * cam.width * cam.height
 
 
+@pytest.mark.parametrize("ff", [False, True])
+def test_translucent_discs_at_and_behind_the_camera(R, ff):
+    """The hand-placed discs at and behind the camera in the translucent
+    render: centres behind the camera have negative camera depths, which
+    must order before every other centre, and the walls reach through the
+    near plane."""
+    import camera_discs as cd
+    cam, base = cd.camera(), cd.background()
+    for discs, seed in ((cd.walls(), 37), (cd.tilted(), 38)):
+        sc = cd.with_discs(base, discs, seed)
+        w = np.random.default_rng(seed).uniform(0.3, 3.0, sc.n_surfels).astype(np.float32).astype(np.float64)
+        gs, out = _run(R, sc, cam, w, ff)
+        gs.close()
+        ref = oracle.render_translucent(sc, cam, w, ff)
+        res = _fwd_compare(out, ref)
+        assert res["pass"], json.dumps(res)
+        assert (ref["front"] == base.n_surfels).sum() > 50
+
+
 def test_translucent_w255_equals_opaque_render(R):
     """At w = 255 with the front-first order the translucent render equals the
     z-buffer render (surfels only), as the paper states for the end of the
