@@ -65,3 +65,38 @@ def tilted():
 def depth_extent(d, r=math.sqrt(2.0 * math.log(255.0))):
     """Half the camera-depth extent of disc d: r |(s1 tu_z, s2 tv_z)|."""
     return r * math.hypot(d[3][0] * d[1][2], d[3][1] * d[2][2])
+
+
+def flat(scene):
+    """The same scene with 2D Gaussians (the first two axes of each)."""
+    sc = scene.subset()
+    sc.g_scale = np.ascontiguousarray(sc.g_scale[:, :2])
+    return sc
+
+
+def with_splats(scene, splats, seed):
+    """2D-Gaussian scene plus splats = [(centre, tu, tv, (s1, s2), opacity)],
+    appended after the scene's own."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    tu = np.array([d[1] for d in splats], np.float64)
+    tv = np.array([d[2] for d in splats], np.float64)
+    q = sg._frame_to_quat(tu, tv, np.cross(tu, tv))
+    sh = np.zeros((len(splats),) + scene.g_sh.shape[1:], np.float32)
+    sh[:, 0, :] = rng.uniform(0.2, 1.0, (len(splats), 3))
+    f32 = lambda a: np.ascontiguousarray(np.asarray(a, np.float32))
+    out = scene.subset()
+    out.g_pos = f32(np.concatenate([scene.g_pos, [d[0] for d in splats]]))
+    out.g_rot = f32(np.concatenate([scene.g_rot, q]))
+    out.g_scale = f32(np.concatenate([scene.g_scale, [d[3] for d in splats]]))
+    out.g_opac = f32(np.concatenate([scene.g_opac, [d[4] for d in splats]]))
+    out.g_sh = f32(np.concatenate([scene.g_sh, sh]))
+    return out
+
+
+def splats():
+    """2D Gaussians with the centre in front of the camera that reach back
+    through the near plane: (0) a wall in the plane x = -0.05 whose centre
+    is 0.3 in front (reference pixel at the far point at 0.9 r), (1) a small
+    splat crossing the near plane at 60 degrees."""
+    return [((-0.05, 0.0, 0.3), (0, 0, 1), (0, -1, 0), (0.5, 0.3), 0.9),
+            ((0.03, 0.02, 0.03), (1, 0, 0), (0, 0.5, math.sqrt(0.75)), (0.02, 0.02), 0.8)]

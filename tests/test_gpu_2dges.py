@@ -107,6 +107,25 @@ def test_geometry_maps_ragged(R, dim, opts):
     _assert(compare_geom(out, oracle.render_geom(scene, cam, opts), ref))
 
 
+def test_2d_splats_reaching_through_the_near_plane(R):
+    """2D Gaussians whose centre is in front of the camera but whose extent
+    reaches back through the near plane (the set-up's reference pixel at the
+    far point, near-clipped bboxes; Sec. 6.4's ray-splat hit): the render
+    and the geometry maps against the oracle."""
+    import camera_discs as cd
+    cam, base = cd.camera(), cd.flat(cd.background())
+    ref0 = oracle.render(base, cam)
+    for k, sp in enumerate(cd.splats()):
+        sc = cd.with_splats(base, [sp], 40 + k)
+        ref = oracle.render(sc, cam)
+        assert (np.abs(ref["wg"] - ref0["wg"]) > 1e-3).sum() > 300     # the splat contributes
+        _assert(compare(sc, cam, _render(R, sc, cam), ref, max_masked=0.1))
+        gs = R.GESScene.from_arrays(sc)
+        out = R.render_geom(gs, cam)
+        gs.close()
+        _assert(compare_geom(out, oracle.render_geom(sc, cam), ref))
+
+
 def test_geometry_maps_1080p_orbit_camera(R):
     scene, cams = sg.config_scene(1)
     gs = R.GESScene.from_arrays(scene)

@@ -230,15 +230,16 @@ def test_culled_equals_brute_force_bitwise(oracle_lib, seed):
 
 def test_discs_at_and_behind_the_camera_brute_force_and_closed_form(oracle_lib):
     """Discs reaching through the near plane from behind the camera, one
-    wholly behind it and one edge-on: the culled render equals brute force
-    bitwise, and where the wall in the plane x = 0.05 wins, its depth is the
+    wholly behind it and one edge-on, and 2D-Gaussian splats reaching back
+    through it: the culled render equals brute force bitwise, and where the wall in the plane x = 0.05 wins, its depth is the
     ray-plane hit z = 0.05 fx / (u + 1/2 - cx) (a pixel ray (du, dv, 1)
     meets x = 0.05 at t = 0.05 / du)."""
     import camera_discs as cd
     cam, base = cd.camera(), cd.background()
     n0 = base.n_surfels
-    for discs, seed in ((cd.walls(), 37), (cd.tilted(), 38)):
-        sc = cd.with_discs(base, discs, seed)
+    scenes = [cd.with_discs(base, cd.walls(), 37), cd.with_discs(base, cd.tilted(), 38)]
+    scenes += [cd.with_splats(cd.flat(base), [sp], 40 + k) for k, sp in enumerate(cd.splats())]
+    for sc in scenes:
         a = oracle_lib.render(sc, cam, culled=True)
         b = oracle_lib.render(sc, cam, culled=False)
         for k in a:
