@@ -65,6 +65,26 @@ def test_backward_crop_matches_oracle(R, mode):
         assert np.all(gpu["s_sh"] == 0)
 
 
+def test_backward_discs_at_and_behind_the_camera(R):
+    """Gradients with the hand-placed discs at and behind the camera (their
+    SH gradients come from the pixels they win; the Gaussians behind the
+    walls fail the depth test) and with 2D-Gaussian splats reaching back
+    through the near plane (Sec. 4.2; Sec. 6.4)."""
+    import camera_discs as cd
+    cam, base = cd.camera(), cd.background()
+    g = np.random.default_rng(12).standard_normal((3, cam.height, cam.width))
+    keys = ["g_pos", "g_rot", "g_scale", "g_opac", "g_sh", "s_sh"]
+    scenes = [cd.with_discs(base, cd.walls(), 37), cd.with_discs(base, cd.tilted(), 38)]
+    scenes += [cd.with_splats(cd.flat(base), [sp], 40 + k) for k, sp in enumerate(cd.splats())]
+    for sc in scenes:
+        ref = oracle.backward(sc, cam, g)
+        gpu, _ = _grads_gpu(R, sc, cam, g)
+        _check(gpu, ref, keys, sc, cam)
+    # the walls' SH gradients are not trivially zero
+    ref = oracle.backward(scenes[0], cam, g)
+    assert np.abs(ref["s_sh"][base.n_surfels]).max() > 1.0
+
+
 def test_backward_parity_workload(R):
     scene, cams = sg.config_scene(0)
     g = np.random.default_rng(11).standard_normal((3, 128, 128))
