@@ -81,6 +81,38 @@ def test_batch_raster_2d_gaussians(R):
     gb.close()
 
 
+def test_batch_camera_discs_match_oracle(R):
+    """The hand-placed discs at and behind the camera, and 2D splats reaching
+    back through the near plane, through the batch graph (its own set-up and
+    colour-pass kernels): two views of each scene, each against the oracle
+    with the id map the batch writes."""
+    import torch
+    import oracle
+    import camera_discs as cd
+    from parity import compare
+    cam0 = cd.camera()
+    w2c = np.concatenate([np.eye(3), np.array([[0.01], [-0.005], [0.0]])], 1).astype(np.float32)
+    cam1 = sg.Camera(cam0.width, cam0.height, cam0.fx, cam0.fy, cam0.cx, cam0.cy, w2c)
+    base = cd.background()
+    scenes = [cd.with_discs(base, cd.walls(), 37), cd.with_splats(cd.flat(base), cd.splats(), 40)]
+    for sc in scenes:
+        gs = R.GESScene.from_arrays(sc)
+        b = R.GESBatch([gs], [cam0, cam1])
+        ids = [torch.empty((cam0.height, cam0.width), dtype=torch.int32, device="cuda") for _ in range(2)]
+        for v in range(2):
+            b.set_id_output(v, ids[v])
+        b.launch()
+        b.sync()
+        for v, cam in enumerate((cam0, cam1)):
+            ref = oracle.render(sc, cam)
+            res = compare(sc, cam, dict(rgb=b.rgb[v], depth=b.depth[v], id=ids[v]), ref, max_masked=0.1)
+            assert res["pass"], res
+            single = R.render(gs, cam)
+            assert (b.rgb[v] == single["rgb"]).all() and (b.depth[v] == single["depth"]).all(), v
+        b.close()
+        gs.close()
+
+
 def test_timed_orbit_path_matches_oracle(R):
     """The benchmark's own path: a batch graph over views of the 1M-surfel /
     300k-Gaussian 1080p orbit.  One view against the oracle directly (colour,
