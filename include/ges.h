@@ -61,9 +61,13 @@ typedef enum {
     GES_ERR_INVALID_ARG = 1,   /* null pointer, bad size, bad enum, zero-norm quaternion */
     GES_ERR_CUDA = 2,          /* a CUDA runtime call failed (message says which) */
     GES_ERR_OOM = 3,           /* scratch allocation failed */
-    GES_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up */
-    GES_ERR_INTERNAL = 5,      /* a device-side consistency check failed */
-    GES_ERR_UNSUPPORTED = 6,   /* no usable CUDA device of the required architecture */
+    GES_ERR_TIMEOUT = 4,       /* reserved: no call waits on device-side progress */
+    GES_ERR_INTERNAL = 5,      /* a device-side consistency check failed (tile lists
+                                  that kept overflowing after they were grown) */
+    GES_ERR_UNSUPPORTED = 6,   /* no usable CUDA device of the required architecture, or
+                                  a case a call does not take (batch views beyond its
+                                  tile limit or of mixed Gaussian kinds, 2D Gaussians in
+                                  ges_render_noalloc); the message says which */
     GES_ERR_CAPACITY = 7       /* fixed-capacity (graph) buffers were too small */
 } ges_status;
 
