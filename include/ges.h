@@ -358,15 +358,18 @@ GES_API ges_status ges_count_fragments(ges_scene *scene, const ges_camera *cam, 
 
 /* A batch: a fixed set of views (each a camera on one of several scenes,
  * uneven sizes allowed) rendered by one CUDA graph.  Every phase of the
- * render -- preprocess, binning, fill, raster -- is a single launch over all
- * views; the raster is persistent and hands out (view, tile) work items, so
- * small and large views balance across the GPU.  Per-view semantics are
- * exactly those of ges_render_ex.
+ * render is launched once for all views: the preprocess (when a scene has
+ * several views, first a colour pass that evaluates Eq. 1 for all of them
+ * from one read of each SH row; then one set-up launch per primitive kind),
+ * the scans, the fill and the raster.  The raster is persistent and hands
+ * out (view, tile) work items, so small and large views balance across the
+ * GPU.  Per-view semantics are exactly those of ges_render_ex.
  *
  * ges_batch_create renders every view once through the scene's own path to
  * size the tile lists (x1.5 headroom), allocates the batch's own scratch,
- * then autotunes the primitives per preprocess CTA and the persistent raster
- * grid by timing each candidate graph, and keeps the fastest.
+ * then autotunes the primitives per preprocess CTA, the persistent raster's
+ * CTAs per SM and the binning tile (16x16, 32x8 or 8x32 pixels) by timing
+ * each candidate graph, and keeps the fastest.
  * Pointers
  * (scenes' arrays, outputs) are baked into the graph and must stay valid
  * until ges_batch_destroy.  Images must have at most 32768 tiles of 16x16
