@@ -871,13 +871,23 @@ cudaError_t capture_exec(ges_batch *b, const BatchPlan &P, const OptParams &O, b
     const size_t status_words = (size_t)b->n * ST_WORDS + 16;
     cudaGraph_t g = nullptr;
     *out = nullptr;
+    (void)cudaGetLastError();   // an earlier call's error is not this capture's (launch_batch reports the last error)
     cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    cudaMemcpyAsync(b->d_table, b->h_table, sizeof(BatchView) * b->n, cudaMemcpyHostToDevice, b->stream);
-    cudaMemsetAsync(b->d_status, 0, status_words * 4, b->stream);
-    launch_batch(b->d_table, P, O, b->d_status + (size_t)b->n * ST_WORDS, b->stream, b->phase, ids);
-    cudaMemcpyAsync(b->h_status, b->d_status, status_words * 4, cudaMemcpyDeviceToHost, b->stream);
-    if ((e = cudaStreamEndCapture(b->stream, &g)) != cudaSuccess) return e;
+    // the capture is ended whatever fails inside it, so the stream stays usable;
+    // the first error of the sequence is the one reported
+    cudaError_t first = cudaMemcpyAsync(b->d_table, b->h_table, sizeof(BatchView) * b->n, cudaMemcpyHostToDevice,
+                                        b->stream);
+    if (first == cudaSuccess) first = cudaMemsetAsync(b->d_status, 0, status_words * 4, b->stream);
+    if (first == cudaSuccess)
+        first = launch_batch(b->d_table, P, O, b->d_status + (size_t)b->n * ST_WORDS, b->stream, b->phase, ids);
+    if (first == cudaSuccess)
+        first = cudaMemcpyAsync(b->h_status, b->d_status, status_words * 4, cudaMemcpyDeviceToHost, b->stream);
+    e = cudaStreamEndCapture(b->stream, &g);
+    if (first != cudaSuccess || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return first != cudaSuccess ? first : e;
+    }
     e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     return e;
@@ -1111,6 +1121,14 @@ static ges_status batch_create(ges_scene *const *scenes, const ges_camera *cams,
     // autotune: capture a graph per candidate, time it, keep the fastest
     float best_ms = 1e30f;
     int cand = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    BATCH_CUDA(cudaEventCreate(&e0));
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        batch_release(b);
+        return cuda_fail(e, "cudaEventCreate");
+    }
+    auto drop_events = [&]() { cudaEventDestroy(e0); cudaEventDestroy(e1); };
     // raster candidates: resident CTAs per SM (the 4-sample kernels are built
     // for one CTA fewer)
     const int d = O.samples == 4 ? 1 : 0;
@@ -1132,27 +1150,30 @@ static ges_status batch_create(ges_scene *const *scenes, const ges_camera *cams,
                 P.max_T = std::max(P.max_T, b->views[v].T);
             }
             std::memcpy(b->h_table, b->views.data(), sizeof(BatchView) * n_views);
-            BATCH_CUDA(upload_prep_map(b, P));
+            if ((e = upload_prep_map(b, P)) != cudaSuccess) {
+                drop_events();
+                batch_release(b);
+                return cuda_fail(e, "upload_prep_map");
+            }
             cudaGraphExec_t ex = nullptr;
             e = capture_exec(b, P, O, false, &ex);
             if (e != cudaSuccess) {
+                drop_events();
                 batch_release(b);
-                return cuda_fail(e, "cudaGraphInstantiate");
+                return cuda_fail(e, "batch graph capture");
             }
-            cudaEvent_t e0, e1;
-            cudaEventCreate(&e0);
-            cudaEventCreate(&e1);
-            cudaGraphLaunch(ex, b->stream);
-            cudaEventRecord(e0, b->stream);
-            for (int k = 0; k < 3; ++k) cudaGraphLaunch(ex, b->stream);
-            cudaEventRecord(e1, b->stream);
-            e = cudaStreamSynchronize(b->stream);
+            // one untimed replay, then three timed ones
+            e = cudaGraphLaunch(ex, b->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+            for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaGraphLaunch(ex, b->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+            const cudaError_t es = cudaStreamSynchronize(b->stream);
+            if (e == cudaSuccess) e = es;
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
             if (e != cudaSuccess) {
                 cudaGraphExecDestroy(ex);
+                drop_events();
                 batch_release(b);
                 return cuda_fail(e, "batch launch");
             }
@@ -1178,6 +1199,7 @@ static ges_status batch_create(ges_scene *const *scenes, const ges_camera *cams,
             }
         }
     }
+    drop_events();
     if (!b->exec) {
         batch_release(b);
         return fail(GES_ERR_CAPACITY, "every configuration overflowed the batch's tile lists");
@@ -1199,10 +1221,10 @@ static ges_status batch_create(ges_scene *const *scenes, const ges_camera *cams,
     b->info.tuned_ms = best_ms;
     b->info.h2d_bytes = (int64_t)(sizeof(BatchView) * n_views);
     b->info.d2h_bytes = (int64_t)(status_words * 4);
-#undef BATCH_CUDA
     // one checked launch with the chosen configuration
-    cudaGraphLaunch(b->exec, b->stream);
-    cudaEventRecord(b->done, b->stream);
+    BATCH_CUDA(cudaGraphLaunch(b->exec, b->stream));
+    BATCH_CUDA(cudaEventRecord(b->done, b->stream));
+#undef BATCH_CUDA
     *out = b;
     r = ges_batch_sync(b);
     std::memset(&b->profile, 0, sizeof b->profile);
