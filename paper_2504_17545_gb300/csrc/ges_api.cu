@@ -1140,7 +1140,10 @@ static ges_status batch_create(ges_scene *const *scenes, const ges_camera *cams,
         for (int pi = 0; pi < (tune ? 2 : 1); ++pi) {
             const int per_sm = kPerSm[pi];
             batch_layout(b, S, Cs, R, (unsigned char *)b->arena);
-            BatchPlan P{n_views, 0, 0, 0, 0, 0, 0, sms * per_sm, S[0].gdim, nullptr, nullptr};
+            BatchPlan P{};
+            P.n = n_views;
+            P.raster_ctas = sms * per_sm;
+            P.gdim = S[0].gdim;
             for (int v = 0; v < n_views; ++v) {
                 P.total_tiles += b->views[v].T;
                 P.total_prep += b->views[v].B.Ps + b->views[v].B.Pg;
