@@ -34,6 +34,24 @@ def camera_struct(cam) -> N.ges_camera:
     return c
 
 
+def _arg(t, name: str, dtype, numel: int, dev) -> torch.Tensor:
+    """A caller's tensor that a kernel will read or write: it must sit on the
+    scene's device, have the dtype and exactly the element count the kernel
+    addresses, and be contiguous (the ABI takes a bare pointer).  Raises
+    ValueError before anything is launched."""
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name}: expected a tensor, got {type(t).__name__}")
+    if t.device != dev:
+        raise ValueError(f"{name}: on {t.device}, the scene is on {dev}")
+    if t.dtype != dtype:
+        raise ValueError(f"{name}: dtype {t.dtype}, expected {dtype}")
+    if t.numel() != numel:
+        raise ValueError(f"{name}: {t.numel()} elements (shape {tuple(t.shape)}), expected {numel}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: not contiguous")
+    return t
+
+
 def opts_struct(opts: Optional[dict]) -> N.ges_render_opts:
     o = N.ges_default_opts()
     for k, v in (opts or {}).items():
@@ -206,7 +224,7 @@ def render_translucent(scene: GESScene, cam, w: torch.Tensor, front_first: bool 
     c = camera_struct(cam)
     dev = scene.t["s_pos"].device
     H, W = c.height, c.width
-    wt = w.contiguous().float()
+    wt = _arg(w.contiguous().float(), "w", torch.float32, scene.n_surfels, dev)
     out = dict(rgb=torch.empty((3, H, W), device=dev), T=torch.empty((H, W), device=dev),
                front=torch.empty((H, W), device=dev, dtype=torch.int32),
                last=torch.empty((H, W), device=dev, dtype=torch.int32), Tlast=torch.empty((H, W), device=dev))
@@ -233,8 +251,11 @@ def render_translucent_backward(scene: GESScene, cam, w: torch.Tensor, fwd: dict
     gr = N.ges_tgrads()
     for k in ("s_pos", "s_rot", "s_scale", "s_w", "s_sh"):
         setattr(gr, k, g[k].data_ptr() if g[k].numel() else None)
-    wt = w.contiguous().float()
-    dl = dL_drgb.contiguous().float()
+    H, W = c.height, c.width
+    wt = _arg(w.contiguous().float(), "w", torch.float32, n, dev)
+    dl = _arg(dL_drgb.contiguous().float(), "dL_drgb", torch.float32, 3 * H * W, dev)
+    for k, dt in (("T", torch.float32), ("front", torch.int32), ("last", torch.int32), ("Tlast", torch.float32)):
+        _arg(fwd[k], f"fwd[{k!r}]", dt, H * W, dev)
     scene.bind_stream()
     N.ges_render_translucent_backward(scene.handle, c, opts_struct(opts), wt.data_ptr() if wt.numel() else 0,
                                       front_first, dl.data_ptr(), fwd["T"].data_ptr(), fwd["front"].data_ptr(),
@@ -246,7 +267,10 @@ def contribution_scores(scene: GESScene, cam, fwd: dict, opts: Optional[dict] = 
     """Contribution score of each Gaussian (Sec. 4.2, Eq. 9) from a render's
     depth and aux outputs."""
     c = camera_struct(cam)
-    out = torch.empty((scene.n_gaussians,), device=scene.t["g_pos"].device)
+    dev = scene.t["g_pos"].device
+    for k in ("depth", "aux"):
+        _arg(fwd[k], f"fwd[{k!r}]", torch.float32, c.height * c.width, dev)
+    out = torch.empty((scene.n_gaussians,), device=dev)
     scene.bind_stream()
     N.ges_contribution_scores(scene.handle, c, opts_struct(opts), fwd["depth"].data_ptr(), fwd["aux"].data_ptr(),
                               out.data_ptr() if out.numel() else 0)
@@ -269,9 +293,13 @@ def render_backward(scene: GESScene, cam, fwd: dict, dL_drgb: torch.Tensor, opts
     gr = N.ges_grads()
     for k in _GRAD_KEYS:
         setattr(gr, k, g[k].data_ptr() if g[k].numel() else None)
-    dl = dL_drgb.contiguous().float()
+    H, W, o = c.height, c.width, opts_struct(opts)
+    dl = _arg(dL_drgb.contiguous().float(), "dL_drgb", torch.float32, 3 * H * W, dev)
+    for k, dt, n in (("rgb", torch.float32, 3 * H * W), ("depth", torch.float32, H * W),
+                     ("id", torch.int32, o.samples * H * W), ("aux", torch.float32, H * W)):
+        _arg(fwd[k], f"fwd[{k!r}]", dt, n, dev)
     scene.bind_stream()
-    N.ges_render_backward(scene.handle, c, opts_struct(opts), dl.data_ptr(), fwd["rgb"].data_ptr(),
+    N.ges_render_backward(scene.handle, c, o, dl.data_ptr(), fwd["rgb"].data_ptr(),
                           fwd["depth"].data_ptr(), fwd["id"].data_ptr(), fwd["aux"].data_ptr(), gr)
     return g
 
@@ -312,6 +340,12 @@ def render_batch(scenes: Sequence[GESScene], cams: Sequence, scene_of_view: Opti
     if outputs is None:
         outputs = [(torch.empty((3, c.height, c.width), device=dev), torch.empty((c.height, c.width), device=dev))
                    for c in cstructs]
+    if len(outputs) != n:
+        raise ValueError(f"outputs: {len(outputs)} pairs for {n} views")
+    for v, (c, (rgb, depth)) in enumerate(zip(cstructs, outputs)):
+        _arg(rgb, f"outputs[{v}][0]", torch.float32, 3 * c.height * c.width, dev)
+        if depth is not None:
+            _arg(depth, f"outputs[{v}][1]", torch.float32, c.height * c.width, dev)
     scenes[0].bind_stream()
     N.ges_render_batch([s.handle for s in scenes], cstructs, list(scene_of_view), opts_struct(opts),
                        [o[0].data_ptr() for o in outputs], [o[1].data_ptr() if o[1] is not None else 0
@@ -330,6 +364,8 @@ class GESBatch:
         self.scenes = list(scenes)
         self.scene_of_view = list(scene_of_view) if scene_of_view is not None else [0] * n
         cs = [camera_struct(c) for c in cams]
+        self._sizes = [(c.height, c.width) for c in cs]
+        self._samples = opts_struct(opts).samples
         dev = self.scenes[0].t["s_pos"].device
         self.rgb = [torch.empty((3, c.height, c.width), device=dev) for c in cs]
         self.depth = [torch.empty((c.height, c.width), device=dev) for c in cs] if with_depth else None
@@ -351,6 +387,14 @@ class GESBatch:
         """Also write view ``view``'s surfel id map (int32 [samples,H,W]) and
         W_G (float32 [H,W]) in the following launches (None: not written).
         The tensors must stay alive while they are set."""
+        if not 0 <= view < len(self._sizes):
+            raise ValueError(f"view {view} out of range (0..{len(self._sizes) - 1})")
+        H, W = self._sizes[view]
+        dev = self.rgb[0].device
+        if out_id is not None:
+            _arg(out_id, "out_id", torch.int32, self._samples * H * W, dev)
+        if aux is not None:
+            _arg(aux, "aux", torch.float32, H * W, dev)
         self._id_keep = getattr(self, "_id_keep", {})
         self._id_keep[view] = (out_id, aux)
         N.ges_batch_set_id_output(self.handle, view, out_id.data_ptr() if out_id is not None else 0,
