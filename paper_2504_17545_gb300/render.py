@@ -63,6 +63,45 @@ def opts_struct(opts: Optional[dict]) -> N.ges_render_opts:
     return o
 
 
+def _scene_layout(t: Dict[str, torch.Tensor], sh_degree: int) -> int:
+    """Check the scene tensors against the ABI's layout (N surfels and M
+    Gaussians taken from the positions, K = (sh_degree + 1)^2): one device,
+    positions float32 [N,3] / [M,3], rotations [.,4], surfel scales [N,2],
+    Gaussian scales [M,3] (or [M,2]: 2D Gaussians), opacities [M], SH [.,K,3],
+    one dtype for rotations, scales and opacities and one for both SH arrays.
+    Returns the Gaussian kind (3 or 2); raises ValueError / TypeError before the
+    library sees a pointer whose array is shorter than its kernels read."""
+    if not 0 <= int(sh_degree) <= 3:
+        raise ValueError(f"sh_degree {sh_degree} outside 0..3")
+    K = (int(sh_degree) + 1) ** 2
+    dev = t["s_pos"].device
+    for k in _SCENE_KEYS:
+        if t[k].device != dev:
+            raise ValueError(f"{k} is on {t[k].device}, s_pos on {dev}")
+    if t["s_pos"].dtype != torch.float32 or t["g_pos"].dtype != torch.float32:
+        raise TypeError("positions are float32")
+    attr = t["s_rot"].dtype
+    for k in ("s_scale", "g_rot", "g_scale", "g_opac"):
+        if t[k].dtype != attr:
+            raise TypeError("rotations, scales and opacities must share one dtype")
+    if attr not in _DTYPES or t["s_sh"].dtype not in _DTYPES:
+        raise TypeError("attributes are float32, float16 or bfloat16")
+    if t["s_sh"].dtype != t["g_sh"].dtype:
+        raise TypeError("surfel and Gaussian SH must share one dtype")
+    for k in ("s_pos", "g_pos"):
+        if t[k].dim() != 2 or t[k].shape[1] != 3:
+            raise ValueError(f"{k} must be [n,3], got {tuple(t[k].shape)}")
+    n, m = t["s_pos"].shape[0], t["g_pos"].shape[0]
+    gs = t["g_scale"]
+    gdim = 2 if gs.dim() == 2 and gs.shape[1] == 2 else 3
+    want = {"s_rot": (n, 4), "s_scale": (n, 2), "s_sh": (n, K, 3), "g_rot": (m, 4), "g_scale": (m, gdim),
+            "g_opac": (m,), "g_sh": (m, K, 3)}
+    for k, shape in want.items():
+        if tuple(t[k].shape) != shape:
+            raise ValueError(f"{k} must be {list(shape)}, got {list(t[k].shape)}")
+    return gdim
+
+
 class GESScene:
     """A GES scene resident in device memory (tensors owned here) and the
     library's handle that views them."""
@@ -78,18 +117,9 @@ class GESScene:
             if not v.is_cuda:
                 raise ValueError(f"{k} must be a CUDA tensor")
             self.t[k] = v.contiguous()
+        self.gauss_dim = _scene_layout(self.t, self.sh_degree)
         self.g_filter3d = self._check_filter(g_filter3d)
-        attr = self.t["s_rot"].dtype
-        for k in ("s_scale", "g_rot", "g_scale", "g_opac"):
-            if self.t[k].dtype != attr:
-                raise TypeError("rotations, scales and opacities must share one dtype")
-        if self.t["s_sh"].dtype != self.t["g_sh"].dtype:
-            raise TypeError("surfel and Gaussian SH must share one dtype")
-        if self.t["s_pos"].dtype != torch.float32 or self.t["g_pos"].dtype != torch.float32:
-            raise TypeError("positions are float32")
-        gs = self.t["g_scale"]
-        self.gauss_dim = 2 if gs.dim() == 2 and gs.shape[1] == 2 else 3
-        self.attr_dtype = _DTYPES[attr]
+        self.attr_dtype = _DTYPES[self.t["s_rot"].dtype]
         self.sh_dtype = _DTYPES[self.t["s_sh"].dtype]
         self._desc = self._make_desc()
         self.handle = N.ges_create_scene(self._desc)
@@ -97,8 +127,8 @@ class GESScene:
     def _check_filter(self, f: Optional[torch.Tensor]) -> Optional[torch.Tensor]:
         if f is None:
             return None
-        if not f.is_cuda or f.dtype != torch.float32 or tuple(f.shape) != (self.n_gaussians,):
-            raise ValueError("g_filter3d must be a float32 CUDA tensor of shape [M]")
+        if f.device != self.t["g_pos"].device or f.dtype != torch.float32 or tuple(f.shape) != (self.n_gaussians,):
+            raise ValueError("g_filter3d must be a float32 tensor of shape [M] on the scene's device")
         return f.contiguous()
 
     @classmethod
@@ -140,14 +170,27 @@ class GESScene:
     def update(self, **tensors: torch.Tensor):
         """Swap some attribute tensors (same dtypes) and re-point the handle.
         ``g_filter3d=None`` removes the Mip-GES 3D filter."""
+        t = dict(self.t)
         for k, v in tensors.items():
             if k == "g_filter3d":
                 continue
             if k not in _SCENE_KEYS:
                 raise KeyError(k)
-            self.t[k] = v.contiguous()
-        if "g_filter3d" in tensors:
-            self.g_filter3d = self._check_filter(tensors["g_filter3d"])
+            t[k] = v.contiguous()
+        # checked before anything changes: a rejected update leaves the scene as it was
+        if self.t["s_rot"].dtype != t["s_rot"].dtype or self.t["s_sh"].dtype != t["s_sh"].dtype:
+            raise TypeError("an update keeps the scene's attribute and SH dtypes")
+        gdim = _scene_layout(t, self.sh_degree)
+        old = (self.t, self.gauss_dim, self.g_filter3d)
+        self.t, self.gauss_dim = t, gdim
+        try:
+            if "g_filter3d" in tensors:
+                self.g_filter3d = self._check_filter(tensors["g_filter3d"])
+            elif self.g_filter3d is not None:
+                self._check_filter(self.g_filter3d)     # the kept filter must still fit M
+        except ValueError:
+            self.t, self.gauss_dim, self.g_filter3d = old
+            raise
         self._desc = self._make_desc()
         N.ges_scene_update(self.handle, self._desc)
 

@@ -103,3 +103,37 @@ def test_batch_id_outputs_are_checked(calls):
     with pytest.raises(ValueError, match="out of range"):
         b.set_id_output(2, None)
     assert len(calls) == 2
+
+
+def _scene_tensors(n=NS, m=NG, deg=3, gdim=3):
+    k = (deg + 1) ** 2
+    z = torch.zeros
+    return dict(s_pos=z(n, 3), s_rot=z(n, 4), s_scale=z(n, 2), s_sh=z(n, k, 3), g_pos=z(m, 3), g_rot=z(m, 4),
+                g_scale=z(m, gdim), g_opac=z(m), g_sh=z(m, k, 3))
+
+
+def test_scene_layout_is_checked_against_the_abi():
+    assert R._scene_layout(_scene_tensors(), 3) == 3
+    assert R._scene_layout(_scene_tensors(gdim=2), 3) == 2
+    assert R._scene_layout(_scene_tensors(n=0, m=0, deg=0), 0) == 3
+    bad = [("s_sh", torch.zeros(NS, 9, 3)), ("s_rot", torch.zeros(NS - 1, 4)), ("g_opac", torch.zeros(NG, 1)),
+           ("g_scale", torch.zeros(NG, 4)), ("g_pos", torch.zeros(NG, 4)), ("g_sh", torch.zeros(NG + 1, K, 3))]
+    for k, v in bad:
+        t = _scene_tensors()
+        t[k] = v
+        with pytest.raises(ValueError, match=k):
+            R._scene_layout(t, 3)
+    t = _scene_tensors()
+    t["g_opac"] = torch.zeros(NG, dtype=torch.float16)
+    with pytest.raises(TypeError, match="one dtype"):
+        R._scene_layout(t, 3)
+    t = _scene_tensors()
+    t["g_pos"] = torch.zeros(NG, 3, dtype=torch.float16)
+    with pytest.raises(TypeError, match="float32"):
+        R._scene_layout(t, 3)
+    t = _scene_tensors()
+    t["g_sh"] = torch.zeros(NG, K, 3, device="meta")
+    with pytest.raises(ValueError, match="g_sh"):
+        R._scene_layout(t, 3)
+    with pytest.raises(ValueError, match="sh_degree"):
+        R._scene_layout(_scene_tensors(), 4)
