@@ -255,6 +255,34 @@ def test_discs_at_and_behind_the_camera_brute_force_and_closed_form(oracle_lib):
     assert not (a["id"] == n0 + 3).any()           # edge-on: no area on screen
 
 
+def test_frame_tilt_moves_depth_by_the_ratio_bound(oracle_lib):
+    """The depth tolerance's frame term: tilting a disc's frame by eps about
+    an axis through its centre P moves the hit X = z d by at most
+    eps |X - P| / (|X| |cos|) relative (first order: t = n.P / n.d, so
+    dz/z = delta.(P - X) / n.P and |n.P| = |X| |cos|).  Checked in FP64 on the
+    wall whose centre is 3.1 behind the camera (|X - P| / |X| about 45), where
+    the bound must also be nearly reached."""
+    import camera_discs as cd
+    cam = cd.camera()
+    sc = f64(cd.with_discs(cd.background().subset(s_idx=np.zeros(0, int)), cd.walls()[:1], 37))
+    eps = 1e-7
+    tilted = f64(sc)
+    tilted.s_rot = _quat_mul(sc.s_rot[0], np.array([[math.cos(eps / 2), 0.0, math.sin(eps / 2), 0.0]]))
+    jj, ii = np.nonzero(oracle_lib.render(sc, cam)["id"] == 0)
+    assert jj.size > 1000
+    z0, _, nd, ok = oracle_lib.surfel_eval(sc, cam, ii, jj, np.zeros(ii.size, int))
+    z1, _, _, ok1 = oracle_lib.surfel_eval(tilted, cam, ii, jj, np.zeros(ii.size, int))
+    keep = (ok != 0) & (ok1 != 0)
+    d = np.stack([(ii + 0.5 - cam.cx) / cam.fx, (jj + 0.5 - cam.cy) / cam.fy, np.ones(ii.size)], 1)[keep]
+    X = z0[keep, None] * d
+    ratio = np.linalg.norm(X - sc.s_pos[0], axis=1) / np.linalg.norm(X, axis=1)
+    rel = np.abs(z1[keep] - z0[keep]) / z0[keep]
+    bound = eps * ratio / np.abs(nd[keep])
+    assert ratio.min() > 10.0                          # far outside the 0.3 of small discs
+    assert np.all(rel <= bound * (1 + 1e-6))
+    assert (rel / bound).max() > 0.5                   # the ratio term is needed, not just safe
+
+
 def test_culled_equals_brute_force_parity_workload(oracle_lib):
     sc, cams = sg.config_scene(0)
     a = oracle_lib.render(sc, cams[0], culled=True)
